@@ -1,0 +1,148 @@
+"""Adaptive cross approximation that rebuilds the HT tensor from sampled entries (the
+HTACA step of SLAR, Sec. 3.1 "SLAR(F; a, dt, eps)" and Sec. 1).
+
+Test infrastructure: part of the FP64 oracle, never called by the CUDA path.
+
+The paper defers HTACA's details to earlier work; it states only that entries are sampled
+"typically along fibers" without forming the full tensor and that the final step is the
+HSVD truncation of Supp. B.1.  The reading implemented here (deterministic):
+
+1. Cross approximation with partial pivoting of the matricisation A = F_(x | v) at the
+   root split (rows = spatial multi-index, columns = velocity multi-index).  Every step
+   samples one full row fibre and one full column fibre of A:
+     r = A(i_k, :) - sum_{l<k} u_l[i_k] v_l,   j_k = argmax |r|,  v_k = r / r[j_k],
+     u_k = A(:, j_k) - sum_{l<k} v_l[j_k] u_l,  i_{k+1} = argmax_{i not used} |u_k[i]|.
+   Start row i_1 = 0 (f > 0 makes every row non-zero).  Stop when
+   ||u_k|| ||v_k|| <= eps ||A_k||_F (running estimate) or k = cap, or when the residual
+   row vanishes.  Arg-max ties: values within a relative 1e-10 of the maximum are
+   treated as equal and the lowest index wins, so that pivots are reproducible across
+   implementations that round differently.
+2. The factors A ~ U V^T are embedded exactly as an HT: d = 2: leaves U, V and root I;
+   d = 4: identity leaves, B12[a,b,p] = U[(a,b),p], B34[c,e,q] = V[(c,e),q], root I.
+3. HSVD truncation (``ht.truncate``) with eps and the rank cap gives the new HT, whose
+   leaf columns 0 are the leading mode singular vectors needed by the LoMaC weight.
+
+The number of sampled entries per call is sum_k (M1 + M2) = k (M1 + M2).
+"""
+from __future__ import annotations
+
+from typing import Callable, Optional
+
+import numpy as np
+
+from . import ht as htmod
+
+TIE_RTOL = 1e-10
+
+
+def argmax_tie(a: np.ndarray, excluded: Optional[np.ndarray] = None) -> int:
+    """Index of max |a| (excluded positions ignored); near-ties go to the lowest index."""
+    m = np.abs(a).astype(np.float64)
+    if excluded is not None:
+        m = m.copy()
+        m[excluded] = -1.0
+    top = m.max()
+    if top < 0.0:
+        return -1
+    cand = np.nonzero(m >= top * (1.0 - TIE_RTOL))[0]
+    return int(cand[0])
+
+
+def aca(row_fn: Callable[[int], np.ndarray], col_fn: Callable[[int], np.ndarray], M1: int, M2: int,
+        eps: float, kmax: int, pivots=None):
+    """Partially pivoted cross approximation A ~ U V^T.
+
+    row_fn(i) -> A(i, :) (length M2) and col_fn(j) -> A(:, j) (length M1) sample fibres.
+    ``pivots`` (list of (i, j)) replays a given pivot sequence instead of choosing.
+    Returns dict(U (M1,k), V (M2,k), I, J, entries)."""
+    Us, Vs, I, J = [], [], [], []
+    used_r = np.zeros(M1, dtype=bool)
+    used_c = np.zeros(M2, dtype=bool)
+    normA2 = 0.0
+    i = 0 if pivots is None else pivots[0][0]
+    n_entries = 0
+    kmax = min(kmax, M1, M2)
+    for k in range(kmax):
+        if pivots is not None:
+            if k >= len(pivots):
+                break
+            i = pivots[k][0]
+        r = row_fn(i).astype(np.float64)
+        n_entries += M2
+        for l in range(len(Us)):
+            r = r - Us[l][i] * Vs[l]
+        used_r[i] = True
+        if pivots is None:
+            if np.max(np.abs(np.where(used_c, 0.0, r))) == 0.0:
+                break
+            j = argmax_tie(r, used_c)
+        else:
+            j = pivots[k][1]
+        piv = r[j]
+        if piv == 0.0:
+            break
+        v = r / piv
+        c = col_fn(j).astype(np.float64)
+        n_entries += M1
+        for l in range(len(Us)):
+            c = c - Vs[l][j] * Us[l]
+        used_c[j] = True
+        u = c
+        # running Frobenius norm of the approximation (standard ACA estimate)
+        cross = 0.0
+        for l in range(len(Us)):
+            cross += float(Us[l] @ u) * float(Vs[l] @ v)
+        nu, nv = float(np.linalg.norm(u)), float(np.linalg.norm(v))
+        normA2 = normA2 + 2.0 * cross + (nu * nv) ** 2
+        Us.append(u)
+        Vs.append(v)
+        I.append(i)
+        J.append(j)
+        if pivots is None:
+            if nu * nv <= eps * np.sqrt(max(normA2, 0.0)):
+                break
+            i = argmax_tie(u, used_r)
+    k = len(Us)
+    U = np.stack(Us, axis=1) if k else np.zeros((M1, 0))
+    V = np.stack(Vs, axis=1) if k else np.zeros((M2, 0))
+    return dict(U=U, V=V, I=I, J=J, entries=n_entries)
+
+
+def embed(U: np.ndarray, V: np.ndarray, N) -> htmod.HT:
+    """Exact HT of U V^T on the root split (step 2 of the module docstring)."""
+    k = U.shape[1]
+    if len(N) == 2:
+        return htmod.HT(U=[U.copy(), V.copy()], Broot=np.eye(k))
+    B12 = U.reshape(N[0], N[1], k)
+    B34 = V.reshape(N[2], N[3], k)
+    return htmod.HT(U=[np.eye(N[0]), np.eye(N[1]), np.eye(N[2]), np.eye(N[3])],
+                    Broot=np.eye(k), B12=B12.copy(), B34=B34.copy())
+
+
+def htaca(entry_fn: Callable[[np.ndarray], np.ndarray], N, eps: float, cap: int,
+          pivots=None, return_info: bool = False):
+    """Build the HT of the tensor whose entries are entry_fn(idx (S, d)) from sampled row
+    and column fibres of the root-split matricisation, then truncate (module docstring)."""
+    d = len(N)
+    half = d // 2
+    Nl, Nr = N[:half], N[half:]
+    M1, M2 = int(np.prod(Nl)), int(np.prod(Nr))
+    left = np.stack(np.unravel_index(np.arange(M1), Nl), axis=1)
+    right = np.stack(np.unravel_index(np.arange(M2), Nr), axis=1)
+
+    def row_fn(i):
+        idx = np.concatenate([np.repeat(left[i:i + 1], M2, axis=0), right], axis=1)
+        return entry_fn(idx)
+
+    def col_fn(j):
+        idx = np.concatenate([left, np.repeat(right[j:j + 1], M1, axis=0)], axis=1)
+        return entry_fn(idx)
+
+    res = aca(row_fn, col_fn, M1, M2, eps, cap, pivots)
+    full = embed(res["U"], res["V"], N)
+    out, tinfo = htmod.truncate(full, eps, cap, return_info=True)
+    if return_info:
+        info = dict(aca_rank=res["U"].shape[1], pivots=list(zip(res["I"], res["J"])),
+                    entries=res["entries"], ranks=tinfo["ranks"])
+        return out, info
+    return out

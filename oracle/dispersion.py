@@ -1,0 +1,56 @@
+"""Linear dispersion relations used as physics pins of the Vlasov-Poisson oracle.
+
+Test infrastructure: part of the FP64 oracle, never called by the CUDA path.
+
+For a sum of drifting Maxwellians with densities n_s, drifts u_s and unit temperature,
+the electrostatic dielectric function (electron charge -1, omega_p = 1 for total density
+1, rescaling of Sec. 2.1) is
+
+    eps(k, w) = 1 + sum_s n_s (1 + zeta_s Z(zeta_s)) / k^2,   zeta_s = (w - k u_s)/(k sqrt 2),
+
+with the plasma dispersion function Z(z) = i sqrt(pi) w(z) (Faddeeva function).  A zero
+of eps gives the complex frequency; Im w is the amplitude growth (damping) rate of E.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import wofz
+
+
+def plasma_Z(z: complex) -> complex:
+    return 1j * math.sqrt(math.pi) * complex(wofz(z))
+
+
+def dielectric(k: float, w: complex, species) -> complex:
+    out = 1.0 + 0j
+    for n_s, u_s in species:
+        z = (w - k * u_s) / (k * math.sqrt(2.0))
+        out += n_s * (1.0 + z * plasma_Z(z)) / (k * k)
+    return out
+
+
+def root(k: float, w0: complex, species=((1.0, 0.0),), iters: int = 100) -> complex:
+    """Secant iteration for eps(k, w) = 0 from the initial guess w0."""
+    w_prev, w = w0, w0 * (1.0 + 1e-3) + 1e-3j
+    f_prev, f = dielectric(k, w_prev, species), dielectric(k, w, species)
+    for _ in range(iters):
+        if f == f_prev:
+            break
+        w_new = w - f * (w - w_prev) / (f - f_prev)
+        w_prev, f_prev = w, f
+        w, f = w_new, dielectric(k, w_new, species)
+        if abs(w - w_prev) < 1e-14:
+            break
+    return w
+
+
+def landau_rate(k: float = 0.5) -> complex:
+    """Least-damped Langmuir root of a unit Maxwellian."""
+    return root(k, 1.4 - 0.15j)
+
+
+def two_stream_rate(k: float, v0: float) -> complex:
+    """Unstable root of two half-density beams at +-v0."""
+    return root(k, 0.0 + 0.3j, species=((0.5, v0), (0.5, -v0)))

@@ -1,0 +1,170 @@
+"""SLAR, SLAR_VP (third-order commutator-free RK exponential integrator) and the
+LoMaC-coupled time step of the flowchart (Sec. 3.1, Eq. slarvp; Sec. 3.2.3 and the
+flowchart figure; Sec. 4 start-up with DIRK3 then BDF3).
+
+Test infrastructure: part of the FP64 oracle, never called by the CUDA path.
+
+Readings:
+* RKEI = CF3 of Celledoni, Marthinsen and Owren (2003):
+    Y2 = exp(dt/3 F(Y1)) Y1,  Y3 = exp(2dt/3 F(Y2)) Y1,
+    Y^{n+1} = exp(dt(-F(Y1)/12 + 3F(Y3)/4)) Y2,
+  with F(Y) the frozen-field advection operator of the field of Y.  The combination in
+  the last exponential is itself a frozen-field advection over tau = 2dt/3 with the field
+  E_c = -E1/8 + 9E3/8 (the advection operator is linear in v-speed and field).
+* Each exponential is one SLAR call (cross approximation of the SL-updated tensor,
+  then HSVD truncation).
+* The LoMaC state F^{n+1} = HT(F*) + separable correction is never truncated; the next
+  SLAR samples its entries (interpolation is linear, so both parts are interpolated with
+  the same weights).
+* Time stepping of the macroscopic system: DIRK3 (each stage: one SLAR_VP to the stage
+  time c_i dt from F^n, one JFNK) for the first two steps, fixed-step BDF3 afterwards.
+  Without LoMaC the step is F^{n+1} = F*.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field as dfield
+from typing import List, Optional
+
+import numpy as np
+
+from . import cross, field, lomac, macro, sl
+from .ht import HT, from_terms, truncate
+from .sl import PhaseGrid
+
+
+@dataclass
+class Params:
+    eps: float
+    cap: int
+    newton_tol: float = 1e-12
+    krylov_tol: float = 1e-4
+    krylov_restart: int = 30
+    newton_max: int = 20
+    krylov_max: int = 200
+    foot: str = "rk3"
+    delta: float = lomac.DELTA_DEFAULT
+    lomac: bool = True
+
+
+@dataclass
+class State:
+    F: HT
+    U: np.ndarray                      # conserved variables (dv+2, Nx)
+    hist: List[np.ndarray]             # previous U (most recent first), for BDF3
+    n_i: float
+    t: float = 0.0
+    step: int = 0
+
+
+@dataclass
+class StepStats:
+    entries: int = 0
+    ranks: list = dfield(default_factory=list)
+    newton: int = 0
+    krylov: int = 0
+    residual: float = 0.0
+    converged: bool = True
+    W: float = 0.0
+
+
+def init_state(factors, g: PhaseGrid, prm: Params) -> State:
+    """F^0 = HSVD-truncated HT of the separable initial data; n_i = mean M0(F^0);
+    U^0 = U(F^0)."""
+    F0 = truncate(from_terms(factors), prm.eps, prm.cap)
+    mom = field.moments(F0, g)
+    n_i = float(np.mean(mom[0]))
+    U0 = lomac.conserved_from_moments(mom, g, n_i)
+    return State(F=F0, U=U0, hist=[], n_i=n_i)
+
+
+def field_of(F: HT, g: PhaseGrid, n_i: float) -> np.ndarray:
+    """E of a state: rho = n_i - M0(F), spectral Poisson, E = -grad phi."""
+    M0 = field.ht_moment(F, g, field.moment_monomials(g.dv)[0])
+    if F.corr is not None:
+        M0 = M0 + field.correction_moment(F.corr, g, field.moment_monomials(g.dv)[0])
+    return field.poisson_field(n_i - M0, g)[1]
+
+
+def slar(F: HT, E: np.ndarray, tau: float, g: PhaseGrid, prm: Params, pivots=None):
+    """SLAR(F; E, tau, eps): cross approximation of the SL-updated tensor, then truncation."""
+    fn = lambda idx: sl.sl_eval(F, E, tau, idx, g, prm.foot)
+    return cross.htaca(fn, g.N, prm.eps, prm.cap, pivots=pivots, return_info=True)
+
+
+def slar_vp(F: HT, dt: float, g: PhaseGrid, prm: Params, n_i: float, pivots=None):
+    """One SLAR_VP step (Eq. slarvp) by CF3.  Returns (F*, info)."""
+    piv = pivots or [None, None, None]
+    E1 = field_of(F, g, n_i)
+    Y2, i1 = slar(F, E1, dt / 3.0, g, prm, piv[0])
+    E2 = field_of(Y2, g, n_i)
+    Y3, i2 = slar(F, E2, 2.0 * dt / 3.0, g, prm, piv[1])
+    E3 = field_of(Y3, g, n_i)
+    Ec = -E1 / 8.0 + 9.0 * E3 / 8.0
+    Fs, i3 = slar(Y2, Ec, 2.0 * dt / 3.0, g, prm, piv[2])
+    info = dict(entries=i1["entries"] + i2["entries"] + i3["entries"],
+                pivots=[i1["pivots"], i2["pivots"], i3["pivots"]],
+                ranks=i3["ranks"], fields=(E1, E2, E3))
+    return Fs, info
+
+
+def _solve(cl: macro.Closure, rhs: np.ndarray, coef: float, U_guess: np.ndarray, tol_abs: float,
+           prm: Params):
+    """JFNK on G(U) = U - rhs - coef K(U) = 0."""
+    Gfun = lambda U: U - rhs - coef * macro.K_operator(U, cl)
+    return macro.jfnk(Gfun, U_guess, tol_abs, prm.krylov_tol, prm.krylov_restart,
+                      prm.newton_max, prm.krylov_max)
+
+
+def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None) -> StepStats:
+    """Advance the state by one step (flowchart of Sec. 3.2.3)."""
+    stats = StepStats()
+    if not prm.lomac:
+        Fs, info = slar_vp(st.F, dt, g, prm, st.n_i, pivots)
+        st.F = Fs
+        st.U = lomac.conserved_from_moments(field.moments(Fs, g), g, st.n_i)
+        stats.entries, stats.ranks = info["entries"], info["ranks"]
+    elif st.step < 2:
+        A, c = macro.dirk3_tableau()
+        tol_abs = macro.newton_tol_abs(prm.newton_tol, st.U)
+        Ks = []
+        for i in range(3):
+            Fs, info = slar_vp(st.F, c[i] * dt, g, prm, st.n_i, None if pivots is None else pivots[i])
+            stats.entries += info["entries"]
+            cl = macro.make_closure(Fs, g, st.n_i, prm.delta)
+            rhs = st.U + dt * sum(A[i, j] * Ks[j] for j in range(i)) if i else st.U.copy()
+            Ustar = lomac.conserved_from_moments(cl.mom_star, g, st.n_i)
+            Ui, ns = _solve(cl, rhs, dt * A[i, i], Ustar, tol_abs, prm)
+            stats.newton += ns.newton
+            stats.krylov += ns.krylov
+            stats.residual = max(stats.residual, ns.residual)
+            stats.converged &= ns.converged
+            Ks.append(macro.K_operator(Ui, cl))
+        # stiffly accurate: U^{n+1} = U_3 with the stage-3 closure
+        st.hist = [st.U] + st.hist[:1]
+        st.U = Ui
+        st.F = lomac.correct(Fs, cl.basis, Ui, g, st.n_i)
+        stats.ranks = info["ranks"]
+    else:
+        Fs, info = slar_vp(st.F, dt, g, prm, st.n_i, pivots)
+        stats.entries, stats.ranks = info["entries"], info["ranks"]
+        cl = macro.make_closure(Fs, g, st.n_i, prm.delta)
+        a = macro.BDF3["a"]
+        rhs = a[0] * st.U + a[1] * st.hist[0] + a[2] * st.hist[1]
+        tol_abs = macro.newton_tol_abs(prm.newton_tol, st.U)
+        Ustar = lomac.conserved_from_moments(cl.mom_star, g, st.n_i)
+        Un, ns = _solve(cl, rhs, macro.BDF3["beta"] * dt, Ustar, tol_abs, prm)
+        stats.newton, stats.krylov = ns.newton, ns.krylov
+        stats.residual, stats.converged = ns.residual, ns.converged
+        st.hist = [st.U] + st.hist[:1]
+        st.U = Un
+        st.F = lomac.correct(Fs, cl.basis, Un, g, st.n_i)
+    st.t += dt
+    st.step += 1
+    stats.W = field.poisson_field(st.n_i - st.U[0], g)[2]
+    return stats
+
+
+def totals(st: State, g: PhaseGrid):
+    """Total mass, momentum (per direction) and energy of the conserved variables."""
+    cell = float(np.prod([g.h(m) for m in range(g.dx)]))
+    return st.U.sum(axis=1) * cell

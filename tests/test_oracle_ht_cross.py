@@ -1,0 +1,134 @@
+"""Oracle pins: HT orthogonalisation, HSVD truncation and the cross approximation
+(Supp. B.1; the HTACA reading)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cross, sl
+from oracle import ht as htmod
+from paper_2606_29027_b300 import inputs
+
+
+def _dense(h):
+    return htmod.densify(h)
+
+
+@pytest.mark.parametrize("N,ranks", [((9, 11), (6, 5)), ((6, 7, 5, 8), (5, 6, 4, 5, 7, 6))])
+def test_orthogonalize_preserves_tensor(N, ranks):
+    h = htmod.from_raw(inputs.random_ht(N, ranks, 3, smooth=False))
+    o = htmod.orthogonalize(h)
+    assert np.allclose(_dense(o), _dense(h), atol=1e-12 * np.abs(_dense(h)).max())
+    for u in o.U:
+        assert np.allclose(u.T @ u, np.eye(u.shape[1]), atol=1e-13)
+    if len(N) == 4:
+        for B in (o.B12, o.B34):
+            M = B.reshape(-1, B.shape[2])
+            assert np.allclose(M.T @ M, np.eye(M.shape[1]), atol=1e-13)
+
+
+def test_truncation_matches_eckart_young_in_2d():
+    """For d = 2 the HSVD is the matrix SVD: the truncation error equals the tail of the
+    singular values (Eckart-Young), computed here by numpy's SVD of the dense matrix."""
+    h = htmod.from_raw(inputs.random_ht((20, 24), (9, 9), 4, smooth=False))
+    F = _dense(h)
+    s = np.linalg.svd(F, compute_uv=False)
+    for cap in (2, 5, 8):
+        t = htmod.truncate(h, 1e-16, cap)
+        err = np.linalg.norm(F - _dense(t))
+        assert err == pytest.approx(np.sqrt(np.sum(s[cap:] ** 2)), rel=1e-9)
+
+
+@pytest.mark.parametrize("eps", [1e-1, 3e-2, 1e-3])
+def test_truncation_error_bound_4d(eps):
+    """||F - F~|| <= eps ||F|| (HSVD bound with the per-node threshold eps^2 ||F||^2/(2d-3))."""
+    N = (7, 8, 9, 6)
+    h = htmod.from_raw(inputs.random_ht(N, (6, 6, 6, 6, 8, 8), 11, smooth=True))
+    F = _dense(h)
+    t, info = htmod.truncate(h, eps, 64, return_info=True)
+    err = np.linalg.norm(F - _dense(t))
+    assert err <= eps * np.linalg.norm(F) * (1 + 1e-12)
+    assert max(info["ranks"]) <= 8
+
+
+def test_truncation_leading_singular_vector():
+    """After HSVD truncation column 0 of every leaf equals (up to sign) the leading left
+    singular vector of the dense mode matricisation (Supp. B.1)."""
+    N = (6, 7, 8, 9)
+    h = htmod.from_raw(inputs.random_ht(N, (5, 5, 5, 5, 6, 6), 21, smooth=False))
+    F = _dense(h)
+    t = htmod.truncate(h, 1e-3, 64)
+    for mu in range(4):
+        A = np.moveaxis(F, mu, 0).reshape(N[mu], -1)
+        u1 = np.linalg.svd(A, full_matrices=False)[0][:, 0]
+        assert abs(float(t.U[mu][:, 0] @ u1)) == pytest.approx(1.0, abs=1e-10)
+        assert np.allclose(t.U[mu].T @ t.U[mu], np.eye(t.U[mu].shape[1]), atol=1e-13)
+
+
+def test_truncation_cap():
+    h = htmod.from_raw(inputs.random_ht((6, 7, 8, 9), (5, 5, 5, 5, 6, 6), 2, smooth=False))
+    t, info = htmod.truncate(h, 1e-14, 3, return_info=True)
+    assert max(info["ranks"]) == 3
+
+
+@pytest.mark.parametrize("N,ranks", [((24, 30), (3, 4)), ((6, 7, 5, 8), (2, 3, 3, 2, 3, 3))])
+def test_cross_exact_recovery_of_low_rank(N, ranks):
+    """HTACA reproduces an exactly low-rank tensor from sampled fibres (eps -> 1e-13)."""
+    h = htmod.from_raw(inputs.random_ht(N, ranks, 8, smooth=False))
+    F = _dense(h)
+    out, info = cross.htaca(lambda idx: htmod.entries(h, idx), N, 1e-13, 64, return_info=True)
+    assert np.linalg.norm(_dense(out) - F) <= 1e-10 * np.linalg.norm(F)
+    M1 = int(np.prod(N[: len(N) // 2]))
+    M2 = int(np.prod(N[len(N) // 2:]))
+    assert info["entries"] == info["aca_rank"] * (M1 + M2)
+    # root-split rank of the data is the ACA rank bound
+    rr = np.linalg.matrix_rank(F.reshape(M1, M2), tol=1e-9 * np.abs(F).max())
+    assert info["aca_rank"] <= rr + 1
+
+
+def test_cross_on_matrix_matches_svd_accuracy():
+    """On a smooth kernel matrix the cross approximation reaches the requested relative
+    accuracy within a small factor of the optimal (SVD) error of the same rank."""
+    x = np.linspace(0, 1, 60)
+    y = np.linspace(0, 2, 70)
+    A = 1.0 / (1.0 + (x[:, None] - y[None, :]) ** 2) + 0.1 * np.cos(3 * x)[:, None]
+    for eps in (1e-3, 1e-6, 1e-9):
+        res = cross.aca(lambda i: A[i], lambda j: A[:, j], 60, 70, eps, 60)
+        err = np.linalg.norm(A - res["U"] @ res["V"].T) / np.linalg.norm(A)
+        assert err <= 10 * eps
+        k = res["U"].shape[1]
+        s = np.linalg.svd(A, compute_uv=False)
+        assert k <= np.count_nonzero(s > 1e-3 * eps * s[0]) + 2
+
+
+def test_cross_pivot_replay_reproduces():
+    N = (12, 14)
+    h = htmod.from_raw(inputs.random_ht(N, (5, 5), 9, smooth=True))
+    fn = lambda idx: htmod.entries(h, idx)
+    a, ia = cross.htaca(fn, N, 1e-8, 16, return_info=True)
+    b, ib = cross.htaca(fn, N, 1e-8, 16, pivots=ia["pivots"], return_info=True)
+    assert ia["pivots"] == ib["pivots"]
+    assert np.allclose(_dense(a), _dense(b), atol=1e-14)
+
+
+def test_argmax_tie_rule():
+    a = np.array([1.0, -3.0, 3.0 * (1 - 1e-13), 2.0, -3.0])
+    assert cross.argmax_tie(a) == 1
+    ex = np.zeros(5, dtype=bool)
+    ex[1] = True
+    assert cross.argmax_tie(a, ex) == 2
+
+
+def test_htaca_of_sl_update_close_to_truncated_dense():
+    """SLAR(F): cross approximation of the SL-updated tensor is within a small multiple of
+    eps of the dense SL step (brute force) on a tiny 2D-2V grid."""
+    N = (10, 10, 12, 12)
+    g = sl.PhaseGrid(2, 2, N, (0, 0, -5, -5), (4 * math.pi, 4 * math.pi, 5, 5))
+    w = inputs.landau_2d2v(n=10, alpha=0.3)
+    w.N, w.lo, w.hi = N, g.lo, g.hi
+    F0 = htmod.truncate(htmod.from_terms(inputs.initial_factors(w)), 1e-12, 20)
+    E = inputs.random_field(N[:2], 2, 0.3, seed=2)
+    eps = 1e-6
+    out = cross.htaca(lambda idx: sl.sl_eval(F0, E, 0.4, idx, g), N, eps, 40)
+    dense = sl.dense_sl_step(htmod.densify(F0), E, 0.4, g)
+    assert np.linalg.norm(_dense(out) - dense) <= 10 * eps * np.linalg.norm(dense)

@@ -1,0 +1,104 @@
+"""End-to-end physics pins of the oracle: linear Landau damping and conservation with the
+LoMaC correction (Sec. 4.1 Landau damping; Sec. 3.2.2 U(F^{n+1}) = U^{n+1})."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dispersion, field, sl, stepper
+from paper_2606_29027_b300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_root():
+    vals = {}
+    with open(os.path.join(GOLDEN, "landau_root.txt")) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                k, v = ln.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_dispersion_root_matches_golden():
+    gr = _golden_root()
+    w = dispersion.landau_rate(gr["k"])
+    assert w.real == pytest.approx(gr["omega_re"], abs=2e-4)
+    assert w.imag == pytest.approx(gr["omega_im"], abs=2e-4)
+
+
+def _run_landau(steps, lomac=True, foot_flip=False, monkeypatch=None):
+    w = inputs.landau_1d1v()
+    g = sl.PhaseGrid(w.dx, w.dv, w.N, w.lo, w.hi)
+    prm = stepper.Params(eps=w.eps, cap=w.rank_cap, lomac=lomac)
+    st = stepper.init_state(inputs.initial_factors(w), g, prm)
+    tot0 = stepper.totals(st, g)
+    ts, Ws = [0.0], [field.poisson_field(st.n_i - st.U[0], g)[2]]
+    for _ in range(steps):
+        s = stepper.sl_step(st, w.dt, g, prm)
+        assert s.converged or not lomac
+        ts.append(st.t)
+        Ws.append(s.W)
+    return np.array(ts), np.array(Ws), tot0, stepper.totals(st, g)
+
+
+def _fit_rate(ts, Ws, t0=2.0, t1=20.0):
+    A = np.sqrt(Ws)
+    pk = [i for i in range(1, len(A) - 1) if A[i] > A[i - 1] and A[i] >= A[i + 1] and t0 <= ts[i] <= t1]
+    return np.polyfit(ts[pk], np.log(A[pk]), 1)[0], len(pk)
+
+
+@pytest.mark.slow
+def test_weak_landau_damping_rate_and_conservation():
+    """1D-1V weak Landau (alpha = 0.01, k = 0.5, 64 x 128, dt = 0.1, eps = 1e-6, cap 16):
+    the amplitude of E decays at the linear rate (within 2%) and mass, momentum and energy
+    are conserved to the Newton tolerance."""
+    ts, Ws, tot0, tot1 = _run_landau(200)
+    rate, npk = _fit_rate(ts, Ws)
+    want = dispersion.landau_rate(0.5).imag
+    assert npk >= 6
+    assert abs(rate - want) <= _golden_root()["rel_tol_rate"] * abs(want), rate
+    drift = np.abs(tot1 - tot0)
+    assert drift[0] <= 1e-12 * abs(tot0[0])
+    assert drift[-1] <= 1e-12 * abs(tot0[-1])
+    assert drift[1] <= 1e-12 * abs(tot0[0])
+
+
+def test_wrong_force_sign_is_caught(monkeypatch):
+    """A planted mistake in the oracle (foot velocity v - E tau instead of v + E tau) turns
+    damping into growth; the Landau pin catches it."""
+    orig = sl.trace_feet
+
+    def flipped(idx, E, tau, g, foot="rk3"):
+        return orig(idx, -E, tau, g, foot)
+
+    monkeypatch.setattr(sl, "trace_feet", flipped)
+    ts, Ws, _, _ = _run_landau(60, lomac=False)
+    assert Ws[-1] > Ws[0]
+
+
+def test_without_lomac_conservation_is_lost():
+    """Without the correction mass/energy drift well above the Newton tolerance
+    (Sec. 4.1 reports O(1e-4) for strong Landau)."""
+    ts, Ws, tot0, tot1 = _run_landau(20, lomac=False)
+    assert abs(tot1[0] - tot0[0]) / tot0[0] > 1e-10
+
+
+@pytest.mark.parametrize("lomac", [True])
+def test_2d2v_conservation_small(lomac):
+    """2D-2V Landau on a 12^4 grid: DIRK3 start-up then BDF3; conservation at the Newton
+    tolerance over four steps."""
+    w = inputs.landau_2d2v(n=12, alpha=0.05, eps=1e-5, cap=12, dt=0.2)
+    g = sl.PhaseGrid(w.dx, w.dv, w.N, w.lo, w.hi)
+    prm = stepper.Params(eps=w.eps, cap=w.rank_cap, lomac=lomac)
+    st = stepper.init_state(inputs.initial_factors(w), g, prm)
+    tot0 = stepper.totals(st, g)
+    for _ in range(4):
+        s = stepper.sl_step(st, w.dt, g, prm)
+        assert s.converged
+    tot1 = stepper.totals(st, g)
+    assert abs(tot1[0] - tot0[0]) <= 1e-12 * tot0[0]
+    assert abs(tot1[-1] - tot0[-1]) <= 1e-12 * tot0[-1]
+    assert np.all(np.abs(tot1[1:3] - tot0[1:3]) <= 1e-12 * tot0[0])
