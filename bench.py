@@ -1,0 +1,307 @@
+"""Benchmark: 2D-2V SLAR steps/s and sampled entries/s on the 2D-2V weak Landau workload
+(64 points per dimension, tree ((x1,x2),(v1,v2)), rank cap 32, eps 1e-5, dt 0.2), with the
+implicit LoMaC correction, for the FP32 entry path (headline) and the plain FP64 path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp32|fp64] [--workload NAME]
+
+One JSON line on rank 0.  Multi-GPU runs are independent replicas (the method has no
+data-parallel exchange): value = steps of all ranks / max-over-ranks time.
+The reference arm (--impl reference) times the FP64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D2V SLAR steps/s"
+UNIT = "steps/s"
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2032 MHz
+FP64_PEAK_TFLOPS = 1.25                              # nominal B300 FP64 (recipe table)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--workload", default="landau_2d2v")
+    p.add_argument("--fp64-steps", type=int, default=4)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(w, precision):
+    return {"workload": f"{w.name}: 2D-2V weak Landau damping, alpha {w.alpha}, k {w.k}, "
+                        f"{w.N[0]} pts/dim, x in [0,4pi)^2, v in [-6,6]^2, tree ((x1,x2),(v1,v2)), "
+                        f"rank cap {w.rank_cap}, eps {w.eps}, dt {w.dt}, LoMaC with BDF3 (DIRK3 start-up), "
+                        f"Newton tol {w.newton_tol}",
+            "entries_precision": precision, "rest_precision": "fp64",
+            "timed_steps": "BDF3 steps after the DIRK3 start-up (in warm-up)",
+            "l2": "flushed between timed steps (256 MiB write, outside the step events)",
+            "global_batch": 1, "parallelism": "replicas"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[1]) for s in self.samples if len(s) >= 9 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) >= 9 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples if len(s) >= 9
+                          for i in range(4) if s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_steps(w, n_warm, n_timed):
+    """Time the FP64 oracle: n_warm untimed steps (DIRK3 start-up), then n_timed steps."""
+    from oracle import sl, stepper
+    from paper_2606_29027_b300 import inputs
+    g = sl.PhaseGrid(w.dx, w.dv, w.N, w.lo, w.hi)
+    prm = stepper.Params(eps=w.eps, cap=w.rank_cap, newton_tol=w.newton_tol)
+    st = stepper.init_state(inputs.initial_factors(w), g, prm)
+    for _ in range(n_warm):
+        stepper.sl_step(st, w.dt, g, prm)
+    t0 = time.perf_counter()
+    ent = 0
+    for _ in range(n_timed):
+        ent += stepper.sl_step(st, w.dt, g, prm).entries
+    dt = time.perf_counter() - t0
+    return n_timed / dt, ent / dt, dt
+
+
+def run_reference(args, w):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    n_warm = max(2, min(args.warmup, 3))
+    n_timed = max(1, min(args.steps, 6))
+    sps, eps_, dt = oracle_steps(w, n_warm, n_timed)
+    cores = cpu_threads()
+    sample = (f"{n_timed} oracle BDF3 steps of {w.name} after {n_warm} untimed start-up steps, "
+              f"{dt:.1f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": sps, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": n_timed, "warmup": n_warm, "ms_per_step": 1000.0 / sps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, "fp64"),
+            "entries_per_s": eps_,
+            "cpu_baseline": {"value": sps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": sps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(ctx, w, K, flush, stream):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    stats = []
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            ev[i][0].record(stream)
+            s = ctx.step(w.dt)
+            ev[i][1].record(stream)
+            stats.append(s)
+            flush.zero_()
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return ms, stats
+
+
+def run_ours(args, w):
+    import torch
+    from paper_2606_29027_b300 import inputs, slar
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    fac = inputs.initial_factors(w)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def make(precision, profile):
+        cfg = slar.make_config(w, precision=precision, profile=profile)
+        return slar.Context(cfg, stream=stream)
+
+    # ---- device-resident timed run (headline precision) ----
+    ctx = make(args.precision, True)
+    with torch.cuda.stream(stream):
+        ctx.init_ht(fac)
+        for _ in range(max(3, args.warmup)):
+            ctx.step(w.dt)
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = slar.launch_count()
+    barrier()
+    t0 = time.perf_counter()
+    ms, stats = time_steps(ctx, w, args.steps, flush, stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    launches = slar.launch_count() - l0
+    clocks = clk.stop()
+    tot_ms = float(sum(ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps / (tot_ms / 1000.0)
+    entries = sum(s.entries for s in stats)
+    eval_ms = sum(s.eval_ms for s in stats)
+    eval_flop = sum(s.eval_flop for s in stats)
+    converged = all(s.converged for s in stats)
+    phase_names = ["cross_approx", "truncation", "fields_moments", "lomac_closure", "newton_krylov", "diagnostics"]
+    phases = {nm: sum(s.phase_ms[i] for s in stats) / args.steps for i, nm in enumerate(phase_names)}
+
+    # ---- FP64 path at the same workload (fewer steps) ----
+    fp64 = None
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        c64 = make("fp64", True)
+        with torch.cuda.stream(stream):
+            c64.init_ht(fac)
+            for _ in range(3):
+                c64.step(w.dt)
+        barrier()
+        ms64, st64 = time_steps(c64, w, args.fp64_steps, flush, stream)
+        t64 = float(sum(ms64))
+        fp64 = {"value": args.fp64_steps / (t64 / 1000.0), "unit": UNIT,
+                "ms_per_step": t64 / args.fp64_steps,
+                "entries_per_s": sum(s.entries for s in st64) / (t64 / 1000.0),
+                "eval_tflops": sum(s.eval_flop for s in st64) / max(sum(s.eval_ms for s in st64), 1e-9) / 1e9,
+                "steps": args.fp64_steps}
+        del c64
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e_steps = max(3, args.warmup) + min(args.steps, 10)
+    ctx_e = make(args.precision, False)
+    U_host = torch.empty((w.dv + 2, ctx_e.NX), dtype=torch.float64, pin_memory=True)
+    U_dev = torch.empty((w.dv + 2, ctx_e.NX), dtype=torch.float64, device="cuda")
+    h2d = sum(sum(np.asarray(f).nbytes for f in term) for term in fac)
+    barrier()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        ctx_e.init_ht(fac)                       # host factors -> device
+        for _ in range(e2e_steps):
+            ctx_e.step(w.dt)                     # stats returned to host
+            ctx_e.get_conserved(U_dev)
+            U_host.copy_(U_dev, non_blocking=True)
+        stream.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e = {"value": e2e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
+           "d2h_bytes_per_step": U_host.numel() * 8 + 200,
+           "note": "fresh context: init_ht upload of the host initial data, DIRK3 start-up and "
+                   "BDF3 steps, each step's U^{n+1} and stats read back to host"}
+
+    if rank != 0:
+        return
+    peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
+    achieved = eval_flop / max(eval_ms, 1e-9) / 1e9          # TFLOP/s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": workload_config(w, args.precision),
+            "entries_per_s": entries / (tot_ms / 1000.0) * world,
+            "entries_per_step": entries / args.steps,
+            "converged": converged,
+            "ranks_last": list(stats[-1].ranks),
+            "fp64_path": fp64,
+            "roofline": {"kernel": "k_sl_eval (SL entry evaluator)", "bound": "alu",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"
+                         if args.precision == "fp32" else "nominal B300 FP64 1.25 TFLOP/s",
+                         "eval_share_of_step": eval_ms / tot_ms},
+            "phase_ms_per_step": phases,
+            "gpu_launches": launches, "wall_s": wall, "clocks": clocks, "e2e": e2e}
+    if not args.no_cpu_baseline and world == 1:
+        sps, eps_, dt = oracle_steps(w, 2, 1)
+        line["cpu_baseline"] = {"value": sps, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                                "sample": f"1 oracle BDF3 step of {w.name} after 2 untimed DIRK3 "
+                                          f"start-up steps ({dt:.1f} s); entries/s {eps_:.3g}"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    from paper_2606_29027_b300 import inputs
+    w = inputs.workload_by_name(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

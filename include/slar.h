@@ -1,0 +1,205 @@
+/*
+ * slar.h -- C ABI of the B300 (sm_103a) SLAR + adaptive-weight implicit LoMaC library.
+ *
+ * Method: "A Mass, Momentum, and Energy Conserving Semi-Lagrangian Adaptive-Rank (SLAR)
+ * Method for the Vlasov-Poisson System" (arXiv 2606.29027).  The distribution function is
+ * a hierarchical-Tucker (HT) tensor on a cell-centred periodic phase-space grid; each time
+ * step advances it with SLAR_VP (Sec. 3.1, Eq. slarvp) and restores mass, momentum and
+ * energy with the implicit adaptive-weight LoMaC correction (Sec. 3.2, Eq.
+ * LoMaC_update_discrete) solved by JFNK on the BDF3/DIRK3-discretised macroscopic system
+ * (Sec. 3.2.3, Eq. BE_nonlinear_system).
+ *
+ * Conventions shared by every entry point
+ *  - Dimension order (x1..x_dx, v1..v_dv), dx = dv in {1, 2}; d = dx + dv in {2, 4}.
+ *    Tree: d = 2 root{0,1}; d = 4 root{12{0,1}, 34{2,3}}.
+ *  - Indices are 0-based.  Spatial fields are row-major over (x1, .., x_dx), x1 slowest;
+ *    a spatial field has NX = prod_{m<dx} N[m] values.
+ *  - Pointers documented "device" are plain CUDA device pointers (any allocator); pointers
+ *    documented "host" are host memory.  The library never frees caller memory and keeps
+ *    no caller pointer after a call returns.
+ *  - All device work is enqueued on the stream given to slar_create; calls that return
+ *    host values (stats, energies, exported tensors) synchronise that stream.
+ *  - One context per stream; a context is not thread-safe.
+ *  - Every function returns a slar_status.  On failure the context (if any) keeps a
+ *    message retrievable with slar_last_error; no C++ exception crosses the ABI.
+ */
+#ifndef SLAR_H
+#define SLAR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int slar_status;
+enum {
+    SLAR_OK = 0,
+    SLAR_EINVAL = 1,    /* bad argument, shape or state */
+    SLAR_ENOMEM = 2,    /* device allocation failed */
+    SLAR_ECUDA = 3,     /* a CUDA call failed (message has the CUDA error string) */
+    SLAR_ENOCONV = 4,   /* Newton / GMRES did not reach its tolerance; state is still advanced */
+    SLAR_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    SLAR_ERANK = 6,     /* rank cap reached before the tolerance was met (result valid) */
+    SLAR_ENAN = 7       /* non-finite values detected */
+};
+
+/* precision of the SL entry evaluation (gathers + transfer-tensor contractions);
+   moments, truncation, LoMaC and the Newton solve are always FP64. */
+enum { SLAR_FP64 = 0, SLAR_FP32 = 1 };
+
+/* flags */
+enum {
+    SLAR_LOMAC = 1,        /* apply the implicit LoMaC correction every step (Sec. 3.2) */
+    SLAR_FOOT_EULER = 2,   /* first-order foot (x - v tau, v + E tau) instead of RK3 */
+    SLAR_PROFILE = 4       /* time every entry-evaluator launch with CUDA events (stats) */
+};
+
+typedef struct slar_config {
+    int dx, dv;             /* 1,1 or 2,2 */
+    int N[4];               /* points per dimension, 4 <= N <= 128 */
+    double lo[4], hi[4];    /* periodic box [lo, hi) per dimension */
+    double eps;             /* relative truncation tolerance eps_Base (Sec. 3.1) */
+    int rank_cap;           /* maximum HT rank, <= 64 */
+    double newton_tol;      /* Newton tolerance on ||G||_inf relative to max(1,||U^n||_inf) */
+    double krylov_tol;      /* GMRES relative tolerance */
+    int krylov_restart;     /* GMRES restart length, <= 64 */
+    int newton_max;         /* Newton iteration cap */
+    int krylov_max;         /* Krylov iterations cap per Newton step */
+    int precision;          /* SLAR_FP64 or SLAR_FP32 */
+    int flags;              /* SLAR_LOMAC | SLAR_FOOT_EULER */
+    double delta_floor;     /* positivity floor of the adaptive weight (Supp. B.1) */
+} slar_config;
+
+typedef struct slar_stats {
+    long long entries;      /* SL entries sampled by the cross approximation this step */
+    int ranks[6];           /* HT ranks of F* after truncation: leaves, then r12, r34 */
+    int aca_rank[9];        /* cross-approximation rank of each SLAR call this step */
+    int n_slar;             /* number of SLAR calls this step (3, or 9 in a DIRK3 step) */
+    int newton, krylov;     /* Newton and GMRES iterations this step */
+    double residual;        /* final ||G||_inf */
+    int converged;          /* 1 if every Newton solve met its tolerance */
+    double field_energy;    /* W = 1/2 sum |E|^2 dx^dx of the new state */
+    double totals[4];       /* mass, momentum (dv components), energy of U^{n+1} */
+    double eval_ms;         /* SLAR_PROFILE: summed device time of the entry-evaluator launches */
+    double eval_flop;       /* algorithmic flops of the sampled entries this step */
+    long long launches;     /* kernels this library launched during the step */
+    double phase_ms[6];     /* SLAR_PROFILE: device time of cross approximation, truncation,
+                               fields/moments, LoMaC closure, Newton-Krylov, diagnostics */
+} slar_stats;
+
+/* Host-side view of an HT state for import/export.  Layouts (row-major):
+ *   U[mu]  : N[mu] x rank[mu]                       (leaf bases, row = grid index)
+ *   B12    : rank[4] x rank[0] x rank[1]  ([p][a][b]) (d = 4)
+ *   B34    : rank[5] x rank[2] x rank[3]  ([q][c][e]) (d = 4)
+ *   Broot  : d = 2: rank[0] x rank[1];  d = 4: rank[4] x rank[5]
+ *   dC     : (dv+2) x NX   separable LoMaC correction coefficients (if has_corr)
+ *   qv     : 3 x dv x N[dx]  velocity factors omega, q1, q2 per velocity dimension
+ * On export with any array pointer NULL only d, N, rank and has_corr are filled. */
+typedef struct slar_ht_view {
+    int d;
+    int N[4];
+    int rank[6];
+    double* U[4];
+    double* B12;
+    double* B34;
+    double* Broot;
+    int has_corr;
+    double* dC;
+    double* qv;
+} slar_ht_view;
+
+typedef struct slar_ctx slar_ctx;
+
+/* Create a context: validates the grid and tolerances, allocates all device workspaces
+ * on the current device.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Errors: SLAR_EINVAL, SLAR_ENOMEM, SLAR_ECUDA.  *out is NULL on failure. */
+slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out);
+
+/* Free all device memory of the context (after synchronising its stream). */
+slar_status slar_destroy(slar_ctx* ctx);
+
+/* Last error message of the context ("" if none); static storage owned by the context. */
+const char* slar_last_error(const slar_ctx* ctx);
+
+/* Initial data (Sec. 4 test problems): F^0 = sum_t prod_mu f_{t,mu}, given as host FP64
+ * `factors` of n_terms * (N[0]+..+N[d-1]) values laid out [t][mu][i].  The separable sum
+ * is converted to an HT, HSVD-truncated with eps and rank_cap (Supp. B.1), the ion
+ * density is set to mean(M0(F^0)) and U^0 = U(F^0).  Resets the step counter.
+ * Errors: SLAR_EINVAL (n_terms < 1 or > rank limit). */
+slar_status init_ht(slar_ctx* ctx, int n_terms, const double* factors);
+
+/* One full time step of size dt (flowchart of Sec. 3.2.3): SLAR_VP by the third-order
+ * RK exponential integrator (Eq. slarvp; three frozen-field SLAR calls), then, with
+ * SLAR_LOMAC, the moments of F*, the adaptive weight and basis (Supp. B), the JFNK solve
+ * of the macroscopic system (DIRK3 for the first two steps, BDF3 after) and the update
+ * F^{n+1} = F* - R(U(F*)) + R(U^{n+1}).  `stats` (host, may be NULL) receives the
+ * step diagnostics.  Errors: SLAR_EINVAL (no state), SLAR_ENOCONV (Newton or GMRES did
+ * not converge; the state is advanced with the last iterate). */
+slar_status sl_step(slar_ctx* ctx, double dt, slar_stats* stats);
+
+/* HSVD truncation of the HT part of the state (Supp. B.1): orthogonalise, node Gram
+ * matrices from the root down, eigendecomposition, keep per node the smallest rank with
+ * discarded energy <= (eps ||F||)^2/(2d-3), capped at rank_cap.  Afterwards column 0 of
+ * every leaf is the leading left singular vector of its mode matricisation.
+ * Errors: SLAR_EINVAL (eps < 0, rank_cap < 1 or > 64). */
+slar_status ht_truncate(slar_ctx* ctx, double eps, int rank_cap);
+
+/* All velocity moments of the state (HT + correction) as device FP64
+ * out[n_mom][NX] (Eq. raw moments and the flux moments of Eq. macro_sys_comp):
+ * M0, M1_1..M1_dv, M2, <v_a v_b f> (a <= b), <|v|^2 v_a f>;  n_mom = 5 (dv = 1) or 9
+ * (dv = 2).  Midpoint quadrature in v (Supp. B.1). */
+slar_status moments(slar_ctx* ctx, double* out_dev);
+
+/* Adaptive-weight LoMaC update of the current state treated as F* (Sec. 3.2.2,
+ * Supp. B): weight from column 0 of the velocity leaves, weighted Gram-Schmidt, then
+ * F <- F - R(U(F)) + R(U_target).  U_target: device FP64 [dv+2][NX] = (n, m_1..m_dv, e).
+ * The state's HT must carry no correction yet.  Afterwards U(F) = U_target. */
+slar_status lomac_correct(slar_ctx* ctx, const double* U_target_dev);
+
+/* Spectral Poisson solve (Eq. Poisson, Eq. Efromphi): -Lap(phi) = rho, E = -grad(phi),
+ * W = 1/2 sum |E|^2 dx^dx.  rho: device [NX]; E: device [dx][NX]; phi: device [NX] or NULL;
+ * energy: host scalar or NULL. */
+slar_status poisson_field(slar_ctx* ctx, const double* rho_dev, double* E_dev, double* phi_dev,
+                          double* energy);
+
+/* Entries of the state (HT + correction) at n grid tuples idx_dev (device int32 [n][d]);
+ * out_dev: device FP64 [n].  Evaluated in the context's precision. */
+slar_status ht_eval(slar_ctx* ctx, long long n, const int* idx_dev, double* out_dev);
+
+/* The local SL-FD entry evaluator (Sec. 3.1, Eq. SL_basic_formulation, Eq. tp_interp in
+ * HT form): for each tuple, the backward foot of the frozen-field characteristic over
+ * tau (dx/dt = v, dv/dt = -E(x)), quadratic Lagrange weights per dimension
+ * (Eq. 1d_quadratic_interp_weight), gathers of three leaf rows and the contraction up the
+ * tree.  E_dev: device FP64 [dx][NX].  Output device FP64 [n]. */
+slar_status sl_eval(slar_ctx* ctx, double tau, const double* E_dev, long long n, const int* idx_dev,
+                    double* out_dev);
+
+/* One SLAR call (Sec. 3.1): cross approximation of the SL-updated tensor from sampled row
+ * and column fibres of the (x | v) matricisation, exact HT embedding, HSVD truncation;
+ * the state's HT is replaced by the result (its correction is consumed).  aca_rank and
+ * entries (host, may be NULL) receive the cross rank and the number of sampled entries. */
+slar_status slar_advect(slar_ctx* ctx, double tau, const double* E_dev, int* aca_rank,
+                        long long* entries);
+
+/* Replay mode for the cross approximation: the next SLAR calls take their (row, column)
+ * pivots from `pivots` (host int32 [n_calls][kmax][2], -1 ends a call's list) instead of
+ * choosing them.  n_calls = 0 switches replay off. */
+slar_status slar_set_pivot_replay(slar_ctx* ctx, int n_calls, int kmax, const int* pivots);
+
+/* Copy the HT state (and correction) out to / in from host memory (see slar_ht_view). */
+slar_status ht_export(slar_ctx* ctx, slar_ht_view* view);
+slar_status ht_import(slar_ctx* ctx, const slar_ht_view* view);
+
+/* Conserved variables U^n (device FP64 [dv+2][NX]) and the ion density. */
+slar_status slar_get_conserved(slar_ctx* ctx, double* U_dev, double* n_i);
+slar_status slar_set_conserved(slar_ctx* ctx, const double* U_dev, double n_i);
+
+/* Total number of kernels launched by this library in this process (all contexts). */
+slar_status slar_launch_count(long long* out);
+
+/* Number of moments returned by `moments` and the spatial size NX. */
+slar_status slar_sizes(const slar_ctx* ctx, int* n_mom, int* nx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLAR_H */

@@ -65,6 +65,7 @@ class StepStats:
     residual: float = 0.0
     converged: bool = True
     W: float = 0.0
+    aca_ranks: list = dfield(default_factory=list)
 
 
 def init_state(factors, g: PhaseGrid, prm: Params) -> State:
@@ -103,7 +104,8 @@ def slar_vp(F: HT, dt: float, g: PhaseGrid, prm: Params, n_i: float, pivots=None
     Fs, i3 = slar(Y2, Ec, 2.0 * dt / 3.0, g, prm, piv[2])
     info = dict(entries=i1["entries"] + i2["entries"] + i3["entries"],
                 pivots=[i1["pivots"], i2["pivots"], i3["pivots"]],
-                ranks=i3["ranks"], fields=(E1, E2, E3))
+                ranks=i3["ranks"], fields=(E1, E2, E3),
+                aca_ranks=[i1["aca_rank"], i2["aca_rank"], i3["aca_rank"]])
     return Fs, info
 
 
@@ -123,6 +125,7 @@ def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None) -> Ste
         st.F = Fs
         st.U = lomac.conserved_from_moments(field.moments(Fs, g), g, st.n_i)
         stats.entries, stats.ranks = info["entries"], info["ranks"]
+        stats.aca_ranks = info["aca_ranks"]
     elif st.step < 2:
         A, c = macro.dirk3_tableau()
         tol_abs = macro.newton_tol_abs(prm.newton_tol, st.U)
@@ -130,6 +133,7 @@ def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None) -> Ste
         for i in range(3):
             Fs, info = slar_vp(st.F, c[i] * dt, g, prm, st.n_i, None if pivots is None else pivots[i])
             stats.entries += info["entries"]
+            stats.aca_ranks += info["aca_ranks"]
             cl = macro.make_closure(Fs, g, st.n_i, prm.delta)
             rhs = st.U + dt * sum(A[i, j] * Ks[j] for j in range(i)) if i else st.U.copy()
             Ustar = lomac.conserved_from_moments(cl.mom_star, g, st.n_i)
@@ -147,6 +151,7 @@ def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None) -> Ste
     else:
         Fs, info = slar_vp(st.F, dt, g, prm, st.n_i, pivots)
         stats.entries, stats.ranks = info["entries"], info["ranks"]
+        stats.aca_ranks = info["aca_ranks"]
         cl = macro.make_closure(Fs, g, st.n_i, prm.delta)
         a = macro.BDF3["a"]
         rhs = a[0] * st.U + a[1] * st.hist[0] + a[2] * st.hist[1]

@@ -1,0 +1,483 @@
+// C ABI of libslar.so (declared in include/slar.h): argument checks, allocation of the
+// context, and the entry points that are thin orchestration of the kernels.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "context.cuh"
+
+namespace slar {
+namespace {
+std::atomic<long long> g_launches{0};
+}
+int count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return 0;
+}
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace slar
+
+using namespace slar;
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * n);
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+slar_status validate(const slar_config* cfg, char* msg, size_t len) {
+  if (!cfg) { snprintf(msg, len, "null config"); return SLAR_EINVAL; }
+  if (!((cfg->dx == 1 && cfg->dv == 1) || (cfg->dx == 2 && cfg->dv == 2))) {
+    snprintf(msg, len, "dx = dv in {1, 2} required"); return SLAR_EINVAL;
+  }
+  const int d = cfg->dx + cfg->dv;
+  for (int m = 0; m < d; ++m) {
+    if (cfg->N[m] < 4 || cfg->N[m] > SLAR_MAX_N) {
+      snprintf(msg, len, "N[%d] = %d outside [4, %d]", m, cfg->N[m], SLAR_MAX_N); return SLAR_EINVAL;
+    }
+    if (!(cfg->hi[m] > cfg->lo[m])) { snprintf(msg, len, "empty box in dim %d", m); return SLAR_EINVAL; }
+  }
+  for (int m = 0; m < cfg->dx; ++m)
+    if (!is_pow2(cfg->N[m])) {
+      snprintf(msg, len, "spatial N[%d] = %d must be a power of two (FFT)", m, cfg->N[m]);
+      return SLAR_EINVAL;
+    }
+  if (cfg->dv == 2 && cfg->N[2] != cfg->N[3]) {
+    snprintf(msg, len, "velocity dimensions must have equal N"); return SLAR_EINVAL;
+  }
+  if (cfg->rank_cap < 1 || cfg->rank_cap > SLAR_MAX_RANK) {
+    snprintf(msg, len, "rank_cap must be in [1, %d]", SLAR_MAX_RANK); return SLAR_EINVAL;
+  }
+  if (!(cfg->eps >= 0.0)) { snprintf(msg, len, "eps must be >= 0"); return SLAR_EINVAL; }
+  if (cfg->precision != SLAR_FP64 && cfg->precision != SLAR_FP32) {
+    snprintf(msg, len, "unknown precision"); return SLAR_EINVAL;
+  }
+  if (cfg->krylov_restart < 1 || cfg->krylov_restart > 64) {
+    snprintf(msg, len, "krylov_restart must be in [1, 64]"); return SLAR_EINVAL;
+  }
+  return SLAR_OK;
+}
+
+void free_ctx(slar_ctx* c) {
+  if (!c) return;
+  auto F = [](void* p) { if (p) cudaFree(p); };
+  for (int sl = 0; sl < NSLOT; ++sl) {
+    for (int m = 0; m < 4; ++m) F(c->ht[sl].U[m]);
+    F(c->ht[sl].B12); F(c->ht[sl].B34); F(c->ht[sl].Broot);
+  }
+  for (int m = 0; m < 4; ++m) { F(c->U32[m]); F(c->Qleaf[m]); F(c->Rleaf[m]); }
+  F(c->B12_32); F(c->B34_32); F(c->Broot32); F(c->Ik); F(c->Lt[0]); F(c->Lt[1]);
+  F(c->dC); F(c->qv); F(c->Uc); F(c->Uh1); F(c->Uh2);
+  F(c->Ua); F(c->Va); F(c->rowbuf); F(c->usedr); F(c->usedc); F(c->pivI); F(c->pivJ);
+  F(c->ast); F(c->aca_part); F(c->aca_dots);
+  if (c->ast_host) cudaFreeHost(c->ast_host);
+  if (c->h_ranks) cudaFreeHost(c->h_ranks);
+  if (c->scal_host) cudaFreeHost(c->scal_host);
+  F(c->T1); F(c->T2); F(c->T3); F(c->Q12); F(c->Q34); F(c->Rn[0]); F(c->Rn[1]);
+  F(c->sm1); F(c->sm2); F(c->sm3); F(c->sm4);
+  for (int t = 0; t < 6; ++t) { F(c->G[t]); F(c->W[t]); F(c->S[t]); F(c->ework[t]); }
+  F(c->gram_work); F(c->tau); F(c->norm2); F(c->d_ranks); F(c->d_info); F(c->d_eig); F(c->d_rank);
+  F(c->E); F(c->E1); F(c->E2); F(c->E3); F(c->mom); F(c->lvec); F(c->spec); F(c->rho); F(c->Wdev);
+  F(c->macro_ws); F(c->scal);
+  if (c->spectral) { c->spectral->release(); delete c->spectral; }
+  macro_free(c);
+  for (int i = 0; i < kProfEvents; ++i)
+    if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
+  for (int i = 0; i < kPhaseEvents; ++i)
+    if (c->ph_ev[i]) cudaEventDestroy(c->ph_ev[i]);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
+  if (!out) return SLAR_EINVAL;
+  *out = nullptr;
+  char msg[256];
+  slar_status st = validate(cfg, msg, sizeof(msg));
+  if (st != SLAR_OK) { fprintf(stderr, "slar_create: %s\n", msg); return st; }
+  slar_ctx* c = new (std::nothrow) slar_ctx();
+  if (!c) return SLAR_ENOMEM;
+  c->cfg = *cfg;
+  if (c->cfg.delta_floor <= 0.0) c->cfg.delta_floor = 1e-12;
+  if (c->cfg.newton_max <= 0) c->cfg.newton_max = 20;
+  if (c->cfg.krylov_max <= 0) c->cfg.krylov_max = 200;
+  c->s = static_cast<cudaStream_t>(stream);
+  c->dx = cfg->dx;
+  c->dv = cfg->dv;
+  c->d = cfg->dx + cfg->dv;
+  GridDesc& g = c->g;
+  g.d = c->d; g.dx = c->dx; g.dv = c->dv;
+  g.NX = 1; g.NV = 1;
+  for (int m = 0; m < 4; ++m) {
+    g.N[m] = m < c->d ? cfg->N[m] : 1;
+    g.lo[m] = m < c->d ? cfg->lo[m] : 0.0;
+    g.h[m] = m < c->d ? (cfg->hi[m] - cfg->lo[m]) / cfg->N[m] : 1.0;
+  }
+  for (int m = 0; m < c->dx; ++m) g.NX *= g.N[m];
+  for (int m = 0; m < c->dv; ++m) g.NV *= g.N[c->dx + m];
+  c->NX = g.NX;
+  c->NV = g.NV;
+  c->M1 = g.NX;
+  c->M2 = g.NV;
+  c->kmax = std::min(cfg->rank_cap, std::min(c->M1, c->M2));
+  c->n_mom = c->dv == 1 ? 5 : 9;
+  const int R = SLAR_MAX_RANK;
+  const int d = c->d;
+  long long capB = (long long)R * R * R;
+  if (d == 4) {
+    capB = std::max(capB, (long long)c->kmax * g.N[0] * g.N[1]);
+    capB = std::max(capB, (long long)c->kmax * g.N[2] * g.N[3]);
+  } else {
+    capB = std::max(capB, (long long)std::max(c->M1, c->M2) * R);
+  }
+  capB = std::max(capB, (long long)SLAR_MAX_N * R * 9);
+  c->capB = capB;
+#define A(p, n) do { cudaError_t e_ = dalloc(&(p), (size_t)(n)); if (e_ != cudaSuccess) { free_ctx(c); return SLAR_ENOMEM; } } while (0)
+  for (int sl = 0; sl < NSLOT; ++sl) {
+    for (int m = 0; m < d; ++m) A(c->ht[sl].U[m], (size_t)g.N[m] * R);
+    if (d == 4) { A(c->ht[sl].B12, (size_t)R * R * R); A(c->ht[sl].B34, (size_t)R * R * R); }
+    A(c->ht[sl].Broot, (size_t)R * R);
+  }
+  for (int m = 0; m < d; ++m) {
+    A(c->U32[m], (size_t)g.N[m] * R);
+    A(c->Qleaf[m], (size_t)g.N[m] * R);
+    A(c->Rleaf[m], (size_t)R * R);
+  }
+  if (d == 4) { A(c->B12_32, (size_t)R * R * R); A(c->B34_32, (size_t)R * R * R); }
+  A(c->Broot32, (size_t)R * R);
+  A(c->Ik, (size_t)R * R);
+  if (d == 2) { A(c->Lt[0], (size_t)c->M1 * c->kmax); A(c->Lt[1], (size_t)c->M2 * c->kmax); }
+  A(c->dC, (size_t)(c->dv + 2) * c->NX);
+  A(c->qv, (size_t)3 * c->dv * g.N[c->dx]);
+  A(c->Uc, (size_t)(c->dv + 2) * c->NX);
+  A(c->Uh1, (size_t)(c->dv + 2) * c->NX);
+  A(c->Uh2, (size_t)(c->dv + 2) * c->NX);
+  A(c->Ua, (size_t)c->M1 * c->kmax);
+  A(c->Va, (size_t)c->M2 * c->kmax);
+  A(c->rowbuf, (size_t)c->M2);
+  A(c->usedr, (size_t)c->M1);
+  A(c->usedc, (size_t)c->M2);
+  A(c->pivI, (size_t)c->kmax);
+  A(c->pivJ, (size_t)c->kmax);
+  A(c->ast, 1);
+  const int nbu = (c->M1 + 255) / 256, nbv = (c->M2 + 255) / 256;
+  A(c->aca_part, (size_t)(nbu + nbv) * (R + 1));
+  A(c->T1, (size_t)capB); A(c->T2, (size_t)capB); A(c->T3, (size_t)capB);
+  A(c->Q12, (size_t)capB); A(c->Q34, (size_t)capB);
+  A(c->Rn[0], (size_t)R * R); A(c->Rn[1], (size_t)R * R);
+  A(c->sm1, (size_t)R * R); A(c->sm2, (size_t)R * R); A(c->sm3, (size_t)R * R); A(c->sm4, (size_t)R * R);
+  for (int t = 0; t < 6; ++t) {
+    A(c->G[t], (size_t)SLAR_MAX_N * SLAR_MAX_N);
+    A(c->W[t], (size_t)SLAR_MAX_N);
+    A(c->S[t], (size_t)SLAR_MAX_N * SLAR_MAX_N);
+    A(c->ework[t], (size_t)(SLAR_MAX_N + 1) * (SLAR_MAX_N + 1));
+  }
+  const long long gram_rows = std::max((long long)std::max(c->M1, c->M2), capB / 1);
+  c->gram_work_blocks = (int)((std::min(gram_rows, (long long)SLAR_MAX_N * SLAR_MAX_N) + 63) / 64);
+  A(c->gram_work, (size_t)c->gram_work_blocks * R * R);
+  A(c->tau, (size_t)R);
+  A(c->norm2, 4);
+  A(c->d_ranks, 8);
+  A(c->d_info, 2);
+  A(c->d_eig, 6);
+  A(c->d_rank, 6);
+  A(c->E, (size_t)c->dx * c->NX); A(c->E1, (size_t)c->dx * c->NX);
+  A(c->E2, (size_t)c->dx * c->NX); A(c->E3, (size_t)c->dx * c->NX);
+  A(c->mom, (size_t)c->n_mom * c->NX);
+  A(c->lvec, (size_t)2 * 4 * 64 + 9 * 64 + 9 * 64 * 64);
+  c->spec_len = (long long)2 * 24 * c->NX;
+  A(c->spec, (size_t)c->spec_len);
+  A(c->rho, (size_t)c->NX);
+  A(c->Wdev, 8);
+#undef A
+  if (cudaMallocHost(&c->ast_host, sizeof(AcaState)) != cudaSuccess ||
+      cudaMallocHost(&c->h_ranks, sizeof(int) * 16) != cudaSuccess ||
+      cudaMallocHost(&c->scal_host, sizeof(double) * 64) != cudaSuccess) {
+    free_ctx(c);
+    return SLAR_ENOMEM;
+  }
+  c->spectral = new (std::nothrow) Spectral();
+  if (!c->spectral) { free_ctx(c); return SLAR_ENOMEM; }
+  double L[2];
+  for (int m = 0; m < c->dx; ++m) L[m] = cfg->hi[m] - cfg->lo[m];
+  if (c->spectral->init(c->dx, cfg->N, L, c->s) != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
+  for (int i = 0; i < kProfEvents; ++i)
+    if (cudaEventCreate(&c->prof_ev[i]) != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
+  for (int i = 0; i < kPhaseEvents; ++i)
+    if (cudaEventCreate(&c->ph_ev[i]) != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
+  const slar_status mst = macro_alloc(c);
+  if (mst != SLAR_OK) { free_ctx(c); return mst; }
+  *out = c;
+  return SLAR_OK;
+}
+
+slar_status slar_destroy(slar_ctx* c) {
+  if (!c) return SLAR_EINVAL;
+  if (c->s) cudaStreamSynchronize(c->s); else cudaDeviceSynchronize();
+  free_ctx(c);
+  return SLAR_OK;
+}
+
+const char* slar_last_error(const slar_ctx* c) { return c ? c->err : "null context"; }
+
+slar_status slar_launch_count(long long* out) {
+  if (!out) return SLAR_EINVAL;
+  *out = launch_count();
+  return SLAR_OK;
+}
+
+slar_status slar_sizes(const slar_ctx* c, int* n_mom, int* nx) {
+  if (!c) return SLAR_EINVAL;
+  if (n_mom) *n_mom = c->n_mom;
+  if (nx) *nx = c->NX;
+  return SLAR_OK;
+}
+
+static int spare_slot(const slar_ctx* c, int a, int b = -1) {
+  for (int s = 0; s < NSLOT; ++s)
+    if (s != a && s != b) return s;
+  return -1;
+}
+
+// U = (M0, M1, M2/2 + e_p(M0)) of the state, n_i optionally reset to mean(M0)
+static slar_status conserved_of_state(slar_ctx* c, bool reset_ni) {
+  CKS(compute_moments(c, c->cur, true, c->mom, c->dv + 2));
+  if (reset_ni) {
+    std::vector<double> m0(c->NX);
+    CK(cudaMemcpyAsync(m0.data(), c->mom, sizeof(double) * c->NX, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    double s = 0.0;
+    for (double v : m0) s += v;
+    c->n_i = s / c->NX;
+  }
+  CKS(field_from_M0(c, c->mom, c->E, nullptr, nullptr));
+  return conserved_from_moments(c, c->mom, c->E, c->Uc);
+}
+
+slar_status init_ht(slar_ctx* c, int n_terms, const double* factors) {
+  if (!c || !factors) return SLAR_EINVAL;
+  if (n_terms < 1 || n_terms > SLAR_MAX_RANK)
+    return set_error(c, SLAR_EINVAL, "n_terms must be in [1, 64]");
+  const int d = c->d;
+  for (int m = 0; m < d; ++m)
+    if (n_terms > c->g.N[m]) return set_error(c, SLAR_EINVAL, "n_terms exceeds a grid size");
+  int off[5] = {0, 0, 0, 0, 0};
+  for (int m = 0; m < d; ++m) off[m + 1] = off[m] + c->g.N[m];
+  const int tmp = spare_slot(c, c->cur);
+  HTBuf& h = c->ht[tmp];
+  const int T = n_terms;
+  for (int m = 0; m < d; ++m) {
+    const int N = c->g.N[m];
+    std::vector<double> U((size_t)N * T);
+    for (int t = 0; t < T; ++t)
+      for (int i = 0; i < N; ++i) U[(size_t)i * T + t] = factors[(size_t)t * off[d] + off[m] + i];
+    CK(cudaMemcpy(h.U[m], U.data(), sizeof(double) * U.size(), cudaMemcpyHostToDevice));
+    h.r[m] = T;
+  }
+  std::vector<double> I((size_t)T * T, 0.0);
+  for (int t = 0; t < T; ++t) I[(size_t)t * T + t] = 1.0;
+  CK(cudaMemcpy(h.Broot, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice));
+  if (d == 4) {
+    std::vector<double> D((size_t)T * T * T, 0.0);
+    for (int t = 0; t < T; ++t) D[((size_t)t * T + t) * T + t] = 1.0;
+    CK(cudaMemcpy(h.B12, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h.B34, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice));
+    h.r[4] = h.r[5] = T;
+  }
+  h.valid = true;
+  TruncIn in = trunc_in_of_slot(c, tmp);
+  const int dst = spare_slot(c, tmp);
+  CKS(truncate_into(c, in, c->cfg.eps, c->cfg.rank_cap, dst));
+  h.valid = false;
+  c->cur = dst;
+  c->has_corr = 0;
+  c->step = 0;
+  CKS(conserved_of_state(c, true));
+  c->has_U = true;
+  CK(cudaStreamSynchronize(c->s));
+  return SLAR_OK;
+}
+
+slar_status ht_truncate(slar_ctx* c, double eps, int cap) {
+  if (!c) return SLAR_EINVAL;
+  if (!(eps >= 0.0) || cap < 1 || cap > SLAR_MAX_RANK) return set_error(c, SLAR_EINVAL, "bad eps or cap");
+  if (!c->ht[c->cur].valid) return set_error(c, SLAR_EINVAL, "no HT state");
+  const int dst = spare_slot(c, c->cur);
+  CKS(truncate_into(c, trunc_in_of_slot(c, c->cur), eps, cap, dst));
+  c->ht[c->cur].valid = false;
+  c->cur = dst;
+  CK(cudaStreamSynchronize(c->s));
+  return SLAR_OK;
+}
+
+slar_status ht_eval(slar_ctx* c, long long n, const int* idx, double* out) {
+  if (!c || n < 0 || (n > 0 && (!idx || !out))) return SLAR_EINVAL;
+  EvalArgs a{};
+  a.mode = EVAL_TUPLES;
+  a.n = n;
+  a.idx = idx;
+  a.out = out;
+  return eval_entries(c, c->cur, true, a, 1);
+}
+
+slar_status sl_eval(slar_ctx* c, double tau, const double* E, long long n, const int* idx, double* out) {
+  if (!c || n < 0 || !E || (n > 0 && (!idx || !out))) return SLAR_EINVAL;
+  EvalArgs a{};
+  a.mode = EVAL_TUPLES;
+  a.n = n;
+  a.idx = idx;
+  a.out = out;
+  a.tau = tau;
+  a.E = E;
+  a.foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
+  return eval_entries(c, c->cur, true, a, 0);
+}
+
+slar_status slar_advect(slar_ctx* c, double tau, const double* E, int* aca_rank, long long* entries) {
+  if (!c || !E) return SLAR_EINVAL;
+  const int dst = spare_slot(c, c->cur);
+  CKS(slar_call(c, c->cur, true, tau, E, dst, aca_rank, entries));
+  c->ht[c->cur].valid = false;
+  c->cur = dst;
+  c->has_corr = 0;
+  return SLAR_OK;
+}
+
+slar_status slar_set_pivot_replay(slar_ctx* c, int n_calls, int kmax, const int* pivots) {
+  if (!c || n_calls < 0 || (n_calls > 0 && (!pivots || kmax < 1))) return SLAR_EINVAL;
+  c->replay.assign(pivots, pivots + (size_t)n_calls * kmax * 2);
+  c->replay_calls = n_calls;
+  c->replay_kmax = kmax;
+  c->replay_pos = 0;
+  return SLAR_OK;
+}
+
+slar_status moments(slar_ctx* c, double* out) {
+  if (!c || !out) return SLAR_EINVAL;
+  return compute_moments(c, c->cur, true, out, c->n_mom);
+}
+
+slar_status poisson_field(slar_ctx* c, const double* rho, double* E, double* phi, double* energy) {
+  if (!c || !rho || !E) return SLAR_EINVAL;
+  CKS(poisson_dev(c, rho, E, phi, energy ? c->Wdev : nullptr));
+  if (energy) {
+    CK(cudaMemcpyAsync(c->scal_host, c->Wdev, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    *energy = c->scal_host[0];
+  }
+  return SLAR_OK;
+}
+
+slar_status ht_export(slar_ctx* c, slar_ht_view* v) {
+  if (!c || !v) return SLAR_EINVAL;
+  const HTBuf& h = c->ht[c->cur];
+  if (!h.valid) return set_error(c, SLAR_EINVAL, "no HT state");
+  v->d = c->d;
+  for (int m = 0; m < 4; ++m) v->N[m] = m < c->d ? c->g.N[m] : 0;
+  for (int i = 0; i < 6; ++i) v->rank[i] = h.r[i];
+  v->has_corr = c->has_corr;
+  bool any_null = !v->Broot;
+  for (int m = 0; m < c->d; ++m) any_null |= !v->U[m];
+  if (c->d == 4) any_null |= (!v->B12 || !v->B34);
+  if (any_null) return SLAR_OK;
+  CK(cudaStreamSynchronize(c->s));
+  for (int m = 0; m < c->d; ++m)
+    CK(cudaMemcpy(v->U[m], h.U[m], sizeof(double) * c->g.N[m] * h.r[m], cudaMemcpyDeviceToHost));
+  if (c->d == 4) {
+    CK(cudaMemcpy(v->B12, h.B12, sizeof(double) * h.r[4] * h.r[0] * h.r[1], cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(v->B34, h.B34, sizeof(double) * h.r[5] * h.r[2] * h.r[3], cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(v->Broot, h.Broot, sizeof(double) * h.r[4] * h.r[5], cudaMemcpyDeviceToHost));
+  } else {
+    CK(cudaMemcpy(v->Broot, h.Broot, sizeof(double) * h.r[0] * h.r[1], cudaMemcpyDeviceToHost));
+  }
+  if (c->has_corr && v->dC && v->qv) {
+    CK(cudaMemcpy(v->dC, c->dC, sizeof(double) * (c->dv + 2) * c->NX, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(v->qv, c->qv, sizeof(double) * 3 * c->dv * c->g.N[c->dx], cudaMemcpyDeviceToHost));
+  }
+  return SLAR_OK;
+}
+
+slar_status ht_import(slar_ctx* c, const slar_ht_view* v) {
+  if (!c || !v) return SLAR_EINVAL;
+  if (v->d != c->d) return set_error(c, SLAR_EINVAL, "dimension mismatch");
+  for (int m = 0; m < c->d; ++m) {
+    if (v->N[m] != c->g.N[m]) return set_error(c, SLAR_EINVAL, "grid mismatch");
+    if (v->rank[m] < 1 || v->rank[m] > SLAR_MAX_RANK || !v->U[m])
+      return set_error(c, SLAR_EINVAL, "bad leaf rank or pointer");
+  }
+  if (c->d == 4)
+    for (int i = 4; i < 6; ++i)
+      if (v->rank[i] < 1 || v->rank[i] > SLAR_MAX_RANK)
+        return set_error(c, SLAR_EINVAL, "bad node rank");
+  if (!v->Broot || (c->d == 4 && (!v->B12 || !v->B34))) return set_error(c, SLAR_EINVAL, "null factor");
+  const int dst = spare_slot(c, c->cur);
+  HTBuf& h = c->ht[dst];
+  for (int m = 0; m < c->d; ++m) {
+    h.r[m] = v->rank[m];
+    CK(cudaMemcpy(h.U[m], v->U[m], sizeof(double) * c->g.N[m] * h.r[m], cudaMemcpyHostToDevice));
+  }
+  if (c->d == 4) {
+    h.r[4] = v->rank[4];
+    h.r[5] = v->rank[5];
+    CK(cudaMemcpy(h.B12, v->B12, sizeof(double) * h.r[4] * h.r[0] * h.r[1], cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h.B34, v->B34, sizeof(double) * h.r[5] * h.r[2] * h.r[3], cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h.Broot, v->Broot, sizeof(double) * h.r[4] * h.r[5], cudaMemcpyHostToDevice));
+  } else {
+    h.r[4] = h.r[5] = 0;
+    CK(cudaMemcpy(h.Broot, v->Broot, sizeof(double) * h.r[0] * h.r[1], cudaMemcpyHostToDevice));
+  }
+  h.valid = true;
+  c->ht[c->cur].valid = false;
+  c->cur = dst;
+  if (c->f32_slot == dst) c->f32_slot = -1;
+  c->has_corr = 0;
+  if (v->has_corr) {
+    if (!v->dC || !v->qv) return set_error(c, SLAR_EINVAL, "correction arrays missing");
+    CK(cudaMemcpy(c->dC, v->dC, sizeof(double) * (c->dv + 2) * c->NX, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->qv, v->qv, sizeof(double) * 3 * c->dv * c->g.N[c->dx], cudaMemcpyHostToDevice));
+    c->has_corr = 1;
+  }
+  return SLAR_OK;
+}
+
+slar_status slar_get_conserved(slar_ctx* c, double* U, double* n_i) {
+  if (!c) return SLAR_EINVAL;
+  if (U) CK(cudaMemcpyAsync(U, c->Uc, sizeof(double) * (c->dv + 2) * c->NX, cudaMemcpyDeviceToDevice, c->s));
+  if (n_i) *n_i = c->n_i;
+  return SLAR_OK;
+}
+
+slar_status slar_set_conserved(slar_ctx* c, const double* U, double n_i) {
+  if (!c || !U) return SLAR_EINVAL;
+  CK(cudaMemcpyAsync(c->Uc, U, sizeof(double) * (c->dv + 2) * c->NX, cudaMemcpyDeviceToDevice, c->s));
+  c->n_i = n_i;
+  c->has_U = true;
+  return SLAR_OK;
+}
+
+slar_status lomac_correct(slar_ctx* c, const double* U_target) {
+  if (!c || !U_target) return SLAR_EINVAL;
+  if (c->has_corr) return set_error(c, SLAR_EINVAL, "state already carries a correction");
+  return lomac_apply(c, U_target);
+}
+
+slar_status sl_step(slar_ctx* c, double dt, slar_stats* stats) {
+  if (!c) return SLAR_EINVAL;
+  if (!c->ht[c->cur].valid || !c->has_U) return set_error(c, SLAR_EINVAL, "call init_ht first");
+  if (!(dt > 0.0)) return set_error(c, SLAR_EINVAL, "dt must be > 0");
+  return step_impl(c, dt, stats);
+}
+
+}  // extern "C"

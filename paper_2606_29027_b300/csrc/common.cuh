@@ -1,0 +1,124 @@
+// Internal declarations shared by the CUDA translation units of libslar.so.
+// Device layouts (all row-major):
+//   leaf U_mu            : N_mu x r_mu        (row = grid index, ranks contiguous)
+//   B12 / B34            : [p][a][b]          (r12 x r0 x r1 / r34 x r2 x r3)
+//   Broot                : r0 x r1 (d = 2) or r12 x r34 (d = 4)
+//   cross factors Ua, Va : column-major M1 x kmax / M2 x kmax (column k contiguous)
+// With this choice a d = 4 cross factor Ua *is* a transfer tensor [p][(a,b)] for identity
+// leaves, so the exact HT embedding of the cross approximation costs no copy.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/slar.h"
+
+#define SLAR_MAX_RANK 64
+#define SLAR_MAX_N 128
+
+namespace slar {
+
+// Number of kernels this library has launched (all contexts); every launch site bumps it.
+long long launch_count();
+int count_launch();
+
+struct GridDesc {
+  int d, dx, dv;
+  int N[4];
+  double lo[4], h[4];
+  int NX;  // prod of spatial N
+  int NV;  // prod of velocity N
+};
+
+template <typename T>
+struct HTView {
+  const T* U[4];
+  int r[4];
+  const T* B12;
+  const T* B34;
+  const T* Broot;
+  int r12, r34;
+};
+
+struct CorrView {
+  const double* dC;  // [dv+2][NX]
+  const double* qv;  // [3][dv][Nv]  omega, q1, q2 per velocity dim
+  int has;
+};
+
+// What the entry evaluator computes for each entry e of a launch.
+enum { EVAL_TUPLES = 0, EVAL_ROW = 1, EVAL_COL = 2 };
+
+struct EvalArgs {
+  int mode;
+  long long n;
+  const int* idx;        // EVAL_TUPLES: [n][d]
+  const int* pivot;      // EVAL_ROW: device pointer to the row pivot; EVAL_COL: to the column pivot
+  const int* done;       // optional device flag: when non-zero the launch does nothing
+  int kterms;            // number of residual terms l < kterms
+  const double* X;       // residual out[e] = val - sum_l X[*pivot + l*ldX] * Y[e + l*ldY]
+  long long ldX;
+  const double* Y;
+  long long ldY;
+  double* out;           // [n]
+  double tau;
+  const double* E;       // [dx][NX] frozen field
+  int foot_euler;
+};
+
+// ---- launchers (defined in the .cu files) ----
+template <typename T>
+cudaError_t launch_sl_eval(const GridDesc& g, const HTView<T>& ht, const CorrView& corr,
+                           const EvalArgs& a, int evaluate_at_grid, cudaStream_t s);
+
+// dense FP64 linear algebra (linalg.cu)
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b]; row-major; op(A) is M x K.
+cudaError_t dgemm(int tA, int tB, int M, int N, int K, double alpha, const double* A, int lda,
+                  long long sA, const double* B, int ldb, long long sB, double beta, double* C,
+                  int ldc, long long sC, int batch, cudaStream_t s);
+// G = A^T A for A column-major m x n (column stride lda); partial sums over row blocks are
+// reduced in a fixed order (deterministic).  work needs nblk*n*n doubles.
+cudaError_t gram_tall(const double* A, long long lda, int m, int n, double* G, double* work,
+                      int work_blocks, cudaStream_t s);
+// out[i][j] = sum_p sum_c X[p][i][c] Y[p][j][c]   (X: P x I x C, Y: P x J x C)
+cudaError_t contract_last(const double* X, const double* Y, int P, int I, int J, int C,
+                          double* out, cudaStream_t s);
+// out[i][j] = sum_p sum_c X[p][c][i] Y[p][c][j]   (X: P x C x I, Y: P x C x J)
+cudaError_t contract_mid(const double* X, const double* Y, int P, int C, int I, int J,
+                         double* out, cudaStream_t s);
+// Cholesky of an n x n SPD matrix (row-major), returns upper R (G = R^T R) and R^{-1};
+// info[0] != 0 on breakdown.
+cudaError_t chol_inv(const double* G, int n, double* R, double* Rinv, int* info, cudaStream_t s);
+// Householder QR of a column-major m x n matrix A (destroyed): Q column-major m x n,
+// R row-major n x n upper triangular, tau[n] scratch.  One CTA; for set-up paths.
+cudaError_t householder_qr(double* A, int m, int n, double* Q, double* R, double* tau,
+                           cudaStream_t s);
+// Symmetric eigendecomposition of a batch of matrices (cyclic Jacobi, one CTA each).
+// A[b]: n_b x n_b row-major (ld = n_b), W[b]: n_b eigenvalues descending,
+// V[b]: n_b x n_b eigenvectors as columns (row-major, ld = n_b).
+struct EigJob {
+  const double* A;
+  double* W;
+  double* V;
+  double* work;  // (n_b+1)^2 doubles scratch (eigenvectors before sorting)
+  int n;
+};
+cudaError_t eig_batched(const EigJob* jobs_host, int njobs, EigJob* jobs_dev, cudaStream_t s);
+// Rank selection from descending eigenvalues: smallest k with tail sum <= thr2, k in [1, cap].
+struct RankJob {
+  const double* W;
+  int n;
+  int cap;
+  int* out;
+};
+cudaError_t choose_ranks(const RankJob* jobs_host, int njobs, RankJob* jobs_dev, const double* normF2,
+                         double scale, cudaStream_t s);
+cudaError_t transpose(const double* A, int rows, int cols, double* B, cudaStream_t s);  // B = A^T
+cudaError_t copy_cols(const double* A, int lda_rows, int rows, int cols, double* B, int ldb,
+                      cudaStream_t s);
+cudaError_t to_float(const double* a, float* b, long long n, cudaStream_t s);
+cudaError_t fill_identity(double* A, int n, int ld, cudaStream_t s);
+cudaError_t fill_zero(double* A, long long n, cudaStream_t s);
+
+}  // namespace slar

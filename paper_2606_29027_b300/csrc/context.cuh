@@ -1,0 +1,199 @@
+// The opaque slar_ctx: configuration, device state and all workspaces (allocated once in
+// slar_create, sized by the grid and the rank limit).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "spectral.cuh"
+
+namespace slar {
+
+constexpr int kProfEvents = 2048;
+constexpr int kPhaseEvents = 256;
+enum { PH_ACA = 0, PH_TRUNC = 1, PH_FIELD = 2, PH_CLOSURE = 3, PH_NEWTON = 4, PH_DIAG = 5, PH_END = 6 };
+// mark the start of a phase on the context stream (no-op unless SLAR_PROFILE)
+void phase(slar_ctx* c, int tag);
+struct MacroWS;
+
+// One HT tensor on the device (capacity: ranks <= SLAR_MAX_RANK).
+struct HTBuf {
+  double* U[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* B12 = nullptr;
+  double* B34 = nullptr;
+  double* Broot = nullptr;
+  int r[6] = {0, 0, 0, 0, 0, 0};  // leaf ranks, r12, r34
+  bool valid = false;
+};
+
+constexpr int NSLOT = 4;
+
+struct AcaState {
+  int k;          // number of accepted cross terms
+  int done;       // set when the cross approximation stops
+  int stop_row;   // 1 if it stopped on a vanishing residual row (that row was sampled)
+  int pad;
+  double normA2;  // running ||A_k||_F^2 estimate
+  double piv;     // current pivot value
+  double nv2;     // ||v_k||^2
+};
+
+}  // namespace slar
+
+struct slar_ctx {
+  slar_config cfg;
+  cudaStream_t s = nullptr;
+  slar::GridDesc g;
+  int d = 0, dx = 0, dv = 0, NX = 0, NV = 0, M1 = 0, M2 = 0, kmax = 0, n_mom = 0;
+  long long capB = 0;
+
+  // HT slots (FP64 master); `cur` holds the state F^n, the others are RKEI stages.
+  // The FP32 shadow mirrors slot `f32_slot` (-1 = stale).
+  slar::HTBuf ht[slar::NSLOT];
+  int cur = 0;
+  int f32_slot = -1;
+  float* U32[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* B12_32 = nullptr;
+  float* B34_32 = nullptr;
+  float* Broot32 = nullptr;
+  double* Ik = nullptr;     // identity (kmax x kmax)
+  double* Lt[2] = {nullptr, nullptr};  // d = 2 cross factors as row-major leaves
+
+  // separable LoMaC correction of the state
+  int has_corr = 0;
+  double* dC = nullptr;   // [dv+2][NX]
+  double* qv = nullptr;   // [3][dv][Nv]
+
+  // macroscopic state
+  double* Uc = nullptr;   // U^n       [dv+2][NX]
+  double* Uh1 = nullptr;  // U^{n-1}
+  double* Uh2 = nullptr;  // U^{n-2}
+  double n_i = 1.0;
+  int step = 0;
+  bool has_U = false;
+
+  // cross approximation
+  double* Ua = nullptr;   // M1 x kmax column-major
+  double* Va = nullptr;   // M2 x kmax
+  double* rowbuf = nullptr;
+  unsigned char* usedr = nullptr;
+  unsigned char* usedc = nullptr;
+  int* pivI = nullptr;
+  int* pivJ = nullptr;
+  slar::AcaState* ast = nullptr;
+  slar::AcaState* ast_host = nullptr;  // pinned
+  double* aca_part = nullptr;          // partial dot products
+  double* aca_dots = nullptr;
+  std::vector<int> replay;             // [calls][kmax][2]
+  int replay_calls = 0, replay_kmax = 0, replay_pos = 0;
+
+  // truncation workspaces
+  double* Qleaf[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* Rleaf[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* T1 = nullptr;
+  double* T2 = nullptr;
+  double* T3 = nullptr;
+  double* Q12 = nullptr;
+  double* Q34 = nullptr;
+  double* Rn[2] = {nullptr, nullptr};
+  double* sm1 = nullptr;  // small scratch matrices (64 x 64 each)
+  double* sm2 = nullptr;
+  double* sm3 = nullptr;
+  double* sm4 = nullptr;
+  double* G[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* W[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* S[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* ework[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* gram_work = nullptr;
+  int gram_work_blocks = 0;
+  double* tau = nullptr;
+  double* norm2 = nullptr;
+  int* d_ranks = nullptr;
+  int* h_ranks = nullptr;  // pinned
+  int* d_info = nullptr;
+  slar::EigJob* d_eig = nullptr;
+  slar::RankJob* d_rank = nullptr;
+
+  // fields, moments, spectral work, LoMaC and Newton-Krylov buffers
+  double* E = nullptr;       // [dx][NX] current field
+  double* E1 = nullptr;
+  double* E2 = nullptr;
+  double* E3 = nullptr;
+  double* mom = nullptr;     // [n_mom][NX]
+  double* lvec = nullptr;    // leaf moment vectors
+  double* spec = nullptr;    // spectral work (complex), several fields
+  long long spec_len = 0;    // in doubles
+  slar::Spectral* spectral = nullptr;
+  double* rho = nullptr;     // [NX]
+  double* Wdev = nullptr;    // device scalars (electric energy, ...)
+  double* macro_ws = nullptr;
+  long long macro_ws_len = 0;
+  double* lomac_bs = nullptr;   // basis scalars of the closure (LS_SIZE)
+  double* lomac_qv = nullptr;   // basis vectors of the closure [3][dv][Nv]
+  double* lomac_C = nullptr;    // C(F*) [dv+2][NX]
+  slar::MacroWS* mw = nullptr;
+  double* scal = nullptr;    // device scalars for the solver
+  double* scal_host = nullptr;  // pinned mirror
+
+  // profiling of the entry evaluator (SLAR_PROFILE): event pairs around every launch
+  cudaEvent_t prof_ev[2048] = {};
+  int prof_n = 0;          // pairs recorded this step
+  cudaEvent_t ph_ev[256] = {};  // phase boundary events (SLAR_PROFILE)
+  int ph_tag[256] = {};
+  int ph_n = 0;
+  double prof_flop = 0.0;  // algorithmic flops of the sampled entries this step
+
+  char err[512] = {0};
+};
+
+namespace slar {
+
+struct TruncIn {
+  int d;
+  int r[6];
+  const double* U[4];  // nullptr = identity leaf (r[mu] == N[mu])
+  const double* B12;
+  const double* B34;
+  const double* Broot;
+  bool fast_qr;        // CholQR2 (inputs of full column rank) instead of Householder QR
+};
+
+slar_status set_error(slar_ctx* c, slar_status st, const char* msg);
+slar_status cuda_fail(slar_ctx* c, cudaError_t e, const char* where);
+// HSVD truncation of `in` written into slot `out_slot` (which must not be an input).
+slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, int out_slot);
+TruncIn trunc_in_of_slot(const slar_ctx* c, int slot);
+HTView<double> view64(const slar_ctx* c, int slot);
+CorrView corr_view(const slar_ctx* c, bool with_corr);
+// evaluate entries of slot (+ the state's correction if with_corr) in the context precision
+slar_status eval_entries(slar_ctx* c, int slot, bool with_corr, const EvalArgs& a, int at_grid);
+// one SLAR call: cross approximation of the SL update of slot `in` (+ correction), then
+// truncation into slot `out`
+slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const double* E, int out,
+                      int* aca_rank, long long* entries);
+// algorithmic flops of one SL entry of a slot: leaf interpolation 3 r_mu per leaf, transfer
+// tensors r_t1 r_t2 r_t, root r12 r34 (multiply-adds x 2), plus 60 for foot and weights
+double entry_flops(const slar_ctx* c, int slot);
+
+// moments / fields / LoMaC / macro (see the respective .cu files)
+slar_status compute_moments(slar_ctx* c, int slot, bool with_corr, double* out, int nmom);
+slar_status field_from_M0(slar_ctx* c, const double* M0, double* E, double* phi, double* W_dev);
+slar_status poisson_dev(slar_ctx* c, const double* rho, double* E, double* phi, double* W_dev);
+slar_status lomac_apply(slar_ctx* c, const double* Utarget);
+slar_status conserved_from_moments(slar_ctx* c, const double* mom, const double* E, double* U);
+slar_status macro_alloc(slar_ctx* c);
+void macro_free(slar_ctx* c);
+slar_status step_impl(slar_ctx* c, double dt, slar_stats* st);
+
+}  // namespace slar
+
+#define CK(call)                                               \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return slar::cuda_fail(c, e_, #call); \
+  } while (0)
+#define CKS(call)                      \
+  do {                                 \
+    slar_status s_ = (call);           \
+    if (s_ != SLAR_OK) return s_;      \
+  } while (0)

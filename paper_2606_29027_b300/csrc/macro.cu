@@ -1,0 +1,732 @@
+// Implicit macroscopic update closed by the LoMaC-corrected kinetic state and the full time
+// step (Sec. 3.2.3, Eq. BE_macro, Eq. BE_nonlinear_system, flowchart; Sec. 4 solver
+// settings), FP64:
+//   K(U) = -D_x . F(U) + S(U), F from U and the flux moments of F^{n+1}(U) =
+//   F* - R(U(F*)) + R(U) (Eq. macro_sys_comp, Eq. electric_field_flux), spectral D_x;
+//   G(U) = U - rhs - coef K(U) solved by Jacobian-free Newton-Krylov: GMRES(m) with
+//   finite-difference J v, classical Gram-Schmidt applied twice, Givens rotations on
+//   device scalars (the host reads one convergence flag per GMRES cycle and one residual
+//   norm per Newton step);
+//   DIRK3 (Alexander 1977, Thm. 5) for the first two steps, fixed-step BDF3 afterwards;
+//   SLAR_VP by the third-order commutator-free RK exponential integrator (Eq. slarvp).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "context.cuh"
+#include "lomac.cuh"
+
+namespace slar {
+
+struct MacroWS {
+  int nvec = 0, m = 0;
+  double *U = nullptr, *G0 = nullptr, *Ut = nullptr, *Gt = nullptr, *rhs = nullptr;
+  double *delta = nullptr, *r = nullptr, *V = nullptr, *Kst[3] = {nullptr, nullptr, nullptr};
+  double *mom_star = nullptr, *Ufs = nullptr;
+  double *fr = nullptr;        // real staging fields
+  double2 *fz = nullptr;       // spectral staging
+  double *part = nullptr;      // reduction partials
+  double *sc = nullptr;        // device scalars
+  double *tot = nullptr;       // totals
+  int nblk = 0;
+};
+
+namespace {
+
+constexpr int RED_SEG = 1024;
+// scalar layout (sc)
+constexpr int SC_H = 0;                 // (m+1) x m, m <= 64
+constexpr int SC_G = SC_H + 65 * 64;    // m+1
+constexpr int SC_CS = SC_G + 65;
+constexpr int SC_SN = SC_CS + 64;
+constexpr int SC_Y = SC_SN + 64;
+constexpr int SC_MISC = SC_Y + 64;      // beta, bnorm, done, jdone, tmp...
+enum { M_BETA = 0, M_BNORM, M_DONE, M_JDONE, M_NORM, M_RTOL, M_INF, M_UNORM };
+constexpr int SC_SIZE = SC_MISC + 16;
+
+// ---------------- reductions ----------------
+// part[blk][i] = sum over the block's segment of V_i . w   (i < nv), V_i = V + i*ld
+__global__ void k_mdot(const double* __restrict__ V, long long ld, int nv, const double* __restrict__ w,
+                       int n, double* __restrict__ part, int ldp, const double* done) {
+  if (done && done[0] != 0.0) return;
+  const int s0 = blockIdx.x * RED_SEG;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < nv; i += 8) {
+    const double* v = V + i * ld;
+    double acc = 0.0;
+    for (int e = s0 + lane; e < s0 + RED_SEG && e < n; e += 32) acc += v[e] * w[e];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[(long long)blockIdx.x * ldp + i] = acc;
+  }
+}
+
+// out[i] (+)= sum_blk part[blk][i]
+__global__ void k_mdot_fin(const double* part, int nblk, int ldp, int nv, double* out, int accumulate,
+                           const double* done) {
+  if (done && done[0] != 0.0) return;
+  const int i = threadIdx.x;
+  if (i >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(long long)b * ldp + i];
+  out[i] = accumulate ? out[i] + s : s;
+}
+
+__global__ void k_absmax_part(const double* __restrict__ x, int n, double* part) {
+  __shared__ double red[8];
+  double m = 0.0;
+  for (int e = blockIdx.x * RED_SEG + threadIdx.x; e < (blockIdx.x + 1) * RED_SEG && e < n; e += 256)
+    m = fmax(m, fabs(x[e]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t = fmax(t, red[w]);
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_absmax_fin(const double* part, int nblk, double* out) {
+  if (threadIdx.x != 0) return;
+  double t = 0.0;
+  for (int b = 0; b < nblk; ++b) t = fmax(t, part[b]);
+  out[0] = t;
+}
+
+// w -= sum_{i<nv} coef[i] V_i  (coef on device); sign = -1 subtracts, +1 adds
+__global__ void k_axpy_multi(double* __restrict__ w, int n, const double* __restrict__ V, long long ld,
+                             int nv, const double* coef, const int* nv_dev, double sign,
+                             const double* done) {
+  if (done && done[0] != 0.0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int k = nv_dev ? *nv_dev : nv;
+  double s = 0.0;
+  for (int i = 0; i < k; ++i) s += coef[i] * V[i * ld + e];
+  w[e] += sign * s;
+}
+
+// out = (a - b) * s ;  used for w = (G(U + h v) - G0) / h
+__global__ void k_diff_scale(const double* a, const double* b, double s, double* out, int n,
+                             const double* done) {
+  if (done && done[0] != 0.0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = (a[e] - b[e]) * s;
+}
+
+// out = a + s * b (s host scalar)
+__global__ void k_axpby(const double* a, double s, const double* b, double* out, int n,
+                        const double* done) {
+  if (done && done[0] != 0.0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = a[e] + s * b[e];
+}
+
+// out = x / sqrt(*nrm2) ; stores sqrt in *dst
+__global__ void k_normalize(const double* x, const double* nrm2, double* out, int n, double* dst,
+                            const double* done) {
+  if (done && done[0] != 0.0) return;
+  const double nr = sqrt(fmax(nrm2[0], 0.0));
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = nr > 0.0 ? x[e] / nr : 0.0;
+  if (e == 0 && dst) dst[0] = nr;
+}
+
+// Givens update of column j of H, residual estimate and the convergence flag
+__global__ void k_givens(double* sc, int j, int m, int* kcount) {
+  if (threadIdx.x != 0) return;
+  double* misc = sc + SC_MISC;
+  if (misc[M_DONE] != 0.0) return;
+  double* H = sc + SC_H;  // H[i*m + j]
+  double* g = sc + SC_G;
+  double* cs = sc + SC_CS;
+  double* sn = sc + SC_SN;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+    H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+    H[i * m + j] = t;
+  }
+  const double a = H[j * m + j], b = H[(j + 1) * m + j];
+  const double den = hypot(a, b);
+  cs[j] = den > 0.0 ? a / den : 1.0;
+  sn[j] = den > 0.0 ? b / den : 0.0;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  misc[M_JDONE] = j + 1;
+  kcount[0] += 1;
+  if (fabs(g[j + 1]) <= misc[M_RTOL] * misc[M_BNORM] || b == 0.0 || j + 1 == m) misc[M_DONE] = 1.0;
+}
+
+// y = H^{-1} g (upper triangular, jdone x jdone)
+__global__ void k_solve_upper(double* sc, int m, int* jd) {
+  if (threadIdx.x != 0) return;
+  double* H = sc + SC_H;
+  double* g = sc + SC_G;
+  double* y = sc + SC_Y;
+  const int k = (int)sc[SC_MISC + M_JDONE];
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * y[l];
+    y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
+  }
+  jd[0] = k;
+}
+
+__global__ void k_gmres_start(double* sc, const double* beta2, double rtol, int first, double* bn) {
+  if (threadIdx.x != 0) return;
+  double* misc = sc + SC_MISC;
+  const double beta = sqrt(fmax(beta2[0], 0.0));
+  misc[M_BETA] = beta;
+  if (first) misc[M_BNORM] = beta;
+  misc[M_RTOL] = rtol;
+  misc[M_JDONE] = 0;
+  for (int i = 0; i < 65; ++i) sc[SC_G + i] = 0.0;
+  sc[SC_G] = beta;
+  misc[M_DONE] = (beta <= rtol * misc[M_BNORM] || beta == 0.0) ? 1.0 : 0.0;
+  if (bn) bn[0] = misc[M_DONE];
+}
+
+// ---------------- the residual ----------------
+// stage 1: rho = n_i - U0 and the momentum components as real fields
+__global__ void k_prep(const double* U, double n_i, int NX, int dx, double* fr) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= NX) return;
+  fr[x] = n_i - U[x];
+  for (int m = 0; m < dx; ++m) fr[(long long)(1 + m) * NX + x] = U[(long long)(1 + m) * NX + x];
+}
+
+// stage 2 (spectral): phi, E = -grad phi, d_t phi with -Lap(d_t phi) = div(U1), grad(d_t phi)
+__global__ void k_spec_fields(Spectral sp, const double2* zin, double2* zout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sp.NX) return;
+  const int dx = sp.dx;
+  double k[2];
+  if (dx == 1) k[0] = sp.kv[0][i];
+  else { k[0] = sp.kv[0][i / sp.n[1]]; k[1] = sp.kv[1][i % sp.n[1]]; }
+  double k2 = 0.0;
+  for (int m = 0; m < dx; ++m) k2 += k[m] * k[m];
+  const double2 rh = zin[i];
+  double2 ph = make_double2(0.0, 0.0);
+  if (k2 > 0.0) ph = make_double2(rh.x / k2, rh.y / k2);
+  double2 dv = make_double2(0.0, 0.0);
+  for (int m = 0; m < dx; ++m) {
+    const double2 z = zin[(long long)(1 + m) * sp.NX + i];
+    dv.x += -k[m] * z.y;
+    dv.y += k[m] * z.x;
+  }
+  double2 tp = make_double2(0.0, 0.0);
+  if (k2 > 0.0) tp = make_double2(dv.x / k2, dv.y / k2);
+  zout[i] = ph;
+  for (int m = 0; m < dx; ++m) {
+    zout[(long long)(1 + m) * sp.NX + i] = make_double2(k[m] * ph.y, -k[m] * ph.x);        // -i k phi
+    zout[(long long)(1 + dx + m) * sp.NX + i] = make_double2(-k[m] * tp.y, k[m] * tp.x);  // i k tp
+  }
+}
+
+// stage 3: fluxes F[eq][dir] and sources from U, phi, E, grad(d_t phi) and the closure
+__global__ void k_flux(int dx, int dv, int NX, int nmom, const double* U, const double* fr2,
+                       const double* mom_star, const double* Cstar, const double* bs, double* flux,
+                       double* src) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= NX) return;
+  const double phi = fr2[x];
+  double E[2], gt[2];
+  double ep = 0.0;
+  for (int m = 0; m < dx; ++m) {
+    E[m] = fr2[(long long)(1 + m) * NX + x];
+    gt[m] = fr2[(long long)(1 + dx + m) * NX + x];
+    ep += E[m] * E[m];
+  }
+  ep *= 0.5;
+  const double U0 = U[x];
+  double U1[2];
+  for (int m = 0; m < dv; ++m) U1[m] = U[(long long)(1 + m) * NX + x];
+  const double U2 = U[(long long)(1 + dv) * NX + x];
+  double C[4];
+  lomac_coeffs(dv, bs, U0, U1, 2.0 * (U2 - ep), C);
+  double dC[4];
+  for (int k = 0; k < dv + 2; ++k) dC[k] = C[k] - Cstar[(long long)k * NX + x];
+  auto mnew = [&](int a) {
+    double s = mom_star[(long long)a * NX + x];
+    for (int k = 0; k < dv + 2; ++k) s += bs[LS_TABLE + a * (dv + 2) + k] * dC[k];
+    return s;
+  };
+  const int neq = dv + 2;
+  // F[eq][dir] at flux[(eq*dx + dir)*NX + x]
+  for (int a = 0; a < dx; ++a) flux[((long long)0 * dx + a) * NX + x] = U1[a];
+  if (dv == 1) {
+    const double Pi = mnew(3), Q3 = mnew(4);
+    flux[((long long)1 * dx + 0) * NX + x] = Pi;
+    flux[((long long)2 * dx + 0) * NX + x] = 0.5 * Q3 - phi * gt[0] - U1[0] * phi;
+  } else {
+    const double P11 = mnew(4), P12 = mnew(5), P22 = mnew(6), Q1 = mnew(7), Q2 = mnew(8);
+    flux[((long long)1 * dx + 0) * NX + x] = P11;
+    flux[((long long)1 * dx + 1) * NX + x] = P12;
+    flux[((long long)2 * dx + 0) * NX + x] = P12;
+    flux[((long long)2 * dx + 1) * NX + x] = P22;
+    flux[((long long)3 * dx + 0) * NX + x] = 0.5 * Q1 - phi * gt[0] - U1[0] * phi;
+    flux[((long long)3 * dx + 1) * NX + x] = 0.5 * Q2 - phi * gt[1] - U1[1] * phi;
+  }
+  (void)neq;
+  (void)nmom;
+  for (int b = 0; b < dv; ++b) src[(long long)b * NX + x] = -U0 * E[b];
+}
+
+// stage 4: out = K(U) = -div + S   or   out = U - rhs - coef K(U)
+__global__ void k_final(int dv, int NX, const double* div, const double* src, const double* U,
+                        const double* rhs, double coef, double* out, int mode_g) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= NX) return;
+  for (int e = 0; e < dv + 2; ++e) {
+    double K = -div[(long long)e * NX + x];
+    if (e >= 1 && e <= dv) K += src[(long long)(e - 1) * NX + x];
+    const long long id = (long long)e * NX + x;
+    out[id] = mode_g ? (U[id] - rhs[id] - coef * K) : K;
+  }
+}
+
+__global__ void k_totals(const double* U, int nvar, int NX, double cell, double* out) {
+  __shared__ double red[32];
+  const int v = blockIdx.x;
+  double s = 0.0;
+  for (int x = threadIdx.x; x < NX; x += blockDim.x) s += U[(long long)v * NX + x];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[v] = t * cell;
+  }
+}
+
+__global__ void k_lincomb3(double* out, const double* a, double ca, const double* b, double cb,
+                           const double* cc_, double cc, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double s = ca * a[e];
+  if (b) s += cb * b[e];
+  if (cc_) s += cc * cc_[e];
+  out[e] = s;
+}
+
+__global__ void k_field_comb(const double* E1, const double* E3, double* Ec, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) Ec[e] = -E1[e] / 8.0 + 9.0 * E3[e] / 8.0;
+}
+
+inline unsigned nb(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+slar_status macro_alloc(slar_ctx* c) {
+  MacroWS* w = new MacroWS();
+  c->mw = w;
+  w->nvec = (c->dv + 2) * c->NX;
+  w->m = c->cfg.krylov_restart;
+  w->nblk = (w->nvec + RED_SEG - 1) / RED_SEG;
+  const long long n = w->nvec;
+  const int nfr = (c->dv + 2) * c->dx + 1 + 2 * c->dx + c->dv + (c->dv + 2) + 4;
+  long long total = n * (7 + (w->m + 1) + 3) + (long long)c->n_mom * c->NX + n +
+                    (long long)nfr * c->NX + 2LL * ((c->dv + 2) * c->dx + 1 + 2 * c->dx) * c->NX +
+                    (long long)w->nblk * 72 + SC_SIZE + 16 + LS_SIZE + 3LL * c->dv * c->g.N[c->dx] +
+                    (long long)(c->dv + 2) * c->NX + 64;
+  if (cudaMalloc(&c->macro_ws, sizeof(double) * total) != cudaSuccess) return SLAR_ENOMEM;
+  c->macro_ws_len = total;
+  double* p = c->macro_ws;
+  auto take = [&](long long k) { double* q = p; p += k; return q; };
+  w->U = take(n); w->G0 = take(n); w->Ut = take(n); w->Gt = take(n); w->rhs = take(n);
+  w->delta = take(n); w->r = take(n);
+  w->V = take(n * (w->m + 1));
+  for (int i = 0; i < 3; ++i) w->Kst[i] = take(n);
+  w->mom_star = take((long long)c->n_mom * c->NX);
+  w->Ufs = take(n);
+  w->fr = take((long long)nfr * c->NX);
+  w->fz = reinterpret_cast<double2*>(take(2LL * ((c->dv + 2) * c->dx + 1 + 2 * c->dx) * c->NX));
+  w->part = take((long long)w->nblk * 72);
+  w->sc = take(SC_SIZE);
+  w->tot = take(16);
+  c->lomac_bs = take(LS_SIZE);
+  c->lomac_qv = take(3LL * c->dv * c->g.N[c->dx]);
+  c->lomac_C = take((long long)(c->dv + 2) * c->NX);
+  return SLAR_OK;
+}
+
+void macro_free(slar_ctx* c) {
+  delete c->mw;
+  c->mw = nullptr;
+}
+
+namespace {
+
+// out = K(U) (mode_g = 0) or G(U) = U - rhs - coef K(U) (mode_g = 1)
+slar_status eval_residual(slar_ctx* c, const double* U, const double* rhs, double coef, double* out,
+                          int mode_g) {
+  MacroWS* w = c->mw;
+  const Spectral& sp = *c->spectral;
+  const int NX = c->NX, dx = c->dx, dv = c->dv;
+  cudaStream_t s = c->s;
+  double* fr = w->fr;
+  double2* fz = w->fz;
+  const int nf1 = 1 + dx;                  // rho, U1
+  const int nf2 = 1 + 2 * dx;              // phi, E, grad d_t phi
+  const int nflux = (dv + 2) * dx;
+  double* fr2 = fr + (long long)nf1 * NX;
+  double* flux = fr2 + (long long)nf2 * NX;
+  double* src = flux + (long long)nflux * NX;
+  double* div = src + (long long)dv * NX;
+  double2* z1 = fz;
+  double2* z2 = fz + (long long)nflux * NX;
+  slar::count_launch(), k_prep<<<nb(NX), 256, 0, s>>>(U, c->n_i, NX, dx, fr);
+  CK(cudaGetLastError());
+  CK(sp.forward(fr, z1, nf1));
+  slar::count_launch(), k_spec_fields<<<nb(NX), 256, 0, s>>>(sp, z1, z2);
+  CK(cudaGetLastError());
+  CK(sp.inverse(z2, fr2, nf2));
+  slar::count_launch(), k_flux<<<nb(NX), 256, 0, s>>>(dx, dv, NX, c->n_mom, U, fr2, w->mom_star, c->lomac_C, c->lomac_bs,
+                                flux, src);
+  CK(cudaGetLastError());
+  CK(sp.forward(flux, z1, nflux));
+  CK(spec_div(sp, z1, dv + 2, z2));
+  CK(sp.inverse(z2, div, dv + 2));
+  slar::count_launch(), k_final<<<nb(NX), 256, 0, s>>>(dv, NX, div, src, U, rhs, coef, out, mode_g);
+  CK(cudaGetLastError());
+  return SLAR_OK;
+}
+
+slar_status dot_into(slar_ctx* c, const double* V, long long ld, int nv, const double* x, double* out,
+                     int accumulate, const double* done) {
+  MacroWS* w = c->mw;
+  slar::count_launch(), k_mdot<<<w->nblk, 256, 0, c->s>>>(V, ld, nv, x, w->nvec, w->part, 72, done);
+  CK(cudaGetLastError());
+  slar::count_launch(), k_mdot_fin<<<1, 128, 0, c->s>>>(w->part, w->nblk, 72, nv, out, accumulate, done);
+  CK(cudaGetLastError());
+  return SLAR_OK;
+}
+
+slar_status absmax(slar_ctx* c, const double* x, double* out_dev) {
+  MacroWS* w = c->mw;
+  slar::count_launch(), k_absmax_part<<<w->nblk, 256, 0, c->s>>>(x, w->nvec, w->part);
+  CK(cudaGetLastError());
+  slar::count_launch(), k_absmax_fin<<<1, 32, 0, c->s>>>(w->part, w->nblk, out_dev);
+  CK(cudaGetLastError());
+  return SLAR_OK;
+}
+
+__global__ void k_hcol_acc(double* H, const double* hcol, int m, int j, int pass, const double* done) {
+  if (done && done[0] != 0.0) return;
+  const int i = threadIdx.x;
+  if (i > j) return;
+  if (pass == 0) H[i * m + j] = hcol[i];
+  else H[i * m + j] += hcol[i];
+}
+
+__global__ void k_set_sub(double* H, const double* nrm2, int m, int j, const double* done) {
+  if (done && done[0] != 0.0) return;
+  if (threadIdx.x == 0) H[(j + 1) * m + j] = sqrt(fmax(nrm2[0], 0.0));
+}
+
+
+struct SolveStats {
+  int newton = 0, krylov = 0;
+  double residual = 0.0;
+  bool converged = false;
+};
+
+// JFNK on G(U) = U - rhs - coef K(U); w->U holds the initial guess and the result.
+slar_status jfnk(slar_ctx* c, double coef, double tol_abs, SolveStats* st) {
+  MacroWS* w = c->mw;
+  phase(c, PH_NEWTON);
+  cudaStream_t s = c->s;
+  const int n = w->nvec, m = w->m;
+  double* sc = w->sc;
+  double* misc = sc + SC_MISC;
+  int* kcount = reinterpret_cast<int*>(w->tot + 8);
+  CK(cudaMemsetAsync(kcount, 0, sizeof(int) * 2, s));
+  const double sqeps = std::sqrt(std::ldexp(1.0, -52));
+  CKS(eval_residual(c, w->U, w->rhs, coef, w->G0, 1));
+  for (int it = 0;; ++it) {
+    CKS(absmax(c, w->G0, misc + M_INF));
+    CKS(dot_into(c, w->U, 0, 1, w->U, misc + M_UNORM, 0, nullptr));
+    CK(cudaMemcpyAsync(c->scal_host, misc, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double ginf = c->scal_host[M_INF];
+    const double unorm = std::sqrt(c->scal_host[M_UNORM]);
+    st->residual = ginf;
+    if (!(ginf == ginf)) return set_error(c, SLAR_ENAN, "non-finite Newton residual");
+    if (ginf <= tol_abs) { st->converged = true; break; }
+    if (it >= c->cfg.newton_max) break;
+    // GMRES(m) on J delta = -G0 from delta = 0
+    const double h = sqeps * (1.0 + unorm);  // ||v_j|| = 1
+    CK(cudaMemsetAsync(w->delta, 0, sizeof(double) * n, s));
+    int kry = 0;
+    bool first = true;
+    while (true) {
+      // r = -G0 - J delta   (J delta by a finite difference when delta != 0)
+      if (first) {
+        slar::count_launch(), k_lincomb3<<<nb(n), 256, 0, s>>>(w->r, w->G0, -1.0, nullptr, 0.0, nullptr, 0.0, n);
+      } else {
+        double dn2;
+        CKS(dot_into(c, w->delta, 0, 1, w->delta, misc + M_NORM, 0, nullptr));
+        CK(cudaMemcpyAsync(c->scal_host, misc + M_NORM, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        dn2 = std::sqrt(c->scal_host[0]);
+        const double hd = sqeps * (1.0 + unorm) / (dn2 > 0.0 ? dn2 : 1.0);
+        slar::count_launch(), k_axpby<<<nb(n), 256, 0, s>>>(w->U, hd, w->delta, w->Ut, n, nullptr);
+        CKS(eval_residual(c, w->Ut, w->rhs, coef, w->Gt, 1));
+        // r = -G0 - (Gt - G0)/hd = -Gt/hd + G0 (1/hd - 1)
+        slar::count_launch(), k_lincomb3<<<nb(n), 256, 0, s>>>(w->r, w->Gt, -1.0 / hd, w->G0, 1.0 / hd - 1.0, nullptr, 0.0, n);
+      }
+      CK(cudaGetLastError());
+      CKS(dot_into(c, w->r, 0, 1, w->r, misc + M_NORM, 0, nullptr));
+      slar::count_launch(), k_gmres_start<<<1, 32, 0, s>>>(sc, misc + M_NORM, c->cfg.krylov_tol, first ? 1 : 0, nullptr);
+      CK(cudaGetLastError());
+      slar::count_launch(), k_normalize<<<nb(n), 256, 0, s>>>(w->r, misc + M_NORM, w->V, n, nullptr, misc + M_DONE);
+      CK(cudaGetLastError());
+      const double* done = misc + M_DONE;
+      for (int j = 0; j < m; ++j) {
+        double* vj = w->V + (long long)j * n;
+        double* wv = w->V + (long long)(j + 1) * n;
+        slar::count_launch(), k_axpby<<<nb(n), 256, 0, s>>>(w->U, h, vj, w->Ut, n, done);
+        CK(cudaGetLastError());
+        CKS(eval_residual(c, w->Ut, w->rhs, coef, w->Gt, 1));
+        slar::count_launch(), k_diff_scale<<<nb(n), 256, 0, s>>>(w->Gt, w->G0, 1.0 / h, wv, n, done);
+        CK(cudaGetLastError());
+        // classical Gram-Schmidt, twice; H[i][j] for i <= j
+        double* hcol = sc + SC_Y;  // temporary coefficient column
+        for (int pass = 0; pass < 2; ++pass) {
+          CKS(dot_into(c, w->V, n, j + 1, wv, hcol, 0, done));
+          slar::count_launch(), k_axpy_multi<<<nb(n), 256, 0, s>>>(wv, n, w->V, n, j + 1, hcol, nullptr, -1.0, done);
+          CK(cudaGetLastError());
+          slar::count_launch(), k_hcol_acc<<<1, 128, 0, s>>>(sc + SC_H, hcol, m, j, pass, done);
+          CK(cudaGetLastError());
+        }
+        CKS(dot_into(c, wv, 0, 1, wv, misc + M_NORM, 0, done));
+        slar::count_launch(), k_set_sub<<<1, 32, 0, s>>>(sc + SC_H, misc + M_NORM, m, j, done);
+        slar::count_launch(), k_normalize<<<nb(n), 256, 0, s>>>(wv, misc + M_NORM, wv, n, nullptr, done);
+        slar::count_launch(), k_givens<<<1, 32, 0, s>>>(sc, j, m, kcount);
+        CK(cudaGetLastError());
+      }
+      slar::count_launch(), k_solve_upper<<<1, 32, 0, s>>>(sc, m, kcount + 1);
+      slar::count_launch(), k_axpy_multi<<<nb(n), 256, 0, s>>>(w->delta, n, w->V, n, m, sc + SC_Y, kcount + 1, 1.0, nullptr);
+      CK(cudaGetLastError());
+      // converged? (true residual estimate below tolerance)
+      CK(cudaMemcpyAsync(c->scal_host, misc, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(c->h_ranks + 12, kcount, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      kry = c->h_ranks[12];
+      const double* ms = c->scal_host;
+      const int jd = (int)ms[M_JDONE];
+      // the cycle converged if it stopped before m iterations or met the tolerance
+      double gres;
+      CK(cudaMemcpy(&gres, sc + SC_G + jd, sizeof(double), cudaMemcpyDeviceToHost));
+      const bool conv = std::fabs(gres) <= ms[M_RTOL] * ms[M_BNORM] || jd == 0;
+      first = false;
+      if (conv || kry >= c->cfg.krylov_max) break;
+    }
+    st->krylov += kry;
+    CK(cudaMemsetAsync(kcount, 0, sizeof(int) * 2, s));
+    slar::count_launch(), k_axpby<<<nb(n), 256, 0, s>>>(w->U, 1.0, w->delta, w->U, n, nullptr);
+    CK(cudaGetLastError());
+    CKS(eval_residual(c, w->U, w->rhs, coef, w->G0, 1));
+    st->newton += 1;
+  }
+  return SLAR_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// E of a slot (HT [+ the state's correction]): M0 -> rho = n_i - M0 -> Poisson
+slar_status field_of_slot(slar_ctx* c, int slot, bool with_corr, double* E) {
+  phase(c, PH_FIELD);
+  CKS(compute_moments(c, slot, with_corr, c->mom, 1));
+  return field_from_M0(c, c->mom, E, nullptr, nullptr);
+}
+
+struct VPInfo {
+  long long entries = 0;
+  int aca[3] = {0, 0, 0};
+};
+
+// F* = SLAR_VP(F^n; dt) by CF3 (Eq. slarvp): Y2 = exp(dt/3 F(Y1)) Y1,
+// Y3 = exp(2dt/3 F(Y2)) Y1, F* = exp(dt (-F(Y1)/12 + 3F(Y3)/4)) Y2, the last being a
+// frozen-field advection over 2dt/3 with E_c = -E1/8 + 9E3/8.  Returns the slot of F*.
+slar_status slar_vp(slar_ctx* c, double dt, int* out_slot, VPInfo* info) {
+  const int S = c->cur;
+  int fr[3], k = 0;
+  for (int i = 0; i < NSLOT; ++i)
+    if (i != S) fr[k++] = i;
+  const int A = fr[0], B = fr[1];
+  long long e[3] = {0, 0, 0};
+  CKS(field_of_slot(c, S, true, c->E1));
+  CKS(slar_call(c, S, true, dt / 3.0, c->E1, A, &info->aca[0], &e[0]));
+  CKS(field_of_slot(c, A, false, c->E2));
+  CKS(slar_call(c, S, true, 2.0 * dt / 3.0, c->E2, B, &info->aca[1], &e[1]));
+  CKS(field_of_slot(c, B, false, c->E3));
+  slar::count_launch(), k_field_comb<<<nb((long long)c->dx * c->NX), 256, 0, c->s>>>(c->E1, c->E3, c->E, c->dx * c->NX);
+  CK(cudaGetLastError());
+  CKS(slar_call(c, A, false, 2.0 * dt / 3.0, c->E, B, &info->aca[2], &e[2]));
+  c->ht[A].valid = false;
+  info->entries = e[0] + e[1] + e[2];
+  *out_slot = B;
+  return SLAR_OK;
+}
+
+// closure data of F* in `slot`: LoMaC basis, moments, C(F*), U(F*) (Newton initial guess)
+slar_status make_closure(slar_ctx* c, int slot) {
+  MacroWS* w = c->mw;
+  phase(c, PH_CLOSURE);
+  CKS(lomac_basis(c, slot, c->lomac_qv, c->lomac_bs));
+  CKS(compute_moments(c, slot, false, w->mom_star, c->n_mom));
+  CKS(coeffs_from_moments(c, c->lomac_bs, w->mom_star, c->lomac_C));
+  CKS(field_from_M0(c, w->mom_star, c->E, nullptr, nullptr));
+  return conserved_from_moments(c, w->mom_star, c->E, w->Ufs);
+}
+
+double host_absmax(slar_ctx* c, const double* x, slar_status* st) {
+  *st = absmax(c, x, c->mw->tot);
+  if (*st != SLAR_OK) return 0.0;
+  cudaMemcpyAsync(c->scal_host, c->mw->tot, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+  cudaStreamSynchronize(c->s);
+  return c->scal_host[0];
+}
+
+void dirk3_tableau(double A[3][3], double cst[3]) {
+  double g = 0.4358665215;
+  for (int i = 0; i < 60; ++i) {
+    const double f = g * g * g - 3 * g * g + 1.5 * g - 1.0 / 6.0;
+    const double df = 3 * g * g - 6 * g + 1.5;
+    g -= f / df;
+  }
+  const double b1 = -(6 * g * g - 16 * g + 1) / 4.0, b2 = (6 * g * g - 20 * g + 5) / 4.0;
+  const double a[3][3] = {{g, 0, 0}, {(1 - g) / 2.0, g, 0}, {b1, b2, g}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A[i][j] = a[i][j];
+  cst[0] = g;
+  cst[1] = (1 + g) / 2.0;
+  cst[2] = 1.0;
+}
+
+}  // namespace
+
+slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
+  MacroWS* w = c->mw;
+  cudaStream_t s = c->s;
+  const int n = w->nvec;
+  slar_stats st{};
+  st.converged = 1;
+  int fslot = -1;
+  const long long launches0 = launch_count();
+  c->prof_n = 0;
+  c->prof_flop = 0.0;
+  c->ph_n = 0;
+  const bool lomac = (c->cfg.flags & SLAR_LOMAC) != 0;
+  if (!lomac) {
+    VPInfo vi;
+    CKS(slar_vp(c, dt, &fslot, &vi));
+    st.entries = vi.entries;
+    for (int i = 0; i < 3; ++i) st.aca_rank[i] = vi.aca[i];
+    st.n_slar = 3;
+    c->ht[c->cur].valid = false;
+    c->cur = fslot;
+    c->has_corr = 0;
+    double* t = c->Uh2; c->Uh2 = c->Uh1; c->Uh1 = c->Uc; c->Uc = t;
+    CKS(compute_moments(c, c->cur, false, c->mom, c->dv + 2));
+    CKS(field_from_M0(c, c->mom, c->E, nullptr, nullptr));
+    CKS(conserved_from_moments(c, c->mom, c->E, c->Uc));
+  } else {
+    slar_status e0;
+    const double tol_abs = c->cfg.newton_tol * std::max(1.0, host_absmax(c, c->Uc, &e0));
+    CKS(e0);
+    if (c->step < 2) {
+      double A[3][3], cst[3];
+      dirk3_tableau(A, cst);
+      for (int i = 0; i < 3; ++i) {
+        VPInfo vi;
+        CKS(slar_vp(c, cst[i] * dt, &fslot, &vi));
+        st.entries += vi.entries;
+        for (int q = 0; q < 3; ++q) st.aca_rank[3 * i + q] = vi.aca[q];
+        CKS(make_closure(c, fslot));
+        // rhs = U^n + dt sum_{j<i} a_ij K_j
+        CK(cudaMemcpyAsync(w->rhs, c->Uc, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        for (int j = 0; j < i; ++j)
+          slar::count_launch(), k_axpby<<<nb(n), 256, 0, s>>>(w->rhs, dt * A[i][j], w->Kst[j], w->rhs, n, nullptr);
+        CK(cudaMemcpyAsync(w->U, w->Ufs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        SolveStats ss;
+        CKS(jfnk(c, dt * A[i][i], tol_abs, &ss));
+        st.newton += ss.newton;
+        st.krylov += ss.krylov;
+        st.residual = std::max(st.residual, ss.residual);
+        st.converged &= ss.converged ? 1 : 0;
+        CKS(eval_residual(c, w->U, nullptr, 0.0, w->Kst[i], 0));
+        if (i < 2) c->ht[fslot].valid = false;
+      }
+      st.n_slar = 9;
+    } else {
+      VPInfo vi;
+      CKS(slar_vp(c, dt, &fslot, &vi));
+      st.entries = vi.entries;
+      for (int i = 0; i < 3; ++i) st.aca_rank[i] = vi.aca[i];
+      st.n_slar = 3;
+      CKS(make_closure(c, fslot));
+      // BDF3: U - (18 U^n - 9 U^{n-1} + 2 U^{n-2}) / 11 - (6/11) dt K(U) = 0
+      slar::count_launch(), k_lincomb3<<<nb(n), 256, 0, s>>>(w->rhs, c->Uc, 18.0 / 11.0, c->Uh1, -9.0 / 11.0, c->Uh2,
+                                       2.0 / 11.0, n);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(w->U, w->Ufs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      SolveStats ss;
+      CKS(jfnk(c, 6.0 / 11.0 * dt, tol_abs, &ss));
+      st.newton = ss.newton;
+      st.krylov = ss.krylov;
+      st.residual = ss.residual;
+      st.converged = ss.converged ? 1 : 0;
+    }
+    // F^{n+1} = F* - R(U(F*)) + R(U^{n+1}); history shift
+    double* t = c->Uh2; c->Uh2 = c->Uh1; c->Uh1 = c->Uc; c->Uc = t;
+    CK(cudaMemcpyAsync(c->Uc, w->U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    c->ht[c->cur].valid = false;
+    c->cur = fslot;
+    CKS(dC_from_U(c, c->lomac_bs, c->Uc, c->lomac_C, c->dC));
+    CK(cudaMemcpyAsync(c->qv, c->lomac_qv, sizeof(double) * 3 * c->dv * c->g.N[c->dx],
+                       cudaMemcpyDeviceToDevice, s));
+    c->has_corr = 1;
+  }
+  for (int i = 0; i < 6; ++i) st.ranks[i] = c->ht[c->cur].r[i];
+  // diagnostics: electric energy and totals of U^{n+1}
+  phase(c, PH_DIAG);
+  CKS(field_from_M0(c, c->Uc, c->E, nullptr, c->Wdev));
+  double cell = 1.0;
+  for (int m = 0; m < c->dx; ++m) cell *= c->g.h[m];
+  slar::count_launch(), k_totals<<<c->dv + 2, 256, 0, s>>>(c->Uc, c->dv + 2, c->NX, cell, w->tot);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->scal_host, c->Wdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->scal_host + 1, w->tot, sizeof(double) * (c->dv + 2), cudaMemcpyDeviceToHost, s));
+  phase(c, PH_END);
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i + 1 < c->ph_n; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ph_ev[i], c->ph_ev[i + 1]));
+    if (c->ph_tag[i] < 6) st.phase_ms[c->ph_tag[i]] += ms;
+  }
+  c->ph_n = 0;
+  st.field_energy = c->scal_host[0];
+  for (int k = 0; k < c->dv + 2; ++k) st.totals[k] = c->scal_host[1 + k];
+  st.eval_flop = c->prof_flop;
+  st.eval_ms = 0.0;
+  for (int i = 0; i < c->prof_n; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
+    st.eval_ms += ms;
+  }
+  c->prof_n = 0;
+  st.launches = launch_count() - launches0;
+  c->step += 1;
+  if (out) *out = st;
+  return st.converged ? SLAR_OK : set_error(c, SLAR_ENOCONV, "Newton-Krylov did not converge");
+}
+
+}  // namespace slar

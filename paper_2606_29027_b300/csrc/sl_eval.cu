@@ -1,0 +1,383 @@
+// The local SL-FD entry evaluator on an HT tensor (Sec. 3.1, Eq. SL_basic_formulation and
+// Eq. tp_interp evaluated in HT form).
+//
+// One CTA evaluates TILE entries:
+//   1. foot: backward characteristic of the frozen-field advection through the entry's grid
+//      point (Kutta RK3 on dz/ds = (-v, E(x)), E interpolated with the tensor-product
+//      quadratic weights; or the first-order foot), then per dimension the cell j and the
+//      weights w(xi) of Eq. 1d_quadratic_interp_weight.  Always FP64; written with explicit
+//      round-to-nearest intrinsics (no FMA contraction) so the cell choice is reproducible.
+//   2. leaf gathers c^(mu) = w . U^(mu)[j-1..j+1, :]  (coalesced row loads, staged in smem)
+//   3. transfer-tensor contractions c12 = B12 x1 c0 x2 c1 (a [TILE x r0 r1] x [r0 r1 x r12]
+//      product whose left operand -- the outer products c0 (x) c1 -- is formed on the fly),
+//      likewise c34; B is streamed through shared memory in K-chunks.
+//   4. root: c12 . Broot . c34 (warp-shuffle reduction)
+//   5. separable LoMaC correction (if present) and, for cross-approximation fibres, the
+//      residual epilogue out = value - sum_l X[pivot, l] Y[e, l].
+// T = double (FP64 path) or float (FP32 path: gathers and contractions in FP32).
+#include "common.cuh"
+
+namespace slar {
+namespace {
+
+constexpr int NTHREADS = 256;
+constexpr int KC = 32;          // K-chunk of the transfer-tensor contraction
+constexpr int PSTRIDE = 65;     // padded row of the staged B chunk (p <= 64)
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+// cell and quadratic weights of coordinate y in dimension m (oracle: grid.locate/weights)
+__device__ __forceinline__ void cell_weights(const GridDesc& g, int m, double y, int rows[3],
+                                             double w[3]) {
+  double t = __ddiv_rn(dsub(y, g.lo[m]), g.h[m]);
+  if (!(fabs(t) < 1e15)) t = 0.0;  // non-finite or absurd feet still index inside the grid
+  double jf = floor(t);
+  double xi = dsub(dsub(t, jf), 0.5);
+  double hx = dmul(0.5, xi);
+  w[0] = dmul(hx, dsub(xi, 1.0));
+  w[1] = dsub(1.0, dmul(xi, xi));
+  w[2] = dmul(hx, dadd(xi, 1.0));
+  int n = g.N[m];
+  long long j = (long long)jf;
+  long long r0 = (j - 1) % n;
+  if (r0 < 0) r0 += n;
+  rows[0] = (int)r0;
+  rows[1] = (int)((r0 + 1) % n);
+  rows[2] = (int)((r0 + 2) % n);
+}
+
+// tensor-product quadratic interpolation of a spatial field at point p (dx dims),
+// lexicographic stencil order, acc = acc + (w1 w2) v  (oracle: sl.interp_spatial)
+__device__ double interp_spatial(const GridDesc& g, const double* F, const double* p) {
+  int r0[3], r1[3];
+  double w0[3], w1[3];
+  cell_weights(g, 0, p[0], r0, w0);
+  double acc = 0.0;
+  if (g.dx == 1) {
+    for (int s = 0; s < 3; ++s) acc = dadd(acc, dmul(w0[s], F[r0[s]]));
+    return acc;
+  }
+  cell_weights(g, 1, p[1], r1, w1);
+  const int N1 = g.N[1];
+  for (int s0 = 0; s0 < 3; ++s0)
+    for (int s1 = 0; s1 < 3; ++s1)
+      acc = dadd(acc, dmul(dmul(w0[s0], w1[s1]), F[r0[s0] * N1 + r1[s1]]));
+  return acc;
+}
+
+__device__ __forceinline__ double centre(const GridDesc& g, int m, int i) {
+  return dadd(g.lo[m], dmul((double)i + 0.5, g.h[m]));
+}
+
+// backward foot of the frozen-field characteristic (oracle: sl.trace_feet)
+__device__ void trace_foot(const GridDesc& g, const double* E, double tau, int euler,
+                           const int* idx, double* foot) {
+  const int dx = g.dx;
+  double x[2], v[2];
+  for (int m = 0; m < dx; ++m) {
+    x[m] = centre(g, m, idx[m]);
+    v[m] = centre(g, dx + m, idx[dx + m]);
+  }
+  const long long NX = g.NX;
+  if (euler) {
+    for (int m = 0; m < dx; ++m) {
+      double e = interp_spatial(g, E + m * NX, x);
+      foot[m] = dsub(x[m], dmul(v[m], tau));
+      foot[dx + m] = dadd(v[m], dmul(e, tau));
+    }
+    return;
+  }
+  const double h = tau;
+  const double half = h / 2.0, two_h = 2.0 * h, sixth = __ddiv_rn(h, 6.0);
+  double k1x[2], k1v[2], x2[2], v2[2], k2x[2], k2v[2], x3[2], v3[2], k3x[2], k3v[2];
+  for (int m = 0; m < dx; ++m) {
+    k1x[m] = -v[m];
+    k1v[m] = interp_spatial(g, E + m * NX, x);
+  }
+  for (int m = 0; m < dx; ++m) {
+    x2[m] = dadd(x[m], dmul(half, k1x[m]));
+    v2[m] = dadd(v[m], dmul(half, k1v[m]));
+  }
+  for (int m = 0; m < dx; ++m) {
+    k2x[m] = -v2[m];
+    k2v[m] = interp_spatial(g, E + m * NX, x2);
+  }
+  for (int m = 0; m < dx; ++m) {
+    x3[m] = dadd(dsub(x[m], dmul(h, k1x[m])), dmul(two_h, k2x[m]));
+    v3[m] = dadd(dsub(v[m], dmul(h, k1v[m])), dmul(two_h, k2v[m]));
+  }
+  for (int m = 0; m < dx; ++m) {
+    k3x[m] = -v3[m];
+    k3v[m] = interp_spatial(g, E + m * NX, x3);
+  }
+  for (int m = 0; m < dx; ++m) {
+    foot[m] = dadd(x[m], dmul(sixth, dadd(dadd(k1x[m], dmul(4.0, k2x[m])), k3x[m])));
+    foot[dx + m] = dadd(v[m], dmul(sixth, dadd(dadd(k1v[m], dmul(4.0, k2v[m])), k3v[m])));
+  }
+}
+
+// quadratic 1D interpolation of a velocity vector (oracle: grid.interp_1d)
+__device__ __forceinline__ double interp_1d(const GridDesc& g, int m, const double* vec, double y) {
+  int r[3];
+  double w[3];
+  cell_weights(g, m, y, r, w);
+  return (w[0] * vec[r[0]] + w[1] * vec[r[1]]) + w[2] * vec[r[2]];
+}
+
+// separable LoMaC correction sum_k dC_k(x*) Q_k(v*) at a foot (oracle: sl.correction_at)
+__device__ double correction_at(const GridDesc& g, const CorrView& c, const double* foot) {
+  const int dx = g.dx, dv = g.dv;
+  const long long NX = g.NX;
+  const int Nv = g.N[dx];
+  double dCi[4];
+  for (int k = 0; k < dv + 2; ++k) dCi[k] = interp_spatial(g, c.dC + k * NX, foot);
+  double om[2], q1[2], q2[2];
+  for (int m = 0; m < dv; ++m) {
+    const double y = foot[dx + m];
+    om[m] = interp_1d(g, dx + m, c.qv + (0 * dv + m) * Nv, y);
+    q1[m] = interp_1d(g, dx + m, c.qv + (1 * dv + m) * Nv, y);
+    q2[m] = interp_1d(g, dx + m, c.qv + (2 * dv + m) * Nv, y);
+  }
+  // terms in the order (0: prod omega), (1+m: q1 at m), (1+dv: q2 at m) for m = 0..dv-1
+  double out = 0.0;
+  double t = dCi[0];
+  for (int m = 0; m < dv; ++m) t *= om[m];
+  out += t;
+  for (int j = 0; j < dv; ++j) {
+    t = dCi[1 + j];
+    for (int m = 0; m < dv; ++m) t *= (m == j ? q1[m] : om[m]);
+    out += t;
+  }
+  for (int j = 0; j < dv; ++j) {
+    t = dCi[1 + dv];
+    for (int m = 0; m < dv; ++m) t *= (m == j ? q2[m] : om[m]);
+    out += t;
+  }
+  return out;
+}
+
+struct Smem {
+  double* foot;  // [TILE][4]
+  double* w;     // [TILE][4][3]
+  int* rows;     // [TILE][4][3]
+};
+
+// c_out[t][p] = sum_{a,b} ca[t][a] cb[t][b] B[p][a][b]   for t < nT, p < rp
+template <typename T, int TILE>
+__device__ void contract_node(const T* __restrict__ ca, int ra, const T* __restrict__ cb, int rb,
+                              const T* __restrict__ B, int rp, T* __restrict__ cout, T* sB, int nT) {
+  constexpr int TPT = TILE / 8;  // entries per thread
+  const int tid = threadIdx.x;
+  const int tg = tid >> 5, lane = tid & 31;
+  const int K = ra * rb;
+  T acc[TPT][2];
+#pragma unroll
+  for (int i = 0; i < TPT; ++i) acc[i][0] = acc[i][1] = T(0);
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    const int kc = min(KC, K - k0);
+    __syncthreads();
+    for (int it = tid; it < kc * rp; it += NTHREADS) {
+      const int p = it / kc, kk = it - p * kc;
+      sB[kk * PSTRIDE + p] = B[(long long)p * K + k0 + kk];
+    }
+    __syncthreads();
+    int a = k0 / rb, b = k0 - a * rb;
+    for (int kk = 0; kk < kc; ++kk) {
+      const T b0 = (lane < rp) ? sB[kk * PSTRIDE + lane] : T(0);
+      const T b1 = (lane + 32 < rp) ? sB[kk * PSTRIDE + lane + 32] : T(0);
+#pragma unroll
+      for (int i = 0; i < TPT; ++i) {
+        const int t = tg * TPT + i;
+        const T x = ca[t * ra + a] * cb[t * rb + b];
+        acc[i][0] += x * b0;
+        acc[i][1] += x * b1;
+      }
+      if (++b == rb) { b = 0; ++a; }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TPT; ++i) {
+    const int t = tg * TPT + i;
+    if (t < nT) {
+      if (lane < rp) cout[t * rp + lane] = acc[i][0];
+      if (lane + 32 < rp) cout[t * rp + lane + 32] = acc[i][1];
+    }
+  }
+}
+
+__device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& a, long long e,
+                                             int* idx) {
+  if (a.mode == EVAL_TUPLES) {
+    for (int m = 0; m < g.d; ++m) idx[m] = a.idx[e * g.d + m];
+    return;
+  }
+  const long long left = (a.mode == EVAL_ROW) ? (long long)(*a.pivot) : e;
+  const long long right = (a.mode == EVAL_ROW) ? e : (long long)(*a.pivot);
+  if (g.d == 2) {
+    idx[0] = (int)left;
+    idx[1] = (int)right;
+  } else {
+    idx[0] = (int)(left / g.N[1]);
+    idx[1] = (int)(left % g.N[1]);
+    idx[2] = (int)(right / g.N[3]);
+    idx[3] = (int)(right % g.N[3]);
+  }
+}
+
+template <typename T, int TILE>
+__global__ void __launch_bounds__(NTHREADS)
+k_sl_eval(GridDesc g, HTView<T> ht, CorrView corr, EvalArgs a, int at_grid) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.done && *a.done) return;
+  const long long e0 = (long long)blockIdx.x * TILE;
+  if (e0 >= a.n) return;
+  const int nT = (int)min((long long)TILE, a.n - e0);
+  const int tid = threadIdx.x;
+  const int d = g.d;
+
+  double* sfoot = reinterpret_cast<double*>(smem_raw);        // TILE*4
+  double* sw = sfoot + TILE * 4;                               // TILE*12
+  double* sval = sw + TILE * 12;                               // TILE
+  int* srow = reinterpret_cast<int*>(sval + TILE);             // TILE*12
+  T* sc = reinterpret_cast<T*>(srow + TILE * 12);              // leaves
+  T* sc_mu[4];
+  {
+    T* p = sc;
+    for (int m = 0; m < d; ++m) { sc_mu[m] = p; p += TILE * ht.r[m]; }
+    sc = p;
+  }
+  T* sc12 = sc;
+  T* sc34 = sc12 + (d == 4 ? TILE * ht.r12 : 0);
+  T* sB = sc34 + (d == 4 ? TILE * ht.r34 : 0);
+
+  // 1. feet and weights
+  if (tid < nT) {
+    int idx[4];
+    decode_tuple(g, a, e0 + tid, idx);
+    double foot[4];
+    if (at_grid) {
+      for (int m = 0; m < d; ++m) foot[m] = centre(g, m, idx[m]);
+    } else {
+      trace_foot(g, a.E, a.tau, a.foot_euler, idx, foot);
+    }
+    for (int m = 0; m < d; ++m) {
+      int r[3];
+      double w[3];
+      if (at_grid) {
+        r[0] = idx[m]; r[1] = idx[m]; r[2] = idx[m];
+        w[0] = 0.0; w[1] = 1.0; w[2] = 0.0;
+      } else {
+        cell_weights(g, m, foot[m], r, w);
+      }
+      for (int s = 0; s < 3; ++s) {
+        srow[(tid * 4 + m) * 3 + s] = r[s];
+        sw[(tid * 4 + m) * 3 + s] = w[s];
+      }
+      sfoot[tid * 4 + m] = foot[m];
+    }
+  }
+  __syncthreads();
+
+  // 2. leaf gathers
+  for (int m = 0; m < d; ++m) {
+    const int r = ht.r[m];
+    const T* U = ht.U[m];
+    T* c = sc_mu[m];
+    for (int it = tid; it < TILE * r; it += NTHREADS) {
+      const int t = it / r, q = it - t * r;
+      T val = T(0);
+      if (t < nT) {
+        const int* rr = srow + (t * 4 + m) * 3;
+        const double* ww = sw + (t * 4 + m) * 3;
+        val = T(ww[0]) * U[(long long)rr[0] * r + q] + T(ww[1]) * U[(long long)rr[1] * r + q] +
+              T(ww[2]) * U[(long long)rr[2] * r + q];
+      }
+      c[it] = val;
+    }
+  }
+  __syncthreads();
+
+  // 3. transfer tensors
+  const T* left;
+  const T* right;
+  int rl, rr;
+  if (d == 4) {
+    contract_node<T, TILE>(sc_mu[0], ht.r[0], sc_mu[1], ht.r[1], ht.B12, ht.r12, sc12, sB, nT);
+    contract_node<T, TILE>(sc_mu[2], ht.r[2], sc_mu[3], ht.r[3], ht.B34, ht.r34, sc34, sB, nT);
+    left = sc12; right = sc34; rl = ht.r12; rr = ht.r34;
+  } else {
+    left = sc_mu[0]; right = sc_mu[1]; rl = ht.r[0]; rr = ht.r[1];
+  }
+  __syncthreads();
+
+  // 4. root: sum_p left[t][p] sum_q Broot[p][q] right[t][q]
+  {
+    constexpr int TPE = NTHREADS / TILE;  // threads per entry
+    const int t = tid / TPE, sub = tid - t * TPE;
+    T acc = T(0);
+    if (t < nT) {
+      for (int p = sub; p < rl; p += TPE) {
+        T s = T(0);
+        const T* Bp = ht.Broot + (long long)p * rr;
+        for (int q = 0; q < rr; ++q) s += Bp[q] * right[t * rr + q];
+        acc += left[t * rl + p] * s;
+      }
+    }
+#pragma unroll
+    for (int off = TPE / 2; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, TPE);
+    if (sub == 0 && t < TILE) sval[t] = (double)acc;
+  }
+  __syncthreads();
+
+  // 5. correction and residual epilogue
+  if (tid < nT) {
+    double val = sval[tid];
+    if (corr.has) val += correction_at(g, corr, sfoot + tid * 4);
+    const long long e = e0 + tid;
+    if (a.X) {
+      const int k = a.kterms;
+      const long long piv = (long long)(*a.pivot);
+      for (int l = 0; l < k; ++l) val -= a.X[piv + l * a.ldX] * a.Y[e + l * a.ldY];
+    }
+    a.out[e] = val;
+  }
+}
+
+template <typename T, int TILE>
+size_t smem_bytes(const GridDesc& g, const HTView<T>& ht) {
+  size_t b = sizeof(double) * (TILE * 4 + TILE * 12 + TILE) + sizeof(int) * TILE * 12;
+  int rs = 0;
+  for (int m = 0; m < g.d; ++m) rs += ht.r[m];
+  if (g.d == 4) rs += ht.r12 + ht.r34;
+  b += sizeof(T) * ((size_t)TILE * rs + (g.d == 4 ? KC * PSTRIDE : 0));
+  return (b + 15) & ~size_t(15);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_sl_eval(const GridDesc& g, const HTView<T>& ht, const CorrView& corr,
+                           const EvalArgs& a, int at_grid, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  constexpr int TILE = sizeof(T) == 8 ? 32 : 64;
+  const size_t sm = smem_bytes<T, TILE>(g, ht);
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(T) == 8]) {
+    cudaError_t e = cudaFuncSetAttribute(k_sl_eval<T, TILE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set[sizeof(T) == 8] = true;
+  }
+  const long long blocks = (a.n + TILE - 1) / TILE;
+  slar::count_launch(), k_sl_eval<T, TILE><<<(unsigned)blocks, NTHREADS, sm, s>>>(g, ht, corr, a, at_grid);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_sl_eval<double>(const GridDesc&, const HTView<double>&,
+                                            const CorrView&, const EvalArgs&, int, cudaStream_t);
+template cudaError_t launch_sl_eval<float>(const GridDesc&, const HTView<float>&,
+                                           const CorrView&, const EvalArgs&, int, cudaStream_t);
+
+}  // namespace slar

@@ -1,0 +1,309 @@
+"""Thin ctypes binding of libslar.so (include/slar.h).  Argument marshalling only: every
+step of the method runs in the library's CUDA kernels.  Device arrays are torch CUDA
+tensors (float64 / int32, contiguous); host arrays are numpy.
+
+The library must have been built (``python -m paper_2606_29027_b300.build``); importing
+this module without it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libslar.so")
+
+SLAR_OK, SLAR_EINVAL, SLAR_ENOMEM, SLAR_ECUDA, SLAR_ENOCONV, SLAR_ETIMEOUT, SLAR_ERANK, SLAR_ENAN = range(8)
+SLAR_FP64, SLAR_FP32 = 0, 1
+SLAR_LOMAC, SLAR_FOOT_EULER, SLAR_PROFILE = 1, 2, 4
+
+# every entry point declared in include/slar.h
+EXPORTED = ["slar_create", "slar_destroy", "slar_last_error", "init_ht", "sl_step", "ht_truncate",
+            "moments", "lomac_correct", "poisson_field", "ht_eval", "sl_eval", "slar_advect",
+            "slar_set_pivot_replay", "ht_export", "ht_import", "slar_get_conserved",
+            "slar_set_conserved", "slar_sizes", "slar_launch_count"]
+
+
+class Config(C.Structure):
+    _fields_ = [("dx", C.c_int), ("dv", C.c_int), ("N", C.c_int * 4), ("lo", C.c_double * 4),
+                ("hi", C.c_double * 4), ("eps", C.c_double), ("rank_cap", C.c_int),
+                ("newton_tol", C.c_double), ("krylov_tol", C.c_double), ("krylov_restart", C.c_int),
+                ("newton_max", C.c_int), ("krylov_max", C.c_int), ("precision", C.c_int),
+                ("flags", C.c_int), ("delta_floor", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("entries", C.c_longlong), ("ranks", C.c_int * 6), ("aca_rank", C.c_int * 9),
+                ("n_slar", C.c_int), ("newton", C.c_int), ("krylov", C.c_int),
+                ("residual", C.c_double), ("converged", C.c_int), ("field_energy", C.c_double),
+                ("totals", C.c_double * 4), ("eval_ms", C.c_double), ("eval_flop", C.c_double),
+                ("launches", C.c_longlong), ("phase_ms", C.c_double * 6)]
+
+    def to_dict(self):
+        return dict(entries=self.entries, ranks=list(self.ranks), aca_rank=list(self.aca_rank[: self.n_slar]),
+                    newton=self.newton, krylov=self.krylov, residual=self.residual,
+                    converged=bool(self.converged), field_energy=self.field_energy,
+                    totals=list(self.totals), eval_ms=self.eval_ms, eval_flop=self.eval_flop,
+                    launches=self.launches, phase_ms=list(self.phase_ms))
+
+
+class HTView(C.Structure):
+    _fields_ = [("d", C.c_int), ("N", C.c_int * 4), ("rank", C.c_int * 6),
+                ("U", C.POINTER(C.c_double) * 4), ("B12", C.POINTER(C.c_double)),
+                ("B34", C.POINTER(C.c_double)), ("Broot", C.POINTER(C.c_double)),
+                ("has_corr", C.c_int), ("dC", C.POINTER(C.c_double)), ("qv", C.POINTER(C.c_double))]
+
+
+_lib = None
+
+
+def load():
+    """Load libslar.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} not built; run python -m paper_2606_29027_b300.build")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, LL = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+    sig = {
+        "slar_create": ([C.POINTER(Config), P, C.POINTER(P)], I),
+        "slar_destroy": ([P], I),
+        "slar_last_error": ([P], C.c_char_p),
+        "init_ht": ([P, I, P], I),
+        "sl_step": ([P, D, C.POINTER(Stats)], I),
+        "ht_truncate": ([P, D, I], I),
+        "moments": ([P, P], I),
+        "lomac_correct": ([P, P], I),
+        "poisson_field": ([P, P, P, P, C.POINTER(D)], I),
+        "ht_eval": ([P, LL, P, P], I),
+        "sl_eval": ([P, D, P, LL, P, P], I),
+        "slar_advect": ([P, D, P, C.POINTER(I), C.POINTER(LL)], I),
+        "slar_set_pivot_replay": ([P, I, I, P], I),
+        "ht_export": ([P, C.POINTER(HTView)], I),
+        "ht_import": ([P, C.POINTER(HTView)], I),
+        "slar_get_conserved": ([P, P, C.POINTER(D)], I),
+        "slar_set_conserved": ([P, P, D], I),
+        "slar_sizes": ([P, C.POINTER(I), C.POINTER(I)], I),
+        "slar_launch_count": ([C.POINTER(LL)], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    n = C.c_longlong()
+    st = load().slar_launch_count(C.byref(n))
+    if st != SLAR_OK:
+        raise SlarError(st, "slar_launch_count failed")
+    return n.value
+
+
+class SlarError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"slar status {status}: {msg}")
+        self.status = status
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous torch tensor (0 for None)."""
+    if t is None:
+        return 0
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, eps=1e-6, rank_cap=16,
+                newton_tol=1e-12, krylov_tol=1e-4, krylov_restart=30, newton_max=20, krylov_max=200,
+                precision="fp64", lomac=True, foot="rk3", delta_floor=1e-12, profile=False) -> Config:
+    if workload is not None:
+        dx, dv, N, lo, hi = workload.dx, workload.dv, workload.N, workload.lo, workload.hi
+        eps, rank_cap = workload.eps, workload.rank_cap
+        newton_tol, krylov_tol, lomac = workload.newton_tol, workload.krylov_tol, workload.lomac
+    cfg = Config()
+    cfg.dx, cfg.dv = dx, dv
+    d = dx + dv
+    for m in range(4):
+        cfg.N[m] = int(N[m]) if m < d else 1
+        cfg.lo[m] = float(lo[m]) if m < d else 0.0
+        cfg.hi[m] = float(hi[m]) if m < d else 1.0
+    cfg.eps, cfg.rank_cap = eps, rank_cap
+    cfg.newton_tol, cfg.krylov_tol = newton_tol, krylov_tol
+    cfg.krylov_restart, cfg.newton_max, cfg.krylov_max = krylov_restart, newton_max, krylov_max
+    cfg.precision = SLAR_FP32 if precision == "fp32" else SLAR_FP64
+    cfg.flags = ((SLAR_LOMAC if lomac else 0) | (SLAR_FOOT_EULER if foot == "euler" else 0)
+                 | (SLAR_PROFILE if profile else 0))
+    cfg.delta_floor = delta_floor
+    return cfg
+
+
+class Context:
+    """One library context bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, cfg: Config, stream=None):
+        import torch
+        self.lib = load()
+        self.cfg = cfg
+        self.d = cfg.dx + cfg.dv
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        st = self.lib.slar_create(C.byref(cfg), C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st != SLAR_OK:
+            raise SlarError(st, "slar_create failed")
+        self.h = h
+        nm, nx = C.c_int(), C.c_int()
+        self.lib.slar_sizes(self.h, C.byref(nm), C.byref(nx))
+        self.n_mom, self.NX = nm.value, nx.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.slar_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != SLAR_OK:
+            raise SlarError(st, self.lib.slar_last_error(self.h).decode())
+
+    # ---- entry points ----
+    def init_ht(self, factors):
+        """factors: [term][mu] -> 1D numpy arrays."""
+        T = len(factors)
+        flat = np.concatenate([np.concatenate([np.asarray(f, np.float64) for f in term]) for term in factors])
+        flat = np.ascontiguousarray(flat)
+        self._check(self.lib.init_ht(self.h, T, flat.ctypes.data_as(C.c_void_p)))
+
+    def step(self, dt: float) -> Stats:
+        st = Stats()
+        status = self.lib.sl_step(self.h, dt, C.byref(st))
+        if status not in (SLAR_OK, SLAR_ENOCONV):
+            self._check(status)
+        st.status = status
+        return st
+
+    def truncate(self, eps: float, cap: int):
+        self._check(self.lib.ht_truncate(self.h, eps, cap))
+
+    def moments(self, out):
+        self._check(self.lib.moments(self.h, C.c_void_p(_ptr(out))))
+
+    def lomac_correct(self, U_target):
+        self._check(self.lib.lomac_correct(self.h, C.c_void_p(_ptr(U_target))))
+
+    def poisson_field(self, rho, E, phi=None) -> float:
+        W = C.c_double()
+        self._check(self.lib.poisson_field(self.h, C.c_void_p(_ptr(rho)), C.c_void_p(_ptr(E)),
+                                           C.c_void_p(_ptr(phi)), C.byref(W)))
+        return W.value
+
+    def ht_eval(self, idx, out):
+        self._check(self.lib.ht_eval(self.h, idx.shape[0], C.c_void_p(_ptr(idx)), C.c_void_p(_ptr(out))))
+
+    def sl_eval(self, tau, E, idx, out):
+        self._check(self.lib.sl_eval(self.h, tau, C.c_void_p(_ptr(E)), idx.shape[0],
+                                     C.c_void_p(_ptr(idx)), C.c_void_p(_ptr(out))))
+
+    def advect(self, tau, E):
+        k, n = C.c_int(), C.c_longlong()
+        self._check(self.lib.slar_advect(self.h, tau, C.c_void_p(_ptr(E)), C.byref(k), C.byref(n)))
+        return k.value, n.value
+
+    def set_pivot_replay(self, calls):
+        """calls: list (per SLAR call) of lists of (i, j) pivots."""
+        if not calls:
+            self._check(self.lib.slar_set_pivot_replay(self.h, 0, 1, None))
+            return
+        kmax = max(len(c) for c in calls) + 1
+        arr = -np.ones((len(calls), kmax, 2), dtype=np.int32)
+        for a, piv in enumerate(calls):
+            for k, (i, j) in enumerate(piv):
+                arr[a, k] = (i, j)
+        arr = np.ascontiguousarray(arr)
+        self._check(self.lib.slar_set_pivot_replay(self.h, len(calls), kmax, arr.ctypes.data_as(C.c_void_p)))
+
+    def get_conserved(self, U_out):
+        ni = C.c_double()
+        self._check(self.lib.slar_get_conserved(self.h, C.c_void_p(_ptr(U_out)), C.byref(ni)))
+        return ni.value
+
+    def set_conserved(self, U, n_i):
+        self._check(self.lib.slar_set_conserved(self.h, C.c_void_p(_ptr(U)), float(n_i)))
+
+    def export(self) -> dict:
+        """Copy the HT state to host: dict(U=[...], B12, B34, Broot, dC, qv) in the library
+        layouts ([p][a][b] transfer tensors)."""
+        v = HTView()
+        self._check(self.lib.ht_export(self.h, C.byref(v)))
+        d = v.d
+        r = list(v.rank)
+        N = list(v.N)
+        out = dict(d=d, ranks=r, N=N, has_corr=bool(v.has_corr))
+        U = [np.zeros((N[m], r[m])) for m in range(d)]
+        for m in range(d):
+            v.U[m] = _dptr(U[m])
+        if d == 4:
+            B12 = np.zeros((r[4], r[0], r[1]))
+            B34 = np.zeros((r[5], r[2], r[3]))
+            Broot = np.zeros((r[4], r[5]))
+            v.B12, v.B34 = _dptr(B12), _dptr(B34)
+        else:
+            B12 = B34 = None
+            Broot = np.zeros((r[0], r[1]))
+        v.Broot = _dptr(Broot)
+        dv = self.cfg.dv
+        dC = np.zeros((dv + 2, self.NX))
+        qv = np.zeros((3, dv, N[self.cfg.dx]))
+        v.dC, v.qv = _dptr(dC), _dptr(qv)
+        self._check(self.lib.ht_export(self.h, C.byref(v)))
+        out.update(U=U, B12=B12, B34=B34, Broot=Broot)
+        if out["has_corr"]:
+            out.update(dC=dC, qv=qv)
+        return out
+
+    def import_ht(self, U, Broot, B12=None, B34=None, dC=None, qv=None):
+        """Set the state from host arrays in the library layouts."""
+        v = HTView()
+        v.d = self.d
+        keep = []
+        for m in range(self.d):
+            u = np.ascontiguousarray(U[m], dtype=np.float64)
+            keep.append(u)
+            v.N[m] = u.shape[0]
+            v.rank[m] = u.shape[1]
+            v.U[m] = _dptr(u)
+        br = np.ascontiguousarray(Broot, dtype=np.float64)
+        keep.append(br)
+        v.Broot = _dptr(br)
+        if self.d == 4:
+            b12 = np.ascontiguousarray(B12, dtype=np.float64)
+            b34 = np.ascontiguousarray(B34, dtype=np.float64)
+            keep += [b12, b34]
+            v.B12, v.B34 = _dptr(b12), _dptr(b34)
+            v.rank[4], v.rank[5] = b12.shape[0], b34.shape[0]
+        if dC is not None:
+            dc = np.ascontiguousarray(dC, dtype=np.float64)
+            q = np.ascontiguousarray(qv, dtype=np.float64)
+            keep += [dc, q]
+            v.has_corr = 1
+            v.dC, v.qv = _dptr(dc), _dptr(q)
+        self._check(self.lib.ht_import(self.h, C.byref(v)))
