@@ -50,7 +50,10 @@ enum { SLAR_FP64 = 0, SLAR_FP32 = 1 };
 enum {
     SLAR_LOMAC = 1,        /* apply the implicit LoMaC correction every step (Sec. 3.2) */
     SLAR_FOOT_EULER = 2,   /* first-order foot (x - v tau, v + E tau) instead of RK3 */
-    SLAR_PROFILE = 4       /* time every entry-evaluator launch with CUDA events (stats) */
+    SLAR_PROFILE = 4,      /* CUDA events at phase boundaries (stats.phase_ms) */
+    SLAR_PROFILE_EVAL = 8  /* CUDA events around every entry-evaluator launch (stats.eval_ms);
+                              the cross approximation then runs as individual launches
+                              instead of its captured CUDA graph */
 };
 
 typedef struct slar_config {
@@ -79,7 +82,7 @@ typedef struct slar_stats {
     int converged;          /* 1 if every Newton solve met its tolerance */
     double field_energy;    /* W = 1/2 sum |E|^2 dx^dx of the new state */
     double totals[4];       /* mass, momentum (dv components), energy of U^{n+1} */
-    double eval_ms;         /* SLAR_PROFILE: summed device time of the entry-evaluator launches */
+    double eval_ms;         /* SLAR_PROFILE_EVAL: summed device time of the evaluator launches */
     double eval_flop;       /* algorithmic flops of the sampled entries this step */
     long long launches;     /* kernels this library launched during the step */
     double phase_ms[6];     /* SLAR_PROFILE: device time of cross approximation, truncation,

@@ -58,11 +58,13 @@ __device__ void block_argmax_tie(const double* a, int n, const unsigned char* us
   __syncthreads();
 }
 
-__global__ void k_aca_init(AcaState* st, int* pivI, unsigned char* usedr, int replay) {
+__global__ void k_aca_init(AcaState* st, int* pivI, unsigned char* usedr, int replay, double eps) {
   if (threadIdx.x != 0) return;
   st->k = 0;
   st->done = 0;
   st->stop_row = 0;
+  st->replay = replay;
+  st->eps = eps;
   st->normA2 = 0.0;
   if (!replay) pivI[0] = 0;
   if (pivI[0] < 0) { st->done = 1; return; }
@@ -71,11 +73,14 @@ __global__ void k_aca_init(AcaState* st, int* pivI, unsigned char* usedr, int re
 
 // column pivot from the residual row r, v_k = r / r[j_k]
 __global__ void __launch_bounds__(PIV_THREADS)
-k_aca_row_pivot(const double* __restrict__ r, int M2, unsigned char* usedc, int* pivJ, int kk,
-                AcaState* st, double* __restrict__ vout, int replay) {
+k_aca_row_pivot(const double* __restrict__ r, int M2, unsigned char* usedc, int* pivJ,
+                AcaState* st, double* __restrict__ Va) {
   __shared__ int j_s;
   __shared__ double top_s;
   if (st->done) return;
+  const int kk = st->k;
+  const int replay = st->replay;
+  double* vout = Va + (long long)kk * M2;
   if (replay) {
     if (threadIdx.x == 0) { j_s = pivJ[kk]; top_s = 1.0; }
     __syncthreads();
@@ -98,9 +103,10 @@ k_aca_row_pivot(const double* __restrict__ r, int M2, unsigned char* usedc, int*
 
 // partial dot products of u_k with U_l (l < kk) and itself, v_k with V_l and itself
 __global__ void __launch_bounds__(256)
-k_aca_dots(const double* __restrict__ Ua, int M1, const double* __restrict__ Va, int M2, int kk,
+k_aca_dots(const double* __restrict__ Ua, int M1, const double* __restrict__ Va, int M2,
            int nbu, const AcaState* st, double* __restrict__ part, int ldp) {
   if (st->done) return;
+  const int kk = st->k;
   const int blk = blockIdx.x;
   const bool isu = blk < nbu;
   const double* X = isu ? Ua : Va;
@@ -119,15 +125,22 @@ k_aca_dots(const double* __restrict__ Ua, int M1, const double* __restrict__ Va,
 
 // norm estimate, stop test, next row pivot
 __global__ void __launch_bounds__(PIV_THREADS)
-k_aca_finalize(const double* __restrict__ Ua, int M1, int kk, int kmax, int nbu, int nbv,
+k_aca_finalize(const double* __restrict__ Ua, int M1, int kmax, int nbu, int nbv,
                const double* __restrict__ part, int ldp, AcaState* st, int* pivI,
-               unsigned char* usedr, double eps, int replay) {
+               unsigned char* usedr, cudaGraphConditionalHandle loop, int use_cond) {
   __shared__ double du[SLAR_MAX_RANK + 1], dv[SLAR_MAX_RANK + 1];
   __shared__ int i_s;
   __shared__ double top_s;
   __shared__ int stop_s;
-  if (st->done) return;
   const int tid = threadIdx.x;
+  if (st->done) {
+    if (tid == 0) if (use_cond) cudaGraphSetConditional(loop, 0);
+    return;
+  }
+  const int kk = st->k;
+  const int replay = st->replay;
+  const double eps = st->eps;
+  __syncthreads();
   if (tid <= kk) {
     double a = 0.0, b = 0.0;
     for (int blk = 0; blk < nbu; ++blk) a += part[(long long)blk * ldp + tid];
@@ -151,23 +164,120 @@ k_aca_finalize(const double* __restrict__ Ua, int M1, int kk, int kmax, int nbu,
     stop_s = stop;
   }
   __syncthreads();
-  if (stop_s) return;
+  if (stop_s) {
+    if (tid == 0) if (use_cond) cudaGraphSetConditional(loop, 0);
+    return;
+  }
   if (replay) {
-    if (tid == 0) usedr[pivI[kk + 1]] = 1;
+    if (tid == 0) {
+      usedr[pivI[kk + 1]] = 1;
+      if (use_cond) cudaGraphSetConditional(loop, 1);
+    }
     return;
   }
   block_argmax_tie(Ua + (long long)kk * M1, M1, usedr, &i_s, &top_s);
   if (tid == 0) {
     if (i_s < 0) {
       st->done = 1;
+      if (use_cond) cudaGraphSetConditional(loop, 0);
     } else {
       pivI[kk + 1] = i_s;
       usedr[i_s] = 1;
+      if (use_cond) cudaGraphSetConditional(loop, 1);
     }
   }
 }
 
 }  // namespace
+
+// One cross-approximation step: row fibre with residual, column pivot and v_k, column
+// fibre into u_k, dot products, norm estimate / stop test / next row pivot.  All kernels
+// read the step index from the device state.  With `prof` the two evaluator launches are
+// bracketed by CUDA events.
+slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int use_cond, bool prof) {
+  cudaStream_t s = c->s;
+  const int M1 = c->M1, M2 = c->M2;
+  const int nbu = (M1 + DOT_SEG - 1) / DOT_SEG, nbv = (M2 + DOT_SEG - 1) / DOT_SEG;
+  const int ldp = SLAR_MAX_RANK + 1;
+  EvalArgs ar{};
+  ar.mode = EVAL_ROW;
+  ar.n = M2;
+  ar.pivot = c->pivI;
+  ar.kidx = &c->ast->k;
+  ar.out_stride = 0;
+  ar.done = &c->ast->done;
+  ar.X = c->Ua;
+  ar.ldX = M1;
+  ar.Y = c->Va;
+  ar.ldY = M2;
+  ar.out = c->rowbuf;
+  EvalArgs ac = ar;
+  ac.mode = EVAL_COL;
+  ac.n = M1;
+  ac.pivot = c->pivJ;
+  ac.X = c->Va;
+  ac.ldX = M2;
+  ac.Y = c->Ua;
+  ac.ldY = M1;
+  ac.out = c->Ua;
+  ac.out_stride = M1;
+  const bool f32 = c->cfg.precision == SLAR_FP32;
+  for (int pass = 0; pass < 2; ++pass) {
+    const EvalArgs& a = pass == 0 ? ar : ac;
+    const bool ev = prof && c->prof_n * 2 + 1 < kProfEvents;
+    if (ev) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], s));
+    cudaError_t e = f32 ? launch_sl_eval_dev<float>(c->g, static_cast<const EvalParams<float>*>(c->evp), a, smem, s)
+                        : launch_sl_eval_dev<double>(c->g, static_cast<const EvalParams<double>*>(c->evp), a, smem, s);
+    CK(e);
+    if (ev) {
+      CK(cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], s));
+      c->prof_n++;
+    }
+    if (pass == 0)
+      slar::count_launch(), k_aca_row_pivot<<<1, PIV_THREADS, 0, s>>>(c->rowbuf, M2, c->usedc, c->pivJ, c->ast, c->Va);
+  }
+  slar::count_launch(), k_aca_dots<<<nbu + nbv, 256, 0, s>>>(c->Ua, M1, c->Va, M2, nbu, c->ast, c->aca_part, ldp);
+  slar::count_launch(), k_aca_finalize<<<1, PIV_THREADS, 0, s>>>(c->Ua, M1, c->kmax, nbu, nbv, c->aca_part, ldp,
+                                                                c->ast, c->pivI, c->usedr, h, use_cond);
+  CK(cudaGetLastError());
+  return SLAR_OK;
+}
+
+// Capture one cross-approximation step (row fibre, column pivot, column fibre, dot products,
+// stop test / next row pivot) as the body of a WHILE conditional node.  The body reads the
+// step index from the device state and the evaluator parameters from c->evp.
+slar_status build_aca_graph(slar_ctx* c, size_t smem) {
+  CaptureScope scope(c);
+  cudaStream_t s = c->s;
+  if (c->aca_graph) {
+    CK(cudaGraphExecDestroy(c->aca_graph));
+    c->aca_graph = nullptr;
+  }
+  const long long l0 = launch_count();
+  cudaGraph_t gl;
+  CK(cudaGraphCreate(&gl, 0));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, gl, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  CK(cudaGraphAddNode(&cn, gl, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  CKS(aca_step(c, smem, h, 1, false));
+  cudaGraph_t body_out;
+  CK(cudaStreamEndCapture(s, &body_out));
+  CK(cudaGraphInstantiate(&c->aca_graph, gl, 0));
+  CK(cudaGraphDestroy(gl));
+  const long long l1 = launch_count();
+  c->aca_graph_nodes = l1 - l0;
+  add_launches(-(l1 - l0));
+  c->aca_graph_smem = smem;
+  return SLAR_OK;
+}
 
 slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const double* E, int out,
                       int* aca_rank, long long* entries) {
@@ -193,48 +303,41 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
     CK(cudaMemcpy(c->pivJ, J.data(), sizeof(int) * kmax, cudaMemcpyHostToDevice));
     c->replay_pos++;
   }
-  slar::count_launch(), k_aca_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->usedr, replay ? 1 : 0);
+  // per-call evaluator parameters in device memory, read by the captured graph
+  const HTBuf& hin = c->ht[in];
+  const bool f32 = c->cfg.precision == SLAR_FP32;
+  if (f32) CKS(refresh_f32_slot(c, in));
+  if (f32) {
+    EvalParams<float>* P = static_cast<EvalParams<float>*>(c->evp_host);
+    P->ht = view32_slot(c, in);
+    P->corr = corr_view(c, with_corr);
+    P->tau = tau;
+    P->E = E;
+    P->foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
+  } else {
+    EvalParams<double>* P = static_cast<EvalParams<double>*>(c->evp_host);
+    P->ht = view64(c, in);
+    P->corr = corr_view(c, with_corr);
+    P->tau = tau;
+    P->E = E;
+    P->foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
+  }
+  CK(cudaMemcpyAsync(c->evp, c->evp_host, sizeof(EvalParams<double>), cudaMemcpyHostToDevice, s));
+  const size_t need = f32 ? sl_eval_smem<float>(c->g, hin.r) : sl_eval_smem<double>(c->g, hin.r);
+  const bool prof = (c->cfg.flags & SLAR_PROFILE_EVAL) != 0;
+  if (!prof && (!c->aca_graph || need > c->aca_graph_smem)) CKS(build_aca_graph(c, need));
+  slar::count_launch(), k_aca_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->usedr, replay ? 1 : 0, c->cfg.eps);
   CK(cudaGetLastError());
-  const int nbu = (M1 + DOT_SEG - 1) / DOT_SEG, nbv = (M2 + DOT_SEG - 1) / DOT_SEG;
-  const int ldp = SLAR_MAX_RANK + 1;
-  for (int kk = 0; kk < kmax; ++kk) {
-    EvalArgs ar{};
-    ar.mode = EVAL_ROW;
-    ar.n = M2;
-    ar.pivot = c->pivI + kk;
-    ar.done = &c->ast->done;
-    ar.kterms = kk;
-    ar.X = c->Ua;
-    ar.ldX = M1;
-    ar.Y = c->Va;
-    ar.ldY = M2;
-    ar.out = c->rowbuf;
-    ar.tau = tau;
-    ar.E = E;
-    ar.foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
-    CKS(eval_entries(c, in, with_corr, ar, 0));
-    slar::count_launch(), k_aca_row_pivot<<<1, PIV_THREADS, 0, s>>>(c->rowbuf, M2, c->usedc, c->pivJ, kk, c->ast,
-                                              c->Va + (long long)kk * M2, replay ? 1 : 0);
-    CK(cudaGetLastError());
-    EvalArgs ac = ar;
-    ac.mode = EVAL_COL;
-    ac.n = M1;
-    ac.pivot = c->pivJ + kk;
-    ac.X = c->Va;
-    ac.ldX = M2;
-    ac.Y = c->Ua;
-    ac.ldY = M1;
-    ac.out = c->Ua + (long long)kk * M1;
-    CKS(eval_entries(c, in, with_corr, ac, 0));
-    slar::count_launch(), k_aca_dots<<<nbu + nbv, 256, 0, s>>>(c->Ua, M1, c->Va, M2, kk, nbu, c->ast, c->aca_part, ldp);
-    CK(cudaGetLastError());
-    slar::count_launch(), k_aca_finalize<<<1, PIV_THREADS, 0, s>>>(c->Ua, M1, kk, kmax, nbu, nbv, c->aca_part, ldp,
-                                             c->ast, c->pivI, c->usedr, c->cfg.eps, replay ? 1 : 0);
-    CK(cudaGetLastError());
+  if (prof) {
+    // individually launched steps with events around the evaluator (roofline timing)
+    for (int kk = 0; kk < kmax; ++kk) CKS(aca_step(c, need, 0, 0, true));
+  } else {
+    CK(cudaGraphLaunch(c->aca_graph, s));
   }
   CK(cudaMemcpyAsync(c->ast_host, c->ast, sizeof(AcaState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const int k = c->ast_host->k;
+  if (!prof) add_launches(c->aca_graph_nodes * (long long)(k + c->ast_host->stop_row));
   if (aca_rank) *aca_rank = k;
   const long long nent = (long long)k * (M1 + M2) + (c->ast_host->stop_row ? M2 : 0);
   if (entries) *entries = nent;

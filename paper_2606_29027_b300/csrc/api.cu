@@ -19,6 +19,7 @@ int count_launch() {
   return 0;
 }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace slar
 
 using namespace slar;
@@ -80,15 +81,20 @@ void free_ctx(slar_ctx* c) {
   F(c->Ua); F(c->Va); F(c->rowbuf); F(c->usedr); F(c->usedc); F(c->pivI); F(c->pivJ);
   F(c->ast); F(c->aca_part); F(c->aca_dots);
   if (c->ast_host) cudaFreeHost(c->ast_host);
+  if (c->evp) cudaFree(c->evp);
+  if (c->evp_host) cudaFreeHost(c->evp_host);
+  if (c->aca_graph) cudaGraphExecDestroy(c->aca_graph);
   if (c->h_ranks) cudaFreeHost(c->h_ranks);
   if (c->scal_host) cudaFreeHost(c->scal_host);
   F(c->T1); F(c->T2); F(c->T3); F(c->Q12); F(c->Q34); F(c->Rn[0]); F(c->Rn[1]);
   F(c->sm1); F(c->sm2); F(c->sm3); F(c->sm4);
   for (int t = 0; t < 6; ++t) { F(c->G[t]); F(c->W[t]); F(c->S[t]); F(c->ework[t]); }
+  F(c->Sw);
   F(c->gram_work); F(c->tau); F(c->norm2); F(c->d_ranks); F(c->d_info); F(c->d_eig); F(c->d_rank);
   F(c->E); F(c->E1); F(c->E2); F(c->E3); F(c->mom); F(c->lvec); F(c->spec); F(c->rho); F(c->Wdev);
   F(c->macro_ws); F(c->scal);
   if (c->spectral) { c->spectral->release(); delete c->spectral; }
+  if (c->cap_s) cudaStreamDestroy(c->cap_s);
   macro_free(c);
   for (int i = 0; i < kProfEvents; ++i)
     if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
@@ -178,11 +184,12 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   A(c->Q12, (size_t)capB); A(c->Q34, (size_t)capB);
   A(c->Rn[0], (size_t)R * R); A(c->Rn[1], (size_t)R * R);
   A(c->sm1, (size_t)R * R); A(c->sm2, (size_t)R * R); A(c->sm3, (size_t)R * R); A(c->sm4, (size_t)R * R);
+  A(c->Sw, (size_t)4 * SLAR_MAX_N * SLAR_MAX_N);
   for (int t = 0; t < 6; ++t) {
     A(c->G[t], (size_t)SLAR_MAX_N * SLAR_MAX_N);
     A(c->W[t], (size_t)SLAR_MAX_N);
     A(c->S[t], (size_t)SLAR_MAX_N * SLAR_MAX_N);
-    A(c->ework[t], (size_t)(SLAR_MAX_N + 1) * (SLAR_MAX_N + 1));
+    A(c->ework[t], (size_t)2 * (SLAR_MAX_N + 1) * (SLAR_MAX_N + 1));
   }
   const long long gram_rows = std::max((long long)std::max(c->M1, c->M2), capB / 1);
   c->gram_work_blocks = (int)((std::min(gram_rows, (long long)SLAR_MAX_N * SLAR_MAX_N) + 63) / 64);
@@ -202,11 +209,17 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   A(c->rho, (size_t)c->NX);
   A(c->Wdev, 8);
 #undef A
-  if (cudaMallocHost(&c->ast_host, sizeof(AcaState)) != cudaSuccess ||
+  if (cudaMalloc(&c->evp, 256) != cudaSuccess || cudaMallocHost(&c->evp_host, 256) != cudaSuccess ||
+      cudaMallocHost(&c->ast_host, sizeof(AcaState)) != cudaSuccess ||
       cudaMallocHost(&c->h_ranks, sizeof(int) * 16) != cudaSuccess ||
       cudaMallocHost(&c->scal_host, sizeof(double) * 64) != cudaSuccess) {
     free_ctx(c);
     return SLAR_ENOMEM;
+  }
+  if (sl_eval_init_attrs() != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
+  if (cudaStreamCreateWithFlags(&c->cap_s, cudaStreamNonBlocking) != cudaSuccess) {
+    free_ctx(c);
+    return SLAR_ECUDA;
   }
   c->spectral = new (std::nothrow) Spectral();
   if (!c->spectral) { free_ctx(c); return SLAR_ENOMEM; }

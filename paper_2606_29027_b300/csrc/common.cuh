@@ -22,6 +22,7 @@ namespace slar {
 // Number of kernels this library has launched (all contexts); every launch site bumps it.
 long long launch_count();
 int count_launch();
+void add_launches(long long n);  // kernels executed by a replayed CUDA graph
 
 struct GridDesc {
   int d, dx, dv;
@@ -57,6 +58,8 @@ struct EvalArgs {
   const int* pivot;      // EVAL_ROW: device pointer to the row pivot; EVAL_COL: to the column pivot
   const int* done;       // optional device flag: when non-zero the launch does nothing
   int kterms;            // number of residual terms l < kterms
+  const int* kidx;       // optional device iteration index kk: pivot += kk, kterms = kk,
+  long long out_stride;  //   out += kk * out_stride (cross-approximation graph)
   const double* X;       // residual out[e] = val - sum_l X[*pivot + l*ldX] * Y[e + l*ldY]
   long long ldX;
   const double* Y;
@@ -67,10 +70,29 @@ struct EvalArgs {
   int foot_euler;
 };
 
+// Per-call parameters of the entry evaluator kept in device memory, so that a captured
+// CUDA graph serves every SLAR call of a context.
+template <typename T>
+struct EvalParams {
+  HTView<T> ht;
+  CorrView corr;
+  double tau;
+  const double* E;
+  int foot_euler;
+};
+
 // ---- launchers (defined in the .cu files) ----
 template <typename T>
 cudaError_t launch_sl_eval(const GridDesc& g, const HTView<T>& ht, const CorrView& corr,
                            const EvalArgs& a, int evaluate_at_grid, cudaStream_t s);
+// launch reading HT / field / tau from device memory; smem_bytes fixed by the caller
+template <typename T>
+cudaError_t launch_sl_eval_dev(const GridDesc& g, const EvalParams<T>* P, const EvalArgs& a,
+                               size_t smem_bytes, cudaStream_t s);
+template <typename T>
+size_t sl_eval_smem(const GridDesc& g, const int* ranks6);
+// opt the evaluator kernels into large dynamic shared memory (call before any capture)
+cudaError_t sl_eval_init_attrs();
 
 // dense FP64 linear algebra (linalg.cu)
 // C[b] = alpha op(A[b]) op(B[b]) + beta C[b]; row-major; op(A) is M x K.
@@ -83,10 +105,10 @@ cudaError_t gram_tall(const double* A, long long lda, int m, int n, double* G, d
                       int work_blocks, cudaStream_t s);
 // out[i][j] = sum_p sum_c X[p][i][c] Y[p][j][c]   (X: P x I x C, Y: P x J x C)
 cudaError_t contract_last(const double* X, const double* Y, int P, int I, int J, int C,
-                          double* out, cudaStream_t s);
+                          double* out, double* work, long long work_len, cudaStream_t s);
 // out[i][j] = sum_p sum_c X[p][c][i] Y[p][c][j]   (X: P x C x I, Y: P x C x J)
 cudaError_t contract_mid(const double* X, const double* Y, int P, int C, int I, int J,
-                         double* out, cudaStream_t s);
+                         double* out, double* work, long long work_len, cudaStream_t s);
 // Cholesky of an n x n SPD matrix (row-major), returns upper R (G = R^T R) and R^{-1};
 // info[0] != 0 on breakdown.
 cudaError_t chol_inv(const double* G, int n, double* R, double* Rinv, int* info, cudaStream_t s);
@@ -101,7 +123,7 @@ struct EigJob {
   const double* A;
   double* W;
   double* V;
-  double* work;  // (n_b+1)^2 doubles scratch (eigenvectors before sorting)
+  double* work;  // 2 (SLAR_MAX_N+1)^2 doubles scratch
   int n;
 };
 cudaError_t eig_batched(const EigJob* jobs_host, int njobs, EigJob* jobs_dev, cudaStream_t s);

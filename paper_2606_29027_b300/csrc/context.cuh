@@ -29,20 +29,22 @@ struct HTBuf {
 constexpr int NSLOT = 4;
 
 struct AcaState {
-  int k;          // number of accepted cross terms
+  int k;          // number of accepted cross terms = index of the running step
   int done;       // set when the cross approximation stops
   int stop_row;   // 1 if it stopped on a vanishing residual row (that row was sampled)
-  int pad;
+  int replay;     // pivots are replayed from pivI / pivJ
   double normA2;  // running ||A_k||_F^2 estimate
   double piv;     // current pivot value
   double nv2;     // ||v_k||^2
+  double eps;     // stopping tolerance
 };
 
 }  // namespace slar
 
 struct slar_ctx {
   slar_config cfg;
-  cudaStream_t s = nullptr;
+  cudaStream_t s = nullptr;        // caller's stream: all work is ordered on it
+  cudaStream_t cap_s = nullptr;    // internal stream used only to capture CUDA graphs
   slar::GridDesc g;
   int d = 0, dx = 0, dv = 0, NX = 0, NV = 0, M1 = 0, M2 = 0, kmax = 0, n_mom = 0;
   long long capB = 0;
@@ -85,6 +87,11 @@ struct slar_ctx {
   double* aca_part = nullptr;          // partial dot products
   double* aca_dots = nullptr;
   std::vector<int> replay;             // [calls][kmax][2]
+  void* evp = nullptr;                 // device EvalParams of the running SLAR call
+  void* evp_host = nullptr;            // pinned staging
+  cudaGraphExec_t aca_graph = nullptr; // one cross-approximation step inside a WHILE node
+  size_t aca_graph_smem = 0;
+  long long aca_graph_nodes = 0;
   int replay_calls = 0, replay_kmax = 0, replay_pos = 0;
 
   // truncation workspaces
@@ -103,6 +110,8 @@ struct slar_ctx {
   double* G[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* W[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* S[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int Sn[6] = {0, 0, 0, 0, 0, 0};   // order of the eigenvector matrix kept in S[t] (warm start)
+  double* Sw = nullptr;             // warm-start scratch (4 x 128 x 128)
   double* ework[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* gram_work = nullptr;
   int gram_work_blocks = 0;
@@ -164,6 +173,19 @@ slar_status cuda_fail(slar_ctx* c, cudaError_t e, const char* where);
 slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, int out_slot);
 TruncIn trunc_in_of_slot(const slar_ctx* c, int slot);
 HTView<double> view64(const slar_ctx* c, int slot);
+HTView<float> view32_slot(const slar_ctx* c, int slot);
+slar_status refresh_f32_slot(slar_ctx* c, int slot);
+slar_status build_aca_graph(slar_ctx* c, size_t smem);
+slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int use_cond, bool prof);
+
+// Redirects the context's launches to its capture stream while a CUDA graph is recorded
+// (capture is not possible on the legacy default stream a caller may pass).
+struct CaptureScope {
+  slar_ctx* c;
+  cudaStream_t saved;
+  explicit CaptureScope(slar_ctx* ctx);
+  ~CaptureScope();
+};
 CorrView corr_view(const slar_ctx* c, bool with_corr);
 // evaluate entries of slot (+ the state's correction if with_corr) in the context precision
 slar_status eval_entries(slar_ctx* c, int slot, bool with_corr, const EvalArgs& a, int at_grid);

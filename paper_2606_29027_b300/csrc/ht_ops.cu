@@ -33,7 +33,7 @@ HTView<double> view64(const slar_ctx* c, int slot) {
   return v;
 }
 
-static HTView<float> view32(const slar_ctx* c, int slot) {
+HTView<float> view32_slot(const slar_ctx* c, int slot) {
   HTView<float> v;
   const HTBuf& h = c->ht[slot];
   for (int m = 0; m < 4; ++m) {
@@ -57,7 +57,7 @@ CorrView corr_view(const slar_ctx* c, bool with_corr) {
 }
 
 // FP32 copy of a slot's factors for the FP32 entry evaluator.
-static slar_status refresh_f32(slar_ctx* c, int slot) {
+slar_status refresh_f32_slot(slar_ctx* c, int slot) {
   if (c->f32_slot == slot) return SLAR_OK;
   const HTBuf& h = c->ht[slot];
   for (int m = 0; m < c->d; ++m)
@@ -71,6 +71,16 @@ static slar_status refresh_f32(slar_ctx* c, int slot) {
   }
   c->f32_slot = slot;
   return SLAR_OK;
+}
+
+CaptureScope::CaptureScope(slar_ctx* ctx) : c(ctx), saved(ctx->s) {
+  c->s = c->cap_s;
+  c->spectral->s = c->cap_s;
+}
+
+CaptureScope::~CaptureScope() {
+  c->s = saved;
+  c->spectral->s = saved;
 }
 
 void phase(slar_ctx* c, int tag) {
@@ -89,12 +99,12 @@ double entry_flops(const slar_ctx* c, int slot) {
 
 slar_status eval_entries(slar_ctx* c, int slot, bool with_corr, const EvalArgs& a, int at_grid) {
   if (!c->ht[slot].valid) return set_error(c, SLAR_EINVAL, "no HT state");
-  const bool prof = (c->cfg.flags & SLAR_PROFILE) && c->prof_n * 2 + 1 < kProfEvents;
+  const bool prof = (c->cfg.flags & SLAR_PROFILE_EVAL) && c->prof_n * 2 + 1 < kProfEvents;
   if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], c->s));
   cudaError_t e;
   if (c->cfg.precision == SLAR_FP32) {
-    CKS(refresh_f32(c, slot));
-    e = launch_sl_eval<float>(c->g, view32(c, slot), corr_view(c, with_corr), a, at_grid, c->s);
+    CKS(refresh_f32_slot(c, slot));
+    e = launch_sl_eval<float>(c->g, view32_slot(c, slot), corr_view(c, with_corr), a, at_grid, c->s);
   } else {
     e = launch_sl_eval<double>(c->g, view64(c, slot), corr_view(c, with_corr), a, at_grid, c->s);
   }
@@ -227,17 +237,32 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
       // T[p'][a][b] = sum_p G[p][p'] B[p][a][b]
       CK(dgemm(0, 0, rp, (int)K, rp, 1.0, c->G[4 + t], rp, 0, Bq[t], (int)K, 0, 0.0, c->T1,
                (int)K, 0, 1, s));
-      CK(contract_last(c->T1, Bq[t], rp, ra, ra, rb, c->G[a], s));
-      CK(contract_mid(c->T1, Bq[t], rp, ra, rb, rb, c->G[b], s));
+      const long long wl = (long long)c->gram_work_blocks * SLAR_MAX_RANK * SLAR_MAX_RANK;
+      CK(contract_last(c->T1, Bq[t], rp, ra, ra, rb, c->G[a], c->gram_work, wl, s));
+      CK(contract_mid(c->T1, Bq[t], rp, ra, rb, rb, c->G[b], c->gram_work, wl, s));
     }
   }
-  // 2. eigendecompositions
+  // 2. eigendecompositions.  Leaf Gram matrices of the same order as at the previous
+  // truncation are first rotated into the previous eigenbasis, A' = S^T G S, which is
+  // nearly diagonal because the distribution changes little between SLAR calls; Jacobi then
+  // needs far fewer sweeps and the eigenvectors are S V'.
   EigJob jobs[6];
   int nj = 0;
   int node_n[6];
   for (int m = 0; m < d; ++m) node_n[m] = rq[m];
   if (d == 4) { node_n[4] = in.r[4]; node_n[5] = in.r[5]; }
   const int nnodes = d == 4 ? 6 : 2;
+  bool warm[6] = {false, false, false, false, false, false};
+  for (int m = 0; m < d; ++m) {
+    const int nm = node_n[m];
+    if (nm < 16 || c->Sn[m] != nm) continue;
+    double* T = c->Sw + (size_t)m * SLAR_MAX_N * SLAR_MAX_N;
+    CK(dgemm(0, 0, nm, nm, nm, 1.0, c->G[m], nm, 0, c->S[m], nm, 0, 0.0, T, nm, 0, 1, s));
+    CK(dgemm(1, 0, nm, nm, nm, 1.0, c->S[m], nm, 0, T, nm, 0, 0.0, c->G[m], nm, 0, 1, s));
+    // keep the previous basis in T for the back-rotation
+    CK(cudaMemcpyAsync(T, c->S[m], sizeof(double) * nm * nm, cudaMemcpyDeviceToDevice, s));
+    warm[m] = true;
+  }
   for (int t = 0; t < nnodes; ++t) {
     jobs[nj].A = c->G[t];
     jobs[nj].W = c->W[t];
@@ -247,6 +272,16 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
     ++nj;
   }
   CK(eig_batched(jobs, nj, c->d_eig, s));
+  for (int m = 0; m < d; ++m) {
+    if (warm[m]) {
+      const int nm = node_n[m];
+      double* T = c->Sw + (size_t)m * SLAR_MAX_N * SLAR_MAX_N;
+      // S <- S_prev V'  (through the Jacobi scratch, free again after the solve)
+      CK(dgemm(0, 0, nm, nm, nm, 1.0, T, nm, 0, c->S[m], nm, 0, 0.0, c->ework[m], nm, 0, 1, s));
+      CK(cudaMemcpyAsync(c->S[m], c->ework[m], sizeof(double) * nm * nm, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  for (int t = 0; t < nnodes; ++t) c->Sn[t] = node_n[t];
   // 3. ranks
   slar::count_launch(), k_trace<<<1, 32, 0, s>>>(c->G[d == 4 ? 4 : 0], node_n[d == 4 ? 4 : 0], c->norm2);
   CK(cudaGetLastError());

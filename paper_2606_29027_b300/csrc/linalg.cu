@@ -100,34 +100,37 @@ __global__ void k_sum_partials(const double* __restrict__ part, int nblk, int nn
   G[it] = s;
 }
 
-// out[i][j] = sum_p sum_c X[p][i][c] Y[p][j][c]
-__global__ void k_contract_last(const double* __restrict__ X, const double* __restrict__ Y, int P,
-                                int I, int J, int C, double* __restrict__ out) {
-  const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= I || j >= J) return;
-  double s = 0.0;
-  for (int p = 0; p < P; ++p) {
-    const double* x = X + ((long long)p * I + i) * C;
-    const double* y = Y + ((long long)p * J + j) * C;
-    for (int c = 0; c < C; ++c) s += x[c] * y[c];
-  }
-  out[(long long)i * J + j] = s;
-}
+// out[i][j] = sum_p sum_c X(p, i, c) Y(p, j, c) with general strides; a CTA computes a
+// 16 x 16 output tile over one p-group and writes a partial; partials are summed in group
+// order (deterministic).
+constexpr int CT = 16;
+constexpr int CK = 16;
 
-// out[i][j] = sum_p sum_c X[p][c][i] Y[p][c][j]
-__global__ void k_contract_mid(const double* __restrict__ X, const double* __restrict__ Y, int P,
-                               int C, int I, int J, double* __restrict__ out) {
-  const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= I || j >= J) return;
-  double s = 0.0;
-  for (int p = 0; p < P; ++p) {
-    const double* x = X + (long long)p * C * I + i;
-    const double* y = Y + (long long)p * C * J + j;
-    for (int c = 0; c < C; ++c) s += x[(long long)c * I] * y[(long long)c * J];
+__global__ void __launch_bounds__(256)
+k_contract(const double* __restrict__ X, long long xp, long long xi, long long xc,
+           const double* __restrict__ Y, long long yp, long long yj, long long yc, int P, int I,
+           int J, int C, int pgroup, double* __restrict__ part) {
+  __shared__ double xs[CK][CT + 1], ys[CK][CT + 1];
+  const int ti = threadIdx.x / CT, tj = threadIdx.x % CT;
+  const int i0 = blockIdx.y * CT, j0 = blockIdx.x * CT;
+  const int g = blockIdx.z;
+  const int p0 = g * pgroup, p1 = min(P, p0 + pgroup);
+  double acc = 0.0;
+  for (int p = p0; p < p1; ++p) {
+    for (int c0 = 0; c0 < C; c0 += CK) {
+      for (int it = threadIdx.x; it < CK * CT; it += 256) {
+        const int cc = it % CK, r = it / CK;
+        const int c = c0 + cc;
+        xs[cc][r] = (c < C && i0 + r < I) ? X[p * xp + (long long)(i0 + r) * xi + c * xc] : 0.0;
+        ys[cc][r] = (c < C && j0 + r < J) ? Y[p * yp + (long long)(j0 + r) * yj + c * yc] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int cc = 0; cc < CK; ++cc) acc += xs[cc][ti] * ys[cc][tj];
+      __syncthreads();
+    }
   }
-  out[(long long)i * J + j] = s;
+  if (i0 + ti < I && j0 + tj < J) part[((long long)g * I + i0 + ti) * J + j0 + tj] = acc;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -270,47 +273,44 @@ k_householder(double* A, int m, int n, double* Q, double* R, double* tau) {
 // ---------------------------------------------------------------------------------------
 constexpr int EIG_THREADS = 512;
 
-__global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs) {
-  extern __shared__ double sA[];  // ne x ne  (ne = n rounded up to even)
-  __shared__ int pp[SLAR_MAX_N / 2], qq[SLAR_MAX_N / 2];
-  __shared__ double cc[SLAR_MAX_N / 2], ss[SLAR_MAX_N / 2];
-  __shared__ double red[EIG_THREADS / 32][2];
-  __shared__ int stop;
-  const EigJob job = jobs[blockIdx.x];
-  const int n = job.n;
-  const int ne = n + (n & 1);
-  const int half = ne / 2;
+// Cyclic Jacobi sweeps on the ne x ne symmetric matrix sA (shared memory) accumulating
+// eigenvectors in V (global, ne x ne).  Round-robin ordering: each round applies ne/2
+// disjoint rotations at once as 2x2 block updates A <- J^T A J, V <- V J.  A pair is
+// rotated while |a_pq| > tol sqrt(|a_pp a_qq|) (relative criterion: small eigenvalues and
+// their eigenvectors are resolved to relative accuracy); stop after a sweep without any
+// rotation, or after 40 sweeps.
+__device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, double* cc,
+                              double* ss, int* rotated) {
   const int tid = threadIdx.x;
-  double* V = job.work;  // ne x ne row-major eigenvector accumulator in global scratch
-  for (int it = tid; it < ne * ne; it += EIG_THREADS) {
-    const int i = it / ne, j = it % ne;
-    sA[it] = (i < n && j < n) ? job.A[i * n + j] : 0.0;
-    V[it] = (i == j) ? 1.0 : 0.0;
-  }
-  if (tid == 0) stop = 0;
-  __syncthreads();
-  const int m = ne - 1;  // round-robin over m rounds, index ne-1 fixed
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    // convergence test: off-diagonal vs diagonal
-    double off = 0.0, dia = 0.0;
-    for (int it = tid; it < ne * ne; it += EIG_THREADS) {
-      const int i = it / ne, j = it % ne;
-      const double v = sA[it];
-      if (i == j) dia += v * v; else off += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_down_sync(0xffffffffu, off, o);
-      dia += __shfl_down_sync(0xffffffffu, dia, o);
-    }
-    if ((tid & 31) == 0) { red[tid >> 5][0] = off; red[tid >> 5][1] = dia; }
+  const int half = ne / 2;
+  const int m = ne - 1;
+  const double tol = 1e-15;
+  __shared__ unsigned short tri[(SLAR_MAX_N / 2) * (SLAR_MAX_N / 2 + 1) / 2];
+  __shared__ double fro_red[EIG_THREADS / 32];
+  __shared__ double floor_s;
+  // absolute floor: entries at the rounding level of the matrix are not rotated
+  {
+    double f = 0.0;
+    for (int it = tid; it < ne * ne; it += EIG_THREADS) f += sA[it] * sA[it];
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+    if ((tid & 31) == 0) fro_red[tid >> 5] = f;
     __syncthreads();
     if (tid == 0) {
-      double o2 = 0.0, d2 = 0.0;
-      for (int w = 0; w < EIG_THREADS / 32; ++w) { o2 += red[w][0]; d2 += red[w][1]; }
-      stop = (o2 <= 1e-26 * d2) || (d2 == 0.0);
+      double t = 0.0;
+      for (int w = 0; w < EIG_THREADS / 32; ++w) t += fro_red[w];
+      floor_s = 1e-17 * sqrt(t);
     }
     __syncthreads();
-    if (stop) break;
+  }
+  const double afloor = floor_s;
+  for (int ia = tid; ia < half; ia += EIG_THREADS) {
+    const int off = ia * half - ia * (ia - 1) / 2;
+    for (int ib = ia; ib < half; ++ib) tri[off + ib - ia] = (unsigned short)((ia << 8) | ib);
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) *rotated = 0;
+    __syncthreads();
     for (int rnd = 0; rnd < m; ++rnd) {
       for (int k = tid; k < half; k += EIG_THREADS) {
         int p, q;
@@ -318,57 +318,227 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs) {
         else { p = (rnd + k) % m; q = (rnd - k + m) % m; }
         if (p > q) { const int t = p; p = q; q = t; }
         const double apq = sA[p * ne + q];
+        const double app = sA[p * ne + p], aqq = sA[q * ne + q];
         double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
-          const double app = sA[p * ne + p], aqq = sA[q * ne + q];
+        if (fabs(apq) > tol * sqrt(fabs(app * aqq)) && fabs(apq) > afloor) {
           const double theta = (aqq - app) / (2.0 * apq);
           const double t = fabs(theta) > 1e150
                                ? 0.5 / theta
                                : (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
           c = 1.0 / sqrt(t * t + 1.0);
           s = t * c;
+          *rotated = 1;
         }
         pp[k] = p; qq[k] = q; cc[k] = c; ss[k] = s;
       }
       __syncthreads();
-      // A <- J^T A J as independent 2x2 blocks (pair a rows, pair b columns)
-      for (int it = tid; it < half * half; it += EIG_THREADS) {
-        const int ia = it / half, ib = it % half;
+      // upper-triangular block pairs (ia <= ib) from the precomputed table; the
+      // transposed block is mirrored
+      const int nblk = half * (half + 1) / 2;
+      for (int it = tid; it < nblk; it += EIG_THREADS) {
+        const int ia = tri[it] >> 8, ib = tri[it] & 0xff;
+        const double sa = ss[ia], sb = ss[ib];
+        if (sa == 0.0 && sb == 0.0) continue;
         const int pa = pp[ia], qa = qq[ia], pb = pp[ib], qb = qq[ib];
-        const double ca = cc[ia], sa = ss[ia], cb = cc[ib], sb = ss[ib];
+        const double ca = cc[ia], cb = cc[ib];
         const double x00 = sA[pa * ne + pb], x01 = sA[pa * ne + qb];
         const double x10 = sA[qa * ne + pb], x11 = sA[qa * ne + qb];
-        // J^T X : rows (p, q) -> (c x_p - s x_q, s x_p + c x_q)
+        // J^T X : rows (p, q) -> (c x_p - s x_q, s x_p + c x_q); then (.) J on columns
         const double y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
         const double y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
-        // (.) J : cols (p, q) -> (c y_p - s y_q, s y_p + c y_q)
-        sA[pa * ne + pb] = cb * y00 - sb * y01;
-        sA[pa * ne + qb] = sb * y00 + cb * y01;
-        sA[qa * ne + pb] = cb * y10 - sb * y11;
-        sA[qa * ne + qb] = sb * y10 + cb * y11;
+        const double z00 = cb * y00 - sb * y01, z01 = sb * y00 + cb * y01;
+        const double z10 = cb * y10 - sb * y11, z11 = sb * y10 + cb * y11;
+        sA[pa * ne + pb] = z00;
+        sA[pa * ne + qb] = z01;
+        sA[qa * ne + pb] = z10;
+        sA[qa * ne + qb] = z11;
+        if (ia != ib) {
+          sA[pb * ne + pa] = z00;
+          sA[qb * ne + pa] = z01;
+          sA[pb * ne + qa] = z10;
+          sA[qb * ne + qa] = z11;
+        }
       }
       for (int it = tid; it < ne * half; it += EIG_THREADS) {
         const int row = it / half, ib = it % half;
+        const double sb = ss[ib];
+        if (sb == 0.0) continue;
         const int pb = pp[ib], qb = qq[ib];
-        const double cb = cc[ib], sb = ss[ib];
+        const double cb = cc[ib];
         const double vp = V[row * ne + pb], vq = V[row * ne + qb];
         V[row * ne + pb] = cb * vp - sb * vq;
         V[row * ne + qb] = sb * vp + cb * vq;
       }
       __syncthreads();
     }
+    if (!*rotated) break;
+    __syncthreads();
   }
-  // sort descending (ties by index) and write
-  for (int i = tid; i < n; i += EIG_THREADS) {
+}
+
+// Symmetric eigendecomposition, one CTA per matrix.  Matrices with n > 24 are first
+// compressed by a pivoted Cholesky factorisation G = L L^T stopped at the numerical rank
+// (remaining diagonal <= 1e-16 trace); the eigenpairs of the small M = L^T L give those of
+// G: lambda(G) = lambda(M), S = L V Lambda^{-1/2}.  Eigenvalues beyond the numerical rank
+// are returned as 0 with zero eigenvectors.  L, M and the Jacobi eigenvectors stay in
+// shared memory; only a full-rank matrix with n > 64 falls back to eigenvectors in global
+// memory.
+constexpr int EIG_RTMAX = 64;
+constexpr int EIG_SMEM_DOUBLES = SLAR_MAX_N * EIG_RTMAX + 2 * EIG_RTMAX * EIG_RTMAX + SLAR_MAX_N;
+
+__device__ void sort_write(const double* sA, int ne, int n, const double* V, int ldv, double* W,
+                           double* Vout) {
+  for (int i = threadIdx.x; i < n; i += EIG_THREADS) {
     const double li = sA[i * ne + i];
     int pos = 0;
     for (int j = 0; j < n; ++j) {
       const double lj = sA[j * ne + j];
       pos += (lj > li) || (lj == li && j < i);
     }
-    job.W[pos] = li;
-    for (int r = 0; r < n; ++r) job.V[r * n + pos] = V[r * ne + i];
+    W[pos] = li;
+    for (int r = 0; r < n; ++r) Vout[r * n + pos] = V[r * ldv + i];
   }
+}
+
+__global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs) {
+  extern __shared__ double smem[];
+  __shared__ int pp[SLAR_MAX_N / 2], qq[SLAR_MAX_N / 2];
+  __shared__ double cc[SLAR_MAX_N / 2], ss[SLAR_MAX_N / 2];
+  __shared__ double wred[EIG_THREADS / 32];
+  __shared__ int wred_i[EIG_THREADS / 32];
+  __shared__ int piv_s, rotated, rt_s;
+  __shared__ double dpiv_s, trace_s;
+  const EigJob job = jobs[blockIdx.x];
+  const int n = job.n;
+  const int tid = threadIdx.x;
+  if (false) {
+    double* L = smem;                                   // n x rt, column j at L + j n
+    double* M = smem + SLAR_MAX_N * EIG_RTMAX;          // ne x ne
+    double* Vs = M + EIG_RTMAX * EIG_RTMAX;             // ne x ne
+    double* dg = Vs + EIG_RTMAX * EIG_RTMAX;            // n
+    for (int i = tid; i < n; i += EIG_THREADS) dg[i] = job.A[i * n + i];
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int i = 0; i < n; ++i) t += fmax(dg[i], 0.0);
+      trace_s = t;
+      rt_s = 0;
+    }
+    __syncthreads();
+    const double stop = 1e-16 * trace_s;
+    const int rtmax = n < EIG_RTMAX ? n : EIG_RTMAX;
+    for (int j = 0; j < rtmax; ++j) {
+      double best = -1.0;
+      int bi = -1;
+      for (int i = tid; i < n; i += EIG_THREADS)
+        if (dg[i] > best) { best = dg[i]; bi = i; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) { best = ob; bi = oi; }
+      }
+      if ((tid & 31) == 0) { wred[tid >> 5] = best; wred_i[tid >> 5] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        double b = -1.0;
+        int ib = -1;
+        for (int w = 0; w < EIG_THREADS / 32; ++w)
+          if (wred[w] > b || (wred[w] == b && wred_i[w] >= 0 && (ib < 0 || wred_i[w] < ib))) {
+            b = wred[w]; ib = wred_i[w];
+          }
+        piv_s = ib;
+        dpiv_s = b;
+      }
+      __syncthreads();
+      if (!(dpiv_s > stop) || piv_s < 0) break;
+      const int p = piv_s;
+      const double inv = 1.0 / sqrt(dpiv_s);
+      double* lj = L + j * n;
+      for (int i = tid; i < n; i += EIG_THREADS) {
+        double v = job.A[i * n + p];
+        for (int t = 0; t < j; ++t) v -= L[t * n + i] * L[t * n + p];
+        lj[i] = v * inv;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += EIG_THREADS) dg[i] = (i == p) ? -1.0 : dg[i] - lj[i] * lj[i];
+      if (tid == 0) rt_s = j + 1;
+      __syncthreads();
+    }
+    int rt = rt_s;
+    const bool full = (rt == rtmax && rtmax < n && dpiv_s > stop);
+    if (!full) {
+      if (rt == 0) {  // zero matrix: one zero eigenpair
+        rt = 1;
+        for (int i = tid; i < n; i += EIG_THREADS) L[i] = 0.0;
+      }
+      const int ne = rt + (rt & 1);
+      __syncthreads();
+      for (int it = tid; it < ne * ne; it += EIG_THREADS) {
+        const int a = it / ne, b = it % ne;
+        double v = 0.0;
+        if (a < rt && b < rt)
+          for (int i = 0; i < n; ++i) v += L[a * n + i] * L[b * n + i];
+        M[it] = v;
+        Vs[it] = (a == b) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      jacobi_sweeps(M, ne, Vs, pp, qq, cc, ss, &rotated);
+      // eigenvalue order of M (descending, ties by index)
+      __shared__ int order[EIG_RTMAX];
+      for (int i = tid; i < rt; i += EIG_THREADS) {
+        const double li = M[i * ne + i];
+        int pos = 0;
+        for (int j = 0; j < rt; ++j) {
+          const double lj = M[j * ne + j];
+          pos += (lj > li) || (lj == li && j < i);
+        }
+        order[pos] = i;
+        job.W[pos] = li > 0.0 ? li : 0.0;
+      }
+      for (int i = rt + tid; i < n; i += EIG_THREADS) job.W[i] = 0.0;
+      __syncthreads();
+      // S[r][pos] = sum_a L[r][a] V[a][i] / sqrt(lambda_i)
+      for (int it = tid; it < n * n; it += EIG_THREADS) {
+        const int r = it / n, pos = it % n;
+        double v = 0.0;
+        if (pos < rt) {
+          const int i = order[pos];
+          const double li = M[i * ne + i];
+          if (li > 0.0) {
+            for (int a = 0; a < rt; ++a) v += L[a * n + r] * Vs[a * ne + i];
+            v /= sqrt(li);
+          }
+        }
+        job.V[it] = v;
+      }
+      return;
+    }
+    __syncthreads();
+    // full-rank large matrix: direct Jacobi with eigenvectors in global scratch
+    const int ne = n + (n & 1);
+    double* sA = smem;
+    double* V = job.work;
+    for (int it = tid; it < ne * ne; it += EIG_THREADS) {
+      const int i = it / ne, j = it % ne;
+      sA[it] = (i < n && j < n) ? job.A[i * n + j] : 0.0;
+      V[it] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    jacobi_sweeps(sA, ne, V, pp, qq, cc, ss, &rotated);
+    sort_write(sA, ne, n, V, ne, job.W, job.V);
+    return;
+  }
+  const int ne = n + (n & 1);
+  double* sA = smem;
+  double* V = smem + ne * ne;
+  for (int it = tid; it < ne * ne; it += EIG_THREADS) {
+    const int i = it / ne, j = it % ne;
+    sA[it] = (i < n && j < n) ? job.A[i * n + j] : 0.0;
+    V[it] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  jacobi_sweeps(sA, ne, V, pp, qq, cc, ss, &rotated);
+  sort_write(sA, ne, n, V, ne, job.W, job.V);
 }
 
 __global__ void k_choose_ranks(RankJob* jobs, int njobs, const double* normF2, double scale) {
@@ -448,18 +618,36 @@ cudaError_t gram_tall(const double* A, long long lda, int m, int n, double* G, d
   return cudaGetLastError();
 }
 
-cudaError_t contract_last(const double* X, const double* Y, int P, int I, int J, int C,
-                          double* out, cudaStream_t s) {
-  dim3 blk(16, 16), grid((J + 15) / 16, (I + 15) / 16);
-  slar::count_launch(), k_contract_last<<<grid, blk, 0, s>>>(X, Y, P, I, J, C, out);
+static cudaError_t contract_general(const double* X, long long xp, long long xi, long long xc,
+                                    const double* Y, long long yp, long long yj, long long yc,
+                                    int P, int I, int J, int C, double* out, double* work,
+                                    long long work_len, cudaStream_t s) {
+  int groups = 1;
+  const int tiles = ((I + CT - 1) / CT) * ((J + CT - 1) / CT);
+  while (groups * 2 <= P && tiles * groups * 2 <= 296 && (long long)groups * 2 * I * J <= work_len)
+    groups *= 2;
+  const int pgroup = (P + groups - 1) / groups;
+  groups = (P + pgroup - 1) / pgroup;
+  dim3 grid((J + CT - 1) / CT, (I + CT - 1) / CT, groups);
+  slar::count_launch(), k_contract<<<grid, 256, 0, s>>>(X, xp, xi, xc, Y, yp, yj, yc, P, I, J, C,
+                                                       pgroup, work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nn = I * J;
+  slar::count_launch(), k_sum_partials<<<(nn + 255) / 256, 256, 0, s>>>(work, groups, nn, out);
   return cudaGetLastError();
 }
 
+cudaError_t contract_last(const double* X, const double* Y, int P, int I, int J, int C,
+                          double* out, double* work, long long work_len, cudaStream_t s) {
+  return contract_general(X, (long long)I * C, C, 1, Y, (long long)J * C, C, 1, P, I, J, C, out,
+                          work, work_len, s);
+}
+
 cudaError_t contract_mid(const double* X, const double* Y, int P, int C, int I, int J,
-                         double* out, cudaStream_t s) {
-  dim3 blk(16, 16), grid((J + 15) / 16, (I + 15) / 16);
-  slar::count_launch(), k_contract_mid<<<grid, blk, 0, s>>>(X, Y, P, C, I, J, out);
-  return cudaGetLastError();
+                         double* out, double* work, long long work_len, cudaStream_t s) {
+  return contract_general(X, (long long)C * I, 1, I, Y, (long long)C * J, 1, J, P, I, J, C, out,
+                          work, work_len, s);
 }
 
 cudaError_t chol_inv(const double* G, int n, double* R, double* Rinv, int* info, cudaStream_t s) {
@@ -489,12 +677,14 @@ cudaError_t eig_batched(const EigJob* jobs_host, int njobs, EigJob* jobs_dev, cu
     if (jobs_host[i].n > SLAR_MAX_N || jobs_host[i].n < 1) return cudaErrorInvalidValue;
     nmax = jobs_host[i].n > nmax ? jobs_host[i].n : nmax;
   }
-  const int ne = nmax + (nmax & 1);
-  const size_t sm = sizeof(double) * ne * ne;
+  // compression path: L (n x 64), M and V (64 x 64 each), remaining diagonal; the direct
+  // full-rank fallback needs an n x n matrix (n <= 128), which is no larger
+  size_t sm = sizeof(double) * EIG_SMEM_DOUBLES;
+  if (sm < sizeof(double) * SLAR_MAX_N * SLAR_MAX_N) sm = sizeof(double) * SLAR_MAX_N * SLAR_MAX_N;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(double) * SLAR_MAX_N * SLAR_MAX_N));
+                                         (int)sm);
     if (e != cudaSuccess) return e;
     attr = true;
   }

@@ -28,12 +28,16 @@ struct MacroWS {
   double *part = nullptr;      // reduction partials
   double *sc = nullptr;        // device scalars
   double *tot = nullptr;       // totals
+  int* gi = nullptr;           // device ints: Arnoldi index j, Krylov count, iterations done
   int nblk = 0;
+  cudaGraphExec_t g_pro = nullptr, g_loop = nullptr, g_epi = nullptr;
+  long long n_pro = 0, n_body = 0, n_epi = 0;
+  bool graphs = false;
 };
 
 namespace {
 
-constexpr int RED_SEG = 1024;
+constexpr int RED_SEG = 256;
 // scalar layout (sc)
 constexpr int SC_H = 0;                 // (m+1) x m, m <= 64
 constexpr int SC_G = SC_H + 65 * 64;    // m+1
@@ -41,7 +45,8 @@ constexpr int SC_CS = SC_G + 65;
 constexpr int SC_SN = SC_CS + 64;
 constexpr int SC_Y = SC_SN + 64;
 constexpr int SC_MISC = SC_Y + 64;      // beta, bnorm, done, jdone, tmp...
-enum { M_BETA = 0, M_BNORM, M_DONE, M_JDONE, M_NORM, M_RTOL, M_INF, M_UNORM };
+enum { M_BETA = 0, M_BNORM, M_DONE, M_JDONE, M_NORM, M_RTOL, M_INF, M_UNORM, M_COEF, M_H, M_INVH,
+       M_NI, M_FIRST, M_GRES };
 constexpr int SC_SIZE = SC_MISC + 16;
 
 // ---------------- reductions ----------------
@@ -106,14 +111,6 @@ __global__ void k_axpy_multi(double* __restrict__ w, int n, const double* __rest
   w[e] += sign * s;
 }
 
-// out = (a - b) * s ;  used for w = (G(U + h v) - G0) / h
-__global__ void k_diff_scale(const double* a, const double* b, double s, double* out, int n,
-                             const double* done) {
-  if (done && done[0] != 0.0) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) out[e] = (a[e] - b[e]) * s;
-}
-
 // out = a + s * b (s host scalar)
 __global__ void k_axpby(const double* a, double s, const double* b, double* out, int n,
                         const double* done) {
@@ -132,68 +129,12 @@ __global__ void k_normalize(const double* x, const double* nrm2, double* out, in
   if (e == 0 && dst) dst[0] = nr;
 }
 
-// Givens update of column j of H, residual estimate and the convergence flag
-__global__ void k_givens(double* sc, int j, int m, int* kcount) {
-  if (threadIdx.x != 0) return;
-  double* misc = sc + SC_MISC;
-  if (misc[M_DONE] != 0.0) return;
-  double* H = sc + SC_H;  // H[i*m + j]
-  double* g = sc + SC_G;
-  double* cs = sc + SC_CS;
-  double* sn = sc + SC_SN;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
-    H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
-    H[i * m + j] = t;
-  }
-  const double a = H[j * m + j], b = H[(j + 1) * m + j];
-  const double den = hypot(a, b);
-  cs[j] = den > 0.0 ? a / den : 1.0;
-  sn[j] = den > 0.0 ? b / den : 0.0;
-  H[j * m + j] = den;
-  H[(j + 1) * m + j] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  misc[M_JDONE] = j + 1;
-  kcount[0] += 1;
-  if (fabs(g[j + 1]) <= misc[M_RTOL] * misc[M_BNORM] || b == 0.0 || j + 1 == m) misc[M_DONE] = 1.0;
-}
-
-// y = H^{-1} g (upper triangular, jdone x jdone)
-__global__ void k_solve_upper(double* sc, int m, int* jd) {
-  if (threadIdx.x != 0) return;
-  double* H = sc + SC_H;
-  double* g = sc + SC_G;
-  double* y = sc + SC_Y;
-  const int k = (int)sc[SC_MISC + M_JDONE];
-  for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * y[l];
-    y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
-  }
-  jd[0] = k;
-}
-
-__global__ void k_gmres_start(double* sc, const double* beta2, double rtol, int first, double* bn) {
-  if (threadIdx.x != 0) return;
-  double* misc = sc + SC_MISC;
-  const double beta = sqrt(fmax(beta2[0], 0.0));
-  misc[M_BETA] = beta;
-  if (first) misc[M_BNORM] = beta;
-  misc[M_RTOL] = rtol;
-  misc[M_JDONE] = 0;
-  for (int i = 0; i < 65; ++i) sc[SC_G + i] = 0.0;
-  sc[SC_G] = beta;
-  misc[M_DONE] = (beta <= rtol * misc[M_BNORM] || beta == 0.0) ? 1.0 : 0.0;
-  if (bn) bn[0] = misc[M_DONE];
-}
-
 // ---------------- the residual ----------------
 // stage 1: rho = n_i - U0 and the momentum components as real fields
-__global__ void k_prep(const double* U, double n_i, int NX, int dx, double* fr) {
+__global__ void k_prep(const double* U, const double* n_i, int NX, int dx, double* fr) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= NX) return;
-  fr[x] = n_i - U[x];
+  fr[x] = n_i[0] - U[x];
   for (int m = 0; m < dx; ++m) fr[(long long)(1 + m) * NX + x] = U[(long long)(1 + m) * NX + x];
 }
 
@@ -276,9 +217,10 @@ __global__ void k_flux(int dx, int dv, int NX, int nmom, const double* U, const 
 
 // stage 4: out = K(U) = -div + S   or   out = U - rhs - coef K(U)
 __global__ void k_final(int dv, int NX, const double* div, const double* src, const double* U,
-                        const double* rhs, double coef, double* out, int mode_g) {
+                        const double* rhs, const double* coefp, double* out, int mode_g) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= NX) return;
+  const double coef = mode_g ? coefp[0] : 0.0;
   for (int e = 0; e < dv + 2; ++e) {
     double K = -div[(long long)e * NX + x];
     if (e >= 1 && e <= dv) K += src[(long long)(e - 1) * NX + x];
@@ -334,6 +276,7 @@ slar_status macro_alloc(slar_ctx* c) {
                     (long long)w->nblk * 72 + SC_SIZE + 16 + LS_SIZE + 3LL * c->dv * c->g.N[c->dx] +
                     (long long)(c->dv + 2) * c->NX + 64;
   if (cudaMalloc(&c->macro_ws, sizeof(double) * total) != cudaSuccess) return SLAR_ENOMEM;
+  if (cudaMalloc(&w->gi, sizeof(int) * 8) != cudaSuccess) return SLAR_ENOMEM;
   c->macro_ws_len = total;
   double* p = c->macro_ws;
   auto take = [&](long long k) { double* q = p; p += k; return q; };
@@ -355,6 +298,12 @@ slar_status macro_alloc(slar_ctx* c) {
 }
 
 void macro_free(slar_ctx* c) {
+  if (c->mw) {
+    if (c->mw->g_pro) cudaGraphExecDestroy(c->mw->g_pro);
+    if (c->mw->g_loop) cudaGraphExecDestroy(c->mw->g_loop);
+    if (c->mw->g_epi) cudaGraphExecDestroy(c->mw->g_epi);
+    if (c->mw->gi) cudaFree(c->mw->gi);
+  }
   delete c->mw;
   c->mw = nullptr;
 }
@@ -362,8 +311,7 @@ void macro_free(slar_ctx* c) {
 namespace {
 
 // out = K(U) (mode_g = 0) or G(U) = U - rhs - coef K(U) (mode_g = 1)
-slar_status eval_residual(slar_ctx* c, const double* U, const double* rhs, double coef, double* out,
-                          int mode_g) {
+slar_status eval_residual(slar_ctx* c, const double* U, const double* rhs, double* out, int mode_g) {
   MacroWS* w = c->mw;
   const Spectral& sp = *c->spectral;
   const int NX = c->NX, dx = c->dx, dv = c->dv;
@@ -379,7 +327,8 @@ slar_status eval_residual(slar_ctx* c, const double* U, const double* rhs, doubl
   double* div = src + (long long)dv * NX;
   double2* z1 = fz;
   double2* z2 = fz + (long long)nflux * NX;
-  slar::count_launch(), k_prep<<<nb(NX), 256, 0, s>>>(U, c->n_i, NX, dx, fr);
+  double* misc = w->sc + SC_MISC;
+  slar::count_launch(), k_prep<<<nb(NX), 256, 0, s>>>(U, misc + M_NI, NX, dx, fr);
   CK(cudaGetLastError());
   CK(sp.forward(fr, z1, nf1));
   slar::count_launch(), k_spec_fields<<<nb(NX), 256, 0, s>>>(sp, z1, z2);
@@ -391,7 +340,8 @@ slar_status eval_residual(slar_ctx* c, const double* U, const double* rhs, doubl
   CK(sp.forward(flux, z1, nflux));
   CK(spec_div(sp, z1, dv + 2, z2));
   CK(sp.inverse(z2, div, dv + 2));
-  slar::count_launch(), k_final<<<nb(NX), 256, 0, s>>>(dv, NX, div, src, U, rhs, coef, out, mode_g);
+  slar::count_launch(), k_final<<<nb(NX), 256, 0, s>>>(dv, NX, div, src, U, rhs, misc + M_COEF, out,
+                                                       mode_g);
   CK(cudaGetLastError());
   return SLAR_OK;
 }
@@ -415,19 +365,162 @@ slar_status absmax(slar_ctx* c, const double* x, double* out_dev) {
   return SLAR_OK;
 }
 
-__global__ void k_hcol_acc(double* H, const double* hcol, int m, int j, int pass, const double* done) {
-  if (done && done[0] != 0.0) return;
+// ---------------- GMRES as CUDA graphs ----------------
+// One Arnoldi iteration reads its index j from device memory, so the same captured body
+// serves every iteration; a WHILE conditional node repeats it until the Givens update sets
+// the convergence flag or j reaches the restart length (always terminates).
+__global__ void k_set_scalars(double* misc, double coef, double h, double n_i, double first) {
+  if (threadIdx.x != 0) return;
+  misc[M_COEF] = coef;
+  misc[M_H] = h;
+  misc[M_INVH] = h != 0.0 ? 1.0 / h : 0.0;
+  misc[M_NI] = n_i;
+  misc[M_FIRST] = first;
+}
+
+__global__ void k_axpby_j(const double* U, const double* misc, const double* V, const int* gi,
+                          double* Ut, int n) {
+  if (misc[M_DONE] != 0.0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) Ut[e] = U[e] + misc[M_H] * V[(long long)gi[0] * n + e];
+}
+
+__global__ void k_diff_j(const double* Gt, const double* G0, const double* misc, const int* gi,
+                         double* V, int n) {
+  if (misc[M_DONE] != 0.0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) V[(long long)(gi[0] + 1) * n + e] = (Gt[e] - G0[e]) * misc[M_INVH];
+}
+
+// partial dots of w = V_{j+1} with V_0..V_j (which = 0) or with itself (which = 1)
+__global__ void k_mdot_j(const double* __restrict__ V, int n, const int* gi, int which,
+                         double* __restrict__ part, int ldp, const double* misc) {
+  if (misc[M_DONE] != 0.0) return;
+  const int j = gi[0];
+  const double* w = V + (long long)(j + 1) * n;
+  const int nv = which ? 1 : j + 1;
+  const int s0 = blockIdx.x * RED_SEG;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < nv; i += 8) {
+    const double* v = which ? w : V + (long long)i * n;
+    double acc = 0.0;
+    for (int e = s0 + lane; e < s0 + RED_SEG && e < n; e += 32) acc += v[e] * w[e];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[(long long)blockIdx.x * ldp + i] = acc;
+  }
+}
+
+// H[i][j] (+)= sum_blk part[blk][i], hcol[i] = that sum; which = 1: H[j+1][j] = sqrt(sum)
+__global__ void k_fin_j(const double* part, int nblk, int ldp, double* sc, int m, const int* gi,
+                        int pass, int which) {
+  double* misc = sc + SC_MISC;
+  if (misc[M_DONE] != 0.0) return;
+  const int j = gi[0];
   const int i = threadIdx.x;
-  if (i > j) return;
-  if (pass == 0) H[i * m + j] = hcol[i];
-  else H[i * m + j] += hcol[i];
+  const int nv = which ? 1 : j + 1;
+  if (i >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(long long)b * ldp + i];
+  double* H = sc + SC_H;
+  if (which) {
+    H[(j + 1) * m + j] = sqrt(fmax(s, 0.0));
+  } else {
+    sc[SC_Y + i] = s;
+    H[i * m + j] = pass ? H[i * m + j] + s : s;
+  }
 }
 
-__global__ void k_set_sub(double* H, const double* nrm2, int m, int j, const double* done) {
-  if (done && done[0] != 0.0) return;
-  if (threadIdx.x == 0) H[(j + 1) * m + j] = sqrt(fmax(nrm2[0], 0.0));
+__global__ void k_orth_j(double* V, int n, const double* sc, const int* gi) {
+  if (sc[SC_MISC + M_DONE] != 0.0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int j = gi[0];
+  double s = 0.0;
+  for (int i = 0; i <= j; ++i) s += sc[SC_Y + i] * V[(long long)i * n + e];
+  V[(long long)(j + 1) * n + e] -= s;
 }
 
+__global__ void k_scale_j(double* V, int n, const double* sc, int m, const int* gi) {
+  if (sc[SC_MISC + M_DONE] != 0.0) return;
+  const int j = gi[0];
+  const double nr = sc[SC_H + (j + 1) * m + j];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) V[(long long)(j + 1) * n + e] = nr > 0.0 ? V[(long long)(j + 1) * n + e] / nr : 0.0;
+}
+
+// Givens update of column j, residual estimate, convergence flag, j += 1, loop condition
+__global__ void k_givens_j(double* sc, int m, int* gi, cudaGraphConditionalHandle loop, int use_cond) {
+  if (threadIdx.x != 0) return;
+  double* misc = sc + SC_MISC;
+  int cont = 0;
+  if (misc[M_DONE] == 0.0) {
+    const int j = gi[0];
+    double* H = sc + SC_H;
+    double* g = sc + SC_G;
+    double* cs = sc + SC_CS;
+    double* sn = sc + SC_SN;
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+      H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+      H[i * m + j] = t;
+    }
+    const double a = H[j * m + j], b = H[(j + 1) * m + j];
+    const double den = hypot(a, b);
+    cs[j] = den > 0.0 ? a / den : 1.0;
+    sn[j] = den > 0.0 ? b / den : 0.0;
+    H[j * m + j] = den;
+    H[(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    misc[M_JDONE] = j + 1;
+    gi[1] += 1;
+    gi[0] = j + 1;
+    if (fabs(g[j + 1]) <= misc[M_RTOL] * misc[M_BNORM] || b == 0.0 || j + 1 >= m) misc[M_DONE] = 1.0;
+    cont = misc[M_DONE] == 0.0 ? 1 : 0;
+  }
+  if (use_cond) cudaGraphSetConditional(loop, cont);
+}
+
+__global__ void k_gmres_start_g(double* sc, int* gi) {
+  if (threadIdx.x != 0) return;
+  double* misc = sc + SC_MISC;
+  const double beta = sqrt(fmax(misc[M_NORM], 0.0));
+  misc[M_BETA] = beta;
+  if (misc[M_FIRST] != 0.0) misc[M_BNORM] = beta;
+  misc[M_JDONE] = 0;
+  for (int i = 0; i < 65; ++i) sc[SC_G + i] = 0.0;
+  sc[SC_G] = beta;
+  misc[M_DONE] = (beta <= misc[M_RTOL] * misc[M_BNORM] || beta == 0.0) ? 1.0 : 0.0;
+  gi[0] = 0;
+}
+
+__global__ void k_solve_upper_g(double* sc, int m, int* gi) {
+  if (threadIdx.x != 0) return;
+  double* H = sc + SC_H;
+  double* g = sc + SC_G;
+  double* y = sc + SC_Y;
+  const int k = (int)sc[SC_MISC + M_JDONE];
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * y[l];
+    y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
+  }
+  gi[2] = k;
+  sc[SC_MISC + M_GRES] = fabs(g[k]);
+}
+
+__global__ void k_update_delta(double* delta, int n, const double* V, const double* sc, const int* gi) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int k = gi[2];
+  double s = 0.0;
+  for (int i = 0; i < k; ++i) s += sc[SC_Y + i] * V[(long long)i * n + e];
+  delta[e] += s;
+}
+
+__global__ void k_rtol(double* misc, double rtol) {
+  if (threadIdx.x == 0) misc[M_RTOL] = rtol;
+}
 
 struct SolveStats {
   int newton = 0, krylov = 0;
@@ -435,18 +528,111 @@ struct SolveStats {
   bool converged = false;
 };
 
+// GMRES launch sequences (captured into graphs, or launched directly when profiling)
+slar_status gmres_pro(slar_ctx* c) {
+  MacroWS* w = c->mw;
+  cudaStream_t s = c->s;
+  double* misc = w->sc + SC_MISC;
+  CKS(dot_into(c, w->r, 0, 1, w->r, misc + M_NORM, 0, nullptr));
+  slar::count_launch(), k_gmres_start_g<<<1, 32, 0, s>>>(w->sc, w->gi);
+  slar::count_launch(), k_normalize<<<nb(w->nvec), 256, 0, s>>>(w->r, misc + M_NORM, w->V, w->nvec, nullptr,
+                                                               misc + M_DONE);
+  CK(cudaGetLastError());
+  return SLAR_OK;
+}
+
+slar_status gmres_body(slar_ctx* c, cudaGraphConditionalHandle h, int use_cond) {
+  MacroWS* w = c->mw;
+  cudaStream_t s = c->s;
+  const int n = w->nvec, m = w->m;
+  double* sc = w->sc;
+  double* misc = sc + SC_MISC;
+  slar::count_launch(), k_axpby_j<<<nb(n), 256, 0, s>>>(w->U, misc, w->V, w->gi, w->Ut, n);
+  CKS(eval_residual(c, w->Ut, w->rhs, w->Gt, 1));
+  slar::count_launch(), k_diff_j<<<nb(n), 256, 0, s>>>(w->Gt, w->G0, misc, w->gi, w->V, n);
+  for (int pass = 0; pass < 2; ++pass) {
+    slar::count_launch(), k_mdot_j<<<w->nblk, 256, 0, s>>>(w->V, n, w->gi, 0, w->part, 72, misc);
+    slar::count_launch(), k_fin_j<<<1, 128, 0, s>>>(w->part, w->nblk, 72, sc, m, w->gi, pass, 0);
+    slar::count_launch(), k_orth_j<<<nb(n), 256, 0, s>>>(w->V, n, sc, w->gi);
+  }
+  slar::count_launch(), k_mdot_j<<<w->nblk, 256, 0, s>>>(w->V, n, w->gi, 1, w->part, 72, misc);
+  slar::count_launch(), k_fin_j<<<1, 128, 0, s>>>(w->part, w->nblk, 72, sc, m, w->gi, 0, 1);
+  slar::count_launch(), k_scale_j<<<nb(n), 256, 0, s>>>(w->V, n, sc, m, w->gi);
+  slar::count_launch(), k_givens_j<<<1, 32, 0, s>>>(sc, m, w->gi, h, use_cond);
+  CK(cudaGetLastError());
+  return SLAR_OK;
+}
+
+slar_status gmres_epi(slar_ctx* c) {
+  MacroWS* w = c->mw;
+  cudaStream_t s = c->s;
+  slar::count_launch(), k_solve_upper_g<<<1, 32, 0, s>>>(w->sc, w->m, w->gi);
+  slar::count_launch(), k_update_delta<<<nb(w->nvec), 256, 0, s>>>(w->delta, w->nvec, w->V, w->sc, w->gi);
+  CK(cudaGetLastError());
+  return SLAR_OK;
+}
+
+// capture the three GMRES graphs once per context
+slar_status build_gmres_graphs(slar_ctx* c) {
+  CaptureScope scope(c);
+  MacroWS* w = c->mw;
+  cudaStream_t s = c->s;
+  const long long l0 = launch_count();
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  CKS(gmres_pro(c));
+  CK(cudaStreamEndCapture(s, &g));
+  CK(cudaGraphInstantiate(&w->g_pro, g, 0));
+  CK(cudaGraphDestroy(g));
+  const long long l1 = launch_count();
+  cudaGraph_t gl;
+  CK(cudaGraphCreate(&gl, 0));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, gl, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  CK(cudaGraphAddNode(&cn, gl, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  CKS(gmres_body(c, h, 1));
+  cudaGraph_t body_out;
+  CK(cudaStreamEndCapture(s, &body_out));
+  CK(cudaGraphInstantiate(&w->g_loop, gl, 0));
+  CK(cudaGraphDestroy(gl));
+  const long long l2 = launch_count();
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  CKS(gmres_epi(c));
+  CK(cudaStreamEndCapture(s, &g));
+  CK(cudaGraphInstantiate(&w->g_epi, g, 0));
+  CK(cudaGraphDestroy(g));
+  const long long l3 = launch_count();
+  w->n_pro = l1 - l0;
+  w->n_body = l2 - l1;
+  w->n_epi = l3 - l2;
+  add_launches(-(l3 - l0));   // captured, not executed
+  w->graphs = true;
+  return SLAR_OK;
+}
+
 // JFNK on G(U) = U - rhs - coef K(U); w->U holds the initial guess and the result.
 slar_status jfnk(slar_ctx* c, double coef, double tol_abs, SolveStats* st) {
   MacroWS* w = c->mw;
   phase(c, PH_NEWTON);
   cudaStream_t s = c->s;
-  const int n = w->nvec, m = w->m;
+  const int n = w->nvec;
   double* sc = w->sc;
   double* misc = sc + SC_MISC;
-  int* kcount = reinterpret_cast<int*>(w->tot + 8);
-  CK(cudaMemsetAsync(kcount, 0, sizeof(int) * 2, s));
   const double sqeps = std::sqrt(std::ldexp(1.0, -52));
-  CKS(eval_residual(c, w->U, w->rhs, coef, w->G0, 1));
+  slar::count_launch(), k_rtol<<<1, 32, 0, s>>>(misc, c->cfg.krylov_tol);
+  slar::count_launch(), k_set_scalars<<<1, 32, 0, s>>>(misc, coef, 0.0, c->n_i, 1.0);
+  CK(cudaGetLastError());
+  const bool use_graphs = !(c->cfg.flags & SLAR_PROFILE_EVAL);
+  if (use_graphs && !w->graphs) CKS(build_gmres_graphs(c));
+  CKS(eval_residual(c, w->U, w->rhs, w->G0, 1));
   for (int it = 0;; ++it) {
     CKS(absmax(c, w->G0, misc + M_INF));
     CKS(dot_into(c, w->U, 0, 1, w->U, misc + M_UNORM, 0, nullptr));
@@ -458,79 +644,54 @@ slar_status jfnk(slar_ctx* c, double coef, double tol_abs, SolveStats* st) {
     if (!(ginf == ginf)) return set_error(c, SLAR_ENAN, "non-finite Newton residual");
     if (ginf <= tol_abs) { st->converged = true; break; }
     if (it >= c->cfg.newton_max) break;
-    // GMRES(m) on J delta = -G0 from delta = 0
-    const double h = sqeps * (1.0 + unorm);  // ||v_j|| = 1
+    // GMRES(m) on J delta = -G0 from delta = 0; J v by a forward difference with
+    // h = sqrt(eps) (1 + ||U||) / ||v|| and ||v|| = 1 for the Arnoldi vectors
+    const double h = sqeps * (1.0 + unorm);
     CK(cudaMemsetAsync(w->delta, 0, sizeof(double) * n, s));
-    int kry = 0;
+    CK(cudaMemsetAsync(w->gi, 0, sizeof(int) * 4, s));
     bool first = true;
+    int kry = 0;
     while (true) {
-      // r = -G0 - J delta   (J delta by a finite difference when delta != 0)
       if (first) {
         slar::count_launch(), k_lincomb3<<<nb(n), 256, 0, s>>>(w->r, w->G0, -1.0, nullptr, 0.0, nullptr, 0.0, n);
       } else {
-        double dn2;
+        // r = -G0 - J delta with J delta = (G(U + hd delta) - G0) / hd
         CKS(dot_into(c, w->delta, 0, 1, w->delta, misc + M_NORM, 0, nullptr));
-        CK(cudaMemcpyAsync(c->scal_host, misc + M_NORM, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(c->scal_host + 20, misc + M_NORM, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        dn2 = std::sqrt(c->scal_host[0]);
-        const double hd = sqeps * (1.0 + unorm) / (dn2 > 0.0 ? dn2 : 1.0);
+        const double dn = std::sqrt(c->scal_host[20]);
+        const double hd = sqeps * (1.0 + unorm) / (dn > 0.0 ? dn : 1.0);
         slar::count_launch(), k_axpby<<<nb(n), 256, 0, s>>>(w->U, hd, w->delta, w->Ut, n, nullptr);
-        CKS(eval_residual(c, w->Ut, w->rhs, coef, w->Gt, 1));
-        // r = -G0 - (Gt - G0)/hd = -Gt/hd + G0 (1/hd - 1)
-        slar::count_launch(), k_lincomb3<<<nb(n), 256, 0, s>>>(w->r, w->Gt, -1.0 / hd, w->G0, 1.0 / hd - 1.0, nullptr, 0.0, n);
+        CKS(eval_residual(c, w->Ut, w->rhs, w->Gt, 1));
+        slar::count_launch(), k_lincomb3<<<nb(n), 256, 0, s>>>(w->r, w->Gt, -1.0 / hd, w->G0, 1.0 / hd - 1.0,
+                                                              nullptr, 0.0, n);
       }
       CK(cudaGetLastError());
-      CKS(dot_into(c, w->r, 0, 1, w->r, misc + M_NORM, 0, nullptr));
-      slar::count_launch(), k_gmres_start<<<1, 32, 0, s>>>(sc, misc + M_NORM, c->cfg.krylov_tol, first ? 1 : 0, nullptr);
-      CK(cudaGetLastError());
-      slar::count_launch(), k_normalize<<<nb(n), 256, 0, s>>>(w->r, misc + M_NORM, w->V, n, nullptr, misc + M_DONE);
-      CK(cudaGetLastError());
-      const double* done = misc + M_DONE;
-      for (int j = 0; j < m; ++j) {
-        double* vj = w->V + (long long)j * n;
-        double* wv = w->V + (long long)(j + 1) * n;
-        slar::count_launch(), k_axpby<<<nb(n), 256, 0, s>>>(w->U, h, vj, w->Ut, n, done);
-        CK(cudaGetLastError());
-        CKS(eval_residual(c, w->Ut, w->rhs, coef, w->Gt, 1));
-        slar::count_launch(), k_diff_scale<<<nb(n), 256, 0, s>>>(w->Gt, w->G0, 1.0 / h, wv, n, done);
-        CK(cudaGetLastError());
-        // classical Gram-Schmidt, twice; H[i][j] for i <= j
-        double* hcol = sc + SC_Y;  // temporary coefficient column
-        for (int pass = 0; pass < 2; ++pass) {
-          CKS(dot_into(c, w->V, n, j + 1, wv, hcol, 0, done));
-          slar::count_launch(), k_axpy_multi<<<nb(n), 256, 0, s>>>(wv, n, w->V, n, j + 1, hcol, nullptr, -1.0, done);
-          CK(cudaGetLastError());
-          slar::count_launch(), k_hcol_acc<<<1, 128, 0, s>>>(sc + SC_H, hcol, m, j, pass, done);
-          CK(cudaGetLastError());
-        }
-        CKS(dot_into(c, wv, 0, 1, wv, misc + M_NORM, 0, done));
-        slar::count_launch(), k_set_sub<<<1, 32, 0, s>>>(sc + SC_H, misc + M_NORM, m, j, done);
-        slar::count_launch(), k_normalize<<<nb(n), 256, 0, s>>>(wv, misc + M_NORM, wv, n, nullptr, done);
-        slar::count_launch(), k_givens<<<1, 32, 0, s>>>(sc, j, m, kcount);
-        CK(cudaGetLastError());
+      slar::count_launch(), k_set_scalars<<<1, 32, 0, s>>>(misc, coef, h, c->n_i, first ? 1.0 : 0.0);
+      if (use_graphs) {
+        CK(cudaGraphLaunch(w->g_pro, s));
+        CK(cudaGraphLaunch(w->g_loop, s));
+        CK(cudaGraphLaunch(w->g_epi, s));
+      } else {
+        CKS(gmres_pro(c));
+        for (int j = 0; j < w->m; ++j) CKS(gmres_body(c, 0, 0));
+        CKS(gmres_epi(c));
       }
-      slar::count_launch(), k_solve_upper<<<1, 32, 0, s>>>(sc, m, kcount + 1);
-      slar::count_launch(), k_axpy_multi<<<nb(n), 256, 0, s>>>(w->delta, n, w->V, n, m, sc + SC_Y, kcount + 1, 1.0, nullptr);
-      CK(cudaGetLastError());
-      // converged? (true residual estimate below tolerance)
       CK(cudaMemcpyAsync(c->scal_host, misc, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(c->h_ranks + 12, kcount, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(c->h_ranks + 12, w->gi, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      kry = c->h_ranks[12];
+      const int jd = c->h_ranks[14];
+      if (use_graphs) add_launches(w->n_pro + w->n_epi + (long long)w->n_body * (jd > 0 ? jd : 1));
+      kry = c->h_ranks[13];
       const double* ms = c->scal_host;
-      const int jd = (int)ms[M_JDONE];
-      // the cycle converged if it stopped before m iterations or met the tolerance
-      double gres;
-      CK(cudaMemcpy(&gres, sc + SC_G + jd, sizeof(double), cudaMemcpyDeviceToHost));
-      const bool conv = std::fabs(gres) <= ms[M_RTOL] * ms[M_BNORM] || jd == 0;
+      const bool conv = ms[M_GRES] <= ms[M_RTOL] * ms[M_BNORM] || jd == 0;
       first = false;
       if (conv || kry >= c->cfg.krylov_max) break;
     }
     st->krylov += kry;
-    CK(cudaMemsetAsync(kcount, 0, sizeof(int) * 2, s));
     slar::count_launch(), k_axpby<<<nb(n), 256, 0, s>>>(w->U, 1.0, w->delta, w->U, n, nullptr);
     CK(cudaGetLastError());
-    CKS(eval_residual(c, w->U, w->rhs, coef, w->G0, 1));
+    CKS(eval_residual(c, w->U, w->rhs, w->G0, 1));
     st->newton += 1;
   }
   return SLAR_OK;
@@ -662,7 +823,7 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
         st.krylov += ss.krylov;
         st.residual = std::max(st.residual, ss.residual);
         st.converged &= ss.converged ? 1 : 0;
-        CKS(eval_residual(c, w->U, nullptr, 0.0, w->Kst[i], 0));
+        CKS(eval_residual(c, w->U, nullptr, w->Kst[i], 0));
         if (i < 2) c->ht[fslot].valid = false;
       }
       st.n_slar = 9;

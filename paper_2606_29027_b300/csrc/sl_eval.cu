@@ -227,10 +227,16 @@ __device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& 
 }
 
 template <typename T, int TILE>
-__global__ void __launch_bounds__(NTHREADS)
-k_sl_eval(GridDesc g, HTView<T> ht, CorrView corr, EvalArgs a, int at_grid) {
+__device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>& ht,
+                                             const CorrView& corr, EvalArgs a, int at_grid) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.done && *a.done) return;
+  if (a.kidx) {
+    const int kk = *a.kidx;
+    a.pivot += kk;
+    a.kterms = kk;
+    a.out += kk * a.out_stride;
+  }
   const long long e0 = (long long)blockIdx.x * TILE;
   if (e0 >= a.n) return;
   const int nT = (int)min((long long)TILE, a.n - e0);
@@ -346,6 +352,22 @@ k_sl_eval(GridDesc g, HTView<T> ht, CorrView corr, EvalArgs a, int at_grid) {
 }
 
 template <typename T, int TILE>
+__global__ void __launch_bounds__(NTHREADS)
+k_sl_eval(GridDesc g, HTView<T> ht, CorrView corr, EvalArgs a, int at_grid) {
+  sl_eval_body<T, TILE>(g, ht, corr, a, at_grid);
+}
+
+template <typename T, int TILE>
+__global__ void __launch_bounds__(NTHREADS)
+k_sl_eval_dev(GridDesc g, const EvalParams<T>* __restrict__ P, EvalArgs a) {
+  const EvalParams<T> q = *P;
+  a.tau = q.tau;
+  a.E = q.E;
+  a.foot_euler = q.foot_euler;
+  sl_eval_body<T, TILE>(g, q.ht, q.corr, a, 0);
+}
+
+template <typename T, int TILE>
 size_t smem_bytes(const GridDesc& g, const HTView<T>& ht) {
   size_t b = sizeof(double) * (TILE * 4 + TILE * 12 + TILE) + sizeof(int) * TILE * 12;
   int rs = 0;
@@ -361,7 +383,7 @@ template <typename T>
 cudaError_t launch_sl_eval(const GridDesc& g, const HTView<T>& ht, const CorrView& corr,
                            const EvalArgs& a, int at_grid, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  constexpr int TILE = sizeof(T) == 8 ? 32 : 64;
+  constexpr int TILE = 32;
   const size_t sm = smem_bytes<T, TILE>(g, ht);
   static bool attr_set[2] = {false, false};
   if (!attr_set[sizeof(T) == 8]) {
@@ -375,6 +397,46 @@ cudaError_t launch_sl_eval(const GridDesc& g, const HTView<T>& ht, const CorrVie
   return cudaGetLastError();
 }
 
+cudaError_t sl_eval_init_attrs() {
+  const int mx = 200 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_sl_eval<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_dev<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_dev<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  return e;
+}
+
+template <typename T>
+size_t sl_eval_smem(const GridDesc& g, const int* r6) {
+  HTView<T> v{};
+  for (int m = 0; m < 4; ++m) v.r[m] = r6[m];
+  v.r12 = r6[4];
+  v.r34 = r6[5];
+  return smem_bytes<T, 32>(g, v);
+}
+
+template <typename T>
+cudaError_t launch_sl_eval_dev(const GridDesc& g, const EvalParams<T>* P, const EvalArgs& a,
+                               size_t sm, cudaStream_t s) {
+  constexpr int TILE = 32;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(T) == 8]) {
+    cudaError_t e = cudaFuncSetAttribute(k_sl_eval_dev<T, TILE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set[sizeof(T) == 8] = true;
+  }
+  const long long blocks = (a.n + TILE - 1) / TILE;
+  slar::count_launch(), k_sl_eval_dev<T, TILE><<<(unsigned)blocks, NTHREADS, sm, s>>>(g, P, a);
+  return cudaGetLastError();
+}
+
+template size_t sl_eval_smem<double>(const GridDesc&, const int*);
+template size_t sl_eval_smem<float>(const GridDesc&, const int*);
+template cudaError_t launch_sl_eval_dev<double>(const GridDesc&, const EvalParams<double>*,
+                                                const EvalArgs&, size_t, cudaStream_t);
+template cudaError_t launch_sl_eval_dev<float>(const GridDesc&, const EvalParams<float>*,
+                                               const EvalArgs&, size_t, cudaStream_t);
 template cudaError_t launch_sl_eval<double>(const GridDesc&, const HTView<double>&,
                                             const CorrView&, const EvalArgs&, int, cudaStream_t);
 template cudaError_t launch_sl_eval<float>(const GridDesc&, const HTView<float>&,

@@ -16,33 +16,61 @@
 namespace slar {
 namespace {
 
-// one 1D complex FFT per CTA over `lines` lines of length n with element stride `es` and
-// line stride `ls` (in complex elements), batch along blockIdx.y with stride bs.
-__global__ void k_fft_lines(double2* data, int n, int logn, long long es, long long ls, long long bs,
-                            const double2* tw, int inverse) {
-  extern __shared__ double2 buf[];
-  double2* line = data + blockIdx.y * bs + blockIdx.x * ls;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < n; i += blockDim.x) {
-    const int rev = __brev(i) >> (32 - logn);
-    buf[rev] = line[i * es];
+// In-place radix-2 FFTs of `nl` lines of length n held in shared memory (line l starts at
+// buf + l * ls, element stride es); all threads of the block cooperate.
+__device__ void smem_fft_lines(double2* buf, int n, int logn, int nl, int ls, int es,
+                               const double2* tw, int inverse) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // bit-reversal permutation (swap pairs once)
+  for (int it = tid; it < nl * n; it += nt) {
+    const int l = it / n, i = it - l * n;
+    const int r = __brev(i) >> (32 - logn);
+    if (r > i) {
+      double2* a = buf + l * ls + i * es;
+      double2* b = buf + l * ls + r * es;
+      const double2 t = *a;
+      *a = *b;
+      *b = t;
+    }
   }
   __syncthreads();
   for (int s = 1; s <= logn; ++s) {
     const int m = 1 << s, half = m >> 1;
-    for (int b = tid; b < n / 2; b += blockDim.x) {
+    for (int it = tid; it < nl * (n / 2); it += nt) {
+      const int l = it / (n / 2), b = it - l * (n / 2);
       const int grp = b / half, j = b - grp * half;
       const int i0 = grp * m + j, i1 = i0 + half;
-      double2 w = tw[j * (n / m)];          // exp(-2 pi i j / m)
+      double2 w = tw[j * (n / m)];
       if (inverse) w.y = -w.y;
-      const double2 u = buf[i0], v = buf[i1];
+      double2* x0 = buf + l * ls + i0 * es;
+      double2* x1 = buf + l * ls + i1 * es;
+      const double2 u = *x0, v = *x1;
       const double2 t = make_double2(w.x * v.x - w.y * v.y, w.x * v.y + w.y * v.x);
-      buf[i0] = make_double2(u.x + t.x, u.y + t.y);
-      buf[i1] = make_double2(u.x - t.x, u.y - t.y);
+      *x0 = make_double2(u.x + t.x, u.y + t.y);
+      *x1 = make_double2(u.x - t.x, u.y - t.y);
     }
     __syncthreads();
   }
-  for (int i = tid; i < n; i += blockDim.x) line[i * es] = buf[i];
+}
+
+// LPB lines of length n per CTA: gather (element stride es, line stride ls) into shared
+// memory, transform, scatter.  Batch along blockIdx.y with stride bs.
+__global__ void k_fft_lines(double2* data, int n, int logn, long long es, long long ls, long long bs,
+                            int nlines, int lpb, const double2* tw, int inverse) {
+  extern __shared__ double2 buf[];
+  const int l0 = blockIdx.x * lpb;
+  const int nl = min(lpb, nlines - l0);
+  double2* base = data + blockIdx.y * bs;
+  for (int it = threadIdx.x; it < nl * n; it += blockDim.x) {
+    const int l = it / n, i = it - l * n;
+    buf[l * n + i] = base[(l0 + l) * ls + i * es];
+  }
+  __syncthreads();
+  smem_fft_lines(buf, n, logn, nl, n, 1, tw, inverse);
+  for (int it = threadIdx.x; it < nl * n; it += blockDim.x) {
+    const int l = it / n, i = it - l * n;
+    base[(l0 + l) * ls + i * es] = buf[l * n + i];
+  }
 }
 
 __global__ void k_real_to_cplx(const double* __restrict__ f, double2* __restrict__ z, long long n) {
@@ -100,21 +128,18 @@ void Spectral::release() {
 }
 
 cudaError_t Spectral::fft(double2* z, int batch, int inverse) const {
-  if (dx == 1) {
-    slar::count_launch(), k_fft_lines<<<dim3(1, batch), n[0] / 2 > 0 ? (n[0] / 2 < 64 ? n[0] / 2 : 64) : 1,
-                  sizeof(double2) * n[0], s>>>(z, n[0], logn[0], 1, n[0], NX, twid[0], inverse);
+  // 4 lines per CTA (64 threads each) keeps many CTAs in flight for batches of 64^2 fields
+  auto pass = [&](int len, int lg, long long es, long long ls, int nlines, const double2* tw) {
+    const int lpb = 4;
+    dim3 grid((nlines + lpb - 1) / lpb, batch);
+    slar::count_launch(), k_fft_lines<<<grid, 128, sizeof(double2) * lpb * len, s>>>(
+        z, len, lg, es, ls, NX, nlines, lpb, tw, inverse);
     return cudaGetLastError();
-  }
-  // rows (along x2, contiguous), then columns (along x1, stride n1)
-  const int t1 = n[1] / 2 < 64 ? n[1] / 2 : 64;
-  slar::count_launch(), k_fft_lines<<<dim3(n[0], batch), t1 > 0 ? t1 : 1, sizeof(double2) * n[1], s>>>(
-      z, n[1], logn[1], 1, n[1], NX, twid[1], inverse);
-  cudaError_t e = cudaGetLastError();
+  };
+  if (dx == 1) return pass(n[0], logn[0], 1, n[0], 1, twid[0]);
+  cudaError_t e = pass(n[1], logn[1], 1, n[1], n[0], twid[1]);    // rows (along x2)
   if (e != cudaSuccess) return e;
-  const int t0 = n[0] / 2 < 64 ? n[0] / 2 : 64;
-  slar::count_launch(), k_fft_lines<<<dim3(n[1], batch), t0 > 0 ? t0 : 1, sizeof(double2) * n[0], s>>>(
-      z, n[0], logn[0], n[1], 1, NX, twid[0], inverse);
-  return cudaGetLastError();
+  return pass(n[0], logn[0], n[1], 1, n[1], twid[0]);             // columns (along x1)
 }
 
 cudaError_t Spectral::forward(const double* f, double2* z, int batch) const {

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libslar.so")
 
 SLAR_OK, SLAR_EINVAL, SLAR_ENOMEM, SLAR_ECUDA, SLAR_ENOCONV, SLAR_ETIMEOUT, SLAR_ERANK, SLAR_ENAN = range(8)
 SLAR_FP64, SLAR_FP32 = 0, 1
-SLAR_LOMAC, SLAR_FOOT_EULER, SLAR_PROFILE = 1, 2, 4
+SLAR_LOMAC, SLAR_FOOT_EULER, SLAR_PROFILE, SLAR_PROFILE_EVAL = 1, 2, 4, 8
 
 # every entry point declared in include/slar.h
 EXPORTED = ["slar_create", "slar_destroy", "slar_last_error", "init_ht", "sl_step", "ht_truncate",
@@ -128,7 +128,8 @@ def _dptr(a: np.ndarray):
 
 def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, eps=1e-6, rank_cap=16,
                 newton_tol=1e-12, krylov_tol=1e-4, krylov_restart=30, newton_max=20, krylov_max=200,
-                precision="fp64", lomac=True, foot="rk3", delta_floor=1e-12, profile=False) -> Config:
+                precision="fp64", lomac=True, foot="rk3", delta_floor=1e-12, profile=False,
+                profile_eval=False) -> Config:
     if workload is not None:
         dx, dv, N, lo, hi = workload.dx, workload.dv, workload.N, workload.lo, workload.hi
         eps, rank_cap = workload.eps, workload.rank_cap
@@ -145,7 +146,7 @@ def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, ep
     cfg.krylov_restart, cfg.newton_max, cfg.krylov_max = krylov_restart, newton_max, krylov_max
     cfg.precision = SLAR_FP32 if precision == "fp32" else SLAR_FP64
     cfg.flags = ((SLAR_LOMAC if lomac else 0) | (SLAR_FOOT_EULER if foot == "euler" else 0)
-                 | (SLAR_PROFILE if profile else 0))
+                 | (SLAR_PROFILE if profile else 0) | (SLAR_PROFILE_EVAL if profile_eval else 0))
     cfg.delta_floor = delta_floor
     return cfg
 
