@@ -196,6 +196,25 @@ slar_status ht_import(slar_ctx* ctx, const slar_ht_view* view);
 slar_status slar_get_conserved(slar_ctx* ctx, double* U_dev, double* n_i);
 slar_status slar_set_conserved(slar_ctx* ctx, const double* U_dev, double n_i);
 
+/* Allocation-free spectral Poisson solve for callers that cannot allocate device memory:
+ * code that runs while a stream is recorded into a CUDA graph in a capture mode in which
+ * cudaMalloc is illegal, or a host framework that owns a fixed, pre-reserved device pool
+ * and does not let libraries allocate.  The paper has no counterpart of this entry point;
+ * it computes what poisson_field computes, without a context.
+ *   dx in {1, 2}; N[m] a power of two <= 128; L[m] > 0 the period of dimension m;
+ *   rho_dev: device [NX]; E_dev: device [dx][NX]; phi_dev: device [NX] or NULL;
+ *   energy: host scalar or NULL (then the call synchronises `stream`);
+ *   stream: cudaStream_t (NULL = legacy default stream).
+ * Scratch (1 MiB of spectra plus twiddle and wavenumber tables) is a set of file-scope
+ * static __device__ arrays that every GPU loading the library holds until process exit;
+ * this call allocates nothing (no cudaMalloc/cudaFree).  The first call on a device looks
+ * up the arrays' device addresses (cudaGetSymbolAddress), so make that first call before
+ * any stream capture.  All calls share the arrays and overwrite them completely; calls that
+ * overlap on the GPU (several streams or threads) race.  Returns SLAR_EINVAL for sizes
+ * beyond the maximum or bad arguments, SLAR_ECUDA if a CUDA call fails. */
+slar_status slar_poisson_field_static(int dx, const int* N, const double* L, const double* rho_dev,
+                                      double* E_dev, double* phi_dev, double* energy, void* stream);
+
 /* Total number of kernels launched by this library in this process (all contexts). */
 slar_status slar_launch_count(long long* out);
 

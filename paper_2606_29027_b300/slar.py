@@ -24,7 +24,7 @@ SLAR_LOMAC, SLAR_FOOT_EULER, SLAR_PROFILE, SLAR_PROFILE_EVAL = 1, 2, 4, 8
 EXPORTED = ["slar_create", "slar_destroy", "slar_last_error", "init_ht", "sl_step", "ht_truncate",
             "moments", "lomac_correct", "poisson_field", "ht_eval", "sl_eval", "slar_advect",
             "slar_set_pivot_replay", "ht_export", "ht_import", "slar_get_conserved",
-            "slar_set_conserved", "slar_sizes", "slar_launch_count"]
+            "slar_set_conserved", "slar_sizes", "slar_launch_count", "slar_poisson_field_static"]
 
 
 class Config(C.Structure):
@@ -89,6 +89,7 @@ def load():
         "slar_set_conserved": ([P, P, D], I),
         "slar_sizes": ([P, C.POINTER(I), C.POINTER(I)], I),
         "slar_launch_count": ([C.POINTER(LL)], I),
+        "slar_poisson_field_static": ([I, P, P, P, P, P, C.POINTER(D), P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -105,6 +106,23 @@ def launch_count() -> int:
     if st != SLAR_OK:
         raise SlarError(st, "slar_launch_count failed")
     return n.value
+
+
+def poisson_field_static(N, L, rho, E, phi=None, stream=None, energy=True):
+    """Context-free, allocation-free spectral Poisson solve (see include/slar.h).  rho, E,
+    phi: torch CUDA float64 tensors.  Returns the electric energy (or None)."""
+    import torch
+    dx = len(N)
+    Na = (C.c_int * 2)(*[int(n) for n in N] + [1] * (2 - dx))
+    La = (C.c_double * 2)(*[float(x) for x in L] + [1.0] * (2 - dx))
+    W = C.c_double()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    status = load().slar_poisson_field_static(dx, Na, La, C.c_void_p(_ptr(rho)), C.c_void_p(_ptr(E)),
+                                              C.c_void_p(_ptr(phi)), C.byref(W) if energy else None,
+                                              C.c_void_p(st.cuda_stream))
+    if status != SLAR_OK:
+        raise SlarError(status, "slar_poisson_field_static failed")
+    return W.value if energy else None
 
 
 class SlarError(RuntimeError):
