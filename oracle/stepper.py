@@ -27,7 +27,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from . import cross, field, lomac, macro, sl
+from . import cross, field, lomac, macro, net, precond, sl
 from .ht import HT, from_terms, truncate
 from .sl import PhaseGrid
 
@@ -44,6 +44,13 @@ class Params:
     foot: str = "rk3"
     delta: float = lomac.DELTA_DEFAULT
     lomac: bool = True
+    # Newton-Krylov solve of the BDF3 steps: "none" (the paper's plain JFNK), "circulant"
+    # (block-circulant right preconditioner) or "learned" (network guess and block on top
+    # of the circulant preconditioner; plain JFNK from U* is the fallback).
+    precond: str = "none"
+    net_theta: Optional[np.ndarray] = None
+    net_hidden: int = net.HIDDEN
+    probes: int = 4
 
 
 @dataclass
@@ -66,6 +73,8 @@ class StepStats:
     converged: bool = True
     W: float = 0.0
     aca_ranks: list = dfield(default_factory=list)
+    guess_used: bool = False
+    fallback: bool = False
 
 
 def init_state(factors, g: PhaseGrid, prm: Params) -> State:
@@ -117,7 +126,62 @@ def _solve(cl: macro.Closure, rhs: np.ndarray, coef: float, U_guess: np.ndarray,
                       prm.newton_max, prm.krylov_max)
 
 
-def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None) -> StepStats:
+def spatial_shape(g: PhaseGrid):
+    """The spatial grid as a 2D array shape (n0, n1), n1 = 1 in one dimension."""
+    return (g.N[0], g.N[1]) if g.dx == 2 else (g.N[0], 1)
+
+
+def _solve_precond(Gfun, Un_prev: np.ndarray, Ustar: np.ndarray, tol_abs: float, prm: Params,
+                   shape2d, stats: StepStats):
+    """Preconditioned (and, with a network, warm-started) JFNK; plain JFNK from U* if it
+    does not converge."""
+    m = Ustar.shape[0]
+    U0, y = Ustar, None
+    if prm.precond == "learned":
+        x, sD = net.features(Un_prev, Ustar, shape2d)
+        y, _ = net.forward(prm.net_theta, x, m, prm.net_hidden)
+        Ug = net.guess_from_output(y, Ustar, sD)
+        if np.max(np.abs(Gfun(Ug))) <= np.max(np.abs(Gfun(Ustar))):
+            U0 = Ug
+            stats.guess_used = True
+    P = precond.circulant_blocks(Gfun, U0, Gfun(U0), shape2d)
+    if y is None:
+        Papply = lambda v: precond.apply_circulant(P, v)
+    else:
+        Papply = lambda v: precond.apply_circulant(P, net.apply_block(y, v))
+    Un, ns = precond.jfnk_right(Gfun, U0, tol_abs, prm.krylov_tol, Papply, prm.krylov_restart,
+                                prm.newton_max, prm.krylov_max)
+    stats.newton, stats.krylov = ns.newton, ns.krylov
+    stats.residual, stats.converged = ns.residual, ns.converged
+    if not ns.converged:
+        stats.fallback = True
+        Un, ps = macro.jfnk(Gfun, Ustar, tol_abs, prm.krylov_tol, prm.krylov_restart,
+                            prm.newton_max, prm.krylov_max)
+        stats.newton += ps.newton
+        stats.krylov += ps.krylov
+        stats.residual, stats.converged = ps.residual, ps.converged
+    return Un
+
+
+def training_sample(Gfun, Un_prev: np.ndarray, Ustar: np.ndarray, Unew: np.ndarray, shape2d,
+                    probes: np.ndarray) -> net.Sample:
+    """Training sample of one BDF3 solve: features, scaled guess target, and probe pairs
+    (v_s, J P v_s) with J and the block-circulant P at U*.  probes (S-1, m, NX) are the
+    random directions; the first direction is the residual -G(U*), RMS-scaled per channel."""
+    m = Ustar.shape[0]
+    x, sD = net.features(Un_prev, Ustar, shape2d)
+    t = ((Unew - Ustar) / sD[:, None]).reshape((m,) + tuple(shape2d))
+    G0 = Gfun(Ustar)
+    P = precond.circulant_blocks(Gfun, Ustar, G0, shape2d)
+    v0 = -G0 / net.rms_scales(G0, net.SCALE_FLOOR)[:, None]
+    vs = [v0] + [p for p in probes]
+    ws = [precond.fd_jv(Gfun, Ustar, G0, precond.apply_circulant(P, v)) for v in vs]
+    shp = (len(vs), m) + tuple(shape2d)
+    return net.Sample(x=x, t=t, v=np.stack(vs).reshape(shp), w=np.stack(ws).reshape(shp))
+
+
+def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None,
+            record: Optional[list] = None, probes: Optional[np.ndarray] = None) -> StepStats:
     """Advance the state by one step (flowchart of Sec. 3.2.3)."""
     stats = StepStats()
     if not prm.lomac:
@@ -157,9 +221,16 @@ def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None) -> Ste
         rhs = a[0] * st.U + a[1] * st.hist[0] + a[2] * st.hist[1]
         tol_abs = macro.newton_tol_abs(prm.newton_tol, st.U)
         Ustar = lomac.conserved_from_moments(cl.mom_star, g, st.n_i)
-        Un, ns = _solve(cl, rhs, macro.BDF3["beta"] * dt, Ustar, tol_abs, prm)
-        stats.newton, stats.krylov = ns.newton, ns.krylov
-        stats.residual, stats.converged = ns.residual, ns.converged
+        coef = macro.BDF3["beta"] * dt
+        Gfun = lambda U: U - rhs - coef * macro.K_operator(U, cl)
+        if prm.precond == "none":
+            Un, ns = _solve(cl, rhs, coef, Ustar, tol_abs, prm)
+            stats.newton, stats.krylov = ns.newton, ns.krylov
+            stats.residual, stats.converged = ns.residual, ns.converged
+        else:
+            Un = _solve_precond(Gfun, st.U, Ustar, tol_abs, prm, spatial_shape(g), stats)
+        if record is not None:
+            record.append(training_sample(Gfun, st.U, Ustar, Un, spatial_shape(g), probes))
         st.hist = [st.U] + st.hist[:1]
         st.U = Un
         st.F = lomac.correct(Fs, cl.basis, Un, g, st.n_i)
