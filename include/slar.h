@@ -51,9 +51,21 @@ enum {
     SLAR_LOMAC = 1,        /* apply the implicit LoMaC correction every step (Sec. 3.2) */
     SLAR_FOOT_EULER = 2,   /* first-order foot (x - v tau, v + E tau) instead of RK3 */
     SLAR_PROFILE = 4,      /* CUDA events at phase boundaries (stats.phase_ms) */
-    SLAR_PROFILE_EVAL = 8  /* CUDA events around every entry-evaluator launch (stats.eval_ms);
+    SLAR_PROFILE_EVAL = 8, /* CUDA events around every entry-evaluator launch (stats.eval_ms);
                               the cross approximation then runs as individual launches
                               instead of its captured CUDA graph */
+    SLAR_PRECOND = 16,     /* BDF3 Newton-Krylov solves with a block-circulant right
+                              preconditioner: the Jacobian of G (Eq. BE_nonlinear_system) is
+                              probed at the initial guess with one impulse per conserved
+                              component, its (dv+2) x (dv+2) Fourier-mode blocks are inverted
+                              and applied mode by mode (an addition to the paper, whose JFNK is
+                              unpreconditioned; the Newton stop test is unchanged) */
+    SLAR_LEARNED = 32      /* warm start of the BDF3 solves from the network attached with
+                              slar_attach_net: initial guess U* + s_D d(x) (kept only if its
+                              residual is not larger than that of U(F*)) and a per-point block
+                              B(x) = I + b(x) applied before the block-circulant
+                              preconditioner; if the solve does not converge it is repeated by
+                              plain JFNK from U(F*).  Implies SLAR_PRECOND. */
 };
 
 typedef struct slar_config {
@@ -87,6 +99,10 @@ typedef struct slar_stats {
     long long launches;     /* kernels this library launched during the step */
     double phase_ms[6];     /* SLAR_PROFILE: device time of cross approximation, truncation,
                                fields/moments, LoMaC closure, Newton-Krylov, diagnostics */
+    int guess_used;         /* SLAR_LEARNED: the network's initial guess was taken */
+    int fallback;           /* the preconditioned solve failed and plain JFNK was run */
+    int recorded;           /* a training sample was written (slar_set_record) */
+    int g_evals;            /* residual evaluations G(U) of the Newton-Krylov solves */
 } slar_stats;
 
 /* Host-side view of an HT state for import/export.  Layouts (row-major):
@@ -214,6 +230,71 @@ slar_status slar_set_conserved(slar_ctx* ctx, const double* U_dev, double n_i);
  * beyond the maximum or bad arguments, SLAR_ECUDA if a CUDA call fails. */
 slar_status slar_poisson_field_static(int dx, const int* N, const double* L, const double* rho_dev,
                                       double* E_dev, double* phi_dev, double* energy, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned JFNK warm start (an addition to the paper's method).  A network of four periodic
+ * 3x3 convolutions on the spatial grid, FP32, channels 2m -> H -> H -> H -> m + m*m
+ * (m = dv + 2, H <= 32 hidden channels, tanh after the first three layers):
+ *   input  x[2m][NX]: the fluctuations of U^n about their means (= -rho, -J, e for the
+ *          electron moments of Sec. 2), each divided by its RMS over the grid, then
+ *          U* - U^n (U* = U(F*), the moments after SLAR_VP), each divided by its RMS s_D;
+ *   output y[m + m*m][NX]: d (guess U* + s_D d) and b, the per-point block B = I + b
+ *          (row-major m x m per point).
+ * Parameters are one flat FP32 vector: per layer W (Cout, Cin, 3, 3) row-major, then the
+ * bias (Cout).  A convolution is the periodic cross-correlation
+ *   out[o][i][j] = bias[o] + sum_c sum_{p,q=-1..1} W[o][c][p+1][q+1] in[c][i+p][j+q].
+ * Training sample (FP32, written by slar_set_record, n_probes = S >= 1), consecutive:
+ *   x[2m][NX] | t[m][NX] = (U^{n+1} - U*) / s_D | v[S][m][NX] | w[S][m][NX]
+ * with w_s = J P v_s (J the Jacobian of G and P the block-circulant preconditioner, both
+ * at U*; v_0 = -G(U*) scaled to unit RMS per component, v_s>0 random signs from
+ * SplitMix64).  Loss per sample, averaged over the batch:
+ *   mean_x,c (d - t)^2  +  mean_s,x,c ((B w_s - v_s))^2.
+ * ------------------------------------------------------------------------------------- */
+typedef struct slar_net slar_net;
+
+/* Number of FP32 parameters of a network for m conserved variables, H hidden channels. */
+slar_status slar_net_param_count(int m, int hidden, long long* out);
+
+/* Floats of one training sample on a grid of nx points with n_probes probe pairs. */
+slar_status slar_sample_floats(int m, int nx, int n_probes, long long* out);
+
+/* Create a network for grids n0 x n1 (n1 = 1 in one dimension; n0, n1 powers of two
+ * <= 128), up to max_batch samples per training step, parameters zero, work on `stream`
+ * (cudaStream_t, NULL = legacy default stream).  Errors: SLAR_EINVAL, SLAR_ENOMEM. */
+slar_status slar_net_create(int m, int hidden, int n0, int n1, int max_batch, void* stream,
+                            slar_net** out);
+slar_status slar_net_destroy(slar_net* net);
+
+/* Copy the parameters in (host FP32 [n], n = slar_net_param_count; also resets the Adam
+ * moments and step counter) or out (synchronises the stream). */
+slar_status slar_net_set_params(slar_net* net, const float* theta_host, long long n);
+slar_status slar_net_get_params(slar_net* net, float* theta_host, long long n);
+
+/* Inference: x_dev device FP32 [batch][2m][NX] -> y_dev device FP32 [batch][m + m*m][NX]. */
+slar_status slar_net_forward(slar_net* net, const float* x_dev, int batch, float* y_dev);
+
+/* Mean loss over the samples idx_dev[0..batch) (device int32) of the sample array
+ * samples_dev (device FP32, sample k at k * slar_sample_floats) and its gradient with
+ * respect to the parameters.  loss: host scalar or NULL; grad_dev: device FP32 [n] or
+ * NULL.  With a non-NULL loss the call synchronises the stream. */
+slar_status slar_net_loss_grad(slar_net* net, const float* samples_dev, int n_probes,
+                               const int* idx_dev, int batch, double* loss, float* grad_dev);
+
+/* One Adam step (Kingma and Ba 2015; beta1 0.9, beta2 0.999, epsilon 1e-8, bias-corrected)
+ * with learning rate lr on the mean loss of the given samples. */
+slar_status slar_net_train_step(slar_net* net, const float* samples_dev, int n_probes,
+                                const int* idx_dev, int batch, float lr, double* loss);
+
+/* Use `net` (NULL detaches) for the SLAR_LEARNED warm start of the context; the network's
+ * m and grid must match the context.  The context keeps the pointer until detached. */
+slar_status slar_attach_net(slar_ctx* ctx, slar_net* net);
+
+/* Write the training sample of the next BDF3 step to sample_dev (device FP32,
+ * slar_sample_floats(dv+2, NX, n_probes) floats; NULL cancels).  The random probe signs
+ * come from SplitMix64 seeded with `seed` and the step index.  One-shot: call again for
+ * the next step.  Recording costs n_probes + dv + 2 extra residual evaluations. */
+slar_status slar_set_record(slar_ctx* ctx, float* sample_dev, int n_probes,
+                            unsigned long long seed);
 
 /* Total number of kernels launched by this library in this process (all contexts). */
 slar_status slar_launch_count(long long* out);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "context.cuh"
+#include "macro.cuh"
 
 namespace slar {
 namespace {
@@ -61,6 +62,9 @@ slar_status validate(const slar_config* cfg, char* msg, size_t len) {
   if (!(cfg->eps >= 0.0)) { snprintf(msg, len, "eps must be >= 0"); return SLAR_EINVAL; }
   if (cfg->precision != SLAR_FP64 && cfg->precision != SLAR_FP32) {
     snprintf(msg, len, "unknown precision"); return SLAR_EINVAL;
+  }
+  if (cfg->flags & ~(SLAR_LOMAC | SLAR_FOOT_EULER | SLAR_PROFILE | SLAR_PROFILE_EVAL | SLAR_PRECOND | SLAR_LEARNED)) {
+    snprintf(msg, len, "unknown flag bits"); return SLAR_EINVAL;
   }
   if (cfg->krylov_restart < 1 || cfg->krylov_restart > 64) {
     snprintf(msg, len, "krylov_restart must be in [1, 64]"); return SLAR_EINVAL;
@@ -486,8 +490,29 @@ slar_status lomac_correct(slar_ctx* c, const double* U_target) {
   return lomac_apply(c, U_target);
 }
 
+slar_status slar_attach_net(slar_ctx* c, slar_net* net) {
+  if (!c) return SLAR_EINVAL;
+  if (net) {
+    const int n1 = c->dx == 2 ? c->g.N[1] : 1;
+    if (net_m(net) != c->dv + 2 || net_n0(net) != c->g.N[0] || net_n1(net) != n1)
+      return set_error(c, SLAR_EINVAL, "network does not match the context's grid");
+  }
+  c->net = net;
+  return SLAR_OK;
+}
+
+slar_status slar_set_record(slar_ctx* c, float* dst, int n_probes, unsigned long long seed) {
+  if (!c || (dst && (n_probes < 1 || n_probes > 64))) return SLAR_EINVAL;
+  c->rec_dst = dst;
+  c->rec_S = n_probes;
+  c->rec_seed = seed;
+  return SLAR_OK;
+}
+
 slar_status sl_step(slar_ctx* c, double dt, slar_stats* stats) {
   if (!c) return SLAR_EINVAL;
+  if ((c->cfg.flags & SLAR_LEARNED) && !c->net)
+    return set_error(c, SLAR_EINVAL, "SLAR_LEARNED needs a network (slar_attach_net)");
   if (!c->ht[c->cur].valid || !c->has_U) return set_error(c, SLAR_EINVAL, "call init_ht first");
   if (!(dt > 0.0)) return set_error(c, SLAR_EINVAL, "dt must be > 0");
   return step_impl(c, dt, stats);

@@ -41,6 +41,8 @@ struct AcaState {
 
 }  // namespace slar
 
+struct slar_net;
+
 struct slar_ctx {
   slar_config cfg;
   cudaStream_t s = nullptr;        // caller's stream: all work is ordered on it
@@ -151,6 +153,12 @@ struct slar_ctx {
   int ph_tag[256] = {};
   int ph_n = 0;
   double prof_flop = 0.0;  // algorithmic flops of the sampled entries this step
+
+  // learned warm start and training-sample recording
+  slar_net* net = nullptr;         // attached network (not owned)
+  float* rec_dst = nullptr;        // device destination of the next sample (one-shot)
+  int rec_S = 0;
+  unsigned long long rec_seed = 0;
 
   char err[512] = {0};
 };

@@ -15,39 +15,11 @@
 
 #include "context.cuh"
 #include "lomac.cuh"
+#include "macro.cuh"
 
 namespace slar {
 
-struct MacroWS {
-  int nvec = 0, m = 0;
-  double *U = nullptr, *G0 = nullptr, *Ut = nullptr, *Gt = nullptr, *rhs = nullptr;
-  double *delta = nullptr, *r = nullptr, *V = nullptr, *Kst[3] = {nullptr, nullptr, nullptr};
-  double *mom_star = nullptr, *Ufs = nullptr;
-  double *fr = nullptr;        // real staging fields
-  double2 *fz = nullptr;       // spectral staging
-  double *part = nullptr;      // reduction partials
-  double *sc = nullptr;        // device scalars
-  double *tot = nullptr;       // totals
-  int* gi = nullptr;           // device ints: Arnoldi index j, Krylov count, iterations done
-  int nblk = 0;
-  cudaGraphExec_t g_pro = nullptr, g_loop = nullptr, g_epi = nullptr;
-  long long n_pro = 0, n_body = 0, n_epi = 0;
-  bool graphs = false;
-};
-
 namespace {
-
-constexpr int RED_SEG = 256;
-// scalar layout (sc)
-constexpr int SC_H = 0;                 // (m+1) x m, m <= 64
-constexpr int SC_G = SC_H + 65 * 64;    // m+1
-constexpr int SC_CS = SC_G + 65;
-constexpr int SC_SN = SC_CS + 64;
-constexpr int SC_Y = SC_SN + 64;
-constexpr int SC_MISC = SC_Y + 64;      // beta, bnorm, done, jdone, tmp...
-enum { M_BETA = 0, M_BNORM, M_DONE, M_JDONE, M_NORM, M_RTOL, M_INF, M_UNORM, M_COEF, M_H, M_INVH,
-       M_NI, M_FIRST, M_GRES };
-constexpr int SC_SIZE = SC_MISC + 16;
 
 // ---------------- reductions ----------------
 // part[blk][i] = sum over the block's segment of V_i . w   (i < nv), V_i = V + i*ld
@@ -109,14 +81,6 @@ __global__ void k_axpy_multi(double* __restrict__ w, int n, const double* __rest
   double s = 0.0;
   for (int i = 0; i < k; ++i) s += coef[i] * V[i * ld + e];
   w[e] += sign * s;
-}
-
-// out = a + s * b (s host scalar)
-__global__ void k_axpby(const double* a, double s, const double* b, double* out, int n,
-                        const double* done) {
-  if (done && done[0] != 0.0) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) out[e] = a[e] + s * b[e];
 }
 
 // out = x / sqrt(*nrm2) ; stores sqrt in *dst
@@ -259,9 +223,15 @@ __global__ void k_field_comb(const double* E1, const double* E3, double* Ec, int
   if (e < n) Ec[e] = -E1[e] / 8.0 + 9.0 * E3[e] / 8.0;
 }
 
-inline unsigned nb(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
-
 }  // namespace
+
+// out = a + s * b (s host scalar)
+__global__ void k_axpby(const double* a, double s, const double* b, double* out, int n,
+                        const double* done) {
+  if (done && done[0] != 0.0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = a[e] + s * b[e];
+}
 
 slar_status macro_alloc(slar_ctx* c) {
   MacroWS* w = new MacroWS();
@@ -294,7 +264,7 @@ slar_status macro_alloc(slar_ctx* c) {
   c->lomac_bs = take(LS_SIZE);
   c->lomac_qv = take(3LL * c->dv * c->g.N[c->dx]);
   c->lomac_C = take((long long)(c->dv + 2) * c->NX);
-  return SLAR_OK;
+  return pc_alloc(c);
 }
 
 void macro_free(slar_ctx* c) {
@@ -302,13 +272,14 @@ void macro_free(slar_ctx* c) {
     if (c->mw->g_pro) cudaGraphExecDestroy(c->mw->g_pro);
     if (c->mw->g_loop) cudaGraphExecDestroy(c->mw->g_loop);
     if (c->mw->g_epi) cudaGraphExecDestroy(c->mw->g_epi);
+    if (c->mw->g_loop_pc) cudaGraphExecDestroy(c->mw->g_loop_pc);
+    if (c->mw->g_epi_pc) cudaGraphExecDestroy(c->mw->g_epi_pc);
     if (c->mw->gi) cudaFree(c->mw->gi);
+    pc_free(c);
   }
   delete c->mw;
   c->mw = nullptr;
 }
-
-namespace {
 
 // out = K(U) (mode_g = 0) or G(U) = U - rhs - coef K(U) (mode_g = 1)
 slar_status eval_residual(slar_ctx* c, const double* U, const double* rhs, double* out, int mode_g) {
@@ -365,10 +336,6 @@ slar_status absmax(slar_ctx* c, const double* x, double* out_dev) {
   return SLAR_OK;
 }
 
-// ---------------- GMRES as CUDA graphs ----------------
-// One Arnoldi iteration reads its index j from device memory, so the same captured body
-// serves every iteration; a WHILE conditional node repeats it until the Givens update sets
-// the convergence flag or j reaches the restart length (always terminates).
 __global__ void k_set_scalars(double* misc, double coef, double h, double n_i, double first) {
   if (threadIdx.x != 0) return;
   misc[M_COEF] = coef;
@@ -376,13 +343,38 @@ __global__ void k_set_scalars(double* misc, double coef, double h, double n_i, d
   misc[M_INVH] = h != 0.0 ? 1.0 / h : 0.0;
   misc[M_NI] = n_i;
   misc[M_FIRST] = first;
+  misc[M_HC] = h;
 }
+
+namespace {
+
+// ---------------- GMRES as CUDA graphs ----------------
+// One Arnoldi iteration reads its index j from device memory, so the same captured body
+// serves every iteration; a WHILE conditional node repeats it until the Givens update sets
+// the convergence flag or j reaches the restart length (always terminates).
 
 __global__ void k_axpby_j(const double* U, const double* misc, const double* V, const int* gi,
                           double* Ut, int n) {
   if (misc[M_DONE] != 0.0) return;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) Ut[e] = U[e] + misc[M_H] * V[(long long)gi[0] * n + e];
+}
+
+// Ut = U + h Z with h from the device scalars (preconditioned Arnoldi direction Z = P B V_j)
+__global__ void k_axpby_h(const double* U, const double* misc, const double* Z, double* Ut, int n) {
+  if (misc[M_DONE] != 0.0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) Ut[e] = U[e] + misc[M_H] * Z[e];
+}
+
+// out = sum_{i < k} y_i V_i with k = gi[2] (the GMRES correction before preconditioning)
+__global__ void k_comb_y(double* out, int n, const double* V, const double* sc, const int* gi) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int k = gi[2];
+  double s = 0.0;
+  for (int i = 0; i < k; ++i) s += sc[SC_Y + i] * V[(long long)i * n + e];
+  out[e] = s;
 }
 
 __global__ void k_diff_j(const double* Gt, const double* G0, const double* misc, const int* gi,
@@ -523,7 +515,7 @@ __global__ void k_rtol(double* misc, double rtol) {
 }
 
 struct SolveStats {
-  int newton = 0, krylov = 0;
+  int newton = 0, krylov = 0, g_evals = 0;
   double residual = 0.0;
   bool converged = false;
 };
@@ -541,13 +533,20 @@ slar_status gmres_pro(slar_ctx* c) {
   return SLAR_OK;
 }
 
-slar_status gmres_body(slar_ctx* c, cudaGraphConditionalHandle h, int use_cond) {
+slar_status gmres_body(slar_ctx* c, cudaGraphConditionalHandle h, int use_cond, bool pc) {
   MacroWS* w = c->mw;
   cudaStream_t s = c->s;
   const int n = w->nvec, m = w->m;
   double* sc = w->sc;
   double* misc = sc + SC_MISC;
-  slar::count_launch(), k_axpby_j<<<nb(n), 256, 0, s>>>(w->U, misc, w->V, w->gi, w->Ut, n);
+  if (pc) {
+    // right preconditioning: the Jacobian acts on Z = P B V_j, with the finite-difference
+    // step h = sqrt(eps) (1 + ||U||) / ||Z|| set on the device by pc_apply_j
+    CKS(pc_apply_j(c));
+    slar::count_launch(), k_axpby_h<<<nb(n), 256, 0, s>>>(w->U, misc, w->Zr, w->Ut, n);
+  } else {
+    slar::count_launch(), k_axpby_j<<<nb(n), 256, 0, s>>>(w->U, misc, w->V, w->gi, w->Ut, n);
+  }
   CKS(eval_residual(c, w->Ut, w->rhs, w->Gt, 1));
   slar::count_launch(), k_diff_j<<<nb(n), 256, 0, s>>>(w->Gt, w->G0, misc, w->gi, w->V, n);
   for (int pass = 0; pass < 2; ++pass) {
@@ -563,28 +562,26 @@ slar_status gmres_body(slar_ctx* c, cudaGraphConditionalHandle h, int use_cond) 
   return SLAR_OK;
 }
 
-slar_status gmres_epi(slar_ctx* c) {
+slar_status gmres_epi(slar_ctx* c, bool pc) {
   MacroWS* w = c->mw;
   cudaStream_t s = c->s;
   slar::count_launch(), k_solve_upper_g<<<1, 32, 0, s>>>(w->sc, w->m, w->gi);
-  slar::count_launch(), k_update_delta<<<nb(w->nvec), 256, 0, s>>>(w->delta, w->nvec, w->V, w->sc, w->gi);
+  if (pc) {
+    // delta += P B (V y)
+    slar::count_launch(), k_comb_y<<<nb(w->nvec), 256, 0, s>>>(w->Zr, w->nvec, w->V, w->sc, w->gi);
+    CK(cudaGetLastError());
+    CKS(pc_apply(c, w->Zr, w->Zr));
+    slar::count_launch(), k_axpby<<<nb(w->nvec), 256, 0, s>>>(w->delta, 1.0, w->Zr, w->delta, w->nvec, nullptr);
+  } else {
+    slar::count_launch(), k_update_delta<<<nb(w->nvec), 256, 0, s>>>(w->delta, w->nvec, w->V, w->sc, w->gi);
+  }
   CK(cudaGetLastError());
   return SLAR_OK;
 }
 
-// capture the three GMRES graphs once per context
-slar_status build_gmres_graphs(slar_ctx* c) {
-  CaptureScope scope(c);
-  MacroWS* w = c->mw;
+// WHILE-loop graph around one Arnoldi iteration (plain or right-preconditioned)
+slar_status capture_loop(slar_ctx* c, bool pc, cudaGraphExec_t* exec) {
   cudaStream_t s = c->s;
-  const long long l0 = launch_count();
-  cudaGraph_t g;
-  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  CKS(gmres_pro(c));
-  CK(cudaStreamEndCapture(s, &g));
-  CK(cudaGraphInstantiate(&w->g_pro, g, 0));
-  CK(cudaGraphDestroy(g));
-  const long long l1 = launch_count();
   cudaGraph_t gl;
   CK(cudaGraphCreate(&gl, 0));
   cudaGraphConditionalHandle h;
@@ -598,28 +595,50 @@ slar_status build_gmres_graphs(slar_ctx* c) {
   CK(cudaGraphAddNode(&cn, gl, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  CKS(gmres_body(c, h, 1));
+  CKS(gmres_body(c, h, 1, pc));
   cudaGraph_t body_out;
   CK(cudaStreamEndCapture(s, &body_out));
-  CK(cudaGraphInstantiate(&w->g_loop, gl, 0));
+  CK(cudaGraphInstantiate(exec, gl, 0));
   CK(cudaGraphDestroy(gl));
-  const long long l2 = launch_count();
+  return SLAR_OK;
+}
+
+slar_status capture_linear(slar_ctx* c, int which, bool pc, cudaGraphExec_t* exec) {
+  cudaStream_t s = c->s;
+  cudaGraph_t g;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  CKS(gmres_epi(c));
+  if (which == 0) CKS(gmres_pro(c));
+  else CKS(gmres_epi(c, pc));
   CK(cudaStreamEndCapture(s, &g));
-  CK(cudaGraphInstantiate(&w->g_epi, g, 0));
+  CK(cudaGraphInstantiate(exec, g, 0));
   CK(cudaGraphDestroy(g));
+  return SLAR_OK;
+}
+
+// capture the GMRES graphs (prologue, Arnoldi loop, epilogue) once per context and variant
+slar_status build_gmres_graphs(slar_ctx* c, bool pc) {
+  CaptureScope scope(c);
+  MacroWS* w = c->mw;
+  if (!w->g_pro) {
+    const long long l0 = launch_count();
+    CKS(capture_linear(c, 0, false, &w->g_pro));
+    w->n_pro = launch_count() - l0;
+    add_launches(-w->n_pro);
+  }
+  const long long l1 = launch_count();
+  CKS(capture_loop(c, pc, pc ? &w->g_loop_pc : &w->g_loop));
+  const long long l2 = launch_count();
+  CKS(capture_linear(c, 1, pc, pc ? &w->g_epi_pc : &w->g_epi));
   const long long l3 = launch_count();
-  w->n_pro = l1 - l0;
-  w->n_body = l2 - l1;
-  w->n_epi = l3 - l2;
-  add_launches(-(l3 - l0));   // captured, not executed
-  w->graphs = true;
+  (pc ? w->n_body_pc : w->n_body) = l2 - l1;
+  (pc ? w->n_epi_pc : w->n_epi) = l3 - l2;
+  add_launches(-(l3 - l1));   // captured, not executed
+  (pc ? w->graphs_pc : w->graphs) = true;
   return SLAR_OK;
 }
 
 // JFNK on G(U) = U - rhs - coef K(U); w->U holds the initial guess and the result.
-slar_status jfnk(slar_ctx* c, double coef, double tol_abs, SolveStats* st) {
+slar_status jfnk(slar_ctx* c, double coef, double tol_abs, SolveStats* st, bool pc) {
   MacroWS* w = c->mw;
   phase(c, PH_NEWTON);
   cudaStream_t s = c->s;
@@ -631,8 +650,9 @@ slar_status jfnk(slar_ctx* c, double coef, double tol_abs, SolveStats* st) {
   slar::count_launch(), k_set_scalars<<<1, 32, 0, s>>>(misc, coef, 0.0, c->n_i, 1.0);
   CK(cudaGetLastError());
   const bool use_graphs = !(c->cfg.flags & SLAR_PROFILE_EVAL);
-  if (use_graphs && !w->graphs) CKS(build_gmres_graphs(c));
+  if (use_graphs && !(pc ? w->graphs_pc : w->graphs)) CKS(build_gmres_graphs(c, pc));
   CKS(eval_residual(c, w->U, w->rhs, w->G0, 1));
+  st->g_evals += 1;
   for (int it = 0;; ++it) {
     CKS(absmax(c, w->G0, misc + M_INF));
     CKS(dot_into(c, w->U, 0, 1, w->U, misc + M_UNORM, 0, nullptr));
@@ -665,23 +685,27 @@ slar_status jfnk(slar_ctx* c, double coef, double tol_abs, SolveStats* st) {
         CKS(eval_residual(c, w->Ut, w->rhs, w->Gt, 1));
         slar::count_launch(), k_lincomb3<<<nb(n), 256, 0, s>>>(w->r, w->Gt, -1.0 / hd, w->G0, 1.0 / hd - 1.0,
                                                               nullptr, 0.0, n);
+        st->g_evals += 1;
       }
       CK(cudaGetLastError());
       slar::count_launch(), k_set_scalars<<<1, 32, 0, s>>>(misc, coef, h, c->n_i, first ? 1.0 : 0.0);
       if (use_graphs) {
         CK(cudaGraphLaunch(w->g_pro, s));
-        CK(cudaGraphLaunch(w->g_loop, s));
-        CK(cudaGraphLaunch(w->g_epi, s));
+        CK(cudaGraphLaunch(pc ? w->g_loop_pc : w->g_loop, s));
+        CK(cudaGraphLaunch(pc ? w->g_epi_pc : w->g_epi, s));
       } else {
         CKS(gmres_pro(c));
-        for (int j = 0; j < w->m; ++j) CKS(gmres_body(c, 0, 0));
-        CKS(gmres_epi(c));
+        for (int j = 0; j < w->m; ++j) CKS(gmres_body(c, 0, 0, pc));
+        CKS(gmres_epi(c, pc));
       }
       CK(cudaMemcpyAsync(c->scal_host, misc, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(c->h_ranks + 12, w->gi, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       const int jd = c->h_ranks[14];
-      if (use_graphs) add_launches(w->n_pro + w->n_epi + (long long)w->n_body * (jd > 0 ? jd : 1));
+      if (use_graphs)
+        add_launches(w->n_pro + (pc ? w->n_epi_pc : w->n_epi) +
+                     (long long)(pc ? w->n_body_pc : w->n_body) * (jd > 0 ? jd : 1));
+      st->g_evals += c->h_ranks[13] - kry;
       kry = c->h_ranks[13];
       const double* ms = c->scal_host;
       const bool conv = ms[M_GRES] <= ms[M_RTOL] * ms[M_BNORM] || jd == 0;
@@ -692,6 +716,7 @@ slar_status jfnk(slar_ctx* c, double coef, double tol_abs, SolveStats* st) {
     slar::count_launch(), k_axpby<<<nb(n), 256, 0, s>>>(w->U, 1.0, w->delta, w->U, n, nullptr);
     CK(cudaGetLastError());
     CKS(eval_residual(c, w->U, w->rhs, w->G0, 1));
+    st->g_evals += 1;
     st->newton += 1;
   }
   return SLAR_OK;
@@ -772,6 +797,66 @@ void dirk3_tableau(double A[3][3], double cst[3]) {
   cst[2] = 1.0;
 }
 
+// The BDF3 solve from U* = U(F*) (in w->Ufs): plain JFNK (the paper), or with the
+// block-circulant preconditioner, optionally warm-started by the attached network; a
+// preconditioned solve that fails is repeated by plain JFNK from U*.
+slar_status solve_bdf(slar_ctx* c, double coef, double tol_abs, slar_stats* st) {
+  MacroWS* w = c->mw;
+  cudaStream_t s = c->s;
+  const int n = w->nvec;
+  double* misc = w->sc + SC_MISC;
+  const bool learned = (c->cfg.flags & SLAR_LEARNED) && c->net;
+  const bool pc = learned || (c->cfg.flags & (SLAR_PRECOND | SLAR_LEARNED));
+  CK(cudaMemcpyAsync(w->U, w->Ufs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  SolveStats ss;
+  if (!pc) {
+    CKS(jfnk(c, coef, tol_abs, &ss, false));
+  } else {
+    phase(c, PH_NEWTON);
+    slar::count_launch(), k_set_scalars<<<1, 32, 0, s>>>(misc, coef, 0.0, c->n_i, 1.0);
+    slar::count_launch(), k_set_misc<<<1, 1, 0, s>>>(misc, M_BLK, learned ? 1.0 : 0.0);
+    CK(cudaGetLastError());
+    if (learned) {
+      // guess U* + s_D d, kept only if its residual is not larger than that of U*
+      CKS(warm_features(c, c->Uc, w->Ufs, w->feat));
+      CKS(warm_guess(c, w->Ufs, w->Ut));
+      CKS(eval_residual(c, w->Ufs, w->rhs, w->G0, 1));
+      CKS(absmax(c, w->G0, w->tot));
+      CKS(eval_residual(c, w->Ut, w->rhs, w->Gt, 1));
+      CKS(absmax(c, w->Gt, w->tot + 1));
+      CK(cudaMemcpyAsync(c->scal_host + 24, w->tot, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      st->g_evals += 2;
+      if (c->scal_host[25] <= c->scal_host[24]) {
+        CK(cudaMemcpyAsync(w->U, w->Ut, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(w->G0, w->Gt, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        st->guess_used = 1;
+      }
+    } else {
+      CKS(eval_residual(c, w->U, w->rhs, w->G0, 1));
+      st->g_evals += 1;
+    }
+    CKS(pc_probe(c, w->U));
+    st->g_evals += c->dv + 2;
+    CKS(jfnk(c, coef, tol_abs, &ss, true));
+    if (!ss.converged) {
+      st->fallback = 1;
+      st->newton += ss.newton;
+      st->krylov += ss.krylov;
+      st->g_evals += ss.g_evals;
+      ss = SolveStats();
+      CK(cudaMemcpyAsync(w->U, w->Ufs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      CKS(jfnk(c, coef, tol_abs, &ss, false));
+    }
+  }
+  st->newton += ss.newton;
+  st->krylov += ss.krylov;
+  st->g_evals += ss.g_evals;
+  st->residual = ss.residual;
+  st->converged = ss.converged ? 1 : 0;
+  return SLAR_OK;
+}
+
 }  // namespace
 
 slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
@@ -818,7 +903,8 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
           slar::count_launch(), k_axpby<<<nb(n), 256, 0, s>>>(w->rhs, dt * A[i][j], w->Kst[j], w->rhs, n, nullptr);
         CK(cudaMemcpyAsync(w->U, w->Ufs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         SolveStats ss;
-        CKS(jfnk(c, dt * A[i][i], tol_abs, &ss));
+        CKS(jfnk(c, dt * A[i][i], tol_abs, &ss, false));
+        st.g_evals += ss.g_evals;
         st.newton += ss.newton;
         st.krylov += ss.krylov;
         st.residual = std::max(st.residual, ss.residual);
@@ -838,13 +924,13 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
       slar::count_launch(), k_lincomb3<<<nb(n), 256, 0, s>>>(w->rhs, c->Uc, 18.0 / 11.0, c->Uh1, -9.0 / 11.0, c->Uh2,
                                        2.0 / 11.0, n);
       CK(cudaGetLastError());
-      CK(cudaMemcpyAsync(w->U, w->Ufs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      SolveStats ss;
-      CKS(jfnk(c, 6.0 / 11.0 * dt, tol_abs, &ss));
-      st.newton = ss.newton;
-      st.krylov = ss.krylov;
-      st.residual = ss.residual;
-      st.converged = ss.converged ? 1 : 0;
+      const double coef = 6.0 / 11.0 * dt;
+      CKS(solve_bdf(c, coef, tol_abs, &st));
+      if (c->rec_dst) {
+        CKS(record_sample(c));
+        st.recorded = 1;
+        c->rec_dst = nullptr;
+      }
     }
     // F^{n+1} = F* - R(U(F*)) + R(U^{n+1}); history shift
     double* t = c->Uh2; c->Uh2 = c->Uh1; c->Uh1 = c->Uc; c->Uc = t;

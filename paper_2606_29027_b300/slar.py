@@ -19,12 +19,16 @@ LIB_PATH = os.path.join(HERE, "libslar.so")
 SLAR_OK, SLAR_EINVAL, SLAR_ENOMEM, SLAR_ECUDA, SLAR_ENOCONV, SLAR_ETIMEOUT, SLAR_ERANK, SLAR_ENAN = range(8)
 SLAR_FP64, SLAR_FP32 = 0, 1
 SLAR_LOMAC, SLAR_FOOT_EULER, SLAR_PROFILE, SLAR_PROFILE_EVAL = 1, 2, 4, 8
+SLAR_PRECOND, SLAR_LEARNED = 16, 32
 
 # every entry point declared in include/slar.h
 EXPORTED = ["slar_create", "slar_destroy", "slar_last_error", "init_ht", "sl_step", "ht_truncate",
             "moments", "lomac_correct", "poisson_field", "ht_eval", "sl_eval", "slar_advect",
             "slar_set_pivot_replay", "ht_export", "ht_import", "slar_get_conserved",
-            "slar_set_conserved", "slar_sizes", "slar_launch_count", "slar_poisson_field_static"]
+            "slar_set_conserved", "slar_sizes", "slar_launch_count", "slar_poisson_field_static",
+            "slar_net_param_count", "slar_sample_floats", "slar_net_create", "slar_net_destroy",
+            "slar_net_set_params", "slar_net_get_params", "slar_net_forward", "slar_net_loss_grad",
+            "slar_net_train_step", "slar_attach_net", "slar_set_record"]
 
 
 class Config(C.Structure):
@@ -40,14 +44,18 @@ class Stats(C.Structure):
                 ("n_slar", C.c_int), ("newton", C.c_int), ("krylov", C.c_int),
                 ("residual", C.c_double), ("converged", C.c_int), ("field_energy", C.c_double),
                 ("totals", C.c_double * 4), ("eval_ms", C.c_double), ("eval_flop", C.c_double),
-                ("launches", C.c_longlong), ("phase_ms", C.c_double * 6)]
+                ("launches", C.c_longlong), ("phase_ms", C.c_double * 6),
+                ("guess_used", C.c_int), ("fallback", C.c_int), ("recorded", C.c_int),
+                ("g_evals", C.c_int)]
 
     def to_dict(self):
         return dict(entries=self.entries, ranks=list(self.ranks), aca_rank=list(self.aca_rank[: self.n_slar]),
                     newton=self.newton, krylov=self.krylov, residual=self.residual,
                     converged=bool(self.converged), field_energy=self.field_energy,
                     totals=list(self.totals), eval_ms=self.eval_ms, eval_flop=self.eval_flop,
-                    launches=self.launches, phase_ms=list(self.phase_ms))
+                    launches=self.launches, phase_ms=list(self.phase_ms),
+                    guess_used=bool(self.guess_used), fallback=bool(self.fallback),
+                    recorded=bool(self.recorded), g_evals=self.g_evals)
 
 
 class HTView(C.Structure):
@@ -90,6 +98,17 @@ def load():
         "slar_sizes": ([P, C.POINTER(I), C.POINTER(I)], I),
         "slar_launch_count": ([C.POINTER(LL)], I),
         "slar_poisson_field_static": ([I, P, P, P, P, P, C.POINTER(D), P], I),
+        "slar_net_param_count": ([I, I, C.POINTER(LL)], I),
+        "slar_sample_floats": ([I, I, I, C.POINTER(LL)], I),
+        "slar_net_create": ([I, I, I, I, I, P, C.POINTER(P)], I),
+        "slar_net_destroy": ([P], I),
+        "slar_net_set_params": ([P, P, LL], I),
+        "slar_net_get_params": ([P, P, LL], I),
+        "slar_net_forward": ([P, P, I, P], I),
+        "slar_net_loss_grad": ([P, P, I, P, I, C.POINTER(D), P], I),
+        "slar_net_train_step": ([P, P, I, P, I, C.c_float, C.POINTER(D)], I),
+        "slar_attach_net": ([P, P], I),
+        "slar_set_record": ([P, P, I, C.c_ulonglong], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -147,7 +166,9 @@ def _dptr(a: np.ndarray):
 def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, eps=1e-6, rank_cap=16,
                 newton_tol=1e-12, krylov_tol=1e-4, krylov_restart=30, newton_max=20, krylov_max=200,
                 precision="fp64", lomac=True, foot="rk3", delta_floor=1e-12, profile=False,
-                profile_eval=False) -> Config:
+                profile_eval=False, solver="plain") -> Config:
+    """solver: "plain" (the paper's JFNK), "precond" (block-circulant preconditioner) or
+    "learned" (network warm start; attach a network with Context.attach_net)."""
     if workload is not None:
         dx, dv, N, lo, hi = workload.dx, workload.dv, workload.N, workload.lo, workload.hi
         eps, rank_cap = workload.eps, workload.rank_cap
@@ -164,7 +185,8 @@ def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, ep
     cfg.krylov_restart, cfg.newton_max, cfg.krylov_max = krylov_restart, newton_max, krylov_max
     cfg.precision = SLAR_FP32 if precision == "fp32" else SLAR_FP64
     cfg.flags = ((SLAR_LOMAC if lomac else 0) | (SLAR_FOOT_EULER if foot == "euler" else 0)
-                 | (SLAR_PROFILE if profile else 0) | (SLAR_PROFILE_EVAL if profile_eval else 0))
+                 | (SLAR_PROFILE if profile else 0) | (SLAR_PROFILE_EVAL if profile_eval else 0)
+                 | {"plain": 0, "precond": SLAR_PRECOND, "learned": SLAR_LEARNED}[solver])
     cfg.delta_floor = delta_floor
     return cfg
 
@@ -260,6 +282,21 @@ class Context:
         arr = np.ascontiguousarray(arr)
         self._check(self.lib.slar_set_pivot_replay(self.h, len(calls), kmax, arr.ctypes.data_as(C.c_void_p)))
 
+    def attach_net(self, net: Optional["Net"]):
+        """Use `net` for the SLAR_LEARNED warm start (None detaches)."""
+        self._net = net
+        self._check(self.lib.slar_attach_net(self.h, net.h if net is not None else None))
+
+    def set_record(self, sample, n_probes: int, seed: int):
+        """Write the training sample of the next BDF3 step into `sample` (torch CUDA float32
+        tensor of sample_floats(dv+2, NX, n_probes) elements; None cancels)."""
+        if sample is not None and (sample.numel() != sample_floats(self.cfg.dv + 2, self.NX, n_probes)
+                                   or sample.dtype.itemsize != 4):
+            raise ValueError("sample buffer has the wrong size or type")
+        self._rec = sample
+        self._check(self.lib.slar_set_record(self.h, C.c_void_p(_ptr(sample)), int(n_probes),
+                                             C.c_ulonglong(seed)))
+
     def get_conserved(self, U_out):
         ni = C.c_double()
         self._check(self.lib.slar_get_conserved(self.h, C.c_void_p(_ptr(U_out)), C.byref(ni)))
@@ -326,3 +363,103 @@ class Context:
             v.has_corr = 1
             v.dC, v.qv = _dptr(dc), _dptr(q)
         self._check(self.lib.ht_import(self.h, C.byref(v)))
+
+
+def net_param_count(m: int, hidden: int = 32) -> int:
+    n = C.c_longlong()
+    st = load().slar_net_param_count(m, hidden, C.byref(n))
+    if st != SLAR_OK:
+        raise SlarError(st, "slar_net_param_count failed")
+    return n.value
+
+
+def sample_floats(m: int, nx: int, n_probes: int) -> int:
+    n = C.c_longlong()
+    st = load().slar_sample_floats(m, nx, n_probes, C.byref(n))
+    if st != SLAR_OK:
+        raise SlarError(st, "slar_sample_floats failed")
+    return n.value
+
+
+class Net:
+    """The warm-start network of the library (see include/slar.h): FP32 parameters,
+    forward, loss gradient and Adam training step run in the library's kernels."""
+
+    def __init__(self, m: int, n0: int, n1: int, hidden: int = 32, max_batch: int = 16, stream=None):
+        import torch
+        self.lib = load()
+        self.m, self.n0, self.n1, self.hidden = m, n0, n1, hidden
+        self.NX = n0 * n1
+        self.max_batch = max_batch
+        self.np = net_param_count(m, hidden)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        st = self.lib.slar_net_create(m, hidden, n0, n1, max_batch, C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st != SLAR_OK:
+            raise SlarError(st, "slar_net_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.slar_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != SLAR_OK:
+            raise SlarError(st, what)
+
+    def set_params(self, theta: np.ndarray):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        if t.size != self.np:
+            raise ValueError(f"expected {self.np} parameters, got {t.size}")
+        self._check(self.lib.slar_net_set_params(self.h, t.ctypes.data_as(C.c_void_p), self.np), "set_params")
+
+    def get_params(self) -> np.ndarray:
+        t = np.zeros(self.np, dtype=np.float32)
+        self._check(self.lib.slar_net_get_params(self.h, t.ctypes.data_as(C.c_void_p), self.np), "get_params")
+        return t
+
+    def forward(self, x, y):
+        """x: float32 CUDA [batch][2m][NX] -> y: float32 CUDA [batch][m+m^2][NX]."""
+        b = x.shape[0]
+        if not (1 <= b <= self.max_batch) or x.numel() != b * 2 * self.m * self.NX or \
+                y.numel() != b * (self.m + self.m * self.m) * self.NX:
+            raise ValueError("bad forward shapes")
+        self._check(self.lib.slar_net_forward(self.h, C.c_void_p(_ptr(x)), x.shape[0], C.c_void_p(_ptr(y))),
+                    "forward")
+
+    def _check_batch(self, samples, n_probes, idx):
+        """The library cannot see buffer sizes: check them here."""
+        L = sample_floats(self.m, self.NX, n_probes)
+        if samples.dim() != 2 or samples.shape[1] != L or samples.dtype.itemsize != 4:
+            raise ValueError(f"samples must be float32 [n, {L}]")
+        if idx.dtype.itemsize != 4 or idx.dim() != 1 or not (1 <= idx.shape[0] <= self.max_batch):
+            raise ValueError("idx must be int32 [batch], 1 <= batch <= max_batch")
+        if int(idx.min()) < 0 or int(idx.max()) >= samples.shape[0]:
+            raise ValueError("sample index out of range")
+
+    def loss_grad(self, samples, n_probes: int, idx, grad=None) -> float:
+        self._check_batch(samples, n_probes, idx)
+        if grad is not None and grad.numel() != self.np:
+            raise ValueError("grad must hold every parameter")
+        L = C.c_double()
+        self._check(self.lib.slar_net_loss_grad(self.h, C.c_void_p(_ptr(samples)), n_probes,
+                                                C.c_void_p(_ptr(idx)), idx.shape[0], C.byref(L),
+                                                C.c_void_p(_ptr(grad))), "loss_grad")
+        return L.value
+
+    def train_step(self, samples, n_probes: int, idx, lr: float, want_loss: bool = False):
+        self._check_batch(samples, n_probes, idx)
+        L = C.c_double()
+        self._check(self.lib.slar_net_train_step(self.h, C.c_void_p(_ptr(samples)), n_probes,
+                                                 C.c_void_p(_ptr(idx)), idx.shape[0], C.c_float(lr),
+                                                 C.byref(L) if want_loss else None), "train_step")
+        return L.value if want_loss else None
