@@ -1,9 +1,12 @@
 """Benchmark: 2D-2V SLAR steps/s and sampled entries/s on the 2D-2V weak Landau workload
 (64 points per dimension, tree ((x1,x2),(v1,v2)), rank cap 32, eps 1e-5, dt 0.2), with the
-implicit LoMaC correction, for the FP32 entry path (headline) and the plain FP64 path.
+implicit LoMaC correction.  Headline: the FP32 entry path with the learned JFNK warm start
+(network trained in the same run, untimed, on samples of seeded weak-Landau runs that the
+solver generates); beside it the plain FP64 path and the plain FP32 path on the same steps,
+with the electric-energy history of each compared with the FP64 path's.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision fp32|fp64] [--workload NAME]
+                    [--precision fp32|fp64] [--solver learned|precond|plain] [--workload NAME]
 
 One JSON line on rank 0.  Multi-GPU runs are independent replicas (the method has no
 data-parallel exchange): value = steps of all ranks / max-over-ranks time.
@@ -40,7 +43,12 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--workload", default="landau_2d2v")
-    p.add_argument("--fp64-steps", type=int, default=4)
+    p.add_argument("--fp64-steps", type=int, default=None,
+                   help="steps of the comparison forms (default: --steps, the same steps as the headline)")
+    p.add_argument("--solver", default="learned", choices=["learned", "precond", "plain"])
+    p.add_argument("--train-runs", type=int, default=8)
+    p.add_argument("--train-steps", type=int, default=40)
+    p.add_argument("--train-iters", type=int, default=1500)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-step", action="store_true",
                    help="profiling configuration: init, 3 steps, then one BDF3 step with every "
@@ -48,12 +56,16 @@ def parse():
     return p.parse_args()
 
 
-def workload_config(w, precision):
+def workload_config(w, precision, solver="plain"):
     return {"workload": f"{w.name}: 2D-2V weak Landau damping, alpha {w.alpha}, k {w.k}, "
                         f"{w.N[0]} pts/dim, x in [0,4pi)^2, v in [-6,6]^2, tree ((x1,x2),(v1,v2)), "
                         f"rank cap {w.rank_cap}, eps {w.eps}, dt {w.dt}, LoMaC with BDF3 (DIRK3 start-up), "
                         f"Newton tol {w.newton_tol}",
             "entries_precision": precision, "rest_precision": "fp64",
+            "newton_krylov": {"plain": "JFNK from U(F*), unpreconditioned GMRES (the paper)",
+                              "precond": "block-circulant right preconditioner",
+                              "learned": "network guess and per-point block on top of the "
+                                         "block-circulant preconditioner; plain JFNK fallback"}[solver],
             "timed_steps": "BDF3 steps after the DIRK3 start-up (in warm-up)",
             "l2": "flushed between timed steps (256 MiB write, outside the step events)",
             "global_batch": 1, "parallelism": "replicas"}
@@ -192,9 +204,38 @@ def run_ours(args, w):
             import torch.distributed as dist
             dist.barrier()
 
-    def make(precision, profile, profile_eval=False):
-        cfg = slar.make_config(w, precision=precision, profile=profile, profile_eval=profile_eval)
-        return slar.Context(cfg, stream=stream)
+    net = None
+    train_info = None
+    if args.solver == "learned":
+        # untimed: samples from seeded weak-Landau runs (alpha ~ U[0.005, 0.05], k ~ U[0.4,
+        # 0.6]; the benchmark run itself, alpha 0.01 and k 0.5, is not among them), then Adam
+        from paper_2606_29027_b300 import warmstart
+        tt0 = time.perf_counter()
+        fam = warmstart.training_family("weak_landau", w.N[0], args.train_runs, seed=7 + rank)
+        with torch.cuda.stream(stream):
+            samples = warmstart.generate_samples(fam, args.train_steps, 4, seed=7 + rank)
+            n0, n1 = warmstart.spatial_shape(w)
+            net = slar.Net(w.dv + 2, n0, n1, max_batch=16, stream=stream)
+            net.set_params(warmstart.init_params(w.dv + 2, 7))
+            L0 = warmstart.mean_loss(net, samples, 4)
+            warmstart.train(net, samples, 4, args.train_iters, 16, 2e-3, seed=1)
+            L1 = warmstart.mean_loss(net, samples, 4)
+        torch.cuda.synchronize()
+        train_info = {"samples": int(samples.shape[0]), "runs": args.train_runs,
+                      "steps_per_run": args.train_steps, "adam_iters": args.train_iters,
+                      "loss_initial": L0, "loss_final": L1,
+                      "seconds": time.perf_counter() - tt0,
+                      "family": "2D2V weak Landau, alpha ~ U[0.005,0.05], k ~ U[0.4,0.6], seed 7"}
+        del samples
+
+    def make(precision, profile, profile_eval=False, solver=None):
+        solver = args.solver if solver is None else solver
+        cfg = slar.make_config(w, precision=precision, profile=profile, profile_eval=profile_eval,
+                               solver=solver)
+        c = slar.Context(cfg, stream=stream)
+        if solver == "learned":
+            c.attach_net(net)
+        return c
 
     def eval_roofline(precision, steps=3):
         # separate pass: events around every evaluator launch (cross approximation launched
@@ -216,8 +257,7 @@ def run_ours(args, w):
     ctx = make(args.precision, True)
     with torch.cuda.stream(stream):
         ctx.init_ht(fac)
-        for _ in range(max(3, args.warmup)):
-            ctx.step(w.dt)
+        warm_stats = [ctx.step(w.dt) for _ in range(max(3, args.warmup))]
     barrier()
     clk = ClockSampler(local)
     clk.start()
@@ -242,27 +282,67 @@ def run_ours(args, w):
     phase_names = ["cross_approx", "truncation", "fields_moments", "lomac_closure", "newton_krylov", "diagnostics"]
     phases = {nm: sum(s.phase_ms[i] for s in stats) / args.steps for i, nm in enumerate(phase_names)}
 
-    # ---- FP64 path at the same workload (fewer steps) ----
-    fp64 = None
-    if args.precision != "fp64" and args.fp64_steps > 0:
-        c64 = make("fp64", True)
+    # ---- the plain FP64 GPU form and the plain FP32 form on the same steps ----
+    def short_run(precision, solver, K, eps=None, cap=None):
+        if eps is None:
+            cc = make(precision, True, solver=solver)
+        else:
+            cfg = slar.make_config(w, precision=precision, profile=True, solver=solver)
+            cfg.eps, cfg.rank_cap = eps, cap
+            cc = slar.Context(cfg, stream=stream)
         with torch.cuda.stream(stream):
-            c64.init_ht(fac)
-            for _ in range(3):
-                c64.step(w.dt)
+            cc.init_ht(fac)
+            warm = [cc.step(w.dt) for _ in range(max(3, args.warmup))]
         barrier()
-        ms64, st64 = time_steps(c64, w, args.fp64_steps, flush, stream)
-        t64 = float(sum(ms64))
-        del c64
+        msk, stk = time_steps(cc, w, K, flush, stream)
+        del cc
+        return msk, warm + stk
+
+    def summary(msk, stk, K):
+        tk = float(sum(msk))
+        return {"value": K / (tk / 1000.0), "unit": UNIT, "ms_per_step": tk / K,
+                "entries_per_s": sum(s.entries for s in stk[-K:]) / (tk / 1000.0),
+                "newton_per_step": float(np.mean([s.newton for s in stk[-K:]])),
+                "krylov_per_step": float(np.mean([s.krylov for s in stk[-K:]])),
+                "g_evals_per_step": float(np.mean([s.g_evals for s in stk[-K:]])),
+                "phase_ms_per_step": {nm: sum(s.phase_ms[i] for s in stk[-K:]) / K
+                                      for i, nm in enumerate(phase_names)}}
+
+    fp64 = None
+    forms = None
+    K = args.steps if args.fp64_steps is None else args.fp64_steps
+    if K > 0:
+        ms64, st64 = short_run("fp64", "plain", K)
+        fp64 = summary(ms64, st64, K)
         em64, ef64, _ = eval_roofline("fp64", 2)
-        t32 = float(sum(ms[: args.fp64_steps]))
-        fp64 = {"value": args.fp64_steps / (t64 / 1000.0), "unit": UNIT,
-                "fp32_value_same_steps": args.fp64_steps / (t32 / 1000.0),
-                "ms_per_step": t64 / args.fp64_steps,
-                "entries_per_s": sum(s.entries for s in st64) / (t64 / 1000.0),
-                "eval_tflops": ef64 / max(em64, 1e-9) / 1e9,
-                "eval_frac_of_fp64_peak": ef64 / max(em64, 1e-9) / 1e9 / FP64_PEAK_TFLOPS,
-                "steps": args.fp64_steps}
+        fp64.update({"eval_tflops": ef64 / max(em64, 1e-9) / 1e9,
+                     "eval_frac_of_fp64_peak": ef64 / max(em64, 1e-9) / 1e9 / FP64_PEAK_TFLOPS,
+                     "steps": K, "form": "plain FP64 GPU path: FP64 entries, unpreconditioned JFNK"})
+        forms = {"steps": K}
+        if not (args.precision == "fp32" and args.solver == "plain"):
+            ms32, st32 = short_run("fp32", "plain", K)
+            forms["fp32_plain"] = summary(ms32, st32, K)
+        Kh = min(K, args.steps)
+        forms["headline"] = summary(ms[:Kh], stats[:Kh], Kh)
+        # accuracy: electric-energy history W(t) of each form against an FP64 run truncated
+        # 100 times more tightly (rank cap 64), on the same steps
+        _, stref = short_run("fp64", "plain", K, eps=w.eps / 100.0, cap=64)
+        Wref = np.array([s.field_energy for s in stref])
+        W64 = np.array([s.field_energy for s in st64])
+        Wh = np.array([s.field_energy for s in (warm_stats + stats)])
+        n = min(len(Wref), len(W64), len(Wh))
+        scale = np.max(np.abs(Wref[:n]))
+        forms["accuracy"] = {
+            "steps_compared": n,
+            "reference": f"FP64 plain, eps {w.eps / 100.0:g}, rank cap 64",
+            "W_err_headline": float(np.max(np.abs(Wh[:n] - Wref[:n])) / scale),
+            "W_err_fp64_plain": float(np.max(np.abs(W64[:n] - Wref[:n])) / scale),
+            "W_diff_headline_vs_fp64": float(np.max(np.abs(Wh[:n] - W64[:n])) / scale),
+            "W_first_step_rel_diff_headline_vs_fp64": float(abs(Wh[0] - W64[0]) / abs(W64[0])),
+            "measure": "max over steps of |W - W_ref| / max |W_ref|",
+            "note": "weak Landau perturbs f by alpha = 0.01, so a truncation error eps ||f|| is "
+                    "eps / alpha relative to the field: the eps-1e-5 method itself is accurate "
+                    "to about 1e-3 in W"}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e_steps = max(3, args.warmup) + min(args.steps, 10)
@@ -293,12 +373,17 @@ def run_ours(args, w):
             "warmup": max(3, args.warmup), "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-            "config": workload_config(w, args.precision),
+            "config": workload_config(w, args.precision, args.solver),
             "entries_per_s": entries / (tot_ms / 1000.0) * world,
             "entries_per_step": entries / args.steps,
             "converged": converged,
             "ranks_last": list(stats[-1].ranks),
             "fp64_path": fp64,
+            "forms": forms,
+            "warm_start_training": train_info,
+            "newton_per_step": float(np.mean([s.newton for s in stats])),
+            "krylov_per_step": float(np.mean([s.krylov for s in stats])),
+            "guess_used_steps": int(sum(s.guess_used for s in stats)),
             "roofline": {"kernel": "k_sl_eval (SL entry evaluator)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
@@ -322,7 +407,14 @@ def run_ours(args, w):
 def profile_step(args, w):
     import torch
     from paper_2606_29027_b300 import inputs, slar
-    ctx = slar.Context(slar.make_config(w, precision=args.precision, profile_eval=True))
+    ctx = slar.Context(slar.make_config(w, precision=args.precision, profile_eval=True, solver=args.solver))
+    if args.solver == "learned":
+        # untrained parameters: the same kernels and launch structure as the trained network
+        from paper_2606_29027_b300 import warmstart
+        n0, n1 = warmstart.spatial_shape(w)
+        net = slar.Net(w.dv + 2, n0, n1, max_batch=1)
+        net.set_params(warmstart.init_params(w.dv + 2, 7))
+        ctx.attach_net(net)
     ctx.init_ht(inputs.initial_factors(w))
     for _ in range(3):
         ctx.step(w.dt)

@@ -13,19 +13,27 @@ HSVD truncation of Supp. B.1.  The reading implemented here (deterministic):
      r = A(i_k, :) - sum_{l<k} u_l[i_k] v_l,   j_k = argmax |r|,  v_k = r / r[j_k],
      u_k = A(:, j_k) - sum_{l<k} v_l[j_k] u_l,  i_{k+1} = argmax_{i not used} |u_k[i]|.
    Start row i_1 = 0 (f > 0 makes every row non-zero).  Stop when
-   ||u_k|| ||v_k|| <= eps ||A_k||_F (running estimate) or k = cap, or when the residual
-   row vanishes.  Arg-max ties: values within a relative 1e-10 of the maximum are
-   treated as equal and the lowest index wins, so that pivots are reproducible across
-   implementations that round differently.
+   ||u_k|| ||v_k|| <= eps ||A_k||_F (running estimate) and the residual sampled on a fixed
+   set of check rows confirms it, or k = cap, or when the residual row vanishes.
+   Check rows: the q = min(8, M1) distinct rows floor(frac(c g) M1), c = 1, 2, ..., with
+   g = (sqrt 5 - 1)/2 (golden-ratio sequence, spread over the spatial grid); their
+   residuals R_c = A(c, :) - sum_l u_l[c] v_l are kept up to date, and the stop is
+   accepted only if (M1 / q) sum_c ||R_c||^2 <= eps^2 ||A_k||_F^2; otherwise the next
+   row pivot is the unused check row of largest residual.  (The rank-1 test alone only
+   sees the pivot row: on weak Landau it stopped at rank 4 with a cross error of 84 eps.)
+   Arg-max ties: values within a relative 1e-10 of the maximum are treated as equal and
+   the lowest index wins, so that pivots are reproducible across implementations that
+   round differently.
 2. The factors A ~ U V^T are embedded exactly as an HT: d = 2: leaves U, V and root I;
    d = 4: identity leaves, B12[a,b,p] = U[(a,b),p], B34[c,e,q] = V[(c,e),q], root I.
 3. HSVD truncation (``ht.truncate``) with eps and the rank cap gives the new HT, whose
    leaf columns 0 are the leading mode singular vectors needed by the LoMaC weight.
 
-The number of sampled entries per call is sum_k (M1 + M2) = k (M1 + M2).
+The number of sampled entries per call is k (M1 + M2) + q M2 (check rows; none in replay).
 """
 from __future__ import annotations
 
+import math
 from typing import Callable, Optional
 
 import numpy as np
@@ -33,6 +41,20 @@ import numpy as np
 from . import ht as htmod
 
 TIE_RTOL = 1e-10
+N_CHECK = 8
+GOLDEN = (math.sqrt(5.0) - 1.0) / 2.0
+
+
+def check_rows(M1: int, q: int = N_CHECK):
+    """The check rows of the stop test: distinct floor(frac(c g) M1), c = 1, 2, ..."""
+    rows = []
+    c = 1
+    while len(rows) < min(q, M1) and c <= 64 * q + M1:
+        i = int(math.floor(math.fmod(c * GOLDEN, 1.0) * M1))
+        if i not in rows:
+            rows.append(i)
+        c += 1
+    return rows
 
 
 def argmax_tie(a: np.ndarray, excluded: Optional[np.ndarray] = None) -> int:
@@ -62,6 +84,9 @@ def aca(row_fn: Callable[[int], np.ndarray], col_fn: Callable[[int], np.ndarray]
     i = 0 if pivots is None else pivots[0][0]
     n_entries = 0
     kmax = min(kmax, M1, M2)
+    chk = check_rows(M1) if pivots is None else []
+    R = np.stack([row_fn(c).astype(np.float64) for c in chk]) if chk else np.zeros((0, M2))
+    n_entries += len(chk) * M2
     for k in range(kmax):
         if pivots is not None:
             if k >= len(pivots):
@@ -99,8 +124,17 @@ def aca(row_fn: Callable[[int], np.ndarray], col_fn: Callable[[int], np.ndarray]
         I.append(i)
         J.append(j)
         if pivots is None:
+            for q, c in enumerate(chk):
+                R[q] = R[q] - u[c] * v
             if nu * nv <= eps * np.sqrt(max(normA2, 0.0)):
-                break
+                n2 = np.array([float(R[q] @ R[q]) for q in range(len(chk))])
+                if M1 / len(chk) * float(np.sum(n2)) <= eps * eps * normA2:
+                    break
+                free = [q for q in range(len(chk)) if not used_r[chk[q]]]
+                if not free:
+                    break
+                i = chk[max(free, key=lambda q: (n2[q], -q))]
+                continue
             i = argmax_tie(u, used_r)
     k = len(Us)
     U = np.stack(Us, axis=1) if k else np.zeros((M1, 0))

@@ -4,7 +4,10 @@
 //
 // Reading of the paper (which defers HTACA to earlier work): partially pivoted ACA on the
 // root split, start row 0, stop when ||u_k|| ||v_k|| <= eps ||A_k||_F (running estimate)
-// or k = cap; arg-max ties within a relative 1e-10 go to the lowest index.
+// and the residual on q = min(8, M1) fixed check rows (golden-ratio sequence
+// floor(frac(c g) M1)) confirms it, (M1/q) sum_c ||R_c||^2 <= eps^2 ||A_k||_F^2, or k = cap;
+// when the check fails the next row pivot is the unused check row of largest residual.
+// Arg-max ties within a relative 1e-10 go to the lowest index.
 //
 // Every step runs on the device with no host round trip: the entry evaluator samples the
 // residual row (fused residual epilogue), one CTA picks the column pivot and scales v_k,
@@ -123,15 +126,45 @@ k_aca_dots(const double* __restrict__ Ua, int M1, const double* __restrict__ Va,
   }
 }
 
-// norm estimate, stop test, next row pivot
+// check-row residuals R_c -= u_k[row_c] v_k and their squared norms (one CTA per row)
+__global__ void __launch_bounds__(256)
+k_aca_check(const double* __restrict__ Ua, int M1, const double* __restrict__ Va, int M2,
+            const int* __restrict__ rows, double* __restrict__ R, double* __restrict__ n2,
+            const AcaState* st) {
+  __shared__ double red[8];
+  if (st->done || st->replay) return;
+  const int kk = st->k;
+  const int c = blockIdx.x;
+  const double a = Ua[(long long)kk * M1 + rows[c]];
+  const double* v = Va + (long long)kk * M2;
+  double* r = R + (long long)c * M2;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < M2; e += 256) {
+    const double t = r[e] - a * v[e];
+    r[e] = t;
+    s += t * t;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    n2[c] = t;
+  }
+}
+
+// norm estimate, stop test (confirmed on the check rows), next row pivot
 __global__ void __launch_bounds__(PIV_THREADS)
 k_aca_finalize(const double* __restrict__ Ua, int M1, int kmax, int nbu, int nbv,
                const double* __restrict__ part, int ldp, AcaState* st, int* pivI,
-               unsigned char* usedr, cudaGraphConditionalHandle loop, int use_cond) {
+               unsigned char* usedr, int n_chk, const int* __restrict__ chk_rows,
+               const double* __restrict__ chk_n2, cudaGraphConditionalHandle loop, int use_cond) {
   __shared__ double du[SLAR_MAX_RANK + 1], dv[SLAR_MAX_RANK + 1];
   __shared__ int i_s;
   __shared__ double top_s;
   __shared__ int stop_s;
+  __shared__ int next_s;
   const int tid = threadIdx.x;
   if (st->done) {
     if (tid == 0) if (use_cond) cudaGraphSetConditional(loop, 0);
@@ -157,13 +190,41 @@ k_aca_finalize(const double* __restrict__ Ua, int M1, int kmax, int nbu, int nbv
     st->normA2 = n2;
     st->k = kk + 1;
     int stop = 0;
-    if (kk + 1 >= kmax) stop = 1;
-    else if (!replay && sqrt(nu2) * sqrt(nv2) <= eps * sqrt(fmax(n2, 0.0))) stop = 1;
-    else if (replay && pivI[kk + 1] < 0) stop = 1;
+    int next = -1;
+    if (kk + 1 >= kmax) {
+      stop = 1;
+    } else if (!replay && sqrt(nu2) * sqrt(nv2) <= eps * sqrt(fmax(n2, 0.0))) {
+      stop = 1;
+      if (n_chk > 0) {
+        double sum = 0.0;
+        for (int q = 0; q < n_chk; ++q) sum += chk_n2[q];
+        if ((double)M1 / n_chk * sum > eps * eps * n2) {
+          // the residual elsewhere is too large: continue from the worst unused check row
+          int best = -1;
+          for (int q = 0; q < n_chk; ++q)
+            if (!usedr[chk_rows[q]] && (best < 0 || chk_n2[q] > chk_n2[best])) best = q;
+          if (best >= 0) {
+            stop = 0;
+            next = chk_rows[best];
+          }
+        }
+      }
+    } else if (replay && pivI[kk + 1] < 0) {
+      stop = 1;
+    }
     if (stop) st->done = 1;
     stop_s = stop;
+    next_s = next;
   }
   __syncthreads();
+  if (!stop_s && next_s >= 0) {
+    if (tid == 0) {
+      pivI[kk + 1] = next_s;
+      usedr[next_s] = 1;
+      if (use_cond) cudaGraphSetConditional(loop, 1);
+    }
+    return;
+  }
   if (stop_s) {
     if (tid == 0) if (use_cond) cudaGraphSetConditional(loop, 0);
     return;
@@ -236,9 +297,13 @@ slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int
     if (pass == 0)
       slar::count_launch(), k_aca_row_pivot<<<1, PIV_THREADS, 0, s>>>(c->rowbuf, M2, c->usedc, c->pivJ, c->ast, c->Va);
   }
+  if (c->n_chk > 0)
+    slar::count_launch(), k_aca_check<<<c->n_chk, 256, 0, s>>>(c->Ua, M1, c->Va, M2, c->chk_rows, c->chk_R,
+                                                               c->chk_n2, c->ast);
   slar::count_launch(), k_aca_dots<<<nbu + nbv, 256, 0, s>>>(c->Ua, M1, c->Va, M2, nbu, c->ast, c->aca_part, ldp);
   slar::count_launch(), k_aca_finalize<<<1, PIV_THREADS, 0, s>>>(c->Ua, M1, c->kmax, nbu, nbv, c->aca_part, ldp,
-                                                                c->ast, c->pivI, c->usedr, h, use_cond);
+                                                                c->ast, c->pivI, c->usedr, c->n_chk, c->chk_rows,
+                                                                c->chk_n2, h, use_cond);
   CK(cudaGetLastError());
   return SLAR_OK;
 }
@@ -328,6 +393,20 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
   if (!prof && (!c->aca_graph || need > c->aca_graph_smem)) CKS(build_aca_graph(c, need));
   slar::count_launch(), k_aca_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->usedr, replay ? 1 : 0, c->cfg.eps);
   CK(cudaGetLastError());
+  long long chk_entries = 0;
+  if (!replay && c->n_chk > 0) {
+    // residuals of the check rows start as the rows themselves
+    EvalArgs a{};
+    a.mode = EVAL_TUPLES;
+    a.n = (long long)c->n_chk * M2;
+    a.idx = c->chk_idx;
+    a.out = c->chk_R;
+    a.tau = tau;
+    a.E = E;
+    a.foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
+    CKS(eval_entries(c, in, with_corr, a, 0));
+    chk_entries = a.n;
+  }
   if (prof) {
     // individually launched steps with events around the evaluator (roofline timing)
     for (int kk = 0; kk < kmax; ++kk) CKS(aca_step(c, need, 0, 0, true));
@@ -339,7 +418,7 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
   const int k = c->ast_host->k;
   if (!prof) add_launches(c->aca_graph_nodes * (long long)(k + c->ast_host->stop_row));
   if (aca_rank) *aca_rank = k;
-  const long long nent = (long long)k * (M1 + M2) + (c->ast_host->stop_row ? M2 : 0);
+  const long long nent = (long long)k * (M1 + M2) + (c->ast_host->stop_row ? M2 : 0) + chk_entries;
   if (entries) *entries = nent;
   c->prof_flop += (double)nent * entry_flops(c, in);
   if (k == 0) return set_error(c, SLAR_ENAN, "cross approximation found no pivot (zero tensor)");

@@ -84,6 +84,7 @@ void free_ctx(slar_ctx* c) {
   F(c->dC); F(c->qv); F(c->Uc); F(c->Uh1); F(c->Uh2);
   F(c->Ua); F(c->Va); F(c->rowbuf); F(c->usedr); F(c->usedc); F(c->pivI); F(c->pivJ);
   F(c->ast); F(c->aca_part); F(c->aca_dots);
+  F(c->chk_rows); F(c->chk_idx); F(c->chk_R); F(c->chk_n2);
   if (c->ast_host) cudaFreeHost(c->ast_host);
   if (c->evp) cudaFree(c->evp);
   if (c->evp_host) cudaFreeHost(c->evp_host);
@@ -184,6 +185,21 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   A(c->ast, 1);
   const int nbu = (c->M1 + 255) / 256, nbv = (c->M2 + 255) / 256;
   A(c->aca_part, (size_t)(nbu + nbv) * (R + 1));
+  // check rows of the cross-approximation stop test: distinct floor(frac(c g) M1),
+  // g = (sqrt 5 - 1)/2, c = 1, 2, ...; at most 8
+  std::vector<int> rows;
+  {
+    const double gold = (std::sqrt(5.0) - 1.0) / 2.0;
+    for (int q = 1; (int)rows.size() < std::min(8, c->M1) && q <= 64 * 8 + c->M1; ++q) {
+      const int i = (int)std::floor(std::fmod(q * gold, 1.0) * c->M1);
+      if (std::find(rows.begin(), rows.end(), i) == rows.end()) rows.push_back(i);
+    }
+  }
+  c->n_chk = (int)rows.size();
+  A(c->chk_rows, (size_t)c->n_chk);
+  A(c->chk_idx, (size_t)c->n_chk * c->M2 * d);
+  A(c->chk_R, (size_t)c->n_chk * c->M2);
+  A(c->chk_n2, (size_t)c->n_chk);
   A(c->T1, (size_t)capB); A(c->T2, (size_t)capB); A(c->T3, (size_t)capB);
   A(c->Q12, (size_t)capB); A(c->Q34, (size_t)capB);
   A(c->Rn[0], (size_t)R * R); A(c->Rn[1], (size_t)R * R);
@@ -221,6 +237,22 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
     return SLAR_ENOMEM;
   }
   if (sl_eval_init_attrs() != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
+  {
+    // index tuples of the check rows: row i (spatial multi-index) x every velocity column
+    std::vector<int> tup((size_t)c->n_chk * c->M2 * d);
+    for (int q = 0; q < c->n_chk; ++q)
+      for (int j = 0; j < c->M2; ++j) {
+        int* t = tup.data() + ((size_t)q * c->M2 + j) * d;
+        const int i = rows[q];
+        if (d == 2) { t[0] = i; t[1] = j; }
+        else { t[0] = i / g.N[1]; t[1] = i % g.N[1]; t[2] = j / g.N[3]; t[3] = j % g.N[3]; }
+      }
+    if (cudaMemcpy(c->chk_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->chk_idx, tup.data(), sizeof(int) * tup.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_ctx(c);
+      return SLAR_ECUDA;
+    }
+  }
   if (cudaStreamCreateWithFlags(&c->cap_s, cudaStreamNonBlocking) != cudaSuccess) {
     free_ctx(c);
     return SLAR_ECUDA;

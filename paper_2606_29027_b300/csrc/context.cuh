@@ -95,6 +95,12 @@ struct slar_ctx {
   size_t aca_graph_smem = 0;
   long long aca_graph_nodes = 0;
   int replay_calls = 0, replay_kmax = 0, replay_pos = 0;
+  // check rows of the cross-approximation stop test
+  int n_chk = 0;
+  int* chk_rows = nullptr;     // [n_chk]
+  int* chk_idx = nullptr;      // [n_chk * M2][d] index tuples of the check rows
+  double* chk_R = nullptr;     // [n_chk][M2] residual rows
+  double* chk_n2 = nullptr;    // [n_chk] their squared norms
 
   // truncation workspaces
   double* Qleaf[4] = {nullptr, nullptr, nullptr, nullptr};

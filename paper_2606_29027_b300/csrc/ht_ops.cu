@@ -269,6 +269,7 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
     jobs[nj].V = c->S[t];
     jobs[nj].work = c->ework[t];
     jobs[nj].n = node_n[t];
+    jobs[nj].floor_rel = c->cfg.precision == SLAR_FP32 ? 1e-13 : 1e-17;
     ++nj;
   }
   CK(eig_batched(jobs, nj, c->d_eig, s));

@@ -278,9 +278,11 @@ constexpr int EIG_THREADS = 512;
 // disjoint rotations at once as 2x2 block updates A <- J^T A J, V <- V J.  A pair is
 // rotated while |a_pq| > tol sqrt(|a_pp a_qq|) (relative criterion: small eigenvalues and
 // their eigenvectors are resolved to relative accuracy); stop after a sweep without any
-// rotation, or after 40 sweeps.
+// rotation, or after 40 sweeps.  Entries below floor_rel ||A||_F are never rotated: 1e-17 for
+// Gram matrices of FP64 data (the rounding level), 1e-13 for those of FP32 entries, whose
+// noise puts a cluster of eigenvalues near 1e-14 ||A|| that the truncation discards anyway.
 __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, double* cc,
-                              double* ss, int* rotated) {
+                              double* ss, int* rotated, double floor_rel) {
   const int tid = threadIdx.x;
   const int half = ne / 2;
   const int m = ne - 1;
@@ -288,7 +290,7 @@ __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, d
   __shared__ unsigned short tri[(SLAR_MAX_N / 2) * (SLAR_MAX_N / 2 + 1) / 2];
   __shared__ double fro_red[EIG_THREADS / 32];
   __shared__ double floor_s;
-  // absolute floor: entries at the rounding level of the matrix are not rotated
+  // absolute floor: entries at the rounding (or data-noise) level of the matrix are not rotated
   {
     double f = 0.0;
     for (int it = tid; it < ne * ne; it += EIG_THREADS) f += sA[it] * sA[it];
@@ -298,7 +300,7 @@ __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, d
     if (tid == 0) {
       double t = 0.0;
       for (int w = 0; w < EIG_THREADS / 32; ++w) t += fro_red[w];
-      floor_s = 1e-17 * sqrt(t);
+      floor_s = floor_rel * sqrt(t);
     }
     __syncthreads();
   }
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs) {
         Vs[it] = (a == b) ? 1.0 : 0.0;
       }
       __syncthreads();
-      jacobi_sweeps(M, ne, Vs, pp, qq, cc, ss, &rotated);
+      jacobi_sweeps(M, ne, Vs, pp, qq, cc, ss, &rotated, job.floor_rel);
       // eigenvalue order of M (descending, ties by index)
       __shared__ int order[EIG_RTMAX];
       for (int i = tid; i < rt; i += EIG_THREADS) {
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs) {
       V[it] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
-    jacobi_sweeps(sA, ne, V, pp, qq, cc, ss, &rotated);
+    jacobi_sweeps(sA, ne, V, pp, qq, cc, ss, &rotated, job.floor_rel);
     sort_write(sA, ne, n, V, ne, job.W, job.V);
     return;
   }
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs) {
     V[it] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  jacobi_sweeps(sA, ne, V, pp, qq, cc, ss, &rotated);
+  jacobi_sweeps(sA, ne, V, pp, qq, cc, ss, &rotated, job.floor_rel);
   sort_write(sA, ne, n, V, ne, job.W, job.V);
 }
 

@@ -80,7 +80,7 @@ def test_cross_exact_recovery_of_low_rank(N, ranks):
     assert np.linalg.norm(_dense(out) - F) <= 1e-10 * np.linalg.norm(F)
     M1 = int(np.prod(N[: len(N) // 2]))
     M2 = int(np.prod(N[len(N) // 2:]))
-    assert info["entries"] == info["aca_rank"] * (M1 + M2)
+    assert info["entries"] == info["aca_rank"] * (M1 + M2) + len(cross.check_rows(M1)) * M2
     # root-split rank of the data is the ACA rank bound
     rr = np.linalg.matrix_rank(F.reshape(M1, M2), tol=1e-9 * np.abs(F).max())
     assert info["aca_rank"] <= rr + 1
@@ -132,3 +132,28 @@ def test_htaca_of_sl_update_close_to_truncated_dense():
     out = cross.htaca(lambda idx: sl.sl_eval(F0, E, 0.4, idx, g), N, eps, 40)
     dense = sl.dense_sl_step(htmod.densify(F0), E, 0.4, g)
     assert np.linalg.norm(_dense(out) - dense) <= 10 * eps * np.linalg.norm(dense)
+
+
+def test_cross_stop_rule_catches_missed_structure():
+    """First SLAR call of 2D2V weak Landau at 32^4 (eps 1e-5): the cross approximation of
+    the SL-updated tensor is within eps of the dense SL update.  The rank-1 stop test alone
+    stopped this call at rank 4 with an error of about 84 eps."""
+    from oracle import sl, stepper
+    w = inputs.landau_2d2v(n=32, cap=32)
+    g = sl.PhaseGrid(w.dx, w.dv, w.N, w.lo, w.hi)
+    prm = stepper.Params(eps=1e-5, cap=w.rank_cap, lomac=False)
+    st = stepper.init_state(inputs.initial_factors(w), g, prm)
+    E = stepper.field_of(st.F, g, st.n_i)
+    ref = sl.dense_sl_step(htmod.densify(st.F), E, w.dt / 3, g)
+    G, info = stepper.slar(st.F, E, w.dt / 3, g, prm)
+    err = np.linalg.norm(htmod.densify(G) - ref) / np.linalg.norm(ref)
+    assert err <= 1e-5, (info["aca_rank"], err)
+
+
+def test_check_rows_are_distinct_and_spread():
+    for M1 in (1, 5, 64, 4096):
+        rows = cross.check_rows(M1)
+        assert len(rows) == min(8, M1) == len(set(rows))
+        assert all(0 <= r < M1 for r in rows)
+    r = sorted(cross.check_rows(4096))
+    assert max(np.diff([0] + r + [4096])) < 4096 / 3
