@@ -60,12 +60,16 @@ enum {
                               component, its (dv+2) x (dv+2) Fourier-mode blocks are inverted
                               and applied mode by mode (an addition to the paper, whose JFNK is
                               unpreconditioned; the Newton stop test is unchanged) */
-    SLAR_LEARNED = 32      /* warm start of the BDF3 solves from the network attached with
+    SLAR_LEARNED = 32,     /* warm start of the BDF3 solves from the network attached with
                               slar_attach_net: initial guess U* + s_D d(x) (kept only if its
                               residual is not larger than that of U(F*)) and a per-point block
                               B(x) = I + b(x) applied before the block-circulant
                               preconditioner; if the solve does not converge it is repeated by
                               plain JFNK from U(F*).  Implies SLAR_PRECOND. */
+    SLAR_NO_AUTOTUNE = 64, /* keep the entry evaluator at 32 entries per CTA instead of the
+                              autotuned tile (results then do not depend on timings) */
+    SLAR_OWN_STREAM = 128  /* the context creates (and destroys) a private non-blocking stream
+                              and ignores the stream argument of slar_create; see slar_stream */
 };
 
 typedef struct slar_config {
@@ -103,6 +107,7 @@ typedef struct slar_stats {
     int fallback;           /* the preconditioned solve failed and plain JFNK was run */
     int recorded;           /* a training sample was written (slar_set_record) */
     int g_evals;            /* residual evaluations G(U) of the Newton-Krylov solves */
+    int eval_tile;          /* entries per CTA of the entry evaluator (autotuned: 16, 32, 64) */
 } slar_stats;
 
 /* Host-side view of an HT state for import/export.  Layouts (row-major):
@@ -145,6 +150,12 @@ const char* slar_last_error(const slar_ctx* ctx);
  * density is set to mean(M0(F^0)) and U^0 = U(F^0).  Resets the step counter.
  * Errors: SLAR_EINVAL (n_terms < 1 or > rank limit). */
 slar_status init_ht(slar_ctx* ctx, int n_terms, const double* factors);
+
+/* Autotuning (an addition to the paper): the first SLAR call that meets a new (tree,
+ * precision, grid, rank bucket 8/16/32/64) times the entry evaluator with 16, 32 and 64
+ * entries per CTA on that call's check-row evaluation and keeps the fastest for the
+ * process; SLAR_NO_AUTOTUNE disables it.  The tile changes the summation order of the root
+ * contraction only (results agree to rounding). */
 
 /* One full time step of size dt (flowchart of Sec. 3.2.3): SLAR_VP by the third-order
  * RK exponential integrator (Eq. slarvp; three frozen-field SLAR calls), then, with
@@ -296,8 +307,26 @@ slar_status slar_attach_net(slar_ctx* ctx, slar_net* net);
 slar_status slar_set_record(slar_ctx* ctx, float* sample_dev, int n_probes,
                             unsigned long long seed);
 
+/* Measured FMA throughput of the current GPU in TFLOP/s (2 flops per FMA): a kernel of
+ * eight independent FMA chains per thread, iters x 128 FMAs each, 8 CTAs of 256 threads per
+ * SM, in double (fp64 = 1) or float (fp64 = 0), timed with CUDA events on `stream`
+ * (cudaStream_t; synchronised).  The ALU denominators of the entry evaluator's roofline.
+ * Errors: SLAR_EINVAL (iters outside [1, 2^24]), SLAR_ECUDA. */
+slar_status slar_fma_peak(int fp64, int iters, double* tflops, void* stream);
+
+/* Ensemble step: advance n independent contexts (uneven grids, ranks and tolerances
+ * allowed) by one step each, dts[i] for context i, concurrently.  Each context's work stays
+ * on its own stream, so the contexts must have pairwise distinct streams; up to `threads`
+ * host threads drive them (a context is only ever touched by one thread).  stats: host
+ * array of n or NULL.  Returns SLAR_OK, or after every context has finished its step the
+ * status of the first context (in index order) that failed. */
+slar_status slar_ensemble_step(slar_ctx** ctxs, int n, const double* dts, int threads, slar_stats* stats);
+
 /* Total number of kernels launched by this library in this process (all contexts). */
 slar_status slar_launch_count(long long* out);
+
+/* The stream the context works on (the caller's, or its own with SLAR_OWN_STREAM). */
+slar_status slar_stream(const slar_ctx* ctx, void** stream);
 
 /* Number of moments returned by `moments` and the spatial size NX. */
 slar_status slar_sizes(const slar_ctx* ctx, int* n_mom, int* nx);

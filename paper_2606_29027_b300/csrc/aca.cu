@@ -15,6 +15,10 @@
 // of the norm estimate, and one CTA updates the estimate, tests the stop rule and picks the
 // next row pivot.  A device flag makes the remaining launches of a stopped approximation
 // exit immediately; the host reads the final rank once.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "context.cuh"
 
 namespace slar {
@@ -287,8 +291,10 @@ slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int
     const EvalArgs& a = pass == 0 ? ar : ac;
     const bool ev = prof && c->prof_n * 2 + 1 < kProfEvents;
     if (ev) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], s));
-    cudaError_t e = f32 ? launch_sl_eval_dev<float>(c->g, static_cast<const EvalParams<float>*>(c->evp), a, smem, s)
-                        : launch_sl_eval_dev<double>(c->g, static_cast<const EvalParams<double>*>(c->evp), a, smem, s);
+    cudaError_t e = f32 ? launch_sl_eval_dev<float>(c->g, static_cast<const EvalParams<float>*>(c->evp), a, smem, s,
+                                                    c->eval_tile)
+                        : launch_sl_eval_dev<double>(c->g, static_cast<const EvalParams<double>*>(c->evp), a, smem, s,
+                                                     c->eval_tile);
     CK(e);
     if (ev) {
       CK(cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], s));
@@ -341,7 +347,81 @@ slar_status build_aca_graph(slar_ctx* c, size_t smem) {
   c->aca_graph_nodes = l1 - l0;
   add_launches(-(l1 - l0));
   c->aca_graph_smem = smem;
+  c->aca_graph_tile = c->eval_tile;
   return SLAR_OK;
+}
+
+namespace {
+
+// Autotuner of the entry evaluator's tile (entries per CTA): per (tree, precision, grid,
+// rank bucket) the candidates 16, 32, 64 are timed on the check-row evaluation of the
+// first SLAR call that meets the key (two launches each, CUDA events); the fastest is kept
+// for the process.
+using TuneKey = std::tuple<int, int, int, int, int, int, int>;
+std::map<TuneKey, int> g_tile_cache;
+std::mutex g_tile_mutex;
+
+int rank_bucket(const int* r6, int d) {
+  int mx = 1;
+  for (int i = 0; i < (d == 4 ? 6 : 2); ++i) mx = std::max(mx, r6[i]);
+  int b = 8;
+  while (b < mx) b *= 2;
+  return b;
+}
+
+TuneKey tune_key(const slar_ctx* c, const int* r6) {
+  return TuneKey(c->d, c->cfg.precision, c->g.N[0], c->g.N[1], c->g.N[2], c->g.N[3], rank_bucket(r6, c->d));
+}
+
+}  // namespace
+
+// Evaluate the check rows of a SLAR call into c->chk_R (and, the first time a tuning key is
+// met, choose the evaluator tile on this work).
+slar_status eval_check_rows(slar_ctx* c, int in, bool with_corr, double tau, const double* E) {
+  EvalArgs a{};
+  a.mode = EVAL_TUPLES;
+  a.n = (long long)c->n_chk * c->M2;
+  a.idx = c->chk_idx;
+  a.out = c->chk_R;
+  a.tau = tau;
+  a.E = E;
+  a.foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
+  if (c->cfg.flags & SLAR_NO_AUTOTUNE) {
+    c->eval_tile = 32;
+    return eval_entries(c, in, with_corr, a, 0);
+  }
+  const TuneKey key = tune_key(c, c->ht[in].r);
+  int tile = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_tile_mutex);
+    auto it = g_tile_cache.find(key);
+    if (it != g_tile_cache.end()) tile = it->second;
+  }
+  if (tile) {
+    c->eval_tile = tile;
+    return eval_entries(c, in, with_corr, a, 0);
+  }
+  const int cand[3] = {16, 32, 64};
+  float best_ms = 1e30f;
+  int best = 32;
+  for (int q = 0; q < 3; ++q) {
+    c->eval_tile = cand[q];
+    CKS(eval_entries(c, in, with_corr, a, 0));   // warm-up (and the values, if last)
+    CK(cudaEventRecord(c->tune_ev[0], c->s));
+    CKS(eval_entries(c, in, with_corr, a, 0));
+    CKS(eval_entries(c, in, with_corr, a, 0));
+    CK(cudaEventRecord(c->tune_ev[1], c->s));
+    CK(cudaEventSynchronize(c->tune_ev[1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]));
+    if (ms < best_ms) { best_ms = ms; best = cand[q]; }
+  }
+  c->eval_tile = best;
+  {
+    std::lock_guard<std::mutex> lock(g_tile_mutex);
+    g_tile_cache[key] = best;
+  }
+  return eval_entries(c, in, with_corr, a, 0);
 }
 
 slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const double* E, int out,
@@ -388,28 +468,27 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
     P->foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
   }
   CK(cudaMemcpyAsync(c->evp, c->evp_host, sizeof(EvalParams<double>), cudaMemcpyHostToDevice, s));
-  const size_t need = f32 ? sl_eval_smem<float>(c->g, hin.r) : sl_eval_smem<double>(c->g, hin.r);
-  const bool prof = (c->cfg.flags & SLAR_PROFILE_EVAL) != 0;
-  if (!prof && (!c->aca_graph || need > c->aca_graph_smem)) CKS(build_aca_graph(c, need));
-  slar::count_launch(), k_aca_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->usedr, replay ? 1 : 0, c->cfg.eps);
-  CK(cudaGetLastError());
   long long chk_entries = 0;
   if (!replay && c->n_chk > 0) {
-    // residuals of the check rows start as the rows themselves
-    EvalArgs a{};
-    a.mode = EVAL_TUPLES;
-    a.n = (long long)c->n_chk * M2;
-    a.idx = c->chk_idx;
-    a.out = c->chk_R;
-    a.tau = tau;
-    a.E = E;
-    a.foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
-    CKS(eval_entries(c, in, with_corr, a, 0));
-    chk_entries = a.n;
+    // residuals of the check rows start as the rows themselves (this also fixes the tile)
+    CKS(eval_check_rows(c, in, with_corr, tau, E));
+    chk_entries = (long long)c->n_chk * M2;
   }
+  const size_t need = f32 ? sl_eval_smem<float>(c->g, hin.r, c->eval_tile)
+                          : sl_eval_smem<double>(c->g, hin.r, c->eval_tile);
+  const bool prof = (c->cfg.flags & SLAR_PROFILE_EVAL) != 0;
+  if (!prof && (!c->aca_graph || need > c->aca_graph_smem || c->aca_graph_tile != c->eval_tile))
+    CKS(build_aca_graph(c, need));
+  slar::count_launch(), k_aca_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->usedr, replay ? 1 : 0, c->cfg.eps);
+  CK(cudaGetLastError());
   if (prof) {
     // individually launched steps with events around the evaluator (roofline timing)
-    for (int kk = 0; kk < kmax; ++kk) CKS(aca_step(c, need, 0, 0, true));
+    for (int kk = 0; kk < kmax; ++kk) {
+      CK(cudaMemcpyAsync(c->ast_host, c->ast, sizeof(AcaState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (c->ast_host->done) break;   // where the WHILE node would stop
+      CKS(aca_step(c, need, 0, 0, true));
+    }
   } else {
     CK(cudaGraphLaunch(c->aca_graph, s));
   }

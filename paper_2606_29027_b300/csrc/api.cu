@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "context.cuh"
@@ -63,7 +64,8 @@ slar_status validate(const slar_config* cfg, char* msg, size_t len) {
   if (cfg->precision != SLAR_FP64 && cfg->precision != SLAR_FP32) {
     snprintf(msg, len, "unknown precision"); return SLAR_EINVAL;
   }
-  if (cfg->flags & ~(SLAR_LOMAC | SLAR_FOOT_EULER | SLAR_PROFILE | SLAR_PROFILE_EVAL | SLAR_PRECOND | SLAR_LEARNED)) {
+  if (cfg->flags & ~(SLAR_LOMAC | SLAR_FOOT_EULER | SLAR_PROFILE | SLAR_PROFILE_EVAL | SLAR_PRECOND | SLAR_LEARNED |
+                     SLAR_NO_AUTOTUNE | SLAR_OWN_STREAM)) {
     snprintf(msg, len, "unknown flag bits"); return SLAR_EINVAL;
   }
   if (cfg->krylov_restart < 1 || cfg->krylov_restart > 64) {
@@ -100,9 +102,12 @@ void free_ctx(slar_ctx* c) {
   F(c->macro_ws); F(c->scal);
   if (c->spectral) { c->spectral->release(); delete c->spectral; }
   if (c->cap_s) cudaStreamDestroy(c->cap_s);
+  if (c->own_s) { cudaStreamSynchronize(c->own_s); cudaStreamDestroy(c->own_s); }
   macro_free(c);
   for (int i = 0; i < kProfEvents; ++i)
     if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
+  for (int i = 0; i < 2; ++i)
+    if (c->tune_ev[i]) cudaEventDestroy(c->tune_ev[i]);
   for (int i = 0; i < kPhaseEvents; ++i)
     if (c->ph_ev[i]) cudaEventDestroy(c->ph_ev[i]);
   delete c;
@@ -125,6 +130,13 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   if (c->cfg.newton_max <= 0) c->cfg.newton_max = 20;
   if (c->cfg.krylov_max <= 0) c->cfg.krylov_max = 200;
   c->s = static_cast<cudaStream_t>(stream);
+  if (cfg->flags & SLAR_OWN_STREAM) {
+    if (cudaStreamCreateWithFlags(&c->own_s, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return SLAR_ECUDA;
+    }
+    c->s = c->own_s;
+  }
   c->dx = cfg->dx;
   c->dv = cfg->dv;
   c->d = cfg->dx + cfg->dv;
@@ -236,7 +248,7 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
     free_ctx(c);
     return SLAR_ENOMEM;
   }
-  if (sl_eval_init_attrs() != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
+  if (sl_eval_init_attrs() != cudaSuccess || linalg_init_attrs() != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
   {
     // index tuples of the check rows: row i (spatial multi-index) x every velocity column
     std::vector<int> tup((size_t)c->n_chk * c->M2 * d);
@@ -266,6 +278,8 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
     if (cudaEventCreate(&c->prof_ev[i]) != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
   for (int i = 0; i < kPhaseEvents; ++i)
     if (cudaEventCreate(&c->ph_ev[i]) != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreate(&c->tune_ev[i]) != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
   const slar_status mst = macro_alloc(c);
   if (mst != SLAR_OK) { free_ctx(c); return mst; }
   *out = c;
@@ -538,6 +552,41 @@ slar_status slar_set_record(slar_ctx* c, float* dst, int n_probes, unsigned long
   c->rec_dst = dst;
   c->rec_S = n_probes;
   c->rec_seed = seed;
+  return SLAR_OK;
+}
+
+slar_status slar_ensemble_step(slar_ctx** ctxs, int n, const double* dts, int threads, slar_stats* stats) {
+  if (!ctxs || !dts || n < 1) return SLAR_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return SLAR_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i] || (n > 1 && ctxs[j]->s == ctxs[i]->s)) return SLAR_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SLAR_ECUDA;
+  std::vector<slar_status> st(n, SLAR_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n) break;
+      st[i] = sl_step(ctxs[i], dts[i], stats ? &stats[i] : nullptr);
+    }
+  };
+  const int nt = std::max(1, std::min(threads, n));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  for (int i = 0; i < n; ++i)
+    if (st[i] != SLAR_OK) return st[i];
+  return SLAR_OK;
+}
+
+slar_status slar_stream(const slar_ctx* c, void** stream) {
+  if (!c || !stream) return SLAR_EINVAL;
+  *stream = c->s;
   return SLAR_OK;
 }
 

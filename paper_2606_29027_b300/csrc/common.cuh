@@ -82,17 +82,20 @@ struct EvalParams {
 };
 
 // ---- launchers (defined in the .cu files) ----
+// `tile` = entries per CTA of the evaluator, 16, 32 or 64 (chosen by the autotuner)
+bool eval_tile_ok(int tile);
 template <typename T>
 cudaError_t launch_sl_eval(const GridDesc& g, const HTView<T>& ht, const CorrView& corr,
-                           const EvalArgs& a, int evaluate_at_grid, cudaStream_t s);
+                           const EvalArgs& a, int evaluate_at_grid, cudaStream_t s, int tile = 32);
 // launch reading HT / field / tau from device memory; smem_bytes fixed by the caller
 template <typename T>
 cudaError_t launch_sl_eval_dev(const GridDesc& g, const EvalParams<T>* P, const EvalArgs& a,
-                               size_t smem_bytes, cudaStream_t s);
+                               size_t smem_bytes, cudaStream_t s, int tile = 32);
 template <typename T>
-size_t sl_eval_smem(const GridDesc& g, const int* ranks6);
+size_t sl_eval_smem(const GridDesc& g, const int* ranks6, int tile = 32);
 // opt the evaluator kernels into large dynamic shared memory (call before any capture)
 cudaError_t sl_eval_init_attrs();
+cudaError_t linalg_init_attrs();
 
 // dense FP64 linear algebra (linalg.cu)
 // C[b] = alpha op(A[b]) op(B[b]) + beta C[b]; row-major; op(A) is M x K.

@@ -47,6 +47,7 @@ struct slar_ctx {
   slar_config cfg;
   cudaStream_t s = nullptr;        // caller's stream: all work is ordered on it
   cudaStream_t cap_s = nullptr;    // internal stream used only to capture CUDA graphs
+  cudaStream_t own_s = nullptr;    // private stream (SLAR_OWN_STREAM)
   slar::GridDesc g;
   int d = 0, dx = 0, dv = 0, NX = 0, NV = 0, M1 = 0, M2 = 0, kmax = 0, n_mom = 0;
   long long capB = 0;
@@ -95,6 +96,11 @@ struct slar_ctx {
   size_t aca_graph_smem = 0;
   long long aca_graph_nodes = 0;
   int replay_calls = 0, replay_kmax = 0, replay_pos = 0;
+  // entry-evaluator tile (entries per CTA) chosen by the autotuner, and the tile the
+  // cross-approximation graph was captured with
+  int eval_tile = 32;
+  int aca_graph_tile = 0;
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
   // check rows of the cross-approximation stop test
   int n_chk = 0;
   int* chk_rows = nullptr;     // [n_chk]

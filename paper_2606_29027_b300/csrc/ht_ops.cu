@@ -104,9 +104,9 @@ slar_status eval_entries(slar_ctx* c, int slot, bool with_corr, const EvalArgs& 
   cudaError_t e;
   if (c->cfg.precision == SLAR_FP32) {
     CKS(refresh_f32_slot(c, slot));
-    e = launch_sl_eval<float>(c->g, view32_slot(c, slot), corr_view(c, with_corr), a, at_grid, c->s);
+    e = launch_sl_eval<float>(c->g, view32_slot(c, slot), corr_view(c, with_corr), a, at_grid, c->s, c->eval_tile);
   } else {
-    e = launch_sl_eval<double>(c->g, view64(c, slot), corr_view(c, with_corr), a, at_grid, c->s);
+    e = launch_sl_eval<double>(c->g, view64(c, slot), corr_view(c, with_corr), a, at_grid, c->s, c->eval_tile);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "sl_eval kernel");
   if (prof) {

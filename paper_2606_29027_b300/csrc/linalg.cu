@@ -402,7 +402,7 @@ __device__ void sort_write(const double* sA, int ne, int n, const double* V, int
   }
 }
 
-__global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs) {
+__global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long smem_doubles) {
   extern __shared__ double smem[];
   __shared__ int pp[SLAR_MAX_N / 2], qq[SLAR_MAX_N / 2];
   __shared__ double cc[SLAR_MAX_N / 2], ss[SLAR_MAX_N / 2];
@@ -530,9 +530,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs) {
     sort_write(sA, ne, n, V, ne, job.W, job.V);
     return;
   }
+  // the matrix in shared memory; its eigenvectors there too while both fit in the dynamic
+  // allocation (smem_doubles), else in the job's global scratch (n > 90)
   const int ne = n + (n & 1);
   double* sA = smem;
-  double* V = smem + ne * ne;
+  double* V = (2LL * ne * ne <= smem_doubles) ? smem + ne * ne : job.work;
   for (int it = tid; it < ne * ne; it += EIG_THREADS) {
     const int i = it / ne, j = it % ne;
     sA[it] = (i < n && j < n) ? job.A[i * n + j] : 0.0;
@@ -652,15 +654,19 @@ cudaError_t contract_mid(const double* X, const double* Y, int P, int C, int I, 
                           work, work_len, s);
 }
 
+// large dynamic shared memory for the Cholesky and Jacobi kernels (called at context creation)
+cudaError_t linalg_init_attrs() {
+  const int sm_chol = (int)(sizeof(double) * 2 * SLAR_MAX_RANK * (SLAR_MAX_RANK + 1));
+  cudaError_t e = cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_chol);
+  if (e != cudaSuccess) return e;
+  size_t sm = sizeof(double) * EIG_SMEM_DOUBLES;
+  if (sm < sizeof(double) * SLAR_MAX_N * SLAR_MAX_N) sm = sizeof(double) * SLAR_MAX_N * SLAR_MAX_N;
+  return cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
 cudaError_t chol_inv(const double* G, int n, double* R, double* Rinv, int* info, cudaStream_t s) {
   if (n > SLAR_MAX_RANK) return cudaErrorInvalidValue;
   const int sm = (int)(sizeof(double) * 2 * SLAR_MAX_RANK * (SLAR_MAX_RANK + 1));
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   slar::count_launch(), k_chol_inv<<<1, 256, sm, s>>>(G, n, R, Rinv, info);
   return cudaGetLastError();
 }
@@ -683,17 +689,10 @@ cudaError_t eig_batched(const EigJob* jobs_host, int njobs, EigJob* jobs_dev, cu
   // full-rank fallback needs an n x n matrix (n <= 128), which is no larger
   size_t sm = sizeof(double) * EIG_SMEM_DOUBLES;
   if (sm < sizeof(double) * SLAR_MAX_N * SLAR_MAX_N) sm = sizeof(double) * SLAR_MAX_N * SLAR_MAX_N;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   cudaError_t e = cudaMemcpyAsync(jobs_dev, jobs_host, sizeof(EigJob) * njobs,
                                   cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
-  slar::count_launch(), k_jacobi<<<njobs, EIG_THREADS, sm, s>>>(jobs_dev);
+  slar::count_launch(), k_jacobi<<<njobs, EIG_THREADS, sm, s>>>(jobs_dev, (long long)(sm / sizeof(double)));
   return cudaGetLastError();
 }
 

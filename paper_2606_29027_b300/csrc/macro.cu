@@ -694,8 +694,14 @@ slar_status jfnk(slar_ctx* c, double coef, double tol_abs, SolveStats* st, bool 
         CK(cudaGraphLaunch(pc ? w->g_loop_pc : w->g_loop, s));
         CK(cudaGraphLaunch(pc ? w->g_epi_pc : w->g_epi, s));
       } else {
+        // launched one by one (profiling): stop where the WHILE node would stop
         CKS(gmres_pro(c));
-        for (int j = 0; j < w->m; ++j) CKS(gmres_body(c, 0, 0, pc));
+        for (int j = 0; j < w->m; ++j) {
+          CK(cudaMemcpyAsync(c->scal_host + 30, misc + M_DONE, sizeof(double), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          if (c->scal_host[30] != 0.0) break;
+          CKS(gmres_body(c, 0, 0, pc));
+        }
         CKS(gmres_epi(c, pc));
       }
       CK(cudaMemcpyAsync(c->scal_host, misc, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
@@ -971,6 +977,7 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
   }
   c->prof_n = 0;
   st.launches = launch_count() - launches0;
+  st.eval_tile = c->eval_tile;
   c->step += 1;
   if (out) *out = st;
   return st.converged ? SLAR_OK : set_error(c, SLAR_ENOCONV, "Newton-Krylov did not converge");

@@ -377,69 +377,88 @@ size_t smem_bytes(const GridDesc& g, const HTView<T>& ht) {
   return (b + 15) & ~size_t(15);
 }
 
-}  // namespace
-
-template <typename T>
-cudaError_t launch_sl_eval(const GridDesc& g, const HTView<T>& ht, const CorrView& corr,
-                           const EvalArgs& a, int at_grid, cudaStream_t s) {
-  if (a.n <= 0) return cudaSuccess;
-  constexpr int TILE = 32;
+template <typename T, int TILE>
+cudaError_t launch_tile(const GridDesc& g, const HTView<T>& ht, const CorrView& corr, const EvalArgs& a,
+                        int at_grid, cudaStream_t s) {
   const size_t sm = smem_bytes<T, TILE>(g, ht);
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(T) == 8]) {
-    cudaError_t e = cudaFuncSetAttribute(k_sl_eval<T, TILE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set[sizeof(T) == 8] = true;
-  }
   const long long blocks = (a.n + TILE - 1) / TILE;
   slar::count_launch(), k_sl_eval<T, TILE><<<(unsigned)blocks, NTHREADS, sm, s>>>(g, ht, corr, a, at_grid);
   return cudaGetLastError();
 }
 
-cudaError_t sl_eval_init_attrs() {
-  const int mx = 200 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_sl_eval<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_dev<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_dev<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  return e;
-}
-
-template <typename T>
-size_t sl_eval_smem(const GridDesc& g, const int* r6) {
-  HTView<T> v{};
-  for (int m = 0; m < 4; ++m) v.r[m] = r6[m];
-  v.r12 = r6[4];
-  v.r34 = r6[5];
-  return smem_bytes<T, 32>(g, v);
-}
-
-template <typename T>
-cudaError_t launch_sl_eval_dev(const GridDesc& g, const EvalParams<T>* P, const EvalArgs& a,
-                               size_t sm, cudaStream_t s) {
-  constexpr int TILE = 32;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(T) == 8]) {
-    cudaError_t e = cudaFuncSetAttribute(k_sl_eval_dev<T, TILE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set[sizeof(T) == 8] = true;
-  }
+template <typename T, int TILE>
+cudaError_t launch_tile_dev(const GridDesc& g, const EvalParams<T>* P, const EvalArgs& a, size_t sm,
+                            cudaStream_t s) {
   const long long blocks = (a.n + TILE - 1) / TILE;
   slar::count_launch(), k_sl_eval_dev<T, TILE><<<(unsigned)blocks, NTHREADS, sm, s>>>(g, P, a);
   return cudaGetLastError();
 }
 
-template size_t sl_eval_smem<double>(const GridDesc&, const int*);
-template size_t sl_eval_smem<float>(const GridDesc&, const int*);
+template <typename T, int TILE>
+cudaError_t set_attrs_tile() {
+  const int mx = 200 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_sl_eval<T, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_dev<T, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  return e;
+}
+
+}  // namespace
+
+bool eval_tile_ok(int tile) { return tile == 16 || tile == 32 || tile == 64; }
+
+template <typename T>
+cudaError_t launch_sl_eval(const GridDesc& g, const HTView<T>& ht, const CorrView& corr,
+                           const EvalArgs& a, int at_grid, cudaStream_t s, int tile) {
+  if (a.n <= 0) return cudaSuccess;
+  switch (tile) {
+    case 16: return launch_tile<T, 16>(g, ht, corr, a, at_grid, s);
+    case 64: return launch_tile<T, 64>(g, ht, corr, a, at_grid, s);
+    default: return launch_tile<T, 32>(g, ht, corr, a, at_grid, s);
+  }
+}
+
+cudaError_t sl_eval_init_attrs() {
+  cudaError_t e = set_attrs_tile<double, 16>();
+  if (e == cudaSuccess) e = set_attrs_tile<double, 32>();
+  if (e == cudaSuccess) e = set_attrs_tile<double, 64>();
+  if (e == cudaSuccess) e = set_attrs_tile<float, 16>();
+  if (e == cudaSuccess) e = set_attrs_tile<float, 32>();
+  if (e == cudaSuccess) e = set_attrs_tile<float, 64>();
+  return e;
+}
+
+template <typename T>
+size_t sl_eval_smem(const GridDesc& g, const int* r6, int tile) {
+  HTView<T> v{};
+  for (int m = 0; m < 4; ++m) v.r[m] = r6[m];
+  v.r12 = r6[4];
+  v.r34 = r6[5];
+  switch (tile) {
+    case 16: return smem_bytes<T, 16>(g, v);
+    case 64: return smem_bytes<T, 64>(g, v);
+    default: return smem_bytes<T, 32>(g, v);
+  }
+}
+
+template <typename T>
+cudaError_t launch_sl_eval_dev(const GridDesc& g, const EvalParams<T>* P, const EvalArgs& a,
+                               size_t sm, cudaStream_t s, int tile) {
+  switch (tile) {
+    case 16: return launch_tile_dev<T, 16>(g, P, a, sm, s);
+    case 64: return launch_tile_dev<T, 64>(g, P, a, sm, s);
+    default: return launch_tile_dev<T, 32>(g, P, a, sm, s);
+  }
+}
+
+template size_t sl_eval_smem<double>(const GridDesc&, const int*, int);
+template size_t sl_eval_smem<float>(const GridDesc&, const int*, int);
 template cudaError_t launch_sl_eval_dev<double>(const GridDesc&, const EvalParams<double>*,
-                                                const EvalArgs&, size_t, cudaStream_t);
+                                                const EvalArgs&, size_t, cudaStream_t, int);
 template cudaError_t launch_sl_eval_dev<float>(const GridDesc&, const EvalParams<float>*,
-                                               const EvalArgs&, size_t, cudaStream_t);
+                                               const EvalArgs&, size_t, cudaStream_t, int);
 template cudaError_t launch_sl_eval<double>(const GridDesc&, const HTView<double>&,
-                                            const CorrView&, const EvalArgs&, int, cudaStream_t);
+                                            const CorrView&, const EvalArgs&, int, cudaStream_t, int);
 template cudaError_t launch_sl_eval<float>(const GridDesc&, const HTView<float>&,
-                                           const CorrView&, const EvalArgs&, int, cudaStream_t);
+                                           const CorrView&, const EvalArgs&, int, cudaStream_t, int);
 
 }  // namespace slar

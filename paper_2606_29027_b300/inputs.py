@@ -151,6 +151,33 @@ def two_stream_2d2v(n=128, alpha=0.005, k=0.2, v0=2.4, vmax=8.0, eps=5e-4, cap=4
                     rank_cap=cap, dt=dt, steps=steps, terms=terms, alpha=alpha, k=k)
 
 
+def ensemble(n_runs: int = 64, seed: int = 20261202, sizes=(32, 64, 128), cap_range=(8, 48),
+             dt: float = 0.1) -> List[Workload]:
+    """An ensemble of uneven runs: kinds cycle through 1D-1V Landau, 1D-1V two-stream,
+    2D-2V Landau, 2D-2V two-stream; alpha ~ U[0.001, 0.5] (two-stream: alpha / 10),
+    k ~ U[0.2, 0.6] (L = 2 pi / k per spatial dimension), points per dimension drawn from
+    `sizes` (2D-2V: one size for all four dimensions), rank caps ~ U{cap_range}, eps 1e-5,
+    dt 0.1.  Seeded numpy Generator (PCG64)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n_runs):
+        kind = r % 4
+        alpha = float(rng.uniform(0.001, 0.5))
+        k = float(rng.uniform(0.2, 0.6))
+        cap = int(rng.integers(cap_range[0], cap_range[1] + 1))
+        if kind < 2:
+            N = (int(rng.choice(sizes)), int(rng.choice(sizes)))
+            w = (landau_1d1v(N=N, alpha=alpha, k=k, eps=1e-5, cap=cap, dt=dt) if kind == 0 else
+                 two_stream_1d1v(N=N, alpha=alpha / 10, k=k, eps=1e-5, cap=cap, dt=dt))
+        else:
+            n = int(rng.choice(sizes))
+            w = (landau_2d2v(n=n, alpha=alpha, k=k, eps=1e-5, cap=cap, dt=dt) if kind == 2 else
+                 two_stream_2d2v(n=n, alpha=alpha / 10, k=k, eps=1e-5, cap=cap, dt=dt))
+        w.name = f"run{r:02d}_{w.name}"
+        out.append(w)
+    return out
+
+
 def workload_by_name(name: str) -> Workload:
     table = {
         "landau_1d1v": lambda: landau_1d1v(),

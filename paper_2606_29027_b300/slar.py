@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libslar.so")
 SLAR_OK, SLAR_EINVAL, SLAR_ENOMEM, SLAR_ECUDA, SLAR_ENOCONV, SLAR_ETIMEOUT, SLAR_ERANK, SLAR_ENAN = range(8)
 SLAR_FP64, SLAR_FP32 = 0, 1
 SLAR_LOMAC, SLAR_FOOT_EULER, SLAR_PROFILE, SLAR_PROFILE_EVAL = 1, 2, 4, 8
-SLAR_PRECOND, SLAR_LEARNED = 16, 32
+SLAR_PRECOND, SLAR_LEARNED, SLAR_NO_AUTOTUNE, SLAR_OWN_STREAM = 16, 32, 64, 128
 
 # every entry point declared in include/slar.h
 EXPORTED = ["slar_create", "slar_destroy", "slar_last_error", "init_ht", "sl_step", "ht_truncate",
@@ -28,7 +28,8 @@ EXPORTED = ["slar_create", "slar_destroy", "slar_last_error", "init_ht", "sl_ste
             "slar_set_conserved", "slar_sizes", "slar_launch_count", "slar_poisson_field_static",
             "slar_net_param_count", "slar_sample_floats", "slar_net_create", "slar_net_destroy",
             "slar_net_set_params", "slar_net_get_params", "slar_net_forward", "slar_net_loss_grad",
-            "slar_net_train_step", "slar_attach_net", "slar_set_record"]
+            "slar_net_train_step", "slar_attach_net", "slar_set_record", "slar_fma_peak",
+            "slar_ensemble_step", "slar_stream"]
 
 
 class Config(C.Structure):
@@ -46,7 +47,7 @@ class Stats(C.Structure):
                 ("totals", C.c_double * 4), ("eval_ms", C.c_double), ("eval_flop", C.c_double),
                 ("launches", C.c_longlong), ("phase_ms", C.c_double * 6),
                 ("guess_used", C.c_int), ("fallback", C.c_int), ("recorded", C.c_int),
-                ("g_evals", C.c_int)]
+                ("g_evals", C.c_int), ("eval_tile", C.c_int)]
 
     def to_dict(self):
         return dict(entries=self.entries, ranks=list(self.ranks), aca_rank=list(self.aca_rank[: self.n_slar]),
@@ -55,7 +56,7 @@ class Stats(C.Structure):
                     totals=list(self.totals), eval_ms=self.eval_ms, eval_flop=self.eval_flop,
                     launches=self.launches, phase_ms=list(self.phase_ms),
                     guess_used=bool(self.guess_used), fallback=bool(self.fallback),
-                    recorded=bool(self.recorded), g_evals=self.g_evals)
+                    recorded=bool(self.recorded), g_evals=self.g_evals, eval_tile=self.eval_tile)
 
 
 class HTView(C.Structure):
@@ -109,6 +110,9 @@ def load():
         "slar_net_train_step": ([P, P, I, P, I, C.c_float, C.POINTER(D)], I),
         "slar_attach_net": ([P, P], I),
         "slar_set_record": ([P, P, I, C.c_ulonglong], I),
+        "slar_fma_peak": ([I, I, C.POINTER(D), P], I),
+        "slar_ensemble_step": ([P, I, P, I, P], I),
+        "slar_stream": ([P, C.POINTER(P)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -144,6 +148,18 @@ def poisson_field_static(N, L, rho, E, phi=None, stream=None, energy=True):
     return W.value if energy else None
 
 
+def fma_peak(fp64: bool, iters: int = 0, stream=None) -> float:
+    """Measured FMA throughput of the GPU in TFLOP/s (see include/slar.h)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    it = iters or (512 if fp64 else 4096)
+    t = C.c_double()
+    status = load().slar_fma_peak(1 if fp64 else 0, it, C.byref(t), C.c_void_p(st.cuda_stream))
+    if status != SLAR_OK:
+        raise SlarError(status, "slar_fma_peak failed")
+    return t.value
+
+
 class SlarError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"slar status {status}: {msg}")
@@ -166,7 +182,7 @@ def _dptr(a: np.ndarray):
 def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, eps=1e-6, rank_cap=16,
                 newton_tol=1e-12, krylov_tol=1e-4, krylov_restart=30, newton_max=20, krylov_max=200,
                 precision="fp64", lomac=True, foot="rk3", delta_floor=1e-12, profile=False,
-                profile_eval=False, solver="plain") -> Config:
+                profile_eval=False, solver="plain", autotune=True, own_stream=False) -> Config:
     """solver: "plain" (the paper's JFNK), "precond" (block-circulant preconditioner) or
     "learned" (network warm start; attach a network with Context.attach_net)."""
     if workload is not None:
@@ -186,7 +202,8 @@ def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, ep
     cfg.precision = SLAR_FP32 if precision == "fp32" else SLAR_FP64
     cfg.flags = ((SLAR_LOMAC if lomac else 0) | (SLAR_FOOT_EULER if foot == "euler" else 0)
                  | (SLAR_PROFILE if profile else 0) | (SLAR_PROFILE_EVAL if profile_eval else 0)
-                 | {"plain": 0, "precond": SLAR_PRECOND, "learned": SLAR_LEARNED}[solver])
+                 | {"plain": 0, "precond": SLAR_PRECOND, "learned": SLAR_LEARNED}[solver]
+                 | (0 if autotune else SLAR_NO_AUTOTUNE) | (SLAR_OWN_STREAM if own_stream else 0))
     cfg.delta_floor = delta_floor
     return cfg
 
@@ -207,6 +224,10 @@ class Context:
         if st != SLAR_OK:
             raise SlarError(st, "slar_create failed")
         self.h = h
+        if cfg.flags & SLAR_OWN_STREAM:
+            sp = C.c_void_p()
+            self.lib.slar_stream(self.h, C.byref(sp))
+            self.stream = torch.cuda.ExternalStream(sp.value)
         nm, nx = C.c_int(), C.c_int()
         self.lib.slar_sizes(self.h, C.byref(nm), C.byref(nx))
         self.n_mom, self.NX = nm.value, nx.value
@@ -363,6 +384,19 @@ class Context:
             v.has_corr = 1
             v.dC, v.qv = _dptr(dc), _dptr(q)
         self._check(self.lib.ht_import(self.h, C.byref(v)))
+
+
+def ensemble_step(contexts, dts, threads: int = 16):
+    """Advance every context by one step concurrently (slar_ensemble_step); the contexts must
+    have distinct streams.  Returns the list of Stats."""
+    n = len(contexts)
+    arr = (C.c_void_p * n)(*[c.h.value for c in contexts])
+    d = (C.c_double * n)(*[float(x) for x in dts])
+    stats = (Stats * n)()
+    status = load().slar_ensemble_step(arr, n, d, int(threads), stats)
+    if status not in (SLAR_OK, SLAR_ENOCONV):
+        raise SlarError(status, "slar_ensemble_step failed")
+    return list(stats)
 
 
 def net_param_count(m: int, hidden: int = 32) -> int:

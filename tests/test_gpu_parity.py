@@ -194,9 +194,11 @@ def _landau_state(N, alpha=0.3, eps=1e-8, cap=24):
     return F0, g
 
 
-@pytest.mark.parametrize("N", [(32, 64), (16, 16, 16, 16)])
+@pytest.mark.parametrize("N", [(32, 64), (16, 16, 16, 16), (128, 128, 8, 8)])
 @pytest.mark.parametrize("replay", [True, False])
 def test_slar_call_matches_oracle(N, replay):
+    """(128, 128, 8, 8): the identity spatial leaves of the cross approximation give node
+    Gram matrices of order 128 (eigenvectors in global scratch)."""
     eps, cap = 1e-7, 24
     F0, g = _landau_state(N, eps=1e-12, cap=cap)
     dx = len(N) // 2
