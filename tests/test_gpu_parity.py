@@ -198,8 +198,11 @@ def _landau_state(N, alpha=0.3, eps=1e-8, cap=24):
 @pytest.mark.parametrize("replay", [True, False])
 def test_slar_call_matches_oracle(N, replay):
     """(128, 128, 8, 8): the identity spatial leaves of the cross approximation give node
-    Gram matrices of order 128 (eigenvectors in global scratch)."""
-    eps, cap = 1e-7, 24
+    Gram matrices of order 128 (eigenvectors in global scratch).  Their spectra end in a
+    flat cluster of rounding-level eigenvalues near 2e-14 lambda_max; a threshold inside it
+    (eps 1e-7 at cap 24) keeps an arbitrary subset of those directions, so this case uses
+    eps 1e-5, whose threshold (2e-11 lambda_max) lies above the cluster."""
+    eps, cap = (1e-5 if N[0] == 128 else 1e-7), 24
     F0, g = _landau_state(N, eps=1e-12, cap=cap)
     dx = len(N) // 2
     E = inputs.random_field(N[:dx], dx, 0.3, seed=13)
