@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--train-runs", type=int, default=8)
     p.add_argument("--train-steps", type=int, default=40)
     p.add_argument("--train-iters", type=int, default=1500)
+    p.add_argument("--ensemble-runs", type=int, default=64)
+    p.add_argument("--ensemble-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-step", action="store_true",
                    help="profiling configuration: init, 3 steps, then one BDF3 step with every "
@@ -344,6 +346,42 @@ def run_ours(args, w):
                     "eps / alpha relative to the field: the eps-1e-5 method itself is accurate "
                     "to about 1e-3 in W"}
 
+    # ---- ensemble of uneven runs (1D1V/2D2V Landau/two-stream, 32-128 points per
+    # dimension, rank caps 8-48), concurrent on private streams vs one after another ----
+    ensemble = None
+    if args.ensemble_runs > 0:
+        ews = inputs.ensemble(n_runs=args.ensemble_runs)
+        ectx = []
+        for ew in ews:
+            ec = slar.Context(slar.make_config(ew, precision="fp32", solver="precond", own_stream=True))
+            ec.init_ht(inputs.initial_factors(ew))
+            ectx.append(ec)
+        torch.cuda.synchronize()
+        edts = [ew.dt for ew in ews]
+        for _ in range(max(3, args.warmup)):
+            slar.ensemble_step(ectx, edts, threads=16)
+        torch.cuda.synchronize()
+        ens = {}
+        for label, thr in (("concurrent", 16), ("sequential", 1)):
+            t0 = time.perf_counter()
+            for _ in range(args.ensemble_steps):
+                est = slar.ensemble_step(ectx, edts, threads=thr)
+            torch.cuda.synchronize()
+            ens[label] = len(ews) * args.ensemble_steps / (time.perf_counter() - t0)
+        ensemble = {"metric": "run-steps/s", "runs": len(ews), "steps": args.ensemble_steps,
+                    "concurrent": ens["concurrent"], "sequential": ens["sequential"],
+                    "speedup": ens["concurrent"] / ens["sequential"],
+                    "threads": 16, "converged": all(s.converged for s in est),
+                    "tiles_chosen": sorted({s.eval_tile for s in est}),
+                    "workload": "64 seeded runs (PCG64 seed 20261202): 1D1V/2D2V x Landau/"
+                                "two-stream round-robin, alpha ~ U[0.001,0.5], k ~ U[0.2,0.6], "
+                                "N per dim in {32,64,128}, caps ~ U{8..48}, eps 1e-5, dt 0.1, "
+                                "FP32 entries, block-circulant preconditioner, after the DIRK3 "
+                                "start-up; host wall clock around each ensemble step"}
+        for ec in ectx:
+            ec.close()
+        del ectx
+
     # ---- end to end through the C ABI with host buffers ----
     e2e_steps = max(3, args.warmup) + min(args.steps, 10)
     ctx_e = make(args.precision, False)
@@ -384,6 +422,7 @@ def run_ours(args, w):
             "fp64_path": fp64,
             "forms": forms,
             "warm_start_training": train_info,
+            "ensemble": ensemble,
             "newton_per_step": float(np.mean([s.newton for s in stats])),
             "krylov_per_step": float(np.mean([s.krylov for s in stats])),
             "guess_used_steps": int(sum(s.guess_used for s in stats)),

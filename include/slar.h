@@ -43,8 +43,12 @@ enum {
 };
 
 /* precision of the SL entry evaluation (gathers + transfer-tensor contractions);
-   moments, truncation, LoMaC and the Newton solve are always FP64. */
-enum { SLAR_FP64 = 0, SLAR_FP32 = 1 };
+   moments, truncation, LoMaC and the Newton solve are always FP64.
+   SLAR_FP32_BF16X3: FP32 gathers, transfer-tensor contractions of d = 4 trees on the tensor
+   cores (tcgen05, operands split x = hi + lo into BF16, three products hi.hi + hi.lo +
+   lo.hi accumulated in FP32; about 2^-16 relative per product), 128 entries per CTA;
+   d = 2 trees use the FP32 path. */
+enum { SLAR_FP64 = 0, SLAR_FP32 = 1, SLAR_FP32_BF16X3 = 2 };
 
 /* flags */
 enum {

@@ -72,6 +72,7 @@ __global__ void k_aca_init(AcaState* st, int* pivI, unsigned char* usedr, int re
   st->stop_row = 0;
   st->replay = replay;
   st->eps = eps;
+  st->tc_err = 0;
   st->normA2 = 0.0;
   if (!replay) pivI[0] = 0;
   if (pivI[0] < 0) { st->done = 1; return; }
@@ -286,15 +287,19 @@ slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int
   ac.ldY = M1;
   ac.out = c->Ua;
   ac.out_stride = M1;
-  const bool f32 = c->cfg.precision == SLAR_FP32;
+  const bool f32 = c->cfg.precision != SLAR_FP64;
+  const bool tc = c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4;
   for (int pass = 0; pass < 2; ++pass) {
     const EvalArgs& a = pass == 0 ? ar : ac;
     const bool ev = prof && c->prof_n * 2 + 1 < kProfEvents;
     if (ev) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], s));
-    cudaError_t e = f32 ? launch_sl_eval_dev<float>(c->g, static_cast<const EvalParams<float>*>(c->evp), a, smem, s,
-                                                    c->eval_tile)
-                        : launch_sl_eval_dev<double>(c->g, static_cast<const EvalParams<double>*>(c->evp), a, smem, s,
-                                                     c->eval_tile);
+    cudaError_t e =
+        tc ? launch_sl_eval_tc_dev(c->g, static_cast<const EvalParams<float>*>(c->evp), a, c->tc_b12, c->tc_b34,
+                                   &c->ast->tc_err, smem, s)
+        : f32 ? launch_sl_eval_dev<float>(c->g, static_cast<const EvalParams<float>*>(c->evp), a, smem, s,
+                                          c->eval_tile)
+              : launch_sl_eval_dev<double>(c->g, static_cast<const EvalParams<double>*>(c->evp), a, smem, s,
+                                           c->eval_tile);
     CK(e);
     if (ev) {
       CK(cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], s));
@@ -386,6 +391,10 @@ slar_status eval_check_rows(slar_ctx* c, int in, bool with_corr, double tau, con
   a.tau = tau;
   a.E = E;
   a.foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
+  if (c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4) {
+    c->eval_tile = 128;   // the tensor-core evaluator's fixed MMA tile
+    return eval_entries(c, in, with_corr, a, 0);
+  }
   if (c->cfg.flags & SLAR_NO_AUTOTUNE) {
     c->eval_tile = 32;
     return eval_entries(c, in, with_corr, a, 0);
@@ -450,7 +459,8 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
   }
   // per-call evaluator parameters in device memory, read by the captured graph
   const HTBuf& hin = c->ht[in];
-  const bool f32 = c->cfg.precision == SLAR_FP32;
+  const bool f32 = c->cfg.precision != SLAR_FP64;
+  const bool tc = c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4;
   if (f32) CKS(refresh_f32_slot(c, in));
   if (f32) {
     EvalParams<float>* P = static_cast<EvalParams<float>*>(c->evp_host);
@@ -468,19 +478,20 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
     P->foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
   }
   CK(cudaMemcpyAsync(c->evp, c->evp_host, sizeof(EvalParams<double>), cudaMemcpyHostToDevice, s));
+  slar::count_launch(), k_aca_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->usedr, replay ? 1 : 0, c->cfg.eps);
+  CK(cudaGetLastError());
   long long chk_entries = 0;
   if (!replay && c->n_chk > 0) {
     // residuals of the check rows start as the rows themselves (this also fixes the tile)
     CKS(eval_check_rows(c, in, with_corr, tau, E));
     chk_entries = (long long)c->n_chk * M2;
   }
-  const size_t need = f32 ? sl_eval_smem<float>(c->g, hin.r, c->eval_tile)
-                          : sl_eval_smem<double>(c->g, hin.r, c->eval_tile);
+  const size_t need = tc ? sl_eval_tc_smem(hin.r)
+                         : f32 ? sl_eval_smem<float>(c->g, hin.r, c->eval_tile)
+                               : sl_eval_smem<double>(c->g, hin.r, c->eval_tile);
   const bool prof = (c->cfg.flags & SLAR_PROFILE_EVAL) != 0;
   if (!prof && (!c->aca_graph || need > c->aca_graph_smem || c->aca_graph_tile != c->eval_tile))
     CKS(build_aca_graph(c, need));
-  slar::count_launch(), k_aca_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->usedr, replay ? 1 : 0, c->cfg.eps);
-  CK(cudaGetLastError());
   if (prof) {
     // individually launched steps with events around the evaluator (roofline timing)
     for (int kk = 0; kk < kmax; ++kk) {
@@ -495,6 +506,8 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
   CK(cudaMemcpyAsync(c->ast_host, c->ast, sizeof(AcaState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const int k = c->ast_host->k;
+  if (c->ast_host->tc_err)
+    return set_error(c, SLAR_ETIMEOUT, "tensor-core evaluator: an MMA completion wait ran out");
   if (!prof) add_launches(c->aca_graph_nodes * (long long)(k + c->ast_host->stop_row));
   if (aca_rank) *aca_rank = k;
   const long long nent = (long long)k * (M1 + M2) + (c->ast_host->stop_row ? M2 : 0) + chk_entries;

@@ -61,7 +61,7 @@ slar_status validate(const slar_config* cfg, char* msg, size_t len) {
     snprintf(msg, len, "rank_cap must be in [1, %d]", SLAR_MAX_RANK); return SLAR_EINVAL;
   }
   if (!(cfg->eps >= 0.0)) { snprintf(msg, len, "eps must be >= 0"); return SLAR_EINVAL; }
-  if (cfg->precision != SLAR_FP64 && cfg->precision != SLAR_FP32) {
+  if (cfg->precision != SLAR_FP64 && cfg->precision != SLAR_FP32 && cfg->precision != SLAR_FP32_BF16X3) {
     snprintf(msg, len, "unknown precision"); return SLAR_EINVAL;
   }
   if (cfg->flags & ~(SLAR_LOMAC | SLAR_FOOT_EULER | SLAR_PROFILE | SLAR_PROFILE_EVAL | SLAR_PRECOND | SLAR_LEARNED |
@@ -82,7 +82,7 @@ void free_ctx(slar_ctx* c) {
     F(c->ht[sl].B12); F(c->ht[sl].B34); F(c->ht[sl].Broot);
   }
   for (int m = 0; m < 4; ++m) { F(c->U32[m]); F(c->Qleaf[m]); F(c->Rleaf[m]); }
-  F(c->B12_32); F(c->B34_32); F(c->Broot32); F(c->Ik); F(c->Lt[0]); F(c->Lt[1]);
+  F(c->B12_32); F(c->B34_32); F(c->Broot32); F(c->tc_b12); F(c->tc_b34); F(c->Ik); F(c->Lt[0]); F(c->Lt[1]);
   F(c->dC); F(c->qv); F(c->Uc); F(c->Uh1); F(c->Uh2);
   F(c->Ua); F(c->Va); F(c->rowbuf); F(c->usedr); F(c->usedc); F(c->pivI); F(c->pivJ);
   F(c->ast); F(c->aca_part); F(c->aca_dots);
@@ -180,6 +180,13 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   }
   if (d == 4) { A(c->B12_32, (size_t)R * R * R); A(c->B34_32, (size_t)R * R * R); }
   A(c->Broot32, (size_t)R * R);
+  if (cfg->precision == SLAR_FP32_BF16X3 && d == 4) {
+    if (cudaMalloc(&c->tc_b12, (size_t)tc_split_bytes()) != cudaSuccess ||
+        cudaMalloc(&c->tc_b34, (size_t)tc_split_bytes()) != cudaSuccess) {
+      free_ctx(c);
+      return SLAR_ENOMEM;
+    }
+  }
   A(c->Ik, (size_t)R * R);
   if (d == 2) { A(c->Lt[0], (size_t)c->M1 * c->kmax); A(c->Lt[1], (size_t)c->M2 * c->kmax); }
   A(c->dC, (size_t)(c->dv + 2) * c->NX);
@@ -248,7 +255,12 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
     free_ctx(c);
     return SLAR_ENOMEM;
   }
-  if (sl_eval_init_attrs() != cudaSuccess || linalg_init_attrs() != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
+  if (cudaMemset(c->ast, 0, sizeof(AcaState)) != cudaSuccess) { free_ctx(c); return SLAR_ECUDA; }
+  if (sl_eval_init_attrs() != cudaSuccess || linalg_init_attrs() != cudaSuccess ||
+      (c->tc_b12 && sl_eval_tc_init_attrs() != cudaSuccess)) {
+    free_ctx(c);
+    return SLAR_ECUDA;
+  }
   {
     // index tuples of the check rows: row i (spatial multi-index) x every velocity column
     std::vector<int> tup((size_t)c->n_chk * c->M2 * d);

@@ -37,6 +37,7 @@ struct AcaState {
   double piv;     // current pivot value
   double nv2;     // ||v_k||^2
   double eps;     // stopping tolerance
+  int tc_err;     // set by the tensor-core evaluator if an MMA completion wait ran out
 };
 
 }  // namespace slar
@@ -61,6 +62,8 @@ struct slar_ctx {
   float* B12_32 = nullptr;
   float* B34_32 = nullptr;
   float* Broot32 = nullptr;
+  void* tc_b12 = nullptr;   // BF16x3 pre-split transfer tensors of the FP32 shadow
+  void* tc_b34 = nullptr;
   double* Ik = nullptr;     // identity (kmax x kmax)
   double* Lt[2] = {nullptr, nullptr};  // d = 2 cross factors as row-major leaves
 

@@ -1,0 +1,168 @@
+// Device functions shared by the entry evaluators (sl_eval.cu: SIMT, FP32/FP64;
+// sl_eval_tc.cu: tensor-core transfer-tensor contractions): the characteristic foot, the
+// quadratic cell weights, spatial and velocity interpolation, the separable LoMaC
+// correction and the decoding of an entry index into a grid tuple.  Foot arithmetic uses
+// explicit round-to-nearest intrinsics (no FMA contraction) so cell choices are
+// reproducible.
+#pragma once
+
+#include "common.cuh"
+
+namespace slar {
+namespace {
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+// cell and quadratic weights of coordinate y in dimension m (oracle: grid.locate/weights)
+__device__ __forceinline__ void cell_weights(const GridDesc& g, int m, double y, int rows[3],
+                                             double w[3]) {
+  double t = __ddiv_rn(dsub(y, g.lo[m]), g.h[m]);
+  if (!(fabs(t) < 1e15)) t = 0.0;  // non-finite or absurd feet still index inside the grid
+  double jf = floor(t);
+  double xi = dsub(dsub(t, jf), 0.5);
+  double hx = dmul(0.5, xi);
+  w[0] = dmul(hx, dsub(xi, 1.0));
+  w[1] = dsub(1.0, dmul(xi, xi));
+  w[2] = dmul(hx, dadd(xi, 1.0));
+  int n = g.N[m];
+  long long j = (long long)jf;
+  long long r0 = (j - 1) % n;
+  if (r0 < 0) r0 += n;
+  rows[0] = (int)r0;
+  rows[1] = (int)((r0 + 1) % n);
+  rows[2] = (int)((r0 + 2) % n);
+}
+
+// tensor-product quadratic interpolation of a spatial field at point p (dx dims),
+// lexicographic stencil order, acc = acc + (w1 w2) v  (oracle: sl.interp_spatial)
+__device__ double interp_spatial(const GridDesc& g, const double* F, const double* p) {
+  int r0[3], r1[3];
+  double w0[3], w1[3];
+  cell_weights(g, 0, p[0], r0, w0);
+  double acc = 0.0;
+  if (g.dx == 1) {
+    for (int s = 0; s < 3; ++s) acc = dadd(acc, dmul(w0[s], F[r0[s]]));
+    return acc;
+  }
+  cell_weights(g, 1, p[1], r1, w1);
+  const int N1 = g.N[1];
+  for (int s0 = 0; s0 < 3; ++s0)
+    for (int s1 = 0; s1 < 3; ++s1)
+      acc = dadd(acc, dmul(dmul(w0[s0], w1[s1]), F[r0[s0] * N1 + r1[s1]]));
+  return acc;
+}
+
+__device__ __forceinline__ double centre(const GridDesc& g, int m, int i) {
+  return dadd(g.lo[m], dmul((double)i + 0.5, g.h[m]));
+}
+
+// backward foot of the frozen-field characteristic (oracle: sl.trace_feet)
+__device__ void trace_foot(const GridDesc& g, const double* E, double tau, int euler,
+                           const int* idx, double* foot) {
+  const int dx = g.dx;
+  double x[2], v[2];
+  for (int m = 0; m < dx; ++m) {
+    x[m] = centre(g, m, idx[m]);
+    v[m] = centre(g, dx + m, idx[dx + m]);
+  }
+  const long long NX = g.NX;
+  if (euler) {
+    for (int m = 0; m < dx; ++m) {
+      double e = interp_spatial(g, E + m * NX, x);
+      foot[m] = dsub(x[m], dmul(v[m], tau));
+      foot[dx + m] = dadd(v[m], dmul(e, tau));
+    }
+    return;
+  }
+  const double h = tau;
+  const double half = h / 2.0, two_h = 2.0 * h, sixth = __ddiv_rn(h, 6.0);
+  double k1x[2], k1v[2], x2[2], v2[2], k2x[2], k2v[2], x3[2], v3[2], k3x[2], k3v[2];
+  for (int m = 0; m < dx; ++m) {
+    k1x[m] = -v[m];
+    k1v[m] = interp_spatial(g, E + m * NX, x);
+  }
+  for (int m = 0; m < dx; ++m) {
+    x2[m] = dadd(x[m], dmul(half, k1x[m]));
+    v2[m] = dadd(v[m], dmul(half, k1v[m]));
+  }
+  for (int m = 0; m < dx; ++m) {
+    k2x[m] = -v2[m];
+    k2v[m] = interp_spatial(g, E + m * NX, x2);
+  }
+  for (int m = 0; m < dx; ++m) {
+    x3[m] = dadd(dsub(x[m], dmul(h, k1x[m])), dmul(two_h, k2x[m]));
+    v3[m] = dadd(dsub(v[m], dmul(h, k1v[m])), dmul(two_h, k2v[m]));
+  }
+  for (int m = 0; m < dx; ++m) {
+    k3x[m] = -v3[m];
+    k3v[m] = interp_spatial(g, E + m * NX, x3);
+  }
+  for (int m = 0; m < dx; ++m) {
+    foot[m] = dadd(x[m], dmul(sixth, dadd(dadd(k1x[m], dmul(4.0, k2x[m])), k3x[m])));
+    foot[dx + m] = dadd(v[m], dmul(sixth, dadd(dadd(k1v[m], dmul(4.0, k2v[m])), k3v[m])));
+  }
+}
+
+// quadratic 1D interpolation of a velocity vector (oracle: grid.interp_1d)
+__device__ __forceinline__ double interp_1d(const GridDesc& g, int m, const double* vec, double y) {
+  int r[3];
+  double w[3];
+  cell_weights(g, m, y, r, w);
+  return (w[0] * vec[r[0]] + w[1] * vec[r[1]]) + w[2] * vec[r[2]];
+}
+
+// separable LoMaC correction sum_k dC_k(x*) Q_k(v*) at a foot (oracle: sl.correction_at)
+__device__ double correction_at(const GridDesc& g, const CorrView& c, const double* foot) {
+  const int dx = g.dx, dv = g.dv;
+  const long long NX = g.NX;
+  const int Nv = g.N[dx];
+  double dCi[4];
+  for (int k = 0; k < dv + 2; ++k) dCi[k] = interp_spatial(g, c.dC + k * NX, foot);
+  double om[2], q1[2], q2[2];
+  for (int m = 0; m < dv; ++m) {
+    const double y = foot[dx + m];
+    om[m] = interp_1d(g, dx + m, c.qv + (0 * dv + m) * Nv, y);
+    q1[m] = interp_1d(g, dx + m, c.qv + (1 * dv + m) * Nv, y);
+    q2[m] = interp_1d(g, dx + m, c.qv + (2 * dv + m) * Nv, y);
+  }
+  // terms in the order (0: prod omega), (1+m: q1 at m), (1+dv: q2 at m) for m = 0..dv-1
+  double out = 0.0;
+  double t = dCi[0];
+  for (int m = 0; m < dv; ++m) t *= om[m];
+  out += t;
+  for (int j = 0; j < dv; ++j) {
+    t = dCi[1 + j];
+    for (int m = 0; m < dv; ++m) t *= (m == j ? q1[m] : om[m]);
+    out += t;
+  }
+  for (int j = 0; j < dv; ++j) {
+    t = dCi[1 + dv];
+    for (int m = 0; m < dv; ++m) t *= (m == j ? q2[m] : om[m]);
+    out += t;
+  }
+  return out;
+}
+
+__device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& a, long long e,
+                                             int* idx) {
+  if (a.mode == EVAL_TUPLES) {
+    for (int m = 0; m < g.d; ++m) idx[m] = a.idx[e * g.d + m];
+    return;
+  }
+  const long long left = (a.mode == EVAL_ROW) ? (long long)(*a.pivot) : e;
+  const long long right = (a.mode == EVAL_ROW) ? e : (long long)(*a.pivot);
+  if (g.d == 2) {
+    idx[0] = (int)left;
+    idx[1] = (int)right;
+  } else {
+    idx[0] = (int)(left / g.N[1]);
+    idx[1] = (int)(left % g.N[1]);
+    idx[2] = (int)(right / g.N[3]);
+    idx[3] = (int)(right % g.N[3]);
+  }
+}
+
+}  // namespace
+}  // namespace slar

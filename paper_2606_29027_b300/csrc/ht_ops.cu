@@ -66,6 +66,10 @@ slar_status refresh_f32_slot(slar_ctx* c, int slot) {
     CK(to_float(h.B12, c->B12_32, (long long)h.r[4] * h.r[0] * h.r[1], c->s));
     CK(to_float(h.B34, c->B34_32, (long long)h.r[5] * h.r[2] * h.r[3], c->s));
     CK(to_float(h.Broot, c->Broot32, (long long)h.r[4] * h.r[5], c->s));
+    if (c->cfg.precision == SLAR_FP32_BF16X3) {
+      CK(split_transfer_bf16(c->B12_32, h.r[4], h.r[0], h.r[1], c->tc_b12, c->s));
+      CK(split_transfer_bf16(c->B34_32, h.r[5], h.r[2], h.r[3], c->tc_b34, c->s));
+    }
   } else {
     CK(to_float(h.Broot, c->Broot32, (long long)h.r[0] * h.r[1], c->s));
   }
@@ -102,7 +106,11 @@ slar_status eval_entries(slar_ctx* c, int slot, bool with_corr, const EvalArgs& 
   const bool prof = (c->cfg.flags & SLAR_PROFILE_EVAL) && c->prof_n * 2 + 1 < kProfEvents;
   if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], c->s));
   cudaError_t e;
-  if (c->cfg.precision == SLAR_FP32) {
+  if (c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4 && !at_grid) {
+    CKS(refresh_f32_slot(c, slot));
+    e = launch_sl_eval_tc(c->g, view32_slot(c, slot), corr_view(c, with_corr), a, c->tc_b12, c->tc_b34,
+                          &c->ast->tc_err, c->s);
+  } else if (c->cfg.precision != SLAR_FP64) {
     CKS(refresh_f32_slot(c, slot));
     e = launch_sl_eval<float>(c->g, view32_slot(c, slot), corr_view(c, with_corr), a, at_grid, c->s, c->eval_tile);
   } else {
@@ -269,7 +277,7 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
     jobs[nj].V = c->S[t];
     jobs[nj].work = c->ework[t];
     jobs[nj].n = node_n[t];
-    jobs[nj].floor_rel = c->cfg.precision == SLAR_FP32 ? 1e-13 : 1e-17;
+    jobs[nj].floor_rel = c->cfg.precision != SLAR_FP64 ? 1e-13 : 1e-17;
     ++nj;
   }
   CK(eig_batched(jobs, nj, c->d_eig, s));

@@ -1,0 +1,105 @@
+"""GPU tests of the tensor-core (tcgen05, BF16x3) entry evaluator against the FP64 oracle
+and the FP32 SIMT path.  The BF16x3 product a_hi b_hi + a_hi b_lo + a_lo b_hi drops
+a_lo b_lo and the residual below the 16th bit of each operand: about 2^-16 relative per
+product.  Errors are stated relative to the largest entry (relative L2 over the sample)."""
+import numpy as np
+import pytest
+
+from oracle import sl
+from paper_2606_29027_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import test_gpu_parity as P  # noqa: E402
+
+BF16X3_TOL = 1e-4   # relative L2 against FP64 (2^-16 ~ 1.5e-5 per product, summed over K terms)
+
+CASES = [((16, 16, 16, 16), (3, 5, 4, 6, 7, 9)),          # K < 64, N < 16: one padded chunk
+         ((16, 16, 32, 32), (12, 9, 16, 11, 20, 24)),     # ragged K and N
+         ((32, 32, 32, 32), (32, 32, 32, 32, 32, 32)),     # K = 1024: 16 chunks
+         ((64, 64, 64, 64), (64, 64, 48, 40, 64, 61))]     # K = 4096: 64 chunks, N = 64
+
+
+@pytest.mark.parametrize("N,ranks", CASES)
+def test_tc_entries_match_oracle(N, ranks):
+    h, _, _ = P.rand_state(N, ranks, 21)
+    E_np = inputs.random_field(N[:2], 2, 0.6, seed=22)
+    E = P.dev(E_np)
+    idx_np = inputs.random_tuples(N, 3000, seed=23)
+    idx = P.dev(idx_np, torch.int32)
+    want = sl.sl_eval(h, E_np, 1.1, idx_np, P.ctx_for(N)[1])
+    outs = {}
+    for prec in ("fp32", "bf16x3"):
+        ctx, g = P.ctx_for(N, precision=prec)
+        P.load(ctx, h)
+        o = torch.zeros(idx.shape[0], dtype=torch.float64, device="cuda")
+        ctx.sl_eval(1.1, E, idx, o)
+        outs[prec] = o.cpu().numpy()
+        ctx.close()
+    e32 = P.relerr(outs["fp32"], want)
+    etc = P.relerr(outs["bf16x3"], want)
+    print(f"N={N} ranks={ranks}: fp32 {e32:.2e} bf16x3 {etc:.2e}")
+    assert e32 < 1e-5
+    assert etc < BF16X3_TOL
+
+
+def test_tc_ragged_tail_and_single_entry():
+    N, ranks = (16, 16, 16, 16), (8, 8, 8, 8, 16, 16)
+    h, _, _ = P.rand_state(N, ranks, 24)
+    E_np = inputs.random_field(N[:2], 2, 0.3, seed=25)
+    ctx, g = P.ctx_for(N, precision="bf16x3")
+    P.load(ctx, h)
+    for n in (1, 127, 129, 300):
+        idx_np = inputs.random_tuples(N, n, seed=26 + n)
+        o = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.sl_eval(0.7, P.dev(E_np), P.dev(idx_np, torch.int32), o)
+        want = sl.sl_eval(h, E_np, 0.7, idx_np, g)
+        assert P.relerr(o.cpu().numpy(), want) < BF16X3_TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("replay", [True, False])
+def test_tc_slar_call_close_to_oracle(replay):
+    """Cross approximation with the tensor-core evaluator (graph path, parameters read from
+    device memory): with the oracle's pivots the result differs by the BF16x3 rounding."""
+    from oracle import cross
+    from oracle import ht as htmod
+    import convert
+    N = (16, 16, 16, 16)
+    eps, cap = 1e-5, 24
+    F0, g = P._landau_state(N, eps=1e-12, cap=cap)
+    E = inputs.random_field(N[:2], 2, 0.3, seed=13)
+    want, info = cross.htaca(lambda idx: sl.sl_eval(F0, E, 0.45, idx, g), N, eps, cap, return_info=True)
+    ctx, _ = P.ctx_for(N, eps=eps, cap=cap, precision="bf16x3")
+    P.load(ctx, F0)
+    if replay:
+        ctx.set_pivot_replay([info["pivots"]])
+    ctx.advect(0.45, P.dev(E))
+    got = htmod.densify(convert.from_lib(ctx.export()))
+    err = P.relerr(got, htmod.densify(want))
+    print("slar call bf16x3 vs oracle", err)
+    assert err < (1e-4 if replay else 3 * eps)
+    ctx.close()
+
+
+def test_tc_step_conserves_and_tracks_fp64():
+    w = inputs.landau_2d2v(n=16, alpha=0.3, cap=12)
+    res = {}
+    for prec in ("fp64", "bf16x3"):
+        c = slar.Context(slar.make_config(w, precision=prec))
+        c.init_ht(inputs.initial_factors(w))
+        st = [c.step(w.dt) for _ in range(5)]
+        res[prec] = st
+        c.close()
+    W64 = np.array([s.field_energy for s in res["fp64"]])
+    Wtc = np.array([s.field_energy for s in res["bf16x3"]])
+    assert np.max(np.abs(Wtc - W64)) / np.max(W64) < 1e-3
+    tot0 = np.array(res["bf16x3"][0].totals)
+    for s in res["bf16x3"]:
+        assert s.converged and s.eval_tile == 128
+        assert abs(s.totals[0] - tot0[0]) <= 1e-12 * abs(tot0[0])
+        assert abs(s.totals[3] - tot0[3]) <= 1e-11 * abs(tot0[3])
+
+
+from paper_2606_29027_b300 import slar  # noqa: E402
