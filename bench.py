@@ -52,6 +52,13 @@ def parse():
     p.add_argument("--ensemble-runs", type=int, default=64)
     p.add_argument("--ensemble-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-eval", default=None, choices=["fp64", "fp32", "bf16x3"],
+                   help="evaluator microbenchmark: one warm-up and one measured sl_eval launch on "
+                        "a random 2D2V HT (--eval-rank, --eval-n points per dimension, "
+                        "--eval-entries tuples), for ncu captures of the evaluator kernels")
+    p.add_argument("--eval-rank", type=int, default=64)
+    p.add_argument("--eval-n", type=int, default=128)
+    p.add_argument("--eval-entries", type=int, default=65536)
     p.add_argument("--profile-step", action="store_true",
                    help="profiling configuration: init, 3 steps, then one BDF3 step with every "
                         "kernel launched individually; prints the launch counts for ncu -s/-c")
@@ -470,8 +477,39 @@ def profile_step(args, w):
           flush=True)
 
 
+def profile_eval(args):
+    """Time the entry evaluator alone (CUDA events, one launch after one warm-up)."""
+    import torch
+    from paper_2606_29027_b300 import inputs, slar
+    n, r = args.eval_n, args.eval_rank
+    N = (n, n, n, n)
+    L = 4 * math.pi
+    cfg = slar.make_config(dx=2, dv=2, N=N, lo=(0, 0, -6, -6), hi=(L, L, 6, 6), eps=1e-6, rank_cap=64,
+                           precision=args.profile_eval)
+    ctx = slar.Context(cfg)
+    h = inputs.random_ht(N, (r,) * 6, seed=5)
+    ctx.import_ht(U=h.U, Broot=h.Broot, B12=np.transpose(h.B12, (2, 0, 1)), B34=np.transpose(h.B34, (2, 0, 1)))
+    E = torch.as_tensor(inputs.random_field(N[:2], 2, 0.6, seed=4), device="cuda")
+    idx = torch.as_tensor(inputs.random_tuples(N, args.eval_entries, seed=7), device="cuda")
+    out = torch.zeros(args.eval_entries, dtype=torch.float64, device="cuda")
+    ctx.sl_eval(1.1, E, idx, out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    ctx.sl_eval(1.1, E, idx, out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    flop = (2 * (3 * 4 * r + 2 * r ** 3 + r * r) + 60) * args.eval_entries
+    print(json.dumps({"profile_eval": args.profile_eval, "rank": r, "n": n, "entries": args.eval_entries,
+                      "ms": ms, "tflops": flop / ms / 1e9}), flush=True)
+
+
 def main():
     args = parse()
+    if args.profile_eval:
+        profile_eval(args)
+        return
     from paper_2606_29027_b300 import inputs
     w = inputs.workload_by_name(args.workload)
     if args.profile_step:

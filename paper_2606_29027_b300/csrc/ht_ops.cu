@@ -277,7 +277,13 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
     jobs[nj].V = c->S[t];
     jobs[nj].work = c->ework[t];
     jobs[nj].n = node_n[t];
-    jobs[nj].floor_rel = c->cfg.precision != SLAR_FP64 ? 1e-13 : 1e-17;
+    // entries below the data noise of the Gram matrix are not rotated -- FP64 rounding
+    // (1e-17), FP32 entries (u^2 ~ 4e-15: 1e-13), BF16x3 entries (about 2^-16 per product:
+    // 1e-9) -- but never at or above the rank threshold eps^2/(2d-3) of the truncation: the
+    // floor stays at 1/100 of it so that the eigenvalues that decide the ranks are resolved;
+    // and never below the FP64 rounding level
+    const double noise = c->cfg.precision == SLAR_FP64 ? 1e-17 : (c->cfg.precision == SLAR_FP32 ? 1e-13 : 1e-9);
+    jobs[nj].floor_rel = std::max(1e-17, std::min(noise, 1e-2 * eps * eps / (2.0 * d - 3.0)));
     ++nj;
   }
   CK(eig_batched(jobs, nj, c->d_eig, s));

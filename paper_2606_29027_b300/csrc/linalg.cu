@@ -279,8 +279,9 @@ constexpr int EIG_THREADS = 512;
 // rotated while |a_pq| > tol sqrt(|a_pp a_qq|) (relative criterion: small eigenvalues and
 // their eigenvectors are resolved to relative accuracy); stop after a sweep without any
 // rotation, or after 40 sweeps.  Entries below floor_rel ||A||_F are never rotated: 1e-17 for
-// Gram matrices of FP64 data (the rounding level), 1e-13 for those of FP32 entries, whose
-// noise puts a cluster of eigenvalues near 1e-14 ||A|| that the truncation discards anyway.
+// Gram matrices of FP64 data (the rounding level), 1e-13 for those of FP32 entries and 1e-9
+// for BF16x3 entries, whose noise puts a cluster of eigenvalues near u^2 ||A|| (u the
+// entries' relative precision) that carries no information.
 __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, double* cc,
                               double* ss, int* rotated, double floor_rel) {
   const int tid = threadIdx.x;

@@ -49,12 +49,12 @@ __host__ __device__ __forceinline__ TcLayout tc_layout(int r0, int r1, int r2, i
   const int ra = r0 > r2 ? r0 : r2, rb = r1 > r3 ? r1 : r3;
   const int np = tc_np(r12) > tc_np(r34) ? tc_np(r12) : tc_np(r34);
   int o = TC_HEAD_BYTES;
-  L.ca = o; o = al128(o + 4 * TC_TILE * ra);
-  L.cb = o; o = al128(o + 4 * TC_TILE * rb);
+  L.ca = o; o = al128(o + 4 * TC_TILE * (ra + 1));
+  L.cb = o; o = al128(o + 4 * TC_TILE * (rb + 1));
   L.c12 = o; o = al128(o + 4 * TC_TILE * r12);
   L.c34 = o; o = al128(o + 4 * TC_TILE * r34);
   L.A = o; o += TC_A_BYTES;
-  L.B = o; o += tc_chunk_bytes(np);
+  L.B = o; o += 2 * tc_chunk_bytes(np);   // double buffer
   L.total = o;
   return L;
 }
@@ -120,6 +120,15 @@ __device__ __forceinline__ void split8(const float* x, uint4* hi, uint4* lo) {
   *lo = *reinterpret_cast<uint4*>(l);
 }
 
+// asynchronous copy of one pre-split chunk (bytes a multiple of 16) into shared memory,
+// one commit group per chunk
+__device__ __forceinline__ void copy_chunk_async(unsigned char* dst, const unsigned char* src, int bytes) {
+  const uint32_t d = smem_u32(dst);
+  for (int it = threadIdx.x; it < bytes / 16; it += TC_THREADS)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * it), "l"(src + 16LL * it) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // Pre-split B [rp][K] (FP32, row = p) into per-chunk hi/lo operand tiles (layout above).
 __global__ void k_split_bf16(const float* __restrict__ B, int rp, int K, int np, int nch,
                              unsigned char* __restrict__ out) {
@@ -151,21 +160,32 @@ __device__ bool contract_tc(const float* ca, int ra, const float* cb, int rb, co
   const int K = ra * rb, np = tc_np(rp), nch = (K + 63) / 64;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(np >> 3) << 17) |
                          ((uint32_t)(TC_TILE >> 4) << 24);
-  const uint32_t a_addr = smem_u32(Abuf), b_addr = smem_u32(Bbuf);
+  const uint32_t a_addr = smem_u32(Abuf);
+  const int cb_bytes = tc_chunk_bytes(np);
+  copy_chunk_async(Bbuf, Bg, cb_bytes);   // chunk 0 into buffer 0
   for (int c = 0; c < nch; ++c) {
-    // Khatri-Rao chunk of the left operand, split into hi / lo
+    // prefetch chunk c+1 into the other buffer (its previous MMA has completed)
+    if (c + 1 < nch) copy_chunk_async(Bbuf + ((c + 1) & 1) * cb_bytes, Bg + (long long)(c + 1) * cb_bytes, cb_bytes);
+    // Khatri-Rao chunk of the left operand, split into hi / lo.  A warp takes 32
+    // consecutive entries of one 8-wide k-group: its 16-byte stores fill whole 128-byte
+    // rows of core matrices (no bank conflicts), its reads of ca / cb use the odd padded
+    // strides, and (a, b) of the group's first k is the same across the warp.
+    const int lda = ra + 1, ldb = rb + 1;
     for (int it = tid; it < TC_TILE * 8; it += TC_THREADS) {
-      const int e = it >> 3, kg = it & 7;
+      const int kg = it >> 7, e = it & (TC_TILE - 1);
+      const int k0 = c * 64 + kg * 8;
+      int a = k0 / rb, b = k0 - a * rb;
+      const bool live = e < nT;
+      const float* cae = ca + e * lda;
+      const float* cbe = cb + e * ldb;
       float x[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int k = c * 64 + kg * 8 + j;
-        float v = 0.f;
-        if (k < K && e < nT) {
-          const int a = k / rb, b = k - a * rb;
-          v = ca[e * ra + a] * cb[e * rb + b];
+        x[j] = (live && k0 + j < K) ? cae[a] * cbe[b] : 0.f;
+        if (++b == rb) {
+          b = 0;
+          ++a;
         }
-        x[j] = v;
       }
       uint4 hi, lo;
       split8(x, &hi, &lo);
@@ -173,12 +193,14 @@ __device__ bool contract_tc(const float* ca, int ra, const float* cb, int rb, co
       *reinterpret_cast<uint4*>(Abuf + off) = hi;
       *reinterpret_cast<uint4*>(Abuf + 16384 + off) = lo;
     }
-    const uint4* src = reinterpret_cast<const uint4*>(Bg + (long long)c * tc_chunk_bytes(np));
-    for (int it = tid; it < tc_chunk_bytes(np) / 16; it += TC_THREADS) reinterpret_cast<uint4*>(Bbuf)[it] = src[it];
+    // chunk c's copy done (chunk c+1 may still be in flight)
+    if (c + 1 < nch) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       fence_after();
+      const uint32_t b_addr = smem_u32(Bbuf + (c & 1) * cb_bytes);
       for (int s = 0; s < 4; ++s) {
         if (c * 64 + s * 16 >= K) break;
         const uint64_t ah = tc_desc(a_addr + s * 4096), al = tc_desc(a_addr + 16384 + s * 4096);
@@ -201,7 +223,10 @@ __device__ bool contract_tc(const float* ca, int ra, const float* cb, int rb, co
     }
     phase ^= 1u;
     __syncthreads();
-    if (!*s_ok) return false;
+    if (!*s_ok) {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      return false;
+    }
   }
   fence_after();
   if (warp < 4) {
@@ -319,7 +344,7 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
           val = (float)ww[0] * U[(long long)rr[0] * r + q] + (float)ww[1] * U[(long long)rr[1] * r + q] +
                 (float)ww[2] * U[(long long)rr[2] * r + q];
         }
-        c[it] = val;
+        c[t * (r + 1) + q] = val;   // odd row stride (conflict-free reads across entries)
       }
     }
     __syncthreads();
