@@ -139,7 +139,8 @@ struct EigJob {
   double* V;
   double* work;  // 2 (SLAR_MAX_N+1)^2 doubles scratch
   int n;
-  double floor_rel;  // off-diagonals below floor_rel ||A||_F are not rotated
+  double floor_rel;     // off-diagonals below floor_rel ||A||_F are not rotated
+  double compress_rel;  // > 0: pivoted-Cholesky compression down to compress_rel x trace first
 };
 cudaError_t eig_batched(const EigJob* jobs_host, int njobs, EigJob* jobs_dev, cudaStream_t s);
 // Rank selection from descending eigenvalues: smallest k with tail sum <= thr2, k in [1, cap].

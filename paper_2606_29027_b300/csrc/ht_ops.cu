@@ -284,6 +284,10 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
     // and never below the FP64 rounding level
     const double noise = c->cfg.precision == SLAR_FP64 ? 1e-17 : (c->cfg.precision == SLAR_FP32 ? 1e-13 : 1e-9);
     jobs[nj].floor_rel = std::max(1e-17, std::min(noise, 1e-2 * eps * eps / (2.0 * d - 3.0)));
+    // FP32 / BF16x3 data: eigen-solve only the numerical range of the Gram matrix -- a
+    // pivoted Cholesky G ~ L L^T stopped when the trace left out is below 1/10 of the rank
+    // threshold eps^2/(2d-3) (relative to trace G = ||F||^2), then Jacobi on L^T L
+    jobs[nj].compress_rel = c->cfg.precision == SLAR_FP64 ? 0.0 : std::max(1e-16, 0.1 * eps * eps / (2.0 * d - 3.0));
     ++nj;
   }
   CK(eig_batched(jobs, nj, c->d_eig, s));

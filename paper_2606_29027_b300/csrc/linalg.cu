@@ -67,6 +67,53 @@ k_dgemm(int tA, int tB, int M, int N, int K, double alpha, const double* __restr
   }
 }
 
+// Small-output variant: T x T output tile per CTA, one output per thread.  The truncation's
+// GEMMs are mostly 64 x 64 or smaller: 32 x 32 tiles leave four CTAs on a GPU whose FP64
+// rate per SM is low, so smaller tiles spread the same work over 4-16 times more SMs.
+template <int T>
+__global__ void __launch_bounds__(T * T)
+k_dgemm_small(int tA, int tB, int M, int N, int K, double alpha, const double* __restrict__ A, int lda,
+              long long sA, const double* __restrict__ B, int ldb, long long sB, double beta,
+              double* __restrict__ C, int ldc, long long sC) {
+  __shared__ double As[GK][T + 1];
+  __shared__ double Bs[GK][T + 1];
+  const int bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int row0 = blockIdx.y * T, col0 = blockIdx.x * T;
+  const int tid = threadIdx.x;
+  const int tx = tid % T, ty = tid / T;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int it = tid; it < GK * T; it += T * T) {
+      int kk, mm;
+      if (tA) { mm = it % T; kk = it / T; } else { kk = it % GK; mm = it / GK; }
+      const int gm = row0 + mm, gk = k0 + kk;
+      double v = 0.0;
+      if (gm < M && gk < K) v = tA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+      As[kk][mm] = v;
+    }
+    for (int it = tid; it < GK * T; it += T * T) {
+      int kk, nn;
+      if (tB) { kk = it % GK; nn = it / GK; } else { nn = it % T; kk = it / T; }
+      const int gn = col0 + nn, gk = k0 + kk;
+      double v = 0.0;
+      if (gn < N && gk < K) v = tB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) acc += As[kk][ty] * Bs[kk][tx];
+    __syncthreads();
+  }
+  const int gm = row0 + ty, gn = col0 + tx;
+  if (gm < M && gn < N) {
+    double* c = C + (long long)gm * ldc + gn;
+    *c = alpha * acc + (beta == 0.0 ? 0.0 : beta * *c);
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // G = A^T A for a tall column-major A (m x n, n <= 64): each CTA reduces ROWS rows into a
 // partial n x n; a second kernel sums the partials in block order.
@@ -414,7 +461,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
   const EigJob job = jobs[blockIdx.x];
   const int n = job.n;
   const int tid = threadIdx.x;
-  if (false) {
+  if (job.compress_rel > 0.0 && n > 24) {
     double* L = smem;                                   // n x rt, column j at L + j n
     double* M = smem + SLAR_MAX_N * EIG_RTMAX;          // ne x ne
     double* Vs = M + EIG_RTMAX * EIG_RTMAX;             // ne x ne
@@ -428,7 +475,9 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
       rt_s = 0;
     }
     __syncthreads();
-    const double stop = 1e-16 * trace_s;
+    // stop once the trace left outside L L^T is at most compress_rel x trace: the eigenvalues
+    // dropped with it lie far below the rank threshold of the truncation
+    const double stop = job.compress_rel * trace_s;
     const int rtmax = n < EIG_RTMAX ? n : EIG_RTMAX;
     for (int j = 0; j < rtmax; ++j) {
       double best = -1.0;
@@ -453,7 +502,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
         dpiv_s = b;
       }
       __syncthreads();
-      if (!(dpiv_s > stop) || piv_s < 0) break;
+      if (!(dpiv_s > 0.0) || piv_s < 0) break;
       const int p = piv_s;
       const double inv = 1.0 / sqrt(dpiv_s);
       double* lj = L + j * n;
@@ -463,9 +512,23 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
         lj[i] = v * inv;
       }
       __syncthreads();
-      for (int i = tid; i < n; i += EIG_THREADS) dg[i] = (i == p) ? -1.0 : dg[i] - lj[i] * lj[i];
-      if (tid == 0) rt_s = j + 1;
+      double rem = 0.0;
+      for (int i = tid; i < n; i += EIG_THREADS) {
+        const double v = (i == p) ? -1.0 : dg[i] - lj[i] * lj[i];
+        dg[i] = v;
+        rem += fmax(v, 0.0);
+      }
+      for (int o = 16; o > 0; o >>= 1) rem += __shfl_down_sync(0xffffffffu, rem, o);
+      if ((tid & 31) == 0) wred[tid >> 5] = rem;
       __syncthreads();
+      if (tid == 0) {
+        rt_s = j + 1;
+        double t = 0.0;
+        for (int w = 0; w < EIG_THREADS / 32; ++w) t += wred[w];
+        dpiv_s = t;   // trace left outside L L^T
+      }
+      __syncthreads();
+      if (!(dpiv_s > stop)) break;
     }
     int rt = rt_s;
     const bool full = (rt == rtmax && rtmax < n && dpiv_s > stop);
@@ -608,8 +671,19 @@ cudaError_t dgemm(int tA, int tB, int M, int N, int K, double alpha, const doubl
                   long long sA, const double* B, int ldb, long long sB, double beta, double* C,
                   int ldc, long long sC, int batch, cudaStream_t s) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
-  dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, batch);
-  slar::count_launch(), k_dgemm<<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+  const long long tiles32 = (long long)((N + GT - 1) / GT) * ((M + GT - 1) / GT) * batch;
+  if (tiles32 >= 148) {
+    dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, batch);
+    slar::count_launch(), k_dgemm<<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+  } else if (4 * tiles32 >= 148) {
+    dim3 grid((N + 15) / 16, (M + 15) / 16, batch);
+    slar::count_launch(), k_dgemm_small<16><<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB,
+                                                                beta, C, ldc, sC);
+  } else {
+    dim3 grid((N + 7) / 8, (M + 7) / 8, batch);
+    slar::count_launch(), k_dgemm_small<8><<<grid, 64, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB,
+                                                              beta, C, ldc, sC);
+  }
   return cudaGetLastError();
 }
 
