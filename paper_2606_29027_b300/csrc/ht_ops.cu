@@ -263,7 +263,10 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
   bool warm[6] = {false, false, false, false, false, false};
   for (int m = 0; m < d; ++m) {
     const int nm = node_n[m];
-    if (nm < 16 || c->Sn[m] != nm) continue;
+    // (no warm start with the compressed eigen-solve of FP32 / BF16x3 data: its basis holds
+    // only the numerical range, and rotating the next Gram matrix into it would lose every
+    // new direction)
+    if (nm < 16 || c->Sn[m] != nm || c->cfg.precision != SLAR_FP64) continue;
     double* T = c->Sw + (size_t)m * SLAR_MAX_N * SLAR_MAX_N;
     CK(dgemm(0, 0, nm, nm, nm, 1.0, c->G[m], nm, 0, c->S[m], nm, 0, 0.0, T, nm, 0, 1, s));
     CK(dgemm(1, 0, nm, nm, nm, 1.0, c->S[m], nm, 0, T, nm, 0, 0.0, c->G[m], nm, 0, 1, s));
@@ -300,7 +303,7 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
       CK(cudaMemcpyAsync(c->S[m], c->ework[m], sizeof(double) * nm * nm, cudaMemcpyDeviceToDevice, s));
     }
   }
-  for (int t = 0; t < nnodes; ++t) c->Sn[t] = node_n[t];
+  for (int t = 0; t < nnodes; ++t) c->Sn[t] = c->cfg.precision == SLAR_FP64 ? node_n[t] : 0;
   // 3. ranks
   slar::count_launch(), k_trace<<<1, 32, 0, s>>>(c->G[d == 4 ? 4 : 0], node_n[d == 4 ? 4 : 0], c->norm2);
   CK(cudaGetLastError());

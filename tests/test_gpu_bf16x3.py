@@ -103,3 +103,20 @@ def test_tc_step_conserves_and_tracks_fp64():
 
 
 from paper_2606_29027_b300 import slar  # noqa: E402
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_reduced_precision_tracks_fp64_at_64(prec):
+    """The bench workload (2D2V weak Landau 64^4, eps 1e-5): 64-point leaves take the
+    compressed eigen-solve in FP32 / BF16x3 mode.  Their energy history stays with the FP64
+    path's to well inside the method's own truncation error on W (~eps / alpha = 1e-3)."""
+    w = inputs.landau_2d2v()
+    hist = {}
+    for p in ("fp64", prec):
+        c = slar.Context(slar.make_config(w, precision=p, solver="precond"))
+        c.init_ht(inputs.initial_factors(w))
+        hist[p] = np.array([c.step(w.dt).field_energy for _ in range(12)])
+        c.close()
+    err = np.max(np.abs(hist[prec] - hist["fp64"])) / np.max(hist["fp64"])
+    print(prec, "max |W - W_fp64| / max W", err)
+    assert err < 5e-4
