@@ -33,6 +33,9 @@ METRIC = "2D2V SLAR steps/s"
 UNIT = "steps/s"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2032 MHz
 FP64_PEAK_TFLOPS = 1.25                              # nominal B300 FP64 (recipe table)
+# DRAM bytes (read + write) per launch of the FP32 entry evaluator on this workload, from the
+# ncu launch list in profiles/launch_list_landau_2d2v_64.md (cold cache, one BDF3 step)
+EVAL_TRAFFIC_BYTES = 353.0e3
 
 
 def parse():
@@ -467,7 +470,10 @@ def run_ours(args, w):
             "guess_used_steps": int(sum(s.guess_used for s in stats)),
             "roofline": {"kernel": "k_sl_eval (SL entry evaluator)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": EVAL_TRAFFIC_BYTES if args.precision == "fp32" else None,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                                           "profiles/launch_list_landau_2d2v_64.md (cold cache)",
                          "peak_source": "measured in this run: FMA-chain kernel (slar_fma_peak), "
                                         "best of 3; derived FP32 148 SMs x 128 lanes x 2 x 2032 MHz = "
                                         f"{FP32_PEAK_TFLOPS:.1f}, nominal FP64 {FP64_PEAK_TFLOPS}",

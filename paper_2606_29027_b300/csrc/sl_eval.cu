@@ -31,6 +31,52 @@ struct Smem {
   int* rows;     // [TILE][4][3]
 };
 
+// Transfer tensors small enough for this byte budget are staged whole in shared memory
+// ([k][p], k = (a, b)) by the warps that do not trace feet, while the feet are traced;
+// larger ones stream through a [KC][PSTRIDE] chunk buffer.
+constexpr int RES_BYTES = 48 * 1024;
+
+template <typename T>
+__host__ __device__ __forceinline__ bool b_resident(int d, int r0, int r1, int r2, int r3, int r12, int r34) {
+  return d == 4 && (long long)(r0 * r1 * r12 + r2 * r3 * r34) * (long long)sizeof(T) <= RES_BYTES;
+}
+
+// c_out[t][p] = sum_{a,b} ca[t][a] cb[t][b] sB[(a,b)][p] with the whole transfer tensor resident
+template <typename T, int TILE>
+__device__ void contract_node_res(const T* __restrict__ ca, int ra, const T* __restrict__ cb, int rb,
+                                  const T* __restrict__ sBn, int rp, T* __restrict__ cout, int nT) {
+  constexpr int TPT = TILE / 8;
+  const int tid = threadIdx.x;
+  const int tg = tid >> 5, lane = tid & 31;
+  T acc[TPT][2];
+#pragma unroll
+  for (int i = 0; i < TPT; ++i) acc[i][0] = acc[i][1] = T(0);
+  int kk = 0;
+  for (int a = 0; a < ra; ++a) {
+    T xa[TPT];
+#pragma unroll
+    for (int i = 0; i < TPT; ++i) xa[i] = ca[(tg * TPT + i) * ra + a];
+    for (int b = 0; b < rb; ++b, ++kk) {
+      const T b0 = (lane < rp) ? sBn[kk * rp + lane] : T(0);
+      const T b1 = (lane + 32 < rp) ? sBn[kk * rp + lane + 32] : T(0);
+#pragma unroll
+      for (int i = 0; i < TPT; ++i) {
+        const T x = xa[i] * cb[(tg * TPT + i) * rb + b];
+        acc[i][0] += x * b0;
+        acc[i][1] += x * b1;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TPT; ++i) {
+    const int t = tg * TPT + i;
+    if (t < nT) {
+      if (lane < rp) cout[t * rp + lane] = acc[i][0];
+      if (lane + 32 < rp) cout[t * rp + lane + 32] = acc[i][1];
+    }
+  }
+}
+
 // c_out[t][p] = sum_{a,b} ca[t][a] cb[t][b] B[p][a][b]   for t < nT, p < rp
 template <typename T, int TILE>
 __device__ void contract_node(const T* __restrict__ ca, int ra, const T* __restrict__ cb, int rb,
@@ -94,7 +140,8 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
   double* sfoot = reinterpret_cast<double*>(smem_raw);        // TILE*4
   double* sw = sfoot + TILE * 4;                               // TILE*12
   double* sval = sw + TILE * 12;                               // TILE
-  int* srow = reinterpret_cast<int*>(sval + TILE);             // TILE*12
+  double* sres = sval + TILE;                                  // TILE residual sums
+  int* srow = reinterpret_cast<int*>(sres + TILE);             // TILE*12
   T* sc = reinterpret_cast<T*>(srow + TILE * 12);              // leaves
   T* sc_mu[4];
   {
@@ -105,6 +152,47 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
   T* sc12 = sc;
   T* sc34 = sc12 + (d == 4 ? TILE * ht.r12 : 0);
   T* sB = sc34 + (d == 4 ? TILE * ht.r34 : 0);
+  const bool resident = b_resident<T>(d, ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34);
+  const int K12 = ht.r[0] * ht.r[1];
+
+  // 0. work that does not need the feet, done by the other warps while they are traced:
+  // the cross-approximation residual sum_l X[pivot, l] Y[e, l] of each entry, and the
+  // resident transfer tensors
+  if (tid >= TILE) {
+    if (a.X && tid < 2 * TILE) {
+      const int t = tid - TILE;
+      double r = 0.0;
+      if (t < nT) {
+        const long long piv = (long long)(*a.pivot);
+        const long long e = e0 + t;
+        const int k = a.kterms;
+        int l = 0;
+        for (; l + 4 <= k; l += 4) {
+          const double y0 = a.Y[e + l * a.ldY], y1 = a.Y[e + (l + 1) * a.ldY];
+          const double y2 = a.Y[e + (l + 2) * a.ldY], y3 = a.Y[e + (l + 3) * a.ldY];
+          r += a.X[piv + l * a.ldX] * y0;
+          r += a.X[piv + (l + 1) * a.ldX] * y1;
+          r += a.X[piv + (l + 2) * a.ldX] * y2;
+          r += a.X[piv + (l + 3) * a.ldX] * y3;
+        }
+        for (; l < k; ++l) r += a.X[piv + l * a.ldX] * a.Y[e + l * a.ldY];
+      }
+      sres[t] = r;
+    }
+    if (resident) {
+      const int n12 = K12 * ht.r12, n34 = ht.r[2] * ht.r[3] * ht.r34;
+      for (int it = tid - TILE; it < n12 + n34; it += NTHREADS - TILE) {
+        if (it < n12) {
+          const int p = it / K12, k = it - p * K12;
+          sB[k * ht.r12 + p] = ht.B12[it];
+        } else {
+          const int j = it - n12, K34 = ht.r[2] * ht.r[3];
+          const int p = j / K34, k = j - p * K34;
+          sB[n12 + k * ht.r34 + p] = ht.B34[j];
+        }
+      }
+    }
+  }
 
   // 1. feet and weights
   if (tid < nT) {
@@ -158,8 +246,13 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
   const T* right;
   int rl, rr;
   if (d == 4) {
-    contract_node<T, TILE>(sc_mu[0], ht.r[0], sc_mu[1], ht.r[1], ht.B12, ht.r12, sc12, sB, nT);
-    contract_node<T, TILE>(sc_mu[2], ht.r[2], sc_mu[3], ht.r[3], ht.B34, ht.r34, sc34, sB, nT);
+    if (resident) {
+      contract_node_res<T, TILE>(sc_mu[0], ht.r[0], sc_mu[1], ht.r[1], sB, ht.r12, sc12, nT);
+      contract_node_res<T, TILE>(sc_mu[2], ht.r[2], sc_mu[3], ht.r[3], sB + K12 * ht.r12, ht.r34, sc34, nT);
+    } else {
+      contract_node<T, TILE>(sc_mu[0], ht.r[0], sc_mu[1], ht.r[1], ht.B12, ht.r12, sc12, sB, nT);
+      contract_node<T, TILE>(sc_mu[2], ht.r[2], sc_mu[3], ht.r[3], ht.B34, ht.r34, sc34, sB, nT);
+    }
     left = sc12; right = sc34; rl = ht.r12; rr = ht.r34;
   } else {
     left = sc_mu[0]; right = sc_mu[1]; rl = ht.r[0]; rr = ht.r[1];
@@ -190,11 +283,7 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
     double val = sval[tid];
     if (corr.has) val += correction_at(g, corr, sfoot + tid * 4);
     const long long e = e0 + tid;
-    if (a.X) {
-      const int k = a.kterms;
-      const long long piv = (long long)(*a.pivot);
-      for (int l = 0; l < k; ++l) val -= a.X[piv + l * a.ldX] * a.Y[e + l * a.ldY];
-    }
+    if (a.X) val -= sres[tid];
     a.out[e] = val;
   }
 }
@@ -217,11 +306,16 @@ k_sl_eval_dev(GridDesc g, const EvalParams<T>* __restrict__ P, EvalArgs a) {
 
 template <typename T, int TILE>
 size_t smem_bytes(const GridDesc& g, const HTView<T>& ht) {
-  size_t b = sizeof(double) * (TILE * 4 + TILE * 12 + TILE) + sizeof(int) * TILE * 12;
+  size_t b = sizeof(double) * (TILE * 4 + TILE * 12 + TILE + TILE) + sizeof(int) * TILE * 12;
   int rs = 0;
   for (int m = 0; m < g.d; ++m) rs += ht.r[m];
   if (g.d == 4) rs += ht.r12 + ht.r34;
-  b += sizeof(T) * ((size_t)TILE * rs + (g.d == 4 ? KC * PSTRIDE : 0));
+  size_t nb = 0;
+  if (g.d == 4)
+    nb = b_resident<T>(g.d, ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34)
+             ? (size_t)ht.r[0] * ht.r[1] * ht.r12 + (size_t)ht.r[2] * ht.r[3] * ht.r34
+             : (size_t)KC * PSTRIDE;
+  b += sizeof(T) * ((size_t)TILE * rs + nb);
   return (b + 15) & ~size_t(15);
 }
 
