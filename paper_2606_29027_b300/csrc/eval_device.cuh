@@ -164,5 +164,152 @@ __device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& 
   }
 }
 
+
+// ---- FP32 variants (FP32 / BF16x3 entry paths): the same formulas in single precision.
+// Their feet can differ from the FP64 ones by ~1e-7 relative, which moves an entry to the
+// neighbouring stencil only when its foot lies within that distance of a cell face (the two
+// stencils then differ by O(Delta^3)); the entries are only required to agree with FP64 to
+// the FP32 tolerance.
+
+__device__ __forceinline__ void cell_weights_f(const GridDesc& g, int m, float y, int rows[3], float w[3]) {
+  float t = (y - (float)g.lo[m]) / (float)g.h[m];
+  if (!(fabsf(t) < 1e15f)) t = 0.f;
+  const float jf = floorf(t);
+  const float xi = t - jf - 0.5f;
+  const float hx = 0.5f * xi;
+  w[0] = hx * (xi - 1.f);
+  w[1] = 1.f - xi * xi;
+  w[2] = hx * (xi + 1.f);
+  const int n = g.N[m];
+  long long r0 = ((long long)jf - 1) % n;
+  if (r0 < 0) r0 += n;
+  rows[0] = (int)r0;
+  rows[1] = (int)((r0 + 1) % n);
+  rows[2] = (int)((r0 + 2) % n);
+}
+
+// both (dx) components of a spatial vector field at p, one set of weights
+__device__ void interp_vec_f(const GridDesc& g, const double* F, const float* p, float* out) {
+  int r0[3], r1[3];
+  float w0[3], w1[3];
+  cell_weights_f(g, 0, p[0], r0, w0);
+  const long long NX = g.NX;
+  if (g.dx == 1) {
+    for (int c = 0; c < g.dx; ++c) {
+      const double* Fc = F + c * NX;
+      out[c] = w0[0] * (float)Fc[r0[0]] + w0[1] * (float)Fc[r0[1]] + w0[2] * (float)Fc[r0[2]];
+    }
+    return;
+  }
+  cell_weights_f(g, 1, p[1], r1, w1);
+  const int N1 = g.N[1];
+  float acc[2] = {0.f, 0.f};
+#pragma unroll
+  for (int s0 = 0; s0 < 3; ++s0)
+#pragma unroll
+    for (int s1 = 0; s1 < 3; ++s1) {
+      const float ww = w0[s0] * w1[s1];
+      const long long o = (long long)r0[s0] * N1 + r1[s1];
+      acc[0] += ww * (float)F[o];
+      acc[1] += ww * (float)F[NX + o];
+    }
+  out[0] = acc[0];
+  out[1] = acc[1];
+}
+
+__device__ __forceinline__ float centre_f(const GridDesc& g, int m, int i) {
+  return (float)g.lo[m] + ((float)i + 0.5f) * (float)g.h[m];
+}
+
+// backward foot of the frozen-field characteristic (Kutta RK3 or first order), FP32
+__device__ void trace_foot_f(const GridDesc& g, const double* E, double tau_d, int euler, const int* idx,
+                             float* foot) {
+  const int dx = g.dx;
+  const float tau = (float)tau_d;
+  float x[2], v[2], e[2];
+  for (int m = 0; m < dx; ++m) {
+    x[m] = centre_f(g, m, idx[m]);
+    v[m] = centre_f(g, dx + m, idx[dx + m]);
+  }
+  if (euler) {
+    interp_vec_f(g, E, x, e);
+    for (int m = 0; m < dx; ++m) {
+      foot[m] = x[m] - v[m] * tau;
+      foot[dx + m] = v[m] + e[m] * tau;
+    }
+    return;
+  }
+  const float half = 0.5f * tau, two_h = 2.f * tau, sixth = tau / 6.f;
+  float k1v[2], k2x[2], k2v[2], k3v[2], x2[2], x3[2], v3[2];
+  interp_vec_f(g, E, x, k1v);
+  for (int m = 0; m < dx; ++m) {
+    x2[m] = x[m] - half * v[m];
+    k2x[m] = -(v[m] + half * k1v[m]);
+  }
+  interp_vec_f(g, E, x2, k2v);
+  for (int m = 0; m < dx; ++m) {
+    x3[m] = x[m] + tau * v[m] + two_h * k2x[m];
+    v3[m] = v[m] - tau * k1v[m] + two_h * k2v[m];
+  }
+  interp_vec_f(g, E, x3, k3v);
+  for (int m = 0; m < dx; ++m) {
+    foot[m] = x[m] + sixth * ((-v[m]) + 4.f * k2x[m] + (-v3[m]));
+    foot[dx + m] = v[m] + sixth * (k1v[m] + 4.f * k2v[m] + k3v[m]);
+  }
+}
+
+__device__ __forceinline__ float interp_1d_f(const GridDesc& g, int m, const double* vec, float y) {
+  int r[3];
+  float w[3];
+  cell_weights_f(g, m, y, r, w);
+  return w[0] * (float)vec[r[0]] + w[1] * (float)vec[r[1]] + w[2] * (float)vec[r[2]];
+}
+
+// separable LoMaC correction at a foot, FP32
+__device__ float correction_at_f(const GridDesc& g, const CorrView& c, const float* foot) {
+  const int dx = g.dx, dv = g.dv;
+  const long long NX = g.NX;
+  const int Nv = g.N[dx];
+  float dCi[4];
+  {
+    int r0[3], r1[3];
+    float w0[3], w1[3];
+    cell_weights_f(g, 0, foot[0], r0, w0);
+    if (dx == 2) cell_weights_f(g, 1, foot[1], r1, w1);
+    for (int k = 0; k < dv + 2; ++k) {
+      const double* F = c.dC + k * NX;
+      float acc = 0.f;
+      if (dx == 1) {
+        for (int s0 = 0; s0 < 3; ++s0) acc += w0[s0] * (float)F[r0[s0]];
+      } else {
+        for (int s0 = 0; s0 < 3; ++s0)
+          for (int s1 = 0; s1 < 3; ++s1) acc += w0[s0] * w1[s1] * (float)F[(long long)r0[s0] * g.N[1] + r1[s1]];
+      }
+      dCi[k] = acc;
+    }
+  }
+  float om[2], q1[2], q2[2];
+  for (int m = 0; m < dv; ++m) {
+    const float y = foot[dx + m];
+    om[m] = interp_1d_f(g, dx + m, c.qv + (0 * dv + m) * Nv, y);
+    q1[m] = interp_1d_f(g, dx + m, c.qv + (1 * dv + m) * Nv, y);
+    q2[m] = interp_1d_f(g, dx + m, c.qv + (2 * dv + m) * Nv, y);
+  }
+  float out = 0.f, t = dCi[0];
+  for (int m = 0; m < dv; ++m) t *= om[m];
+  out += t;
+  for (int j = 0; j < dv; ++j) {
+    t = dCi[1 + j];
+    for (int m = 0; m < dv; ++m) t *= (m == j ? q1[m] : om[m]);
+    out += t;
+  }
+  for (int j = 0; j < dv; ++j) {
+    t = dCi[1 + dv];
+    for (int m = 0; m < dv; ++m) t *= (m == j ? q2[m] : om[m]);
+    out += t;
+  }
+  return out;
+}
+
 }  // namespace
 }  // namespace slar

@@ -5,8 +5,10 @@
 //   1. foot: backward characteristic of the frozen-field advection through the entry's grid
 //      point (Kutta RK3 on dz/ds = (-v, E(x)), E interpolated with the tensor-product
 //      quadratic weights; or the first-order foot), then per dimension the cell j and the
-//      weights w(xi) of Eq. 1d_quadratic_interp_weight.  Always FP64; written with explicit
-//      round-to-nearest intrinsics (no FMA contraction) so the cell choice is reproducible.
+//      weights w(xi) of Eq. 1d_quadratic_interp_weight.  FP64 path: explicit round-to-nearest
+//      intrinsics (no FMA contraction) so the cell choice reproduces the FP64 oracle's; FP32
+//      path: the same formulas in FP32 (B300's FP64 rate per SM sub-partition made the FP64
+//      foot the longest phase of a low-rank FP32 evaluation).
 //   2. leaf gathers c^(mu) = w . U^(mu)[j-1..j+1, :]  (coalesced row loads, staged in smem)
 //   3. transfer-tensor contractions c12 = B12 x1 c0 x2 c1 (a [TILE x r0 r1] x [r0 r1 x r12]
 //      product whose left operand -- the outer products c0 (x) c1 -- is formed on the fly),
@@ -194,8 +196,34 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
     }
   }
 
-  // 1. feet and weights
-  if (tid < nT) {
+  // 1. feet and weights (FP32 entries: traced in FP32, see eval_device.cuh)
+  if constexpr (sizeof(T) == 4) {
+    if (tid < nT) {
+      int idx[4];
+      decode_tuple(g, a, e0 + tid, idx);
+      float foot[4];
+      if (at_grid) {
+        for (int m = 0; m < d; ++m) foot[m] = centre_f(g, m, idx[m]);
+      } else {
+        trace_foot_f(g, a.E, a.tau, a.foot_euler, idx, foot);
+      }
+      for (int m = 0; m < d; ++m) {
+        int r[3];
+        float w[3];
+        if (at_grid) {
+          r[0] = idx[m]; r[1] = idx[m]; r[2] = idx[m];
+          w[0] = 0.f; w[1] = 1.f; w[2] = 0.f;
+        } else {
+          cell_weights_f(g, m, foot[m], r, w);
+        }
+        for (int s = 0; s < 3; ++s) {
+          srow[(tid * 4 + m) * 3 + s] = r[s];
+          sw[(tid * 4 + m) * 3 + s] = w[s];
+        }
+        sfoot[tid * 4 + m] = foot[m];
+      }
+    }
+  } else if (tid < nT) {
     int idx[4];
     decode_tuple(g, a, e0 + tid, idx);
     double foot[4];
@@ -281,7 +309,15 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
   // 5. correction and residual epilogue
   if (tid < nT) {
     double val = sval[tid];
-    if (corr.has) val += correction_at(g, corr, sfoot + tid * 4);
+    if (corr.has) {
+      if constexpr (sizeof(T) == 4) {
+        float f4[4];
+        for (int m = 0; m < d; ++m) f4[m] = (float)sfoot[tid * 4 + m];
+        val += (double)correction_at_f(g, corr, f4);
+      } else {
+        val += correction_at(g, corr, sfoot + tid * 4);
+      }
+    }
     const long long e = e0 + tid;
     if (a.X) val -= sres[tid];
     a.out[e] = val;

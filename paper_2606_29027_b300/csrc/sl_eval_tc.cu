@@ -5,7 +5,7 @@
 // Trees with d = 4 only (a d = 2 tree has no transfer tensor).
 //
 // One CTA evaluates 128 entries (the MMA's M):
-//   1. feet and quadratic weights (FP64, shared with the SIMT evaluator),
+//   1. feet and quadratic weights (FP32, shared with the FP32 SIMT evaluator),
 //   2. leaf gathers c^(mu) (FP32) for the two children of the node,
 //   3. c_t[e][p] = sum_k KR[e][k] B_t[p][k], k = (a, b), KR[e][(a,b)] = c1[e][a] c2[e][b]:
 //      a [128 x K] x [K x N] GEMM.  Per K-chunk of 64 the CTA writes KR (hi, lo) into
@@ -312,12 +312,12 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   if (tid < nT) {
     int idx[4];
     decode_tuple(g, a, e0 + tid, idx);
-    double foot[4];
-    trace_foot(g, a.E, a.tau, a.foot_euler, idx, foot);
+    float foot[4];
+    trace_foot_f(g, a.E, a.tau, a.foot_euler, idx, foot);
     for (int m = 0; m < d; ++m) {
       int r[3];
-      double w[3];
-      cell_weights(g, m, foot[m], r, w);
+      float w[3];
+      cell_weights_f(g, m, foot[m], r, w);
       for (int s = 0; s < 3; ++s) {
         srow[(tid * 4 + m) * 3 + s] = r[s];
         sw[(tid * 4 + m) * 3 + s] = w[s];
@@ -376,7 +376,11 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     // 5. correction and residual epilogue
     if (tid < nT) {
       double val = sval[tid];
-      if (corr.has) val += correction_at(g, corr, sfoot + tid * 4);
+      if (corr.has) {
+        float f4[4];
+        for (int m = 0; m < d; ++m) f4[m] = (float)sfoot[tid * 4 + m];
+        val += (double)correction_at_f(g, corr, f4);
+      }
       const long long e = e0 + tid;
       if (a.X) {
         const long long piv = (long long)(*a.pivot);

@@ -54,34 +54,29 @@ __device__ void smem_fft_lines(double2* buf, int n, int logn, int nl, int ls, in
 }
 
 // LPB lines of length n per CTA: gather (element stride es, line stride ls) into shared
-// memory, transform, scatter.  Batch along blockIdx.y with stride bs.
-__global__ void k_fft_lines(double2* data, int n, int logn, long long es, long long ls, long long bs,
+// memory, transform, scatter.  Batch along blockIdx.y with stride bs.  With rin the lines are
+// read from a real array of the same layout (imaginary part 0); with rout only the real part,
+// times scale, is written, to a real array of the same layout.
+__global__ void k_fft_lines(double2* data, const double* __restrict__ rin, double* __restrict__ rout,
+                            double scale, int n, int logn, long long es, long long ls, long long bs,
                             int nlines, int lpb, const double2* tw, int inverse) {
   extern __shared__ double2 buf[];
   const int l0 = blockIdx.x * lpb;
   const int nl = min(lpb, nlines - l0);
-  double2* base = data + blockIdx.y * bs;
+  const long long boff = blockIdx.y * bs;
   for (int it = threadIdx.x; it < nl * n; it += blockDim.x) {
     const int l = it / n, i = it - l * n;
-    buf[l * n + i] = base[(l0 + l) * ls + i * es];
+    const long long off = boff + (l0 + l) * ls + i * es;
+    buf[l * n + i] = rin ? make_double2(rin[off], 0.0) : data[off];
   }
   __syncthreads();
   smem_fft_lines(buf, n, logn, nl, n, 1, tw, inverse);
   for (int it = threadIdx.x; it < nl * n; it += blockDim.x) {
     const int l = it / n, i = it - l * n;
-    base[(l0 + l) * ls + i * es] = buf[l * n + i];
+    const long long off = boff + (l0 + l) * ls + i * es;
+    if (rout) rout[off] = buf[l * n + i].x * scale;
+    else data[off] = buf[l * n + i];
   }
-}
-
-__global__ void k_real_to_cplx(const double* __restrict__ f, double2* __restrict__ z, long long n) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) z[i] = make_double2(f[i], 0.0);
-}
-
-__global__ void k_cplx_to_real(const double2* __restrict__ z, double* __restrict__ f, long long n,
-                               double scale) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) f[i] = z[i].x * scale;
 }
 
 }  // namespace
@@ -127,35 +122,35 @@ void Spectral::release() {
   }
 }
 
-cudaError_t Spectral::fft(double2* z, int batch, int inverse) const {
+// passes of a batched 1D / 2D transform; the first may read real input, the last may write
+// the scaled real part
+static cudaError_t fft_passes(const Spectral& sp, double2* z, const double* rin, double* rout, double scale,
+                              int batch, int inverse) {
   // 4 lines per CTA (64 threads each) keeps many CTAs in flight for batches of 64^2 fields
-  auto pass = [&](int len, int lg, long long es, long long ls, int nlines, const double2* tw) {
+  auto pass = [&](int len, int lg, long long es, long long ls, int nlines, const double2* tw, const double* ri,
+                  double* ro) {
     const int lpb = 4;
     dim3 grid((nlines + lpb - 1) / lpb, batch);
-    slar::count_launch(), k_fft_lines<<<grid, 128, sizeof(double2) * lpb * len, s>>>(
-        z, len, lg, es, ls, NX, nlines, lpb, tw, inverse);
+    slar::count_launch(), k_fft_lines<<<grid, 128, sizeof(double2) * lpb * len, sp.s>>>(
+        z, ri, ro, scale, len, lg, es, ls, sp.NX, nlines, lpb, tw, inverse);
     return cudaGetLastError();
   };
-  if (dx == 1) return pass(n[0], logn[0], 1, n[0], 1, twid[0]);
-  cudaError_t e = pass(n[1], logn[1], 1, n[1], n[0], twid[1]);    // rows (along x2)
+  if (sp.dx == 1) return pass(sp.n[0], sp.logn[0], 1, sp.n[0], 1, sp.twid[0], rin, rout);
+  cudaError_t e = pass(sp.n[1], sp.logn[1], 1, sp.n[1], sp.n[0], sp.twid[1], rin, nullptr);   // rows (x2)
   if (e != cudaSuccess) return e;
-  return pass(n[0], logn[0], n[1], 1, n[1], twid[0]);             // columns (along x1)
+  return pass(sp.n[0], sp.logn[0], sp.n[1], 1, sp.n[1], sp.twid[0], nullptr, rout);          // columns (x1)
+}
+
+cudaError_t Spectral::fft(double2* z, int batch, int inverse) const {
+  return fft_passes(*this, z, nullptr, nullptr, 1.0, batch, inverse);
 }
 
 cudaError_t Spectral::forward(const double* f, double2* z, int batch) const {
-  const long long tot = (long long)batch * NX;
-  slar::count_launch(), k_real_to_cplx<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(f, z, tot);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return fft(z, batch, 0);
+  return fft_passes(*this, z, f, nullptr, 1.0, batch, 0);
 }
 
 cudaError_t Spectral::inverse(double2* z, double* f, int batch) const {
-  cudaError_t e = fft(z, batch, 1);
-  if (e != cudaSuccess) return e;
-  const long long tot = (long long)batch * NX;
-  slar::count_launch(), k_cplx_to_real<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(z, f, tot, 1.0 / NX);
-  return cudaGetLastError();
+  return fft_passes(*this, z, nullptr, f, 1.0 / NX, batch, 1);
 }
 
 }  // namespace slar

@@ -18,7 +18,8 @@ struct Spectral {
   void release();
   // in-place batched complex FFT of `batch` spatial fields (inverse unscaled)
   cudaError_t fft(double2* z, int batch, int inverse) const;
-  // real fields -> spectra / spectra -> real fields (inverse scaled by 1/NX)
+  // real fields -> spectra / spectra -> real fields (inverse scaled by 1/NX; z is used as
+  // scratch and holds no defined values afterwards)
   cudaError_t forward(const double* f, double2* z, int batch) const;
   cudaError_t inverse(double2* z, double* f, int batch) const;
 };
