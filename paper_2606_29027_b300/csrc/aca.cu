@@ -31,19 +31,20 @@ constexpr double TIE_RTOL = 1e-10;
 __device__ void block_argmax_tie(const double* a, int n, const unsigned char* used, int* out_idx,
                                  double* out_max) {
   // two passes: global max of |a| over unused, then the lowest index within the tie band
-  __shared__ double wmax[PIV_THREADS / 32];
-  __shared__ int widx[PIV_THREADS / 32];
+  __shared__ double wmax[32];
+  __shared__ int widx[32];
+  const int nthr = blockDim.x, nw = blockDim.x >> 5;
   __shared__ double top_s;
   const int tid = threadIdx.x;
   double m = -1.0;
-  for (int i = tid; i < n; i += PIV_THREADS)
+  for (int i = tid; i < n; i += nthr)
     if (!used[i]) m = fmax(m, fabs(a[i]));
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((tid & 31) == 0) wmax[tid >> 5] = m;
   __syncthreads();
   if (tid == 0) {
     double t = -1.0;
-    for (int w = 0; w < PIV_THREADS / 32; ++w) t = fmax(t, wmax[w]);
+    for (int w = 0; w < nw; ++w) t = fmax(t, wmax[w]);
     top_s = t;
   }
   __syncthreads();
@@ -51,14 +52,14 @@ __device__ void block_argmax_tie(const double* a, int n, const unsigned char* us
   const double thr = top * (1.0 - TIE_RTOL);
   int best = 0x7fffffff;
   if (top >= 0.0)
-    for (int i = tid; i < n; i += PIV_THREADS)
+    for (int i = tid; i < n; i += nthr)
       if (!used[i] && fabs(a[i]) >= thr && i < best) best = i;
   for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, o));
   if ((tid & 31) == 0) widx[tid >> 5] = best;
   __syncthreads();
   if (tid == 0) {
     int b = 0x7fffffff;
-    for (int w = 0; w < PIV_THREADS / 32; ++w) b = min(b, widx[w]);
+    for (int w = 0; w < nw; ++w) b = min(b, widx[w]);
     *out_idx = (top >= 0.0 && b != 0x7fffffff) ? b : -1;
     *out_max = top;
   }
@@ -109,59 +110,9 @@ k_aca_row_pivot(const double* __restrict__ r, int M2, unsigned char* usedc, int*
   }
 }
 
-// partial dot products of u_k with U_l (l < kk) and itself, v_k with V_l and itself
-__global__ void __launch_bounds__(256)
-k_aca_dots(const double* __restrict__ Ua, int M1, const double* __restrict__ Va, int M2,
-           int nbu, const AcaState* st, double* __restrict__ part, int ldp) {
-  if (st->done) return;
-  const int kk = st->k;
-  const int blk = blockIdx.x;
-  const bool isu = blk < nbu;
-  const double* X = isu ? Ua : Va;
-  const int M = isu ? M1 : M2;
-  const int s0 = (isu ? blk : blk - nbu) * DOT_SEG;
-  const double* xk = X + (long long)kk * M;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int l = warp; l <= kk; l += 8) {
-    const double* xl = X + (long long)l * M;
-    double acc = 0.0;
-    for (int i = s0 + lane; i < s0 + DOT_SEG && i < M; i += 32) acc += xl[i] * xk[i];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) part[(long long)blk * ldp + l] = acc;
-  }
-}
-
-// check-row residuals R_c -= u_k[row_c] v_k and their squared norms (one CTA per row)
-__global__ void __launch_bounds__(256)
-k_aca_check(const double* __restrict__ Ua, int M1, const double* __restrict__ Va, int M2,
-            const int* __restrict__ rows, double* __restrict__ R, double* __restrict__ n2,
-            const AcaState* st) {
-  __shared__ double red[8];
-  if (st->done || st->replay) return;
-  const int kk = st->k;
-  const int c = blockIdx.x;
-  const double a = Ua[(long long)kk * M1 + rows[c]];
-  const double* v = Va + (long long)kk * M2;
-  double* r = R + (long long)c * M2;
-  double s = 0.0;
-  for (int e = threadIdx.x; e < M2; e += 256) {
-    const double t = r[e] - a * v[e];
-    r[e] = t;
-    s += t * t;
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += red[w];
-    n2[c] = t;
-  }
-}
-
-// norm estimate, stop test (confirmed on the check rows), next row pivot
-__global__ void __launch_bounds__(PIV_THREADS)
-k_aca_finalize(const double* __restrict__ Ua, int M1, int kmax, int nbu, int nbv,
+// norm estimate, stop test (confirmed on the check rows), next row pivot; run by the last
+// block of k_aca_post (partial sums and check-row norms are read through L2)
+__device__ void aca_finalize_body(const double* __restrict__ Ua, int M1, int kmax, int nbu, int nbv,
                const double* __restrict__ part, int ldp, AcaState* st, int* pivI,
                unsigned char* usedr, int n_chk, const int* __restrict__ chk_rows,
                const double* __restrict__ chk_n2, cudaGraphConditionalHandle loop, int use_cond) {
@@ -171,18 +122,14 @@ k_aca_finalize(const double* __restrict__ Ua, int M1, int kmax, int nbu, int nbv
   __shared__ int stop_s;
   __shared__ int next_s;
   const int tid = threadIdx.x;
-  if (st->done) {
-    if (tid == 0) if (use_cond) cudaGraphSetConditional(loop, 0);
-    return;
-  }
   const int kk = st->k;
   const int replay = st->replay;
   const double eps = st->eps;
   __syncthreads();
   if (tid <= kk) {
     double a = 0.0, b = 0.0;
-    for (int blk = 0; blk < nbu; ++blk) a += part[(long long)blk * ldp + tid];
-    for (int blk = nbu; blk < nbu + nbv; ++blk) b += part[(long long)blk * ldp + tid];
+    for (int blk = 0; blk < nbu; ++blk) a += __ldcg(part + (long long)blk * ldp + tid);
+    for (int blk = nbu; blk < nbu + nbv; ++blk) b += __ldcg(part + (long long)blk * ldp + tid);
     du[tid] = a;
     dv[tid] = b;
   }
@@ -202,12 +149,16 @@ k_aca_finalize(const double* __restrict__ Ua, int M1, int kmax, int nbu, int nbv
       stop = 1;
       if (n_chk > 0) {
         double sum = 0.0;
-        for (int q = 0; q < n_chk; ++q) sum += chk_n2[q];
+        double n2c[8];
+        for (int q = 0; q < n_chk; ++q) {
+          n2c[q] = __ldcg(chk_n2 + q);
+          sum += n2c[q];
+        }
         if ((double)M1 / n_chk * sum > eps * eps * n2) {
           // the residual elsewhere is too large: continue from the worst unused check row
           int best = -1;
           for (int q = 0; q < n_chk; ++q)
-            if (!usedr[chk_rows[q]] && (best < 0 || chk_n2[q] > chk_n2[best])) best = q;
+            if (!usedr[chk_rows[q]] && (best < 0 || n2c[q] > n2c[best])) best = q;
           if (best >= 0) {
             stop = 0;
             next = chk_rows[best];
@@ -252,6 +203,66 @@ k_aca_finalize(const double* __restrict__ Ua, int M1, int kmax, int nbu, int nbv
       if (use_cond) cudaGraphSetConditional(loop, 1);
     }
   }
+}
+
+// One kernel after the column fibre: blocks [0, nbu + nbv) form the partial dot products of
+// u_k with U_l and of v_k with V_l (l <= k), blocks [nbu + nbv, + n_chk) update the check-row
+// residuals; the last block to finish (atomic ticket after a fence) runs the finalize step.
+__global__ void __launch_bounds__(256)
+k_aca_post(const double* __restrict__ Ua, int M1, const double* __restrict__ Va, int M2, int kmax, int nbu,
+           int nbv, double* __restrict__ part, int ldp, AcaState* st, int* pivI, unsigned char* usedr, int n_chk,
+           const int* __restrict__ chk_rows, double* __restrict__ chk_R, double* __restrict__ chk_n2,
+           cudaGraphConditionalHandle loop, int use_cond) {
+  __shared__ double red[8];
+  __shared__ int s_last;
+  if (st->done) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && use_cond) cudaGraphSetConditional(loop, 0);
+    return;
+  }
+  const int kk = st->k;
+  const int blk = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (blk < nbu + nbv) {
+    const bool isu = blk < nbu;
+    const double* X = isu ? Ua : Va;
+    const int M = isu ? M1 : M2;
+    const int s0 = (isu ? blk : blk - nbu) * DOT_SEG;
+    const double* xk = X + (long long)kk * M;
+    for (int l = warp; l <= kk; l += 8) {
+      const double* xl = X + (long long)l * M;
+      double acc = 0.0;
+      for (int i = s0 + lane; i < s0 + DOT_SEG && i < M; i += 32) acc += xl[i] * xk[i];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) part[(long long)blk * ldp + l] = acc;
+    }
+  } else if (!st->replay) {
+    const int c = blk - nbu - nbv;
+    const double a = Ua[(long long)kk * M1 + chk_rows[c]];
+    const double* v = Va + (long long)kk * M2;
+    double* r = chk_R + (long long)c * M2;
+    double sq = 0.0;
+    for (int e = threadIdx.x; e < M2; e += 256) {
+      const double t = r[e] - a * v[e];
+      r[e] = t;
+      sq += t * t;
+    }
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+    if (lane == 0) red[warp] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      chk_n2[c] = t;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->post_ctr, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) st->post_ctr = 0;
+  aca_finalize_body(Ua, M1, kmax, nbu, nbv, part, ldp, st, pivI, usedr, n_chk, chk_rows, chk_n2, loop, use_cond);
 }
 
 }  // namespace
@@ -308,13 +319,9 @@ slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int
     if (pass == 0)
       slar::count_launch(), k_aca_row_pivot<<<1, PIV_THREADS, 0, s>>>(c->rowbuf, M2, c->usedc, c->pivJ, c->ast, c->Va);
   }
-  if (c->n_chk > 0)
-    slar::count_launch(), k_aca_check<<<c->n_chk, 256, 0, s>>>(c->Ua, M1, c->Va, M2, c->chk_rows, c->chk_R,
-                                                               c->chk_n2, c->ast);
-  slar::count_launch(), k_aca_dots<<<nbu + nbv, 256, 0, s>>>(c->Ua, M1, c->Va, M2, nbu, c->ast, c->aca_part, ldp);
-  slar::count_launch(), k_aca_finalize<<<1, PIV_THREADS, 0, s>>>(c->Ua, M1, c->kmax, nbu, nbv, c->aca_part, ldp,
-                                                                c->ast, c->pivI, c->usedr, c->n_chk, c->chk_rows,
-                                                                c->chk_n2, h, use_cond);
+  slar::count_launch(), k_aca_post<<<nbu + nbv + c->n_chk, 256, 0, s>>>(
+      c->Ua, M1, c->Va, M2, c->kmax, nbu, nbv, c->aca_part, ldp, c->ast, c->pivI, c->usedr, c->n_chk, c->chk_rows,
+      c->chk_R, c->chk_n2, h, use_cond);
   CK(cudaGetLastError());
   return SLAR_OK;
 }

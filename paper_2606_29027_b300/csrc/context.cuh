@@ -38,6 +38,7 @@ struct AcaState {
   double nv2;     // ||v_k||^2
   double eps;     // stopping tolerance
   int tc_err;     // set by the tensor-core evaluator if an MMA completion wait ran out
+  unsigned int post_ctr;  // block tickets of k_aca_post (reset by its last block)
 };
 
 }  // namespace slar
