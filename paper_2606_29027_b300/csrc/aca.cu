@@ -25,6 +25,7 @@ namespace slar {
 namespace {
 
 constexpr int PIV_THREADS = 1024;
+constexpr int ACA_UNROLL = 2;      // pivot steps per iteration of the captured WHILE loop
 constexpr int DOT_SEG = 256;
 constexpr double TIE_RTOL = 1e-10;
 
@@ -350,7 +351,9 @@ slar_status build_aca_graph(slar_ctx* c, size_t smem) {
   CK(cudaGraphAddNode(&cn, gl, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  CKS(aca_step(c, smem, h, 1, false));
+  // two pivot steps per loop iteration: the second one's kernels exit at once when the first
+  // has stopped the approximation (device flag), and both report the stop to the WHILE node
+  for (int u = 0; u < ACA_UNROLL; ++u) CKS(aca_step(c, smem, h, 1, false));
   cudaGraph_t body_out;
   CK(cudaStreamEndCapture(s, &body_out));
   CK(cudaGraphInstantiate(&c->aca_graph, gl, 0));
@@ -515,7 +518,7 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
   const int k = c->ast_host->k;
   if (c->ast_host->tc_err)
     return set_error(c, SLAR_ETIMEOUT, "tensor-core evaluator: an MMA completion wait ran out");
-  if (!prof) add_launches(c->aca_graph_nodes * (long long)(k + c->ast_host->stop_row));
+  if (!prof) add_launches(c->aca_graph_nodes * (long long)((k + c->ast_host->stop_row + ACA_UNROLL - 1) / ACA_UNROLL));
   if (aca_rank) *aca_rank = k;
   const long long nent = (long long)k * (M1 + M2) + (c->ast_host->stop_row ? M2 : 0) + chk_entries;
   if (entries) *entries = nent;
