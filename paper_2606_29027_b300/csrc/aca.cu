@@ -472,12 +472,14 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
   const bool f32 = c->cfg.precision != SLAR_FP64;
   const bool tc = c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4;
   if (f32) CKS(refresh_f32_slot(c, in));
+  if (f32) CKS(refresh_f32_fields(c, E, with_corr));
   if (f32) {
     EvalParams<float>* P = static_cast<EvalParams<float>*>(c->evp_host);
     P->ht = view32_slot(c, in);
     P->corr = corr_view(c, with_corr);
     P->tau = tau;
     P->E = E;
+    P->E32 = c->E32;
     P->foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
   } else {
     EvalParams<double>* P = static_cast<EvalParams<double>*>(c->evp_host);

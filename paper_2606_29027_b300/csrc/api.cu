@@ -83,7 +83,7 @@ void free_ctx(slar_ctx* c) {
   }
   for (int m = 0; m < 4; ++m) { F(c->U32[m]); F(c->Qleaf[m]); F(c->Rleaf[m]); }
   F(c->B12_32); F(c->B34_32); F(c->Broot32); F(c->tc_b12); F(c->tc_b34); F(c->Ik); F(c->Lt[0]); F(c->Lt[1]);
-  F(c->dC); F(c->qv); F(c->Uc); F(c->Uh1); F(c->Uh2);
+  F(c->dC); F(c->qv); F(c->dC32); F(c->qv32); F(c->E32); F(c->Uc); F(c->Uh1); F(c->Uh2);
   F(c->Ua); F(c->Va); F(c->rowbuf); F(c->usedr); F(c->usedc); F(c->pivI); F(c->pivJ);
   F(c->ast); F(c->aca_part); F(c->aca_dots);
   F(c->chk_rows); F(c->chk_idx); F(c->chk_R); F(c->chk_n2);
@@ -147,6 +147,8 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
     g.N[m] = m < c->d ? cfg->N[m] : 1;
     g.lo[m] = m < c->d ? cfg->lo[m] : 0.0;
     g.h[m] = m < c->d ? (cfg->hi[m] - cfg->lo[m]) / cfg->N[m] : 1.0;
+    g.lof[m] = (float)g.lo[m];
+    g.hf[m] = (float)g.h[m];
   }
   for (int m = 0; m < c->dx; ++m) g.NX *= g.N[m];
   for (int m = 0; m < c->dv; ++m) g.NV *= g.N[c->dx + m];
@@ -191,6 +193,11 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   if (d == 2) { A(c->Lt[0], (size_t)c->M1 * c->kmax); A(c->Lt[1], (size_t)c->M2 * c->kmax); }
   A(c->dC, (size_t)(c->dv + 2) * c->NX);
   A(c->qv, (size_t)3 * c->dv * g.N[c->dx]);
+  if (cfg->precision != SLAR_FP64) {
+    A(c->dC32, (size_t)(c->dv + 2) * c->NX);
+    A(c->qv32, (size_t)3 * c->dv * g.N[c->dx]);
+    A(c->E32, (size_t)c->dx * c->NX);
+  }
   A(c->Uc, (size_t)(c->dv + 2) * c->NX);
   A(c->Uh1, (size_t)(c->dv + 2) * c->NX);
   A(c->Uh2, (size_t)(c->dv + 2) * c->NX);
@@ -404,6 +411,7 @@ slar_status ht_eval(slar_ctx* c, long long n, const int* idx, double* out) {
   a.n = n;
   a.idx = idx;
   a.out = out;
+  CKS(refresh_f32_fields(c, nullptr, true));
   return eval_entries(c, c->cur, true, a, 1);
 }
 
@@ -417,6 +425,7 @@ slar_status sl_eval(slar_ctx* c, double tau, const double* E, long long n, const
   a.tau = tau;
   a.E = E;
   a.foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
+  CKS(refresh_f32_fields(c, E, true));
   return eval_entries(c, c->cur, true, a, 0);
 }
 

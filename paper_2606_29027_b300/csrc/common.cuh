@@ -28,6 +28,7 @@ struct GridDesc {
   int d, dx, dv;
   int N[4];
   double lo[4], h[4];
+  float lof[4], hf[4];   // the same in FP32 (the FP32 / BF16x3 paths do no FP64 arithmetic)
   int NX;  // prod of spatial N
   int NV;  // prod of velocity N
 };
@@ -45,6 +46,8 @@ struct HTView {
 struct CorrView {
   const double* dC;  // [dv+2][NX]
   const double* qv;  // [3][dv][Nv]  omega, q1, q2 per velocity dim
+  const float* dC32; // FP32 copies for the FP32 / BF16x3 paths
+  const float* qv32;
   int has;
 };
 
@@ -67,6 +70,7 @@ struct EvalArgs {
   double* out;           // [n]
   double tau;
   const double* E;       // [dx][NX] frozen field
+  const float* E32;      // its FP32 copy (FP32 / BF16x3 paths)
   int foot_euler;
 };
 
@@ -78,6 +82,7 @@ struct EvalParams {
   CorrView corr;
   double tau;
   const double* E;
+  const float* E32;
   int foot_euler;
 };
 

@@ -72,6 +72,9 @@ struct slar_ctx {
   int has_corr = 0;
   double* dC = nullptr;   // [dv+2][NX]
   double* qv = nullptr;   // [3][dv][Nv]
+  float* dC32 = nullptr;  // FP32 copies of dC, qv and of the SLAR field (FP32 / BF16x3 paths)
+  float* qv32 = nullptr;
+  float* E32 = nullptr;   // [dx][NX]
 
   // macroscopic state
   double* Uc = nullptr;   // U^n       [dv+2][NX]
@@ -199,6 +202,9 @@ TruncIn trunc_in_of_slot(const slar_ctx* c, int slot);
 HTView<double> view64(const slar_ctx* c, int slot);
 HTView<float> view32_slot(const slar_ctx* c, int slot);
 slar_status refresh_f32_slot(slar_ctx* c, int slot);
+// FP32 copies of the field E (if given) and of the LoMaC correction (if with_corr) for the
+// FP32 / BF16x3 evaluators; nothing in FP64 mode
+slar_status refresh_f32_fields(slar_ctx* c, const double* E, bool with_corr);
 slar_status build_aca_graph(slar_ctx* c, size_t smem);
 slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int use_cond, bool prof);
 

@@ -15,6 +15,45 @@ __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 
+// periodic stencil rows (r0, r0 + 1, r0 + 2) mod n for the cell index jf (an integer value,
+// |jf| < 1e15): 32-bit arithmetic when jf fits, the 64-bit remainder otherwise; the same rows
+// either way
+__device__ __forceinline__ void stencil_rows(double jf, int n, int rows[3]) {
+  int r0;
+  if (fabs(jf) < 1e9) {
+    r0 = (int)jf - 1;
+    if (r0 < 0 || r0 >= n) {
+      r0 %= n;
+      if (r0 < 0) r0 += n;
+    }
+  } else {
+    long long t = ((long long)jf - 1) % n;
+    if (t < 0) t += n;
+    r0 = (int)t;
+  }
+  rows[0] = r0;
+  rows[1] = r0 + 1 == n ? 0 : r0 + 1;
+  rows[2] = rows[1] + 1 == n ? 0 : rows[1] + 1;
+}
+
+__device__ __forceinline__ void stencil_rows_f(float jf, int n, int rows[3]) {
+  int r0;
+  if (fabsf(jf) < 1e9f) {
+    r0 = (int)jf - 1;
+    if (r0 < 0 || r0 >= n) {
+      r0 %= n;
+      if (r0 < 0) r0 += n;
+    }
+  } else {
+    long long t = ((long long)jf - 1) % n;
+    if (t < 0) t += n;
+    r0 = (int)t;
+  }
+  rows[0] = r0;
+  rows[1] = r0 + 1 == n ? 0 : r0 + 1;
+  rows[2] = rows[1] + 1 == n ? 0 : rows[1] + 1;
+}
+
 // cell and quadratic weights of coordinate y in dimension m (oracle: grid.locate/weights)
 __device__ __forceinline__ void cell_weights(const GridDesc& g, int m, double y, int rows[3],
                                              double w[3]) {
@@ -26,13 +65,7 @@ __device__ __forceinline__ void cell_weights(const GridDesc& g, int m, double y,
   w[0] = dmul(hx, dsub(xi, 1.0));
   w[1] = dsub(1.0, dmul(xi, xi));
   w[2] = dmul(hx, dadd(xi, 1.0));
-  int n = g.N[m];
-  long long j = (long long)jf;
-  long long r0 = (j - 1) % n;
-  if (r0 < 0) r0 += n;
-  rows[0] = (int)r0;
-  rows[1] = (int)((r0 + 1) % n);
-  rows[2] = (int)((r0 + 2) % n);
+  stencil_rows(jf, g.N[m], rows);
 }
 
 // tensor-product quadratic interpolation of a spatial field at point p (dx dims),
@@ -148,7 +181,9 @@ __device__ double correction_at(const GridDesc& g, const CorrView& c, const doub
 __device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& a, long long e,
                                              int* idx) {
   if (a.mode == EVAL_TUPLES) {
-    for (int m = 0; m < g.d; ++m) idx[m] = a.idx[e * g.d + m];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      if (m < g.d) idx[m] = a.idx[e * g.d + m];
     return;
   }
   const long long left = (a.mode == EVAL_ROW) ? (long long)(*a.pivot) : e;
@@ -172,7 +207,7 @@ __device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& 
 // the FP32 tolerance.
 
 __device__ __forceinline__ void cell_weights_f(const GridDesc& g, int m, float y, int rows[3], float w[3]) {
-  float t = (y - (float)g.lo[m]) / (float)g.h[m];
+  float t = (y - g.lof[m]) / g.hf[m];
   if (!(fabsf(t) < 1e15f)) t = 0.f;
   const float jf = floorf(t);
   const float xi = t - jf - 0.5f;
@@ -180,135 +215,159 @@ __device__ __forceinline__ void cell_weights_f(const GridDesc& g, int m, float y
   w[0] = hx * (xi - 1.f);
   w[1] = 1.f - xi * xi;
   w[2] = hx * (xi + 1.f);
-  const int n = g.N[m];
-  long long r0 = ((long long)jf - 1) % n;
-  if (r0 < 0) r0 += n;
-  rows[0] = (int)r0;
-  rows[1] = (int)((r0 + 1) % n);
-  rows[2] = (int)((r0 + 2) % n);
+  stencil_rows_f(jf, g.N[m], rows);
 }
 
-// both (dx) components of a spatial vector field at p, one set of weights
-__device__ void interp_vec_f(const GridDesc& g, const double* F, const float* p, float* out) {
-  int r0[3], r1[3];
-  float w0[3], w1[3];
+// both (DX) components of a spatial vector field at p, one set of weights; static loops
+// over the dimensions keep every small array in registers
+template <int DX>
+__device__ __forceinline__ void interp_vec_ft(const GridDesc& g, const float* F, const float* p, float* out) {
+  int r0[3];
+  float w0[3];
   cell_weights_f(g, 0, p[0], r0, w0);
   const long long NX = g.NX;
-  if (g.dx == 1) {
-    for (int c = 0; c < g.dx; ++c) {
-      const double* Fc = F + c * NX;
-      out[c] = w0[0] * (float)Fc[r0[0]] + w0[1] * (float)Fc[r0[1]] + w0[2] * (float)Fc[r0[2]];
-    }
-    return;
+  if constexpr (DX == 1) {
+    out[0] = w0[0] * F[r0[0]] + w0[1] * F[r0[1]] + w0[2] * F[r0[2]];
+  } else {
+    int r1[3];
+    float w1[3];
+    cell_weights_f(g, 1, p[1], r1, w1);
+    const int N1 = g.N[1];
+    float acc[2] = {0.f, 0.f};
+#pragma unroll
+    for (int s0 = 0; s0 < 3; ++s0)
+#pragma unroll
+      for (int s1 = 0; s1 < 3; ++s1) {
+        const float ww = w0[s0] * w1[s1];
+        const long long o = (long long)r0[s0] * N1 + r1[s1];
+        acc[0] += ww * F[o];
+        acc[1] += ww * F[NX + o];
+      }
+    out[0] = acc[0];
+    out[1] = acc[1];
   }
-  cell_weights_f(g, 1, p[1], r1, w1);
-  const int N1 = g.N[1];
-  float acc[2] = {0.f, 0.f};
-#pragma unroll
-  for (int s0 = 0; s0 < 3; ++s0)
-#pragma unroll
-    for (int s1 = 0; s1 < 3; ++s1) {
-      const float ww = w0[s0] * w1[s1];
-      const long long o = (long long)r0[s0] * N1 + r1[s1];
-      acc[0] += ww * (float)F[o];
-      acc[1] += ww * (float)F[NX + o];
-    }
-  out[0] = acc[0];
-  out[1] = acc[1];
 }
 
 __device__ __forceinline__ float centre_f(const GridDesc& g, int m, int i) {
-  return (float)g.lo[m] + ((float)i + 0.5f) * (float)g.h[m];
+  return g.lof[m] + ((float)i + 0.5f) * g.hf[m];
 }
 
-// backward foot of the frozen-field characteristic (Kutta RK3 or first order), FP32
-__device__ void trace_foot_f(const GridDesc& g, const double* E, double tau_d, int euler, const int* idx,
-                             float* foot) {
-  const int dx = g.dx;
+// backward foot of the frozen-field characteristic (Kutta RK3 or first order), FP32, for
+// DX spatial dimensions
+template <int DX>
+__device__ __forceinline__ void trace_foot_ft(const GridDesc& g, const float* E, double tau_d, int euler,
+                                              const int* idx, float* foot) {
   const float tau = (float)tau_d;
-  float x[2], v[2], e[2];
-  for (int m = 0; m < dx; ++m) {
+  float x[DX], v[DX], e[DX];
+#pragma unroll
+  for (int m = 0; m < DX; ++m) {
     x[m] = centre_f(g, m, idx[m]);
-    v[m] = centre_f(g, dx + m, idx[dx + m]);
+    v[m] = centre_f(g, DX + m, idx[DX + m]);
   }
   if (euler) {
-    interp_vec_f(g, E, x, e);
-    for (int m = 0; m < dx; ++m) {
+    interp_vec_ft<DX>(g, E, x, e);
+#pragma unroll
+    for (int m = 0; m < DX; ++m) {
       foot[m] = x[m] - v[m] * tau;
-      foot[dx + m] = v[m] + e[m] * tau;
+      foot[DX + m] = v[m] + e[m] * tau;
     }
     return;
   }
   const float half = 0.5f * tau, two_h = 2.f * tau, sixth = tau / 6.f;
-  float k1v[2], k2x[2], k2v[2], k3v[2], x2[2], x3[2], v3[2];
-  interp_vec_f(g, E, x, k1v);
-  for (int m = 0; m < dx; ++m) {
+  float k1v[DX], k2x[DX], k2v[DX], k3v[DX], x2[DX], x3[DX], v3[DX];
+  interp_vec_ft<DX>(g, E, x, k1v);
+#pragma unroll
+  for (int m = 0; m < DX; ++m) {
     x2[m] = x[m] - half * v[m];
     k2x[m] = -(v[m] + half * k1v[m]);
   }
-  interp_vec_f(g, E, x2, k2v);
-  for (int m = 0; m < dx; ++m) {
+  interp_vec_ft<DX>(g, E, x2, k2v);
+#pragma unroll
+  for (int m = 0; m < DX; ++m) {
     x3[m] = x[m] + tau * v[m] + two_h * k2x[m];
     v3[m] = v[m] - tau * k1v[m] + two_h * k2v[m];
   }
-  interp_vec_f(g, E, x3, k3v);
-  for (int m = 0; m < dx; ++m) {
+  interp_vec_ft<DX>(g, E, x3, k3v);
+#pragma unroll
+  for (int m = 0; m < DX; ++m) {
     foot[m] = x[m] + sixth * ((-v[m]) + 4.f * k2x[m] + (-v3[m]));
-    foot[dx + m] = v[m] + sixth * (k1v[m] + 4.f * k2v[m] + k3v[m]);
+    foot[DX + m] = v[m] + sixth * (k1v[m] + 4.f * k2v[m] + k3v[m]);
   }
 }
 
-__device__ __forceinline__ float interp_1d_f(const GridDesc& g, int m, const double* vec, float y) {
+__device__ __forceinline__ void trace_foot_f(const GridDesc& g, const float* E, double tau_d, int euler,
+                                             const int* idx, float* foot) {
+  if (g.dx == 2) trace_foot_ft<2>(g, E, tau_d, euler, idx, foot);
+  else trace_foot_ft<1>(g, E, tau_d, euler, idx, foot);
+}
+
+__device__ __forceinline__ float interp_1d_f(const GridDesc& g, int m, const float* vec, float y) {
   int r[3];
   float w[3];
   cell_weights_f(g, m, y, r, w);
-  return w[0] * (float)vec[r[0]] + w[1] * (float)vec[r[1]] + w[2] * (float)vec[r[2]];
+  return w[0] * vec[r[0]] + w[1] * vec[r[1]] + w[2] * vec[r[2]];
 }
 
-// separable LoMaC correction at a foot, FP32
-__device__ float correction_at_f(const GridDesc& g, const CorrView& c, const float* foot) {
-  const int dx = g.dx, dv = g.dv;
+// separable LoMaC correction at a foot, FP32, for DX = dv spatial dimensions
+template <int DX>
+__device__ __forceinline__ float correction_at_ft(const GridDesc& g, const CorrView& c, const float* foot) {
+  constexpr int DV = DX;
   const long long NX = g.NX;
-  const int Nv = g.N[dx];
-  float dCi[4];
+  const int Nv = g.N[DX];
+  float dCi[DV + 2];
   {
     int r0[3], r1[3];
     float w0[3], w1[3];
     cell_weights_f(g, 0, foot[0], r0, w0);
-    if (dx == 2) cell_weights_f(g, 1, foot[1], r1, w1);
-    for (int k = 0; k < dv + 2; ++k) {
-      const double* F = c.dC + k * NX;
+    if constexpr (DX == 2) cell_weights_f(g, 1, foot[1], r1, w1);
+#pragma unroll
+    for (int k = 0; k < DV + 2; ++k) {
+      const float* F = c.dC32 + k * NX;
       float acc = 0.f;
-      if (dx == 1) {
-        for (int s0 = 0; s0 < 3; ++s0) acc += w0[s0] * (float)F[r0[s0]];
+      if constexpr (DX == 1) {
+#pragma unroll
+        for (int s0 = 0; s0 < 3; ++s0) acc += w0[s0] * F[r0[s0]];
       } else {
+#pragma unroll
         for (int s0 = 0; s0 < 3; ++s0)
-          for (int s1 = 0; s1 < 3; ++s1) acc += w0[s0] * w1[s1] * (float)F[(long long)r0[s0] * g.N[1] + r1[s1]];
+#pragma unroll
+          for (int s1 = 0; s1 < 3; ++s1) acc += w0[s0] * w1[s1] * F[(long long)r0[s0] * g.N[1] + r1[s1]];
       }
       dCi[k] = acc;
     }
   }
-  float om[2], q1[2], q2[2];
-  for (int m = 0; m < dv; ++m) {
-    const float y = foot[dx + m];
-    om[m] = interp_1d_f(g, dx + m, c.qv + (0 * dv + m) * Nv, y);
-    q1[m] = interp_1d_f(g, dx + m, c.qv + (1 * dv + m) * Nv, y);
-    q2[m] = interp_1d_f(g, dx + m, c.qv + (2 * dv + m) * Nv, y);
+  float om[DV], q1[DV], q2[DV];
+#pragma unroll
+  for (int m = 0; m < DV; ++m) {
+    const float y = foot[DX + m];
+    om[m] = interp_1d_f(g, DX + m, c.qv32 + (0 * DV + m) * Nv, y);
+    q1[m] = interp_1d_f(g, DX + m, c.qv32 + (1 * DV + m) * Nv, y);
+    q2[m] = interp_1d_f(g, DX + m, c.qv32 + (2 * DV + m) * Nv, y);
   }
   float out = 0.f, t = dCi[0];
-  for (int m = 0; m < dv; ++m) t *= om[m];
+#pragma unroll
+  for (int m = 0; m < DV; ++m) t *= om[m];
   out += t;
-  for (int j = 0; j < dv; ++j) {
+#pragma unroll
+  for (int j = 0; j < DV; ++j) {
     t = dCi[1 + j];
-    for (int m = 0; m < dv; ++m) t *= (m == j ? q1[m] : om[m]);
+#pragma unroll
+    for (int m = 0; m < DV; ++m) t *= (m == j ? q1[m] : om[m]);
     out += t;
   }
-  for (int j = 0; j < dv; ++j) {
-    t = dCi[1 + dv];
-    for (int m = 0; m < dv; ++m) t *= (m == j ? q2[m] : om[m]);
+#pragma unroll
+  for (int j = 0; j < DV; ++j) {
+    t = dCi[1 + DV];
+#pragma unroll
+    for (int m = 0; m < DV; ++m) t *= (m == j ? q2[m] : om[m]);
     out += t;
   }
   return out;
+}
+
+// separable LoMaC correction at a foot, FP32 (dv = dx)
+__device__ __forceinline__ float correction_at_f(const GridDesc& g, const CorrView& c, const float* foot) {
+  return g.dx == 2 ? correction_at_ft<2>(g, c, foot) : correction_at_ft<1>(g, c, foot);
 }
 
 }  // namespace

@@ -52,6 +52,8 @@ CorrView corr_view(const slar_ctx* c, bool with_corr) {
   CorrView v;
   v.dC = c->dC;
   v.qv = c->qv;
+  v.dC32 = c->dC32;
+  v.qv32 = c->qv32;
   v.has = (with_corr && c->has_corr) ? 1 : 0;
   return v;
 }
@@ -74,6 +76,16 @@ slar_status refresh_f32_slot(slar_ctx* c, int slot) {
     CK(to_float(h.Broot, c->Broot32, (long long)h.r[0] * h.r[1], c->s));
   }
   c->f32_slot = slot;
+  return SLAR_OK;
+}
+
+slar_status refresh_f32_fields(slar_ctx* c, const double* E, bool with_corr) {
+  if (c->cfg.precision == SLAR_FP64) return SLAR_OK;
+  if (E) CK(to_float(E, c->E32, (long long)c->dx * c->NX, c->s));
+  if (with_corr && c->has_corr) {
+    CK(to_float(c->dC, c->dC32, (long long)(c->dv + 2) * c->NX, c->s));
+    CK(to_float(c->qv, c->qv32, (long long)3 * c->dv * c->g.N[c->dx], c->s));
+  }
   return SLAR_OK;
 }
 
@@ -106,13 +118,15 @@ slar_status eval_entries(slar_ctx* c, int slot, bool with_corr, const EvalArgs& 
   const bool prof = (c->cfg.flags & SLAR_PROFILE_EVAL) && c->prof_n * 2 + 1 < kProfEvents;
   if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], c->s));
   cudaError_t e;
+  EvalArgs b = a;
+  b.E32 = c->E32;   // refreshed by the caller (refresh_f32_fields)
   if (c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4 && !at_grid) {
     CKS(refresh_f32_slot(c, slot));
-    e = launch_sl_eval_tc(c->g, view32_slot(c, slot), corr_view(c, with_corr), a, c->tc_b12, c->tc_b34,
+    e = launch_sl_eval_tc(c->g, view32_slot(c, slot), corr_view(c, with_corr), b, c->tc_b12, c->tc_b34,
                           &c->ast->tc_err, c->s);
   } else if (c->cfg.precision != SLAR_FP64) {
     CKS(refresh_f32_slot(c, slot));
-    e = launch_sl_eval<float>(c->g, view32_slot(c, slot), corr_view(c, with_corr), a, at_grid, c->s, c->eval_tile);
+    e = launch_sl_eval<float>(c->g, view32_slot(c, slot), corr_view(c, with_corr), b, at_grid, c->s, c->eval_tile);
   } else {
     e = launch_sl_eval<double>(c->g, view64(c, slot), corr_view(c, with_corr), a, at_grid, c->s, c->eval_tile);
   }

@@ -144,6 +144,8 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
   double* sval = sw + TILE * 12;                               // TILE
   double* sres = sval + TILE;                                  // TILE residual sums
   int* srow = reinterpret_cast<int*>(sres + TILE);             // TILE*12
+  T* sfootT = reinterpret_cast<T*>(sfoot);   // the feet and weights in the entry type (FP32
+  T* swT = reinterpret_cast<T*>(sw);         // paths: no FP64 conversions in the gathers)
   T* sc = reinterpret_cast<T*>(srow + TILE * 12);              // leaves
   T* sc_mu[4];
   {
@@ -203,11 +205,15 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
       decode_tuple(g, a, e0 + tid, idx);
       float foot[4];
       if (at_grid) {
-        for (int m = 0; m < d; ++m) foot[m] = centre_f(g, m, idx[m]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (m < d) foot[m] = centre_f(g, m, idx[m]);
       } else {
-        trace_foot_f(g, a.E, a.tau, a.foot_euler, idx, foot);
+        trace_foot_f(g, a.E32, a.tau, a.foot_euler, idx, foot);
       }
-      for (int m = 0; m < d; ++m) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (m >= d) break;
         int r[3];
         float w[3];
         if (at_grid) {
@@ -218,9 +224,9 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
         }
         for (int s = 0; s < 3; ++s) {
           srow[(tid * 4 + m) * 3 + s] = r[s];
-          sw[(tid * 4 + m) * 3 + s] = w[s];
+          swT[(tid * 4 + m) * 3 + s] = w[s];
         }
-        sfoot[tid * 4 + m] = foot[m];
+        sfootT[tid * 4 + m] = foot[m];
       }
     }
   } else if (tid < nT) {
@@ -260,9 +266,9 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
       T val = T(0);
       if (t < nT) {
         const int* rr = srow + (t * 4 + m) * 3;
-        const double* ww = sw + (t * 4 + m) * 3;
-        val = T(ww[0]) * U[(long long)rr[0] * r + q] + T(ww[1]) * U[(long long)rr[1] * r + q] +
-              T(ww[2]) * U[(long long)rr[2] * r + q];
+        const T* ww = swT + (t * 4 + m) * 3;
+        val = ww[0] * U[(long long)rr[0] * r + q] + ww[1] * U[(long long)rr[1] * r + q] +
+              ww[2] * U[(long long)rr[2] * r + q];
       }
       c[it] = val;
     }
@@ -312,7 +318,8 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
     if (corr.has) {
       if constexpr (sizeof(T) == 4) {
         float f4[4];
-        for (int m = 0; m < d; ++m) f4[m] = (float)sfoot[tid * 4 + m];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) f4[m] = (float)sfootT[tid * 4 + m];
         val += (double)correction_at_f(g, corr, f4);
       } else {
         val += correction_at(g, corr, sfoot + tid * 4);
@@ -336,6 +343,7 @@ k_sl_eval_dev(GridDesc g, const EvalParams<T>* __restrict__ P, EvalArgs a) {
   const EvalParams<T> q = *P;
   a.tau = q.tau;
   a.E = q.E;
+  a.E32 = q.E32;
   a.foot_euler = q.foot_euler;
   sl_eval_body<T, TILE>(g, q.ht, q.corr, a, 0);
 }

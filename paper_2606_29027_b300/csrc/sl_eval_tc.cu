@@ -4,20 +4,35 @@
 // x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
 // Trees with d = 4 only (a d = 2 tree has no transfer tensor).
 //
-// One CTA evaluates 128 entries (the MMA's M):
-//   1. feet and quadratic weights (FP32, shared with the FP32 SIMT evaluator),
-//   2. leaf gathers c^(mu) (FP32) for the two children of the node,
-//   3. c_t[e][p] = sum_k KR[e][k] B_t[p][k], k = (a, b), KR[e][(a,b)] = c1[e][a] c2[e][b]:
-//      a [128 x K] x [K x N] GEMM.  Per K-chunk of 64 the CTA writes KR (hi, lo) into
-//      shared memory and copies the pre-split chunk of B_t (hi, lo); one thread issues
-//      3 x 4 MMAs (K-steps of 16) into the node's TMEM accumulator and commits them to an
-//      mbarrier, which every thread waits on (bounded) before the buffers are reused,
-//   4. the root contraction, correction and residual epilogue as in the SIMT evaluator.
+// A transfer node t with children (mu1, mu2) maps the leaf rows c1 = c^(mu1)[e][.],
+// c2 = c^(mu2)[e][.] to c_t[e][p] = sum_a c1[e][a] sum_b B_t[p][a][b] c2[e][b].  One CTA
+// evaluates 128 entries (the MMA's M) in two stages per node:
+//   T[e][(p, a)] = sum_b c2[e][b] B_t[p][a][b]        a [128 x rb] x [rb x rp ra] GEMM on
+//                                                      the tensor cores (K = rb),
+//   c_t[e][p]    = sum_a c1[e][a] T[e][(p, a)]        per-entry dot products on the CUDA
+//                                                      cores, reading T from tensor memory.
+// The columns (p, a) of both nodes (a padded to ra16, a multiple of 16) form one stream of
+// 128-column chunks, each holding an even number of whole p.  Three warp roles run the
+// stream through a 3-stage ring:
+//   warp 9 (one thread)   bulk-copies chunk j's pre-split B tile (hi, lo) into shared slot
+//                         j % 3 once the MMAs of chunk j - 3 have released it,
+//   warp 8 (one thread)   issues chunk j's 3 x K/16 MMAs into tensor-memory slot j % 3 once
+//                         the tile has landed and chunk j - 3 has been read out, and commits
+//                         them to an mbarrier,
+//   warps 0-7             read chunk j out of tensor memory (one 64-column load per warp:
+//                         the warp pair of a lane quadrant splits the chunk's p in halves),
+//                         dot it with c1 held in registers and store c_t[e][p] as a tensor-
+//                         memory column; each warp then arrives on the slot's mbarrier.
+// c2 of both nodes is the MMA's A operand (gathered and split once per CTA), c1 of the
+// current node sits in registers (the thread's own entry), and c_12, c_34 stay in tensor
+// memory for the root contraction and the correction / residual epilogue of the SIMT
+// evaluator.
 // Shared-memory operand layout (canonical, no swizzle, K-major): K-step s | 8-row group |
 // K core matrix | 8 rows x 16 bytes; byte (row, kk) = (row / 8) 256 + (kk / 8) 128 +
 // (row % 8) 16 + (kk % 8) 2 for kk < 16, i.e. leading (K) byte offset 128, stride (M/N)
-// byte offset 256.  Every address the descriptors can form lies inside its 16-row-group
-// tile whichever of the two offsets the hardware applies along K.
+// byte offset 256.
+// Every wait is bounded: a wait that runs out sets *err, the CTA skips the remaining work,
+// waits (bounded) for its copies and MMAs in flight and frees its tensor memory.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -27,36 +42,64 @@ namespace slar {
 namespace {
 
 constexpr int TC_TILE = 128;
-constexpr int TC_THREADS = 256;
-constexpr int TC_TMEM_COLS = 128;          // two accumulators of <= 64 columns
+constexpr int TC_CONSUMERS = 256;        // warps 0-7
+constexpr int TC_MMA_WARP = 8;
+constexpr int TC_COPY_WARP = 9;
+constexpr int TC_THREADS = 320;
+constexpr int TC_W = 128;                // columns of a chunk
+constexpr int TC_STAGES = 3;
+constexpr int TC_TMEM_COLS = 512;        // 3 chunk slots, c_12 and c_34
+constexpr int TC_OUT12 = 384;
+constexpr int TC_OUT34 = 448;
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;
-constexpr int TC_HEAD_BYTES = 23552;       // feet, weights, values (FP64) and rows (int)
-constexpr int TC_A_BYTES = 32768;          // KR chunk: 2 parts x 4 K-steps x 4096 B
+constexpr int TC_HEAD_BYTES = 16384;     // feet, weights, rows, values, partial sums
+constexpr int TC_MIN_SMEM = 120 * 1024;  // one CTA per SM: the 512-column allocation never waits
 
-__host__ __device__ __forceinline__ int tc_np(int rp) {
-  const int n = ((rp + 15) / 16) * 16;
-  return n < 16 ? 16 : n;
-}
-__host__ __device__ __forceinline__ int tc_chunk_bytes(int np) { return 256 * np; }
+__host__ __device__ __forceinline__ int r16(int r) { return ((r + 15) / 16) * 16; }
+__host__ __device__ __forceinline__ int tc_width(int ra16) { return (TC_W / ra16) * ra16; }
 __host__ __device__ __forceinline__ int al128(int x) { return (x + 127) & ~127; }
+__host__ __device__ __forceinline__ int stage_ld(int r) { return r | 1; }   // odd row stride
 
 struct TcLayout {
-  int ca, cb, c12, c34, A, B, total;
+  int stage, A0, A1, B, slot, total;
 };
 
 __host__ __device__ __forceinline__ TcLayout tc_layout(int r0, int r1, int r2, int r3, int r12, int r34) {
   TcLayout L;
+  (void)r34;
   const int ra = r0 > r2 ? r0 : r2, rb = r1 > r3 ? r1 : r3;
-  const int np = tc_np(r12) > tc_np(r34) ? tc_np(r12) : tc_np(r34);
+  const int rmax = ra > rb ? ra : rb;
+  int st = TC_TILE * stage_ld(rmax);
+  if (r12 * 64 > st) st = r12 * 64;   // Broot staged with row stride 64
   int o = TC_HEAD_BYTES;
-  L.ca = o; o = al128(o + 4 * TC_TILE * (ra + 1));
-  L.cb = o; o = al128(o + 4 * TC_TILE * (rb + 1));
-  L.c12 = o; o = al128(o + 4 * TC_TILE * r12);
-  L.c34 = o; o = al128(o + 4 * TC_TILE * r34);
-  L.A = o; o += TC_A_BYTES;
-  L.B = o; o += 2 * tc_chunk_bytes(np);   // double buffer
-  L.total = o;
+  L.stage = o; o = al128(o + 4 * st);
+  L.A0 = o; o += TC_TILE * r16(r1) * 4;
+  L.A1 = o; o += TC_TILE * r16(r3) * 4;
+  const int s0 = tc_width(r16(r0)) * r16(r1) * 4, s1 = tc_width(r16(r2)) * r16(r3) * 4;
+  L.slot = s0 > s1 ? s0 : s1;
+  L.B = o; o += TC_STAGES * L.slot;
+  L.total = o > TC_MIN_SMEM ? o : TC_MIN_SMEM;
   return L;
+}
+
+// one transfer node as the chunk stream sees it
+struct TcNode {
+  int ra, rp, ra16, rb16, ks, w, pc, ntot, nch, out_col;
+  uint32_t a_addr;                 // A operand (c2 split) in shared memory
+  const unsigned char* bg;         // pre-split B tiles in global memory
+};
+
+__device__ __forceinline__ TcNode tc_node(int ra, int rb, int rp, uint32_t a_addr, const unsigned char* bg,
+                                          int out_col) {
+  TcNode n;
+  n.ra = ra; n.rp = rp;
+  n.ra16 = r16(ra); n.rb16 = r16(rb); n.ks = n.rb16 / 16;
+  n.w = tc_width(n.ra16); n.pc = n.w / n.ra16;
+  n.ntot = rp * n.ra16; n.nch = (n.ntot + n.w - 1) / n.w;
+  n.out_col = out_col;
+  n.a_addr = a_addr;
+  n.bg = bg;
+  return n;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -84,6 +127,18 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -95,19 +150,47 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// bounded wait of one thread
+__device__ __forceinline__ bool wait_one(uint32_t bar, uint32_t parity) {
+  for (long long n = 0; n < TC_WAIT_LIMIT; ++n)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// bounded wait of a whole warp: true on every lane once every lane has seen the phase
+__device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity) {
+  bool ok = false;
+  for (long long n = 0; n < TC_WAIT_LIMIT; ++n) {
+    ok = ok || mbar_try_wait(bar, parity);
+    if (__all_sync(0xffffffffu, ok)) return true;
+  }
+  return false;
+}
+
+// bulk copy global -> shared, completion counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
       : "r"(taddr)
       : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, float v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(__float_as_uint(v)) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void split8(const float* x, uint4* hi, uint4* lo) {
   __align__(16) __nv_bfloat16 h[8], l[8];
@@ -120,139 +203,122 @@ __device__ __forceinline__ void split8(const float* x, uint4* hi, uint4* lo) {
   *lo = *reinterpret_cast<uint4*>(l);
 }
 
-// asynchronous copy of one pre-split chunk (bytes a multiple of 16) into shared memory,
-// one commit group per chunk
-__device__ __forceinline__ void copy_chunk_async(unsigned char* dst, const unsigned char* src, int bytes) {
-  const uint32_t d = smem_u32(dst);
-  for (int it = threadIdx.x; it < bytes / 16; it += TC_THREADS)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * it), "l"(src + 16LL * it) : "memory");
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-// Pre-split B [rp][K] (FP32, row = p) into per-chunk hi/lo operand tiles (layout above).
-__global__ void k_split_bf16(const float* __restrict__ B, int rp, int K, int np, int nch,
-                             unsigned char* __restrict__ out) {
+// Pre-split B [rp][ra][b] (FP32) into the chunk tiles of the column stream: row n = (p, a)
+// (a padded to ra16), K = b (padded to rb16); chunk c holds rows [c W, c W + Wc) as
+// [hi: ks K-step tiles of Wc x 16][lo: same], tile layout as above.
+__global__ void k_split_bf16(const float* __restrict__ B, int rp, int ra, int rb, unsigned char* __restrict__ out) {
+  const int ra16 = r16(ra), rb16 = r16(rb), ks = rb16 / 16, W = tc_width(ra16), ntot = rp * ra16, ng = rb16 / 8;
   const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (it >= (long long)nch * np * 8) return;
-  const int c = (int)(it / (np * 8));
-  const int r = (int)(it % (np * 8));
-  const int p = r >> 3, kg = r & 7;
+  if (it >= (long long)ntot * ng) return;
+  const int n = (int)(it / ng), kg = (int)(it % ng);
+  const int p = n / ra16, a = n - p * ra16;
   float x[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const int k = c * 64 + kg * 8 + j;
-    x[j] = (p < rp && k < K) ? B[(long long)p * K + k] : 0.f;
+    const int b = kg * 8 + j;
+    x[j] = (a < ra && b < rb) ? B[((long long)p * ra + a) * rb + b] : 0.f;
   }
   uint4 hi, lo;
   split8(x, &hi, &lo);
-  unsigned char* base = out + (long long)c * tc_chunk_bytes(np);
-  const int off = (kg >> 1) * 32 * np + (p >> 3) * 256 + (kg & 1) * 128 + (p & 7) * 16;
+  const int cl = n / W, nl = n - cl * W;
+  const int wc = min(W, ntot - cl * W);
+  unsigned char* base = out + (long long)cl * W * rb16 * 4;
+  const int off = (kg >> 1) * wc * 32 + (nl >> 3) * 256 + (kg & 1) * 128 + (nl & 7) * 16;
   *reinterpret_cast<uint4*>(base + off) = hi;
-  *reinterpret_cast<uint4*>(base + 128 * np + off) = lo;
+  *reinterpret_cast<uint4*>(base + ks * wc * 32 + off) = lo;
 }
 
-// c_out[e][p] = sum_{a,b} ca[e][a] cb[e][b] B[p][a][b] on the tensor cores; returns false
-// (with *err set) if an MMA completion wait ran out.
-__device__ bool contract_tc(const float* ca, int ra, const float* cb, int rb, const unsigned char* Bg, int rp,
-                            float* cout, uint32_t tmem_d, unsigned char* Abuf, unsigned char* Bbuf, uint32_t bar,
-                            uint32_t& phase, int nT, int* s_ok, int* err) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int K = ra * rb, np = tc_np(rp), nch = (K + 63) / 64;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(np >> 3) << 17) |
-                         ((uint32_t)(TC_TILE >> 4) << 24);
-  const uint32_t a_addr = smem_u32(Abuf);
-  const int cb_bytes = tc_chunk_bytes(np);
-  copy_chunk_async(Bbuf, Bg, cb_bytes);   // chunk 0 into buffer 0
-  for (int c = 0; c < nch; ++c) {
-    // prefetch chunk c+1 into the other buffer (its previous MMA has completed)
-    if (c + 1 < nch) copy_chunk_async(Bbuf + ((c + 1) & 1) * cb_bytes, Bg + (long long)(c + 1) * cb_bytes, cb_bytes);
-    // Khatri-Rao chunk of the left operand, split into hi / lo.  A warp takes 32
-    // consecutive entries of one 8-wide k-group: its 16-byte stores fill whole 128-byte
-    // rows of core matrices (no bank conflicts), its reads of ca / cb use the odd padded
-    // strides, and (a, b) of the group's first k is the same across the warp.
-    const int lda = ra + 1, ldb = rb + 1;
-    for (int it = tid; it < TC_TILE * 8; it += TC_THREADS) {
-      const int kg = it >> 7, e = it & (TC_TILE - 1);
-      const int k0 = c * 64 + kg * 8;
-      int a = k0 / rb, b = k0 - a * rb;
-      const bool live = e < nT;
-      const float* cae = ca + e * lda;
-      const float* cbe = cb + e * ldb;
-      float x[8];
+// stage[e][q] = sum_s w[e][m][s] U_m[row_s][q] (FP32), zero rows for e >= nT.  Lanes run
+// over q (coalesced reads of U, conflict-free writes with the odd stride); each thread
+// issues the loads of four items before it uses them.
+__device__ __forceinline__ void gather_leaf(float* stage, const float* __restrict__ U, int r, int m, int nT,
+                                            const int* srow, const float* sw) {
+  const int ld = stage_ld(r), n = TC_TILE * r;
+  for (int base = threadIdx.x; base < n; base += 4 * TC_THREADS) {
+    float u[4][3], w[4][3];
+    int dst[4];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        x[j] = (live && k0 + j < K) ? cae[a] * cbe[b] : 0.f;
-        if (++b == rb) {
-          b = 0;
-          ++a;
+    for (int k = 0; k < 4; ++k) {
+      const int it = base + k * TC_THREADS;
+      dst[k] = -1;
+      u[k][0] = u[k][1] = u[k][2] = 0.f;
+      w[k][0] = w[k][1] = w[k][2] = 0.f;
+      if (it < n) {
+        const int e = it / r, q = it - e * r;
+        dst[k] = e * ld + q;
+        if (e < nT) {
+          const int* rr = srow + (e * 4 + m) * 3;
+          const float* ww = sw + (e * 4 + m) * 3;
+#pragma unroll
+          for (int s = 0; s < 3; ++s) {
+            u[k][s] = __ldg(U + (long long)rr[s] * r + q);
+            w[k][s] = ww[s];
+          }
         }
       }
-      uint4 hi, lo;
-      split8(x, &hi, &lo);
-      const int off = (kg >> 1) * 4096 + (e >> 3) * 256 + (kg & 1) * 128 + (e & 7) * 16;
-      *reinterpret_cast<uint4*>(Abuf + off) = hi;
-      *reinterpret_cast<uint4*>(Abuf + 16384 + off) = lo;
     }
-    // chunk c's copy done (chunk c+1 may still be in flight)
-    if (c + 1 < nch) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      fence_after();
-      const uint32_t b_addr = smem_u32(Bbuf + (c & 1) * cb_bytes);
-      for (int s = 0; s < 4; ++s) {
-        if (c * 64 + s * 16 >= K) break;
-        const uint64_t ah = tc_desc(a_addr + s * 4096), al = tc_desc(a_addr + 16384 + s * 4096);
-        const uint64_t bh = tc_desc(b_addr + s * 32 * np), bl = tc_desc(b_addr + 128 * np + s * 32 * np);
-        mma_bf16(tmem_d, ah, bh, idesc, (c > 0 || s > 0) ? 1u : 0u);
-        mma_bf16(tmem_d, ah, bl, idesc, 1u);
-        mma_bf16(tmem_d, al, bh, idesc, 1u);
-      }
-      mma_commit(bar);
-      long long n = 0;
-      bool ok = mbar_try_wait(bar, phase);
-      while (!ok && ++n < TC_WAIT_LIMIT) ok = mbar_try_wait(bar, phase);
-      if (!ok) {
-        atomicExch(err, 1);
-        n = 0;
-        while (!mbar_try_wait(bar, phase) && ++n < TC_WAIT_LIMIT) {
-        }
-        *s_ok = 0;
-      }
-    }
-    phase ^= 1u;
-    __syncthreads();
-    if (!*s_ok) {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      return false;
-    }
-  }
-  fence_after();
-  if (warp < 4) {
-    const int e = 32 * warp + lane;
-    for (int j0 = 0; j0 < np; j0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(tmem_d + ((uint32_t)(32 * warp) << 16) + (uint32_t)j0, r);
-      if (e < nT)
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj)
-          if (j0 + jj < rp) cout[e * rp + j0 + jj] = __uint_as_float(r[jj]);
-    }
+    for (int k = 0; k < 4; ++k)
+      if (dst[k] >= 0) stage[dst[k]] = w[k][0] * u[k][0] + w[k][1] * u[k][1] + w[k][2] * u[k][2];
   }
-  fence_before();
-  __syncthreads();
-  return true;
+}
+
+// stage (128 x r) -> A operand tiles (hi, lo), K padded to r16 with zeros
+__device__ __forceinline__ void stage_to_operand(const float* stage, int r, unsigned char* A) {
+  const int ld = stage_ld(r), rb16 = r16(r), ks = rb16 / 16, ng = rb16 / 8;
+  for (int it = threadIdx.x; it < TC_TILE * ng; it += TC_THREADS) {
+    const int e = it & (TC_TILE - 1), kg = it >> 7;
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int b = kg * 8 + j;
+      x[j] = b < r ? stage[e * ld + b] : 0.f;
+    }
+    uint4 hi, lo;
+    split8(x, &hi, &lo);
+    const int off = (kg >> 1) * 4096 + (e >> 3) * 256 + (kg & 1) * 128 + (e & 7) * 16;
+    *reinterpret_cast<uint4*>(A + off) = hi;
+    *reinterpret_cast<uint4*>(A + ks * 4096 + off) = lo;
+  }
+}
+
+// the thread's own row of the stage into registers (zero beyond r)
+__device__ __forceinline__ void stage_to_regs(const float* stage, int r, int e, float* c) {
+  const int ld = stage_ld(r);
+#pragma unroll
+  for (int a = 0; a < 64; ++a) c[a] = a < r ? stage[e * ld + a] : 0.f;
+}
+
+// Read-out of one chunk by one warp: the warp takes the half `half` of the chunk's p (NP
+// consecutive p, NP x 16 NB <= 64 consecutive columns), loads them with one 64-column
+// tensor-memory load and stores c_t[e][p] = sum_a c1[e][a] T[e][(p, a)] into column
+// out_col + p.  Columns of p >= p1 (a ragged last chunk) are loaded but not used.
+template <int NB>
+__device__ __forceinline__ void drain_chunk(const float* creg, uint32_t trow, uint32_t slot_col, int p0, int p1,
+                                            int half, int out_col) {
+  constexpr int RA16 = 16 * NB;
+  constexpr int NP = (TC_W / RA16) / 2;
+  float v[64];
+  tmem_ld64(trow + slot_col + (uint32_t)(half * NP * RA16), v);
+  tmem_wait_ld();
+#pragma unroll
+  for (int pi = 0; pi < NP; ++pi) {
+    const int p = p0 + half * NP + pi;
+    float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < RA16; ++a) s4[a & 3] = fmaf(creg[a], v[pi * RA16 + a], s4[a & 3]);
+    if (p < p1) tmem_st1(trow + (uint32_t)(out_col + p), (s4[0] + s4[1]) + (s4[2] + s4[3]));
+  }
 }
 
 template <bool DEV>
-__global__ void __launch_bounds__(TC_THREADS)
+__global__ void __launch_bounds__(TC_THREADS, 1)
 k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalParams<float>* __restrict__ P,
              EvalArgs a, const unsigned char* __restrict__ b12, const unsigned char* __restrict__ b34, int* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long s_bar;
+  __shared__ __align__(8) unsigned long long s_bar[3 * TC_STAGES];   // full, mma_done, drained
   __shared__ uint32_t s_tmem;
-  __shared__ int s_ok;
+  __shared__ int s_abort;
   HTView<float> ht;
   CorrView corr;
   if (DEV) {
@@ -261,6 +327,7 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     corr = q.corr;
     a.tau = q.tau;
     a.E = q.E;
+    a.E32 = q.E32;
     a.foot_euler = q.foot_euler;
   } else {
     ht = ht_arg;
@@ -276,19 +343,24 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   const long long e0 = (long long)blockIdx.x * TC_TILE;
   if (e0 >= a.n) return;
   const int nT = (int)min((long long)TC_TILE, a.n - e0);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = g.d;
   const TcLayout L = tc_layout(ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34);
-  double* sfoot = reinterpret_cast<double*>(smem_raw);   // 128 x 4
-  double* sw = sfoot + TC_TILE * 4;                       // 128 x 12
-  double* sval = sw + TC_TILE * 12;                       // 128
-  int* srow = reinterpret_cast<int*>(sval + TC_TILE);     // 128 x 12
-  float* ca = reinterpret_cast<float*>(smem_raw + L.ca);
-  float* cb = reinterpret_cast<float*>(smem_raw + L.cb);
-  float* c12 = reinterpret_cast<float*>(smem_raw + L.c12);
-  float* c34 = reinterpret_cast<float*>(smem_raw + L.c34);
-  unsigned char* Abuf = smem_raw + L.A;
-  unsigned char* Bbuf = smem_raw + L.B;
+  float* sfoot = reinterpret_cast<float*>(smem_raw);                 // 128 x 4
+  float* sw = sfoot + TC_TILE * 4;                                    // 128 x 12
+  int* srow = reinterpret_cast<int*>(sw + TC_TILE * 12);              // 128 x 12
+  double* sval = reinterpret_cast<double*>(srow + TC_TILE * 12);      // 128
+  float* spart = reinterpret_cast<float*>(sval + TC_TILE);            // 128
+  float* stage = reinterpret_cast<float*>(smem_raw + L.stage);
+  unsigned char* A0 = smem_raw + L.A0;
+  unsigned char* A1 = smem_raw + L.A1;
+  const uint32_t bslot = smem_u32(smem_raw + L.B);
+  const uint32_t full = smem_u32(&s_bar[0]), mdone = smem_u32(&s_bar[TC_STAGES]),
+                 drained = smem_u32(&s_bar[2 * TC_STAGES]);
+
+  const TcNode N0 = tc_node(ht.r[0], ht.r[1], ht.r12, smem_u32(A0), b12, TC_OUT12);
+  const TcNode N1 = tc_node(ht.r[2], ht.r[3], ht.r34, smem_u32(A1), b34, TC_OUT34);
+  const int nchunk = N0.nch + N1.nch;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -297,27 +369,53 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)) : "memory");
+    for (int i = 0; i < TC_STAGES; ++i) {
+      mbar_init(full + 8 * i, 1);
+      mbar_init(mdone + 8 * i, 1);
+      mbar_init(drained + 8 * i, TC_CONSUMERS / 32);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_ok = 1;
+    s_abort = 0;
   }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = s_tmem;
-  const uint32_t bar = smem_u32(&s_bar);
-  uint32_t phase = 0;
+
+  // chunk j of the column stream: its node (by value: field selects, no local memory),
+  // local chunk index and width
+  auto chunk = [&](int j, TcNode& N, int& cl, int& wc) {
+    const bool first = j < N0.nch;
+    N = first ? N0 : N1;
+    cl = first ? j : j - N0.nch;
+    wc = min(N.w, N.ntot - cl * N.w);
+  };
+  auto issue_copy = [&](int j) {
+    TcNode N;
+    int cl, wc;
+    chunk(j, N, cl, wc);
+    const uint32_t bytes = (uint32_t)(wc * N.rb16 * 4);
+    const int s = j % TC_STAGES;
+    mbar_expect_tx(full + 8 * s, bytes);
+    bulk_g2s(bslot + s * L.slot, N.bg + (long long)cl * N.w * N.rb16 * 4, bytes, full + 8 * s);
+  };
+  const bool copier = tid == TC_COPY_WARP * 32, issuer = tid == TC_MMA_WARP * 32;
+  int n_copy = 0;
+  if (copier)
+    for (; n_copy < TC_STAGES && n_copy < nchunk; ++n_copy) issue_copy(n_copy);
 
   // 1. feet and weights
   if (tid < nT) {
     int idx[4];
     decode_tuple(g, a, e0 + tid, idx);
     float foot[4];
-    trace_foot_f(g, a.E, a.tau, a.foot_euler, idx, foot);
-    for (int m = 0; m < d; ++m) {
+    trace_foot_ft<2>(g, a.E32, a.tau, a.foot_euler, idx, foot);   // d = 4: two spatial dimensions
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
       int r[3];
       float w[3];
       cell_weights_f(g, m, foot[m], r, w);
+#pragma unroll
       for (int s = 0; s < 3; ++s) {
         srow[(tid * 4 + m) * 3 + s] = r[s];
         sw[(tid * 4 + m) * 3 + s] = w[s];
@@ -327,59 +425,177 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   }
   __syncthreads();
 
-  bool ok = true;
-  for (int node = 0; node < 2 && ok; ++node) {
-    // 2. leaf gathers of the node's two children
-    for (int side = 0; side < 2; ++side) {
-      const int m = 2 * node + side;
-      const int r = ht.r[m];
-      const float* U = ht.U[m];
-      float* c = side == 0 ? ca : cb;
-      for (int it = tid; it < TC_TILE * r; it += TC_THREADS) {
-        const int t = it / r, q = it - t * r;
-        float val = 0.f;
-        if (t < nT) {
-          const int* rr = srow + (t * 4 + m) * 3;
-          const double* ww = sw + (t * 4 + m) * 3;
-          val = (float)ww[0] * U[(long long)rr[0] * r + q] + (float)ww[1] * U[(long long)rr[1] * r + q] +
-                (float)ww[2] * U[(long long)rr[2] * r + q];
+  // 2. operands: c2 of both nodes split into the A tiles, c1 of node 0 into registers,
+  //    c1 of node 1 left in the stage for the node switch
+  const int e_own = 32 * (warp & 3) + lane;   // the tensor-memory lane this warp may access
+  const int half = (warp >> 2) & 1;           // the two warps of a lane quadrant split the p's
+  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  float creg[64];
+  gather_leaf(stage, ht.U[1], ht.r[1], 1, nT, srow, sw);
+  __syncthreads();
+  stage_to_operand(stage, ht.r[1], A0);
+  __syncthreads();
+  gather_leaf(stage, ht.U[3], ht.r[3], 3, nT, srow, sw);
+  __syncthreads();
+  stage_to_operand(stage, ht.r[3], A1);
+  __syncthreads();
+  gather_leaf(stage, ht.U[0], ht.r[0], 0, nT, srow, sw);
+  __syncthreads();
+  if (warp < 8) stage_to_regs(stage, ht.r[0], e_own, creg);
+  __syncthreads();
+  gather_leaf(stage, ht.U[2], ht.r[2], 2, nT, srow, sw);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A tiles -> tensor cores
+  __syncthreads();
+
+  // 3. the chunk stream
+  int n_mma = 0;
+  if (issuer) {
+    for (int j = 0; j < nchunk; ++j) {
+      if (*(volatile int*)&s_abort) break;
+      const int s = j % TC_STAGES;
+      bool ok = wait_one(full + 8 * s, (j / TC_STAGES) & 1);
+      if (ok && j >= TC_STAGES) ok = wait_one(drained + 8 * s, ((j - TC_STAGES) / TC_STAGES) & 1);
+      if (!ok) {
+        *(volatile int*)&s_abort = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      TcNode N;
+      int cl, wc;
+      chunk(j, N, cl, wc);
+      fence_after();
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(wc >> 3) << 17) |
+                             ((uint32_t)(TC_TILE >> 4) << 24);
+      const uint32_t dt = tmem + (uint32_t)(s * TC_W);
+      const uint32_t bb = bslot + s * L.slot;
+      for (int k = 0; k < N.ks; ++k) {
+        const uint64_t ah = tc_desc(N.a_addr + k * 4096), al = tc_desc(N.a_addr + (N.ks + k) * 4096);
+        const uint64_t bh = tc_desc(bb + k * wc * 32), bl = tc_desc(bb + (N.ks + k) * wc * 32);
+        mma_bf16(dt, ah, bh, idesc, k > 0 ? 1u : 0u);
+        mma_bf16(dt, ah, bl, idesc, 1u);
+        mma_bf16(dt, al, bh, idesc, 1u);
+      }
+      mma_commit(mdone + 8 * s);
+      n_mma = j + 1;
+    }
+  } else if (copier) {
+    for (int j = TC_STAGES; j < nchunk; ++j) {
+      if (*(volatile int*)&s_abort) break;
+      const int s = j % TC_STAGES;
+      if (!wait_one(mdone + 8 * s, ((j - TC_STAGES) / TC_STAGES) & 1)) {
+        *(volatile int*)&s_abort = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      issue_copy(j);
+      n_copy = j + 1;
+    }
+  } else if (warp < 8) {
+    for (int c = 0; c < nchunk; ++c) {
+      if (c == N0.nch) {
+        // node switch: c1 of node 1 (left in the stage) into registers
+        consumer_sync();
+        stage_to_regs(stage, ht.r[2], e_own, creg);
+      }
+      const int s = c % TC_STAGES;
+      if (!__any_sync(0xffffffffu, *(volatile int*)&s_abort != 0)) {
+        if (!wait_warp(mdone + 8 * s, (c / TC_STAGES) & 1)) {
+          if (lane == 0) {
+            *(volatile int*)&s_abort = 1;
+            atomicExch(err, 1);
+          }
+        } else {
+          fence_after();
+          TcNode N;
+          int cl, wc;
+          chunk(c, N, cl, wc);
+          const int p0 = cl * N.pc, p1 = min(N.rp, p0 + N.pc);
+          const uint32_t sc = (uint32_t)(s * TC_W);
+          switch (N.ra16) {
+            case 16: drain_chunk<1>(creg, trow, sc, p0, p1, half, N.out_col); break;
+            case 32: drain_chunk<2>(creg, trow, sc, p0, p1, half, N.out_col); break;
+            case 48: drain_chunk<3>(creg, trow, sc, p0, p1, half, N.out_col); break;
+            default: drain_chunk<4>(creg, trow, sc, p0, p1, half, N.out_col); break;
+          }
+          fence_before();
         }
-        c[t * (r + 1) + q] = val;   // odd row stride (conflict-free reads across entries)
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(drained + 8 * s);
+    }
+  }
+
+  // copies and MMAs still in flight (only after an abort) end before the CTA does
+  if (copier)
+    for (int k = n_copy - TC_STAGES < 0 ? 0 : n_copy - TC_STAGES; k < n_copy; ++k)
+      wait_one(full + 8 * (k % TC_STAGES), (k / TC_STAGES) & 1);
+  if (issuer && n_mma > 0) wait_one(mdone + 8 * ((n_mma - 1) % TC_STAGES), ((n_mma - 1) / TC_STAGES) & 1);
+  __syncwarp();
+  tmem_wait_st();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const bool ok = *(volatile int*)&s_abort == 0;
+
+  if (ok) {
+    // 4. root: sum_p c12[e][p] sum_q Broot[p][q] c34[e][q]; the two warps of a lane
+    //    quadrant take p < 32 and p >= 32
+    const int rl = ht.r12, rr = ht.r34;
+    {
+      const int n = rl * 64;
+      for (int base = tid; base < n; base += 4 * TC_THREADS) {
+        float x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int it = base + k * TC_THREADS, p = it >> 6, q = it & 63;
+          x[k] = (it < n && q < rr) ? __ldg(ht.Broot + (long long)p * rr + q) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (base + k * TC_THREADS < n) stage[base + k * TC_THREADS] = x[k];
       }
     }
     __syncthreads();
-    // 3. transfer tensor on the tensor cores
-    ok = node == 0 ? contract_tc(ca, ht.r[0], cb, ht.r[1], b12, ht.r12, c12, tmem, Abuf, Bbuf, bar, phase, nT,
-                                 &s_ok, err)
-                   : contract_tc(ca, ht.r[2], cb, ht.r[3], b34, ht.r34, c34, tmem + 64, Abuf, Bbuf, bar, phase,
-                                 nT, &s_ok, err);
-  }
-
-  if (ok) {
-    // 4. root: sum_p c12[t][p] sum_q Broot[p][q] c34[t][q]
-    constexpr int TPE = TC_THREADS / TC_TILE;
-    const int t = tid / TPE, sub = tid - t * TPE;
-    const int rl = ht.r12, rr = ht.r34;
-    float acc = 0.f;
-    if (t < nT) {
-      for (int p = sub; p < rl; p += TPE) {
-        float s = 0.f;
-        const float* Bp = ht.Broot + (long long)p * rr;
-        for (int q = 0; q < rr; ++q) s += Bp[q] * c34[t * rr + q];
-        acc += c12[t * rl + p] * s;
-      }
-    }
+    if (warp < 8) {
+      float c34[64], c12[64];
+      tmem_ld64(trow + TC_OUT34, c34);
+      tmem_ld64(trow + TC_OUT12, c12);
+      tmem_wait_ld();
 #pragma unroll
-    for (int off = TPE / 2; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, TPE);
-    if (sub == 0 && t < TC_TILE) sval[t] = (double)acc;
+      for (int q = 0; q < 64; ++q) {
+        if (q >= rr) c34[q] = 0.f;
+        if (q >= rl) c12[q] = 0.f;
+      }
+      float acc = 0.f;
+#pragma unroll
+      for (int p = 0; p < 64; ++p) {
+        if ((p >> 5) == half && p < rl) {
+          const float4* Bp = reinterpret_cast<const float4*>(stage + p * 64);
+          float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int q4 = 0; q4 < 16; ++q4) {
+            const float4 bq = Bp[q4];
+            s4[0] = fmaf(bq.x, c34[4 * q4], s4[0]);
+            s4[1] = fmaf(bq.y, c34[4 * q4 + 1], s4[1]);
+            s4[2] = fmaf(bq.z, c34[4 * q4 + 2], s4[2]);
+            s4[3] = fmaf(bq.w, c34[4 * q4 + 3], s4[3]);
+          }
+          acc = fmaf(c12[p], (s4[0] + s4[1]) + (s4[2] + s4[3]), acc);
+        }
+      }
+      if (half == 1) spart[e_own] = acc;
+      consumer_sync();
+      if (half == 0) sval[e_own] = (double)(acc + spart[e_own]);
+    }
     __syncthreads();
     // 5. correction and residual epilogue
     if (tid < nT) {
       double val = sval[tid];
       if (corr.has) {
         float f4[4];
-        for (int m = 0; m < d; ++m) f4[m] = (float)sfoot[tid * 4 + m];
-        val += (double)correction_at_f(g, corr, f4);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) f4[m] = sfoot[tid * 4 + m];
+        val += (double)correction_at_ft<2>(g, corr, f4);
       }
       const long long e = e0 + tid;
       if (a.X) {
@@ -403,7 +619,7 @@ size_t sl_eval_tc_smem(const int* r6) {
   return (size_t)tc_layout(r6[0], r6[1], r6[2], r6[3], r6[4], r6[5]).total;
 }
 
-long long tc_split_bytes() { return 64LL * tc_chunk_bytes(64); }
+long long tc_split_bytes() { return 64LL * 64 * 64 * 4; }
 
 cudaError_t sl_eval_tc_init_attrs() {
   const int mx = 220 * 1024;
@@ -413,10 +629,9 @@ cudaError_t sl_eval_tc_init_attrs() {
 }
 
 cudaError_t split_transfer_bf16(const float* B, int rp, int ra, int rb, void* out, cudaStream_t s) {
-  const int K = ra * rb, np = tc_np(rp), nch = (K + 63) / 64;
-  if (rp > 64 || nch > 64) return cudaErrorInvalidValue;
-  const long long n = (long long)nch * np * 8;
-  slar::count_launch(), k_split_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, rp, K, np, nch,
+  if (rp < 1 || ra < 1 || rb < 1 || rp > 64 || ra > 64 || rb > 64) return cudaErrorInvalidValue;
+  const long long n = (long long)rp * r16(ra) * (r16(rb) / 8);
+  slar::count_launch(), k_split_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, rp, ra, rb,
                                                                                 static_cast<unsigned char*>(out));
   return cudaGetLastError();
 }
