@@ -33,9 +33,10 @@ METRIC = "2D2V SLAR steps/s"
 UNIT = "steps/s"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2032 MHz
 FP64_PEAK_TFLOPS = 1.25                              # nominal B300 FP64 (recipe table)
-# DRAM bytes (read + write) per launch of the FP32 entry evaluator on this workload, from the
-# ncu launch list in profiles/launch_list_landau_2d2v_64.md (cold cache, one BDF3 step)
-EVAL_TRAFFIC_BYTES = 353.0e3
+# DRAM bytes (read + write) per launch of the FP32 entry evaluator (k_sl_eval_dev<float, 32>)
+# on this workload, from the ncu launch list in profiles/launch_list_landau_2d2v_64.md (cold
+# cache, one BDF3 step)
+EVAL_TRAFFIC_BYTES = 277.2e3
 
 
 def parse():
@@ -44,7 +45,9 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3"],
+                   help="entry precision of the headline run (bf16x3: 2D2V workloads, "
+                        "--profile-step only)")
     p.add_argument("--workload", default="landau_2d2v")
     p.add_argument("--fp64-steps", type=int, default=None,
                    help="steps of the comparison forms (default: --steps, the same steps as the headline)")
@@ -454,7 +457,7 @@ def run_ours(args, w):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3"}[args.precision], "data": "synthetic",
             "config": workload_config(w, args.precision, args.solver),
             "entries_per_s": entries / (tot_ms / 1000.0) * world,
             "entries_per_step": entries / args.steps,

@@ -146,6 +146,10 @@ struct EigJob {
   int n;
   double floor_rel;     // off-diagonals below floor_rel ||A||_F are not rotated
   double compress_rel;  // > 0: pivoted-Cholesky compression down to compress_rel x trace first
+  int nvec;             // leading eigenvectors the caller reads (<= n)
+  int tri;              // 1: a compressed rank above 40 goes to the tridiagonal solver, which
+                        // returns the nvec leading eigenpairs, W[nvec] = the rest of the trace
+                        // and W[i > nvec] = 0
 };
 cudaError_t eig_batched(const EigJob* jobs_host, int njobs, EigJob* jobs_dev, cudaStream_t s);
 // Rank selection from descending eigenvalues: smallest k with tail sum <= thr2, k in [1, cap].

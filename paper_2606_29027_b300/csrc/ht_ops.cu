@@ -305,6 +305,11 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
     // pivoted Cholesky G ~ L L^T stopped when the trace left out is below 1/10 of the rank
     // threshold eps^2/(2d-3) (relative to trace G = ||F||^2), then Jacobi on L^T L
     jobs[nj].compress_rel = c->cfg.precision == SLAR_FP64 ? 0.0 : std::max(1e-16, 0.1 * eps * eps / (2.0 * d - 3.0));
+    // the truncation reads at most cap leading eigenvectors of each node; FP32 / BF16x3 data
+    // of numerical rank above 40 is solved by the tridiagonal path (FP64 data keeps the
+    // relative-accuracy Jacobi)
+    jobs[nj].nvec = std::min(node_n[t], cap);
+    jobs[nj].tri = (jobs[nj].compress_rel > 0.0 && node_n[t] > 40) ? 1 : 0;
     ++nj;
   }
   CK(eig_batched(jobs, nj, c->d_eig, s));

@@ -434,6 +434,10 @@ __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, d
 // shared memory; only a full-rank matrix with n > 64 falls back to eigenvectors in global
 // memory.
 constexpr int EIG_RTMAX = 64;
+constexpr int TRI_RT = 40;                                          // see EigJob::tri
+constexpr int TRI_WORK = 2 * (SLAR_MAX_N + 1) * (SLAR_MAX_N + 1);    // doubles of EigJob::work
+constexpr int TRI_FLAG = TRI_WORK - 1;                              // 1.0: job handed over
+constexpr int TRI_TRACE = TRI_WORK - 2;                             // trace of the matrix
 constexpr int EIG_SMEM_DOUBLES = SLAR_MAX_N * EIG_RTMAX + 2 * EIG_RTMAX * EIG_RTMAX + SLAR_MAX_N;
 
 __device__ void sort_write(const double* sA, int ne, int n, const double* V, int ldv, double* W,
@@ -478,7 +482,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
     // stop once the trace left outside L L^T is at most compress_rel x trace: the eigenvalues
     // dropped with it lie far below the rank threshold of the truncation
     const double stop = job.compress_rel * trace_s;
-    const int rtmax = n < EIG_RTMAX ? n : EIG_RTMAX;
+    const int rcap = job.tri ? TRI_RT + 1 : EIG_RTMAX;
+    const int rtmax = n < rcap ? n : rcap;
     for (int j = 0; j < rtmax; ++j) {
       double best = -1.0;
       int bi = -1;
@@ -532,6 +537,16 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
     }
     int rt = rt_s;
     const bool full = (rt == rtmax && rtmax < n && dpiv_s > stop);
+    if (job.tri) {
+      // numerical rank above TRI_RT: the FP64 Jacobi of the compressed matrix would cost
+      // O(rt^3) per sweep on one SM; the tridiagonal solver takes the job instead
+      const bool hand_off = full || rt > TRI_RT;
+      if (tid == 0) {
+        job.work[TRI_FLAG] = hand_off ? 1.0 : 0.0;
+        job.work[TRI_TRACE] = trace_s;
+      }
+      if (hand_off) return;
+    }
     if (!full) {
       if (rt == 0) {  // zero matrix: one zero eigenpair
         rt = 1;
@@ -607,6 +622,316 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
   __syncthreads();
   jacobi_sweeps(sA, ne, V, pp, qq, cc, ss, &rotated, job.floor_rel);
   sort_write(sA, ne, n, V, ne, job.W, job.V);
+}
+
+// ---------------------------------------------------------------------------------------
+// Tridiagonal symmetric eigensolver for the jobs k_jacobi hands over (numerical rank above
+// TRI_RT of FP32 / BF16x3 data).  On B300 an SM retires about two FP64 FMAs per clock, so a
+// cyclic Jacobi of order 64-128 (O(n^3) work per sweep, 6-10 sweeps) takes milliseconds to
+// tens of milliseconds on one SM; this path does O(n^3) work once and only for the
+// eigenvectors the truncation reads:
+//   1. Householder reduction A = Q T Q^T in shared memory (one CTA per matrix);
+//   2. the nvec largest eigenvalues of T by bisection on Sturm counts (one thread each);
+//   3. their eigenvectors of T by inverse iteration (LU with partial pivoting of T - lambda I,
+//      three solves from a hashed start vector; one thread each);
+//   4. classical Gram-Schmidt applied twice (near-degenerate eigenvalues give non-orthogonal
+//      inverse-iteration vectors), then the back-transformation Q z.
+// Eigenvalues are accurate to about u ||A|| (the rank threshold of the truncation is
+// eps^2/(2d - 3) ||A|| with eps >= 1e-8, far above).  Outputs follow EigJob::tri.
+// Work layout (doubles): [0, n^2) Householder vectors (v_k in row k, entries k+1..n-1), then
+// tau[n], d[n], e[n], lambda[n] (descending), Z[nvec][n].
+// ---------------------------------------------------------------------------------------
+constexpr int TRI_THREADS = 512;
+constexpr int TRI_EIG_PER_CTA = 8;
+
+__device__ __forceinline__ bool tri_active(const EigJob& job) {
+  return job.tri && job.work[TRI_FLAG] != 0.0;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+__global__ void __launch_bounds__(TRI_THREADS) k_tri_reduce(const EigJob* jobs) {
+  extern __shared__ double sA[];
+  __shared__ double sp[SLAR_MAX_N];
+  __shared__ double red[TRI_THREADS / 32];
+  __shared__ double s_tau, s_beta;
+  const EigJob job = jobs[blockIdx.x];
+  if (!tri_active(job)) return;
+  const int n = job.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = TRI_THREADS / 32;
+  double* wk = job.work;
+  double* tau = wk + n * n;
+  double* dg = tau + n;
+  double* ed = dg + n;
+  for (int it = tid; it < n * n; it += TRI_THREADS) sA[it] = job.A[it];
+  __syncthreads();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double* x = sA + k * n + k + 1;   // row k beyond the diagonal = column k below it
+    double ss = 0.0;
+    for (int i = 1 + tid; i < m; i += TRI_THREADS) ss += x[i] * x[i];
+    const double sigma = block_sum(ss, red);
+    if (tid == 0) {
+      // H = I - t v v^T with v = x - beta e_1, H x = beta e_1 (beta of sign opposite to x_0)
+      const double x0 = x[0];
+      double t = 0.0, beta = x0;
+      if (sigma > 0.0) {
+        const double alpha = sqrt(x0 * x0 + sigma);
+        beta = x0 >= 0.0 ? -alpha : alpha;
+        const double v0 = x0 - beta;
+        t = 2.0 / (sigma + v0 * v0);
+        x[0] = v0;
+      }
+      s_tau = t;
+      s_beta = beta;
+      tau[k] = t;
+      dg[k] = sA[k * n + k];
+      ed[k] = beta;
+    }
+    __syncthreads();
+    const double t = s_tau;
+    for (int i = k + 1 + tid; i < n; i += TRI_THREADS) wk[k * n + i] = sA[k * n + i];
+    if (t == 0.0) continue;
+    // p = t A' v (a warp per row), w = p - (t/2)(p.v) v, A' <- A' - v w^T - w v^T
+    for (int i = k + 1 + warp; i < n; i += NW) {
+      double acc = 0.0;
+      for (int j = k + 1 + lane; j < n; j += 32) acc += sA[i * n + j] * sA[k * n + j];
+      acc = warp_sum_d(acc);
+      if (lane == 0) sp[i] = t * acc;
+    }
+    __syncthreads();
+    double pv = 0.0;
+    for (int i = k + 1 + tid; i < n; i += TRI_THREADS) pv += sp[i] * sA[k * n + i];
+    const double K = 0.5 * t * block_sum(pv, red);
+    for (int i = k + 1 + tid; i < n; i += TRI_THREADS) sp[i] -= K * sA[k * n + i];
+    __syncthreads();
+    for (int it = tid; it < m * m; it += TRI_THREADS) {
+      const int i = k + 1 + it / m, j = k + 1 + it % m;
+      sA[i * n + j] -= sA[k * n + i] * sp[j] + sp[i] * sA[k * n + j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      dg[n - 2] = sA[(n - 2) * n + n - 2];
+      ed[n - 2] = sA[(n - 2) * n + n - 1];
+      tau[n - 2] = 0.0;
+    }
+    dg[n - 1] = sA[(n - 1) * n + n - 1];
+    tau[n - 1] = 0.0;
+  }
+}
+
+// Gershgorin interval of T and the pivot floor of the Sturm recurrence
+__device__ void tri_bounds(const double* d, const double* e, int n, double* gl, double* gu, double* pivmin) {
+  double lo = 1e300, hi = -1e300, e2max = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double r = (j > 0 ? fabs(e[j - 1]) : 0.0) + (j + 1 < n ? fabs(e[j]) : 0.0);
+    lo = fmin(lo, d[j] - r);
+    hi = fmax(hi, d[j] + r);
+    if (j + 1 < n) e2max = fmax(e2max, e[j] * e[j]);
+  }
+  const double bn = fmax(fabs(lo), fabs(hi));
+  *pivmin = 2.2250738585072014e-308 * fmax(1.0, e2max);
+  *gl = lo - 2.220446049250313e-16 * bn * n - *pivmin;
+  *gu = hi + 2.220446049250313e-16 * bn * n + *pivmin;
+}
+
+// number of eigenvalues of T below x (Sturm sequence of the LDL^T factorisation of T - x I)
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int n, double x, double pivmin) {
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int c = q < 0.0;
+  for (int j = 1; j < n; ++j) {
+    q = (d[j] - x) - e2[j - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < 0.0;
+  }
+  return c;
+}
+
+__global__ void k_tri_bisect(const EigJob* jobs) {
+  __shared__ double sd[SLAR_MAX_N], se[SLAR_MAX_N], se2[SLAR_MAX_N];
+  const EigJob job = jobs[blockIdx.y];
+  if (!tri_active(job)) return;
+  const int n = job.n;
+  const double* wk = job.work;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    sd[j] = wk[n * n + n + j];
+    se[j] = j + 1 < n ? wk[n * n + 2 * n + j] : 0.0;
+    se2[j] = se[j] * se[j];
+  }
+  __syncthreads();
+  const int tp = blockIdx.x * blockDim.x + threadIdx.x;   // rank from the largest
+  if (tp >= job.nvec) return;
+  double lo, hi, pivmin;
+  tri_bounds(sd, se, n, &lo, &hi, &pivmin);
+  const double tol = 4.440892098500626e-16 * fmax(fabs(lo), fabs(hi)) + pivmin;
+  const int i = n - 1 - tp;                               // ascending index
+  for (int it = 0; it < 96 && hi - lo > tol; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(sd, se2, n, mid, pivmin) > i) hi = mid;
+    else lo = mid;
+  }
+  job.work[n * n + 3 * n + tp] = 0.5 * (lo + hi);
+}
+
+__device__ __forceinline__ double hash_unit(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 1.1102230246251565e-16 - 0.5;
+}
+
+// inverse iteration on T for the eigenvalue of rank tp: Gaussian elimination with partial
+// pivoting of T - lambda I (two superdiagonals of fill), zero pivots replaced by `tiny`
+__global__ void k_tri_vec(const EigJob* jobs) {
+  const EigJob job = jobs[blockIdx.y];
+  if (!tri_active(job)) return;
+  const int n = job.n;
+  const int tp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tp >= job.nvec) return;
+  double* wk = job.work;
+  const double* d = wk + n * n + n;
+  const double* e = d + n;
+  const double* lam = e + n;
+  double* z = wk + n * n + 4 * n + (long long)tp * n;
+  const double tiny = 2.220446049250313e-16 * fmax(fabs(lam[0]), fabs(lam[job.nvec - 1])) + 1e-300;
+  const double l = lam[tp];
+  double dd[SLAR_MAX_N], dl[SLAR_MAX_N], du[SLAR_MAX_N], du2[SLAR_MAX_N], b[SLAR_MAX_N];
+  unsigned char ip[SLAR_MAX_N];
+  for (int i = 0; i < n; ++i) b[i] = hash_unit((unsigned long long)tp * 1024ull + i);
+  for (int it = 0; it < 3; ++it) {
+    for (int i = 0; i < n; ++i) {
+      dd[i] = d[i] - l;
+      dl[i] = i + 1 < n ? e[i] : 0.0;
+      du[i] = dl[i];
+      du2[i] = 0.0;
+    }
+    for (int i = 0; i + 1 < n; ++i) {
+      if (fabs(dd[i]) >= fabs(dl[i])) {
+        if (dd[i] == 0.0) dd[i] = tiny;
+        const double f = dl[i] / dd[i];
+        dl[i] = f;
+        dd[i + 1] -= f * du[i];
+        ip[i] = 0;
+      } else {
+        const double f = dd[i] / dl[i];
+        dd[i] = dl[i];
+        dl[i] = f;
+        const double tmp = du[i];
+        du[i] = dd[i + 1];
+        dd[i + 1] = tmp - f * dd[i + 1];
+        if (i + 2 < n) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du[i + 1];
+        }
+        ip[i] = 1;
+      }
+    }
+    if (dd[n - 1] == 0.0) dd[n - 1] = tiny;
+    for (int i = 0; i + 1 < n; ++i) {
+      if (ip[i]) {
+        const double t = b[i] - dl[i] * b[i + 1];
+        b[i] = b[i + 1];
+        b[i + 1] = t;
+      } else {
+        b[i + 1] -= dl[i] * b[i];
+      }
+    }
+    b[n - 1] /= dd[n - 1];
+    if (n >= 2) b[n - 2] = (b[n - 2] - du[n - 2] * b[n - 1]) / dd[n - 2];
+    for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(b[i]));
+    if (!(mx > 0.0) || !isfinite(mx)) {
+      for (int i = 0; i < n; ++i) b[i] = hash_unit((unsigned long long)tp * 1024ull + 512ull + i);
+      continue;
+    }
+    double s2 = 0.0;
+    for (int i = 0; i < n; ++i) { b[i] /= mx; s2 += b[i] * b[i]; }
+    const double inv = 1.0 / sqrt(s2);
+    for (int i = 0; i < n; ++i) b[i] *= inv;
+  }
+  for (int i = 0; i < n; ++i) z[i] = b[i];
+}
+
+// CGS2 of the inverse-iteration vectors (largest eigenvalue first), back-transformation
+// y = H_0 ... H_{n-3} z, and the outputs of EigJob::tri
+__global__ void __launch_bounds__(256) k_tri_finish(const EigJob* jobs) {
+  extern __shared__ double sZ[];            // nvec columns of n
+  __shared__ double sc[SLAR_MAX_N];
+  __shared__ double sv[SLAR_MAX_N];
+  __shared__ double red[8];
+  const EigJob job = jobs[blockIdx.x];
+  if (!tri_active(job)) return;
+  const int n = job.n, nv = job.nvec, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* wk = job.work;
+  const double* tau = wk + n * n;
+  const double* lam = wk + n * n + 3 * n;
+  for (int it = tid; it < nv * n; it += 256) sZ[it] = wk[n * n + 4 * n + it];
+  __syncthreads();
+  for (int t = 0; t < nv; ++t) {
+    double* zt = sZ + t * n;
+    for (int pass = 0; pass < 2 && t > 0; ++pass) {
+      for (int q = warp; q < t; q += 8) {
+        double acc = 0.0;
+        for (int i = lane; i < n; i += 32) acc += sZ[q * n + i] * zt[i];
+        acc = warp_sum_d(acc);
+        if (lane == 0) sc[q] = acc;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += 256) {
+        double acc = 0.0;
+        for (int q = 0; q < t; ++q) acc += sc[q] * sZ[q * n + i];
+        zt[i] -= acc;
+      }
+      __syncthreads();
+    }
+    double ss = 0.0;
+    for (int i = tid; i < n; i += 256) ss += zt[i] * zt[i];
+    const double nrm2 = block_sum(ss, red);
+    const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+    for (int i = tid; i < n; i += 256) zt[i] *= inv;
+    __syncthreads();
+  }
+  for (int k = n - 3; k >= 0; --k) {
+    const double t = tau[k];
+    if (t == 0.0) continue;
+    for (int i = k + 1 + tid; i < n; i += 256) sv[i] = wk[k * n + i];
+    __syncthreads();
+    for (int q = warp; q < nv; q += 8) {
+      double acc = 0.0;
+      for (int i = k + 1 + lane; i < n; i += 32) acc += sv[i] * sZ[q * n + i];
+      acc = warp_sum_d(acc);
+      if (lane == 0) sc[q] = t * acc;
+    }
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int it = tid; it < nv * m; it += 256) {
+      const int q = it / m, i = k + 1 + it % m;
+      sZ[q * n + i] -= sc[q] * sv[i];
+    }
+    __syncthreads();
+  }
+  for (int it = tid; it < n * n; it += 256) {
+    const int r = it / n, q = it % n;
+    job.V[it] = q < nv ? sZ[q * n + r] : 0.0;
+  }
+  if (tid == 0) {
+    double kept = 0.0;
+    for (int q = 0; q < nv; ++q) {
+      const double l = lam[q] > 0.0 ? lam[q] : 0.0;
+      job.W[q] = l;
+      kept += l;
+    }
+    for (int q = nv; q < n; ++q) job.W[q] = 0.0;
+    if (nv < n) job.W[nv] = fmax(wk[TRI_TRACE] - kept, 0.0);
+  }
 }
 
 __global__ void k_choose_ranks(RankJob* jobs, int njobs, const double* normF2, double scale) {
@@ -736,7 +1061,13 @@ cudaError_t linalg_init_attrs() {
   if (e != cudaSuccess) return e;
   size_t sm = sizeof(double) * EIG_SMEM_DOUBLES;
   if (sm < sizeof(double) * SLAR_MAX_N * SLAR_MAX_N) sm = sizeof(double) * SLAR_MAX_N * SLAR_MAX_N;
-  return cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tri_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * SLAR_MAX_N * SLAR_MAX_N));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_tri_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(double) * SLAR_MAX_N * SLAR_MAX_RANK));
 }
 
 cudaError_t chol_inv(const double* G, int n, double* R, double* Rinv, int* info, cudaStream_t s) {
@@ -768,6 +1099,22 @@ cudaError_t eig_batched(const EigJob* jobs_host, int njobs, EigJob* jobs_dev, cu
                                   cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   slar::count_launch(), k_jacobi<<<njobs, EIG_THREADS, sm, s>>>(jobs_dev, (long long)(sm / sizeof(double)));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // jobs that k_jacobi handed over (flag in their work array) go through the tridiagonal
+  // solver; the kernels return at once for the others
+  int ntri = 0, nvmax = 0;
+  for (int i = 0; i < njobs; ++i)
+    if (jobs_host[i].tri) {
+      ++ntri;
+      nvmax = jobs_host[i].nvec > nvmax ? jobs_host[i].nvec : nvmax;
+    }
+  if (ntri == 0) return cudaSuccess;
+  slar::count_launch(), k_tri_reduce<<<njobs, TRI_THREADS, sizeof(double) * nmax * nmax, s>>>(jobs_dev);
+  const dim3 gv((nvmax + TRI_EIG_PER_CTA - 1) / TRI_EIG_PER_CTA, njobs);
+  slar::count_launch(), k_tri_bisect<<<gv, TRI_EIG_PER_CTA, 0, s>>>(jobs_dev);
+  slar::count_launch(), k_tri_vec<<<gv, TRI_EIG_PER_CTA, 0, s>>>(jobs_dev);
+  slar::count_launch(), k_tri_finish<<<njobs, 256, sizeof(double) * nvmax * nmax, s>>>(jobs_dev);
   return cudaGetLastError();
 }
 

@@ -79,6 +79,52 @@ __device__ void contract_node_res(const T* __restrict__ ca, int ra, const T* __r
   }
 }
 
+// The same contraction for small output ranks (rp <= PPER * NTHREADS / TILE): thread
+// (t, q) with TPE = NTHREADS / TILE threads per entry accumulates p = q, q + TPE, ...
+// (PPER outputs).  Lanes over p, as above, would leave most of a warp idle at the ranks of
+// weakly perturbed runs (4-20); here every lane works and each product ca cb is formed once
+// per thread for its PPER outputs.
+template <typename T, int TILE, int PPER>
+__device__ void contract_node_res_small(const T* __restrict__ ca, int ra, const T* __restrict__ cb, int rb,
+                                        const T* __restrict__ sBn, int rp, T* __restrict__ cout, int nT) {
+  constexpr int TPE = NTHREADS / TILE;
+  const int t = threadIdx.x / TPE, q = threadIdx.x - t * TPE;
+  T acc[PPER];
+#pragma unroll
+  for (int j = 0; j < PPER; ++j) acc[j] = T(0);
+  const T* cat = ca + t * ra;
+  const T* cbt = cb + t * rb;
+  int kk = 0;
+  for (int a = 0; a < ra; ++a) {
+    const T xa = cat[a];
+    for (int b = 0; b < rb; ++b, ++kk) {
+      const T x = xa * cbt[b];
+      const T* Bk = sBn + kk * rp;
+#pragma unroll
+      for (int j = 0; j < PPER; ++j) {
+        const int p = q + j * TPE;
+        if (p < rp) acc[j] += x * Bk[p];
+      }
+    }
+  }
+  if (t < nT) {
+#pragma unroll
+    for (int j = 0; j < PPER; ++j) {
+      const int p = q + j * TPE;
+      if (p < rp) cout[t * rp + p] = acc[j];
+    }
+  }
+}
+
+template <typename T, int TILE>
+__device__ __forceinline__ void contract_res(const T* ca, int ra, const T* cb, int rb, const T* sBn, int rp,
+                                             T* cout, int nT) {
+  constexpr int TPE = NTHREADS / TILE;
+  if (rp <= 2 * TPE) contract_node_res_small<T, TILE, 2>(ca, ra, cb, rb, sBn, rp, cout, nT);
+  else if (rp <= 4 * TPE) contract_node_res_small<T, TILE, 4>(ca, ra, cb, rb, sBn, rp, cout, nT);
+  else contract_node_res<T, TILE>(ca, ra, cb, rb, sBn, rp, cout, nT);
+}
+
 // c_out[t][p] = sum_{a,b} ca[t][a] cb[t][b] B[p][a][b]   for t < nT, p < rp
 template <typename T, int TILE>
 __device__ void contract_node(const T* __restrict__ ca, int ra, const T* __restrict__ cb, int rb,
@@ -281,8 +327,8 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
   int rl, rr;
   if (d == 4) {
     if (resident) {
-      contract_node_res<T, TILE>(sc_mu[0], ht.r[0], sc_mu[1], ht.r[1], sB, ht.r12, sc12, nT);
-      contract_node_res<T, TILE>(sc_mu[2], ht.r[2], sc_mu[3], ht.r[3], sB + K12 * ht.r12, ht.r34, sc34, nT);
+      contract_res<T, TILE>(sc_mu[0], ht.r[0], sc_mu[1], ht.r[1], sB, ht.r12, sc12, nT);
+      contract_res<T, TILE>(sc_mu[2], ht.r[2], sc_mu[3], ht.r[3], sB + K12 * ht.r12, ht.r34, sc34, nT);
     } else {
       contract_node<T, TILE>(sc_mu[0], ht.r[0], sc_mu[1], ht.r[1], ht.B12, ht.r12, sc12, sB, nT);
       contract_node<T, TILE>(sc_mu[2], ht.r[2], sc_mu[3], ht.r[3], ht.B34, ht.r34, sc34, sB, nT);

@@ -138,6 +138,36 @@ def test_truncate_matches_oracle(N, ranks, eps, cap):
         assert abs(abs(float(ex["U"][m][:, 0] @ want.U[m][:, 0])) - 1.0) < 1e-9
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("cap", [64, 41])
+@pytest.mark.parametrize("N,ranks", [((64, 64, 8, 8), (44, 45, 8, 8, 6, 6)),
+                                     ((16, 16, 8, 8), (6, 8, 8, 8, 44, 43))])
+def test_truncate_tridiagonal_path_matches_oracle(precision, cap, N, ranks):
+    """FP32 / BF16x3 data: node Gram matrices of numerical rank above 40 (Gaussian factors;
+    first case the spatial leaves, orders 44 and 45; second case the transfer nodes, orders
+    44 and 43) go to the tridiagonal eigensolver (Householder reduction, bisection, inverse
+    iteration, back-transformation), which returns the cap leading eigenpairs and the rest
+    of the trace; the other nodes stay on Jacobi.  The truncation itself stays FP64 and must
+    agree with the oracle's HSVD (numpy eigh); cap 41 < order exercises the tail-trace rank
+    rule."""
+    eps = 1e-5
+    ctx, g = ctx_for(N, eps=eps, cap=cap, precision=precision)
+    h, _, _ = rand_state(N, ranks, 31, smooth=False)
+    load(ctx, h)
+    ctx.truncate(eps, cap)
+    ex = ctx.export()
+    want, info = htmod.truncate(h, eps, cap, return_info=True)
+    assert ex["ranks"][: len(info["ranks"])] == info["ranks"]
+    assert max(info["ranks"]) > 40
+    got = htmod.densify(convert.from_lib(ex))
+    assert relerr(got, htmod.densify(want)) < 1e-9
+    for m in range(len(N)):
+        assert abs(abs(float(ex["U"][m][:, 0] @ want.U[m][:, 0])) - 1.0) < 1e-9
+        Um = ex["U"][m]
+        assert np.abs(Um.T @ Um - np.eye(Um.shape[1])).max() < 1e-12
+    ctx.close()
+
+
 @pytest.mark.parametrize("w", [inputs.landau_1d1v(N=(32, 64), alpha=0.05),
                                inputs.landau_2d2v(n=16, alpha=0.05, eps=1e-6, cap=12),
                                inputs.two_stream_2d2v(n=16, eps=1e-5, cap=12)])
