@@ -103,7 +103,10 @@ k_aca_row_pivot(const double* __restrict__ r, int M2, unsigned char* usedc, int*
     return;
   }
   const double piv = r[j];
-  for (int i = threadIdx.x; i < M2; i += PIV_THREADS) vout[i] = r[i] / piv;
+  // one reciprocal instead of M2 FP64 divisions on this single CTA (a division costs about
+  // eight FP64-pipe instructions); v_k[j] = 1 exactly
+  const double inv = 1.0 / piv;
+  for (int i = threadIdx.x; i < M2; i += PIV_THREADS) vout[i] = i == j ? 1.0 : r[i] * inv;
   if (threadIdx.x == 0) {
     pivJ[kk] = j;
     usedc[j] = 1;

@@ -631,11 +631,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
 // tens of milliseconds on one SM; this path does O(n^3) work once and only for the
 // eigenvectors the truncation reads:
 //   1. Householder reduction A = Q T Q^T in shared memory (one CTA per matrix);
-//   2. the nvec largest eigenvalues of T by bisection on Sturm counts (one thread each);
+//   2. the nvec largest eigenvalues of T by multisection on Sturm counts (8 lanes each);
 //   3. their eigenvectors of T by inverse iteration (LU with partial pivoting of T - lambda I,
 //      three solves from a hashed start vector; one thread each);
 //   4. classical Gram-Schmidt applied twice (near-degenerate eigenvalues give non-orthogonal
-//      inverse-iteration vectors), then the back-transformation Q z.
+//      inverse-iteration vectors), then the back-transformation Q z (8 vectors per CTA).
 // Eigenvalues are accurate to about u ||A|| (the rank threshold of the truncation is
 // eps^2/(2d - 3) ||A|| with eps >= 1e-8, far above).  Outputs follow EigJob::tri.
 // Work layout (doubles): [0, n^2) Householder vectors (v_k in row k, entries k+1..n-1), then
@@ -708,9 +708,9 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_reduce(const EigJob* jobs) 
     const double K = 0.5 * t * block_sum(pv, red);
     for (int i = k + 1 + tid; i < n; i += TRI_THREADS) sp[i] -= K * sA[k * n + i];
     __syncthreads();
-    for (int it = tid; it < m * m; it += TRI_THREADS) {
-      const int i = k + 1 + it / m, j = k + 1 + it % m;
-      sA[i * n + j] -= sA[k * n + i] * sp[j] + sp[i] * sA[k * n + j];
+    for (int i = k + 1 + warp; i < n; i += NW) {
+      const double vi = sA[k * n + i], wi = sp[i];
+      for (int j = k + 1 + lane; j < n; j += 32) sA[i * n + j] -= vi * sp[j] + wi * sA[k * n + j];
     }
     __syncthreads();
   }
@@ -753,7 +753,16 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
   return c;
 }
 
-__global__ void k_tri_bisect(const EigJob* jobs) {
+// The nvec largest eigenvalues by multisection: 8 lanes per eigenvalue count the eigenvalues
+// below 8 interior points of its interval, and the first point whose count exceeds the
+// eigenvalue's index bounds the next interval (9 subintervals per pass: 20 passes shrink the
+// Gershgorin interval by 9^20 > 2^63, below the rounding level).  Four eigenvalues per warp,
+// one warp per CTA: the dependent Sturm recurrences are latency-bound, so they are spread over
+// as many SMs as there are eigenvalue groups.
+constexpr int MS_LANES = 8;
+constexpr int MS_PASSES = 20;
+
+__global__ void __launch_bounds__(32) k_tri_bisect(const EigJob* jobs) {
   __shared__ double sd[SLAR_MAX_N], se[SLAR_MAX_N], se2[SLAR_MAX_N];
   const EigJob job = jobs[blockIdx.y];
   if (!tri_active(job)) return;
@@ -765,18 +774,23 @@ __global__ void k_tri_bisect(const EigJob* jobs) {
     se2[j] = se[j] * se[j];
   }
   __syncthreads();
-  const int tp = blockIdx.x * blockDim.x + threadIdx.x;   // rank from the largest
-  if (tp >= job.nvec) return;
+  const int grp = threadIdx.x / MS_LANES, l = threadIdx.x % MS_LANES;
+  const int tp = blockIdx.x * (32 / MS_LANES) + grp;      // rank from the largest
+  const bool valid = tp < job.nvec;
+  const int i = n - 1 - (valid ? tp : 0);                 // ascending index
   double lo, hi, pivmin;
   tri_bounds(sd, se, n, &lo, &hi, &pivmin);
-  const double tol = 4.440892098500626e-16 * fmax(fabs(lo), fabs(hi)) + pivmin;
-  const int i = n - 1 - tp;                               // ascending index
-  for (int it = 0; it < 96 && hi - lo > tol; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (sturm_count(sd, se2, n, mid, pivmin) > i) hi = mid;
-    else lo = mid;
+  for (int pass = 0; pass < MS_PASSES; ++pass) {
+    const double w = (hi - lo) / (double)(MS_LANES + 1);
+    const int c = sturm_count(sd, se2, n, lo + (l + 1) * w, pivmin);
+    const unsigned above = (__ballot_sync(0xffffffffu, c > i) >> (grp * MS_LANES)) & ((1u << MS_LANES) - 1);
+    const int first = above ? __ffs(above) - 1 : MS_LANES;   // first point with lambda_i below it
+    const double nlo = first == 0 ? lo : lo + first * w;
+    const double nhi = first == MS_LANES ? hi : lo + (first + 1) * w;
+    lo = nlo;
+    hi = nhi;
   }
-  job.work[n * n + 3 * n + tp] = 0.5 * (lo + hi);
+  if (valid && l == 0) job.work[n * n + 3 * n + tp] = 0.5 * (lo + hi);
 }
 
 __device__ __forceinline__ double hash_unit(unsigned long long z) {
@@ -860,20 +874,17 @@ __global__ void k_tri_vec(const EigJob* jobs) {
   for (int i = 0; i < n; ++i) z[i] = b[i];
 }
 
-// CGS2 of the inverse-iteration vectors (largest eigenvalue first), back-transformation
-// y = H_0 ... H_{n-3} z, and the outputs of EigJob::tri
-__global__ void __launch_bounds__(256) k_tri_finish(const EigJob* jobs) {
+// CGS2 of the inverse-iteration vectors (largest eigenvalue first), in place in the work
+// array
+__global__ void __launch_bounds__(256) k_tri_orth(const EigJob* jobs) {
   extern __shared__ double sZ[];            // nvec columns of n
   __shared__ double sc[SLAR_MAX_N];
-  __shared__ double sv[SLAR_MAX_N];
   __shared__ double red[8];
   const EigJob job = jobs[blockIdx.x];
   if (!tri_active(job)) return;
   const int n = job.n, nv = job.nvec, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double* wk = job.work;
-  const double* tau = wk + n * n;
-  const double* lam = wk + n * n + 3 * n;
-  for (int it = tid; it < nv * n; it += 256) sZ[it] = wk[n * n + 4 * n + it];
+  double* zg = job.work + n * n + 4 * n;
+  for (int it = tid; it < nv * n; it += 256) sZ[it] = zg[it];
   __syncthreads();
   for (int t = 0; t < nv; ++t) {
     double* zt = sZ + t * n;
@@ -899,30 +910,25 @@ __global__ void __launch_bounds__(256) k_tri_finish(const EigJob* jobs) {
     for (int i = tid; i < n; i += 256) zt[i] *= inv;
     __syncthreads();
   }
-  for (int k = n - 3; k >= 0; --k) {
-    const double t = tau[k];
-    if (t == 0.0) continue;
-    for (int i = k + 1 + tid; i < n; i += 256) sv[i] = wk[k * n + i];
-    __syncthreads();
-    for (int q = warp; q < nv; q += 8) {
-      double acc = 0.0;
-      for (int i = k + 1 + lane; i < n; i += 32) acc += sv[i] * sZ[q * n + i];
-      acc = warp_sum_d(acc);
-      if (lane == 0) sc[q] = t * acc;
-    }
-    __syncthreads();
-    const int m = n - k - 1;
-    for (int it = tid; it < nv * m; it += 256) {
-      const int q = it / m, i = k + 1 + it % m;
-      sZ[q * n + i] -= sc[q] * sv[i];
-    }
-    __syncthreads();
-  }
-  for (int it = tid; it < n * n; it += 256) {
-    const int r = it / n, q = it % n;
-    job.V[it] = q < nv ? sZ[q * n + r] : 0.0;
-  }
-  if (tid == 0) {
+  for (int it = tid; it < nv * n; it += 256) zg[it] = sZ[it];
+}
+
+// back-transformation y = H_0 ... H_{n-3} z of TRI_BACK_COLS vectors per CTA, and the
+// outputs of EigJob::tri (CTA 0 also writes W and the unused columns of V)
+constexpr int TRI_BACK_COLS = 8;
+
+__global__ void __launch_bounds__(256) k_tri_back(const EigJob* jobs) {
+  __shared__ double sZ[TRI_BACK_COLS * SLAR_MAX_N];
+  __shared__ double sv[SLAR_MAX_N];
+  __shared__ double sc[TRI_BACK_COLS];
+  const EigJob job = jobs[blockIdx.y];
+  if (!tri_active(job)) return;
+  const int n = job.n, nv = job.nvec, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int q0 = blockIdx.x * TRI_BACK_COLS;
+  const double* wk = job.work;
+  const double* tau = wk + n * n;
+  const double* lam = wk + n * n + 3 * n;
+  if (blockIdx.x == 0 && tid == 0) {
     double kept = 0.0;
     for (int q = 0; q < nv; ++q) {
       const double l = lam[q] > 0.0 ? lam[q] : 0.0;
@@ -931,6 +937,38 @@ __global__ void __launch_bounds__(256) k_tri_finish(const EigJob* jobs) {
     }
     for (int q = nv; q < n; ++q) job.W[q] = 0.0;
     if (nv < n) job.W[nv] = fmax(wk[TRI_TRACE] - kept, 0.0);
+  }
+  if (blockIdx.x == 0)
+    for (int it = tid; it < n * (n - nv); it += 256) {
+      const int r = it / (n - nv), q = nv + it % (n - nv);
+      job.V[r * n + q] = 0.0;
+    }
+  const int nc = min(TRI_BACK_COLS, nv - q0);
+  if (nc <= 0) return;
+  for (int it = tid; it < nc * n; it += 256) sZ[it] = wk[n * n + 4 * n + (long long)q0 * n + it];
+  __syncthreads();
+  for (int k = n - 3; k >= 0; --k) {
+    const double t = tau[k];
+    if (t == 0.0) continue;
+    for (int i = k + 1 + tid; i < n; i += 256) sv[i] = wk[k * n + i];
+    __syncthreads();
+    if (warp < nc) {
+      double acc = 0.0;
+      for (int i = k + 1 + lane; i < n; i += 32) acc += sv[i] * sZ[warp * n + i];
+      acc = warp_sum_d(acc);
+      if (lane == 0) sc[warp] = t * acc;
+    }
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int it = tid; it < nc * m; it += 256) {
+      const int q = it / m, i = k + 1 + it - q * m;
+      sZ[q * n + i] -= sc[q] * sv[i];
+    }
+    __syncthreads();
+  }
+  for (int it = tid; it < n * nc; it += 256) {
+    const int r = it / nc, q = it % nc;
+    job.V[r * n + q0 + q] = sZ[q * n + r];
   }
 }
 
@@ -1066,7 +1104,7 @@ cudaError_t linalg_init_attrs() {
   e = cudaFuncSetAttribute(k_tri_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * SLAR_MAX_N * SLAR_MAX_N));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_tri_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_tri_orth, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(sizeof(double) * SLAR_MAX_N * SLAR_MAX_RANK));
 }
 
@@ -1111,10 +1149,13 @@ cudaError_t eig_batched(const EigJob* jobs_host, int njobs, EigJob* jobs_dev, cu
     }
   if (ntri == 0) return cudaSuccess;
   slar::count_launch(), k_tri_reduce<<<njobs, TRI_THREADS, sizeof(double) * nmax * nmax, s>>>(jobs_dev);
+  const dim3 gb((nvmax + 32 / MS_LANES - 1) / (32 / MS_LANES), njobs);
+  slar::count_launch(), k_tri_bisect<<<gb, 32, 0, s>>>(jobs_dev);
   const dim3 gv((nvmax + TRI_EIG_PER_CTA - 1) / TRI_EIG_PER_CTA, njobs);
-  slar::count_launch(), k_tri_bisect<<<gv, TRI_EIG_PER_CTA, 0, s>>>(jobs_dev);
   slar::count_launch(), k_tri_vec<<<gv, TRI_EIG_PER_CTA, 0, s>>>(jobs_dev);
-  slar::count_launch(), k_tri_finish<<<njobs, 256, sizeof(double) * nvmax * nmax, s>>>(jobs_dev);
+  slar::count_launch(), k_tri_orth<<<njobs, 256, sizeof(double) * nvmax * nmax, s>>>(jobs_dev);
+  const dim3 gt((nvmax + TRI_BACK_COLS - 1) / TRI_BACK_COLS, njobs);
+  slar::count_launch(), k_tri_back<<<gt, 256, 0, s>>>(jobs_dev);
   return cudaGetLastError();
 }
 
