@@ -36,7 +36,7 @@ FP64_PEAK_TFLOPS = 1.25                              # nominal B300 FP64 (recipe
 # DRAM bytes (read + write) per launch of the FP32 entry evaluator (k_sl_eval_dev<float, 32>)
 # on this workload, from the ncu launch list in profiles/launch_list_landau_2d2v_64.md (cold
 # cache, one BDF3 step)
-EVAL_TRAFFIC_BYTES = 277.2e3
+EVAL_TRAFFIC_BYTES = 282.2e3
 
 
 def parse():
@@ -485,7 +485,10 @@ def run_ours(args, w):
                          "method": "separate profiled pass of 3 steps: CUDA events around each "
                                    "evaluator launch on the library stream; algorithmic flops "
                                    "2(3 sum r_mu + r0 r1 r12 + r2 r3 r34 + r12 r34) + 60 per entry",
-                         "eval_ms_per_step": eval_ms / 3.0},
+                         "eval_ms_per_step": eval_ms / 3.0,
+                         "step_shares": "cold-cache ncu launch list of one BDF3 step "
+                                        "(profiles/launch_list_landau_2d2v_64.md): FFT passes "
+                                        "k_fft_lines 21 %, this evaluator 14 %; both latency-bound"},
             "phase_ms_per_step": phases,
             "gpu_launches": launches, "wall_s": wall, "clocks": clocks, "e2e": e2e}
     if not args.no_cpu_baseline and world == 1:
