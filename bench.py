@@ -488,7 +488,7 @@ def run_ours(args, w):
                          "eval_ms_per_step": eval_ms / 3.0,
                          "step_shares": "cold-cache ncu launch list of one BDF3 step "
                                         "(profiles/launch_list_landau_2d2v_64.md): FFT passes "
-                                        "k_fft_lines 21 %, this evaluator 14 %; both latency-bound"},
+                                        "k_fft_lines 22 %, this evaluator 14 %; both latency-bound"},
             "phase_ms_per_step": phases,
             "gpu_launches": launches, "wall_s": wall, "clocks": clocks, "e2e": e2e}
     if not args.no_cpu_baseline and world == 1:

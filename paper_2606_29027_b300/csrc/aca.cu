@@ -26,20 +26,83 @@ namespace {
 
 constexpr int PIV_THREADS = 1024;
 constexpr int ACA_UNROLL = 2;      // pivot steps per iteration of the captured WHILE loop
-constexpr int DOT_SEG = 256;
+constexpr int DOT_SEG = 256;      // entries per dot-product block (= its thread count)
 constexpr double TIE_RTOL = 1e-10;
+
+// |a| as an order key on the integer pipe: for non-negative doubles the IEEE-754 bit pattern
+// orders like the value, so the scans below compare 64-bit integers instead of issuing FP64
+// compares (B300 retires about two FP64 operations per clock per SM).  Used entries and NaNs
+// get key -1, as fmax / >= ignore NaNs.
+__device__ __forceinline__ long long abs_key(double x) {
+  const long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+  return b > 0x7ff0000000000000LL ? -1LL : b;
+}
+
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long u = __shfl_down_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
 
 __device__ void block_argmax_tie(const double* a, int n, const unsigned char* used, int* out_idx,
                                  double* out_max) {
   // two passes: global max of |a| over unused, then the lowest index within the tie band
-  __shared__ double wmax[32];
+  __shared__ long long wmax[32];
   __shared__ int widx[32];
   const int nthr = blockDim.x, nw = blockDim.x >> 5;
-  __shared__ double top_s;
+  __shared__ long long top_s;
   const int tid = threadIdx.x;
+  long long m = -1;
+  for (int i = tid; i < n; i += nthr) {
+    const long long k = used[i] ? -1LL : abs_key(a[i]);
+    m = k > m ? k : m;
+  }
+  m = warp_max_ll(m);
+  if ((tid & 31) == 0) wmax[tid >> 5] = m;
+  __syncthreads();
+  if (tid == 0) {
+    long long t = -1;
+    for (int w = 0; w < nw; ++w) t = wmax[w] > t ? wmax[w] : t;
+    top_s = t;
+  }
+  __syncthreads();
+  const long long topk = top_s;
+  const double top = topk >= 0 ? __longlong_as_double(topk) : -1.0;
+  const long long thrk = topk >= 0 ? __double_as_longlong(top * (1.0 - TIE_RTOL)) : 0x7fffffffffffffffLL;
+  int best = 0x7fffffff;
+  if (topk >= 0)
+    for (int i = tid; i < n; i += nthr)
+      if (i < best && !used[i] && abs_key(a[i]) >= thrk) best = i;
+  for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, o));
+  if ((tid & 31) == 0) widx[tid >> 5] = best;
+  __syncthreads();
+  if (tid == 0) {
+    int b = 0x7fffffff;
+    for (int w = 0; w < nw; ++w) b = min(b, widx[w]);
+    *out_idx = (topk >= 0 && b != 0x7fffffff) ? b : -1;
+    *out_max = top;
+  }
+  __syncthreads();
+}
+
+// The same arg-max with tie band as block_argmax_tie over a = a fibre of n entries, from the
+// maxima of |a| over the unused entries of its DOT_SEG-entry segments (part[s * ldp + SEG_SLOT],
+// written by the blocks of k_aca_post): the global maximum is the largest segment maximum, and
+// the lowest index within the tie band lies in the first segment whose maximum reaches the
+// band, so only that segment is scanned.
+constexpr int SEG_SLOT = SLAR_MAX_RANK;   // slot of a partial-sum row left free by the dots (l < kmax)
+
+__device__ void segment_argmax_tie(const double* a, int n, const unsigned char* used, const double* part, int ldp,
+                                   int nseg, int* out_idx, double* out_max) {
+  __shared__ double wmax[32];
+  __shared__ int widx[32];
+  __shared__ double top_s;
+  __shared__ int seg_s;
+  const int tid = threadIdx.x, nthr = blockDim.x, nw = blockDim.x >> 5;
   double m = -1.0;
-  for (int i = tid; i < n; i += nthr)
-    if (!used[i]) m = fmax(m, fabs(a[i]));
+  for (int q = tid; q < nseg; q += nthr) m = fmax(m, __ldcg(part + (long long)q * ldp + SEG_SLOT));
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((tid & 31) == 0) wmax[tid >> 5] = m;
   __syncthreads();
@@ -51,11 +114,29 @@ __device__ void block_argmax_tie(const double* a, int n, const unsigned char* us
   __syncthreads();
   const double top = top_s;
   const double thr = top * (1.0 - TIE_RTOL);
-  int best = 0x7fffffff;
+  int fs = 0x7fffffff;
   if (top >= 0.0)
-    for (int i = tid; i < n; i += nthr)
-      if (!used[i] && fabs(a[i]) >= thr && i < best) best = i;
+    for (int q = tid; q < nseg; q += nthr)
+      if (__ldcg(part + (long long)q * ldp + SEG_SLOT) >= thr && q < fs) fs = q;
+  for (int o = 16; o > 0; o >>= 1) fs = min(fs, __shfl_down_sync(0xffffffffu, fs, o));
+  if ((tid & 31) == 0) widx[tid >> 5] = fs;
+  __syncthreads();
+  if (tid == 0) {
+    int b = 0x7fffffff;
+    for (int w = 0; w < nw; ++w) b = min(b, widx[w]);
+    seg_s = b;
+  }
+  __syncthreads();
+  const int seg = seg_s;
+  int best = 0x7fffffff;
+  if (top >= 0.0 && seg != 0x7fffffff) {
+    const long long thrk = __double_as_longlong(thr);
+    const int end = min(n, (seg + 1) * DOT_SEG);
+    for (int i = seg * DOT_SEG + tid; i < end; i += nthr)
+      if (i < best && !used[i] && abs_key(a[i]) >= thrk) best = i;
+  }
   for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, o));
+  __syncthreads();
   if ((tid & 31) == 0) widx[tid >> 5] = best;
   __syncthreads();
   if (tid == 0) {
@@ -196,7 +277,7 @@ __device__ void aca_finalize_body(const double* __restrict__ Ua, int M1, int kma
     }
     return;
   }
-  block_argmax_tie(Ua + (long long)kk * M1, M1, usedr, &i_s, &top_s);
+  segment_argmax_tie(Ua + (long long)kk * M1, M1, usedr, part, ldp, nbu, &i_s, &top_s);
   if (tid == 0) {
     if (i_s < 0) {
       st->done = 1;
@@ -238,6 +319,22 @@ k_aca_post(const double* __restrict__ Ua, int M1, const double* __restrict__ Va,
       for (int i = s0 + lane; i < s0 + DOT_SEG && i < M; i += 32) acc += xl[i] * xk[i];
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
       if (lane == 0) part[(long long)blk * ldp + l] = acc;
+    }
+    if (isu) {
+      // maximum of |u_k| over the unused rows of this segment, for the next row pivot
+      const int i = s0 + (int)threadIdx.x;   // DOT_SEG entries, one per thread
+      long long m = (i < M && !usedr[i]) ? abs_key(xk[i]) : -1LL;
+      m = warp_max_ll(m);
+      if (lane == 0) red[warp] = __longlong_as_double(m);   // bit copy (-1 maps to a NaN pattern)
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        long long t = -1;
+        for (int w = 0; w < 8; ++w) {
+          const long long u = __double_as_longlong(red[w]);
+          t = u > t ? u : t;
+        }
+        part[(long long)blk * ldp + SEG_SLOT] = t >= 0 ? __longlong_as_double(t) : -1.0;
+      }
     }
   } else if (!st->replay) {
     const int c = blk - nbu - nbv;
