@@ -32,21 +32,6 @@ __global__ void k_poisson_grad(Spectral sp, const double2* s_hat, double2* phi_h
       grad_hat[(long long)m * sp.NX + i] = make_double2(-sign * k[m] * ph.y, sign * k[m] * ph.x);
 }
 
-__global__ void k_div(Spectral sp, const double2* v_hat, int nvec, double2* out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y;
-  if (i >= sp.NX || v >= nvec) return;
-  double k[2];
-  kvec(sp, i, k);
-  double2 acc = make_double2(0.0, 0.0);
-  for (int m = 0; m < sp.dx; ++m) {
-    const double2 z = v_hat[((long long)v * sp.dx + m) * sp.NX + i];
-    acc.x += -k[m] * z.y;
-    acc.y += k[m] * z.x;
-  }
-  out[(long long)v * sp.NX + i] = acc;
-}
-
 __global__ void k_rho(const double* M0, double n_i, double* rho, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) rho[i] = n_i - M0[i];
@@ -71,11 +56,6 @@ __global__ void k_energy(const double* E, int dx, int NX, double cell, double* o
 cudaError_t spec_poisson_grad(const Spectral& sp, const double2* s_hat, double2* phi_hat,
                               double2* grad_hat, double sign) {
   slar::count_launch(), k_poisson_grad<<<(sp.NX + 255) / 256, 256, 0, sp.s>>>(sp, s_hat, phi_hat, grad_hat, sign);
-  return cudaGetLastError();
-}
-
-cudaError_t spec_div(const Spectral& sp, const double2* v_hat, int nvec, double2* out) {
-  slar::count_launch(), k_div<<<dim3((sp.NX + 255) / 256, nvec), 256, 0, sp.s>>>(sp, v_hat, nvec, out);
   return cudaGetLastError();
 }
 

@@ -70,19 +70,6 @@ __global__ void k_absmax_fin(const double* part, int nblk, double* out) {
   out[0] = t;
 }
 
-// w -= sum_{i<nv} coef[i] V_i  (coef on device); sign = -1 subtracts, +1 adds
-__global__ void k_axpy_multi(double* __restrict__ w, int n, const double* __restrict__ V, long long ld,
-                             int nv, const double* coef, const int* nv_dev, double sign,
-                             const double* done) {
-  if (done && done[0] != 0.0) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const int k = nv_dev ? *nv_dev : nv;
-  double s = 0.0;
-  for (int i = 0; i < k; ++i) s += coef[i] * V[i * ld + e];
-  w[e] += sign * s;
-}
-
 // out = x / sqrt(*nrm2) ; stores sqrt in *dst
 __global__ void k_normalize(const double* x, const double* nrm2, double* out, int n, double* dst,
                             const double* done) {
@@ -308,9 +295,7 @@ slar_status eval_residual(slar_ctx* c, const double* U, const double* rhs, doubl
   slar::count_launch(), k_flux<<<nb(NX), 256, 0, s>>>(dx, dv, NX, c->n_mom, U, fr2, w->mom_star, c->lomac_C, c->lomac_bs,
                                 flux, src);
   CK(cudaGetLastError());
-  CK(sp.forward(flux, z1, nflux));
-  CK(spec_div(sp, z1, dv + 2, z2));
-  CK(sp.inverse(z2, div, dv + 2));
+  CK(sp.div_lines(flux, dv + 2, div));
   slar::count_launch(), k_final<<<nb(NX), 256, 0, s>>>(dv, NX, div, src, U, rhs, misc + M_COEF, out,
                                                        mode_g);
   CK(cudaGetLastError());

@@ -43,6 +43,15 @@ __host__ __device__ __forceinline__ bool b_resident(int d, int r0, int r1, int r
   return d == 4 && (long long)(r0 * r1 * r12 + r2 * r3 * r34) * (long long)sizeof(T) <= RES_BYTES;
 }
 
+// with resident transfer tensors, a root matrix of at most ROOT_RES_BYTES is staged too, so
+// the root contraction reads shared memory instead of waiting on global loads
+constexpr int ROOT_RES_BYTES = 8 * 1024;
+
+template <typename T>
+__host__ __device__ __forceinline__ bool root_resident(int d, int r0, int r1, int r2, int r3, int r12, int r34) {
+  return b_resident<T>(d, r0, r1, r2, r3, r12, r34) && (long long)r12 * r34 * (long long)sizeof(T) <= ROOT_RES_BYTES;
+}
+
 // c_out[t][p] = sum_{a,b} ca[t][a] cb[t][b] sB[(a,b)][p] with the whole transfer tensor resident
 template <typename T, int TILE>
 __device__ void contract_node_res(const T* __restrict__ ca, int ra, const T* __restrict__ cb, int rb,
@@ -203,7 +212,10 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
   T* sc34 = sc12 + (d == 4 ? TILE * ht.r12 : 0);
   T* sB = sc34 + (d == 4 ? TILE * ht.r34 : 0);
   const bool resident = b_resident<T>(d, ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34);
+  const bool root_res = root_resident<T>(d, ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34);
   const int K12 = ht.r[0] * ht.r[1];
+  const int nB = resident ? K12 * ht.r12 + ht.r[2] * ht.r[3] * ht.r34 : 0;
+  T* sRoot = sB + nB;   // [r12][r34] when root_res
 
   // 0. work that does not need the feet, done by the other warps while they are traced:
   // the cross-approximation residual sum_l X[pivot, l] Y[e, l] of each entry, and the
@@ -231,14 +243,17 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
     }
     if (resident) {
       const int n12 = K12 * ht.r12, n34 = ht.r[2] * ht.r[3] * ht.r34;
-      for (int it = tid - TILE; it < n12 + n34; it += NTHREADS - TILE) {
+      const int nroot = root_res ? ht.r12 * ht.r34 : 0;
+      for (int it = tid - TILE; it < n12 + n34 + nroot; it += NTHREADS - TILE) {
         if (it < n12) {
           const int p = it / K12, k = it - p * K12;
           sB[k * ht.r12 + p] = ht.B12[it];
-        } else {
+        } else if (it < n12 + n34) {
           const int j = it - n12, K34 = ht.r[2] * ht.r[3];
           const int p = j / K34, k = j - p * K34;
           sB[n12 + k * ht.r34 + p] = ht.B34[j];
+        } else {
+          sRoot[it - n12 - n34] = ht.Broot[it - n12 - n34];
         }
       }
     }
@@ -344,10 +359,11 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
     constexpr int TPE = NTHREADS / TILE;  // threads per entry
     const int t = tid / TPE, sub = tid - t * TPE;
     T acc = T(0);
+    const T* Broot = (d == 4 && root_res) ? sRoot : ht.Broot;
     if (t < nT) {
       for (int p = sub; p < rl; p += TPE) {
         T s = T(0);
-        const T* Bp = ht.Broot + (long long)p * rr;
+        const T* Bp = Broot + (long long)p * rr;
         for (int q = 0; q < rr; ++q) s += Bp[q] * right[t * rr + q];
         acc += left[t * rl + p] * s;
       }
@@ -401,10 +417,12 @@ size_t smem_bytes(const GridDesc& g, const HTView<T>& ht) {
   for (int m = 0; m < g.d; ++m) rs += ht.r[m];
   if (g.d == 4) rs += ht.r12 + ht.r34;
   size_t nb = 0;
-  if (g.d == 4)
+  if (g.d == 4) {
     nb = b_resident<T>(g.d, ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34)
              ? (size_t)ht.r[0] * ht.r[1] * ht.r12 + (size_t)ht.r[2] * ht.r[3] * ht.r34
              : (size_t)KC * PSTRIDE;
+    if (root_resident<T>(g.d, ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34)) nb += (size_t)ht.r12 * ht.r34;
+  }
   b += sizeof(T) * ((size_t)TILE * rs + nb);
   return (b + 15) & ~size_t(15);
 }

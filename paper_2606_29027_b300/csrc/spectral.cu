@@ -79,7 +79,62 @@ __global__ void k_fft_lines(double2* data, const double* __restrict__ rin, doubl
   }
 }
 
+// Spectral derivative along one dimension of LPB lines per CTA: forward FFT of the line,
+// times i k (Nyquist wavenumber 0), inverse FFT, 1/n; the real part is written to out or added
+// to it.  Batch (blockIdx.y) over vectors with strides fvs (input) and ovs (output).  Because
+// the 2D DFT factorises, d/dx_m of a field needs transforms along x_m only; a divergence
+// sum_m d_m F[.][m] is one such pass per dimension.
+__global__ void k_deriv_lines(const double* __restrict__ f, double* out, int n, int logn, long long es, long long ls,
+                              int nlines, int lpb, const double2* tw, const double* __restrict__ kv, long long fvs,
+                              long long ovs, int accumulate) {
+  extern __shared__ double2 buf[];
+  const int l0 = blockIdx.x * lpb;
+  const int nl = min(lpb, nlines - l0);
+  const double* fv = f + blockIdx.y * fvs;
+  double* ov = out + blockIdx.y * ovs;
+  for (int it = threadIdx.x; it < nl * n; it += blockDim.x) {
+    const int l = it / n, i = it - l * n;
+    buf[l * n + i] = make_double2(fv[(l0 + l) * ls + i * es], 0.0);
+  }
+  __syncthreads();
+  smem_fft_lines(buf, n, logn, nl, n, 1, tw, 0);
+  for (int it = threadIdx.x; it < nl * n; it += blockDim.x) {
+    const int i = it % n;
+    const double k = kv[i];
+    const double2 z = buf[it];
+    buf[it] = make_double2(-k * z.y, k * z.x);
+  }
+  __syncthreads();
+  smem_fft_lines(buf, n, logn, nl, n, 1, tw, 1);
+  const double scale = 1.0 / n;
+  for (int it = threadIdx.x; it < nl * n; it += blockDim.x) {
+    const int l = it / n, i = it - l * n;
+    const long long off = (l0 + l) * ls + i * es;
+    const double v = buf[l * n + i].x * scale;
+    ov[off] = accumulate ? ov[off] + v : v;
+  }
+}
+
 }  // namespace
+
+cudaError_t Spectral::div_lines(const double* F, int nvec, double* div) const {
+  // F [nvec][dx][NX] -> div [nvec][NX]; x2 lines are contiguous, x1 lines have stride n[1]
+  const int lpb = 2;
+  for (int m = dx - 1; m >= 0; --m) {
+    const int len = n[m];
+    const long long es = (dx == 2 && m == 0) ? n[1] : 1;
+    const long long ls = (dx == 2 && m == 0) ? 1 : len;
+    const int nlines = NX / len;
+    const int thr = len * lpb / 2 < 32 ? 32 : (len * lpb / 2 > 128 ? 128 : len * lpb / 2);
+    dim3 grid((nlines + lpb - 1) / lpb, nvec);
+    slar::count_launch(), k_deriv_lines<<<grid, thr, sizeof(double2) * lpb * len, s>>>(
+        F + (long long)m * NX, div, len, logn[m], es, ls, nlines, lpb, twid[m], kv[m], (long long)dx * NX, NX,
+        m == dx - 1 ? 0 : 1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t Spectral::init(int dx_, const int* N, const double* L, cudaStream_t s_) {
   dx = dx_;
@@ -126,12 +181,14 @@ void Spectral::release() {
 // the scaled real part
 static cudaError_t fft_passes(const Spectral& sp, double2* z, const double* rin, double* rout, double scale,
                               int batch, int inverse) {
-  // 4 lines per CTA (64 threads each) keeps many CTAs in flight for batches of 64^2 fields
+  // 2 lines per CTA (one thread per butterfly): the FP64 butterflies of a pass spread over
+  // 32 x batch CTAs for 64^2 fields (one B300 SM retires about two FP64 FMAs per clock)
   auto pass = [&](int len, int lg, long long es, long long ls, int nlines, const double2* tw, const double* ri,
                   double* ro) {
-    const int lpb = 4;
+    const int lpb = 2;
+    const int thr = len * lpb / 2 < 32 ? 32 : (len * lpb / 2 > 128 ? 128 : len * lpb / 2);
     dim3 grid((nlines + lpb - 1) / lpb, batch);
-    slar::count_launch(), k_fft_lines<<<grid, 128, sizeof(double2) * lpb * len, sp.s>>>(
+    slar::count_launch(), k_fft_lines<<<grid, thr, sizeof(double2) * lpb * len, sp.s>>>(
         z, ri, ro, scale, len, lg, es, ls, sp.NX, nlines, lpb, tw, inverse);
     return cudaGetLastError();
   };

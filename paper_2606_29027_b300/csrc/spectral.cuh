@@ -22,6 +22,9 @@ struct Spectral {
   // scratch and holds no defined values afterwards)
   cudaError_t forward(const double* f, double2* z, int batch) const;
   cudaError_t inverse(double2* z, double* f, int batch) const;
+  // div[v] = sum_m d_m F[v][m] (spectral derivatives, one line pass per dimension);
+  // F [nvec][dx][NX] real, div [nvec][NX] real
+  cudaError_t div_lines(const double* F, int nvec, double* div) const;
 };
 
 // spectral-space operators (field.cu).  All spectra are [NX] complex per field.
@@ -29,8 +32,5 @@ struct Spectral {
 // -i k_m phi_hat (sign = -1, E = -grad phi).
 cudaError_t spec_poisson_grad(const Spectral& sp, const double2* s_hat, double2* phi_hat,
                               double2* grad_hat, double sign);
-// div_hat = sum_m i k_m v_hat[m]  for `nvec` vectors of dx components each:
-// v_hat layout [vec][m][NX], out [vec][NX]
-cudaError_t spec_div(const Spectral& sp, const double2* v_hat, int nvec, double2* out);
 
 }  // namespace slar
