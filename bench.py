@@ -487,8 +487,9 @@ def run_ours(args, w):
                                    "2(3 sum r_mu + r0 r1 r12 + r2 r3 r34 + r12 r34) + 60 per entry",
                          "eval_ms_per_step": eval_ms / 3.0,
                          "step_shares": "cold-cache ncu launch list of one BDF3 step "
-                                        "(profiles/launch_list_landau_2d2v_64.md): FFT passes "
-                                        "this evaluator 14.4 %, FFT passes k_fft_lines 14.4 %; both latency-bound"},
+                                        "(profiles/launch_list_landau_2d2v_64.md): this "
+                                        "evaluator 14.4 %, FFT passes k_fft_lines 14.4 %; "
+                                        "both latency-bound"},
             "phase_ms_per_step": phases,
             "gpu_launches": launches, "wall_s": wall, "clocks": clocks, "e2e": e2e}
     if not args.no_cpu_baseline and world == 1:
