@@ -148,6 +148,23 @@ def cpu_threads():
         return os.cpu_count() or 1
 
 
+def max_over_ranks(x, world, device):
+    """The slowest rank's value of x (all ranks get it); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, max_ms):
+    """Whole-job throughput of independent replicas: the steps of all ranks over the slowest
+    rank's timed region."""
+    return world * steps / (max_ms / 1000.0)
+
+
 def oracle_steps(w, n_warm, n_timed):
     """Time the FP64 oracle: n_warm untimed steps (DIRK3 start-up), then n_timed steps."""
     from oracle import sl, stepper
@@ -286,13 +303,8 @@ def run_ours(args, w):
     wall = time.perf_counter() - t0
     launches = slar.launch_count() - l0
     clocks = clk.stop()
-    tot_ms = float(sum(ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms / 1000.0)
+    tot_ms = max_over_ranks(float(sum(ms)), world, "cuda")
+    value = job_value(world, args.steps, tot_ms)
     entries = sum(s.entries for s in stats)
     eval_ms, eval_flop, eval_entries = eval_roofline(args.precision)
     converged = all(s.converged for s in stats)
