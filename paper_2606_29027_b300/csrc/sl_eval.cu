@@ -10,9 +10,11 @@
 //      path: the same formulas in FP32 (B300's FP64 rate per SM sub-partition made the FP64
 //      foot the longest phase of a low-rank FP32 evaluation).
 //   2. leaf gathers c^(mu) = w . U^(mu)[j-1..j+1, :]  (coalesced row loads, staged in smem)
-//   3. transfer-tensor contractions c12 = B12 x1 c0 x2 c1 (a [TILE x r0 r1] x [r0 r1 x r12]
-//      product whose left operand -- the outer products c0 (x) c1 -- is formed on the fly),
-//      likewise c34; B is streamed through shared memory in K-chunks.
+//   3. transfer-tensor contractions c12 = B12 x1 c0 x2 c1, likewise c34: small transfer
+//      tensors resident in shared memory (outer products c0 (x) c1 formed on the fly, threads
+//      over entries and output ranks); large ones in FP32 as one [TILE x r1] x [r1 x r0] GEMM
+//      per output rank followed by the dot with c0 (contract_node_gemm), in FP64 streamed
+//      through shared memory in K-chunks.
 //   4. root: c12 . Broot . c34 (warp-shuffle reduction)
 //   5. separable LoMaC correction (if present) and, for cross-approximation fibres, the
 //      residual epilogue out = value - sum_l X[pivot, l] Y[e, l].
@@ -173,6 +175,110 @@ __device__ void contract_node(const T* __restrict__ ca, int ra, const T* __restr
     if (t < nT) {
       if (lane < rp) cout[t * rp + lane] = acc[i][0];
       if (lane + 32 < rp) cout[t * rp + lane + 32] = acc[i][1];
+    }
+  }
+}
+
+// FP32 contraction for transfer tensors too large to stay resident (ranks above ~22): for
+// each output rank p, T[t][a] = sum_b cb[t][b] B[p][a][b] is a [TILE x rb] x [rb x ra] GEMM,
+// register-tiled as 4 a x EPT entries per thread (16 a-groups x 16 entry groups), with cb
+// staged transposed so that every k-step is two vector shared loads for 4 EPT FMAs; then
+// c_out[t][p] = sum_a ca[t][a] T[t][a] (the thread's ca values stay in registers across p)
+// reduced over the 16 a-groups of a half-warp.  B[p] (ra x rb, contiguous) is loaded into
+// registers while p - 1 is computed and stored transposed into shared memory.
+constexpr int GEMM_LDB = 68;   // row stride (floats) of the staged B[p]^T: a < 64, 16-byte rows
+
+__host__ __device__ __forceinline__ int gemm_ldt(int tile) { return tile + 4; }
+
+__host__ __device__ __forceinline__ size_t gemm_smem_floats(int tile, int rbmax) {
+  return (size_t)rbmax * gemm_ldt(tile) + (size_t)rbmax * GEMM_LDB;
+}
+
+template <int TILE>
+__device__ void contract_node_gemm(const float* __restrict__ ca, int ra, const float* __restrict__ cb, int rb,
+                                   const float* __restrict__ B, int rp, float* __restrict__ cout, int nT,
+                                   float* sbuf) {
+  constexpr int EPT = TILE / 16;
+  constexpr int LDT = TILE + 4;
+  const int tid = threadIdx.x;
+  const int eg = tid >> 4, ag = tid & 15;
+  float* sCt = sbuf;                 // [rb][LDT]: cb transposed
+  float* sBt = sbuf + rb * LDT;      // [rb][GEMM_LDB]: B[p] transposed, zero beyond ra
+  __syncthreads();                   // the previous user of sbuf is done
+  for (int it = tid; it < TILE * rb; it += NTHREADS) {
+    const int t = it / rb, b = it - t * rb;
+    sCt[b * LDT + t] = cb[it];
+  }
+  for (int it = tid; it < rb * GEMM_LDB; it += NTHREADS) sBt[it] = 0.f;
+  float c1[EPT][4];
+#pragma unroll
+  for (int i = 0; i < EPT; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = ag * 4 + j;
+      c1[i][j] = a < ra ? ca[(eg * EPT + i) * ra + a] : 0.f;
+    }
+  const int nab = ra * rb;           // <= 4096: at most 16 elements per thread
+  float pre[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int it = tid + j * NTHREADS;
+    pre[j] = it < nab ? __ldg(B + it) : 0.f;
+  }
+  for (int p = 0; p < rp; ++p) {
+    __syncthreads();                 // staging of sCt / the previous p's reads of sBt are done
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int it = tid + j * NTHREADS;
+      if (it < nab) {
+        const int a = it / rb, b = it - a * rb;
+        sBt[b * GEMM_LDB + a] = pre[j];
+      }
+    }
+    __syncthreads();
+    if (p + 1 < rp) {
+      const float* Bn = B + (long long)(p + 1) * nab;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int it = tid + j * NTHREADS;
+        pre[j] = it < nab ? __ldg(Bn + it) : 0.f;
+      }
+    }
+    float acc[EPT][4];
+#pragma unroll
+    for (int i = 0; i < EPT; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    const float* cp = sCt + eg * EPT;
+    const float* bp = sBt + ag * 4;
+#pragma unroll 4
+    for (int b = 0; b < rb; ++b) {
+      const float4 bv = *reinterpret_cast<const float4*>(bp + b * GEMM_LDB);
+      float cv[EPT];
+      if constexpr (EPT == 4) {
+        const float4 t4 = *reinterpret_cast<const float4*>(cp + b * LDT);
+        cv[0] = t4.x; cv[1] = t4.y; cv[2] = t4.z; cv[3] = t4.w;
+      } else if constexpr (EPT == 2) {
+        const float2 t2 = *reinterpret_cast<const float2*>(cp + b * LDT);
+        cv[0] = t2.x; cv[1] = t2.y;
+      } else {
+        cv[0] = cp[b * LDT];
+      }
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        acc[i][0] = fmaf(cv[i], bv.x, acc[i][0]);
+        acc[i][1] = fmaf(cv[i], bv.y, acc[i][1]);
+        acc[i][2] = fmaf(cv[i], bv.z, acc[i][2]);
+        acc[i][3] = fmaf(cv[i], bv.w, acc[i][3]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      float s = (c1[i][0] * acc[i][0] + c1[i][1] * acc[i][1]) + (c1[i][2] * acc[i][2] + c1[i][3] * acc[i][3]);
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const int t = eg * EPT + i;
+      if (ag == 0 && t < nT) cout[t * rp + p] = s;
     }
   }
 }
@@ -344,6 +450,9 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
     if (resident) {
       contract_res<T, TILE>(sc_mu[0], ht.r[0], sc_mu[1], ht.r[1], sB, ht.r12, sc12, nT);
       contract_res<T, TILE>(sc_mu[2], ht.r[2], sc_mu[3], ht.r[3], sB + K12 * ht.r12, ht.r34, sc34, nT);
+    } else if constexpr (sizeof(T) == 4) {
+      contract_node_gemm<TILE>(sc_mu[0], ht.r[0], sc_mu[1], ht.r[1], ht.B12, ht.r12, sc12, nT, sB);
+      contract_node_gemm<TILE>(sc_mu[2], ht.r[2], sc_mu[3], ht.r[3], ht.B34, ht.r34, sc34, nT, sB);
     } else {
       contract_node<T, TILE>(sc_mu[0], ht.r[0], sc_mu[1], ht.r[1], ht.B12, ht.r12, sc12, sB, nT);
       contract_node<T, TILE>(sc_mu[2], ht.r[2], sc_mu[3], ht.r[3], ht.B34, ht.r34, sc34, sB, nT);
@@ -418,9 +527,10 @@ size_t smem_bytes(const GridDesc& g, const HTView<T>& ht) {
   if (g.d == 4) rs += ht.r12 + ht.r34;
   size_t nb = 0;
   if (g.d == 4) {
+    const int rbmax = ht.r[1] > ht.r[3] ? ht.r[1] : ht.r[3];
     nb = b_resident<T>(g.d, ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34)
              ? (size_t)ht.r[0] * ht.r[1] * ht.r12 + (size_t)ht.r[2] * ht.r[3] * ht.r34
-             : (size_t)KC * PSTRIDE;
+             : (sizeof(T) == 4 ? gemm_smem_floats(TILE, rbmax) : (size_t)KC * PSTRIDE);
     if (root_resident<T>(g.d, ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34)) nb += (size_t)ht.r12 * ht.r34;
   }
   b += sizeof(T) * ((size_t)TILE * rs + nb);
