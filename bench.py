@@ -36,7 +36,7 @@ FP64_PEAK_TFLOPS = 1.25                              # nominal B300 FP64 (recipe
 # DRAM bytes (read + write) per launch of the FP32 entry evaluator (k_sl_eval_dev<float, 32>)
 # on this workload, from the ncu launch list in profiles/launch_list_landau_2d2v_64.md (cold
 # cache, one BDF3 step)
-EVAL_TRAFFIC_BYTES = 284.4e3
+EVAL_TRAFFIC_BYTES = 289.2e3
 
 
 def parse():
@@ -500,7 +500,7 @@ def run_ours(args, w):
                          "eval_ms_per_step": eval_ms / 3.0,
                          "step_shares": "cold-cache ncu launch list of one BDF3 step "
                                         "(profiles/launch_list_landau_2d2v_64.md): this "
-                                        "evaluator 14.4 %, FFT passes k_fft_lines 14.4 %; "
+                                        "evaluator 14.5 %, FFT passes k_fft_lines 14.6 %; "
                                         "both latency-bound"},
             "phase_ms_per_step": phases,
             "gpu_launches": launches, "wall_s": wall, "clocks": clocks, "e2e": e2e}

@@ -81,15 +81,8 @@ __global__ void k_normalize(const double* x, const double* nrm2, double* out, in
 }
 
 // ---------------- the residual ----------------
-// stage 1: rho = n_i - U0 and the momentum components as real fields
-__global__ void k_prep(const double* U, const double* n_i, int NX, int dx, double* fr) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= NX) return;
-  fr[x] = n_i[0] - U[x];
-  for (int m = 0; m < dx; ++m) fr[(long long)(1 + m) * NX + x] = U[(long long)(1 + m) * NX + x];
-}
-
-// stage 2 (spectral): phi, E = -grad phi, d_t phi with -Lap(d_t phi) = div(U1), grad(d_t phi)
+// stage 2 (spectral; stage 1 is the forward transform of U0 and U1): phi, E = -grad phi,
+// d_t phi with -Lap(d_t phi) = div(U1), grad(d_t phi)
 __global__ void k_spec_fields(Spectral sp, const double2* zin, double2* zout) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= sp.NX) return;
@@ -99,7 +92,7 @@ __global__ void k_spec_fields(Spectral sp, const double2* zin, double2* zout) {
   else { k[0] = sp.kv[0][i / sp.n[1]]; k[1] = sp.kv[1][i % sp.n[1]]; }
   double k2 = 0.0;
   for (int m = 0; m < dx; ++m) k2 += k[m] * k[m];
-  const double2 rh = zin[i];
+  const double2 rh = make_double2(-zin[i].x, -zin[i].y);   // rho^ = -U0^ for |k| > 0
   double2 ph = make_double2(0.0, 0.0);
   if (k2 > 0.0) ph = make_double2(rh.x / k2, rh.y / k2);
   double2 dv = make_double2(0.0, 0.0);
@@ -286,9 +279,9 @@ slar_status eval_residual(slar_ctx* c, const double* U, const double* rhs, doubl
   double2* z1 = fz;
   double2* z2 = fz + (long long)nflux * NX;
   double* misc = w->sc + SC_MISC;
-  slar::count_launch(), k_prep<<<nb(NX), 256, 0, s>>>(U, misc + M_NI, NX, dx, fr);
-  CK(cudaGetLastError());
-  CK(sp.forward(fr, z1, nf1));
+  // spectra of U0 and U1: rho = n_i - U0 differs from -U0 only in the k = 0 mode, which the
+  // Poisson solve sets to zero, so k_spec_fields takes rho^ = -U0^
+  CK(sp.forward(U, z1, nf1));
   slar::count_launch(), k_spec_fields<<<nb(NX), 256, 0, s>>>(sp, z1, z2);
   CK(cudaGetLastError());
   CK(sp.inverse(z2, fr2, nf2));
