@@ -19,6 +19,10 @@ Modules, in the order the method is built from them:
 * ``lomac``     -- adaptive weight, weighted Gram-Schmidt, projection coefficients and the
                    reconstruction R(U) (Sec. 3.2.1-3.2.2; Supp. B)
 * ``macro``     -- macroscopic residual G(U), JFNK, BE / BDF3 / DIRK3 (Sec. 3.2.3)
+* ``precond``   -- block-circulant right preconditioner of the Newton-Krylov solve and the
+                   preconditioned JFNK (an addition to the paper's plain JFNK)
+* ``net``       -- the warm-start network: periodic convolutions, adjoints, losses, Adam
+                   (an addition; the plain JFNK stays its fallback and judge)
 * ``stepper``   -- SLAR, SLAR_VP (RKEI) and the LoMaC-coupled step (Fig. flowchart)
 * ``dispersion``-- linear Landau / two-stream dispersion roots used as physics pins
 
