@@ -51,6 +51,8 @@ def landau_rate(k: float = 0.5) -> complex:
     return root(k, 1.4 - 0.15j)
 
 
-def two_stream_rate(k: float, v0: float) -> complex:
-    """Unstable root of two half-density beams at +-v0."""
-    return root(k, 0.0 + 0.3j, species=((0.5, v0), (0.5, -v0)))
+def two_stream_rate(k: float, v0: float, n_beam: float = 0.5) -> complex:
+    """Unstable root of two beams of density n_beam each at +-v0 (0.5: total density 1, as in
+    the 2D-2V workload; 1.0: the 1D-1V example of Sec. 4.1, whose two unit Gaussians have
+    total density 2)."""
+    return root(k, 0.0 + 0.3j, species=((n_beam, v0), (n_beam, -v0)))
