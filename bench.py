@@ -465,6 +465,17 @@ def run_ours(args, w):
         peak32 = max(slar.fma_peak(False, stream=stream) for _ in range(3))
         peak64 = max(slar.fma_peak(True, stream=stream) for _ in range(3))
     peak = peak32 if args.precision == "fp32" else peak64
+    # where the arithmetic dominates: the same evaluators at rank 64 on one 65536-entry launch
+    bf16, bf16_src = bf16_peak_tflops()
+    eval64 = {"workload": "random HT, all six ranks 64, 2D2V 128^4, 65536 random tuples, RK3 feet; "
+                          "median of 3 launches after one warm-up",
+              "flop_per_entry": 2 * (3 * 4 * 64 + 2 * 64 ** 3 + 64 * 64) + 60}
+    for prec, pk, src in (("fp32", peak32, "measured FP32 FMA peak (this run)"),
+                          ("bf16x3", bf16 / 3.0, bf16_src + " / 3 (three BF16 products per K-step)")):
+        ms64, tf64 = eval_launch(prec, 64, 128, 65536, reps=3)
+        eval64[prec] = {"kernel": "k_sl_eval<float> (GEMM contraction)" if prec == "fp32"
+                        else "k_sl_eval_tc (tcgen05, BF16x3)",
+                        "ms": ms64, "tflops": tf64, "peak_tflops": pk, "frac": tf64 / pk, "peak_source": src}
     achieved = eval_flop / max(eval_ms, 1e-9) / 1e9          # TFLOP/s
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": tot_ms / args.steps,
@@ -502,6 +513,7 @@ def run_ours(args, w):
                                         "(profiles/launch_list_landau_2d2v_64.md): this "
                                         "evaluator 14.5 %, FFT passes k_fft_lines 14.6 %; "
                                         "both latency-bound"},
+            "eval_rank64": eval64,
             "phase_ms_per_step": phases,
             "gpu_launches": launches, "wall_s": wall, "clocks": clocks, "e2e": e2e}
     if not args.no_cpu_baseline and world == 1:
@@ -536,32 +548,53 @@ def profile_step(args, w):
           flush=True)
 
 
-def profile_eval(args):
-    """Time the entry evaluator alone (CUDA events, one launch after one warm-up)."""
+def eval_launch(precision, r, n, entries, reps=1):
+    """Time one entry-evaluator launch (CUDA events on the current stream, after one warm-up;
+    median of reps) on a random 2D2V HT with all six ranks r, n points per dimension and
+    `entries` random tuples (RK3 feet).  Returns (ms, algorithmic TFLOP/s)."""
     import torch
     from paper_2606_29027_b300 import inputs, slar
-    n, r = args.eval_n, args.eval_rank
     N = (n, n, n, n)
     L = 4 * math.pi
     cfg = slar.make_config(dx=2, dv=2, N=N, lo=(0, 0, -6, -6), hi=(L, L, 6, 6), eps=1e-6, rank_cap=64,
-                           precision=args.profile_eval)
+                           precision=precision)
     ctx = slar.Context(cfg)
     h = inputs.random_ht(N, (r,) * 6, seed=5)
     ctx.import_ht(U=h.U, Broot=h.Broot, B12=np.transpose(h.B12, (2, 0, 1)), B34=np.transpose(h.B34, (2, 0, 1)))
     E = torch.as_tensor(inputs.random_field(N[:2], 2, 0.6, seed=4), device="cuda")
-    idx = torch.as_tensor(inputs.random_tuples(N, args.eval_entries, seed=7), device="cuda")
-    out = torch.zeros(args.eval_entries, dtype=torch.float64, device="cuda")
+    idx = torch.as_tensor(inputs.random_tuples(N, entries, seed=7), device="cuda")
+    out = torch.zeros(entries, dtype=torch.float64, device="cuda")
     ctx.sl_eval(1.1, E, idx, out)
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    ctx.sl_eval(1.1, E, idx, out)
-    b.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    flop = (2 * (3 * 4 * r + 2 * r ** 3 + r * r) + 60) * args.eval_entries
-    print(json.dumps({"profile_eval": args.profile_eval, "rank": r, "n": n, "entries": args.eval_entries,
-                      "ms": ms, "tflops": flop / ms / 1e9}), flush=True)
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.sl_eval(1.1, E, idx, out)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    ctx.close()
+    ms = statistics.median(times)
+    flop = (2 * (3 * 4 * r + 2 * r ** 3 + r * r) + 60) * entries
+    return ms, flop / ms / 1e9
+
+
+def bf16_peak_tflops():
+    """Dense BF16 burst peak from MEASURED_PEAKS.json when present, else the fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "MEASURED_PEAKS.json bf16_tflops (burst)"
+    except (OSError, KeyError, ValueError):
+        return 1800.0, "fallback 1.8 PFLOP/s bf16 burst (no MEASURED_PEAKS.json)"
+
+
+def profile_eval(args):
+    """Time the entry evaluator alone (CUDA events, one launch after one warm-up)."""
+    ms, tflops = eval_launch(args.profile_eval, args.eval_rank, args.eval_n, args.eval_entries)
+    print(json.dumps({"profile_eval": args.profile_eval, "rank": args.eval_rank, "n": args.eval_n,
+                      "entries": args.eval_entries, "ms": ms, "tflops": tflops}), flush=True)
 
 
 def main():
