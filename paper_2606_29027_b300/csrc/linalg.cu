@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_reduce(const EigJob* jobs) 
   extern __shared__ double sA[];
   __shared__ double sp[SLAR_MAX_N];
   __shared__ double red[TRI_THREADS / 32];
-  __shared__ double s_tau, s_beta;
+  __shared__ double s_tau;
   const EigJob job = jobs[blockIdx.x];
   if (!tri_active(job)) return;
   const int n = job.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -686,7 +686,6 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_reduce(const EigJob* jobs) 
         x[0] = v0;
       }
       s_tau = t;
-      s_beta = beta;
       tau[k] = t;
       dg[k] = sA[k * n + k];
       ed[k] = beta;

@@ -344,7 +344,6 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   if (e0 >= a.n) return;
   const int nT = (int)min((long long)TC_TILE, a.n - e0);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int d = g.d;
   const TcLayout L = tc_layout(ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34);
   float* sfoot = reinterpret_cast<float*>(smem_raw);                 // 128 x 4
   float* sw = sfoot + TC_TILE * 4;                                    // 128 x 12
