@@ -111,6 +111,24 @@ def landau_1d1v(N=(64, 128), alpha=0.01, k=0.5, vmax=6.0, eps=1e-6, cap=16, dt=0
                     steps=steps, terms=terms, alpha=alpha, k=k)
 
 
+def bump_on_tail_1d1v(N=(64, 128), alpha=0.04, k=0.3, u=4.5, vt=0.5, vmax=13.0, eps=1e-5, cap=16,
+                      dt=0.1, steps=200) -> Workload:
+    # f0 = (1 + alpha cos kx)(n_p exp(-v^2/2) + n_b exp(-(v-u)^2/(2 vt))),
+    # n_p = 9/(10 sqrt(2 pi)), n_b = 2/(10 sqrt(2 pi)); the bulk and the beam are separate
+    # separable terms (Maxwellian factors of temperature 1 and vt)
+    L = 2.0 * math.pi / k
+    n_p = 9.0 / (10.0 * math.sqrt(2.0 * math.pi))
+    n_b = 2.0 / (10.0 * math.sqrt(2.0 * math.pi))
+    bulk = ("maxwell", {"c": n_p * math.sqrt(2.0 * math.pi)})
+    beam = ("maxwell", {"u": u, "T": vt, "c": n_b * math.sqrt(2.0 * math.pi * vt)})
+    one = ("const", {"c": 1.0})
+    cs = ("cos", {"k": k, "c": alpha})
+    terms = [[one, bulk], [one, beam], [cs, bulk], [cs, beam]]
+    return Workload(name=f"bump_on_tail_1d1v_{N[0]}x{N[1]}", dx=1, dv=1, N=tuple(N),
+                    lo=(0.0, -vmax), hi=(L, vmax), eps=eps, rank_cap=cap, dt=dt,
+                    steps=steps, terms=terms, alpha=alpha, k=k)
+
+
 def two_stream_1d1v(N=(64, 128), alpha=1e-3, k=0.2, v0=2.4, vmax=8.0, eps=1e-5, cap=16,
                     dt=0.1, steps=200) -> Workload:
     L = 2.0 * math.pi / k
@@ -185,6 +203,7 @@ def workload_by_name(name: str) -> Workload:
         "two_stream_2d2v": lambda: two_stream_2d2v(),
         "strong_landau_2d2v": lambda: landau_2d2v(n=128, alpha=0.5, cap=64, dt=0.2),
         "two_stream_1d1v": lambda: two_stream_1d1v(),
+        "bump_on_tail_1d1v": lambda: bump_on_tail_1d1v(),
     }
     return table[name]()
 

@@ -98,6 +98,37 @@ def test_two_stream_growth_rate_1d1v():
     assert abs(rate - dispersion.two_stream_rate(w.k, 2.4).imag) > 0.1 * want
 
 
+@pytest.mark.slow
+def test_bump_on_tail_growth_rate_1d1v():
+    """1D-1V bump-on-tail instability with the data of the paper's example (Sec. 4.1: bulk
+    n_p exp(-v^2/2) and beam n_b exp(-(v - 4.5)^2 / (2 * 0.5)), k = 0.3, x in [0, 20 pi / 3),
+    v in [-13, 13]; here 64 x 128, dt = 0.1, eps = 1e-6) at a perturbation of 1e-4 instead of
+    the example's 0.04, which saturates before the beam-driven wave dominates the beating with
+    the bulk Langmuir waves: the k = 0.3 Fourier mode of E grows at the rate of the unstable
+    dispersion root of a bulk and a drifting beam of temperature 0.5 (0.192), within 3 % over
+    t in [15, 40]."""
+    w = inputs.bump_on_tail_1d1v(alpha=1e-4, eps=1e-6)
+    g = sl.PhaseGrid(w.dx, w.dv, w.N, w.lo, w.hi)
+    prm = stepper.Params(eps=w.eps, cap=w.rank_cap)
+    st = stepper.init_state(inputs.initial_factors(w), g, prm)
+
+    def mode1():
+        E = np.asarray(field.poisson_field(st.n_i - st.U[0], g)[1]).reshape(-1)
+        return abs(np.fft.fft(E)[1])
+
+    ts, amp = [0.0], [mode1()]
+    for _ in range(400):
+        s = stepper.sl_step(st, w.dt, g, prm)
+        assert s.converged
+        ts.append(st.t)
+        amp.append(mode1())
+    ts, amp = np.array(ts), np.array(amp)
+    m = (ts >= 15.0) & (ts <= 40.0)
+    rate = np.polyfit(ts[m], np.log(amp[m]), 1)[0]
+    want = dispersion.bump_on_tail_rate(w.k).imag
+    assert abs(rate - want) <= 0.03 * want, (rate, want)
+
+
 def test_wrong_force_sign_is_caught(monkeypatch):
     """A planted mistake in the oracle (foot velocity v - E tau instead of v + E tau) turns
     damping into growth; the Landau pin catches it."""
