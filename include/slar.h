@@ -332,6 +332,14 @@ slar_status slar_launch_count(long long* out);
 /* The stream the context works on (the caller's, or its own with SLAR_OWN_STREAM). */
 slar_status slar_stream(const slar_ctx* ctx, void** stream);
 
+/* Test hook of the bounded device-side waits (no counterpart in the paper): a kernel waits,
+ * with the same bounded poll loop as the tensor-core evaluator's mbarrier waits, for a phase
+ * that never completes, and gives up after `polls` polls (1 <= polls <= 2^22) instead of
+ * hanging.  status_dev: device int that receives 1 (gave up) or 0.  Work on `stream`
+ * (cudaStream_t), synchronised.  Returns SLAR_ETIMEOUT when the wait gave up -- the CUDA
+ * context stays usable -- SLAR_EINVAL for a bad argument, SLAR_ECUDA on a CUDA error. */
+slar_status slar_wait_probe(long long polls, int* status_dev, void* stream);
+
 /* Number of moments returned by `moments` and the spatial size NX. */
 slar_status slar_sizes(const slar_ctx* ctx, int* n_mom, int* nx);
 

@@ -151,10 +151,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // bounded wait of one thread
-__device__ __forceinline__ bool wait_one(uint32_t bar, uint32_t parity) {
-  for (long long n = 0; n < TC_WAIT_LIMIT; ++n)
+__device__ __forceinline__ bool wait_one_n(uint32_t bar, uint32_t parity, long long limit) {
+  for (long long n = 0; n < limit; ++n)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+__device__ __forceinline__ bool wait_one(uint32_t bar, uint32_t parity) {
+  return wait_one_n(bar, parity, TC_WAIT_LIMIT);
 }
 
 // bounded wait of a whole warp: true on every lane once every lane has seen the phase
@@ -612,6 +616,20 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   }
 }
 
+// The bounded-wait path of the evaluator exercised on its own: one thread waits for the first
+// phase of an mbarrier that nothing arrives on, gives up after `polls` polls and records it
+// in *status (1: gave up, 0: the phase completed).
+__global__ void k_wait_probe(long long polls, int* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *status = wait_one_n(b, 0, polls) ? 0 : 1;
+}
+
 }  // namespace
 
 size_t sl_eval_tc_smem(const int* r6) {
@@ -658,3 +676,14 @@ cudaError_t launch_sl_eval_tc_dev(const GridDesc& g, const EvalParams<float>* P,
 }
 
 }  // namespace slar
+
+extern "C" slar_status slar_wait_probe(long long polls, int* status_dev, void* stream) {
+  if (polls < 1 || polls > slar::TC_WAIT_LIMIT || !status_dev) return SLAR_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  slar::count_launch(), slar::k_wait_probe<<<1, 32, 0, s>>>(polls, status_dev);
+  if (cudaGetLastError() != cudaSuccess) return SLAR_ECUDA;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, status_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SLAR_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SLAR_ECUDA;
+  return h ? SLAR_ETIMEOUT : SLAR_OK;
+}

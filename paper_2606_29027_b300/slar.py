@@ -29,7 +29,7 @@ EXPORTED = ["slar_create", "slar_destroy", "slar_last_error", "init_ht", "sl_ste
             "slar_net_param_count", "slar_sample_floats", "slar_net_create", "slar_net_destroy",
             "slar_net_set_params", "slar_net_get_params", "slar_net_forward", "slar_net_loss_grad",
             "slar_net_train_step", "slar_attach_net", "slar_set_record", "slar_fma_peak",
-            "slar_ensemble_step", "slar_stream"]
+            "slar_ensemble_step", "slar_stream", "slar_wait_probe"]
 
 
 class Config(C.Structure):
@@ -113,6 +113,7 @@ def load():
         "slar_fma_peak": ([I, I, C.POINTER(D), P], I),
         "slar_ensemble_step": ([P, I, P, I, P], I),
         "slar_stream": ([P, C.POINTER(P)], I),
+        "slar_wait_probe": ([LL, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -146,6 +147,14 @@ def poisson_field_static(N, L, rho, E, phi=None, stream=None, energy=True):
     if status != SLAR_OK:
         raise SlarError(status, "slar_poisson_field_static failed")
     return W.value if energy else None
+
+
+def wait_probe(polls: int, status, stream=None) -> int:
+    """Run the bounded-wait probe (see include/slar.h); returns the status code
+    (SLAR_ETIMEOUT when the wait gave up).  status: a CUDA int32 tensor of one element."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return load().slar_wait_probe(int(polls), C.c_void_p(_ptr(status)), C.c_void_p(st.cuda_stream))
 
 
 def fma_peak(fp64: bool, iters: int = 0, stream=None) -> float:
