@@ -29,6 +29,33 @@ def test_dispersion_root_matches_golden():
     assert w.imag == pytest.approx(gr["omega_im"], abs=2e-4)
 
 
+def test_two_stream_root_tends_to_the_cold_beam_root():
+    """Fast, narrow beams (k v_t << |w - k v0|): the warm two-stream root approaches the
+    closed-form root of two cold half-density beams, w^2 = ((2a^2 + 1) - sqrt(8a^2 + 1)) / 2
+    with a = k v0 (purely growing for a < 1), and the thermal correction shrinks with k v_t at
+    fixed a."""
+    def cold(a):
+        return math.sqrt(-((2 * a * a + 1) - math.sqrt(8 * a * a + 1)) / 2)
+
+    errs = []
+    for v0, k in ((20.0, 0.03), (40.0, 0.015)):
+        w = dispersion.two_stream_rate(k, v0)
+        assert abs(w.real) < 1e-10
+        errs.append(abs(w.imag - cold(k * v0)) / cold(k * v0))
+    assert errs[0] < 1e-2
+    assert errs[1] < errs[0] / 2
+
+
+@pytest.mark.parametrize("T", [0.25, 2.0])
+@pytest.mark.parametrize("k", [0.4, 0.5])
+def test_dispersion_temperature_scaling(T, k):
+    """eps(k, w; n, T) = eps(k sqrt(T), w; n, 1): zeta = w / (k sqrt(2T)) and n / (T k^2)
+    depend on k and T only through k sqrt(T), so the roots coincide."""
+    r1 = dispersion.root(k, 1.4 - 0.15j, species=((1.0, 0.0, T),))
+    r2 = dispersion.root(k * math.sqrt(T), 1.4 - 0.15j, species=((1.0, 0.0, 1.0),))
+    assert abs(r1 - r2) < 1e-12
+
+
 def _run_landau(steps, lomac=True, foot_flip=False, monkeypatch=None):
     w = inputs.landau_1d1v()
     g = sl.PhaseGrid(w.dx, w.dv, w.N, w.lo, w.hi)
