@@ -607,6 +607,9 @@ def main():
     if args.profile_step:
         profile_step(args, w)
         return
+    if args.precision == "bf16x3":
+        raise SystemExit("--precision bf16x3 is for --profile-step; the benchmark reports BF16x3 "
+                         "in its 128^4 and eval_rank64 sections")
     if args.impl == "reference":
         run_reference(args, w)
     else:
