@@ -95,11 +95,7 @@ def K_operator(U: np.ndarray, cl: Closure) -> np.ndarray:
             Pi[(a, b)] = Pi[(b, a)] = mom_new[idx]
             idx += 1
     Q3 = [mom_new[idx + a] for a in range(dv)]
-    rho = cl.n_i - U[0]
-    phi, E, _ = field.poisson_field(rho, g)
-    J = -U[1:1 + dv]
-    dtphi = field.solve_poisson(-field.div(J, g), g)
-    grad_dtphi = [field.deriv(dtphi, g, a) for a in range(dx)]
+    Fep, E = field_energy_flux(U, g, cl.n_i)
     out = np.zeros_like(U)
     # mass: d_t n + div(M1) = 0
     out[0] = -field.div(U[1:1 + dv], g)
@@ -108,9 +104,25 @@ def K_operator(U: np.ndarray, cl: Closure) -> np.ndarray:
         flux_b = np.stack([Pi[(a, b)] for a in range(dx)])
         out[1 + b] = -field.div(flux_b, g) + (-U[0]) * E[b]
     # energy: d_t e + div( <|v|^2 v f>/2 - phi grad(d_t phi) + J phi ) = 0
-    Fe = np.stack([0.5 * Q3[a] - phi * grad_dtphi[a] + J[a] * phi for a in range(dx)])
+    Fe = np.stack([0.5 * Q3[a] + Fep[a] for a in range(dx)])
     out[1 + dv] = -field.div(Fe, g)
     return out
+
+
+def field_energy_flux(U: np.ndarray, g: PhaseGrid, n_i: float):
+    """The electric-field energy flux F_ep = -phi grad(d_t phi) + J phi of
+    Eq. electric_field_flux (epsilon_0 = 1) and the field E, from the conserved variables:
+    rho = n_i - U0 (Eq. charge_density), J = -U1 (Eq. current_density), phi and E by the
+    spectral Poisson solve, and d_t phi from -Lap(d_t phi) = -div J (Supp. A).  Returns
+    (F_ep (dx, Nx), E (dx, Nx))."""
+    dx, dv = g.dx, g.dv
+    rho = n_i - U[0]
+    phi, E, _ = field.poisson_field(rho, g)
+    J = -U[1:1 + dv]
+    dtphi = field.solve_poisson(-field.div(J, g), g)
+    grad_dtphi = [field.deriv(dtphi, g, a) for a in range(dx)]
+    Fep = np.stack([-phi * grad_dtphi[a] + J[a] * phi for a in range(dx)])
+    return Fep, E
 
 
 def gmres(Aop: Callable[[np.ndarray], np.ndarray], b: np.ndarray, rtol: float, restart: int,
