@@ -1,12 +1,16 @@
 """Benchmark: 2D-2V SLAR steps/s and sampled entries/s on the 2D-2V weak Landau workload
 (64 points per dimension, tree ((x1,x2),(v1,v2)), rank cap 32, eps 1e-5, dt 0.2), with the
-implicit LoMaC correction.  Headline: the FP32 entry path with the learned JFNK warm start
-(network trained in the same run, untimed, on samples of seeded weak-Landau runs that the
-solver generates); beside it the plain FP64 path and the plain FP32 path on the same steps,
-with the electric-energy history of each compared with the FP64 path's.
+implicit LoMaC correction.  Headline: the FP64 path (FP64 entries, truncation, LoMaC and
+Newton) with the block-circulant preconditioner of the Newton-Krylov solve.  Beside it, on
+the same steps: the plain FP64 path (the paper's unpreconditioned JFNK), FP32 entries with
+the preconditioner, and FP32 entries with the learned JFNK warm start (network trained in the
+same run, untimed, on samples of seeded weak-Landau runs that the solver generates), each
+form's electric-energy history compared with an FP64 run truncated 100 times more tightly;
+the 1D-1V weak Landau workload in microseconds per step.  The line ends with a compact
+summary of the forms.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision fp32|fp64] [--solver learned|precond|plain] [--workload NAME]
+                    [--precision fp64|fp32] [--solver precond|plain|learned] [--workload NAME]
 
 One JSON line on rank 0.  Multi-GPU runs are independent replicas (the method has no
 data-parallel exchange): value = steps of all ranks / max-over-ranks time.
@@ -33,10 +37,11 @@ METRIC = "2D2V SLAR steps/s"
 UNIT = "steps/s"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2032 MHz
 FP64_PEAK_TFLOPS = 1.25                              # nominal B300 FP64 (recipe table)
-# DRAM bytes (read + write) per launch of the FP32 entry evaluator (k_sl_eval_dev<float, 32>)
-# on this workload, from the ncu launch list in profiles/launch_list_landau_2d2v_64.md (cold
-# cache, one BDF3 step)
-EVAL_TRAFFIC_BYTES = 289.2e3
+# DRAM bytes (read + write) per launch of the entry evaluator on this workload, by entry
+# precision, from an ncu capture (cold cache); None where no capture of the current kernel
+# exists
+EVAL_TRAFFIC_BYTES = {"fp32": None, "fp64": None}
+EVAL_TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (cold cache)"
 
 
 def parse():
@@ -45,13 +50,16 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3"],
+    p.add_argument("--precision", default="fp64", choices=["fp32", "fp64", "bf16x3"],
                    help="entry precision of the headline run (bf16x3: 2D2V workloads, "
                         "--profile-step only)")
     p.add_argument("--workload", default="landau_2d2v")
     p.add_argument("--fp64-steps", type=int, default=None,
                    help="steps of the comparison forms (default: --steps, the same steps as the headline)")
-    p.add_argument("--solver", default="learned", choices=["learned", "precond", "plain"])
+    p.add_argument("--solver", default="precond", choices=["learned", "precond", "plain"])
+    p.add_argument("--c1-steps", type=int, default=200,
+                   help="steps of the 1D-1V weak Landau workload timed in microseconds per step "
+                        "(0 skips it)")
     p.add_argument("--train-runs", type=int, default=8)
     p.add_argument("--train-steps", type=int, default=40)
     p.add_argument("--train-iters", type=int, default=1500)
@@ -240,7 +248,7 @@ def run_ours(args, w):
 
     net = None
     train_info = None
-    if args.solver == "learned":
+    if args.train_iters > 0:
         # untimed: samples from seeded weak-Landau runs (alpha ~ U[0.005, 0.05], k ~ U[0.4,
         # 0.6]; the benchmark run itself, alpha 0.01 and k 0.5, is not among them), then Adam
         from paper_2606_29027_b300 import warmstart
@@ -261,20 +269,22 @@ def run_ours(args, w):
                       "seconds": time.perf_counter() - tt0,
                       "family": "2D2V weak Landau, alpha ~ U[0.005,0.05], k ~ U[0.4,0.6], seed 7"}
         del samples
+    if args.solver == "learned" and net is None:
+        raise SystemExit("--solver learned needs the trained network (--train-iters > 0)")
 
-    def make(precision, profile, profile_eval=False, solver=None):
+    def make(precision, profile, profile_eval=False, solver=None, wl=None):
         solver = args.solver if solver is None else solver
-        cfg = slar.make_config(w, precision=precision, profile=profile, profile_eval=profile_eval,
+        cfg = slar.make_config(wl or w, precision=precision, profile=profile, profile_eval=profile_eval,
                                solver=solver)
         c = slar.Context(cfg, stream=stream)
         if solver == "learned":
             c.attach_net(net)
         return c
 
-    def eval_roofline(precision, steps=3):
+    def eval_roofline(precision, solver=None, steps=3):
         # separate pass: events around every evaluator launch (cross approximation launched
         # step by step instead of as a graph); same kernels, same workload
-        cp = make(precision, True, True)
+        cp = make(precision, True, True, solver=solver)
         with torch.cuda.stream(stream):
             cp.init_ht(fac)
             for _ in range(3):
@@ -287,7 +297,7 @@ def run_ours(args, w):
         del cp
         return em, ef, nl
 
-    # ---- device-resident timed run (headline precision) ----
+    # ---- device-resident timed run (headline form) ----
     ctx = make(args.precision, True)
     with torch.cuda.stream(stream):
         ctx.init_ht(fac)
@@ -310,8 +320,9 @@ def run_ours(args, w):
     converged = all(s.converged for s in stats)
     phase_names = ["cross_approx", "truncation", "fields_moments", "lomac_closure", "newton_krylov", "diagnostics"]
     phases = {nm: sum(s.phase_ms[i] for s in stats) / args.steps for i, nm in enumerate(phase_names)}
+    del ctx
 
-    # ---- the plain FP64 GPU form and the plain FP32 form on the same steps ----
+    # ---- the other forms on the same steps ----
     def short_run(precision, solver, K, eps=None, cap=None):
         if eps is None:
             cc = make(precision, True, solver=solver)
@@ -334,44 +345,63 @@ def run_ours(args, w):
                 "newton_per_step": float(np.mean([s.newton for s in stk[-K:]])),
                 "krylov_per_step": float(np.mean([s.krylov for s in stk[-K:]])),
                 "g_evals_per_step": float(np.mean([s.g_evals for s in stk[-K:]])),
+                "guess_used_steps": int(sum(s.guess_used for s in stk[-K:])),
+                "launches_per_step": float(np.mean([s.launches for s in stk[-K:]])),
                 "phase_ms_per_step": {nm: sum(s.phase_ms[i] for s in stk[-K:]) / K
                                       for i, nm in enumerate(phase_names)}}
 
-    fp64 = None
-    forms = None
+    head_key = f"{args.precision}_{args.solver}"
+    forms = {}
+    W_hist = {head_key: np.array([s.field_energy for s in (warm_stats + stats)])}
+    Kh = args.steps
+    forms[head_key] = summary(ms, warm_stats + stats, Kh)
     K = args.steps if args.fp64_steps is None else args.fp64_steps
+    acc = None
     if K > 0:
-        ms64, st64 = short_run("fp64", "plain", K)
-        fp64 = summary(ms64, st64, K)
-        em64, ef64, _ = eval_roofline("fp64", 2)
-        fp64.update({"eval_tflops": ef64 / max(em64, 1e-9) / 1e9,
-                     "eval_frac_of_nominal_fp64_peak": ef64 / max(em64, 1e-9) / 1e9 / FP64_PEAK_TFLOPS,
-                     "steps": K, "form": "plain FP64 GPU path: FP64 entries, unpreconditioned JFNK"})
-        forms = {"steps": K}
-        if not (args.precision == "fp32" and args.solver == "plain"):
-            ms32, st32 = short_run("fp32", "plain", K)
-            forms["fp32_plain"] = summary(ms32, st32, K)
-        Kh = min(K, args.steps)
-        forms["headline"] = summary(ms[:Kh], stats[:Kh], Kh)
+        wanted = [("fp64", "plain"), ("fp32", "precond")] + ([("fp32", "learned")] if net is not None else [])
+        for prec, solver in wanted:
+            key = f"{prec}_{solver}"
+            if key == head_key:
+                continue
+            msk, stk = short_run(prec, solver, K)
+            forms[key] = summary(msk, stk, K)
+            W_hist[key] = np.array([s.field_energy for s in stk])
+        em64, ef64, _ = eval_roofline("fp64", "plain", 2)
+        forms["fp64_plain"]["eval_tflops"] = ef64 / max(em64, 1e-9) / 1e9
         # accuracy: electric-energy history W(t) of each form against an FP64 run truncated
         # 100 times more tightly (rank cap 64), on the same steps
         _, stref = short_run("fp64", "plain", K, eps=w.eps / 100.0, cap=64)
         Wref = np.array([s.field_energy for s in stref])
-        W64 = np.array([s.field_energy for s in st64])
-        Wh = np.array([s.field_energy for s in (warm_stats + stats)])
-        n = min(len(Wref), len(W64), len(Wh))
+        n = min([len(Wref)] + [len(v) for v in W_hist.values()])
         scale = np.max(np.abs(Wref[:n]))
-        forms["accuracy"] = {
-            "steps_compared": n,
-            "reference": f"FP64 plain, eps {w.eps / 100.0:g}, rank cap 64",
-            "W_err_headline": float(np.max(np.abs(Wh[:n] - Wref[:n])) / scale),
-            "W_err_fp64_plain": float(np.max(np.abs(W64[:n] - Wref[:n])) / scale),
-            "W_diff_headline_vs_fp64": float(np.max(np.abs(Wh[:n] - W64[:n])) / scale),
-            "W_first_step_rel_diff_headline_vs_fp64": float(abs(Wh[0] - W64[0]) / abs(W64[0])),
-            "measure": "max over steps of |W - W_ref| / max |W_ref|",
-            "note": "weak Landau perturbs f by alpha = 0.01, so a truncation error eps ||f|| is "
-                    "eps / alpha relative to the field: the eps-1e-5 method itself is accurate "
-                    "to about 1e-3 in W"}
+        acc = {"steps_compared": n, "reference": f"FP64 plain, eps {w.eps / 100.0:g}, rank cap 64",
+               "measure": "max over steps of |W - W_ref| / max |W_ref|",
+               "note": "weak Landau perturbs f by alpha = 0.01, so a truncation error eps ||f|| is "
+                       "eps / alpha relative to the field: the eps-1e-5 method itself is accurate "
+                       "to about 1e-3 in W"}
+        for key, Wk in W_hist.items():
+            forms[key]["W_err"] = float(np.max(np.abs(Wk[:n] - Wref[:n])) / scale)
+            if "fp64_plain" in W_hist:
+                forms[key]["W_diff_vs_fp64_plain"] = float(np.max(np.abs(Wk[:n] - W_hist["fp64_plain"][:n])) / scale)
+
+    # ---- the 1D-1V weak Landau workload (64 x 128, cap 16, eps 1e-6, dt 0.1): FP64, the
+    # paper's JFNK; latency-bound, so microseconds per step ----
+    c1 = None
+    if args.c1_steps > 0:
+        w1 = inputs.landau_1d1v()
+        c1c = make("fp64", True, solver="plain", wl=w1)
+        with torch.cuda.stream(stream):
+            c1c.init_ht(inputs.initial_factors(w1))
+            for _ in range(2):
+                c1c.step(w1.dt)
+        barrier()
+        ms1, st1 = time_steps(c1c, w1, args.c1_steps - 2, flush, stream)
+        c1 = {"workload": "landau_1d1v_64x128: alpha 0.01, k 0.5, cap 16, eps 1e-6, dt 0.1, FP64, plain JFNK; "
+                          f"BDF3 steps 3..{args.c1_steps} (after the 2 DIRK3 steps)",
+              "us_per_step": 1000.0 * float(np.mean(ms1)), "us_per_step_median": 1000.0 * float(np.median(ms1)),
+              "launches_per_step": float(np.mean([s.launches for s in st1])),
+              "W_last": st1[-1].field_energy, "converged": all(s.converged for s in st1)}
+        del c1c
 
     # ---- the 128^4 configurations: FP32 SIMT entries vs BF16x3 tensor-core entries ----
     large = None
@@ -438,7 +468,7 @@ def run_ours(args, w):
             ec.close()
         del ectx
 
-    # ---- end to end through the C ABI with host buffers ----
+    # ---- end to end through the C ABI with host buffers (headline form) ----
     e2e_steps = max(3, args.warmup) + min(args.steps, 10)
     ctx_e = make(args.precision, False)
     U_host = torch.empty((w.dv + 2, ctx_e.NX), dtype=torch.float64, pin_memory=True)
@@ -477,6 +507,7 @@ def run_ours(args, w):
                         else "k_sl_eval_tc (tcgen05, BF16x3)",
                         "ms": ms64, "tflops": tf64, "peak_tflops": pk, "frac": tf64 / pk, "peak_source": src}
     achieved = eval_flop / max(eval_ms, 1e-9) / 1e9          # TFLOP/s
+    traffic = EVAL_TRAFFIC_BYTES.get(args.precision)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -486,20 +517,19 @@ def run_ours(args, w):
             "entries_per_step": entries / args.steps,
             "converged": converged,
             "ranks_last": list(stats[-1].ranks),
-            "fp64_path": fp64,
             "forms": forms,
+            "accuracy": acc,
             "warm_start_training": train_info,
             "ensemble": ensemble,
             "large_128": large,
             "newton_per_step": float(np.mean([s.newton for s in stats])),
             "krylov_per_step": float(np.mean([s.krylov for s in stats])),
-            "guess_used_steps": int(sum(s.guess_used for s in stats)),
-            "roofline": {"kernel": "k_sl_eval (SL entry evaluator)", "bound": "alu",
+            "roofline": {"kernel": f"k_sl_eval_dev<{'double' if args.precision == 'fp64' else 'float'}> "
+                                   "(SL entry evaluator)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": EVAL_TRAFFIC_BYTES if args.precision == "fp32" else None,
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                                           "profiles/launch_list_landau_2d2v_64.md (cold cache)",
+                         "traffic": traffic,
+                         "traffic_source": EVAL_TRAFFIC_SOURCE if traffic is not None else None,
                          "peak_source": "measured in this run: FMA-chain kernel (slar_fma_peak), "
                                         "best of 3; derived FP32 148 SMs x 128 lanes x 2 x 2032 MHz = "
                                         f"{FP32_PEAK_TFLOPS:.1f}, nominal FP64 {FP64_PEAK_TFLOPS}",
@@ -508,19 +538,34 @@ def run_ours(args, w):
                          "method": "separate profiled pass of 3 steps: CUDA events around each "
                                    "evaluator launch on the library stream; algorithmic flops "
                                    "2(3 sum r_mu + r0 r1 r12 + r2 r3 r34 + r12 r34) + 60 per entry",
-                         "eval_ms_per_step": eval_ms / 3.0,
-                         "step_shares": "cold-cache ncu launch list of one BDF3 step "
-                                        "(profiles/launch_list_landau_2d2v_64.md): this "
-                                        "evaluator 14.5 %, FFT passes k_fft_lines 14.6 %; "
-                                        "both latency-bound"},
+                         "eval_ms_per_step": eval_ms / 3.0},
             "eval_rank64": eval64,
             "phase_ms_per_step": phases,
-            "gpu_launches": launches, "wall_s": wall, "clocks": clocks, "e2e": e2e}
+            "gpu_launches": launches, "wall_s": wall, "clocks": clocks, "e2e": e2e,
+            "c1_landau_1d1v": c1}
     if not args.no_cpu_baseline and world == 1:
         sps, eps_, dt = oracle_steps(w, 2, 1)
-        line["cpu_baseline"] = {"value": sps, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+        cores = cpu_threads()
+        try:
+            from threadpoolctl import threadpool_limits
+            with threadpool_limits(limits=1):
+                sps1, _, dt1 = oracle_steps(w, 2, 1)
+        except ImportError:
+            sps1, dt1 = None, None
+        line["cpu_baseline"] = {"value": sps, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"1 oracle BDF3 step of {w.name} after 2 untimed DIRK3 "
-                                          f"start-up steps ({dt:.1f} s); entries/s {eps_:.3g}"}
+                                          f"start-up steps ({dt:.1f} s); entries/s {eps_:.3g}",
+                                "single_thread": sps1}
+    # compact summary last, so that it stays in a short tail of the output
+    line["summary"] = {
+        "headline": f"{head_key}: {value:.1f} steps/s, W_err {forms[head_key].get('W_err', float('nan')):.1e}",
+        "forms_steps_per_s": {k: round(v["value"], 2) for k, v in forms.items()},
+        "forms_W_err": {k: v.get("W_err") for k, v in forms.items()},
+        "forms_launches_per_step": {k: round(v["launches_per_step"], 1) for k, v in forms.items()},
+        "learned_guess_used_steps": forms.get("fp32_learned", {}).get("guess_used_steps"),
+        "c1_us_per_step": c1["us_per_step"] if c1 else None,
+        "cpu_single_thread_steps_per_s": line.get("cpu_baseline", {}).get("single_thread"),
+        "roofline_frac": achieved / peak}
     print(json.dumps(line), flush=True)
 
 

@@ -38,7 +38,11 @@ enum {
     SLAR_ECUDA = 3,     /* a CUDA call failed (message has the CUDA error string) */
     SLAR_ENOCONV = 4,   /* Newton / GMRES did not reach its tolerance; state is still advanced */
     SLAR_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
-    SLAR_ERANK = 6,     /* rank cap reached before the tolerance was met (result valid) */
+    SLAR_ERANK = 6,     /* warning: a rank cap was reached before eps was met, in the cross
+                           approximation (rank-1 stop test unmet at the cap) or in an HSVD
+                           truncation (discarded energy above the threshold at the cap); the
+                           call completed and its result is valid (sl_step, slar_advect,
+                           ht_truncate, init_ht) */
     SLAR_ENAN = 7       /* non-finite values detected */
 };
 
@@ -112,6 +116,8 @@ typedef struct slar_stats {
     int recorded;           /* a training sample was written (slar_set_record) */
     int g_evals;            /* residual evaluations G(U) of the Newton-Krylov solves */
     int eval_tile;          /* entries per CTA of the entry evaluator (autotuned: 16, 32, 64) */
+    int rank_capped;        /* cross approximations and truncations of this step that stopped at
+                               the rank cap with eps unmet (non-zero: sl_step returns SLAR_ERANK) */
 } slar_stats;
 
 /* Host-side view of an HT state for import/export.  Layouts (row-major):
@@ -152,7 +158,8 @@ const char* slar_last_error(const slar_ctx* ctx);
  * `factors` of n_terms * (N[0]+..+N[d-1]) values laid out [t][mu][i].  The separable sum
  * is converted to an HT, HSVD-truncated with eps and rank_cap (Supp. B.1), the ion
  * density is set to mean(M0(F^0)) and U^0 = U(F^0).  Resets the step counter.
- * Errors: SLAR_EINVAL (n_terms < 1 or > rank limit). */
+ * Errors: SLAR_EINVAL (n_terms < 1 or > rank limit); SLAR_ERANK (warning: the truncation
+ * met its cap with eps unmet; the state is set). */
 slar_status init_ht(slar_ctx* ctx, int n_terms, const double* factors);
 
 /* Autotuning (an addition to the paper): the first SLAR call that meets a new (tree,
@@ -166,22 +173,31 @@ slar_status init_ht(slar_ctx* ctx, int n_terms, const double* factors);
  * SLAR_LOMAC, the moments of F*, the adaptive weight and basis (Supp. B), the JFNK solve
  * of the macroscopic system (DIRK3 for the first two steps, BDF3 after) and the update
  * F^{n+1} = F* - R(U(F*)) + R(U^{n+1}).  `stats` (host, may be NULL) receives the
- * step diagnostics.  Errors: SLAR_EINVAL (no state), SLAR_ENOCONV (Newton or GMRES did
- * not converge; the state is advanced with the last iterate). */
+ * step diagnostics.  Errors: SLAR_EINVAL (no state), SLAR_ENAN (U^n, the Newton residual,
+ * the field energy or the totals are not finite; checked before the solve and after the
+ * step), SLAR_ENOCONV (Newton or GMRES did not converge within newton_max / krylov_max;
+ * with SLAR_PRECOND / SLAR_LEARNED the failed solve was first repeated by plain JFNK,
+ * stats.fallback = 1; the state is advanced with the last iterate), SLAR_ERANK (warning,
+ * see above; the state is advanced).  SLAR_ENOCONV takes precedence over SLAR_ERANK. */
 slar_status sl_step(slar_ctx* ctx, double dt, slar_stats* stats);
 
 /* HSVD truncation of the HT part of the state (Supp. B.1): orthogonalise, node Gram
  * matrices from the root down, eigendecomposition, keep per node the smallest rank with
  * discarded energy <= (eps ||F||)^2/(2d-3), capped at rank_cap.  Afterwards column 0 of
  * every leaf is the leading left singular vector of its mode matricisation.
- * Errors: SLAR_EINVAL (eps < 0, rank_cap < 1 or > 64). */
+ * Errors: SLAR_EINVAL (eps < 0, rank_cap < 1 or > 64); SLAR_ERANK (warning: the cap bound
+ * with eps unmet, result valid). */
 slar_status ht_truncate(slar_ctx* ctx, double eps, int rank_cap);
 
-/* All velocity moments of the state (HT + correction) as device FP64
- * out[n_mom][NX] (Eq. raw moments and the flux moments of Eq. macro_sys_comp):
+/* Velocity moments of the state (HT + correction) as device FP64 out[n_sel][NX]
+ * (Eq. raw moments and the flux moments of Eq. macro_sys_comp).  The full table, in order:
  * M0, M1_1..M1_dv, M2, <v_a v_b f> (a <= b), <|v|^2 v_a f>;  n_mom = 5 (dv = 1) or 9
- * (dv = 2).  Midpoint quadrature in v (Supp. B.1). */
-slar_status moments(slar_ctx* ctx, double* out_dev);
+ * (dv = 2).  `mask` selects groups of it (SLAR_MOM_*; 0 = all); the selected rows are
+ * written packed in table order, n_sel = 1 (M0) + dv (M1) + 1 (M2) + (n_mom - dv - 2)
+ * (flux) over the selected groups.  Midpoint quadrature in v (Supp. B.1).
+ * Errors: SLAR_EINVAL (null pointer, unknown mask bits, no state). */
+enum { SLAR_MOM_M0 = 1, SLAR_MOM_M1 = 2, SLAR_MOM_M2 = 4, SLAR_MOM_FLUX = 8, SLAR_MOM_ALL = 15 };
+slar_status moments(slar_ctx* ctx, unsigned mask, double* out_dev);
 
 /* Adaptive-weight LoMaC update of the current state treated as F* (Sec. 3.2.2,
  * Supp. B): weight from column 0 of the velocity leaves, weighted Gram-Schmidt, then
@@ -223,25 +239,41 @@ slar_status slar_set_pivot_replay(slar_ctx* ctx, int n_calls, int kmax, const in
 slar_status ht_export(slar_ctx* ctx, slar_ht_view* view);
 slar_status ht_import(slar_ctx* ctx, const slar_ht_view* view);
 
+/* Checkpoint and restore of a run (Sec. 3.2.3: everything the next step reads).  The file
+ * (host byte order, written by slar_checkpoint at `path`, overwritten if present) holds the
+ * FP64 HT factors of F^n and its LoMaC correction, U^n, U^{n-1}, U^{n-2}, the ion density,
+ * the step counter (which selects DIRK3 start-up or BDF3), the FP64 eigenbases that the next
+ * truncation starts its Jacobi sweeps from, and the parameters of the attached network (if
+ * any).  slar_restore loads it into a context created with the same grid, box and precision
+ * (else SLAR_EINVAL); the network parameters are loaded only if a network of the same size
+ * is attached.  A restored FP64 run continues bit for bit like the run that wrote the file
+ * (same process: the autotuned evaluator tile is kept per process).  Both calls synchronise
+ * the context stream.  Errors: SLAR_EINVAL (no state, file cannot be opened / read /
+ * written, wrong magic or version, mismatch), SLAR_ECUDA. */
+slar_status slar_checkpoint(slar_ctx* ctx, const char* path);
+slar_status slar_restore(slar_ctx* ctx, const char* path);
+
 /* Conserved variables U^n (device FP64 [dv+2][NX]) and the ion density. */
 slar_status slar_get_conserved(slar_ctx* ctx, double* U_dev, double* n_i);
 slar_status slar_set_conserved(slar_ctx* ctx, const double* U_dev, double n_i);
 
 /* Allocation-free spectral Poisson solve for callers that cannot allocate device memory:
- * code that runs while a stream is recorded into a CUDA graph in a capture mode in which
- * cudaMalloc is illegal, or a host framework that owns a fixed, pre-reserved device pool
- * and does not let libraries allocate.  The paper has no counterpart of this entry point;
- * it computes what poisson_field computes, without a context.
+ * a host framework that owns a fixed, pre-reserved device pool and does not let libraries
+ * allocate, or code running where a cudaMalloc is not permitted at that point.  The paper has
+ * no counterpart of this entry point; it computes what poisson_field computes, without a
+ * context.
  *   dx in {1, 2}; N[m] a power of two <= 128; L[m] > 0 the period of dimension m;
  *   rho_dev: device [NX]; E_dev: device [dx][NX]; phi_dev: device [NX] or NULL;
- *   energy: host scalar or NULL (then the call synchronises `stream`);
+ *   energy: host scalar or NULL; when non-NULL the call copies the energy back and
+ *   synchronises `stream`, with NULL it only enqueues work;
  *   stream: cudaStream_t (NULL = legacy default stream).
  * Scratch (1 MiB of spectra plus twiddle and wavenumber tables) is a set of file-scope
  * static __device__ arrays that every GPU loading the library holds until process exit;
  * this call allocates nothing (no cudaMalloc/cudaFree).  The first call on a device looks
  * up the arrays' device addresses (cudaGetSymbolAddress), so make that first call before
- * any stream capture.  All calls share the arrays and overwrite them completely; calls that
- * overlap on the GPU (several streams or threads) race.  Returns SLAR_EINVAL for sizes
+ * any stream capture.  All calls share the arrays: every call rewrites the twiddle and
+ * wavenumber tables as well as the spectra, so calls that overlap on the GPU (several
+ * streams or threads) race, even when their grids differ.  Returns SLAR_EINVAL for sizes
  * beyond the maximum or bad arguments, SLAR_ECUDA if a CUDA call fails. */
 slar_status slar_poisson_field_static(int dx, const int* N, const double* L, const double* rho_dev,
                                       double* E_dev, double* phi_dev, double* energy, void* stream);

@@ -75,6 +75,7 @@ class StepStats:
     aca_ranks: list = dfield(default_factory=list)
     guess_used: bool = False
     fallback: bool = False
+    pivots: list = dfield(default_factory=list)   # (row, column) pivots of each SLAR call
 
 
 def init_state(factors, g: PhaseGrid, prm: Params) -> State:
@@ -190,6 +191,7 @@ def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None,
         st.U = lomac.conserved_from_moments(field.moments(Fs, g), g, st.n_i)
         stats.entries, stats.ranks = info["entries"], info["ranks"]
         stats.aca_ranks = info["aca_ranks"]
+        stats.pivots = info["pivots"]
     elif st.step < 2:
         A, c = macro.dirk3_tableau()
         tol_abs = macro.newton_tol_abs(prm.newton_tol, st.U)
@@ -198,6 +200,7 @@ def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None,
             Fs, info = slar_vp(st.F, c[i] * dt, g, prm, st.n_i, None if pivots is None else pivots[i])
             stats.entries += info["entries"]
             stats.aca_ranks += info["aca_ranks"]
+            stats.pivots += info["pivots"]
             cl = macro.make_closure(Fs, g, st.n_i, prm.delta)
             rhs = st.U + dt * sum(A[i, j] * Ks[j] for j in range(i)) if i else st.U.copy()
             Ustar = lomac.conserved_from_moments(cl.mom_star, g, st.n_i)
@@ -216,6 +219,7 @@ def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None,
         Fs, info = slar_vp(st.F, dt, g, prm, st.n_i, pivots)
         stats.entries, stats.ranks = info["entries"], info["ranks"]
         stats.aca_ranks = info["aca_ranks"]
+        stats.pivots = info["pivots"]
         cl = macro.make_closure(Fs, g, st.n_i, prm.delta)
         a = macro.BDF3["a"]
         rhs = a[0] * st.U + a[1] * st.hist[0] + a[2] * st.hist[1]

@@ -15,6 +15,7 @@
 // of the norm estimate, and one CTA updates the estimate, tests the stop rule and picks the
 // next row pivot.  A device flag makes the remaining launches of a stopped approximation
 // exit immediately; the host reads the final rank once.
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -148,7 +149,7 @@ __device__ void segment_argmax_tie(const double* a, int n, const unsigned char* 
   __syncthreads();
 }
 
-__global__ void k_aca_init(AcaState* st, int* pivI, unsigned char* usedr, int replay, double eps) {
+__global__ void k_aca_init(AcaState* st, int* pivI, unsigned char* usedr, int replay, double eps, int cap_binds) {
   if (threadIdx.x != 0) return;
   st->k = 0;
   st->done = 0;
@@ -157,6 +158,8 @@ __global__ void k_aca_init(AcaState* st, int* pivI, unsigned char* usedr, int re
   st->eps = eps;
   st->tc_err = 0;
   st->normA2 = 0.0;
+  st->cap_binds = cap_binds;
+  st->capped = 0;
   if (!replay) pivI[0] = 0;
   if (pivI[0] < 0) { st->done = 1; return; }
   usedr[pivI[0]] = 1;
@@ -230,6 +233,9 @@ __device__ void aca_finalize_body(const double* __restrict__ Ua, int M1, int kma
     int next = -1;
     if (kk + 1 >= kmax) {
       stop = 1;
+      // the cap ends the approximation although the rank-1 test is not met: eps is not
+      // reached within the cap (a warning; the result is still a valid approximation)
+      if (!replay && st->cap_binds && sqrt(nu2) * sqrt(nv2) > eps * sqrt(fmax(n2, 0.0))) st->capped = 1;
     } else if (!replay && sqrt(nu2) * sqrt(nv2) <= eps * sqrt(fmax(n2, 0.0))) {
       stop = 1;
       if (n_chk > 0) {
@@ -590,7 +596,8 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
     P->foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
   }
   CK(cudaMemcpyAsync(c->evp, c->evp_host, sizeof(EvalParams<double>), cudaMemcpyHostToDevice, s));
-  slar::count_launch(), k_aca_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->usedr, replay ? 1 : 0, c->cfg.eps);
+  slar::count_launch(), k_aca_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->usedr, replay ? 1 : 0, c->cfg.eps,
+                                                    kmax < std::min(M1, M2) ? 1 : 0);
   CK(cudaGetLastError());
   long long chk_entries = 0;
   if (!replay && c->n_chk > 0) {
@@ -618,6 +625,7 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
   CK(cudaMemcpyAsync(c->ast_host, c->ast, sizeof(AcaState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const int k = c->ast_host->k;
+  if (c->ast_host->capped) c->rank_capped++;
   if (c->ast_host->tc_err)
     return set_error(c, SLAR_ETIMEOUT, "tensor-core evaluator: an MMA completion wait ran out");
   if (!prof) add_launches(c->aca_graph_nodes * (long long)((k + c->ast_host->stop_row + ACA_UNROLL - 1) / ACA_UNROLL));

@@ -381,6 +381,7 @@ slar_status init_ht(slar_ctx* c, int n_terms, const double* factors) {
   h.valid = true;
   TruncIn in = trunc_in_of_slot(c, tmp);
   const int dst = spare_slot(c, tmp);
+  const long long capped0 = c->rank_capped;
   CKS(truncate_into(c, in, c->cfg.eps, c->cfg.rank_cap, dst));
   h.valid = false;
   c->cur = dst;
@@ -389,6 +390,7 @@ slar_status init_ht(slar_ctx* c, int n_terms, const double* factors) {
   CKS(conserved_of_state(c, true));
   c->has_U = true;
   CK(cudaStreamSynchronize(c->s));
+  if (c->rank_capped != capped0) return set_error(c, SLAR_ERANK, "rank cap reached with eps unmet (result valid)");
   return SLAR_OK;
 }
 
@@ -397,10 +399,12 @@ slar_status ht_truncate(slar_ctx* c, double eps, int cap) {
   if (!(eps >= 0.0) || cap < 1 || cap > SLAR_MAX_RANK) return set_error(c, SLAR_EINVAL, "bad eps or cap");
   if (!c->ht[c->cur].valid) return set_error(c, SLAR_EINVAL, "no HT state");
   const int dst = spare_slot(c, c->cur);
+  const long long capped0 = c->rank_capped;
   CKS(truncate_into(c, trunc_in_of_slot(c, c->cur), eps, cap, dst));
   c->ht[c->cur].valid = false;
   c->cur = dst;
   CK(cudaStreamSynchronize(c->s));
+  if (c->rank_capped != capped0) return set_error(c, SLAR_ERANK, "rank cap reached with eps unmet (result valid)");
   return SLAR_OK;
 }
 
@@ -432,10 +436,12 @@ slar_status sl_eval(slar_ctx* c, double tau, const double* E, long long n, const
 slar_status slar_advect(slar_ctx* c, double tau, const double* E, int* aca_rank, long long* entries) {
   if (!c || !E) return SLAR_EINVAL;
   const int dst = spare_slot(c, c->cur);
+  const long long capped0 = c->rank_capped;
   CKS(slar_call(c, c->cur, true, tau, E, dst, aca_rank, entries));
   c->ht[c->cur].valid = false;
   c->cur = dst;
   c->has_corr = 0;
+  if (c->rank_capped != capped0) return set_error(c, SLAR_ERANK, "rank cap reached with eps unmet (result valid)");
   return SLAR_OK;
 }
 
@@ -448,9 +454,27 @@ slar_status slar_set_pivot_replay(slar_ctx* c, int n_calls, int kmax, const int*
   return SLAR_OK;
 }
 
-slar_status moments(slar_ctx* c, double* out) {
+slar_status moments(slar_ctx* c, unsigned mask, double* out) {
   if (!c || !out) return SLAR_EINVAL;
-  return compute_moments(c, c->cur, true, out, c->n_mom);
+  if (mask & ~(unsigned)SLAR_MOM_ALL) return set_error(c, SLAR_EINVAL, "unknown moment mask bits");
+  if (mask == 0) mask = SLAR_MOM_ALL;
+  // rows of the full table in order: M0 | M1 (dv) | M2 | flux moments (n_mom - dv - 2)
+  const int dv = c->dv;
+  std::vector<int> rows;
+  if (mask & SLAR_MOM_M0) rows.push_back(0);
+  if (mask & SLAR_MOM_M1)
+    for (int a = 0; a < dv; ++a) rows.push_back(1 + a);
+  if (mask & SLAR_MOM_M2) rows.push_back(1 + dv);
+  if (mask & SLAR_MOM_FLUX)
+    for (int q = dv + 2; q < c->n_mom; ++q) rows.push_back(q);
+  bool prefix = true;
+  for (size_t i = 0; i < rows.size(); ++i) prefix = prefix && rows[i] == (int)i;
+  if (prefix) return compute_moments(c, c->cur, true, out, (int)rows.size());
+  CKS(compute_moments(c, c->cur, true, c->mom, rows.back() + 1));
+  for (size_t i = 0; i < rows.size(); ++i)
+    CK(cudaMemcpyAsync(out + (size_t)i * c->NX, c->mom + (size_t)rows[i] * c->NX, sizeof(double) * c->NX,
+                       cudaMemcpyDeviceToDevice, c->s));
+  return SLAR_OK;
 }
 
 slar_status poisson_field(slar_ctx* c, const double* rho, double* E, double* phi, double* energy) {
@@ -602,6 +626,157 @@ slar_status slar_ensemble_step(slar_ctx** ctxs, int n, const double* dts, int th
   for (auto& th : pool) th.join();
   for (int i = 0; i < n; ++i)
     if (st[i] != SLAR_OK) return st[i];
+  return SLAR_OK;
+}
+
+// ---------------- checkpoint / restore ----------------
+namespace {
+
+constexpr char kCkptMagic[8] = {'S', 'L', 'A', 'R', 'C', 'K', 'P', 'T'};
+constexpr int kCkptVersion = 1;
+
+// Fixed-size header of a checkpoint file (host byte order); the arrays follow in the order
+// written by slar_checkpoint.
+struct CkptHeader {
+  char magic[8];
+  int version;
+  int d, dx, dv;
+  int N[4];
+  double lo[4], hi[4];
+  int precision;
+  int step, has_U, has_corr;
+  int rank[6];
+  int Sn[6];
+  double n_i;
+  long long net_np;   // parameters of the attached network saved (0: none)
+};
+
+struct File {
+  FILE* f = nullptr;
+  ~File() { if (f) fclose(f); }
+};
+
+bool wr(FILE* f, const void* p, size_t bytes) { return fwrite(p, 1, bytes, f) == bytes; }
+bool rd(FILE* f, void* p, size_t bytes) { return fread(p, 1, bytes, f) == bytes; }
+
+// device FP64 array <-> file through a host buffer
+slar_status dev_to_file(slar_ctx* c, FILE* f, const double* d, size_t n) {
+  std::vector<double> h(n);
+  if (n) CK(cudaMemcpy(h.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  if (!wr(f, h.data(), sizeof(double) * n)) return set_error(c, SLAR_EINVAL, "checkpoint: write failed");
+  return SLAR_OK;
+}
+
+slar_status file_to_dev(slar_ctx* c, FILE* f, double* d, size_t n) {
+  std::vector<double> h(n);
+  if (!rd(f, h.data(), sizeof(double) * n)) return set_error(c, SLAR_EINVAL, "restore: file truncated");
+  if (n) CK(cudaMemcpy(d, h.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  return SLAR_OK;
+}
+
+}  // namespace
+
+slar_status slar_checkpoint(slar_ctx* c, const char* path) {
+  if (!c || !path) return SLAR_EINVAL;
+  const HTBuf& h = c->ht[c->cur];
+  if (!h.valid || !c->has_U) return set_error(c, SLAR_EINVAL, "checkpoint: no state (call init_ht first)");
+  CK(cudaStreamSynchronize(c->s));
+  CkptHeader hd{};
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = kCkptVersion;
+  hd.d = c->d; hd.dx = c->dx; hd.dv = c->dv;
+  for (int m = 0; m < 4; ++m) { hd.N[m] = c->cfg.N[m]; hd.lo[m] = c->cfg.lo[m]; hd.hi[m] = c->cfg.hi[m]; }
+  hd.precision = c->cfg.precision;
+  hd.step = c->step; hd.has_U = c->has_U ? 1 : 0; hd.has_corr = c->has_corr;
+  for (int i = 0; i < 6; ++i) { hd.rank[i] = h.r[i]; hd.Sn[i] = c->Sn[i]; }
+  hd.n_i = c->n_i;
+  hd.net_np = c->net ? net_np(c->net) : 0;
+  File F;
+  F.f = fopen(path, "wb");
+  if (!F.f) return set_error(c, SLAR_EINVAL, "checkpoint: cannot open the file for writing");
+  if (!wr(F.f, &hd, sizeof(hd))) return set_error(c, SLAR_EINVAL, "checkpoint: write failed");
+  for (int m = 0; m < c->d; ++m) CKS(dev_to_file(c, F.f, h.U[m], (size_t)c->g.N[m] * h.r[m]));
+  if (c->d == 4) {
+    CKS(dev_to_file(c, F.f, h.B12, (size_t)h.r[4] * h.r[0] * h.r[1]));
+    CKS(dev_to_file(c, F.f, h.B34, (size_t)h.r[5] * h.r[2] * h.r[3]));
+    CKS(dev_to_file(c, F.f, h.Broot, (size_t)h.r[4] * h.r[5]));
+  } else {
+    CKS(dev_to_file(c, F.f, h.Broot, (size_t)h.r[0] * h.r[1]));
+  }
+  const size_t nU = (size_t)(c->dv + 2) * c->NX;
+  if (c->has_corr) {
+    CKS(dev_to_file(c, F.f, c->dC, nU));
+    CKS(dev_to_file(c, F.f, c->qv, (size_t)3 * c->dv * c->g.N[c->dx]));
+  }
+  CKS(dev_to_file(c, F.f, c->Uc, nU));
+  CKS(dev_to_file(c, F.f, c->Uh1, nU));
+  CKS(dev_to_file(c, F.f, c->Uh2, nU));
+  for (int t = 0; t < 6; ++t)
+    if (c->Sn[t] > 0) CKS(dev_to_file(c, F.f, c->S[t], (size_t)c->Sn[t] * c->Sn[t]));
+  if (hd.net_np > 0) {
+    std::vector<float> th((size_t)hd.net_np);
+    CKS(slar_net_get_params(c->net, th.data(), hd.net_np));
+    if (!wr(F.f, th.data(), sizeof(float) * th.size())) return set_error(c, SLAR_EINVAL, "checkpoint: write failed");
+  }
+  if (fflush(F.f) != 0) return set_error(c, SLAR_EINVAL, "checkpoint: write failed");
+  return SLAR_OK;
+}
+
+slar_status slar_restore(slar_ctx* c, const char* path) {
+  if (!c || !path) return SLAR_EINVAL;
+  File F;
+  F.f = fopen(path, "rb");
+  if (!F.f) return set_error(c, SLAR_EINVAL, "restore: cannot open the file");
+  CkptHeader hd{};
+  if (!rd(F.f, &hd, sizeof(hd)) || std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != kCkptVersion)
+    return set_error(c, SLAR_EINVAL, "restore: not a checkpoint of this library version");
+  bool same = hd.d == c->d && hd.dx == c->dx && hd.dv == c->dv && hd.precision == c->cfg.precision;
+  for (int m = 0; m < 4; ++m)
+    same = same && hd.N[m] == c->cfg.N[m] && hd.lo[m] == c->cfg.lo[m] && hd.hi[m] == c->cfg.hi[m];
+  if (!same) return set_error(c, SLAR_EINVAL, "restore: grid, box or precision differ from the context's");
+  for (int i = 0; i < (c->d == 4 ? 6 : 2); ++i)
+    if (hd.rank[i] < 1 || hd.rank[i] > SLAR_MAX_RANK) return set_error(c, SLAR_EINVAL, "restore: bad rank");
+  for (int t = 0; t < 6; ++t)
+    if (hd.Sn[t] < 0 || hd.Sn[t] > SLAR_MAX_N) return set_error(c, SLAR_EINVAL, "restore: bad basis order");
+  if (hd.step < 0 || hd.has_U != 1 || (hd.has_corr != 0 && hd.has_corr != 1) || hd.net_np < 0)
+    return set_error(c, SLAR_EINVAL, "restore: bad header");
+  CK(cudaStreamSynchronize(c->s));
+  const int dst = spare_slot(c, c->cur);
+  HTBuf& h = c->ht[dst];
+  for (int i = 0; i < 6; ++i) h.r[i] = hd.rank[i];
+  if (c->d == 2) h.r[2] = h.r[3] = h.r[4] = h.r[5] = 0;
+  for (int m = 0; m < c->d; ++m) CKS(file_to_dev(c, F.f, h.U[m], (size_t)c->g.N[m] * h.r[m]));
+  if (c->d == 4) {
+    CKS(file_to_dev(c, F.f, h.B12, (size_t)h.r[4] * h.r[0] * h.r[1]));
+    CKS(file_to_dev(c, F.f, h.B34, (size_t)h.r[5] * h.r[2] * h.r[3]));
+    CKS(file_to_dev(c, F.f, h.Broot, (size_t)h.r[4] * h.r[5]));
+  } else {
+    CKS(file_to_dev(c, F.f, h.Broot, (size_t)h.r[0] * h.r[1]));
+  }
+  const size_t nU = (size_t)(c->dv + 2) * c->NX;
+  if (hd.has_corr) {
+    CKS(file_to_dev(c, F.f, c->dC, nU));
+    CKS(file_to_dev(c, F.f, c->qv, (size_t)3 * c->dv * c->g.N[c->dx]));
+  }
+  CKS(file_to_dev(c, F.f, c->Uc, nU));
+  CKS(file_to_dev(c, F.f, c->Uh1, nU));
+  CKS(file_to_dev(c, F.f, c->Uh2, nU));
+  for (int t = 0; t < 6; ++t)
+    if (hd.Sn[t] > 0) CKS(file_to_dev(c, F.f, c->S[t], (size_t)hd.Sn[t] * hd.Sn[t]));
+  if (hd.net_np > 0) {
+    std::vector<float> th((size_t)hd.net_np);
+    if (!rd(F.f, th.data(), sizeof(float) * th.size())) return set_error(c, SLAR_EINVAL, "restore: file truncated");
+    if (c->net && net_np(c->net) == hd.net_np) CKS(slar_net_set_params(c->net, th.data(), hd.net_np));
+  }
+  h.valid = true;
+  if (dst != c->cur) c->ht[c->cur].valid = false;
+  c->cur = dst;
+  if (c->f32_slot == dst) c->f32_slot = -1;
+  c->has_corr = hd.has_corr;
+  c->has_U = true;
+  c->n_i = hd.n_i;
+  c->step = hd.step;
+  for (int t = 0; t < 6; ++t) c->Sn[t] = hd.Sn[t];
   return SLAR_OK;
 }
 

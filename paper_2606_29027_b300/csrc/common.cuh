@@ -153,11 +153,14 @@ struct EigJob {
 };
 cudaError_t eig_batched(const EigJob* jobs_host, int njobs, EigJob* jobs_dev, cudaStream_t s);
 // Rank selection from descending eigenvalues: smallest k with tail sum <= thr2, k in [1, cap].
+// If that k exceeds cap (the tolerance cannot be met within the cap), *capped (when given)
+// is set to 1.
 struct RankJob {
   const double* W;
   int n;
   int cap;
   int* out;
+  int* capped;
 };
 cudaError_t choose_ranks(const RankJob* jobs_host, int njobs, RankJob* jobs_dev, const double* normF2,
                          double scale, cudaStream_t s);

@@ -39,6 +39,8 @@ struct AcaState {
   double eps;     // stopping tolerance
   int tc_err;     // set by the tensor-core evaluator if an MMA completion wait ran out
   unsigned int post_ctr;  // block tickets of k_aca_post (reset by its last block)
+  int cap_binds;  // the rank cap is below min(M1, M2) (reaching it leaves an error)
+  int capped;     // stopped at the rank cap with the stop test unmet
 };
 
 }  // namespace slar
@@ -178,6 +180,10 @@ struct slar_ctx {
   float* rec_dst = nullptr;        // device destination of the next sample (one-shot)
   int rec_S = 0;
   unsigned long long rec_seed = 0;
+
+  // SLAR calls and truncations that stopped at the rank cap with eps unmet (running count;
+  // sl_step, slar_advect, ht_truncate and init_ht report SLAR_ERANK when it grows)
+  long long rank_capped = 0;
 
   char err[512] = {0};
 };

@@ -328,14 +328,16 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
   CK(cudaGetLastError());
   RankJob rj[5];
   int nr = 0;
-  for (int m = 0; m < d; ++m) rj[nr++] = RankJob{c->W[m], node_n[m], cap, c->d_ranks + m};
-  if (d == 4) rj[nr++] = RankJob{c->W[4], node_n[4], cap, c->d_ranks + 4};
+  for (int m = 0; m < d; ++m) rj[nr++] = RankJob{c->W[m], node_n[m], cap, c->d_ranks + m, c->d_ranks + 6};
+  if (d == 4) rj[nr++] = RankJob{c->W[4], node_n[4], cap, c->d_ranks + 4, c->d_ranks + 6};
+  CK(cudaMemsetAsync(c->d_ranks + 6, 0, sizeof(int), s));
   CK(choose_ranks(rj, nr, c->d_rank, c->norm2, eps * eps / (2.0 * d - 3.0), s));
-  CK(cudaMemcpyAsync(c->h_ranks, c->d_ranks, sizeof(int) * 6, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_ranks, c->d_ranks, sizeof(int) * 7, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(c->h_ranks + 8, c->d_info, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (in.fast_qr && (c->h_ranks[8] != 0 || c->h_ranks[9] != 0))
     return set_error(c, SLAR_ENAN, "Cholesky-QR breakdown in truncation (rank-deficient factor)");
+  if (c->h_ranks[6]) c->rank_capped++;
   int k[6];
   for (int m = 0; m < d; ++m) k[m] = c->h_ranks[m];
   if (d == 2) {

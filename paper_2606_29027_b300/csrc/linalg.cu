@@ -984,7 +984,10 @@ __global__ void k_choose_ranks(RankJob* jobs, int njobs, const double* normF2, d
     if (tail + l <= thr) { tail += l; k = i; } else break;
   }
   if (k < 1) k = 1;
-  if (k > jb.cap) k = jb.cap;
+  if (k > jb.cap) {
+    k = jb.cap;
+    if (jb.capped) atomicOr(jb.capped, 1);
+  }
   jb.out[0] = k;
 }
 

@@ -48,17 +48,21 @@ __global__ void k_mdot_fin(const double* part, int nblk, int ldp, int nv, double
   out[i] = accumulate ? out[i] + s : s;
 }
 
+// max that propagates NaN (fmax drops it): a non-finite residual or state must surface as a
+// NaN norm so that the Newton loop reports SLAR_ENAN instead of converging on the rest
+__device__ __forceinline__ double nan_max(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
+
 __global__ void k_absmax_part(const double* __restrict__ x, int n, double* part) {
   __shared__ double red[8];
   double m = 0.0;
   for (int e = blockIdx.x * RED_SEG + threadIdx.x; e < (blockIdx.x + 1) * RED_SEG && e < n; e += 256)
-    m = fmax(m, fabs(x[e]));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    m = nan_max(m, fabs(x[e]));
+  for (int o = 16; o > 0; o >>= 1) m = nan_max(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < 8; ++w) t = fmax(t, red[w]);
+    for (int w = 0; w < 8; ++w) t = nan_max(t, red[w]);
     part[blockIdx.x] = t;
   }
 }
@@ -66,7 +70,7 @@ __global__ void k_absmax_part(const double* __restrict__ x, int n, double* part)
 __global__ void k_absmax_fin(const double* part, int nblk, double* out) {
   if (threadIdx.x != 0) return;
   double t = 0.0;
-  for (int b = 0; b < nblk; ++b) t = fmax(t, part[b]);
+  for (int b = 0; b < nblk; ++b) t = nan_max(t, part[b]);
   out[0] = t;
 }
 
@@ -851,6 +855,7 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
   st.converged = 1;
   int fslot = -1;
   const long long launches0 = launch_count();
+  const long long capped0 = c->rank_capped;
   c->prof_n = 0;
   c->prof_flop = 0.0;
   c->ph_n = 0;
@@ -870,8 +875,10 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
     CKS(conserved_from_moments(c, c->mom, c->E, c->Uc));
   } else {
     slar_status e0;
-    const double tol_abs = c->cfg.newton_tol * std::max(1.0, host_absmax(c, c->Uc, &e0));
+    const double un_inf = host_absmax(c, c->Uc, &e0);
     CKS(e0);
+    if (!(un_inf == un_inf) || std::isinf(un_inf)) return set_error(c, SLAR_ENAN, "non-finite conserved variables U^n");
+    const double tol_abs = c->cfg.newton_tol * std::max(1.0, un_inf);
     if (c->step < 2) {
       double A[3][3], cst[3];
       dirk3_tableau(A, cst);
@@ -956,9 +963,15 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
   c->prof_n = 0;
   st.launches = launch_count() - launches0;
   st.eval_tile = c->eval_tile;
+  st.rank_capped = (int)(c->rank_capped - capped0);
   c->step += 1;
   if (out) *out = st;
-  return st.converged ? SLAR_OK : set_error(c, SLAR_ENOCONV, "Newton-Krylov did not converge");
+  bool finite = std::isfinite(st.field_energy);
+  for (int k = 0; k < c->dv + 2; ++k) finite = finite && std::isfinite(st.totals[k]);
+  if (!finite) return set_error(c, SLAR_ENAN, "non-finite field energy or totals after the step");
+  if (!st.converged) return set_error(c, SLAR_ENOCONV, "Newton-Krylov did not converge");
+  if (st.rank_capped) return set_error(c, SLAR_ERANK, "rank cap reached with eps unmet (result valid)");
+  return SLAR_OK;
 }
 
 }  // namespace slar

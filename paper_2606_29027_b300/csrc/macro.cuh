@@ -87,5 +87,6 @@ int net_m(const slar_net* n);
 int net_nx(const slar_net* n);
 int net_n0(const slar_net* n);
 int net_n1(const slar_net* n);
+long long net_np(const slar_net* n);
 
 }  // namespace slar

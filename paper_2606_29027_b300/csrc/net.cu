@@ -373,6 +373,7 @@ int net_m(const slar_net* n) { return n->m; }
 int net_nx(const slar_net* n) { return n->NX; }
 int net_n0(const slar_net* n) { return n->n0; }
 int net_n1(const slar_net* n) { return n->n1; }
+long long net_np(const slar_net* n) { return n->np; }
 
 namespace {
 

@@ -29,7 +29,9 @@ EXPORTED = ["slar_create", "slar_destroy", "slar_last_error", "init_ht", "sl_ste
             "slar_net_param_count", "slar_sample_floats", "slar_net_create", "slar_net_destroy",
             "slar_net_set_params", "slar_net_get_params", "slar_net_forward", "slar_net_loss_grad",
             "slar_net_train_step", "slar_attach_net", "slar_set_record", "slar_fma_peak",
-            "slar_ensemble_step", "slar_stream", "slar_wait_probe"]
+            "slar_ensemble_step", "slar_stream", "slar_wait_probe", "slar_checkpoint",
+            "slar_restore"]
+SLAR_MOM_M0, SLAR_MOM_M1, SLAR_MOM_M2, SLAR_MOM_FLUX, SLAR_MOM_ALL = 1, 2, 4, 8, 15
 
 
 class Config(C.Structure):
@@ -47,7 +49,7 @@ class Stats(C.Structure):
                 ("totals", C.c_double * 4), ("eval_ms", C.c_double), ("eval_flop", C.c_double),
                 ("launches", C.c_longlong), ("phase_ms", C.c_double * 6),
                 ("guess_used", C.c_int), ("fallback", C.c_int), ("recorded", C.c_int),
-                ("g_evals", C.c_int), ("eval_tile", C.c_int)]
+                ("g_evals", C.c_int), ("eval_tile", C.c_int), ("rank_capped", C.c_int)]
 
     def to_dict(self):
         return dict(entries=self.entries, ranks=list(self.ranks), aca_rank=list(self.aca_rank[: self.n_slar]),
@@ -56,7 +58,8 @@ class Stats(C.Structure):
                     totals=list(self.totals), eval_ms=self.eval_ms, eval_flop=self.eval_flop,
                     launches=self.launches, phase_ms=list(self.phase_ms),
                     guess_used=bool(self.guess_used), fallback=bool(self.fallback),
-                    recorded=bool(self.recorded), g_evals=self.g_evals, eval_tile=self.eval_tile)
+                    recorded=bool(self.recorded), g_evals=self.g_evals, eval_tile=self.eval_tile,
+                    rank_capped=self.rank_capped)
 
 
 class HTView(C.Structure):
@@ -85,7 +88,7 @@ def load():
         "init_ht": ([P, I, P], I),
         "sl_step": ([P, D, C.POINTER(Stats)], I),
         "ht_truncate": ([P, D, I], I),
-        "moments": ([P, P], I),
+        "moments": ([P, C.c_uint, P], I),
         "lomac_correct": ([P, P], I),
         "poisson_field": ([P, P, P, P, C.POINTER(D)], I),
         "ht_eval": ([P, LL, P, P], I),
@@ -114,6 +117,8 @@ def load():
         "slar_ensemble_step": ([P, I, P, I, P], I),
         "slar_stream": ([P, C.POINTER(P)], I),
         "slar_wait_probe": ([LL, P, P], I),
+        "slar_checkpoint": ([P, C.c_char_p], I),
+        "slar_restore": ([P, C.c_char_p], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -253,7 +258,10 @@ class Context:
             pass
 
     def _check(self, st):
-        if st != SLAR_OK:
+        """Raise on an error status.  SLAR_ERANK is a warning (the call completed and its
+        result is valid): it is kept in self.last_status instead."""
+        self.last_status = st
+        if st not in (SLAR_OK, SLAR_ERANK):
             raise SlarError(st, self.lib.slar_last_error(self.h).decode())
 
     # ---- entry points ----
@@ -267,16 +275,24 @@ class Context:
     def step(self, dt: float) -> Stats:
         st = Stats()
         status = self.lib.sl_step(self.h, dt, C.byref(st))
-        if status not in (SLAR_OK, SLAR_ENOCONV):
+        if status not in (SLAR_OK, SLAR_ENOCONV, SLAR_ERANK):
             self._check(status)
+        self.last_status = status
         st.status = status
         return st
 
     def truncate(self, eps: float, cap: int):
         self._check(self.lib.ht_truncate(self.h, eps, cap))
 
-    def moments(self, out):
-        self._check(self.lib.moments(self.h, C.c_void_p(_ptr(out))))
+    def moments(self, out, mask: int = 0):
+        """Moments selected by `mask` (SLAR_MOM_*; 0 = all) into out [n_sel][NX]."""
+        self._check(self.lib.moments(self.h, int(mask), C.c_void_p(_ptr(out))))
+
+    def checkpoint(self, path: str):
+        self._check(self.lib.slar_checkpoint(self.h, os.fsencode(path)))
+
+    def restore(self, path: str):
+        self._check(self.lib.slar_restore(self.h, os.fsencode(path)))
 
     def lomac_correct(self, U_target):
         self._check(self.lib.lomac_correct(self.h, C.c_void_p(_ptr(U_target))))
@@ -403,7 +419,7 @@ def ensemble_step(contexts, dts, threads: int = 16):
     d = (C.c_double * n)(*[float(x) for x in dts])
     stats = (Stats * n)()
     status = load().slar_ensemble_step(arr, n, d, int(threads), stats)
-    if status not in (SLAR_OK, SLAR_ENOCONV):
+    if status not in (SLAR_OK, SLAR_ENOCONV, SLAR_ERANK):
         raise SlarError(status, "slar_ensemble_step failed")
     return list(stats)
 
