@@ -75,6 +75,8 @@ def parse():
     p.add_argument("--eval-rank", type=int, default=64)
     p.add_argument("--eval-n", type=int, default=128)
     p.add_argument("--eval-entries", type=int, default=65536)
+    p.add_argument("--oracle-timing", action="store_true",
+                   help="time the FP64 oracle (1 BDF3 step after 2 start-up steps) and print it")
     p.add_argument("--profile-step", action="store_true",
                    help="profiling configuration: init, 3 steps, then one BDF3 step with every "
                         "kernel launched individually; prints the launch counts for ncu -s/-c")
@@ -188,6 +190,18 @@ def oracle_steps(w, n_warm, n_timed):
         ent += stepper.sl_step(st, w.dt, g, prm).entries
     dt = time.perf_counter() - t0
     return n_timed / dt, ent / dt, dt
+
+
+def oracle_single_thread(workload):
+    """The same oracle timing in a child process whose BLAS / OpenMP pools have one thread
+    (the variables must be set before numpy loads).  Returns steps/s or None."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-timing", "--workload", workload],
+                           env=env, capture_output=True, text=True, timeout=600)
+        return float(json.loads(r.stdout.strip().splitlines()[-1])["steps_per_s"])
+    except (subprocess.SubprocessError, ValueError, IndexError, KeyError):
+        return None
 
 
 def run_reference(args, w):
@@ -546,12 +560,7 @@ def run_ours(args, w):
     if not args.no_cpu_baseline and world == 1:
         sps, eps_, dt = oracle_steps(w, 2, 1)
         cores = cpu_threads()
-        try:
-            from threadpoolctl import threadpool_limits
-            with threadpool_limits(limits=1):
-                sps1, _, dt1 = oracle_steps(w, 2, 1)
-        except ImportError:
-            sps1, dt1 = None, None
+        sps1 = oracle_single_thread(args.workload)
         line["cpu_baseline"] = {"value": sps, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"1 oracle BDF3 step of {w.name} after 2 untimed DIRK3 "
                                           f"start-up steps ({dt:.1f} s); entries/s {eps_:.3g}",
@@ -649,6 +658,10 @@ def main():
         return
     from paper_2606_29027_b300 import inputs
     w = inputs.workload_by_name(args.workload)
+    if args.oracle_timing:
+        sps, eps_, dt = oracle_steps(w, 2, 1)
+        print(json.dumps({"steps_per_s": sps, "entries_per_s": eps_, "seconds": dt}), flush=True)
+        return
     if args.profile_step:
         profile_step(args, w)
         return

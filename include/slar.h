@@ -244,9 +244,10 @@ slar_status ht_import(slar_ctx* ctx, const slar_ht_view* view);
  * FP64 HT factors of F^n and its LoMaC correction, U^n, U^{n-1}, U^{n-2}, the ion density,
  * the step counter (which selects DIRK3 start-up or BDF3), the FP64 eigenbases that the next
  * truncation starts its Jacobi sweeps from, and the parameters of the attached network (if
- * any).  slar_restore loads it into a context created with the same grid, box and precision
- * (else SLAR_EINVAL); the network parameters are loaded only if a network of the same size
- * is attached.  A restored FP64 run continues bit for bit like the run that wrote the file
+ * any).  slar_restore loads it into a context created with the same grid and box (else
+ * SLAR_EINVAL); the state is FP64 in every precision, so the run may resume in another entry
+ * precision.  The network parameters are loaded only if a network of the same size is
+ * attached.  A restored FP64 run continues bit for bit like the run that wrote the file
  * (same process: the autotuned evaluator tile is kept per process).  Both calls synchronise
  * the context stream.  Errors: SLAR_EINVAL (no state, file cannot be opened / read /
  * written, wrong magic or version, mismatch), SLAR_ECUDA. */

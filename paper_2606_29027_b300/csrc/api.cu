@@ -730,10 +730,12 @@ slar_status slar_restore(slar_ctx* c, const char* path) {
   CkptHeader hd{};
   if (!rd(F.f, &hd, sizeof(hd)) || std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != kCkptVersion)
     return set_error(c, SLAR_EINVAL, "restore: not a checkpoint of this library version");
-  bool same = hd.d == c->d && hd.dx == c->dx && hd.dv == c->dv && hd.precision == c->cfg.precision;
+  // the saved state is FP64 whatever the writer's entry precision, so a run may resume in
+  // another precision; the grid and the box must be the same
+  bool same = hd.d == c->d && hd.dx == c->dx && hd.dv == c->dv;
   for (int m = 0; m < 4; ++m)
     same = same && hd.N[m] == c->cfg.N[m] && hd.lo[m] == c->cfg.lo[m] && hd.hi[m] == c->cfg.hi[m];
-  if (!same) return set_error(c, SLAR_EINVAL, "restore: grid, box or precision differ from the context's");
+  if (!same) return set_error(c, SLAR_EINVAL, "restore: grid or box differ from the context's");
   for (int i = 0; i < (c->d == 4 ? 6 : 2); ++i)
     if (hd.rank[i] < 1 || hd.rank[i] > SLAR_MAX_RANK) return set_error(c, SLAR_EINVAL, "restore: bad rank");
   for (int t = 0; t < 6; ++t)

@@ -201,10 +201,10 @@ __device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& 
 
 
 // ---- FP32 variants (FP32 / BF16x3 entry paths): the same formulas in single precision.
-// Their feet can differ from the FP64 ones by ~1e-7 relative, which moves an entry to the
-// neighbouring stencil only when its foot lies within that distance of a cell face (the two
-// stencils then differ by O(Delta^3)); the entries are only required to agree with FP64 to
-// the FP32 tolerance.
+// Their feet can differ from the FP64 ones by ~1e-7 relative.  Where that could move an
+// entry to the neighbouring stencil -- its FP32 foot lies within kFaceGuard cells of a cell
+// face, and the two quadratic stencils there differ by Delta^3 f''' / 8 -- the foot is traced
+// again in FP64 (foot_cells_ft), so both paths interpolate from the same cells.
 
 __device__ __forceinline__ void cell_weights_f(const GridDesc& g, int m, float y, int rows[3], float w[3]) {
   float t = (y - g.lof[m]) / g.hf[m];
@@ -301,6 +301,44 @@ __device__ __forceinline__ void trace_foot_f(const GridDesc& g, const float* E, 
   else trace_foot_ft<1>(g, E, tau_d, euler, idx, foot);
 }
 
+// Distance (in cells) from a cell face below which an FP32 foot is traced again in FP64.
+// The FP32 foot's error is a few ulps of its cell coordinate t = (y - lo) / Delta (|t| of a
+// few hundred at most), i.e. below 1e-4 cells; 1/2048 leaves a factor of four.
+constexpr float kFaceGuard = 1.0f / 2048.0f;
+
+// Foot, cells and weights of one entry in the FP32 paths (2 DX dimensions): the FP32 foot,
+// unless it lies within kFaceGuard of a cell face in some dimension, in which case the entry
+// takes the FP64 foot (E64 given) with the FP64 path's cells and weights (rounded to FP32).
+// rows / w: [2 DX][3].
+template <int DX>
+__device__ __forceinline__ void foot_cells_ft(const GridDesc& g, const float* E32, const double* E64, double tau,
+                                              int euler, const int* idx, float* foot, int* rows, float* w) {
+  constexpr int D = 2 * DX;
+  trace_foot_ft<DX>(g, E32, tau, euler, idx, foot);
+  bool near = false;
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    const float t = (foot[m] - g.lof[m]) / g.hf[m];
+    const float fr = t - floorf(t);
+    near |= !(fr >= kFaceGuard && fr <= 1.f - kFaceGuard);   // also catches a non-finite t
+  }
+  if (near && E64) {
+    double fd[4];
+    trace_foot(g, E64, tau, euler, idx, fd);
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      double wd[3];
+      cell_weights(g, m, fd[m], rows + 3 * m, wd);
+#pragma unroll
+      for (int s = 0; s < 3; ++s) w[3 * m + s] = (float)wd[s];
+      foot[m] = (float)fd[m];
+    }
+    return;
+  }
+#pragma unroll
+  for (int m = 0; m < D; ++m) cell_weights_f(g, m, foot[m], rows + 3 * m, w + 3 * m);
+}
+
 __device__ __forceinline__ float interp_1d_f(const GridDesc& g, int m, const float* vec, float y) {
   int r[3];
   float w[3];
@@ -368,6 +406,67 @@ __device__ __forceinline__ float correction_at_ft(const GridDesc& g, const CorrV
 // separable LoMaC correction at a foot, FP32 (dv = dx)
 __device__ __forceinline__ float correction_at_f(const GridDesc& g, const CorrView& c, const float* foot) {
   return g.dx == 2 ? correction_at_ft<2>(g, c, foot) : correction_at_ft<1>(g, c, foot);
+}
+
+// The same correction from the entry's cells and weights (rows / w: [2 DX][3]), so that it
+// interpolates from the cells the HT part used (foot_cells_ft).
+template <int DX>
+__device__ __forceinline__ float correction_rw_ft(const GridDesc& g, const CorrView& c, const int* rows,
+                                                  const float* w) {
+  constexpr int DV = DX;
+  const long long NX = g.NX;
+  const int Nv = g.N[DX];
+  float dCi[DV + 2];
+  const int* r0 = rows;
+  const float* w0 = w;
+  const int* r1 = rows + 3;
+  const float* w1 = w + 3;
+#pragma unroll
+  for (int k = 0; k < DV + 2; ++k) {
+    const float* F = c.dC32 + k * NX;
+    float acc = 0.f;
+    if constexpr (DX == 1) {
+#pragma unroll
+      for (int s0 = 0; s0 < 3; ++s0) acc += w0[s0] * F[r0[s0]];
+    } else {
+#pragma unroll
+      for (int s0 = 0; s0 < 3; ++s0)
+#pragma unroll
+        for (int s1 = 0; s1 < 3; ++s1) acc += w0[s0] * w1[s1] * F[(long long)r0[s0] * g.N[1] + r1[s1]];
+    }
+    dCi[k] = acc;
+  }
+  float om[DV], q1[DV], q2[DV];
+#pragma unroll
+  for (int m = 0; m < DV; ++m) {
+    const int* rv = rows + 3 * (DX + m);
+    const float* wv = w + 3 * (DX + m);
+    const float* vo = c.qv32 + (0 * DV + m) * Nv;
+    const float* v1 = c.qv32 + (1 * DV + m) * Nv;
+    const float* v2 = c.qv32 + (2 * DV + m) * Nv;
+    om[m] = wv[0] * vo[rv[0]] + wv[1] * vo[rv[1]] + wv[2] * vo[rv[2]];
+    q1[m] = wv[0] * v1[rv[0]] + wv[1] * v1[rv[1]] + wv[2] * v1[rv[2]];
+    q2[m] = wv[0] * v2[rv[0]] + wv[1] * v2[rv[1]] + wv[2] * v2[rv[2]];
+  }
+  float out = 0.f, t = dCi[0];
+#pragma unroll
+  for (int m = 0; m < DV; ++m) t *= om[m];
+  out += t;
+#pragma unroll
+  for (int j = 0; j < DV; ++j) {
+    t = dCi[1 + j];
+#pragma unroll
+    for (int m = 0; m < DV; ++m) t *= (m == j ? q1[m] : om[m]);
+    out += t;
+  }
+#pragma unroll
+  for (int j = 0; j < DV; ++j) {
+    t = dCi[1 + DV];
+#pragma unroll
+    for (int m = 0; m < DV; ++m) t *= (m == j ? q2[m] : om[m]);
+    out += t;
+  }
+  return out;
 }
 
 }  // namespace

@@ -370,28 +370,28 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
     if (tid < nT) {
       int idx[4];
       decode_tuple(g, a, e0 + tid, idx);
-      float foot[4];
+      float foot[4] = {0.f, 0.f, 0.f, 0.f};
+      int r[12];
+      float w[12];
       if (at_grid) {
 #pragma unroll
         for (int m = 0; m < 4; ++m)
-          if (m < d) foot[m] = centre_f(g, m, idx[m]);
+          if (m < d) {
+            foot[m] = centre_f(g, m, idx[m]);
+            r[3 * m] = r[3 * m + 1] = r[3 * m + 2] = idx[m];
+            w[3 * m] = 0.f; w[3 * m + 1] = 1.f; w[3 * m + 2] = 0.f;
+          }
+      } else if (g.dx == 2) {
+        foot_cells_ft<2>(g, a.E32, a.E, a.tau, a.foot_euler, idx, foot, r, w);
       } else {
-        trace_foot_f(g, a.E32, a.tau, a.foot_euler, idx, foot);
+        foot_cells_ft<1>(g, a.E32, a.E, a.tau, a.foot_euler, idx, foot, r, w);
       }
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         if (m >= d) break;
-        int r[3];
-        float w[3];
-        if (at_grid) {
-          r[0] = idx[m]; r[1] = idx[m]; r[2] = idx[m];
-          w[0] = 0.f; w[1] = 1.f; w[2] = 0.f;
-        } else {
-          cell_weights_f(g, m, foot[m], r, w);
-        }
         for (int s = 0; s < 3; ++s) {
-          srow[(tid * 4 + m) * 3 + s] = r[s];
-          swT[(tid * 4 + m) * 3 + s] = w[s];
+          srow[(tid * 4 + m) * 3 + s] = r[3 * m + s];
+          swT[(tid * 4 + m) * 3 + s] = w[3 * m + s];
         }
         sfootT[tid * 4 + m] = foot[m];
       }
@@ -488,10 +488,10 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
     double val = sval[tid];
     if (corr.has) {
       if constexpr (sizeof(T) == 4) {
-        float f4[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) f4[m] = (float)sfootT[tid * 4 + m];
-        val += (double)correction_at_f(g, corr, f4);
+        // from the cells the HT part used (foot_cells_ft)
+        const int* rr = srow + tid * 12;
+        const float* ww = reinterpret_cast<const float*>(swT) + tid * 12;
+        val += (double)(d == 4 ? correction_rw_ft<2>(g, corr, rr, ww) : correction_rw_ft<1>(g, corr, rr, ww));
       } else {
         val += correction_at(g, corr, sfoot + tid * 4);
       }

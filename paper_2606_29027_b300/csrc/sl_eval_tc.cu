@@ -412,16 +412,15 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     int idx[4];
     decode_tuple(g, a, e0 + tid, idx);
     float foot[4];
-    trace_foot_ft<2>(g, a.E32, a.tau, a.foot_euler, idx, foot);   // d = 4: two spatial dimensions
+    int r[12];
+    float w[12];
+    foot_cells_ft<2>(g, a.E32, a.E, a.tau, a.foot_euler, idx, foot, r, w);   // d = 4: two spatial dimensions
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      int r[3];
-      float w[3];
-      cell_weights_f(g, m, foot[m], r, w);
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
-        srow[(tid * 4 + m) * 3 + s] = r[s];
-        sw[(tid * 4 + m) * 3 + s] = w[s];
+        srow[(tid * 4 + m) * 3 + s] = r[3 * m + s];
+        sw[(tid * 4 + m) * 3 + s] = w[3 * m + s];
       }
       sfoot[tid * 4 + m] = foot[m];
     }
@@ -594,12 +593,7 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     // 5. correction and residual epilogue
     if (tid < nT) {
       double val = sval[tid];
-      if (corr.has) {
-        float f4[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) f4[m] = sfoot[tid * 4 + m];
-        val += (double)correction_at_ft<2>(g, corr, f4);
-      }
+      if (corr.has) val += (double)correction_rw_ft<2>(g, corr, srow + tid * 12, sw + tid * 12);
       const long long e = e0 + tid;
       if (a.X) {
         const long long piv = (long long)(*a.pivot);
