@@ -275,12 +275,25 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
   if (d == 4) { node_n[4] = in.r[4]; node_n[5] = in.r[5]; }
   const int nnodes = d == 4 ? 6 : 2;
   bool warm[6] = {false, false, false, false, false, false};
+  // Gram matrices above order 24 are compressed before the eigen-solve (k_jacobi: pivoted
+  // Cholesky down to the numerical range, Jacobi of that order, hand-over to the
+  // tridiagonal solver above rank 40).  FP32 / BF16x3 data: the dropped trace is 1/10 of the
+  // rank threshold.  FP64 data: 1e-16 of the trace, the rounding level of a Gram matrix --
+  // the eigenvalues dropped there are the ones a dense solver (LAPACK's, the oracle's) also
+  // resolves only to about u ||G||, and the kept eigenvectors move by ~u ||G|| / gap, far
+  // below the FP64 parity bar at any rank threshold eps^2 / (2d - 3) >= 1e-14.
+  const double thr_rel = eps * eps / (2.0 * d - 3.0);
+  const bool fp64 = c->cfg.precision == SLAR_FP64;
+  auto compress_rel_of = [&](int n) {
+    if (n <= 24) return 0.0;
+    if (fp64) return thr_rel >= 1e-14 ? 1e-16 : 0.0;
+    return std::max(1e-16, 0.1 * thr_rel);
+  };
   for (int m = 0; m < d; ++m) {
     const int nm = node_n[m];
-    // (no warm start with the compressed eigen-solve of FP32 / BF16x3 data: its basis holds
-    // only the numerical range, and rotating the next Gram matrix into it would lose every
-    // new direction)
-    if (nm < 16 || c->Sn[m] != nm || c->cfg.precision != SLAR_FP64) continue;
+    // (no warm start with the compressed eigen-solve: its basis holds only the numerical
+    // range, and rotating the next Gram matrix into it would lose every new direction)
+    if (nm < 16 || c->Sn[m] != nm || compress_rel_of(nm) > 0.0) continue;
     double* T = c->Sw + (size_t)m * SLAR_MAX_N * SLAR_MAX_N;
     CK(dgemm(0, 0, nm, nm, nm, 1.0, c->G[m], nm, 0, c->S[m], nm, 0, 0.0, T, nm, 0, 1, s));
     CK(dgemm(1, 0, nm, nm, nm, 1.0, c->S[m], nm, 0, T, nm, 0, 0.0, c->G[m], nm, 0, 1, s));
@@ -301,13 +314,11 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
     // and never below the FP64 rounding level
     const double noise = c->cfg.precision == SLAR_FP64 ? 1e-17 : (c->cfg.precision == SLAR_FP32 ? 1e-13 : 1e-9);
     jobs[nj].floor_rel = std::max(1e-17, std::min(noise, 1e-2 * eps * eps / (2.0 * d - 3.0)));
-    // FP32 / BF16x3 data: eigen-solve only the numerical range of the Gram matrix -- a
-    // pivoted Cholesky G ~ L L^T stopped when the trace left out is below 1/10 of the rank
-    // threshold eps^2/(2d-3) (relative to trace G = ||F||^2), then Jacobi on L^T L
-    jobs[nj].compress_rel = c->cfg.precision == SLAR_FP64 ? 0.0 : std::max(1e-16, 0.1 * eps * eps / (2.0 * d - 3.0));
-    // the truncation reads at most cap leading eigenvectors of each node; FP32 / BF16x3 data
-    // of numerical rank above 40 is solved by the tridiagonal path (FP64 data keeps the
-    // relative-accuracy Jacobi)
+    // eigen-solve only the numerical range of the Gram matrix: a pivoted Cholesky G ~ L L^T
+    // stopped when the trace left out is below compress_rel trace G, then Jacobi on L^T L
+    jobs[nj].compress_rel = compress_rel_of(node_n[t]);
+    // the truncation reads at most cap leading eigenvectors of each node; a compressed
+    // numerical rank above 40 goes to the tridiagonal path
     jobs[nj].nvec = std::min(node_n[t], cap);
     jobs[nj].tri = (jobs[nj].compress_rel > 0.0 && node_n[t] > 40) ? 1 : 0;
     ++nj;
@@ -322,7 +333,7 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
       CK(cudaMemcpyAsync(c->S[m], c->ework[m], sizeof(double) * nm * nm, cudaMemcpyDeviceToDevice, s));
     }
   }
-  for (int t = 0; t < nnodes; ++t) c->Sn[t] = c->cfg.precision == SLAR_FP64 ? node_n[t] : 0;
+  for (int t = 0; t < nnodes; ++t) c->Sn[t] = compress_rel_of(node_n[t]) > 0.0 ? 0 : node_n[t];
   // 3. ranks
   slar::count_launch(), k_trace<<<1, 32, 0, s>>>(c->G[d == 4 ? 4 : 0], node_n[d == 4 ? 4 : 0], c->norm2);
   CK(cudaGetLastError());
