@@ -58,6 +58,36 @@ def dirk3_tableau():
 
 BDF3 = dict(a=(18.0 / 11.0, -9.0 / 11.0, 2.0 / 11.0), beta=6.0 / 11.0)
 
+# Upper bound on the ratio h_n / h_{n-1} of adjacent steps under which variable-step BDF3 is
+# stable (Sec. 3.2.3 defers to the step-ratio analysis of Li and Liao for it; the paper does
+# not print the value).  Reading: 1.4877, the bound that analysis states for BDF3.
+BDF3_RATIO_MAX = 1.4877
+
+
+def bdf3_variable(h):
+    """Variable-step BDF3 (Gear 1971; Sec. 3.2.3): the cubic through (t_{n+1}, U^{n+1}),
+    (t_n, U^n), (t_{n-1}, U^{n-1}), (t_{n-2}, U^{n-2}) is differentiated at t_{n+1} and set equal
+    to K(U^{n+1}).  h = (h_n, h_{n-1}, h_{n-2}), the current step first.  Returns (a, beta) with
+        U^{n+1} - beta h_n K(U^{n+1}) = a[0] U^n + a[1] U^{n-1} + a[2] U^{n-2}.
+    Equal steps give the fixed-step BDF3 table."""
+    hn, h1, h2 = (float(x) for x in h)
+    t = [0.0, -hn, -hn - h1, -hn - h1 - h2]          # t_{n+1} = 0, then t_n, t_{n-1}, t_{n-2}
+    dl = []                                           # Lagrange basis derivatives at t_{n+1}
+    for j in range(4):
+        if j == 0:
+            dl.append(sum(1.0 / (t[0] - t[m]) for m in range(1, 4)))
+            continue
+        num = 1.0
+        den = 1.0
+        for m in range(4):
+            if m != j:
+                den *= t[j] - t[m]
+                if m != 0:
+                    num *= t[0] - t[m]
+        dl.append(num / den)
+    beta = 1.0 / (dl[0] * hn)
+    return tuple(-dl[j] / dl[0] for j in (1, 2, 3)), beta
+
 
 @dataclass
 class Closure:

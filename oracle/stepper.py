@@ -59,6 +59,7 @@ class State:
     U: np.ndarray                      # conserved variables (dv+2, Nx)
     hist: List[np.ndarray]             # previous U (most recent first), for BDF3
     n_i: float
+    dts: List[float] = dfield(default_factory=list)   # previous step sizes, most recent first
     t: float = 0.0
     step: int = 0
 
@@ -221,11 +222,12 @@ def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None,
         stats.aca_ranks = info["aca_ranks"]
         stats.pivots = info["pivots"]
         cl = macro.make_closure(Fs, g, st.n_i, prm.delta)
-        a = macro.BDF3["a"]
+        # variable-step BDF3 (equal steps: the fixed-step table)
+        a, beta = macro.bdf3_variable((dt, st.dts[0], st.dts[1]))
         rhs = a[0] * st.U + a[1] * st.hist[0] + a[2] * st.hist[1]
         tol_abs = macro.newton_tol_abs(prm.newton_tol, st.U)
         Ustar = lomac.conserved_from_moments(cl.mom_star, g, st.n_i)
-        coef = macro.BDF3["beta"] * dt
+        coef = beta * dt
         Gfun = lambda U: U - rhs - coef * macro.K_operator(U, cl)
         if prm.precond == "none":
             Un, ns = _solve(cl, rhs, coef, Ustar, tol_abs, prm)
@@ -240,8 +242,26 @@ def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None,
         st.F = lomac.correct(Fs, cl.basis, Un, g, st.n_i)
     st.t += dt
     st.step += 1
+    st.dts = [dt] + st.dts[:1]
     stats.W = field.poisson_field(st.n_i - st.U[0], g)[2]
     return stats
+
+
+def cfl_dt(st: State, g: PhaseGrid, cfl: float, dt_max: float,
+           ratio_max: float = macro.BDF3_RATIO_MAX) -> float:
+    """Adaptive step size (Sec. 3.2.3 adaptive time stepping; the dimension-wise CFL numbers
+    lambda_i = a_i dt / Delta_i of Appendix A): dt = cfl / max_i(a_i / Delta_i) with the
+    advection speeds a = max |v_m| in x_m and max |E_m| of the state's field in v_m, capped
+    at dt_max and, after the start-up steps, at ratio_max times the previous step."""
+    E = field_of(st.F, g, st.n_i)
+    rate = 0.0
+    for m in range(g.dx):
+        vmax = float(np.max(np.abs(g.centres(g.dx + m))))
+        rate = max(rate, vmax / g.h(m), float(np.max(np.abs(E[m]))) / g.h(g.dx + m))
+    dt = dt_max if rate == 0.0 else min(dt_max, cfl / rate)
+    if st.step >= 2 and st.dts:
+        dt = min(dt, ratio_max * st.dts[0])
+    return dt
 
 
 def totals(st: State, g: PhaseGrid):
