@@ -172,14 +172,26 @@ slar_status init_ht(slar_ctx* ctx, int n_terms, const double* factors);
  * RK exponential integrator (Eq. slarvp; three frozen-field SLAR calls), then, with
  * SLAR_LOMAC, the moments of F*, the adaptive weight and basis (Supp. B), the JFNK solve
  * of the macroscopic system (DIRK3 for the first two steps, BDF3 after) and the update
- * F^{n+1} = F* - R(U(F*)) + R(U^{n+1}).  `stats` (host, may be NULL) receives the
- * step diagnostics.  Errors: SLAR_EINVAL (no state), SLAR_ENAN (U^n, the Newton residual,
+ * F^{n+1} = F* - R(U(F*)) + R(U^{n+1}).  Steps may vary: BDF3 takes the variable-step
+ * coefficients of the last three step sizes (Gear; equal steps give 18/11, -9/11, 2/11 and
+ * 6/11), and a step longer than 1.4877 times the previous one is rejected after the start-up
+ * (see slar_cfl_dt).  `stats` (host, may be NULL) receives the step diagnostics.
+ * Errors: SLAR_EINVAL (no state, dt <= 0, step ratio above the bound), SLAR_ENAN (U^n, the Newton residual,
  * the field energy or the totals are not finite; checked before the solve and after the
  * step), SLAR_ENOCONV (Newton or GMRES did not converge within newton_max / krylov_max;
  * with SLAR_PRECOND / SLAR_LEARNED the failed solve was first repeated by plain JFNK,
  * stats.fallback = 1; the state is advanced with the last iterate), SLAR_ERANK (warning,
  * see above; the state is advanced).  SLAR_ENOCONV takes precedence over SLAR_ERANK. */
 slar_status sl_step(slar_ctx* ctx, double dt, slar_stats* stats);
+
+/* Adaptive step size for the next sl_step (Sec. 3.2.3: variable-step BDF3 for adaptive time
+ * stepping; CFL numbers lambda_i = a_i dt / Delta_i per dimension as in Appendix A):
+ *   dt = cfl / max_i(a_i / Delta_i),   a = max |v_m| in x_m, max |E_m| of the state's field in v_m,
+ * capped at dt_max and, after the two DIRK3 start-up steps, at 1.4877 times the previous step
+ * (the step-ratio bound under which variable-step BDF3 is stable, after the analysis of Li and
+ * Liao that Sec. 3.2.3 cites).  dt: host output.  Synchronises the stream.
+ * Errors: SLAR_EINVAL (no state, cfl or dt_max not > 0), SLAR_ENAN (non-finite field). */
+slar_status slar_cfl_dt(slar_ctx* ctx, double cfl, double dt_max, double* dt);
 
 /* HSVD truncation of the HT part of the state (Supp. B.1): orthogonalise, node Gram
  * matrices from the root down, eigendecomposition, keep per node the smallest rank with
@@ -242,7 +254,8 @@ slar_status ht_import(slar_ctx* ctx, const slar_ht_view* view);
 /* Checkpoint and restore of a run (Sec. 3.2.3: everything the next step reads).  The file
  * (host byte order, written by slar_checkpoint at `path`, overwritten if present) holds the
  * FP64 HT factors of F^n and its LoMaC correction, U^n, U^{n-1}, U^{n-2}, the ion density,
- * the step counter (which selects DIRK3 start-up or BDF3), the FP64 eigenbases that the next
+ * the step counter (which selects DIRK3 start-up or BDF3), the sizes of the previous two
+ * steps (variable-step BDF3), the FP64 eigenbases that the next
  * truncation starts its Jacobi sweeps from, and the parameters of the attached network (if
  * any).  slar_restore loads it into a context created with the same grid and box (else
  * SLAR_EINVAL); the state is FP64 in every precision, so the run may resume in another entry

@@ -387,6 +387,7 @@ slar_status init_ht(slar_ctx* c, int n_terms, const double* factors) {
   c->cur = dst;
   c->has_corr = 0;
   c->step = 0;
+  c->dt_hist[0] = c->dt_hist[1] = 0.0;
   CKS(conserved_of_state(c, true));
   c->has_U = true;
   CK(cudaStreamSynchronize(c->s));
@@ -633,7 +634,7 @@ slar_status slar_ensemble_step(slar_ctx** ctxs, int n, const double* dts, int th
 namespace {
 
 constexpr char kCkptMagic[8] = {'S', 'L', 'A', 'R', 'C', 'K', 'P', 'T'};
-constexpr int kCkptVersion = 1;
+constexpr int kCkptVersion = 2;
 
 // Fixed-size header of a checkpoint file (host byte order); the arrays follow in the order
 // written by slar_checkpoint.
@@ -649,6 +650,7 @@ struct CkptHeader {
   int Sn[6];
   double n_i;
   long long net_np;   // parameters of the attached network saved (0: none)
+  double dt_hist[2];  // sizes of the previous two steps (variable-step BDF3)
 };
 
 struct File {
@@ -691,6 +693,8 @@ slar_status slar_checkpoint(slar_ctx* c, const char* path) {
   for (int i = 0; i < 6; ++i) { hd.rank[i] = h.r[i]; hd.Sn[i] = c->Sn[i]; }
   hd.n_i = c->n_i;
   hd.net_np = c->net ? net_np(c->net) : 0;
+  hd.dt_hist[0] = c->dt_hist[0];
+  hd.dt_hist[1] = c->dt_hist[1];
   File F;
   F.f = fopen(path, "wb");
   if (!F.f) return set_error(c, SLAR_EINVAL, "checkpoint: cannot open the file for writing");
@@ -740,7 +744,8 @@ slar_status slar_restore(slar_ctx* c, const char* path) {
     if (hd.rank[i] < 1 || hd.rank[i] > SLAR_MAX_RANK) return set_error(c, SLAR_EINVAL, "restore: bad rank");
   for (int t = 0; t < 6; ++t)
     if (hd.Sn[t] < 0 || hd.Sn[t] > SLAR_MAX_N) return set_error(c, SLAR_EINVAL, "restore: bad basis order");
-  if (hd.step < 0 || hd.has_U != 1 || (hd.has_corr != 0 && hd.has_corr != 1) || hd.net_np < 0)
+  if (hd.step < 0 || hd.has_U != 1 || (hd.has_corr != 0 && hd.has_corr != 1) || hd.net_np < 0 ||
+      !(hd.dt_hist[0] >= 0.0) || !(hd.dt_hist[1] >= 0.0) || (hd.step >= 2 && !(hd.dt_hist[1] > 0.0)))
     return set_error(c, SLAR_EINVAL, "restore: bad header");
   CK(cudaStreamSynchronize(c->s));
   const int dst = spare_slot(c, c->cur);
@@ -778,6 +783,8 @@ slar_status slar_restore(slar_ctx* c, const char* path) {
   c->has_U = true;
   c->n_i = hd.n_i;
   c->step = hd.step;
+  c->dt_hist[0] = hd.dt_hist[0];
+  c->dt_hist[1] = hd.dt_hist[1];
   for (int t = 0; t < 6; ++t) c->Sn[t] = hd.Sn[t];
   return SLAR_OK;
 }
@@ -794,7 +801,15 @@ slar_status sl_step(slar_ctx* c, double dt, slar_stats* stats) {
     return set_error(c, SLAR_EINVAL, "SLAR_LEARNED needs a network (slar_attach_net)");
   if (!c->ht[c->cur].valid || !c->has_U) return set_error(c, SLAR_EINVAL, "call init_ht first");
   if (!(dt > 0.0)) return set_error(c, SLAR_EINVAL, "dt must be > 0");
+  if ((c->cfg.flags & SLAR_LOMAC) && c->step >= 2 && dt > kBdf3RatioMax * c->dt_hist[0] * (1.0 + 1e-12))
+    return set_error(c, SLAR_EINVAL, "step ratio above the variable-step BDF3 stability bound");
   return step_impl(c, dt, stats);
+}
+
+slar_status slar_cfl_dt(slar_ctx* c, double cfl, double dt_max, double* dt) {
+  if (!c || !dt || !(cfl > 0.0) || !(dt_max > 0.0)) return SLAR_EINVAL;
+  if (!c->ht[c->cur].valid || !c->has_U) return set_error(c, SLAR_EINVAL, "call init_ht first");
+  return cfl_dt(c, cfl, dt_max, dt);
 }
 
 }  // extern "C"

@@ -85,6 +85,7 @@ struct slar_ctx {
   double n_i = 1.0;
   int step = 0;
   bool has_U = false;
+  double dt_hist[2] = {0.0, 0.0};   // sizes of the previous two steps (most recent first)
 
   // cross approximation
   double* Ua = nullptr;   // M1 x kmax column-major
@@ -242,6 +243,13 @@ slar_status conserved_from_moments(slar_ctx* c, const double* mom, const double*
 slar_status macro_alloc(slar_ctx* c);
 void macro_free(slar_ctx* c);
 slar_status step_impl(slar_ctx* c, double dt, slar_stats* st);
+// variable-step BDF3 coefficients (a[3], beta) for the steps (h_n, h_{n-1}, h_{n-2})
+void bdf3_variable(const double h[3], double a[3], double* beta);
+// the largest ratio h_n / h_{n-1} admitted for variable-step BDF3
+constexpr double kBdf3RatioMax = 1.4877;
+// adaptive step size: cfl / max_i(a_i / Delta_i), capped at dt_max and, after the start-up,
+// at kBdf3RatioMax times the previous step (field of the current state)
+slar_status cfl_dt(slar_ctx* c, double cfl, double dt_max, double* dt);
 
 }  // namespace slar
 

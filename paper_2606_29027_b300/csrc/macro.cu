@@ -847,6 +847,28 @@ slar_status solve_bdf(slar_ctx* c, double coef, double tol_abs, slar_stats* st) 
 
 }  // namespace
 
+// Differentiate the cubic through (t_{n+1}, U^{n+1}) and the three previous states at t_{n+1}
+// (Gear's variable-step BDF3): with t_{n+1} = 0 the nodes are 0, -h_n, -h_n - h_{n-1},
+// -h_n - h_{n-1} - h_{n-2}; the Lagrange basis derivatives l_j'(0) give
+// U^{n+1} - beta h_n K = sum_j a_j U^{n-j}, a_j = -l_{j+1}'(0) / l_0'(0), beta = 1 / (l_0'(0) h_n).
+void bdf3_variable(const double h[3], double a[3], double* beta) {
+  const double t[4] = {0.0, -h[0], -h[0] - h[1], -h[0] - h[1] - h[2]};
+  double dl[4];
+  dl[0] = 0.0;
+  for (int m = 1; m < 4; ++m) dl[0] += 1.0 / (t[0] - t[m]);
+  for (int j = 1; j < 4; ++j) {
+    double num = 1.0, den = 1.0;
+    for (int m = 0; m < 4; ++m) {
+      if (m == j) continue;
+      den *= t[j] - t[m];
+      if (m != 0) num *= t[0] - t[m];
+    }
+    dl[j] = num / den;
+  }
+  for (int j = 0; j < 3; ++j) a[j] = -dl[j + 1] / dl[0];
+  *beta = 1.0 / (dl[0] * h[0]);
+}
+
 slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
   MacroWS* w = c->mw;
   cudaStream_t s = c->s;
@@ -911,11 +933,14 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
       for (int i = 0; i < 3; ++i) st.aca_rank[i] = vi.aca[i];
       st.n_slar = 3;
       CKS(make_closure(c, fslot));
-      // BDF3: U - (18 U^n - 9 U^{n-1} + 2 U^{n-2}) / 11 - (6/11) dt K(U) = 0
-      slar::count_launch(), k_lincomb3<<<nb(n), 256, 0, s>>>(w->rhs, c->Uc, 18.0 / 11.0, c->Uh1, -9.0 / 11.0, c->Uh2,
-                                       2.0 / 11.0, n);
+      // variable-step BDF3: U - (a0 U^n + a1 U^{n-1} + a2 U^{n-2}) - beta dt K(U) = 0 (equal
+      // steps: 18/11, -9/11, 2/11 and 6/11)
+      const double hh[3] = {dt, c->dt_hist[0], c->dt_hist[1]};
+      double ab[3], beta;
+      bdf3_variable(hh, ab, &beta);
+      slar::count_launch(), k_lincomb3<<<nb(n), 256, 0, s>>>(w->rhs, c->Uc, ab[0], c->Uh1, ab[1], c->Uh2, ab[2], n);
       CK(cudaGetLastError());
-      const double coef = 6.0 / 11.0 * dt;
+      const double coef = beta * dt;
       CKS(solve_bdf(c, coef, tol_abs, &st));
       if (c->rec_dst) {
         CKS(record_sample(c));
@@ -965,6 +990,8 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
   st.eval_tile = c->eval_tile;
   st.rank_capped = (int)(c->rank_capped - capped0);
   c->step += 1;
+  c->dt_hist[1] = c->dt_hist[0];
+  c->dt_hist[0] = dt;
   if (out) *out = st;
   bool finite = std::isfinite(st.field_energy);
   for (int k = 0; k < c->dv + 2; ++k) finite = finite && std::isfinite(st.totals[k]);

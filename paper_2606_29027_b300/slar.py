@@ -30,7 +30,7 @@ EXPORTED = ["slar_create", "slar_destroy", "slar_last_error", "init_ht", "sl_ste
             "slar_net_set_params", "slar_net_get_params", "slar_net_forward", "slar_net_loss_grad",
             "slar_net_train_step", "slar_attach_net", "slar_set_record", "slar_fma_peak",
             "slar_ensemble_step", "slar_stream", "slar_wait_probe", "slar_checkpoint",
-            "slar_restore"]
+            "slar_restore", "slar_cfl_dt"]
 SLAR_MOM_M0, SLAR_MOM_M1, SLAR_MOM_M2, SLAR_MOM_FLUX, SLAR_MOM_ALL = 1, 2, 4, 8, 15
 
 
@@ -119,6 +119,7 @@ def load():
         "slar_wait_probe": ([LL, P, P], I),
         "slar_checkpoint": ([P, C.c_char_p], I),
         "slar_restore": ([P, C.c_char_p], I),
+        "slar_cfl_dt": ([P, D, D, C.POINTER(D)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -293,6 +294,12 @@ class Context:
 
     def restore(self, path: str):
         self._check(self.lib.slar_restore(self.h, os.fsencode(path)))
+
+    def cfl_dt(self, cfl: float, dt_max: float) -> float:
+        """Step size of the adaptive rule (see include/slar.h, slar_cfl_dt)."""
+        dt = C.c_double()
+        self._check(self.lib.slar_cfl_dt(self.h, float(cfl), float(dt_max), C.byref(dt)))
+        return dt.value
 
     def lomac_correct(self, U_target):
         self._check(self.lib.lomac_correct(self.h, C.c_void_p(_ptr(U_target))))

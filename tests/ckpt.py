@@ -8,7 +8,7 @@ import numpy as np
 import convert
 
 MAGIC = b"SLARCKPT"
-VERSION = 1
+VERSION = 2
 
 
 def write_checkpoint(path, w, st):
@@ -25,9 +25,10 @@ def write_checkpoint(path, w, st):
     lo = list(w.lo) + [0.0] * (4 - d)
     hi = list(w.hi) + [1.0] * (4 - d)
     has_corr = 1 if st.F.corr is not None else 0
-    hdr = struct.pack("=8si3i4i4d4d4i6i6idq", MAGIC, VERSION, d, w.dx, w.dv, *N, *lo, *hi,
-                      0, st.step, 1, has_corr, *rank, *([0] * 6), st.n_i, 0)
-    assert len(hdr) == 184
+    dts = list(st.dts) + [0.0, 0.0]
+    hdr = struct.pack("=8si3i4i4d4d4i6i6idq2d", MAGIC, VERSION, d, w.dx, w.dv, *N, *lo, *hi,
+                      0, st.step, 1, has_corr, *rank, *([0] * 6), st.n_i, 0, dts[0], dts[1])
+    assert len(hdr) == 200
     nU = (w.dv + 2) * int(np.prod(w.N[:w.dx]))
     with open(path, "wb") as f:
         f.write(hdr)
