@@ -417,11 +417,13 @@ def run_ours(args, w):
               "W_last": st1[-1].field_energy, "converged": all(s.converged for s in st1)}
         del c1c
 
-    # ---- the 128^4 configurations: FP32 SIMT entries vs BF16x3 tensor-core entries ----
+    # ---- the 128^4 configurations (strong Landau, two-stream, and the 2D-2V bump-on-tail
+    # example of Sec. 4.2 at its eps 1e-4 and a CFL-5 step): FP32 SIMT entries vs BF16x3
+    # tensor-core entries ----
     large = None
     if args.large_steps > 0:
         large = {}
-        for wname in ("strong_landau_2d2v", "two_stream_2d2v"):
+        for wname in ("strong_landau_2d2v", "two_stream_2d2v", "bump_on_tail_2d2v"):
             wl = inputs.workload_by_name(wname)
             res = {}
             for prec in ("fp32", "bf16x3"):

@@ -169,6 +169,30 @@ def two_stream_2d2v(n=128, alpha=0.005, k=0.2, v0=2.4, vmax=8.0, eps=5e-4, cap=4
                     rank_cap=cap, dt=dt, steps=steps, terms=terms, alpha=alpha, k=k)
 
 
+def bump_on_tail_2d2v(N=(128, 128, 128, 128), alpha=0.04, k=0.3, u=4.5, vt=2.4, vmax=13.0, eps=1e-4,
+                      cap=48, dt=0.0625, steps=480) -> Workload:
+    # f0 = (1 + alpha cos k x1 cos k x2) (n_p exp(-|v|^2/2) + n_b exp(-((v1-u)^2 + v2^2)/(2 vt))),
+    # n_p = 17/(40 pi), n_b = 3/(40 pi vt), so that n_p 2 pi + n_b 2 pi vt = 1: total density 1
+    # (the printed overall factor 1/(2 sqrt(2 pi))^2 would make it 1/(8 pi); reading: the
+    # densities already carry the normalisation).  Four separable terms: (1, cos cos) x
+    # (bulk, beam).  dt 0.0625: CFL 5 in x at v = 13 on 128 points.
+    L = 2.0 * math.pi / k
+    n_p = 17.0 / (40.0 * math.pi)
+    n_b = 3.0 / (40.0 * math.pi * vt)
+    b1 = ("maxwell", {"c": n_p * 2.0 * math.pi})            # n_p exp(-v1^2/2) (2 pi / sqrt(2 pi) each)
+    b2 = ("maxwell", {})                                     # exp(-v2^2/2) / sqrt(2 pi)
+    m1 = ("maxwell", {"u": u, "T": vt, "c": n_b * 2.0 * math.pi * vt})
+    m2 = ("maxwell", {"T": vt})
+    one = ("const", {"c": 1.0})
+    ca = ("cos", {"k": k, "c": alpha})
+    cb = ("cos", {"k": k, "c": 1.0})
+    terms = [[one, one, b1, b2], [one, one, m1, m2], [ca, cb, b1, b2], [ca, cb, m1, m2]]
+    N = tuple(N)
+    return Workload(name=f"bump_on_tail_2d2v_{N[0]}x{N[1]}x{N[2]}x{N[3]}", dx=2, dv=2, N=N,
+                    lo=(0.0, 0.0, -vmax, -vmax), hi=(L, L, vmax, vmax), eps=eps,
+                    rank_cap=cap, dt=dt, steps=steps, terms=terms, alpha=alpha, k=k)
+
+
 def ensemble(n_runs: int = 64, seed: int = 20261202, sizes=(32, 64, 128), cap_range=(8, 48),
              dt: float = 0.1) -> List[Workload]:
     """An ensemble of uneven runs: kinds cycle through 1D-1V Landau, 1D-1V two-stream,
@@ -204,6 +228,7 @@ def workload_by_name(name: str) -> Workload:
         "strong_landau_2d2v": lambda: landau_2d2v(n=128, alpha=0.5, cap=64, dt=0.2),
         "two_stream_1d1v": lambda: two_stream_1d1v(),
         "bump_on_tail_1d1v": lambda: bump_on_tail_1d1v(),
+        "bump_on_tail_2d2v": lambda: bump_on_tail_2d2v(),
     }
     return table[name]()
 

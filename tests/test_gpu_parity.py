@@ -298,7 +298,8 @@ def _run_pair(w, steps):
 
 @pytest.mark.parametrize("w", [inputs.landau_1d1v(N=(32, 64), alpha=0.05, eps=1e-6, cap=16),
                                inputs.landau_2d2v(n=16, alpha=0.05, eps=1e-5, cap=12),
-                               inputs.bump_on_tail_1d1v(N=(32, 64), eps=1e-6, cap=16)])
+                               inputs.bump_on_tail_1d1v(N=(32, 64), eps=1e-6, cap=16),
+                               inputs.bump_on_tail_2d2v(N=(16, 16, 16, 16), eps=1e-5, cap=12, dt=0.2)])
 def test_sl_step_matches_oracle(w):
     steps = 4
     ctx, st, Wg, Wo, U, g = _run_pair(w, steps)

@@ -50,3 +50,16 @@ def test_two_stream_2d2v():
     w = inputs.two_stream_2d2v(n=8)
     _check(w, lambda x1, x2, v1, v2: (1 + 0.005 * (np.cos(0.2 * x1) + np.cos(0.2 * x2))) / (4 * math.pi)
            * (np.exp(-(v1 - 2.4) ** 2 / 2) + np.exp(-(v1 + 2.4) ** 2 / 2)) * np.exp(-v2 * v2 / 2))
+
+
+def test_bump_on_tail_2d2v():
+    """Sec. 4.2 example with the densities normalised to total density 1 (n_p 2 pi +
+    n_b 2 pi v_t = 1; the reading drops the printed overall factor)."""
+    vt = 2.4
+    n_p = 17 / (40 * math.pi)
+    n_b = 3 / (40 * math.pi * vt)
+    assert n_p * 2 * math.pi + n_b * 2 * math.pi * vt == pytest.approx(1.0, rel=1e-15)
+    w = inputs.bump_on_tail_2d2v(N=(8, 8, 16, 16))
+    assert w.hi[0] == pytest.approx(20 * math.pi / 3) and (w.lo[2], w.hi[2]) == (-13.0, 13.0)
+    _check(w, lambda x1, x2, v1, v2: (1 + 0.04 * np.cos(0.3 * x1) * np.cos(0.3 * x2))
+           * (n_p * np.exp(-(v1 * v1 + v2 * v2) / 2) + n_b * np.exp(-((v1 - 4.5) ** 2 + v2 * v2) / (2 * vt))))

@@ -192,3 +192,56 @@ def test_2d2v_conservation_small(lomac):
     assert abs(tot1[0] - tot0[0]) <= 1e-12 * tot0[0]
     assert abs(tot1[-1] - tot0[-1]) <= 1e-12 * tot0[-1]
     assert np.all(np.abs(tot1[1:3] - tot0[1:3]) <= 1e-12 * tot0[0])
+
+
+@pytest.mark.slow
+def test_bump_on_tail_2d2v_linear_damping():
+    """2D-2V bump-on-tail data (Sec. 4.2 example; total density 1) at a small perturbation
+    (alpha 0.01): the cos(k x1) cos(k x2) perturbation holds the wave vectors (k, +-k),
+    |K| = 0.3 sqrt(2), along which the data reduce to a unit-temperature bulk of density
+    17/20 and a beam of density 3/20, temperature 2.4 and drift 4.5 / sqrt(2).  That
+    distribution has no unstable root at |K|; the electric energy follows its least-damped
+    root, Im w = -0.1155 (Re w = 1.128): the rate fitted to the peaks of sqrt(W) on
+    t in [2, 20] agrees within 2 %."""
+    w = inputs.bump_on_tail_2d2v(N=(16, 16, 32, 32), alpha=0.01, eps=1e-6, cap=24, dt=0.2)
+    g = sl.PhaseGrid(w.dx, w.dv, w.N, w.lo, w.hi)
+    prm = stepper.Params(eps=w.eps, cap=w.rank_cap)
+    st = stepper.init_state(inputs.initial_factors(w), g, prm)
+    tot0 = stepper.totals(st, g)
+    ts, Ws = [], []
+    for _ in range(100):
+        s = stepper.sl_step(st, w.dt, g, prm)
+        assert s.converged
+        ts.append(st.t)
+        Ws.append(s.W)
+    K = 0.3 * math.sqrt(2.0)
+    root = dispersion.root(K, 1.1 - 0.1j, species=((17 / 20, 0.0, 1.0), (3 / 20, 4.5 / math.sqrt(2.0), 2.4)))
+    assert abs(dispersion.dielectric(K, root, ((17 / 20, 0.0, 1.0), (3 / 20, 4.5 / math.sqrt(2.0), 2.4)))) < 1e-12
+    rate, npk = _fit_rate(np.array(ts), np.array(Ws))
+    assert npk >= 5
+    assert abs(rate - root.imag) <= 0.02 * abs(root.imag), (rate, root)
+    tot1 = stepper.totals(st, g)
+    assert abs(tot1[0] - tot0[0]) <= 1e-12 * tot0[0]
+    assert np.all(np.abs(tot1[1:3] - tot0[1:3]) <= 1e-12 * tot0[0])
+    assert abs(tot1[3] - tot0[3]) <= 1e-12 * tot0[3]
+
+
+def test_bump_on_tail_2d2v_mirror_symmetry():
+    """The 2D-2V bump-on-tail data are even under (x2, v2) -> (-x2, -v2), which maps the
+    cell-centred periodic grid onto itself (index j -> N - 1 - j), and the Vlasov-Poisson
+    flow keeps that symmetry: after three steps f and its mirror image agree to the
+    truncation tolerance (the cross approximation and the truncation are not themselves
+    mirror-symmetric), and the v2 momentum stays zero."""
+    w = inputs.bump_on_tail_2d2v(N=(8, 8, 16, 16), alpha=0.04, eps=1e-6, cap=16, dt=0.2)
+    g = sl.PhaseGrid(w.dx, w.dv, w.N, w.lo, w.hi)
+    prm = stepper.Params(eps=w.eps, cap=w.rank_cap)
+    st = stepper.init_state(inputs.initial_factors(w), g, prm)
+    for _ in range(3):
+        assert stepper.sl_step(st, w.dt, g, prm).converged
+    from oracle import ht as htmod
+    f = htmod.densify(st.F)
+    mirror = f[:, ::-1, :, ::-1]
+    assert np.linalg.norm(f - mirror) <= 10 * w.eps * np.linalg.norm(f)
+    assert abs(stepper.totals(st, g)[2]) <= 1e-12 * stepper.totals(st, g)[0]
+    # not trivially symmetric in the other pair: the beam drifts along v1
+    assert np.linalg.norm(f - f[:, :, ::-1, :]) > 1e-3 * np.linalg.norm(f)
