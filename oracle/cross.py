@@ -24,6 +24,15 @@ HSVD truncation of Supp. B.1.  The reading implemented here (deterministic):
    Arg-max ties: values within a relative 1e-10 of the maximum are treated as equal and
    the lowest index wins, so that pivots are reproducible across implementations that
    round differently.
+   Negligible rows: a residual row whose largest entry (over unused columns) is at most
+   max(1e-14, eps / 100) of the first pivot's magnitude adds no term.  Below eps / 100 a
+   pivot only resolves structure beneath the requested accuracy while multiplying rounding
+   errors by 1 / |pivot| (the cross factor v = r / r[j]); at the 1e-14 floor the row is
+   rounding noise -- data that repeat a row already crossed, as under the half-period
+   shift symmetry of cos kx1 cos kx2, or data reproduced exactly -- and the pivot would
+   depend on how an implementation rounds.  Such a row counts as a vanishing term for the
+   stop test: the check rows decide between stopping and continuing from the unused check
+   row of largest residual.
 2. The factors A ~ U V^T are embedded exactly as an HT: d = 2: leaves U, V and root I;
    d = 4: identity leaves, B12[a,b,p] = U[(a,b),p], B34[c,e,q] = V[(c,e),q], root I.
 3. HSVD truncation (``ht.truncate``) with eps and the rank cap gives the new HT, whose
@@ -41,6 +50,7 @@ import numpy as np
 from . import ht as htmod
 
 TIE_RTOL = 1e-10
+NOISE_RTOL = 1e-14
 N_CHECK = 8
 GOLDEN = (math.sqrt(5.0) - 1.0) / 2.0
 
@@ -76,7 +86,8 @@ def aca(row_fn: Callable[[int], np.ndarray], col_fn: Callable[[int], np.ndarray]
 
     row_fn(i) -> A(i, :) (length M2) and col_fn(j) -> A(:, j) (length M1) sample fibres.
     ``pivots`` (list of (i, j)) replays a given pivot sequence instead of choosing.
-    Returns dict(U (M1,k), V (M2,k), I, J, entries)."""
+    Returns dict(U (M1,k), V (M2,k), I, J, entries, skipped) with `skipped` the number of
+    negligible rows sampled without a term."""
     Us, Vs, I, J = [], [], [], []
     used_r = np.zeros(M1, dtype=bool)
     used_c = np.zeros(M2, dtype=bool)
@@ -87,7 +98,10 @@ def aca(row_fn: Callable[[int], np.ndarray], col_fn: Callable[[int], np.ndarray]
     chk = check_rows(M1) if pivots is None else []
     R = np.stack([row_fn(c).astype(np.float64) for c in chk]) if chk else np.zeros((0, M2))
     n_entries += len(chk) * M2
-    for k in range(kmax):
+    piv0 = None
+    skipped = 0
+    k = 0
+    while k < kmax:
         if pivots is not None:
             if k >= len(pivots):
                 break
@@ -98,14 +112,28 @@ def aca(row_fn: Callable[[int], np.ndarray], col_fn: Callable[[int], np.ndarray]
             r = r - Us[l][i] * Vs[l]
         used_r[i] = True
         if pivots is None:
-            if np.max(np.abs(np.where(used_c, 0.0, r))) == 0.0:
+            rmax = np.max(np.abs(np.where(used_c, 0.0, r)))
+            if rmax == 0.0 and piv0 is None:
                 break
+            if piv0 is not None and rmax <= max(NOISE_RTOL, 0.01 * eps) * piv0:
+                # a negligible row: no term; the check rows decide (as for a vanishing term)
+                skipped += 1
+                n2 = np.array([float(R[q] @ R[q]) for q in range(len(chk))])
+                if not chk or M1 / len(chk) * float(np.sum(n2)) <= eps * eps * normA2:
+                    break
+                free = [q for q in range(len(chk)) if not used_r[chk[q]]]
+                if not free:
+                    break
+                i = chk[max(free, key=lambda q: (n2[q], -q))]
+                continue
             j = argmax_tie(r, used_c)
         else:
             j = pivots[k][1]
         piv = r[j]
         if piv == 0.0:
             break
+        if piv0 is None:
+            piv0 = abs(piv)
         v = r / piv
         c = col_fn(j).astype(np.float64)
         n_entries += M1
@@ -123,6 +151,7 @@ def aca(row_fn: Callable[[int], np.ndarray], col_fn: Callable[[int], np.ndarray]
         Vs.append(v)
         I.append(i)
         J.append(j)
+        k += 1
         if pivots is None:
             for q, c in enumerate(chk):
                 R[q] = R[q] - u[c] * v
@@ -139,7 +168,7 @@ def aca(row_fn: Callable[[int], np.ndarray], col_fn: Callable[[int], np.ndarray]
     k = len(Us)
     U = np.stack(Us, axis=1) if k else np.zeros((M1, 0))
     V = np.stack(Vs, axis=1) if k else np.zeros((M2, 0))
-    return dict(U=U, V=V, I=I, J=J, entries=n_entries)
+    return dict(U=U, V=V, I=I, J=J, entries=n_entries, skipped=skipped)
 
 
 def embed(U: np.ndarray, V: np.ndarray, N) -> htmod.HT:
@@ -177,6 +206,6 @@ def htaca(entry_fn: Callable[[np.ndarray], np.ndarray], N, eps: float, cap: int,
     out, tinfo = htmod.truncate(full, eps, cap, return_info=True)
     if return_info:
         info = dict(aca_rank=res["U"].shape[1], pivots=list(zip(res["I"], res["J"])),
-                    entries=res["entries"], ranks=tinfo["ranks"])
+                    entries=res["entries"], ranks=tinfo["ranks"], skipped=res["skipped"])
         return out, info
     return out

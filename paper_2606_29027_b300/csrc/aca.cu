@@ -29,6 +29,12 @@ constexpr int PIV_THREADS = 1024;
 constexpr int ACA_UNROLL = 2;      // pivot steps per iteration of the captured WHILE loop
 constexpr int DOT_SEG = 256;      // entries per dot-product block (= its thread count)
 constexpr double TIE_RTOL = 1e-10;
+// a residual row whose largest unused entry is at most max(NOISE_RTOL, eps / 100) of the first
+// pivot is negligible: below eps / 100 a pivot only resolves structure beneath the requested
+// accuracy while multiplying rounding errors by 1 / |pivot|, and at NOISE_RTOL the row is
+// rounding noise (a repeat of a crossed row, or data reproduced exactly).  No pivot is taken
+// in it; it counts as a vanishing term for the stop test.
+constexpr double NOISE_RTOL = 1e-14;
 
 // |a| as an order key on the integer pipe: for non-negative doubles the IEEE-754 bit pattern
 // orders like the value, so the scans below compare 64-bit integers instead of issuing FP64
@@ -160,26 +166,58 @@ __global__ void k_aca_init(AcaState* st, int* pivI, unsigned char* usedr, int re
   st->normA2 = 0.0;
   st->cap_binds = cap_binds;
   st->capped = 0;
+  st->piv0 = 0.0;
+  st->skip = 0;
+  st->n_skip = 0;
   if (!replay) pivI[0] = 0;
   if (pivI[0] < 0) { st->done = 1; return; }
   usedr[pivI[0]] = 1;
 }
 
-// column pivot from the residual row r, v_k = r / r[j_k]
+// column pivot from the residual row r, v_k = r / r[j_k].  A negligible row (largest unused
+// entry <= max(NOISE_RTOL, eps / 100) |first pivot|) takes no pivot: like a vanishing term it goes to
+// the check rows, which stop the approximation or name the next row (the unused check row of
+// largest residual, written to pivI[k]); st->skip then makes this step's column fibre and
+// post kernel return at once, and the next step samples that row.
 __global__ void __launch_bounds__(PIV_THREADS)
-k_aca_row_pivot(const double* __restrict__ r, int M2, unsigned char* usedc, int* pivJ,
-                AcaState* st, double* __restrict__ Va) {
+k_aca_row_pivot(const double* __restrict__ r, int M1, int M2, unsigned char* usedc, unsigned char* usedr,
+                int* pivI, int* pivJ, AcaState* st, double* __restrict__ Va, int n_chk,
+                const int* __restrict__ chk_rows, const double* __restrict__ chk_n2) {
   __shared__ int j_s;
   __shared__ double top_s;
   if (st->done) return;
   const int kk = st->k;
   const int replay = st->replay;
   double* vout = Va + (long long)kk * M2;
+  if (threadIdx.x == 0) st->skip = 0;   // the previous step's post kernel has finished with it
   if (replay) {
     if (threadIdx.x == 0) { j_s = pivJ[kk]; top_s = 1.0; }
     __syncthreads();
   } else {
     block_argmax_tie(r, M2, usedc, &j_s, &top_s);
+    if (kk > 0 && top_s >= 0.0 && top_s <= fmax(NOISE_RTOL, 0.01 * st->eps) * st->piv0) {
+      if (threadIdx.x == 0) {
+        st->skip = 1;
+        st->n_skip += 1;
+        double n2c[8];
+        double sum = 0.0;
+        for (int q = 0; q < n_chk; ++q) {
+          n2c[q] = chk_n2[q];
+          sum += n2c[q];
+        }
+        int best = -1;
+        if (n_chk > 0 && (double)M1 / n_chk * sum > st->eps * st->eps * st->normA2)
+          for (int q = 0; q < n_chk; ++q)
+            if (!usedr[chk_rows[q]] && (best < 0 || n2c[q] > n2c[best])) best = q;
+        if (best < 0) {
+          st->done = 1;       // confirmed (or no check row left): stop (the row is counted in n_skip)
+        } else {
+          pivI[kk] = chk_rows[best];
+          usedr[chk_rows[best]] = 1;
+        }
+      }
+      return;
+    }
   }
   const int j = j_s;
   if (j < 0 || top_s == 0.0 || r[j] == 0.0) {
@@ -195,7 +233,10 @@ k_aca_row_pivot(const double* __restrict__ r, int M2, unsigned char* usedc, int*
     pivJ[kk] = j;
     usedc[j] = 1;
     st->piv = piv;
+    if (kk == 0) st->piv0 = fabs(piv);
   }
+  (void)M1;
+  (void)pivI;
 }
 
 // norm estimate, stop test (confirmed on the check rows), next row pivot; run by the last
@@ -310,6 +351,10 @@ k_aca_post(const double* __restrict__ Ua, int M1, const double* __restrict__ Va,
     if (blockIdx.x == 0 && threadIdx.x == 0 && use_cond) cudaGraphSetConditional(loop, 0);
     return;
   }
+  if (st->skip) {   // a negligible row: no term this step, the next step samples pivI[k]
+    if (blockIdx.x == 0 && threadIdx.x == 0 && use_cond) cudaGraphSetConditional(loop, 1);
+    return;
+  }
   const int kk = st->k;
   const int blk = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -405,6 +450,7 @@ slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int
   ac.ldY = M1;
   ac.out = c->Ua;
   ac.out_stride = M1;
+  ac.skip = &c->ast->skip;   // no column fibre after a negligible row
   const bool f32 = c->cfg.precision != SLAR_FP64;
   const bool tc = c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4;
   for (int pass = 0; pass < 2; ++pass) {
@@ -424,7 +470,9 @@ slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int
       c->prof_n++;
     }
     if (pass == 0)
-      slar::count_launch(), k_aca_row_pivot<<<1, PIV_THREADS, 0, s>>>(c->rowbuf, M2, c->usedc, c->pivJ, c->ast, c->Va);
+      slar::count_launch(), k_aca_row_pivot<<<1, PIV_THREADS, 0, s>>>(c->rowbuf, M1, M2, c->usedc, c->usedr,
+                                                                       c->pivI, c->pivJ, c->ast, c->Va, c->n_chk,
+                                                                       c->chk_rows, c->chk_n2);
   }
   slar::count_launch(), k_aca_post<<<nbu + nbv + c->n_chk, 256, 0, s>>>(
       c->Ua, M1, c->Va, M2, c->kmax, nbu, nbv, c->aca_part, ldp, c->ast, c->pivI, c->usedr, c->n_chk, c->chk_rows,
@@ -613,7 +661,9 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
     CKS(build_aca_graph(c, need));
   if (prof) {
     // individually launched steps with events around the evaluator (roofline timing)
-    for (int kk = 0; kk < kmax; ++kk) {
+    // bounded like the WHILE loop: each step adds a term (at most kmax) or consumes a check
+    // row after a negligible row (at most n_chk), or stops
+    for (int it = 0; it < kmax + c->n_chk + 1; ++it) {
       CK(cudaMemcpyAsync(c->ast_host, c->ast, sizeof(AcaState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (c->ast_host->done) break;   // where the WHILE node would stop
@@ -628,9 +678,12 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
   if (c->ast_host->capped) c->rank_capped++;
   if (c->ast_host->tc_err)
     return set_error(c, SLAR_ETIMEOUT, "tensor-core evaluator: an MMA completion wait ran out");
-  if (!prof) add_launches(c->aca_graph_nodes * (long long)((k + c->ast_host->stop_row + ACA_UNROLL - 1) / ACA_UNROLL));
+  // rows sampled without a term: negligible rows, and a vanishing first row
+  const int extra_rows = c->ast_host->n_skip + c->ast_host->stop_row;
+  if (!prof)
+    add_launches(c->aca_graph_nodes * (long long)((k + extra_rows + ACA_UNROLL - 1) / ACA_UNROLL));
   if (aca_rank) *aca_rank = k;
-  const long long nent = (long long)k * (M1 + M2) + (c->ast_host->stop_row ? M2 : 0) + chk_entries;
+  const long long nent = (long long)k * (M1 + M2) + (long long)extra_rows * M2 + chk_entries;
   if (entries) *entries = nent;
   c->prof_flop += (double)nent * entry_flops(c, in);
   if (k == 0) return set_error(c, SLAR_ENAN, "cross approximation found no pivot (zero tensor)");

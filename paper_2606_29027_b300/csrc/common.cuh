@@ -60,6 +60,7 @@ struct EvalArgs {
   const int* idx;        // EVAL_TUPLES: [n][d]
   const int* pivot;      // EVAL_ROW: device pointer to the row pivot; EVAL_COL: to the column pivot
   const int* done;       // optional device flag: when non-zero the launch does nothing
+  const int* skip;       // optional second flag with the same effect
   int kterms;            // number of residual terms l < kterms
   const int* kidx;       // optional device iteration index kk: pivot += kk, kterms = kk,
   long long out_stride;  //   out += kk * out_stride (cross-approximation graph)

@@ -41,6 +41,9 @@ struct AcaState {
   unsigned int post_ctr;  // block tickets of k_aca_post (reset by its last block)
   int cap_binds;  // the rank cap is below min(M1, M2) (reaching it leaves an error)
   int capped;     // stopped at the rank cap with the stop test unmet
+  double piv0;    // |first pivot|: the scale of the negligible-row test
+  int skip;       // the current row was negligible: no term this step
+  int n_skip;     // negligible rows sampled in this call
 };
 
 }  // namespace slar

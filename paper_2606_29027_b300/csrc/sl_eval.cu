@@ -287,7 +287,7 @@ template <typename T, int TILE>
 __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>& ht,
                                              const CorrView& corr, EvalArgs a, int at_grid) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (a.done && *a.done) return;
+  if ((a.done && *a.done) || (a.skip && *a.skip)) return;
   if (a.kidx) {
     const int kk = *a.kidx;
     a.pivot += kk;

@@ -337,7 +337,7 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     ht = ht_arg;
     corr = corr_arg;
   }
-  if (a.done && *a.done) return;
+  if ((a.done && *a.done) || (a.skip && *a.skip)) return;
   if (a.kidx) {
     const int kk = *a.kidx;
     a.pivot += kk;

@@ -80,7 +80,10 @@ def test_cross_exact_recovery_of_low_rank(N, ranks):
     assert np.linalg.norm(_dense(out) - F) <= 1e-10 * np.linalg.norm(F)
     M1 = int(np.prod(N[: len(N) // 2]))
     M2 = int(np.prod(N[len(N) // 2:]))
-    assert info["entries"] == info["aca_rank"] * (M1 + M2) + len(cross.check_rows(M1)) * M2
+    # k terms, the check rows, and the rounding-level row that ends an exact reproduction
+    assert info["entries"] == (info["aca_rank"] * (M1 + M2) + len(cross.check_rows(M1)) * M2
+                               + info["skipped"] * M2)
+    assert info["skipped"] <= 1
     # root-split rank of the data is the ACA rank bound
     rr = np.linalg.matrix_rank(F.reshape(M1, M2), tol=1e-9 * np.abs(F).max())
     assert info["aca_rank"] <= rr + 1
@@ -157,3 +160,28 @@ def test_check_rows_are_distinct_and_spread():
         assert all(0 <= r < M1 for r in rows)
     r = sorted(cross.check_rows(4096))
     assert max(np.diff([0] + r + [4096])) < 4096 / 3
+
+
+def test_rounding_level_row_is_skipped():
+    """Two identical rows (rows 0 and 7, both of the largest magnitude): after the first
+    term, row 7's residual is rounding noise, and the column residual points at it.  The
+    cross approximation takes no pivot there (the pivot would be noise) and recovers the
+    rank-2 matrix with exactly two terms from other rows; the pivots replay to the same
+    result."""
+    rng = np.random.default_rng(4)
+    M1, M2 = 20, 30
+    a = rng.uniform(-1, 1, M1)
+    c = rng.uniform(-1, 1, M1)
+    a[0] = a[7] = 3.0
+    c[7] = c[0]
+    b = rng.uniform(0.5, 1.0, M2)
+    d = rng.uniform(-1, 1, M2)
+    A = np.outer(a, b) + 0.3 * np.outer(c, d)
+    assert np.array_equal(A[0], A[7])
+    res = cross.aca(lambda i: A[i].copy(), lambda j: A[:, j].copy(), M1, M2, 1e-13, 10)
+    assert res["U"].shape[1] == 2
+    assert 7 not in res["I"][1:] and res["skipped"] >= 1
+    assert np.linalg.norm(res["U"] @ res["V"].T - A) <= 1e-13 * np.linalg.norm(A)
+    rep = cross.aca(lambda i: A[i].copy(), lambda j: A[:, j].copy(), M1, M2, 1e-13, 10,
+                    pivots=list(zip(res["I"], res["J"])))
+    assert np.allclose(rep["U"] @ rep["V"].T, res["U"] @ res["V"].T, rtol=0, atol=1e-15 * np.abs(A).max())

@@ -229,19 +229,20 @@ def test_bump_on_tail_2d2v_linear_damping():
 def test_bump_on_tail_2d2v_mirror_symmetry():
     """The 2D-2V bump-on-tail data are even under (x2, v2) -> (-x2, -v2), which maps the
     cell-centred periodic grid onto itself (index j -> N - 1 - j), and the Vlasov-Poisson
-    flow keeps that symmetry: after three steps f and its mirror image agree to the
-    truncation tolerance (the cross approximation and the truncation are not themselves
-    mirror-symmetric), and the v2 momentum stays zero."""
-    w = inputs.bump_on_tail_2d2v(N=(8, 8, 16, 16), alpha=0.04, eps=1e-6, cap=16, dt=0.2)
+    flow keeps that symmetry.  The cross approximation and the truncation of a SLAR call
+    are not themselves mirror-symmetric and may each break it by about eps, so after one
+    DIRK3 step (nine SLAR calls, ranks below the cap) f and its mirror image agree within
+    9 eps; the v2 momentum stays zero."""
+    w = inputs.bump_on_tail_2d2v(N=(8, 8, 16, 16), alpha=0.04, eps=1e-8, cap=32, dt=0.2)
     g = sl.PhaseGrid(w.dx, w.dv, w.N, w.lo, w.hi)
     prm = stepper.Params(eps=w.eps, cap=w.rank_cap)
     st = stepper.init_state(inputs.initial_factors(w), g, prm)
-    for _ in range(3):
-        assert stepper.sl_step(st, w.dt, g, prm).converged
+    s = stepper.sl_step(st, w.dt, g, prm)
+    assert s.converged and max(s.aca_ranks) < w.rank_cap
     from oracle import ht as htmod
     f = htmod.densify(st.F)
     mirror = f[:, ::-1, :, ::-1]
-    assert np.linalg.norm(f - mirror) <= 10 * w.eps * np.linalg.norm(f)
+    assert np.linalg.norm(f - mirror) <= 9 * w.eps * np.linalg.norm(f)
     assert abs(stepper.totals(st, g)[2]) <= 1e-12 * stepper.totals(st, g)[0]
     # not trivially symmetric in the other pair: the beam drifts along v1
     assert np.linalg.norm(f - f[:, :, ::-1, :]) > 1e-3 * np.linalg.norm(f)
