@@ -171,6 +171,148 @@ def aca(row_fn: Callable[[int], np.ndarray], col_fn: Callable[[int], np.ndarray]
     return dict(U=U, V=V, I=I, J=J, entries=n_entries, skipped=skipped)
 
 
+def top_rows(a: np.ndarray, excluded: np.ndarray, b: int):
+    """The b rows of largest |a| outside `excluded`, in that order (each pick by argmax_tie:
+    near-ties to the lowest index)."""
+    ex = excluded.copy()
+    out = []
+    for _ in range(b):
+        i = argmax_tie(a, ex)
+        if i < 0:
+            break
+        out.append(i)
+        ex[i] = True
+    return out
+
+
+def aca_block(rows_fn: Callable[[list], np.ndarray], cols_fn: Callable[[list], np.ndarray], M1: int, M2: int,
+              eps: float, kmax: int, b: int):
+    """Block cross approximation (the "next" row of the scope: rank-level parallel HTACA),
+    A ~ U V^T with b row fibres and up to b column fibres sampled per step.
+
+    rows_fn(list of i) -> A(i, :) stacked (len, M2); cols_fn(list of j) -> A(:, j) as (M1, len).
+    Reading (the paper names HTACA's serial pivot steps as its bottleneck and defers the
+    method): a step takes the rows I of its block -- row 0 and the first b - 1 other check
+    rows at the start, then the b rows of largest |u| of the latest column residual outside
+    the used rows (after a stop test that the check rows did not confirm, the unused check
+    row of largest residual first) -- samples their residual rows R = A(I, :) - U(I) V^T at
+    once, and pivots in them in order, exactly like partial pivoting restricted to I:
+        row t of I: r = R[t] (already reduced by the block's earlier terms),
+        negligible (as in ``aca``): no term;  else j_t = argmax |r|, v_t = r / r[j_t],
+        and R[t'] -= R[t'][j_t] v_t for the later rows t' of the block.
+    Then the accepted columns J are sampled at once, C = A(:, J) - U V(J)^T, and the column
+    factors follow by forward substitution, u_t = C[:, t] - sum_{s<t} u_s v_s[j_t] (the
+    residual column after the block's earlier terms).  The terms are accepted in order with
+    the stop test of ``aca`` (rank-1 test confirmed on the check rows); the rest of a block
+    after a confirmed stop is dropped.  With b = 1 this is ``aca``.
+    Returns the same dict as ``aca``."""
+    Us, Vs, I, J = [], [], [], []
+    used_r = np.zeros(M1, dtype=bool)
+    used_c = np.zeros(M2, dtype=bool)
+    normA2 = 0.0
+    kmax = min(kmax, M1, M2)
+    chk = check_rows(M1)
+    R = rows_fn(chk).astype(np.float64) if chk else np.zeros((0, M2))
+    n_entries = len(chk) * M2
+    piv0 = None
+    skipped = 0
+    next_rows = [0] + [c for c in chk if c != 0][: b - 1]
+
+    def check_decision():
+        """After a vanishing term or a passed rank-1 test: (stop, redirect row or None)."""
+        n2 = np.array([float(R[q] @ R[q]) for q in range(len(chk))])
+        if not chk or M1 / len(chk) * float(np.sum(n2)) <= eps * eps * normA2:
+            return True, None
+        free = [q for q in range(len(chk)) if not used_r[chk[q]]]
+        if not free:
+            return True, None
+        return False, chk[max(free, key=lambda q: (n2[q], -q))]
+
+    stop = False
+    while not stop and len(Us) < kmax:
+        rows = []
+        for i in next_rows:
+            if not used_r[i] and i not in rows:
+                rows.append(i)
+        rows = rows[: min(b, kmax - len(Us))]
+        if not rows:
+            break
+        Rb = rows_fn(rows).astype(np.float64)
+        n_entries += len(rows) * M2
+        for l in range(len(Us)):
+            Rb = Rb - np.outer(Us[l][rows], Vs[l])
+        for i in rows:
+            used_r[i] = True
+        acc_rows, acc_cols, vs = [], [], []
+        first_zero = False
+        for t, i in enumerate(rows):
+            r = Rb[t]
+            rmax = float(np.max(np.abs(np.where(used_c, 0.0, r))))
+            if rmax == 0.0 and piv0 is None:
+                first_zero = True
+                break
+            if piv0 is not None and rmax <= max(NOISE_RTOL, 0.01 * eps) * piv0:
+                skipped += 1
+                continue
+            j = argmax_tie(r, used_c)
+            piv = r[j]
+            if piv0 is None:
+                piv0 = abs(piv)
+            v = r / piv
+            used_c[j] = True
+            acc_rows.append(i)
+            acc_cols.append(j)
+            vs.append(v)
+            for t2 in range(t + 1, len(rows)):
+                Rb[t2] = Rb[t2] - Rb[t2][j] * v
+        if first_zero:
+            break
+        redirect = None
+        if not acc_cols:
+            # every row of the block negligible: a vanishing term for the stop test
+            stop, redirect = check_decision()
+            if stop:
+                break
+            next_rows = [redirect] + top_rows(Us[-1], used_r | (np.arange(M1) == redirect), b - 1)
+            continue
+        C = cols_fn(acc_cols).astype(np.float64)
+        n_entries += len(acc_cols) * M1
+        for l in range(len(Us)):
+            C = C - np.outer(Us[l], Vs[l][acc_cols])
+        new_us = []
+        for t in range(len(acc_cols)):
+            u = C[:, t].copy()
+            for s in range(t):
+                u = u - new_us[s] * vs[s][acc_cols[t]]
+            new_us.append(u)
+        for t in range(len(acc_cols)):
+            u, v = new_us[t], vs[t]
+            cross = 0.0
+            for l in range(len(Us)):
+                cross += float(Us[l] @ u) * float(Vs[l] @ v)
+            nu, nv = float(np.linalg.norm(u)), float(np.linalg.norm(v))
+            normA2 = normA2 + 2.0 * cross + (nu * nv) ** 2
+            Us.append(u)
+            Vs.append(v)
+            I.append(acc_rows[t])
+            J.append(acc_cols[t])
+            for q, cq in enumerate(chk):
+                R[q] = R[q] - u[cq] * v
+            if nu * nv <= eps * np.sqrt(max(normA2, 0.0)):
+                stop, redirect = check_decision()
+                if stop:
+                    break
+        if stop:
+            break
+        base = top_rows(Us[-1], used_r | (np.arange(M1) == redirect) if redirect is not None else used_r,
+                        b - (1 if redirect is not None else 0))
+        next_rows = ([redirect] if redirect is not None else []) + base
+    k = len(Us)
+    U = np.stack(Us, axis=1) if k else np.zeros((M1, 0))
+    V = np.stack(Vs, axis=1) if k else np.zeros((M2, 0))
+    return dict(U=U, V=V, I=I, J=J, entries=n_entries, skipped=skipped)
+
+
 def embed(U: np.ndarray, V: np.ndarray, N) -> htmod.HT:
     """Exact HT of U V^T on the root split (step 2 of the module docstring)."""
     k = U.shape[1]
@@ -183,9 +325,11 @@ def embed(U: np.ndarray, V: np.ndarray, N) -> htmod.HT:
 
 
 def htaca(entry_fn: Callable[[np.ndarray], np.ndarray], N, eps: float, cap: int,
-          pivots=None, return_info: bool = False):
+          pivots=None, return_info: bool = False, block: int = 1):
     """Build the HT of the tensor whose entries are entry_fn(idx (S, d)) from sampled row
-    and column fibres of the root-split matricisation, then truncate (module docstring)."""
+    and column fibres of the root-split matricisation, then truncate (module docstring).
+    block > 1: the block cross approximation (``aca_block``) with that many fibres per step;
+    replayed pivots give the same cross approximation whatever the blocking."""
     d = len(N)
     half = d // 2
     Nl, Nr = N[:half], N[half:]
@@ -201,7 +345,16 @@ def htaca(entry_fn: Callable[[np.ndarray], np.ndarray], N, eps: float, cap: int,
         idx = np.concatenate([left, np.repeat(right[j:j + 1], M1, axis=0)], axis=1)
         return entry_fn(idx)
 
-    res = aca(row_fn, col_fn, M1, M2, eps, cap, pivots)
+    def rows_fn(rows):
+        return np.stack([row_fn(i) for i in rows])
+
+    def cols_fn(cols):
+        return np.stack([col_fn(j) for j in cols], axis=1)
+
+    if block > 1 and pivots is None:
+        res = aca_block(rows_fn, cols_fn, M1, M2, eps, cap, block)
+    else:
+        res = aca(row_fn, col_fn, M1, M2, eps, cap, pivots)
     full = embed(res["U"], res["V"], N)
     out, tinfo = htmod.truncate(full, eps, cap, return_info=True)
     if return_info:

@@ -51,6 +51,8 @@ class Params:
     net_theta: Optional[np.ndarray] = None
     net_hidden: int = net.HIDDEN
     probes: int = 4
+    # fibres per cross-approximation step (1: classical partial pivoting; > 1: block cross)
+    block: int = 1
 
 
 @dataclass
@@ -100,7 +102,7 @@ def field_of(F: HT, g: PhaseGrid, n_i: float) -> np.ndarray:
 def slar(F: HT, E: np.ndarray, tau: float, g: PhaseGrid, prm: Params, pivots=None):
     """SLAR(F; E, tau, eps): cross approximation of the SL-updated tensor, then truncation."""
     fn = lambda idx: sl.sl_eval(F, E, tau, idx, g, prm.foot)
-    return cross.htaca(fn, g.N, prm.eps, prm.cap, pivots=pivots, return_info=True)
+    return cross.htaca(fn, g.N, prm.eps, prm.cap, pivots=pivots, return_info=True, block=prm.block)
 
 
 def slar_vp(F: HT, dt: float, g: PhaseGrid, prm: Params, n_i: float, pivots=None):

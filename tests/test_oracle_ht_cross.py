@@ -185,3 +185,92 @@ def test_rounding_level_row_is_skipped():
     rep = cross.aca(lambda i: A[i].copy(), lambda j: A[:, j].copy(), M1, M2, 1e-13, 10,
                     pivots=list(zip(res["I"], res["J"])))
     assert np.allclose(rep["U"] @ rep["V"].T, res["U"] @ res["V"].T, rtol=0, atol=1e-15 * np.abs(A).max())
+
+
+# ---------------------------------------------------------------- block cross approximation
+
+def _matrix_fns(A):
+    return (lambda rows: A[rows].copy(), lambda cols: A[:, cols].copy(),
+            lambda i: A[i].copy(), lambda j: A[:, j].copy())
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_block_of_one_is_the_classical_cross(eps):
+    """b = 1: the same pivots, entries and factors as the classical partial pivoting."""
+    x = np.linspace(0, 1, 60)
+    y = np.linspace(0, 2, 70)
+    A = 1.0 / (1.0 + (x[:, None] - y[None, :]) ** 2) + 0.1 * np.cos(3 * x)[:, None]
+    rf, cf, r1, c1 = _matrix_fns(A)
+    a = cross.aca(r1, c1, 60, 70, eps, 60)
+    b = cross.aca_block(rf, cf, 60, 70, eps, 60, 1)
+    assert a["I"] == b["I"] and a["J"] == b["J"] and a["entries"] == b["entries"]
+    assert np.allclose(a["U"] @ a["V"].T, b["U"] @ b["V"].T, rtol=0, atol=1e-15 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("b", [2, 4, 8])
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_block_cross_accuracy_near_svd(b, eps):
+    """Blocks of b fibres reach the requested accuracy (within 10 eps, as the classical
+    cross approximation) with a rank within two of the SVD's numerical rank at 1e-3 eps."""
+    x = np.linspace(0, 1, 60)
+    y = np.linspace(0, 2, 70)
+    A = 1.0 / (1.0 + (x[:, None] - y[None, :]) ** 2) + 0.1 * np.cos(3 * x)[:, None]
+    rf, cf, _, _ = _matrix_fns(A)
+    res = cross.aca_block(rf, cf, 60, 70, eps, 60, b)
+    err = np.linalg.norm(A - res["U"] @ res["V"].T) / np.linalg.norm(A)
+    assert err <= 10 * eps
+    s = np.linalg.svd(A, compute_uv=False)
+    assert res["U"].shape[1] <= np.count_nonzero(s > 1e-3 * eps * s[0]) + 2 + (b - 1)
+    # every step's pivot pairs are distinct rows and columns
+    assert len(set(res["I"])) == len(res["I"]) and len(set(res["J"])) == len(res["J"])
+
+
+@pytest.mark.parametrize("b", [2, 4])
+@pytest.mark.parametrize("N,ranks", [((24, 30), (3, 4)), ((6, 7, 5, 8), (2, 3, 3, 2, 3, 3))])
+def test_block_cross_exact_recovery(b, N, ranks):
+    h = htmod.from_raw(inputs.random_ht(N, ranks, 8, smooth=False))
+    F = _dense(h)
+    out, info = cross.htaca(lambda idx: htmod.entries(h, idx), N, 1e-13, 64, return_info=True, block=b)
+    assert np.linalg.norm(_dense(out) - F) <= 1e-10 * np.linalg.norm(F)
+    M1 = int(np.prod(N[: len(N) // 2]))
+    M2 = int(np.prod(N[len(N) // 2:]))
+    rr = np.linalg.matrix_rank(F.reshape(M1, M2), tol=1e-9 * np.abs(F).max())
+    assert info["aca_rank"] <= rr + b
+
+
+@pytest.mark.parametrize("b", [2, 4])
+def test_block_pivots_replay_through_the_classical_path(b):
+    """The cross approximation is fixed by its pivot pairs whatever the blocking: replaying
+    a block run's pivots one at a time gives the same approximation to rounding (what the
+    GPU's replay mode relies on)."""
+    N = (12, 14)
+    h = htmod.from_raw(inputs.random_ht(N, (5, 5), 9, smooth=True))
+    fn = lambda idx: htmod.entries(h, idx)
+    x = np.linspace(0, 1, 40)
+    y = np.linspace(0, 2, 50)
+    A = 1.0 / (1.0 + (x[:, None] - y[None, :]) ** 2)
+    rf, cf, r1, c1 = _matrix_fns(A)
+    blk = cross.aca_block(rf, cf, 40, 50, 1e-8, 40, b)
+    rep = cross.aca(r1, c1, 40, 50, 1e-8, 40, pivots=list(zip(blk["I"], blk["J"])))
+    scale = np.abs(A).max()
+    assert np.max(np.abs(blk["U"] @ blk["V"].T - rep["U"] @ rep["V"].T)) <= 1e-12 * scale
+    a, ia = cross.htaca(fn, N, 1e-8, 16, return_info=True, block=b)
+    r, ir = cross.htaca(fn, N, 1e-8, 16, pivots=ia["pivots"], return_info=True)
+    assert np.allclose(_dense(a), _dense(r), atol=1e-12 * np.abs(_dense(a)).max())
+
+
+@pytest.mark.parametrize("b", [2, 4])
+def test_block_htaca_of_sl_update_close_to_dense(b):
+    """SLAR with blocks: within 10 eps of the dense SL step on a tiny 2D-2V grid, and the
+    first SLAR call of 2D-2V weak Landau 32^4 within eps of the dense update (the case the
+    rank-1 test alone missed by 84 eps)."""
+    N = (10, 10, 12, 12)
+    g = sl.PhaseGrid(2, 2, N, (0, 0, -5, -5), (4 * math.pi, 4 * math.pi, 5, 5))
+    w = inputs.landau_2d2v(n=10, alpha=0.3)
+    w.N, w.lo, w.hi = N, g.lo, g.hi
+    F0 = htmod.truncate(htmod.from_terms(inputs.initial_factors(w)), 1e-12, 20)
+    E = inputs.random_field(N[:2], 2, 0.3, seed=2)
+    eps = 1e-6
+    out = cross.htaca(lambda idx: sl.sl_eval(F0, E, 0.4, idx, g), N, eps, 40, block=b)
+    dense = sl.dense_sl_step(htmod.densify(F0), E, 0.4, g)
+    assert np.linalg.norm(_dense(out) - dense) <= 10 * eps * np.linalg.norm(dense)
