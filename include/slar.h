@@ -94,6 +94,14 @@ typedef struct slar_config {
     int precision;          /* SLAR_FP64 or SLAR_FP32 */
     int flags;              /* SLAR_LOMAC | SLAR_FOOT_EULER */
     double delta_floor;     /* positivity floor of the adaptive weight (Supp. B.1) */
+    int aca_block;          /* fibres per cross-approximation step: 0 or 1 = partial pivoting
+                               (one row and one column fibre per step); 2..8 = block cross
+                               approximation: the b rows of largest residual of the latest
+                               column are sampled at once, pivots are taken in them in order,
+                               their columns are sampled at once (an addition: a rank-level
+                               parallel variant of the paper's HTACA).  Replayed pivots always
+                               take the one-fibre path (the approximation depends on the pivots
+                               only). */
 } slar_config;
 
 typedef struct slar_stats {

@@ -417,6 +417,317 @@ k_aca_post(const double* __restrict__ Ua, int M1, const double* __restrict__ Va,
   aca_finalize_body(Ua, M1, kmax, nbu, nbv, part, ldp, st, pivI, usedr, n_chk, chk_rows, chk_n2, loop, use_cond);
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Block cross approximation (slar_config.aca_block = b > 1): a step samples the residuals of
+// the b rows pivI[k .. k + nrows) at once (rowbuf, b x M2), takes pivots in them in order --
+// row t: arg-max j_t of its residual, v_t = r / r[j_t], and the later rows of the block lose
+// r[t'][j_t] v_t -- samples the accepted columns at once (Ua columns k .., the residual
+// against the previous k terms), turns them into the new column factors by forward
+// substitution u_t = C_t - sum_{s<t} u_s v_s[j_t], and accepts the terms in order with the
+// stop test of the one-fibre steps.  Negligible rows (as there) add no term.
+
+// The next rows: up to nsel rows of largest |u| over the unused rows, each pick the lowest
+// index within the tie band of the remaining maximum (block_argmax_tie); the picks are marked
+// used (they are the next block's rows).  Called by every thread of the CTA.
+__device__ void pick_rows(const double* u, int M1, unsigned char* usedr, int nsel, int* out, int* nout) {
+  __shared__ int i_s;
+  __shared__ double t_s;
+  int n = 0;
+  for (int p = 0; p < nsel; ++p) {
+    block_argmax_tie(u, M1, usedr, &i_s, &t_s);
+    const int i = i_s;
+    if (i < 0) break;
+    if (threadIdx.x == 0) {
+      out[n] = i;
+      usedr[i] = 1;
+    }
+    ++n;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nout = n;
+  __syncthreads();
+}
+
+// The check rows decide after a vanishing term or a passed rank-1 test: returns 1 (stop) or
+// 0 with *redirect = the unused check row of largest residual norm n2c[q * stride].
+__device__ __forceinline__ int check_decision(int M1, int n_chk, const int* chk_rows, const double* n2c, int stride,
+                                              const unsigned char* usedr, double eps, double normA2, int* redirect) {
+  double sum = 0.0;
+  for (int q = 0; q < n_chk; ++q) sum += n2c[q * stride];
+  if (n_chk == 0 || (double)M1 / n_chk * sum <= eps * eps * normA2) return 1;
+  int best = -1;
+  for (int q = 0; q < n_chk; ++q)
+    if (!usedr[chk_rows[q]] && (best < 0 || n2c[q * stride] > n2c[best * stride])) best = q;
+  if (best < 0) return 1;
+  *redirect = chk_rows[best];
+  return 0;
+}
+
+// the first block: row 0 and the first b - 1 check rows other than 0
+__global__ void k_aca_block_init(AcaState* st, int* pivI, const int* chk_rows, int n_chk, int b, int kmax) {
+  if (threadIdx.x != 0) return;
+  int n = 0;
+  pivI[n++] = 0;
+  for (int q = 0; q < n_chk && n < b; ++q)
+    if (chk_rows[q] != 0) pivI[n++] = chk_rows[q];
+  st->nrows = n < kmax ? n : kmax;
+  st->nact = 0;
+  st->rows_sampled = 0;
+  st->cols_sampled = 0;
+  st->nsteps = 0;
+}
+
+// Pivots in the block's rows (one CTA).  rowbuf holds the rows' residuals against the k
+// previous terms; they are reduced in place by the block's terms.
+__global__ void __launch_bounds__(PIV_THREADS)
+k_aca_block_pivot(double* __restrict__ rowbuf, int M1, int M2, unsigned char* usedc, unsigned char* usedr, int* pivI,
+                  int* pivJ, AcaState* st, double* __restrict__ Va, const double* __restrict__ Ua, int n_chk,
+                  const int* __restrict__ chk_rows, const double* __restrict__ chk_n2, int b, int kmax) {
+  __shared__ int rows_s[ACA_BMAX], acc_s[ACA_BMAX];
+  __shared__ double coef_s[ACA_BMAX];
+  __shared__ int j_s, nacc_s, next_s[ACA_BMAX], nnext_s;
+  __shared__ double top_s, piv0_s;
+  if (st->done) return;
+  const int tid = threadIdx.x;
+  const int kk = st->k;
+  const int nrows = st->nrows;
+  if (tid == 0) {
+    st->skip = 0;
+    st->rows_sampled += nrows;
+    st->nsteps += 1;
+    nacc_s = 0;
+    piv0_s = st->piv0;
+  }
+  if (tid < nrows) rows_s[tid] = pivI[kk + tid];
+  __syncthreads();
+  const double floor_rel = fmax(NOISE_RTOL, 0.01 * st->eps);
+  for (int t = 0; t < nrows; ++t) {
+    const double* r = rowbuf + (long long)t * M2;
+    if (tid == 0) usedr[rows_s[t]] = 1;
+    block_argmax_tie(r, M2, usedc, &j_s, &top_s);
+    const double top = top_s, piv0 = piv0_s;
+    if (piv0 == 0.0 && !(top > 0.0)) {
+      // the first row of the call vanishes: nothing to approximate (the row was sampled)
+      if (tid == 0) { st->done = 1; st->stop_row = 1; st->nact = 0; }
+      return;
+    }
+    if (j_s < 0 || (piv0 > 0.0 && top <= floor_rel * piv0)) {   // negligible: no term
+      if (tid == 0) st->n_skip += 1;
+      __syncthreads();
+      continue;
+    }
+    const int j = j_s;
+    const double piv = r[j];
+    const int a = nacc_s;
+    double* vout = Va + (long long)(kk + a) * M2;
+    const double inv = 1.0 / piv;
+    for (int i = tid; i < M2; i += PIV_THREADS) vout[i] = i == j ? 1.0 : r[i] * inv;
+    if (tid < nrows) coef_s[tid] = tid > t ? rowbuf[(long long)tid * M2 + j] : 0.0;
+    __syncthreads();
+    if (tid == 0) {
+      usedc[j] = 1;
+      pivJ[kk + a] = j;
+      acc_s[a] = rows_s[t];
+      nacc_s = a + 1;
+      if (piv0 == 0.0) {
+        piv0_s = fabs(piv);
+        st->piv0 = fabs(piv);
+      }
+    }
+    for (int t2 = t + 1; t2 < nrows; ++t2) {
+      const double cf = coef_s[t2];
+      double* r2 = rowbuf + (long long)t2 * M2;
+      for (int i = tid; i < M2; i += PIV_THREADS) r2[i] -= cf * vout[i];
+    }
+    __syncthreads();
+  }
+  const int nacc = nacc_s;
+  if (tid < nacc) pivI[kk + tid] = acc_s[tid];
+  if (tid == 0) {
+    st->nact = nacc;
+    st->cols_sampled += nacc;
+  }
+  if (nacc > 0) return;
+  // every row of the block was negligible: a vanishing term for the stop test
+  __shared__ int stop_s, redirect_s;
+  if (tid == 0) {
+    int redirect = -1;
+    stop_s = check_decision(M1, n_chk, chk_rows, chk_n2, 1, usedr, st->eps, st->normA2, &redirect);
+    redirect_s = redirect;
+    st->skip = 1;
+    if (stop_s) st->done = 1;
+    else usedr[redirect] = 1;
+  }
+  __syncthreads();
+  if (stop_s) return;
+  // the next block: the check row, then the rows of largest |u| of the latest column
+  const int room = kmax - kk;
+  const int nsel = (b < room ? b : room) - 1;
+  pick_rows(Ua + (long long)(kk - 1) * M1, M1, usedr, nsel, next_s, &nnext_s);
+  if (tid == 0) {
+    pivI[kk] = redirect_s;
+    for (int q = 0; q < nnext_s; ++q) pivI[kk + 1 + q] = next_s[q];
+    st->nrows = 1 + nnext_s;
+  }
+}
+
+// forward substitution of the sampled columns: u_t = C_t - sum_{s<t} u_s v_s[j_t]
+__global__ void k_aca_block_fsub(double* __restrict__ Ua, int M1, const double* __restrict__ Va, int M2,
+                                 const int* __restrict__ pivJ, const AcaState* st) {
+  __shared__ double vj[ACA_BMAX][ACA_BMAX];
+  if (st->done || st->skip) return;
+  const int kk = st->k, n = st->nact;
+  if (n <= 1) return;
+  if (threadIdx.x < n * n) {
+    const int s = threadIdx.x / n, t = threadIdx.x - s * n;
+    vj[s][t] = s < t ? Va[(long long)(kk + s) * M2 + pivJ[kk + t]] : 0.0;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M1) return;
+  double u[ACA_BMAX];
+  for (int t = 0; t < n; ++t) {
+    double x = Ua[(long long)(kk + t) * M1 + i];
+    for (int s = 0; s < t; ++s) x -= u[s] * vj[s][t];
+    u[t] = x;
+    Ua[(long long)(kk + t) * M1 + i] = x;
+  }
+}
+
+// After the columns: blocks [0, nbu) form the partial dots of the new u_t with every column
+// of U (t < nact, l < k + nact), blocks [nbu, nbu + nbv) those of the new v_t with V, blocks
+// [nbu + nbv, + n_chk) apply the new terms to the check rows and keep their norms after each
+// term; the last block accepts the terms in order (norm estimate, rank-1 test, check rows),
+// and picks the next block's rows.
+__global__ void __launch_bounds__(256)
+k_aca_block_post(const double* __restrict__ Ua, int M1, const double* __restrict__ Va, int M2, int kmax, int nbu,
+                 int nbv, double* __restrict__ part, int ldp, AcaState* st, int* pivI, unsigned char* usedr, int n_chk,
+                 const int* __restrict__ chk_rows, double* __restrict__ chk_R, double* __restrict__ chk_n2,
+                 double* __restrict__ chk_n2t, int b, cudaGraphConditionalHandle loop, int use_cond) {
+  __shared__ double red[8];
+  __shared__ int s_last;
+  if (st->done) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && use_cond) cudaGraphSetConditional(loop, 0);
+    return;
+  }
+  if (st->skip) {   // every row of the block was negligible: the next block is set
+    if (blockIdx.x == 0 && threadIdx.x == 0 && use_cond) cudaGraphSetConditional(loop, 1);
+    return;
+  }
+  const int kk = st->k, na = st->nact, K = kk + na;
+  const int blk = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (blk < nbu + nbv) {
+    const bool isu = blk < nbu;
+    const double* X = isu ? Ua : Va;
+    const int M = isu ? M1 : M2;
+    const int s0 = (isu ? blk : blk - nbu) * DOT_SEG;
+    for (int w = warp; w < na * K; w += 8) {
+      const int t = w / K, l = w - t * K;
+      const double* xt = X + (long long)(kk + t) * M;
+      const double* xl = X + (long long)l * M;
+      double acc = 0.0;
+      for (int i = s0 + lane; i < s0 + DOT_SEG && i < M; i += 32) acc += xl[i] * xt[i];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) part[(long long)blk * ldp + w] = acc;
+    }
+  } else {
+    const int q = blk - nbu - nbv;
+    double* r = chk_R + (long long)q * M2;
+    for (int t = 0; t < na; ++t) {
+      const double a = Ua[(long long)(kk + t) * M1 + chk_rows[q]];
+      const double* v = Va + (long long)(kk + t) * M2;
+      double sq = 0.0;
+      for (int e = threadIdx.x; e < M2; e += 256) {
+        const double x = r[e] - a * v[e];
+        r[e] = x;
+        sq += x * x;
+      }
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+      if (lane == 0) red[warp] = sq;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        chk_n2t[q * ACA_BMAX + t] = s;
+      }
+      __syncthreads();
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->post_ctr, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // ---- finalize (last block) ----
+  __shared__ double du[ACA_BMAX * (SLAR_MAX_RANK + ACA_BMAX)], dv[ACA_BMAX * (SLAR_MAX_RANK + ACA_BMAX)];
+  __shared__ int stop_s, redirect_s, kend_s, next_s[ACA_BMAX], nnext_s;
+  const int tid = threadIdx.x;
+  if (tid == 0) st->post_ctr = 0;
+  for (int w = tid; w < na * K; w += 256) {
+    double a = 0.0, c = 0.0;
+    for (int q = 0; q < nbu; ++q) a += __ldcg(part + (long long)q * ldp + w);
+    for (int q = nbu; q < nbu + nbv; ++q) c += __ldcg(part + (long long)q * ldp + w);
+    du[w] = a;
+    dv[w] = c;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double n2 = st->normA2;
+    const double eps = st->eps;
+    int stop = 0, redirect = -1, kend = K;
+    for (int t = 0; t < na; ++t) {
+      double cross = 0.0;
+      for (int l = 0; l < kk + t; ++l) cross += du[t * K + l] * dv[t * K + l];
+      const double nu2 = du[t * K + kk + t], nv2 = dv[t * K + kk + t];
+      n2 = n2 + 2.0 * cross + nu2 * nv2;
+      const bool small = sqrt(nu2) * sqrt(nv2) <= eps * sqrt(fmax(n2, 0.0));
+      if (kk + t + 1 >= kmax) {
+        stop = 1;
+        kend = kk + t + 1;
+        if (st->cap_binds && !small) st->capped = 1;
+        break;
+      }
+      if (small) {
+        int rd = -1;
+        if (check_decision(M1, n_chk, chk_rows, chk_n2t + t, ACA_BMAX, usedr, eps, n2, &rd)) {
+          stop = 1;
+          kend = kk + t + 1;
+          break;
+        }
+        redirect = rd;
+      }
+    }
+    st->normA2 = n2;
+    st->k = kend;
+    const int tl = kend - kk - 1;
+    for (int q = 0; q < n_chk; ++q) chk_n2[q] = chk_n2t[q * ACA_BMAX + tl];
+    if (stop) st->done = 1;
+    else if (redirect >= 0) usedr[redirect] = 1;
+    stop_s = stop;
+    redirect_s = redirect;
+    kend_s = kend;
+  }
+  __syncthreads();
+  if (stop_s) {
+    if (tid == 0 && use_cond) cudaGraphSetConditional(loop, 0);
+    return;
+  }
+  const int kend = kend_s;
+  const int room = kmax - kend;
+  const int nsel = (b < room ? b : room) - (redirect_s >= 0 ? 1 : 0);
+  pick_rows(Ua + (long long)(kend - 1) * M1, M1, usedr, nsel, next_s, &nnext_s);
+  if (tid == 0) {
+    int n = 0;
+    if (redirect_s >= 0) pivI[kend + n++] = redirect_s;
+    for (int q = 0; q < nnext_s; ++q) pivI[kend + n++] = next_s[q];
+    st->nrows = n;
+    if (n == 0) st->done = 1;
+    if (use_cond) cudaGraphSetConditional(loop, n > 0 ? 1 : 0);
+  }
+}
 }  // namespace
 
 // One cross-approximation step: row fibre with residual, column pivot and v_k, column
@@ -481,15 +792,84 @@ slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int
   return SLAR_OK;
 }
 
+// One block cross-approximation step: the block's row fibres (residual against the k
+// previous terms), the pivots in them, the accepted column fibres, forward substitution,
+// and the post kernel (dots, check rows, stop test, next rows).  Reads k, the rows and the
+// counts from the device state.
+slar_status aca_block_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int use_cond, bool prof) {
+  cudaStream_t s = c->s;
+  const int M1 = c->M1, M2 = c->M2;
+  const int b = c->cfg.aca_block;
+  const int nbu = (M1 + DOT_SEG - 1) / DOT_SEG, nbv = (M2 + DOT_SEG - 1) / DOT_SEG;
+  const int ldp = ACA_BMAX * (SLAR_MAX_RANK + ACA_BMAX) + 1;
+  EvalArgs ar{};
+  ar.mode = EVAL_ROW;
+  ar.n = (long long)b * M2;
+  ar.nper = M2;
+  ar.nact = &c->ast->nrows;
+  ar.pivot = c->pivI;
+  ar.kidx = &c->ast->k;
+  ar.out_stride = 0;
+  ar.done = &c->ast->done;
+  ar.X = c->Ua;
+  ar.ldX = M1;
+  ar.Y = c->Va;
+  ar.ldY = M2;
+  ar.out = c->rowbuf;
+  EvalArgs ac = ar;
+  ac.mode = EVAL_COL;
+  ac.n = (long long)b * M1;
+  ac.nper = M1;
+  ac.nact = &c->ast->nact;
+  ac.pivot = c->pivJ;
+  ac.X = c->Va;
+  ac.ldX = M2;
+  ac.Y = c->Ua;
+  ac.ldY = M1;
+  ac.out = c->Ua;
+  ac.out_stride = M1;
+  ac.skip = &c->ast->skip;
+  const bool f32 = c->cfg.precision != SLAR_FP64;
+  const bool tc = c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4;
+  for (int pass = 0; pass < 2; ++pass) {
+    const EvalArgs& a = pass == 0 ? ar : ac;
+    const bool ev = prof && c->prof_n * 2 + 1 < kProfEvents;
+    if (ev) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], s));
+    cudaError_t e =
+        tc ? launch_sl_eval_tc_dev(c->g, static_cast<const EvalParams<float>*>(c->evp), a, c->tc_b12, c->tc_b34,
+                                   &c->ast->tc_err, smem, s)
+        : f32 ? launch_sl_eval_dev<float>(c->g, static_cast<const EvalParams<float>*>(c->evp), a, smem, s,
+                                          c->eval_tile)
+              : launch_sl_eval_dev<double>(c->g, static_cast<const EvalParams<double>*>(c->evp), a, smem, s,
+                                           c->eval_tile);
+    CK(e);
+    if (ev) {
+      CK(cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], s));
+      c->prof_n++;
+    }
+    if (pass == 0)
+      slar::count_launch(), k_aca_block_pivot<<<1, PIV_THREADS, 0, s>>>(
+          c->rowbuf, M1, M2, c->usedc, c->usedr, c->pivI, c->pivJ, c->ast, c->Va, c->Ua, c->n_chk, c->chk_rows,
+          c->chk_n2, b, c->kmax);
+  }
+  slar::count_launch(), k_aca_block_fsub<<<(M1 + 255) / 256, 256, 0, s>>>(c->Ua, M1, c->Va, M2, c->pivJ, c->ast);
+  slar::count_launch(), k_aca_block_post<<<nbu + nbv + c->n_chk, 256, 0, s>>>(
+      c->Ua, M1, c->Va, M2, c->kmax, nbu, nbv, c->aca_part, ldp, c->ast, c->pivI, c->usedr, c->n_chk, c->chk_rows,
+      c->chk_R, c->chk_n2, c->chk_n2t, b, h, use_cond);
+  CK(cudaGetLastError());
+  return SLAR_OK;
+}
+
 // Capture one cross-approximation step (row fibre, column pivot, column fibre, dot products,
 // stop test / next row pivot) as the body of a WHILE conditional node.  The body reads the
 // step index from the device state and the evaluator parameters from c->evp.
-slar_status build_aca_graph(slar_ctx* c, size_t smem) {
+slar_status build_aca_graph(slar_ctx* c, size_t smem, bool block) {
   CaptureScope scope(c);
   cudaStream_t s = c->s;
-  if (c->aca_graph) {
-    CK(cudaGraphExecDestroy(c->aca_graph));
-    c->aca_graph = nullptr;
+  cudaGraphExec_t& ge = block ? c->aca_graph_blk : c->aca_graph;
+  if (ge) {
+    CK(cudaGraphExecDestroy(ge));
+    ge = nullptr;
   }
   const long long l0 = launch_count();
   cudaGraph_t gl;
@@ -507,16 +887,22 @@ slar_status build_aca_graph(slar_ctx* c, size_t smem) {
   CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   // two pivot steps per loop iteration: the second one's kernels exit at once when the first
   // has stopped the approximation (device flag), and both report the stop to the WHILE node
-  for (int u = 0; u < ACA_UNROLL; ++u) CKS(aca_step(c, smem, h, 1, false));
+  for (int u = 0; u < ACA_UNROLL; ++u) CKS(block ? aca_block_step(c, smem, h, 1, false) : aca_step(c, smem, h, 1, false));
   cudaGraph_t body_out;
   CK(cudaStreamEndCapture(s, &body_out));
-  CK(cudaGraphInstantiate(&c->aca_graph, gl, 0));
+  CK(cudaGraphInstantiate(&ge, gl, 0));
   CK(cudaGraphDestroy(gl));
   const long long l1 = launch_count();
-  c->aca_graph_nodes = l1 - l0;
   add_launches(-(l1 - l0));
-  c->aca_graph_smem = smem;
-  c->aca_graph_tile = c->eval_tile;
+  if (block) {
+    c->aca_graph_blk_nodes = l1 - l0;
+    c->aca_graph_blk_smem = smem;
+    c->aca_graph_blk_tile = c->eval_tile;
+  } else {
+    c->aca_graph_nodes = l1 - l0;
+    c->aca_graph_smem = smem;
+    c->aca_graph_tile = c->eval_tile;
+  }
   return SLAR_OK;
 }
 
@@ -644,9 +1030,15 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
     P->foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
   }
   CK(cudaMemcpyAsync(c->evp, c->evp_host, sizeof(EvalParams<double>), cudaMemcpyHostToDevice, s));
+  const bool block = !replay && c->cfg.aca_block > 1;
   slar::count_launch(), k_aca_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->usedr, replay ? 1 : 0, c->cfg.eps,
                                                     kmax < std::min(M1, M2) ? 1 : 0);
   CK(cudaGetLastError());
+  if (block) {
+    slar::count_launch(), k_aca_block_init<<<1, 32, 0, s>>>(c->ast, c->pivI, c->chk_rows, c->n_chk,
+                                                            c->cfg.aca_block, kmax);
+    CK(cudaGetLastError());
+  }
   long long chk_entries = 0;
   if (!replay && c->n_chk > 0) {
     // residuals of the check rows start as the rows themselves (this also fixes the tile)
@@ -657,8 +1049,11 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
                          : f32 ? sl_eval_smem<float>(c->g, hin.r, c->eval_tile)
                                : sl_eval_smem<double>(c->g, hin.r, c->eval_tile);
   const bool prof = (c->cfg.flags & SLAR_PROFILE_EVAL) != 0;
-  if (!prof && (!c->aca_graph || need > c->aca_graph_smem || c->aca_graph_tile != c->eval_tile))
-    CKS(build_aca_graph(c, need));
+  if (!prof && !block && (!c->aca_graph || need > c->aca_graph_smem || c->aca_graph_tile != c->eval_tile))
+    CKS(build_aca_graph(c, need, false));
+  if (!prof && block &&
+      (!c->aca_graph_blk || need > c->aca_graph_blk_smem || c->aca_graph_blk_tile != c->eval_tile))
+    CKS(build_aca_graph(c, need, true));
   if (prof) {
     // individually launched steps with events around the evaluator (roofline timing)
     // bounded like the WHILE loop: each step adds a term (at most kmax) or consumes a check
@@ -667,10 +1062,10 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
       CK(cudaMemcpyAsync(c->ast_host, c->ast, sizeof(AcaState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (c->ast_host->done) break;   // where the WHILE node would stop
-      CKS(aca_step(c, need, 0, 0, true));
+      CKS(block ? aca_block_step(c, need, 0, 0, true) : aca_step(c, need, 0, 0, true));
     }
   } else {
-    CK(cudaGraphLaunch(c->aca_graph, s));
+    CK(cudaGraphLaunch(block ? c->aca_graph_blk : c->aca_graph, s));
   }
   CK(cudaMemcpyAsync(c->ast_host, c->ast, sizeof(AcaState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -678,12 +1073,21 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
   if (c->ast_host->capped) c->rank_capped++;
   if (c->ast_host->tc_err)
     return set_error(c, SLAR_ETIMEOUT, "tensor-core evaluator: an MMA completion wait ran out");
-  // rows sampled without a term: negligible rows, and a vanishing first row
-  const int extra_rows = c->ast_host->n_skip + c->ast_host->stop_row;
-  if (!prof)
-    add_launches(c->aca_graph_nodes * (long long)((k + extra_rows + ACA_UNROLL - 1) / ACA_UNROLL));
+  long long nent;
+  if (block) {
+    // every sampled fibre counts, including the rows and columns of terms a stop dropped
+    const int rows = c->ast_host->rows_sampled, cols = c->ast_host->cols_sampled;
+    if (!prof)
+      add_launches(c->aca_graph_blk_nodes * (long long)((c->ast_host->nsteps + ACA_UNROLL - 1) / ACA_UNROLL));
+    nent = (long long)rows * M2 + (long long)cols * M1 + chk_entries;
+  } else {
+    // rows sampled without a term: negligible rows, and a vanishing first row
+    const int extra_rows = c->ast_host->n_skip + c->ast_host->stop_row;
+    if (!prof)
+      add_launches(c->aca_graph_nodes * (long long)((k + extra_rows + ACA_UNROLL - 1) / ACA_UNROLL));
+    nent = (long long)k * (M1 + M2) + (long long)extra_rows * M2 + chk_entries;
+  }
   if (aca_rank) *aca_rank = k;
-  const long long nent = (long long)k * (M1 + M2) + (long long)extra_rows * M2 + chk_entries;
   if (entries) *entries = nent;
   c->prof_flop += (double)nent * entry_flops(c, in);
   if (k == 0) return set_error(c, SLAR_ENAN, "cross approximation found no pivot (zero tensor)");

@@ -71,6 +71,9 @@ slar_status validate(const slar_config* cfg, char* msg, size_t len) {
   if (cfg->krylov_restart < 1 || cfg->krylov_restart > 64) {
     snprintf(msg, len, "krylov_restart must be in [1, 64]"); return SLAR_EINVAL;
   }
+  if (cfg->aca_block < 0 || cfg->aca_block > ACA_BMAX) {
+    snprintf(msg, len, "aca_block must be in [0, %d]", ACA_BMAX); return SLAR_EINVAL;
+  }
   return SLAR_OK;
 }
 
@@ -86,7 +89,8 @@ void free_ctx(slar_ctx* c) {
   F(c->dC); F(c->qv); F(c->dC32); F(c->qv32); F(c->E32); F(c->Uc); F(c->Uh1); F(c->Uh2);
   F(c->Ua); F(c->Va); F(c->rowbuf); F(c->usedr); F(c->usedc); F(c->pivI); F(c->pivJ);
   F(c->ast); F(c->aca_part); F(c->aca_dots);
-  F(c->chk_rows); F(c->chk_idx); F(c->chk_R); F(c->chk_n2);
+  F(c->chk_rows); F(c->chk_idx); F(c->chk_R); F(c->chk_n2); F(c->chk_n2t);
+  if (c->aca_graph_blk) cudaGraphExecDestroy(c->aca_graph_blk);
   if (c->ast_host) cudaFreeHost(c->ast_host);
   if (c->evp) cudaFree(c->evp);
   if (c->evp_host) cudaFreeHost(c->evp_host);
@@ -203,14 +207,16 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   A(c->Uh2, (size_t)(c->dv + 2) * c->NX);
   A(c->Ua, (size_t)c->M1 * c->kmax);
   A(c->Va, (size_t)c->M2 * c->kmax);
-  A(c->rowbuf, (size_t)c->M2);
+  A(c->rowbuf, (size_t)ACA_BMAX * c->M2);
   A(c->usedr, (size_t)c->M1);
   A(c->usedc, (size_t)c->M2);
   A(c->pivI, (size_t)c->kmax);
   A(c->pivJ, (size_t)c->kmax);
   A(c->ast, 1);
   const int nbu = (c->M1 + 255) / 256, nbv = (c->M2 + 255) / 256;
-  A(c->aca_part, (size_t)(nbu + nbv) * (R + 1));
+  // partial sums of the cross-approximation post kernels: per block of rows, R + 1 slots
+  // (one-fibre steps) or ACA_BMAX (R + ACA_BMAX) + 1 (block steps)
+  A(c->aca_part, (size_t)(nbu + nbv) * (ACA_BMAX * (R + ACA_BMAX) + 1));
   // check rows of the cross-approximation stop test: distinct floor(frac(c g) M1),
   // g = (sqrt 5 - 1)/2, c = 1, 2, ...; at most 8
   std::vector<int> rows;
@@ -226,6 +232,7 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   A(c->chk_idx, (size_t)c->n_chk * c->M2 * d);
   A(c->chk_R, (size_t)c->n_chk * c->M2);
   A(c->chk_n2, (size_t)c->n_chk);
+  A(c->chk_n2t, (size_t)c->n_chk * ACA_BMAX);
   A(c->T1, (size_t)capB); A(c->T2, (size_t)capB); A(c->T3, (size_t)capB);
   A(c->Q12, (size_t)capB); A(c->Q34, (size_t)capB);
   A(c->Rn[0], (size_t)R * R); A(c->Rn[1], (size_t)R * R);

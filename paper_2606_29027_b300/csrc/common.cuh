@@ -61,6 +61,11 @@ struct EvalArgs {
   const int* pivot;      // EVAL_ROW: device pointer to the row pivot; EVAL_COL: to the column pivot
   const int* done;       // optional device flag: when non-zero the launch does nothing
   const int* skip;       // optional second flag with the same effect
+  int nper;              // EVAL_ROW / EVAL_COL with a block of fibres: entries per fibre
+                         //   (0: one fibre at *pivot); entry e is element e % nper of the
+                         //   fibre at pivot[e / nper]
+  const int* nact;       // optional device count of active fibres of the block (entries of
+                         //   fibres >= *nact are not evaluated)
   int kterms;            // number of residual terms l < kterms
   const int* kidx;       // optional device iteration index kk: pivot += kk, kterms = kk,
   long long out_stride;  //   out += kk * out_stride (cross-approximation graph)

@@ -44,7 +44,15 @@ struct AcaState {
   double piv0;    // |first pivot|: the scale of the negligible-row test
   int skip;       // the current row was negligible: no term this step
   int n_skip;     // negligible rows sampled in this call
+  // block cross approximation
+  int nrows;      // rows of the current block, at pivI[k .. k + nrows)
+  int nact;       // pivots accepted in the current block (columns sampled)
+  int rows_sampled;  // row and column fibres sampled by the block steps of this call
+  int cols_sampled;
+  int nsteps;        // block steps run in this call
 };
+
+constexpr int ACA_BMAX = 8;   // largest block of the block cross approximation
 
 }  // namespace slar
 
@@ -120,6 +128,11 @@ struct slar_ctx {
   int* chk_idx = nullptr;      // [n_chk * M2][d] index tuples of the check rows
   double* chk_R = nullptr;     // [n_chk][M2] residual rows
   double* chk_n2 = nullptr;    // [n_chk] their squared norms
+  double* chk_n2t = nullptr;   // [n_chk][ACA_BMAX] the norms after each term of a block
+  cudaGraphExec_t aca_graph_blk = nullptr;   // the block cross-approximation loop
+  size_t aca_graph_blk_smem = 0;
+  long long aca_graph_blk_nodes = 0;
+  int aca_graph_blk_tile = 0;
 
   // truncation workspaces
   double* Qleaf[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -215,8 +228,9 @@ slar_status refresh_f32_slot(slar_ctx* c, int slot);
 // FP32 copies of the field E (if given) and of the LoMaC correction (if with_corr) for the
 // FP32 / BF16x3 evaluators; nothing in FP64 mode
 slar_status refresh_f32_fields(slar_ctx* c, const double* E, bool with_corr);
-slar_status build_aca_graph(slar_ctx* c, size_t smem);
+slar_status build_aca_graph(slar_ctx* c, size_t smem, bool block);
 slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int use_cond, bool prof);
+slar_status aca_block_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int use_cond, bool prof);
 
 // Redirects the context's launches to its capture stream while a CUDA graph is recorded
 // (capture is not possible on the legacy default stream a caller may pass).

@@ -186,8 +186,12 @@ __device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& 
       if (m < g.d) idx[m] = a.idx[e * g.d + m];
     return;
   }
-  const long long left = (a.mode == EVAL_ROW) ? (long long)(*a.pivot) : e;
-  const long long right = (a.mode == EVAL_ROW) ? e : (long long)(*a.pivot);
+  // one fibre at *pivot, or fibre e / nper of a block at pivot[e / nper]
+  const long long fib = a.nper ? e / a.nper : 0;
+  const long long within = a.nper ? e - fib * a.nper : e;
+  const long long piv = (long long)a.pivot[fib];
+  const long long left = (a.mode == EVAL_ROW) ? piv : within;
+  const long long right = (a.mode == EVAL_ROW) ? within : piv;
   if (g.d == 2) {
     idx[0] = (int)left;
     idx[1] = (int)right;

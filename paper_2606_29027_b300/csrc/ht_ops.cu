@@ -280,13 +280,14 @@ slar_status truncate_into(slar_ctx* c, const TruncIn& in, double eps, int cap, i
   // tridiagonal solver above rank 40).  FP32 / BF16x3 data: the dropped trace is 1/10 of the
   // rank threshold.  FP64 data: 1e-16 of the trace, the rounding level of a Gram matrix --
   // the eigenvalues dropped there are the ones a dense solver (LAPACK's, the oracle's) also
-  // resolves only to about u ||G||, and the kept eigenvectors move by ~u ||G|| / gap, far
-  // below the FP64 parity bar at any rank threshold eps^2 / (2d - 3) >= 1e-14.
+  // resolves only to about u ||G||, and the kept eigenvectors move by ~u ||G|| / gap: the
+  // truncated tensor by ~u / sqrt(threshold) of ||F||, at most 1e-10 (a tenth of the FP64
+  // parity bar) for the rank thresholds eps^2 / (2d - 3) >= 1e-12 it is used at.
   const double thr_rel = eps * eps / (2.0 * d - 3.0);
   const bool fp64 = c->cfg.precision == SLAR_FP64;
   auto compress_rel_of = [&](int n) {
     if (n <= 24) return 0.0;
-    if (fp64) return thr_rel >= 1e-14 ? 1e-16 : 0.0;
+    if (fp64) return thr_rel >= 1e-12 ? 1e-16 : 0.0;
     return std::max(1e-16, 0.1 * thr_rel);
   };
   for (int m = 0; m < d; ++m) {

@@ -295,8 +295,10 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
     a.out += kk * a.out_stride;
   }
   const long long e0 = (long long)blockIdx.x * TILE;
-  if (e0 >= a.n) return;
-  const int nT = (int)min((long long)TILE, a.n - e0);
+  // a block of fibres evaluates only its *nact active fibres
+  const long long n_act = a.nact ? min(a.n, (long long)(*a.nact) * a.nper) : a.n;
+  if (e0 >= n_act) return;
+  const int nT = (int)min((long long)TILE, n_act - e0);
   const int tid = threadIdx.x;
   const int d = g.d;
 
@@ -331,8 +333,11 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
       const int t = tid - TILE;
       double r = 0.0;
       if (t < nT) {
-        const long long piv = (long long)(*a.pivot);
-        const long long e = e0 + t;
+        // residual of fibre element `e` against the k previous terms: X at the fibre's pivot,
+        // Y at the element's position along the fibre
+        const long long fib = a.nper ? (e0 + t) / a.nper : 0;
+        const long long piv = (long long)a.pivot[fib];
+        const long long e = a.nper ? (e0 + t) - fib * a.nper : e0 + t;
         const int k = a.kterms;
         int l = 0;
         for (; l + 4 <= k; l += 4) {

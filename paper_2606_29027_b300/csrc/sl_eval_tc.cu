@@ -345,8 +345,10 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     a.out += kk * a.out_stride;
   }
   const long long e0 = (long long)blockIdx.x * TC_TILE;
-  if (e0 >= a.n) return;
-  const int nT = (int)min((long long)TC_TILE, a.n - e0);
+  // a block of fibres evaluates only its *nact active fibres
+  const long long n_act = a.nact ? min(a.n, (long long)(*a.nact) * a.nper) : a.n;
+  if (e0 >= n_act) return;
+  const int nT = (int)min((long long)TC_TILE, n_act - e0);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TcLayout L = tc_layout(ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34);
   float* sfoot = reinterpret_cast<float*>(smem_raw);                 // 128 x 4
@@ -596,8 +598,10 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
       if (corr.has) val += (double)correction_rw_ft<2>(g, corr, srow + tid * 12, sw + tid * 12);
       const long long e = e0 + tid;
       if (a.X) {
-        const long long piv = (long long)(*a.pivot);
-        for (int l = 0; l < a.kterms; ++l) val -= a.X[piv + l * a.ldX] * a.Y[e + l * a.ldY];
+        const long long fib = a.nper ? e / a.nper : 0;
+        const long long piv = (long long)a.pivot[fib];
+        const long long ey = a.nper ? e - fib * a.nper : e;
+        for (int l = 0; l < a.kterms; ++l) val -= a.X[piv + l * a.ldX] * a.Y[ey + l * a.ldY];
       }
       a.out[e] = val;
     }

@@ -39,7 +39,7 @@ class Config(C.Structure):
                 ("hi", C.c_double * 4), ("eps", C.c_double), ("rank_cap", C.c_int),
                 ("newton_tol", C.c_double), ("krylov_tol", C.c_double), ("krylov_restart", C.c_int),
                 ("newton_max", C.c_int), ("krylov_max", C.c_int), ("precision", C.c_int),
-                ("flags", C.c_int), ("delta_floor", C.c_double)]
+                ("flags", C.c_int), ("delta_floor", C.c_double), ("aca_block", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -197,7 +197,8 @@ def _dptr(a: np.ndarray):
 def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, eps=1e-6, rank_cap=16,
                 newton_tol=1e-12, krylov_tol=1e-4, krylov_restart=30, newton_max=20, krylov_max=200,
                 precision="fp64", lomac=True, foot="rk3", delta_floor=1e-12, profile=False,
-                profile_eval=False, solver="plain", autotune=True, own_stream=False) -> Config:
+                profile_eval=False, solver="plain", autotune=True, own_stream=False,
+                aca_block=1) -> Config:
     """solver: "plain" (the paper's JFNK), "precond" (block-circulant preconditioner) or
     "learned" (network warm start; attach a network with Context.attach_net)."""
     if workload is not None:
@@ -220,6 +221,7 @@ def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, ep
                  | {"plain": 0, "precond": SLAR_PRECOND, "learned": SLAR_LEARNED}[solver]
                  | (0 if autotune else SLAR_NO_AUTOTUNE) | (SLAR_OWN_STREAM if own_stream else 0))
     cfg.delta_floor = delta_floor
+    cfg.aca_block = int(aca_block)
     return cfg
 
 
