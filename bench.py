@@ -57,6 +57,11 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=None,
                    help="steps of the comparison forms (default: --steps, the same steps as the headline)")
     p.add_argument("--solver", default="precond", choices=["learned", "precond", "plain"])
+    p.add_argument("--aca-block", type=int, default=2,
+                   help="fibres per cross-approximation step of the headline form (1: partial "
+                        "pivoting; 2..8: block cross approximation)")
+    p.add_argument("--block-forms", default="2,4,8",
+                   help="block sizes timed as extra forms of the headline precision and solver")
     p.add_argument("--c1-steps", type=int, default=200,
                    help="steps of the 1D-1V weak Landau workload timed in microseconds per step "
                         "(0 skips it)")
@@ -286,10 +291,10 @@ def run_ours(args, w):
     if args.solver == "learned" and net is None:
         raise SystemExit("--solver learned needs the trained network (--train-iters > 0)")
 
-    def make(precision, profile, profile_eval=False, solver=None, wl=None):
+    def make(precision, profile, profile_eval=False, solver=None, wl=None, block=None):
         solver = args.solver if solver is None else solver
         cfg = slar.make_config(wl or w, precision=precision, profile=profile, profile_eval=profile_eval,
-                               solver=solver)
+                               solver=solver, aca_block=args.aca_block if block is None else block)
         c = slar.Context(cfg, stream=stream)
         if solver == "learned":
             c.attach_net(net)
@@ -337,9 +342,9 @@ def run_ours(args, w):
     del ctx
 
     # ---- the other forms on the same steps ----
-    def short_run(precision, solver, K, eps=None, cap=None):
+    def short_run(precision, solver, K, eps=None, cap=None, block=1):
         if eps is None:
-            cc = make(precision, True, solver=solver)
+            cc = make(precision, True, solver=solver, block=block)
         else:
             cfg = slar.make_config(w, precision=precision, profile=True, solver=solver)
             cfg.eps, cfg.rank_cap = eps, cap
@@ -364,7 +369,7 @@ def run_ours(args, w):
                 "phase_ms_per_step": {nm: sum(s.phase_ms[i] for s in stk[-K:]) / K
                                       for i, nm in enumerate(phase_names)}}
 
-    head_key = f"{args.precision}_{args.solver}"
+    head_key = f"{args.precision}_{args.solver}" + (f"_b{args.aca_block}" if args.aca_block > 1 else "")
     forms = {}
     W_hist = {head_key: np.array([s.field_energy for s in (warm_stats + stats)])}
     Kh = args.steps
@@ -372,12 +377,15 @@ def run_ours(args, w):
     K = args.steps if args.fp64_steps is None else args.fp64_steps
     acc = None
     if K > 0:
-        wanted = [("fp64", "plain"), ("fp32", "precond")] + ([("fp32", "learned")] if net is not None else [])
-        for prec, solver in wanted:
-            key = f"{prec}_{solver}"
-            if key == head_key:
+        wanted = [("fp64", "plain", 1), ("fp32", "precond", 1)] + ([("fp32", "learned", 1)] if net is not None else [])
+        wanted += [(args.precision, args.solver, int(b)) for b in args.block_forms.split(",") if b and int(b) > 1]
+        if args.aca_block > 1:
+            wanted.append((args.precision, args.solver, 1))
+        for prec, solver, blk in wanted:
+            key = f"{prec}_{solver}" + (f"_b{blk}" if blk > 1 else "")
+            if key == head_key or key in forms:
                 continue
-            msk, stk = short_run(prec, solver, K)
+            msk, stk = short_run(prec, solver, K, block=blk)
             forms[key] = summary(msk, stk, K)
             W_hist[key] = np.array([s.field_energy for s in stk])
         em64, ef64, _ = eval_roofline("fp64", "plain", 2)
@@ -585,7 +593,7 @@ def profile_step(args, w):
     from paper_2606_29027_b300 import inputs, slar
     # autotuner off: launch counts (ncu -s / -c) must not depend on timings
     ctx = slar.Context(slar.make_config(w, precision=args.precision, profile_eval=True, solver=args.solver,
-                                        autotune=False))
+                                        autotune=False, aca_block=args.aca_block))
     if args.solver == "learned":
         # untrained parameters: the same kernels and launch structure as the trained network
         from paper_2606_29027_b300 import warmstart
