@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp32", "fp64", "bf16x3"],
+    p.add_argument("--precision", default="fp64", choices=["fp32", "fp64", "bf16x3", "bf16x6"],
                    help="entry precision of the headline run (bf16x3: 2D2V workloads, "
                         "--profile-step only)")
     p.add_argument("--workload", default="landau_2d2v")
@@ -73,7 +73,7 @@ def parse():
     p.add_argument("--ensemble-runs", type=int, default=64)
     p.add_argument("--ensemble-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--profile-eval", default=None, choices=["fp64", "fp32", "bf16x3"],
+    p.add_argument("--profile-eval", default=None, choices=["fp64", "fp32", "bf16x3", "bf16x6"],
                    help="evaluator microbenchmark: one warm-up and one measured sl_eval launch on "
                         "a random 2D2V HT (--eval-rank, --eval-n points per dimension, "
                         "--eval-entries tuples), for ncu captures of the evaluator kernels")
@@ -426,15 +426,15 @@ def run_ours(args, w):
         del c1c
 
     # ---- the 128^4 configurations (strong Landau, two-stream, and the 2D-2V bump-on-tail
-    # example of Sec. 4.2 at its eps 1e-4 and a CFL-5 step): FP32 SIMT entries vs BF16x3
-    # tensor-core entries ----
+    # example of Sec. 4.2 at its eps 1e-4 and a CFL-5 step): FP32 SIMT entries vs BF16x3 and
+    # BF16x6 tensor-core entries ----
     large = None
     if args.large_steps > 0:
         large = {}
         for wname in ("strong_landau_2d2v", "two_stream_2d2v", "bump_on_tail_2d2v"):
             wl = inputs.workload_by_name(wname)
             res = {}
-            for prec in ("fp32", "bf16x3"):
+            for prec in ("fp32", "bf16x3", "bf16x6"):
                 cl = slar.Context(slar.make_config(wl, precision=prec, solver="precond", profile=True), stream=stream)
                 with torch.cuda.stream(stream):
                     cl.init_ht(inputs.initial_factors(wl))
@@ -451,6 +451,7 @@ def run_ours(args, w):
                              "ranks_last": list(stl[-1].ranks), "W_last": stl[-1].field_energy}
                 del cl
             res["speedup_bf16x3"] = res["bf16x3"]["value"] / res["fp32"]["value"]
+            res["speedup_bf16x6"] = res["bf16x6"]["value"] / res["fp32"]["value"]
             res["workload"] = (f"{wl.name}: alpha {wl.alpha}, k {wl.k}, rank cap {wl.rank_cap}, eps {wl.eps}, "
                                f"dt {wl.dt}; block-circulant preconditioner; {args.large_steps} BDF3 steps "
                                f"after the DIRK3 start-up")
@@ -525,17 +526,18 @@ def run_ours(args, w):
                           "median of 3 launches after one warm-up",
               "flop_per_entry": 2 * (3 * 4 * 64 + 2 * 64 ** 3 + 64 * 64) + 60}
     for prec, pk, src in (("fp32", peak32, "measured FP32 FMA peak (this run)"),
-                          ("bf16x3", bf16 / 3.0, bf16_src + " / 3 (three BF16 products per K-step)")):
+                          ("bf16x3", bf16 / 3.0, bf16_src + " / 3 (three BF16 products per K-step)"),
+                          ("bf16x6", bf16 / 6.0, bf16_src + " / 6 (six BF16 products per K-step)")):
         ms64, tf64 = eval_launch(prec, 64, 128, 65536, reps=3)
         eval64[prec] = {"kernel": "k_sl_eval<float> (GEMM contraction)" if prec == "fp32"
-                        else "k_sl_eval_tc (tcgen05, BF16x3)",
+                        else f"k_sl_eval_tc (tcgen05, {prec.upper()})",
                         "ms": ms64, "tflops": tf64, "peak_tflops": pk, "frac": tf64 / pk, "peak_source": src}
     achieved = eval_flop / max(eval_ms, 1e-9) / 1e9          # TFLOP/s
     traffic = EVAL_TRAFFIC_BYTES.get(args.precision)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3"}[args.precision], "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}[args.precision], "data": "synthetic",
             "config": workload_config(w, args.precision, args.solver),
             "entries_per_s": entries / (tot_ms / 1000.0) * world,
             "entries_per_step": entries / args.steps,
@@ -675,9 +677,9 @@ def main():
     if args.profile_step:
         profile_step(args, w)
         return
-    if args.precision == "bf16x3":
-        raise SystemExit("--precision bf16x3 is for --profile-step; the benchmark reports BF16x3 "
-                         "in its 128^4 and eval_rank64 sections")
+    if args.precision in ("bf16x3", "bf16x6"):
+        raise SystemExit(f"--precision {args.precision} is for --profile-step; the benchmark reports the "
+                         "tensor-core splits in its 128^4 and eval_rank64 sections")
     if args.impl == "reference":
         run_reference(args, w)
     else:

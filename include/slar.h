@@ -51,8 +51,11 @@ enum {
    SLAR_FP32_BF16X3: FP32 gathers, transfer-tensor contractions of d = 4 trees on the tensor
    cores (tcgen05, operands split x = hi + lo into BF16, three products hi.hi + hi.lo +
    lo.hi accumulated in FP32; about 2^-16 relative per product), 128 entries per CTA;
-   d = 2 trees use the FP32 path. */
-enum { SLAR_FP64 = 0, SLAR_FP32 = 1, SLAR_FP32_BF16X3 = 2 };
+   d = 2 trees use the FP32 path.
+   SLAR_FP32_BF16X6: as SLAR_FP32_BF16X3 with the operands split x = x1 + x2 + x3 into three
+   BF16 pieces and the six products x1.y1 + x1.y2 + x2.y1 + x1.y3 + x3.y1 + x2.y2 (about
+   2^-24 relative per product, the FP32 evaluator's accuracy), twice the MMAs of BF16x3. */
+enum { SLAR_FP64 = 0, SLAR_FP32 = 1, SLAR_FP32_BF16X3 = 2, SLAR_FP32_BF16X6 = 3 };
 
 /* flags */
 enum {

@@ -763,14 +763,14 @@ slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int
   ac.out_stride = M1;
   ac.skip = &c->ast->skip;   // no column fibre after a negligible row
   const bool f32 = c->cfg.precision != SLAR_FP64;
-  const bool tc = c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4;
+  const int tc = tc_pieces(c);
   for (int pass = 0; pass < 2; ++pass) {
     const EvalArgs& a = pass == 0 ? ar : ac;
     const bool ev = prof && c->prof_n * 2 + 1 < kProfEvents;
     if (ev) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], s));
     cudaError_t e =
         tc ? launch_sl_eval_tc_dev(c->g, static_cast<const EvalParams<float>*>(c->evp), a, c->tc_b12, c->tc_b34,
-                                   &c->ast->tc_err, smem, s)
+                                   &c->ast->tc_err, tc, smem, s)
         : f32 ? launch_sl_eval_dev<float>(c->g, static_cast<const EvalParams<float>*>(c->evp), a, smem, s,
                                           c->eval_tile)
               : launch_sl_eval_dev<double>(c->g, static_cast<const EvalParams<double>*>(c->evp), a, smem, s,
@@ -830,14 +830,14 @@ slar_status aca_block_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle 
   ac.out_stride = M1;
   ac.skip = &c->ast->skip;
   const bool f32 = c->cfg.precision != SLAR_FP64;
-  const bool tc = c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4;
+  const int tc = tc_pieces(c);
   for (int pass = 0; pass < 2; ++pass) {
     const EvalArgs& a = pass == 0 ? ar : ac;
     const bool ev = prof && c->prof_n * 2 + 1 < kProfEvents;
     if (ev) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], s));
     cudaError_t e =
         tc ? launch_sl_eval_tc_dev(c->g, static_cast<const EvalParams<float>*>(c->evp), a, c->tc_b12, c->tc_b34,
-                                   &c->ast->tc_err, smem, s)
+                                   &c->ast->tc_err, tc, smem, s)
         : f32 ? launch_sl_eval_dev<float>(c->g, static_cast<const EvalParams<float>*>(c->evp), a, smem, s,
                                           c->eval_tile)
               : launch_sl_eval_dev<double>(c->g, static_cast<const EvalParams<double>*>(c->evp), a, smem, s,
@@ -941,7 +941,7 @@ slar_status eval_check_rows(slar_ctx* c, int in, bool with_corr, double tau, con
   a.tau = tau;
   a.E = E;
   a.foot_euler = (c->cfg.flags & SLAR_FOOT_EULER) ? 1 : 0;
-  if (c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4) {
+  if (tc_pieces(c) > 0) {
     c->eval_tile = 128;   // the tensor-core evaluator's fixed MMA tile
     return eval_entries(c, in, with_corr, a, 0);
   }
@@ -1010,7 +1010,7 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
   // per-call evaluator parameters in device memory, read by the captured graph
   const HTBuf& hin = c->ht[in];
   const bool f32 = c->cfg.precision != SLAR_FP64;
-  const bool tc = c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4;
+  const int tc = tc_pieces(c);
   if (f32) CKS(refresh_f32_slot(c, in));
   if (f32) CKS(refresh_f32_fields(c, E, with_corr));
   if (f32) {
@@ -1045,7 +1045,7 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
     CKS(eval_check_rows(c, in, with_corr, tau, E));
     chk_entries = (long long)c->n_chk * M2;
   }
-  const size_t need = tc ? sl_eval_tc_smem(hin.r)
+  const size_t need = tc ? sl_eval_tc_smem(hin.r, tc)
                          : f32 ? sl_eval_smem<float>(c->g, hin.r, c->eval_tile)
                                : sl_eval_smem<double>(c->g, hin.r, c->eval_tile);
   const bool prof = (c->cfg.flags & SLAR_PROFILE_EVAL) != 0;

@@ -61,7 +61,8 @@ slar_status validate(const slar_config* cfg, char* msg, size_t len) {
     snprintf(msg, len, "rank_cap must be in [1, %d]", SLAR_MAX_RANK); return SLAR_EINVAL;
   }
   if (!(cfg->eps >= 0.0)) { snprintf(msg, len, "eps must be >= 0"); return SLAR_EINVAL; }
-  if (cfg->precision != SLAR_FP64 && cfg->precision != SLAR_FP32 && cfg->precision != SLAR_FP32_BF16X3) {
+  if (cfg->precision != SLAR_FP64 && cfg->precision != SLAR_FP32 && cfg->precision != SLAR_FP32_BF16X3 &&
+      cfg->precision != SLAR_FP32_BF16X6) {
     snprintf(msg, len, "unknown precision"); return SLAR_EINVAL;
   }
   if (cfg->flags & ~(SLAR_LOMAC | SLAR_FOOT_EULER | SLAR_PROFILE | SLAR_PROFILE_EVAL | SLAR_PRECOND | SLAR_LEARNED |
@@ -186,9 +187,9 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   }
   if (d == 4) { A(c->B12_32, (size_t)R * R * R); A(c->B34_32, (size_t)R * R * R); }
   A(c->Broot32, (size_t)R * R);
-  if (cfg->precision == SLAR_FP32_BF16X3 && d == 4) {
-    if (cudaMalloc(&c->tc_b12, (size_t)tc_split_bytes()) != cudaSuccess ||
-        cudaMalloc(&c->tc_b34, (size_t)tc_split_bytes()) != cudaSuccess) {
+  if (tc_pieces(c) > 0) {
+    if (cudaMalloc(&c->tc_b12, (size_t)tc_split_bytes(tc_pieces(c))) != cudaSuccess ||
+        cudaMalloc(&c->tc_b34, (size_t)tc_split_bytes(tc_pieces(c))) != cudaSuccess) {
       free_ctx(c);
       return SLAR_ENOMEM;
     }

@@ -107,17 +107,18 @@ size_t sl_eval_smem(const GridDesc& g, const int* ranks6, int tile = 32);
 // opt the evaluator kernels into large dynamic shared memory (call before any capture)
 cudaError_t sl_eval_init_attrs();
 cudaError_t linalg_init_attrs();
-// tensor-core (tcgen05, BF16x3) evaluator for d = 4 trees (sl_eval_tc.cu): 128 entries per
-// CTA; b12 / b34 are the transfer tensors pre-split by split_transfer_bf16 (tc_split_bytes
-// each); err (device int) is set if an MMA completion wait runs out
-size_t sl_eval_tc_smem(const int* ranks6);
-long long tc_split_bytes();
+// tensor-core (tcgen05) evaluator for d = 4 trees (sl_eval_tc.cu): 128 entries per CTA;
+// pieces = 2 (BF16x3) or 3 (BF16x6); b12 / b34 are the transfer tensors pre-split by
+// split_transfer_bf16 with the same piece count (tc_split_bytes(pieces) each); err (device
+// int) is set if an MMA completion wait runs out
+size_t sl_eval_tc_smem(const int* ranks6, int pieces);
+long long tc_split_bytes(int pieces);
 cudaError_t sl_eval_tc_init_attrs();
-cudaError_t split_transfer_bf16(const float* B, int rp, int ra, int rb, void* out, cudaStream_t s);
+cudaError_t split_transfer_bf16(const float* B, int rp, int ra, int rb, void* out, int pieces, cudaStream_t s);
 cudaError_t launch_sl_eval_tc(const GridDesc& g, const HTView<float>& ht, const CorrView& corr, const EvalArgs& a,
-                              const void* b12, const void* b34, int* err, cudaStream_t s);
+                              const void* b12, const void* b34, int* err, int pieces, cudaStream_t s);
 cudaError_t launch_sl_eval_tc_dev(const GridDesc& g, const EvalParams<float>* P, const EvalArgs& a, const void* b12,
-                                  const void* b34, int* err, size_t smem_bytes, cudaStream_t s);
+                                  const void* b34, int* err, int pieces, size_t smem_bytes, cudaStream_t s);
 
 // dense FP64 linear algebra (linalg.cu)
 // C[b] = alpha op(A[b]) op(B[b]) + beta C[b]; row-major; op(A) is M x K.

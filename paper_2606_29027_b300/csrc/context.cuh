@@ -268,6 +268,13 @@ constexpr double kBdf3RatioMax = 1.4877;
 // at kBdf3RatioMax times the previous step (field of the current state)
 slar_status cfl_dt(slar_ctx* c, double cfl, double dt_max, double* dt);
 
+// BF16 pieces of the tensor-core evaluator in this context: 2 (BF16x3), 3 (BF16x6), or 0
+// where entries are evaluated on the CUDA cores (FP64, FP32, and every d = 2 tree)
+inline int tc_pieces(const slar_ctx* c) {
+  if (c->d != 4) return 0;
+  return c->cfg.precision == SLAR_FP32_BF16X3 ? 2 : c->cfg.precision == SLAR_FP32_BF16X6 ? 3 : 0;
+}
+
 }  // namespace slar
 
 #define CK(call)                                               \

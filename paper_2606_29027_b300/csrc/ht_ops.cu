@@ -68,9 +68,9 @@ slar_status refresh_f32_slot(slar_ctx* c, int slot) {
     CK(to_float(h.B12, c->B12_32, (long long)h.r[4] * h.r[0] * h.r[1], c->s));
     CK(to_float(h.B34, c->B34_32, (long long)h.r[5] * h.r[2] * h.r[3], c->s));
     CK(to_float(h.Broot, c->Broot32, (long long)h.r[4] * h.r[5], c->s));
-    if (c->cfg.precision == SLAR_FP32_BF16X3) {
-      CK(split_transfer_bf16(c->B12_32, h.r[4], h.r[0], h.r[1], c->tc_b12, c->s));
-      CK(split_transfer_bf16(c->B34_32, h.r[5], h.r[2], h.r[3], c->tc_b34, c->s));
+    if (tc_pieces(c) > 0) {
+      CK(split_transfer_bf16(c->B12_32, h.r[4], h.r[0], h.r[1], c->tc_b12, tc_pieces(c), c->s));
+      CK(split_transfer_bf16(c->B34_32, h.r[5], h.r[2], h.r[3], c->tc_b34, tc_pieces(c), c->s));
     }
   } else {
     CK(to_float(h.Broot, c->Broot32, (long long)h.r[0] * h.r[1], c->s));
@@ -120,10 +120,10 @@ slar_status eval_entries(slar_ctx* c, int slot, bool with_corr, const EvalArgs& 
   cudaError_t e;
   EvalArgs b = a;
   b.E32 = c->E32;   // refreshed by the caller (refresh_f32_fields)
-  if (c->cfg.precision == SLAR_FP32_BF16X3 && c->d == 4 && !at_grid) {
+  if (tc_pieces(c) > 0 && !at_grid) {
     CKS(refresh_f32_slot(c, slot));
     e = launch_sl_eval_tc(c->g, view32_slot(c, slot), corr_view(c, with_corr), b, c->tc_b12, c->tc_b34,
-                          &c->ast->tc_err, c->s);
+                          &c->ast->tc_err, tc_pieces(c), c->s);
   } else if (c->cfg.precision != SLAR_FP64) {
     CKS(refresh_f32_slot(c, slot));
     e = launch_sl_eval<float>(c->g, view32_slot(c, slot), corr_view(c, with_corr), b, at_grid, c->s, c->eval_tile);

@@ -1,7 +1,11 @@
 // Entry evaluator whose transfer-tensor contractions (Sec. 3.1, the O(d r^3) part of an
 // entry, Eq. tp_interp in HT form) run on the 5th-generation tensor cores: tcgen05.mma,
-// kind::f16 with BF16 operands and FP32 accumulation in tensor memory, in the BF16x3 split
-// x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
+// kind::f16 with BF16 operands and FP32 accumulation in tensor memory, in one of two splits:
+//   BF16x3  x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), a b ~ a_hi b_hi + a_hi b_lo +
+//           a_lo b_hi (three products, the dropped a_lo b_lo ~ 2^-16 |a b|),
+//   BF16x6  x = x1 + x2 + x3 (each the BF16 rounding of what is left), a b ~ the six
+//           products a_i b_j with i + j <= 4 (the dropped ones ~ 2^-24 |a b|, FP32's own
+//           rounding), 128-column chunks becoming 64-column ones (see below).
 // Trees with d = 4 only (a d = 2 tree has no transfer tensor).
 //
 // A transfer node t with children (mu1, mu2) maps the leaf rows c1 = c^(mu1)[e][.],
@@ -12,17 +16,20 @@
 //   c_t[e][p]    = sum_a c1[e][a] T[e][(p, a)]        per-entry dot products on the CUDA
 //                                                      cores, reading T from tensor memory.
 // The columns (p, a) of both nodes (a padded to ra16, a multiple of 16) form one stream of
-// 128-column chunks, each holding an even number of whole p.  Three warp roles run the
-// stream through a 3-stage ring:
-//   warp 9 (one thread)   bulk-copies chunk j's pre-split B tile (hi, lo) into shared slot
-//                         j % 3 once the MMAs of chunk j - 3 have released it,
-//   warp 8 (one thread)   issues chunk j's 3 x K/16 MMAs into tensor-memory slot j % 3 once
-//                         the tile has landed and chunk j - 3 has been read out, and commits
-//                         them to an mbarrier,
-//   warps 0-7             read chunk j out of tensor memory (one 64-column load per warp:
-//                         the warp pair of a lane quadrant splits the chunk's p in halves),
-//                         dot it with c1 held in registers and store c_t[e][p] as a tensor-
-//                         memory column; each warp then arrives on the slot's mbarrier.
+// chunks of W columns (W = 128 for BF16x3, each chunk an even number of whole p; W = 64 for
+// BF16x6, whole p, and at ra16 > 32 one p per chunk).  Three warp roles run the stream
+// through a 3-stage ring:
+//   warp 9 (one thread)   bulk-copies chunk j's pre-split B tile (all pieces) into shared
+//                         slot j % 3 once the MMAs of chunk j - 3 have released it,
+//   warp 8 (one thread)   issues chunk j's 3 (6) x K/16 MMAs into tensor-memory slot j % 3
+//                         once the tile has landed and chunk j - 3 has been read out, and
+//                         commits them to an mbarrier,
+//   warps 0-7             read chunk j out of tensor memory (one load of W/2 columns per
+//                         warp: the warp pair of a lane quadrant splits the chunk's columns
+//                         in halves), dot them with c1 held in registers and store c_t[e][p]
+//                         as a tensor-memory column; each warp then arrives on the slot's
+//                         mbarrier.  A BF16x6 p split across the two halves leaves two
+//                         partial sums, added before the root contraction.
 // c2 of both nodes is the MMA's A operand (gathered and split once per CTA), c1 of the
 // current node sits in registers (the thread's own entry), and c_12, c_34 stay in tensor
 // memory for the root contraction and the correction / residual epilogue of the SIMT
@@ -46,17 +53,28 @@ constexpr int TC_CONSUMERS = 256;        // warps 0-7
 constexpr int TC_MMA_WARP = 8;
 constexpr int TC_COPY_WARP = 9;
 constexpr int TC_THREADS = 320;
-constexpr int TC_W = 128;                // columns of a chunk
 constexpr int TC_STAGES = 3;
-constexpr int TC_TMEM_COLS = 512;        // 3 chunk slots, c_12 and c_34
-constexpr int TC_OUT12 = 384;
-constexpr int TC_OUT34 = 448;
+constexpr int TC_TMEM_COLS = 512;        // 3 chunk slots, c_12 and c_34 (and their second halves)
+
+// Operands split into PC BF16 pieces: PC = 2 (x = hi + lo, three products hh + hl + lh, about
+// 2^-16 relative per product) or PC = 3 (x = x1 + x2 + x3, six products 11 + 12 + 21 + 13 + 31
+// + 22, about 2^-24).  Columns per chunk: 128 with two pieces; 64 with three, so that the
+// ring of three 1.5x larger B slots and the 1.5x larger A tiles fit in shared memory at rank
+// 64.  Tensor-memory columns: three chunk slots, then c_12 and c_34; with three pieces the
+// read-out of a p whose a-range spans both 32-column halves of a chunk leaves two partial
+// sums, the second in the columns after c_34 (c_12b, c_34b).
+template <int PC> __host__ __device__ constexpr int tc_w() { return PC == 2 ? 128 : 64; }
+template <int PC> __host__ __device__ constexpr int tc_out12() { return 3 * tc_w<PC>(); }
+template <int PC> __host__ __device__ constexpr int tc_out34() { return 3 * tc_w<PC>() + 64; }
+template <int PC> __host__ __device__ constexpr int tc_out12b() { return 3 * tc_w<PC>() + 128; }
+template <int PC> __host__ __device__ constexpr int tc_out34b() { return 3 * tc_w<PC>() + 192; }
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;
 constexpr int TC_HEAD_BYTES = 16384;     // feet, weights, rows, values, partial sums
 constexpr int TC_MIN_SMEM = 120 * 1024;  // one CTA per SM: the 512-column allocation never waits
 
 __host__ __device__ __forceinline__ int r16(int r) { return ((r + 15) / 16) * 16; }
-__host__ __device__ __forceinline__ int tc_width(int ra16) { return (TC_W / ra16) * ra16; }
+template <int PC>
+__host__ __device__ __forceinline__ int tc_width(int ra16) { return (tc_w<PC>() / ra16) * ra16; }
 __host__ __device__ __forceinline__ int al128(int x) { return (x + 127) & ~127; }
 __host__ __device__ __forceinline__ int stage_ld(int r) { return r | 1; }   // odd row stride
 
@@ -64,6 +82,7 @@ struct TcLayout {
   int stage, A0, A1, B, slot, total;
 };
 
+template <int PC>
 __host__ __device__ __forceinline__ TcLayout tc_layout(int r0, int r1, int r2, int r3, int r12, int r34) {
   TcLayout L;
   (void)r34;
@@ -73,9 +92,9 @@ __host__ __device__ __forceinline__ TcLayout tc_layout(int r0, int r1, int r2, i
   if (r12 * 64 > st) st = r12 * 64;   // Broot staged with row stride 64
   int o = TC_HEAD_BYTES;
   L.stage = o; o = al128(o + 4 * st);
-  L.A0 = o; o += TC_TILE * r16(r1) * 4;
-  L.A1 = o; o += TC_TILE * r16(r3) * 4;
-  const int s0 = tc_width(r16(r0)) * r16(r1) * 4, s1 = tc_width(r16(r2)) * r16(r3) * 4;
+  L.A0 = o; o += TC_TILE * r16(r1) * 2 * PC;
+  L.A1 = o; o += TC_TILE * r16(r3) * 2 * PC;
+  const int s0 = tc_width<PC>(r16(r0)) * r16(r1) * 2 * PC, s1 = tc_width<PC>(r16(r2)) * r16(r3) * 2 * PC;
   L.slot = s0 > s1 ? s0 : s1;
   L.B = o; o += TC_STAGES * L.slot;
   L.total = o > TC_MIN_SMEM ? o : TC_MIN_SMEM;
@@ -89,12 +108,13 @@ struct TcNode {
   const unsigned char* bg;         // pre-split B tiles in global memory
 };
 
+template <int PC>
 __device__ __forceinline__ TcNode tc_node(int ra, int rb, int rp, uint32_t a_addr, const unsigned char* bg,
                                           int out_col) {
   TcNode n;
   n.ra = ra; n.rp = rp;
   n.ra16 = r16(ra); n.rb16 = r16(rb); n.ks = n.rb16 / 16;
-  n.w = tc_width(n.ra16); n.pc = n.w / n.ra16;
+  n.w = tc_width<PC>(n.ra16); n.pc = n.w / n.ra16;
   n.ntot = rp * n.ra16; n.nch = (n.ntot + n.w - 1) / n.w;
   n.out_col = out_col;
   n.a_addr = a_addr;
@@ -190,28 +210,51 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
       : "r"(taddr)
       : "memory");
 }
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_st1(uint32_t taddr, float v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(__float_as_uint(v)) : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void split8(const float* x, uint4* hi, uint4* lo) {
-  __align__(16) __nv_bfloat16 h[8], l[8];
+// x = piece 0 + piece 1 (+ piece 2), each the BF16 rounding of what the earlier pieces leave
+template <int PC>
+__device__ __forceinline__ void split8(const float* x, uint4* out) {
+  __align__(16) __nv_bfloat16 h[PC][8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    h[j] = __float2bfloat16_rn(x[j]);
-    l[j] = __float2bfloat16_rn(x[j] - __bfloat162float(h[j]));
+    float rest = x[j];
+#pragma unroll
+    for (int q = 0; q < PC; ++q) {
+      h[q][j] = __float2bfloat16_rn(rest);
+      rest -= __bfloat162float(h[q][j]);
+    }
   }
-  *hi = *reinterpret_cast<uint4*>(h);
-  *lo = *reinterpret_cast<uint4*>(l);
+#pragma unroll
+  for (int q = 0; q < PC; ++q) out[q] = *reinterpret_cast<uint4*>(h[q]);
 }
 
 // Pre-split B [rp][ra][b] (FP32) into the chunk tiles of the column stream: row n = (p, a)
 // (a padded to ra16), K = b (padded to rb16); chunk c holds rows [c W, c W + Wc) as
 // [hi: ks K-step tiles of Wc x 16][lo: same], tile layout as above.
+template <int PC>
 __global__ void k_split_bf16(const float* __restrict__ B, int rp, int ra, int rb, unsigned char* __restrict__ out) {
-  const int ra16 = r16(ra), rb16 = r16(rb), ks = rb16 / 16, W = tc_width(ra16), ntot = rp * ra16, ng = rb16 / 8;
+  const int ra16 = r16(ra), rb16 = r16(rb), ks = rb16 / 16, W = tc_width<PC>(ra16), ntot = rp * ra16, ng = rb16 / 8;
   const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= (long long)ntot * ng) return;
   const int n = (int)(it / ng), kg = (int)(it % ng);
@@ -222,14 +265,14 @@ __global__ void k_split_bf16(const float* __restrict__ B, int rp, int ra, int rb
     const int b = kg * 8 + j;
     x[j] = (a < ra && b < rb) ? B[((long long)p * ra + a) * rb + b] : 0.f;
   }
-  uint4 hi, lo;
-  split8(x, &hi, &lo);
+  uint4 pc[PC];
+  split8<PC>(x, pc);
   const int cl = n / W, nl = n - cl * W;
   const int wc = min(W, ntot - cl * W);
-  unsigned char* base = out + (long long)cl * W * rb16 * 4;
+  unsigned char* base = out + (long long)cl * W * rb16 * 2 * PC;
   const int off = (kg >> 1) * wc * 32 + (nl >> 3) * 256 + (kg & 1) * 128 + (nl & 7) * 16;
-  *reinterpret_cast<uint4*>(base + off) = hi;
-  *reinterpret_cast<uint4*>(base + ks * wc * 32 + off) = lo;
+#pragma unroll
+  for (int q = 0; q < PC; ++q) *reinterpret_cast<uint4*>(base + q * ks * wc * 32 + off) = pc[q];
 }
 
 // stage[e][q] = sum_s w[e][m][s] U_m[row_s][q] (FP32), zero rows for e >= nT.  Lanes run
@@ -267,7 +310,8 @@ __device__ __forceinline__ void gather_leaf(float* stage, const float* __restric
   }
 }
 
-// stage (128 x r) -> A operand tiles (hi, lo), K padded to r16 with zeros
+// stage (128 x r) -> A operand tiles (PC pieces), K padded to r16 with zeros
+template <int PC>
 __device__ __forceinline__ void stage_to_operand(const float* stage, int r, unsigned char* A) {
   const int ld = stage_ld(r), rb16 = r16(r), ks = rb16 / 16, ng = rb16 / 8;
   for (int it = threadIdx.x; it < TC_TILE * ng; it += TC_THREADS) {
@@ -278,11 +322,11 @@ __device__ __forceinline__ void stage_to_operand(const float* stage, int r, unsi
       const int b = kg * 8 + j;
       x[j] = b < r ? stage[e * ld + b] : 0.f;
     }
-    uint4 hi, lo;
-    split8(x, &hi, &lo);
+    uint4 pc[PC];
+    split8<PC>(x, pc);
     const int off = (kg >> 1) * 4096 + (e >> 3) * 256 + (kg & 1) * 128 + (e & 7) * 16;
-    *reinterpret_cast<uint4*>(A + off) = hi;
-    *reinterpret_cast<uint4*>(A + ks * 4096 + off) = lo;
+#pragma unroll
+    for (int q = 0; q < PC; ++q) *reinterpret_cast<uint4*>(A + q * ks * 4096 + off) = pc[q];
   }
 }
 
@@ -301,7 +345,7 @@ template <int NB>
 __device__ __forceinline__ void drain_chunk(const float* creg, uint32_t trow, uint32_t slot_col, int p0, int p1,
                                             int half, int out_col) {
   constexpr int RA16 = 16 * NB;
-  constexpr int NP = (TC_W / RA16) / 2;
+  constexpr int NP = (tc_w<2>() / RA16) / 2;
   float v[64];
   tmem_ld64(trow + slot_col + (uint32_t)(half * NP * RA16), v);
   tmem_wait_ld();
@@ -315,7 +359,45 @@ __device__ __forceinline__ void drain_chunk(const float* creg, uint32_t trow, ui
   }
 }
 
-template <bool DEV>
+// Read-out of one 64-column chunk of the three-piece variant by one warp: the warp loads the
+// half `half` of the chunk (32 columns).  RA16 <= 32: its whole p (two of 16 or one of 32) ->
+// c_t[e][p] in column out_col + p.  RA16 = 48 or 64: one p per chunk whose a-range spans both
+// halves -> the partial sum over the half's a into out_col + p (half 0) or outb_col + p
+// (half 1), added at the root.
+template <int NB>
+__device__ __forceinline__ void drain_chunk3(const float* creg, uint32_t trow, uint32_t slot_col, int p0, int p1,
+                                             int half, int out_col, int outb_col) {
+  constexpr int RA16 = 16 * NB;
+  float v[32];
+  tmem_ld32(trow + slot_col + (uint32_t)(half * 32), v);
+  tmem_wait_ld();
+  if constexpr (RA16 <= 32) {
+    constexpr int NP = 32 / RA16;
+#pragma unroll
+    for (int pi = 0; pi < NP; ++pi) {
+      const int p = p0 + half * NP + pi;
+      float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int a = 0; a < RA16; ++a) s4[a & 3] = fmaf(creg[a], v[pi * RA16 + a], s4[a & 3]);
+      if (p < p1) tmem_st1(trow + (uint32_t)(out_col + p), (s4[0] + s4[1]) + (s4[2] + s4[3]));
+    }
+  } else {
+    // RA16 = 48: the second half holds 16 columns of the p; the slot's columns past the chunk
+    // are never read (they may hold anything, and 0 x NaN is NaN)
+    const int p = p0;
+    float s4[4] = {0.f, 0.f, 0.f, 0.f};
+    if (half == 0) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) s4[c & 3] = fmaf(creg[c], v[c], s4[c & 3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < RA16 - 32; ++c) s4[c & 3] = fmaf(creg[32 + c], v[c], s4[c & 3]);
+    }
+    if (p < p1) tmem_st1(trow + (uint32_t)((half ? outb_col : out_col) + p), (s4[0] + s4[1]) + (s4[2] + s4[3]));
+  }
+}
+
+template <bool DEV, int PC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalParams<float>* __restrict__ P,
              EvalArgs a, const unsigned char* __restrict__ b12, const unsigned char* __restrict__ b34, int* err) {
@@ -350,7 +432,7 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   if (e0 >= n_act) return;
   const int nT = (int)min((long long)TC_TILE, n_act - e0);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const TcLayout L = tc_layout(ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34);
+  const TcLayout L = tc_layout<PC>(ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34);
   float* sfoot = reinterpret_cast<float*>(smem_raw);                 // 128 x 4
   float* sw = sfoot + TC_TILE * 4;                                    // 128 x 12
   int* srow = reinterpret_cast<int*>(sw + TC_TILE * 12);              // 128 x 12
@@ -363,8 +445,8 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   const uint32_t full = smem_u32(&s_bar[0]), mdone = smem_u32(&s_bar[TC_STAGES]),
                  drained = smem_u32(&s_bar[2 * TC_STAGES]);
 
-  const TcNode N0 = tc_node(ht.r[0], ht.r[1], ht.r12, smem_u32(A0), b12, TC_OUT12);
-  const TcNode N1 = tc_node(ht.r[2], ht.r[3], ht.r34, smem_u32(A1), b34, TC_OUT34);
+  const TcNode N0 = tc_node<PC>(ht.r[0], ht.r[1], ht.r12, smem_u32(A0), b12, tc_out12<PC>());
+  const TcNode N1 = tc_node<PC>(ht.r[2], ht.r[3], ht.r34, smem_u32(A1), b34, tc_out34<PC>());
   const int nchunk = N0.nch + N1.nch;
 
   if (warp == 0) {
@@ -399,10 +481,10 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     TcNode N;
     int cl, wc;
     chunk(j, N, cl, wc);
-    const uint32_t bytes = (uint32_t)(wc * N.rb16 * 4);
+    const uint32_t bytes = (uint32_t)(wc * N.rb16 * 2 * PC);
     const int s = j % TC_STAGES;
     mbar_expect_tx(full + 8 * s, bytes);
-    bulk_g2s(bslot + s * L.slot, N.bg + (long long)cl * N.w * N.rb16 * 4, bytes, full + 8 * s);
+    bulk_g2s(bslot + s * L.slot, N.bg + (long long)cl * N.w * N.rb16 * 2 * PC, bytes, full + 8 * s);
   };
   const bool copier = tid == TC_COPY_WARP * 32, issuer = tid == TC_MMA_WARP * 32;
   int n_copy = 0;
@@ -437,11 +519,11 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   float creg[64];
   gather_leaf(stage, ht.U[1], ht.r[1], 1, nT, srow, sw);
   __syncthreads();
-  stage_to_operand(stage, ht.r[1], A0);
+  stage_to_operand<PC>(stage, ht.r[1], A0);
   __syncthreads();
   gather_leaf(stage, ht.U[3], ht.r[3], 3, nT, srow, sw);
   __syncthreads();
-  stage_to_operand(stage, ht.r[3], A1);
+  stage_to_operand<PC>(stage, ht.r[3], A1);
   __syncthreads();
   gather_leaf(stage, ht.U[0], ht.r[0], 0, nT, srow, sw);
   __syncthreads();
@@ -470,14 +552,20 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
       fence_after();
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(wc >> 3) << 17) |
                              ((uint32_t)(TC_TILE >> 4) << 24);
-      const uint32_t dt = tmem + (uint32_t)(s * TC_W);
+      const uint32_t dt = tmem + (uint32_t)(s * tc_w<PC>());
       const uint32_t bb = bslot + s * L.slot;
       for (int k = 0; k < N.ks; ++k) {
-        const uint64_t ah = tc_desc(N.a_addr + k * 4096), al = tc_desc(N.a_addr + (N.ks + k) * 4096);
-        const uint64_t bh = tc_desc(bb + k * wc * 32), bl = tc_desc(bb + (N.ks + k) * wc * 32);
-        mma_bf16(dt, ah, bh, idesc, k > 0 ? 1u : 0u);
-        mma_bf16(dt, ah, bl, idesc, 1u);
-        mma_bf16(dt, al, bh, idesc, 1u);
+        // piece q of the A / B operands at K-step k
+        auto ad = [&](int q) { return tc_desc(N.a_addr + (q * N.ks + k) * 4096); };
+        auto bd = [&](int q) { return tc_desc(bb + (q * N.ks + k) * wc * 32); };
+        mma_bf16(dt, ad(0), bd(0), idesc, k > 0 ? 1u : 0u);
+        mma_bf16(dt, ad(0), bd(1), idesc, 1u);
+        mma_bf16(dt, ad(1), bd(0), idesc, 1u);
+        if constexpr (PC == 3) {
+          mma_bf16(dt, ad(0), bd(2), idesc, 1u);
+          mma_bf16(dt, ad(2), bd(0), idesc, 1u);
+          mma_bf16(dt, ad(1), bd(1), idesc, 1u);
+        }
       }
       mma_commit(mdone + 8 * s);
       n_mma = j + 1;
@@ -514,12 +602,22 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
           int cl, wc;
           chunk(c, N, cl, wc);
           const int p0 = cl * N.pc, p1 = min(N.rp, p0 + N.pc);
-          const uint32_t sc = (uint32_t)(s * TC_W);
-          switch (N.ra16) {
-            case 16: drain_chunk<1>(creg, trow, sc, p0, p1, half, N.out_col); break;
-            case 32: drain_chunk<2>(creg, trow, sc, p0, p1, half, N.out_col); break;
-            case 48: drain_chunk<3>(creg, trow, sc, p0, p1, half, N.out_col); break;
-            default: drain_chunk<4>(creg, trow, sc, p0, p1, half, N.out_col); break;
+          const uint32_t sc = (uint32_t)(s * tc_w<PC>());
+          if constexpr (PC == 2) {
+            switch (N.ra16) {
+              case 16: drain_chunk<1>(creg, trow, sc, p0, p1, half, N.out_col); break;
+              case 32: drain_chunk<2>(creg, trow, sc, p0, p1, half, N.out_col); break;
+              case 48: drain_chunk<3>(creg, trow, sc, p0, p1, half, N.out_col); break;
+              default: drain_chunk<4>(creg, trow, sc, p0, p1, half, N.out_col); break;
+            }
+          } else {
+            const int outb = N.out_col == tc_out12<PC>() ? tc_out12b<PC>() : tc_out34b<PC>();
+            switch (N.ra16) {
+              case 16: drain_chunk3<1>(creg, trow, sc, p0, p1, half, N.out_col, outb); break;
+              case 32: drain_chunk3<2>(creg, trow, sc, p0, p1, half, N.out_col, outb); break;
+              case 48: drain_chunk3<3>(creg, trow, sc, p0, p1, half, N.out_col, outb); break;
+              default: drain_chunk3<4>(creg, trow, sc, p0, p1, half, N.out_col, outb); break;
+            }
           }
           fence_before();
         }
@@ -562,9 +660,29 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     __syncthreads();
     if (warp < 8) {
       float c34[64], c12[64];
-      tmem_ld64(trow + TC_OUT34, c34);
-      tmem_ld64(trow + TC_OUT12, c12);
+      tmem_ld64(trow + tc_out34<PC>(), c34);
+      tmem_ld64(trow + tc_out12<PC>(), c12);
       tmem_wait_ld();
+      if constexpr (PC == 3) {
+        // the second partial sums of nodes whose a-range spans both halves of a chunk, 16
+        // columns at a time
+#pragma unroll
+        for (int q0 = 0; q0 < 64; q0 += 16) {
+          float cb[16];
+          if (N1.ra16 > 32) {
+            tmem_ld16(trow + tc_out34b<PC>() + q0, cb);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 16; ++q) c34[q0 + q] += cb[q];
+          }
+          if (N0.ra16 > 32) {
+            tmem_ld16(trow + tc_out12b<PC>() + q0, cb);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 16; ++q) c12[q0 + q] += cb[q];
+          }
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 64; ++q) {
         if (q >= rr) c34[q] = 0.f;
@@ -630,46 +748,65 @@ __global__ void k_wait_probe(long long polls, int* status) {
 
 }  // namespace
 
-size_t sl_eval_tc_smem(const int* r6) {
-  return (size_t)tc_layout(r6[0], r6[1], r6[2], r6[3], r6[4], r6[5]).total;
+size_t sl_eval_tc_smem(const int* r6, int pieces) {
+  return (size_t)(pieces == 3 ? tc_layout<3>(r6[0], r6[1], r6[2], r6[3], r6[4], r6[5]).total
+                              : tc_layout<2>(r6[0], r6[1], r6[2], r6[3], r6[4], r6[5]).total);
 }
 
-long long tc_split_bytes() { return 64LL * 64 * 64 * 4; }
+long long tc_split_bytes(int pieces) { return 64LL * 64 * 64 * 2 * pieces; }
 
 cudaError_t sl_eval_tc_init_attrs() {
   const int mx = 220 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_sl_eval_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaError_t e = cudaFuncSetAttribute(k_sl_eval_tc<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_tc<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_tc<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_tc<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   return e;
 }
 
-cudaError_t split_transfer_bf16(const float* B, int rp, int ra, int rb, void* out, cudaStream_t s) {
-  if (rp < 1 || ra < 1 || rb < 1 || rp > 64 || ra > 64 || rb > 64) return cudaErrorInvalidValue;
+cudaError_t split_transfer_bf16(const float* B, int rp, int ra, int rb, void* out, int pieces, cudaStream_t s) {
+  if (rp < 1 || ra < 1 || rb < 1 || rp > 64 || ra > 64 || rb > 64 || (pieces != 2 && pieces != 3))
+    return cudaErrorInvalidValue;
   const long long n = (long long)rp * r16(ra) * (r16(rb) / 8);
-  slar::count_launch(), k_split_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, rp, ra, rb,
-                                                                                static_cast<unsigned char*>(out));
+  if (pieces == 3)
+    slar::count_launch(), k_split_bf16<3><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, rp, ra, rb,
+                                                                                      static_cast<unsigned char*>(out));
+  else
+    slar::count_launch(), k_split_bf16<2><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, rp, ra, rb,
+                                                                                      static_cast<unsigned char*>(out));
   return cudaGetLastError();
 }
 
 cudaError_t launch_sl_eval_tc(const GridDesc& g, const HTView<float>& ht, const CorrView& corr, const EvalArgs& a,
-                              const void* b12, const void* b34, int* err, cudaStream_t s) {
+                              const void* b12, const void* b34, int* err, int pieces, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   if (g.d != 4) return cudaErrorInvalidValue;
   const int r6[6] = {ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34};
-  const size_t sm = sl_eval_tc_smem(r6);
+  const size_t sm = sl_eval_tc_smem(r6, pieces);
   const long long blocks = (a.n + TC_TILE - 1) / TC_TILE;
-  slar::count_launch(), k_sl_eval_tc<false><<<(unsigned)blocks, TC_THREADS, sm, s>>>(
-      g, ht, corr, nullptr, a, static_cast<const unsigned char*>(b12), static_cast<const unsigned char*>(b34), err);
+  const unsigned char* p12 = static_cast<const unsigned char*>(b12);
+  const unsigned char* p34 = static_cast<const unsigned char*>(b34);
+  if (pieces == 3)
+    slar::count_launch(), k_sl_eval_tc<false, 3><<<(unsigned)blocks, TC_THREADS, sm, s>>>(g, ht, corr, nullptr, a, p12,
+                                                                                         p34, err);
+  else
+    slar::count_launch(), k_sl_eval_tc<false, 2><<<(unsigned)blocks, TC_THREADS, sm, s>>>(g, ht, corr, nullptr, a, p12,
+                                                                                         p34, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sl_eval_tc_dev(const GridDesc& g, const EvalParams<float>* P, const EvalArgs& a, const void* b12,
-                                  const void* b34, int* err, size_t sm, cudaStream_t s) {
+                                  const void* b34, int* err, int pieces, size_t sm, cudaStream_t s) {
   if (g.d != 4) return cudaErrorInvalidValue;
   const long long blocks = (a.n + TC_TILE - 1) / TC_TILE;
-  slar::count_launch(), k_sl_eval_tc<true><<<(unsigned)blocks, TC_THREADS, sm, s>>>(
-      g, HTView<float>{}, CorrView{}, P, a, static_cast<const unsigned char*>(b12),
-      static_cast<const unsigned char*>(b34), err);
+  const unsigned char* p12 = static_cast<const unsigned char*>(b12);
+  const unsigned char* p34 = static_cast<const unsigned char*>(b34);
+  if (pieces == 3)
+    slar::count_launch(), k_sl_eval_tc<true, 3><<<(unsigned)blocks, TC_THREADS, sm, s>>>(
+        g, HTView<float>{}, CorrView{}, P, a, p12, p34, err);
+  else
+    slar::count_launch(), k_sl_eval_tc<true, 2><<<(unsigned)blocks, TC_THREADS, sm, s>>>(
+        g, HTView<float>{}, CorrView{}, P, a, p12, p34, err);
   return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libslar.so")
 
 SLAR_OK, SLAR_EINVAL, SLAR_ENOMEM, SLAR_ECUDA, SLAR_ENOCONV, SLAR_ETIMEOUT, SLAR_ERANK, SLAR_ENAN = range(8)
-SLAR_FP64, SLAR_FP32, SLAR_FP32_BF16X3 = 0, 1, 2
+SLAR_FP64, SLAR_FP32, SLAR_FP32_BF16X3, SLAR_FP32_BF16X6 = 0, 1, 2, 3
 SLAR_LOMAC, SLAR_FOOT_EULER, SLAR_PROFILE, SLAR_PROFILE_EVAL = 1, 2, 4, 8
 SLAR_PRECOND, SLAR_LEARNED, SLAR_NO_AUTOTUNE, SLAR_OWN_STREAM = 16, 32, 64, 128
 
@@ -215,7 +215,8 @@ def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, ep
     cfg.eps, cfg.rank_cap = eps, rank_cap
     cfg.newton_tol, cfg.krylov_tol = newton_tol, krylov_tol
     cfg.krylov_restart, cfg.newton_max, cfg.krylov_max = krylov_restart, newton_max, krylov_max
-    cfg.precision = {"fp64": SLAR_FP64, "fp32": SLAR_FP32, "bf16x3": SLAR_FP32_BF16X3}[precision]
+    cfg.precision = {"fp64": SLAR_FP64, "fp32": SLAR_FP32, "bf16x3": SLAR_FP32_BF16X3,
+                     "bf16x6": SLAR_FP32_BF16X6}[precision]
     cfg.flags = ((SLAR_LOMAC if lomac else 0) | (SLAR_FOOT_EULER if foot == "euler" else 0)
                  | (SLAR_PROFILE if profile else 0) | (SLAR_PROFILE_EVAL if profile_eval else 0)
                  | {"plain": 0, "precond": SLAR_PRECOND, "learned": SLAR_LEARNED}[solver]

@@ -101,9 +101,9 @@ def test_block_steps_match_oracle(w, b):
     assert P.relerr(htmod.densify(convert.from_lib(ctx.export())), htmod.densify(st.F)) < 1e-9
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x6"])
 def test_block_reduced_precision_close_to_fp64(prec):
-    """Blocks with FP32 and BF16x3 entries (the tensor-core evaluator evaluates a block of
+    """Blocks with FP32, BF16x3 and BF16x6 entries (the tensor-core evaluator evaluates a block of
     fibres per launch): SLAR calls within the precision bars of the one-fibre path."""
     N = (16, 16, 16, 16)
     eps, cap = 1e-5, 64

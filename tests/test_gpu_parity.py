@@ -138,7 +138,7 @@ def test_truncate_matches_oracle(N, ranks, eps, cap):
         assert abs(abs(float(ex["U"][m][:, 0] @ want.U[m][:, 0])) - 1.0) < 1e-9
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("cap", [64, 41])
 @pytest.mark.parametrize("N,ranks", [((64, 64, 8, 8), (44, 45, 8, 8, 6, 6)),
                                      ((16, 16, 8, 8), (6, 8, 8, 8, 44, 43))])
