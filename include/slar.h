@@ -79,8 +79,12 @@ enum {
                               plain JFNK from U(F*).  Implies SLAR_PRECOND. */
     SLAR_NO_AUTOTUNE = 64, /* keep the entry evaluator at 32 entries per CTA instead of the
                               autotuned tile (results then do not depend on timings) */
-    SLAR_OWN_STREAM = 128  /* the context creates (and destroys) a private non-blocking stream
+    SLAR_OWN_STREAM = 128, /* the context creates (and destroys) a private non-blocking stream
                               and ignores the stream argument of slar_create; see slar_stream */
+    SLAR_DIRK_ONLY = 256   /* with SLAR_LOMAC: the DIRK3 step (three stages, each one SLAR_VP to
+                              the stage time and one JFNK solve) every step, the DIRK coupling
+                              of Sec. 3.2.3, instead of BDF3 after the two start-up steps; no
+                              step-ratio bound applies */
 };
 
 typedef struct slar_config {
@@ -105,6 +109,12 @@ typedef struct slar_config {
                                parallel variant of the paper's HTACA).  Replayed pivots always
                                take the one-fibre path (the approximation depends on the pivots
                                only). */
+    int interp_order;       /* 0 or 2: the paper's quadratic stencil (Eq.
+                               1d_quadratic_interp_weight); 4: quartic centred Lagrange weights
+                               on the five-point stencil {j-2, ..., j+2} in the leaf gathers, the
+                               field interpolation of the feet and the LoMaC correction (the
+                               higher-order option noted after Eq. tp_interp).  Order 4 needs
+                               SLAR_FP64 entries and N >= 5 in every dimension. */
 } slar_config;
 
 typedef struct slar_stats {

@@ -1,4 +1,5 @@
-"""Uniform cell-centred periodic grids and the 1D quadratic Lagrange weights (Sec. 3.1).
+"""Uniform cell-centred periodic grids, the 1D quadratic Lagrange weights (Sec. 3.1) and
+the higher-order centred Lagrange weights of the remark after Eq. tp_interp.
 
 Test infrastructure: part of the FP64 oracle, never called by the CUDA path.
 """
@@ -45,16 +46,46 @@ def weights(xi):
     return np.stack([w0, w1, w2], axis=-1)
 
 
-def stencil_rows(j, n: int):
-    """Periodic stencil row indices (j-1, j, j+1) mod N, shape (..., 3)."""
+def lagrange_weights(xi, order: int):
+    """Lagrange interpolation weights of degree `order` (even) on the centred stencil of
+    order + 1 nodes at the integer offsets k = -order/2 .. order/2 from the cell centre,
+    evaluated at xi: L_k(xi) = prod_{m != k} (xi - m) / (k - m).  The paper uses order 2
+    (Eq. 1d_quadratic_interp_weight) and notes that the HT evaluation extends to higher
+    orders (remark after Eq. tp_interp); order 4 is the five-point quartic stencil.
+    Returns shape (..., order + 1), nodes in increasing k."""
+    if order < 2 or order % 2:
+        raise ValueError("order must be even and >= 2")
+    xi = np.asarray(xi, dtype=np.float64)
+    nodes = range(-(order // 2), order // 2 + 1)
+    cols = []
+    for k in nodes:
+        L = np.ones_like(xi)
+        for m in nodes:
+            if m != k:
+                L = L * (xi - m) / (k - m)
+        cols.append(L)
+    return np.stack(cols, axis=-1)
+
+
+def stencil_weights(xi, order: int = 2):
+    """The weights of an interpolation order: the paper's quadratic formula for order 2,
+    the general centred Lagrange weights otherwise."""
+    return weights(xi) if order == 2 else lagrange_weights(xi, order)
+
+
+def stencil_rows(j, n: int, order: int = 2):
+    """Periodic stencil row indices (j - order/2, ..., j + order/2) mod N, shape
+    (..., order + 1); order 2 gives (j-1, j, j+1)."""
     j = np.asarray(j, dtype=np.int64)
-    return np.stack([(j - 1) % n, j % n, (j + 1) % n], axis=-1)
+    h = order // 2
+    return np.stack([(j + k) % n for k in range(-h, h + 1)], axis=-1)
 
 
-def interp_1d(values: np.ndarray, y, lo: float, hi: float):
-    """Quadratic interpolation of a periodic grid function at points y (Sec. 3.1)."""
+def interp_1d(values: np.ndarray, y, lo: float, hi: float, order: int = 2):
+    """Interpolation of a periodic grid function at points y with the centred stencil of
+    the given order (quadratic by default, Sec. 3.1)."""
     n = values.shape[0]
     j, xi = locate(y, lo, hi, n)
-    w = weights(xi)
-    rows = stencil_rows(j, n)
+    w = stencil_weights(xi, order)
+    rows = stencil_rows(j, n, order)
     return (w * values[rows]).sum(axis=-1)

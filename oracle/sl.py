@@ -16,6 +16,11 @@ Readings of the paper taken here:
 * The arithmetic of the foot and of the field interpolation is written as an explicit
   sequence of scalar operations (no fused multiply-add, fixed summation order) so that
   the cell choice floor((y - a)/Delta) is reproducible.
+* Higher-order interpolation (the remark after Eq. tp_interp): a grid of interpolation
+  order 4 replaces the quadratic weights by the quartic centred Lagrange weights on the
+  five-point stencil {j-2, ..., j+2} everywhere the quadratic ones are used -- the leaf
+  gathers, the field interpolation of the foot, and the LoMaC correction -- with the same
+  cell rule.  Order 2 is the paper's scheme.
 """
 from __future__ import annotations
 
@@ -31,11 +36,18 @@ from .ht import HT, contract_tree, spatial_linear_index
 class PhaseGrid:
     """Grid description: per dimension (lo, hi, N); dimension order (x1..x_dx, v1..v_dv)."""
 
-    def __init__(self, dx: int, dv: int, N: Sequence[int], lo: Sequence[float], hi: Sequence[float]):
+    def __init__(self, dx: int, dv: int, N: Sequence[int], lo: Sequence[float], hi: Sequence[float],
+                 order: int = 2):
         self.dx, self.dv = dx, dv
         self.N = tuple(int(n) for n in N)
         self.lo = tuple(float(a) for a in lo)
         self.hi = tuple(float(b) for b in hi)
+        self.order = int(order)   # interpolation order: 2 (quadratic) or 4 (quartic)
+
+    @property
+    def S(self):
+        """Points of the 1D stencil."""
+        return self.order + 1
 
     @property
     def d(self):
@@ -53,19 +65,19 @@ class PhaseGrid:
 
 
 def interp_spatial(field: np.ndarray, pts: np.ndarray, g: PhaseGrid) -> np.ndarray:
-    """Tensor-product quadratic interpolation of a periodic spatial grid field (flattened,
-    x1 slowest) at points pts (S, dx).  Summation runs over the 3^dx stencil in
-    lexicographic order, accumulating (w_1 ... w_dx) * value."""
+    """Tensor-product interpolation (the grid's order; quadratic by default) of a periodic
+    spatial grid field (flattened, x1 slowest) at points pts (S, dx).  Summation runs over
+    the stencil in lexicographic order, accumulating (w_1 ... w_dx) * value."""
     dx = g.dx
     Nx = g.Nx
     F = field.reshape(Nx)
     rows, ws = [], []
     for m in range(dx):
         j, xi = grid.locate(pts[:, m], g.lo[m], g.hi[m], Nx[m])
-        rows.append(grid.stencil_rows(j, Nx[m]))
-        ws.append(grid.weights(xi))
+        rows.append(grid.stencil_rows(j, Nx[m], g.order))
+        ws.append(grid.stencil_weights(xi, g.order))
     acc = np.zeros(pts.shape[0])
-    for s in itertools.product(range(3), repeat=dx):
+    for s in itertools.product(range(g.S), repeat=dx):
         wprod = ws[0][:, s[0]]
         for m in range(1, dx):
             wprod = wprod * ws[m][:, s[m]]
@@ -112,15 +124,19 @@ def trace_feet(idx: np.ndarray, E: np.ndarray, tau: float, g: PhaseGrid, foot: s
 
 
 def leaf_vectors_at(ht: HT, feet: np.ndarray, g: PhaseGrid) -> List[np.ndarray]:
-    """c^(mu) = w(xi^(mu)) U^(mu)_{J_mu}: the quadratic interpolant of every leaf basis column
-    at the foot coordinate of dimension mu (Sec. 3.1).  Returns list of (S, r_mu)."""
+    """c^(mu) = w(xi^(mu)) U^(mu)_{J_mu}: the interpolant (quadratic, or the grid's order) of
+    every leaf basis column at the foot coordinate of dimension mu (Sec. 3.1).  Returns list
+    of (S, r_mu)."""
     c = []
     for m in range(ht.d):
         j, xi = grid.locate(feet[:, m], g.lo[m], g.hi[m], g.N[m])
-        w = grid.weights(xi)
-        rows = grid.stencil_rows(j, g.N[m])
+        w = grid.stencil_weights(xi, g.order)
+        rows = grid.stencil_rows(j, g.N[m], g.order)
         U = ht.U[m]
-        c.append(w[:, 0:1] * U[rows[:, 0]] + w[:, 1:2] * U[rows[:, 1]] + w[:, 2:3] * U[rows[:, 2]])
+        acc = w[:, 0:1] * U[rows[:, 0]]
+        for s in range(1, g.S):
+            acc = acc + w[:, s:s + 1] * U[rows[:, s]]
+        c.append(acc)
     return c
 
 
@@ -135,7 +151,7 @@ def correction_at(ht: HT, feet: np.ndarray, g: PhaseGrid) -> np.ndarray:
         t = dCi[k].copy()
         for m, vec in enumerate(vecs):
             mu = g.dx + m
-            t = t * grid.interp_1d(vec, feet[:, mu], g.lo[mu], g.hi[mu])
+            t = t * grid.interp_1d(vec, feet[:, mu], g.lo[mu], g.hi[mu], g.order)
         out = out + t
     return out
 
@@ -165,16 +181,16 @@ def all_tuples(N: Sequence[int]) -> np.ndarray:
 
 
 def dense_interp(F: np.ndarray, feet: np.ndarray, g: PhaseGrid) -> np.ndarray:
-    """<F_J, W(xi)>: the full 3^d-point tensor-product quadratic interpolation of a dense
-    tensor at the feet (Eq. tp_interp)."""
+    """<F_J, W(xi)>: the full S^d-point tensor-product interpolation (S = 3: quadratic) of a
+    dense tensor at the feet (Eq. tp_interp)."""
     d = F.ndim
     rows, ws = [], []
     for m in range(d):
         j, xi = grid.locate(feet[:, m], g.lo[m], g.hi[m], g.N[m])
-        rows.append(grid.stencil_rows(j, g.N[m]))
-        ws.append(grid.weights(xi))
+        rows.append(grid.stencil_rows(j, g.N[m], g.order))
+        ws.append(grid.stencil_weights(xi, g.order))
     acc = np.zeros(feet.shape[0])
-    for s in itertools.product(range(3), repeat=d):
+    for s in itertools.product(range(g.S), repeat=d):
         wprod = np.ones(feet.shape[0])
         for m in range(d):
             wprod = wprod * ws[m][:, s[m]]

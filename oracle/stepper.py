@@ -17,8 +17,10 @@ Readings:
   SLAR samples its entries (interpolation is linear, so both parts are interpolated with
   the same weights).
 * Time stepping of the macroscopic system: DIRK3 (each stage: one SLAR_VP to the stage
-  time c_i dt from F^n, one JFNK) for the first two steps, fixed-step BDF3 afterwards.
-  Without LoMaC the step is F^{n+1} = F*.
+  time c_i dt from F^n, one JFNK) for the first two steps, variable-step BDF3 afterwards.
+  Without LoMaC the step is F^{n+1} = F*.  The DIRK-only coupling (the first of the two
+  high-order options of Sec. 3.2.3) takes the DIRK3 step every time: three SLAR_VP calls
+  and three JFNK solves per step instead of one of each.
 """
 from __future__ import annotations
 
@@ -53,6 +55,8 @@ class Params:
     probes: int = 4
     # fibres per cross-approximation step (1: classical partial pivoting; > 1: block cross)
     block: int = 1
+    # DIRK3 every step (the DIRK coupling of Sec. 3.2.3) instead of BDF3 after the start-up
+    dirk_only: bool = False
 
 
 @dataclass
@@ -195,7 +199,7 @@ def sl_step(st: State, dt: float, g: PhaseGrid, prm: Params, pivots=None,
         stats.entries, stats.ranks = info["entries"], info["ranks"]
         stats.aca_ranks = info["aca_ranks"]
         stats.pivots = info["pivots"]
-    elif st.step < 2:
+    elif st.step < 2 or prm.dirk_only:
         A, c = macro.dirk3_tableau()
         tol_abs = macro.newton_tol_abs(prm.newton_tol, st.U)
         Ks = []

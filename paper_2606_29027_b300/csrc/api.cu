@@ -66,8 +66,18 @@ slar_status validate(const slar_config* cfg, char* msg, size_t len) {
     snprintf(msg, len, "unknown precision"); return SLAR_EINVAL;
   }
   if (cfg->flags & ~(SLAR_LOMAC | SLAR_FOOT_EULER | SLAR_PROFILE | SLAR_PROFILE_EVAL | SLAR_PRECOND | SLAR_LEARNED |
-                     SLAR_NO_AUTOTUNE | SLAR_OWN_STREAM)) {
+                     SLAR_NO_AUTOTUNE | SLAR_OWN_STREAM | SLAR_DIRK_ONLY)) {
     snprintf(msg, len, "unknown flag bits"); return SLAR_EINVAL;
+  }
+  if (cfg->interp_order != 0 && cfg->interp_order != 2 && cfg->interp_order != 4) {
+    snprintf(msg, len, "interp_order must be 0, 2 or 4"); return SLAR_EINVAL;
+  }
+  if (cfg->interp_order == 4) {
+    if (cfg->precision != SLAR_FP64) {
+      snprintf(msg, len, "interp_order 4 needs SLAR_FP64 entries"); return SLAR_EINVAL;
+    }
+    for (int m = 0; m < d; ++m)
+      if (cfg->N[m] < 5) { snprintf(msg, len, "interp_order 4 needs N >= 5"); return SLAR_EINVAL; }
   }
   if (cfg->krylov_restart < 1 || cfg->krylov_restart > 64) {
     snprintf(msg, len, "krylov_restart must be in [1, 64]"); return SLAR_EINVAL;
@@ -148,6 +158,7 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   GridDesc& g = c->g;
   g.d = c->d; g.dx = c->dx; g.dv = c->dv;
   g.NX = 1; g.NV = 1;
+  g.S = cfg->interp_order == 4 ? 5 : 3;
   for (int m = 0; m < 4; ++m) {
     g.N[m] = m < c->d ? cfg->N[m] : 1;
     g.lo[m] = m < c->d ? cfg->lo[m] : 0.0;
@@ -809,7 +820,8 @@ slar_status sl_step(slar_ctx* c, double dt, slar_stats* stats) {
     return set_error(c, SLAR_EINVAL, "SLAR_LEARNED needs a network (slar_attach_net)");
   if (!c->ht[c->cur].valid || !c->has_U) return set_error(c, SLAR_EINVAL, "call init_ht first");
   if (!(dt > 0.0)) return set_error(c, SLAR_EINVAL, "dt must be > 0");
-  if ((c->cfg.flags & SLAR_LOMAC) && c->step >= 2 && dt > kBdf3RatioMax * c->dt_hist[0] * (1.0 + 1e-12))
+  if ((c->cfg.flags & SLAR_LOMAC) && !(c->cfg.flags & SLAR_DIRK_ONLY) && c->step >= 2 &&
+      dt > kBdf3RatioMax * c->dt_hist[0] * (1.0 + 1e-12))
     return set_error(c, SLAR_EINVAL, "step ratio above the variable-step BDF3 stability bound");
   return step_impl(c, dt, stats);
 }

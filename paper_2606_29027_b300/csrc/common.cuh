@@ -31,6 +31,7 @@ struct GridDesc {
   float lof[4], hf[4];   // the same in FP32 (the FP32 / BF16x3 paths do no FP64 arithmetic)
   int NX;  // prod of spatial N
   int NV;  // prod of velocity N
+  int S;   // interpolation stencil points per dimension: 3 (quadratic) or 5 (quartic, FP64)
 };
 
 template <typename T>

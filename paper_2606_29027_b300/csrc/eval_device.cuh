@@ -1,9 +1,12 @@
 // Device functions shared by the entry evaluators (sl_eval.cu: SIMT, FP32/FP64;
 // sl_eval_tc.cu: tensor-core transfer-tensor contractions): the characteristic foot, the
-// quadratic cell weights, spatial and velocity interpolation, the separable LoMaC
-// correction and the decoding of an entry index into a grid tuple.  Foot arithmetic uses
-// explicit round-to-nearest intrinsics (no FMA contraction) so cell choices are
-// reproducible.
+// cell weights, spatial and velocity interpolation, the separable LoMaC correction and the
+// decoding of an entry index into a grid tuple.  Foot arithmetic uses explicit
+// round-to-nearest intrinsics (no FMA contraction) so cell choices are reproducible.
+// The FP64 functions take the stencil width S as a template argument: S = 3 is the paper's
+// quadratic stencil (Eq. 1d_quadratic_interp_weight), S = 5 the quartic centred Lagrange
+// stencil {j-2, ..., j+2} of the higher-order option (remark after Eq. tp_interp); the
+// FP32 functions are quadratic only.
 #pragma once
 
 #include "common.cuh"
@@ -15,25 +18,26 @@ __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 
-// periodic stencil rows (r0, r0 + 1, r0 + 2) mod n for the cell index jf (an integer value,
-// |jf| < 1e15): 32-bit arithmetic when jf fits, the 64-bit remainder otherwise; the same rows
-// either way
-__device__ __forceinline__ void stencil_rows(double jf, int n, int rows[3]) {
+// periodic stencil rows (r0, r0 + 1, ..., r0 + S - 1) mod n, r0 = jf - S/2, for the cell
+// index jf (an integer value, |jf| < 1e15): 32-bit arithmetic when jf fits, the 64-bit
+// remainder otherwise; the same rows either way (n >= S)
+template <int S = 3>
+__device__ __forceinline__ void stencil_rows(double jf, int n, int rows[S]) {
   int r0;
   if (fabs(jf) < 1e9) {
-    r0 = (int)jf - 1;
+    r0 = (int)jf - S / 2;
     if (r0 < 0 || r0 >= n) {
       r0 %= n;
       if (r0 < 0) r0 += n;
     }
   } else {
-    long long t = ((long long)jf - 1) % n;
+    long long t = ((long long)jf - S / 2) % n;
     if (t < 0) t += n;
     r0 = (int)t;
   }
   rows[0] = r0;
-  rows[1] = r0 + 1 == n ? 0 : r0 + 1;
-  rows[2] = rows[1] + 1 == n ? 0 : rows[1] + 1;
+#pragma unroll
+  for (int s = 1; s < S; ++s) rows[s] = rows[s - 1] + 1 == n ? 0 : rows[s - 1] + 1;
 }
 
 __device__ __forceinline__ void stencil_rows_f(float jf, int n, int rows[3]) {
@@ -54,35 +58,49 @@ __device__ __forceinline__ void stencil_rows_f(float jf, int n, int rows[3]) {
   rows[2] = rows[1] + 1 == n ? 0 : rows[1] + 1;
 }
 
-// cell and quadratic weights of coordinate y in dimension m (oracle: grid.locate/weights)
-__device__ __forceinline__ void cell_weights(const GridDesc& g, int m, double y, int rows[3],
-                                             double w[3]) {
+// cell and weights of coordinate y in dimension m (oracle: grid.locate and
+// grid.stencil_weights): the quadratic weights for S = 3; for S = 5 the quartic Lagrange
+// weights L_k(xi) = prod_{m != k} (xi - m) / (k - m), k = -2..2
+template <int S = 3>
+__device__ __forceinline__ void cell_weights(const GridDesc& g, int m, double y, int rows[S], double w[S]) {
+  static_assert(S == 3 || S == 5, "quadratic or quartic stencils");
   double t = __ddiv_rn(dsub(y, g.lo[m]), g.h[m]);
   if (!(fabs(t) < 1e15)) t = 0.0;  // non-finite or absurd feet still index inside the grid
   double jf = floor(t);
   double xi = dsub(dsub(t, jf), 0.5);
-  double hx = dmul(0.5, xi);
-  w[0] = dmul(hx, dsub(xi, 1.0));
-  w[1] = dsub(1.0, dmul(xi, xi));
-  w[2] = dmul(hx, dadd(xi, 1.0));
-  stencil_rows(jf, g.N[m], rows);
+  if constexpr (S == 3) {
+    double hx = dmul(0.5, xi);
+    w[0] = dmul(hx, dsub(xi, 1.0));
+    w[1] = dsub(1.0, dmul(xi, xi));
+    w[2] = dmul(hx, dadd(xi, 1.0));
+  } else {
+    const double a = dadd(xi, 2.0), b = dadd(xi, 1.0), e = dsub(xi, 1.0), f = dsub(xi, 2.0);
+    const double ab = dmul(a, b), ef = dmul(e, f);
+    w[0] = __ddiv_rn(dmul(dmul(b, xi), ef), 24.0);
+    w[1] = -__ddiv_rn(dmul(dmul(a, xi), ef), 6.0);
+    w[2] = __ddiv_rn(dmul(ab, ef), 4.0);
+    w[3] = -__ddiv_rn(dmul(dmul(ab, xi), f), 6.0);
+    w[4] = __ddiv_rn(dmul(dmul(ab, xi), e), 24.0);
+  }
+  stencil_rows<S>(jf, g.N[m], rows);
 }
 
-// tensor-product quadratic interpolation of a spatial field at point p (dx dims),
-// lexicographic stencil order, acc = acc + (w1 w2) v  (oracle: sl.interp_spatial)
+// tensor-product interpolation of a spatial field at point p (dx dims), lexicographic
+// stencil order, acc = acc + (w1 w2) v  (oracle: sl.interp_spatial)
+template <int S = 3>
 __device__ double interp_spatial(const GridDesc& g, const double* F, const double* p) {
-  int r0[3], r1[3];
-  double w0[3], w1[3];
-  cell_weights(g, 0, p[0], r0, w0);
+  int r0[S], r1[S];
+  double w0[S], w1[S];
+  cell_weights<S>(g, 0, p[0], r0, w0);
   double acc = 0.0;
   if (g.dx == 1) {
-    for (int s = 0; s < 3; ++s) acc = dadd(acc, dmul(w0[s], F[r0[s]]));
+    for (int s = 0; s < S; ++s) acc = dadd(acc, dmul(w0[s], F[r0[s]]));
     return acc;
   }
-  cell_weights(g, 1, p[1], r1, w1);
+  cell_weights<S>(g, 1, p[1], r1, w1);
   const int N1 = g.N[1];
-  for (int s0 = 0; s0 < 3; ++s0)
-    for (int s1 = 0; s1 < 3; ++s1)
+  for (int s0 = 0; s0 < S; ++s0)
+    for (int s1 = 0; s1 < S; ++s1)
       acc = dadd(acc, dmul(dmul(w0[s0], w1[s1]), F[r0[s0] * N1 + r1[s1]]));
   return acc;
 }
@@ -91,7 +109,9 @@ __device__ __forceinline__ double centre(const GridDesc& g, int m, int i) {
   return dadd(g.lo[m], dmul((double)i + 0.5, g.h[m]));
 }
 
-// backward foot of the frozen-field characteristic (oracle: sl.trace_feet)
+// backward foot of the frozen-field characteristic (oracle: sl.trace_feet); the field is
+// interpolated with the S-point stencil
+template <int S = 3>
 __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int euler,
                            const int* idx, double* foot) {
   const int dx = g.dx;
@@ -103,7 +123,7 @@ __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int e
   const long long NX = g.NX;
   if (euler) {
     for (int m = 0; m < dx; ++m) {
-      double e = interp_spatial(g, E + m * NX, x);
+      double e = interp_spatial<S>(g, E + m * NX, x);
       foot[m] = dsub(x[m], dmul(v[m], tau));
       foot[dx + m] = dadd(v[m], dmul(e, tau));
     }
@@ -114,7 +134,7 @@ __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int e
   double k1x[2], k1v[2], x2[2], v2[2], k2x[2], k2v[2], x3[2], v3[2], k3x[2], k3v[2];
   for (int m = 0; m < dx; ++m) {
     k1x[m] = -v[m];
-    k1v[m] = interp_spatial(g, E + m * NX, x);
+    k1v[m] = interp_spatial<S>(g, E + m * NX, x);
   }
   for (int m = 0; m < dx; ++m) {
     x2[m] = dadd(x[m], dmul(half, k1x[m]));
@@ -122,7 +142,7 @@ __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int e
   }
   for (int m = 0; m < dx; ++m) {
     k2x[m] = -v2[m];
-    k2v[m] = interp_spatial(g, E + m * NX, x2);
+    k2v[m] = interp_spatial<S>(g, E + m * NX, x2);
   }
   for (int m = 0; m < dx; ++m) {
     x3[m] = dadd(dsub(x[m], dmul(h, k1x[m])), dmul(two_h, k2x[m]));
@@ -130,7 +150,7 @@ __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int e
   }
   for (int m = 0; m < dx; ++m) {
     k3x[m] = -v3[m];
-    k3v[m] = interp_spatial(g, E + m * NX, x3);
+    k3v[m] = interp_spatial<S>(g, E + m * NX, x3);
   }
   for (int m = 0; m < dx; ++m) {
     foot[m] = dadd(x[m], dmul(sixth, dadd(dadd(k1x[m], dmul(4.0, k2x[m])), k3x[m])));
@@ -138,27 +158,36 @@ __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int e
   }
 }
 
-// quadratic 1D interpolation of a velocity vector (oracle: grid.interp_1d)
+// 1D interpolation of a velocity vector (oracle: grid.interp_1d)
+template <int S = 3>
 __device__ __forceinline__ double interp_1d(const GridDesc& g, int m, const double* vec, double y) {
-  int r[3];
-  double w[3];
-  cell_weights(g, m, y, r, w);
-  return (w[0] * vec[r[0]] + w[1] * vec[r[1]]) + w[2] * vec[r[2]];
+  int r[S];
+  double w[S];
+  cell_weights<S>(g, m, y, r, w);
+  if constexpr (S == 3) {
+    return (w[0] * vec[r[0]] + w[1] * vec[r[1]]) + w[2] * vec[r[2]];
+  } else {
+    double acc = w[0] * vec[r[0]];
+#pragma unroll
+    for (int s = 1; s < S; ++s) acc += w[s] * vec[r[s]];
+    return acc;
+  }
 }
 
 // separable LoMaC correction sum_k dC_k(x*) Q_k(v*) at a foot (oracle: sl.correction_at)
+template <int S = 3>
 __device__ double correction_at(const GridDesc& g, const CorrView& c, const double* foot) {
   const int dx = g.dx, dv = g.dv;
   const long long NX = g.NX;
   const int Nv = g.N[dx];
   double dCi[4];
-  for (int k = 0; k < dv + 2; ++k) dCi[k] = interp_spatial(g, c.dC + k * NX, foot);
+  for (int k = 0; k < dv + 2; ++k) dCi[k] = interp_spatial<S>(g, c.dC + k * NX, foot);
   double om[2], q1[2], q2[2];
   for (int m = 0; m < dv; ++m) {
     const double y = foot[dx + m];
-    om[m] = interp_1d(g, dx + m, c.qv + (0 * dv + m) * Nv, y);
-    q1[m] = interp_1d(g, dx + m, c.qv + (1 * dv + m) * Nv, y);
-    q2[m] = interp_1d(g, dx + m, c.qv + (2 * dv + m) * Nv, y);
+    om[m] = interp_1d<S>(g, dx + m, c.qv + (0 * dv + m) * Nv, y);
+    q1[m] = interp_1d<S>(g, dx + m, c.qv + (1 * dv + m) * Nv, y);
+    q2[m] = interp_1d<S>(g, dx + m, c.qv + (2 * dv + m) * Nv, y);
   }
   // terms in the order (0: prod omega), (1+m: q1 at m), (1+dv: q2 at m) for m = 0..dv-1
   double out = 0.0;

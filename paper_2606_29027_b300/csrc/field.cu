@@ -127,7 +127,8 @@ slar_status cfl_dt(slar_ctx* c, double cfl, double dt_max, double* dt) {
     rate = std::fmax(rate, std::fmax(vmax / c->g.h[m], emax / h));
   }
   double d = rate == 0.0 ? dt_max : std::fmin(dt_max, cfl / rate);
-  if (c->step >= 2 && c->dt_hist[0] > 0.0) d = std::fmin(d, kBdf3RatioMax * c->dt_hist[0]);
+  if (c->step >= 2 && c->dt_hist[0] > 0.0 && !(c->cfg.flags & SLAR_DIRK_ONLY))
+    d = std::fmin(d, kBdf3RatioMax * c->dt_hist[0]);
   *dt = d;
   return SLAR_OK;
 }

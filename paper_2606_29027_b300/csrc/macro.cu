@@ -7,7 +7,8 @@
 //   finite-difference J v, classical Gram-Schmidt applied twice, Givens rotations on
 //   device scalars (the host reads one convergence flag per GMRES cycle and one residual
 //   norm per Newton step);
-//   DIRK3 (Alexander 1977, Thm. 5) for the first two steps, fixed-step BDF3 afterwards;
+//   DIRK3 (Alexander 1977, Thm. 5) for the first two steps (every step with SLAR_DIRK_ONLY),
+//   variable-step BDF3 afterwards;
 //   SLAR_VP by the third-order commutator-free RK exponential integrator (Eq. slarvp).
 #include <algorithm>
 #include <cmath>
@@ -901,7 +902,7 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* out) {
     CKS(e0);
     if (!(un_inf == un_inf) || std::isinf(un_inf)) return set_error(c, SLAR_ENAN, "non-finite conserved variables U^n");
     const double tol_abs = c->cfg.newton_tol * std::max(1.0, un_inf);
-    if (c->step < 2) {
+    if (c->step < 2 || (c->cfg.flags & SLAR_DIRK_ONLY)) {
       double A[3][3], cst[3];
       dirk3_tableau(A, cst);
       for (int i = 0; i < 3; ++i) {

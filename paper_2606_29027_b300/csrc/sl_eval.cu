@@ -9,7 +9,10 @@
 //      intrinsics (no FMA contraction) so the cell choice reproduces the FP64 oracle's; FP32
 //      path: the same formulas in FP32 (B300's FP64 rate per SM sub-partition made the FP64
 //      foot the longest phase of a low-rank FP32 evaluation).
-//   2. leaf gathers c^(mu) = w . U^(mu)[j-1..j+1, :]  (coalesced row loads, staged in smem)
+//   2. leaf gathers c^(mu) = w . U^(mu)[j-1..j+1, :]  (coalesced row loads, staged in smem);
+//      FP64 entries may take the quartic five-point stencil j-2..j+2 instead (g.S = 5: the
+//      higher-order option of the remark after Eq. tp_interp, also used for the field at the
+//      foot and the correction)
 //   3. transfer-tensor contractions c12 = B12 x1 c0 x2 c1, likewise c34: small transfer
 //      tensors resident in shared memory (outer products c0 (x) c1 formed on the fly, threads
 //      over entries and output ranks); large ones in FP32 as one [TILE x r1] x [r1 x r0] GEMM
@@ -28,12 +31,6 @@ namespace {
 constexpr int NTHREADS = 256;
 constexpr int KC = 32;          // K-chunk of the transfer-tensor contraction
 constexpr int PSTRIDE = 65;     // padded row of the staged B chunk (p <= 64)
-
-struct Smem {
-  double* foot;  // [TILE][4]
-  double* w;     // [TILE][4][3]
-  int* rows;     // [TILE][4][3]
-};
 
 // Transfer tensors small enough for this byte budget are staged whole in shared memory
 // ([k][p], k = (a, b)) by the warps that do not trace feet, while the feet are traced;
@@ -283,6 +280,40 @@ __device__ void contract_node_gemm(const float* __restrict__ ca, int ra, const f
   }
 }
 
+// FP64 foot, cells and weights of entry e with the S-point stencil: foot[4], rows / w [4][S]
+// (at_grid: the grid point itself, weight 1 on its own row)
+template <int S>
+__device__ __forceinline__ void feet_cells64(const GridDesc& g, const EvalArgs& a, long long e, int at_grid,
+                                             double* foot, int* rows, double* w) {
+  int idx[4];
+  decode_tuple(g, a, e, idx);
+  double ft[4];
+  if (at_grid) {
+    for (int m = 0; m < g.d; ++m) ft[m] = centre(g, m, idx[m]);
+  } else {
+    trace_foot<S>(g, a.E, a.tau, a.foot_euler, idx, ft);
+  }
+  for (int m = 0; m < g.d; ++m) {
+    int r[S];
+    double ww[S];
+    if (at_grid) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        r[s] = idx[m];
+        ww[s] = s == S / 2 ? 1.0 : 0.0;
+      }
+    } else {
+      cell_weights<S>(g, m, ft[m], r, ww);
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      rows[m * S + s] = r[s];
+      w[m * S + s] = ww[s];
+    }
+    foot[m] = ft[m];
+  }
+}
+
 template <typename T, int TILE>
 __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>& ht,
                                              const CorrView& corr, EvalArgs a, int at_grid) {
@@ -302,14 +333,15 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
   const int tid = threadIdx.x;
   const int d = g.d;
 
+  const int S = g.S;                                           // stencil points (3 or 5)
   double* sfoot = reinterpret_cast<double*>(smem_raw);        // TILE*4
-  double* sw = sfoot + TILE * 4;                               // TILE*12
-  double* sval = sw + TILE * 12;                               // TILE
+  double* sw = sfoot + TILE * 4;                               // TILE*4*S
+  double* sval = sw + TILE * 4 * S;                            // TILE
   double* sres = sval + TILE;                                  // TILE residual sums
-  int* srow = reinterpret_cast<int*>(sres + TILE);             // TILE*12
+  int* srow = reinterpret_cast<int*>(sres + TILE);             // TILE*4*S
   T* sfootT = reinterpret_cast<T*>(sfoot);   // the feet and weights in the entry type (FP32
   T* swT = reinterpret_cast<T*>(sw);         // paths: no FP64 conversions in the gathers)
-  T* sc = reinterpret_cast<T*>(srow + TILE * 12);              // leaves
+  T* sc = reinterpret_cast<T*>(srow + TILE * 4 * S);           // leaves
   T* sc_mu[4];
   {
     T* p = sc;
@@ -402,29 +434,10 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
       }
     }
   } else if (tid < nT) {
-    int idx[4];
-    decode_tuple(g, a, e0 + tid, idx);
-    double foot[4];
-    if (at_grid) {
-      for (int m = 0; m < d; ++m) foot[m] = centre(g, m, idx[m]);
-    } else {
-      trace_foot(g, a.E, a.tau, a.foot_euler, idx, foot);
-    }
-    for (int m = 0; m < d; ++m) {
-      int r[3];
-      double w[3];
-      if (at_grid) {
-        r[0] = idx[m]; r[1] = idx[m]; r[2] = idx[m];
-        w[0] = 0.0; w[1] = 1.0; w[2] = 0.0;
-      } else {
-        cell_weights(g, m, foot[m], r, w);
-      }
-      for (int s = 0; s < 3; ++s) {
-        srow[(tid * 4 + m) * 3 + s] = r[s];
-        sw[(tid * 4 + m) * 3 + s] = w[s];
-      }
-      sfoot[tid * 4 + m] = foot[m];
-    }
+    if (S == 5)
+      feet_cells64<5>(g, a, e0 + tid, at_grid, sfoot + tid * 4, srow + tid * 4 * 5, sw + tid * 4 * 5);
+    else
+      feet_cells64<3>(g, a, e0 + tid, at_grid, sfoot + tid * 4, srow + tid * 4 * 3, sw + tid * 4 * 3);
   }
   __syncthreads();
 
@@ -437,10 +450,11 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
       const int t = it / r, q = it - t * r;
       T val = T(0);
       if (t < nT) {
-        const int* rr = srow + (t * 4 + m) * 3;
-        const T* ww = swT + (t * 4 + m) * 3;
+        const int* rr = srow + (t * 4 + m) * S;
+        const T* ww = swT + (t * 4 + m) * S;
         val = ww[0] * U[(long long)rr[0] * r + q] + ww[1] * U[(long long)rr[1] * r + q] +
               ww[2] * U[(long long)rr[2] * r + q];
+        if (S == 5) val += ww[3] * U[(long long)rr[3] * r + q] + ww[4] * U[(long long)rr[4] * r + q];
       }
       c[it] = val;
     }
@@ -498,7 +512,7 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
         const float* ww = reinterpret_cast<const float*>(swT) + tid * 12;
         val += (double)(d == 4 ? correction_rw_ft<2>(g, corr, rr, ww) : correction_rw_ft<1>(g, corr, rr, ww));
       } else {
-        val += correction_at(g, corr, sfoot + tid * 4);
+        val += S == 5 ? correction_at<5>(g, corr, sfoot + tid * 4) : correction_at<3>(g, corr, sfoot + tid * 4);
       }
     }
     const long long e = e0 + tid;
@@ -526,7 +540,8 @@ k_sl_eval_dev(GridDesc g, const EvalParams<T>* __restrict__ P, EvalArgs a) {
 
 template <typename T, int TILE>
 size_t smem_bytes(const GridDesc& g, const HTView<T>& ht) {
-  size_t b = sizeof(double) * (TILE * 4 + TILE * 12 + TILE + TILE) + sizeof(int) * TILE * 12;
+  const int ns = TILE * 4 * g.S;   // stencil rows and weights
+  size_t b = sizeof(double) * (TILE * 4 + ns + TILE + TILE) + sizeof(int) * ns;
   int rs = 0;
   for (int m = 0; m < g.d; ++m) rs += ht.r[m];
   if (g.d == 4) rs += ht.r12 + ht.r34;

@@ -20,6 +20,7 @@ SLAR_OK, SLAR_EINVAL, SLAR_ENOMEM, SLAR_ECUDA, SLAR_ENOCONV, SLAR_ETIMEOUT, SLAR
 SLAR_FP64, SLAR_FP32, SLAR_FP32_BF16X3, SLAR_FP32_BF16X6 = 0, 1, 2, 3
 SLAR_LOMAC, SLAR_FOOT_EULER, SLAR_PROFILE, SLAR_PROFILE_EVAL = 1, 2, 4, 8
 SLAR_PRECOND, SLAR_LEARNED, SLAR_NO_AUTOTUNE, SLAR_OWN_STREAM = 16, 32, 64, 128
+SLAR_DIRK_ONLY = 256
 
 # every entry point declared in include/slar.h
 EXPORTED = ["slar_create", "slar_destroy", "slar_last_error", "init_ht", "sl_step", "ht_truncate",
@@ -39,7 +40,8 @@ class Config(C.Structure):
                 ("hi", C.c_double * 4), ("eps", C.c_double), ("rank_cap", C.c_int),
                 ("newton_tol", C.c_double), ("krylov_tol", C.c_double), ("krylov_restart", C.c_int),
                 ("newton_max", C.c_int), ("krylov_max", C.c_int), ("precision", C.c_int),
-                ("flags", C.c_int), ("delta_floor", C.c_double), ("aca_block", C.c_int)]
+                ("flags", C.c_int), ("delta_floor", C.c_double), ("aca_block", C.c_int),
+                ("interp_order", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -198,7 +200,7 @@ def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, ep
                 newton_tol=1e-12, krylov_tol=1e-4, krylov_restart=30, newton_max=20, krylov_max=200,
                 precision="fp64", lomac=True, foot="rk3", delta_floor=1e-12, profile=False,
                 profile_eval=False, solver="plain", autotune=True, own_stream=False,
-                aca_block=1) -> Config:
+                aca_block=1, dirk_only=False, interp_order=2) -> Config:
     """solver: "plain" (the paper's JFNK), "precond" (block-circulant preconditioner) or
     "learned" (network warm start; attach a network with Context.attach_net)."""
     if workload is not None:
@@ -220,9 +222,11 @@ def make_config(workload=None, *, dx=None, dv=None, N=None, lo=None, hi=None, ep
     cfg.flags = ((SLAR_LOMAC if lomac else 0) | (SLAR_FOOT_EULER if foot == "euler" else 0)
                  | (SLAR_PROFILE if profile else 0) | (SLAR_PROFILE_EVAL if profile_eval else 0)
                  | {"plain": 0, "precond": SLAR_PRECOND, "learned": SLAR_LEARNED}[solver]
-                 | (0 if autotune else SLAR_NO_AUTOTUNE) | (SLAR_OWN_STREAM if own_stream else 0))
+                 | (0 if autotune else SLAR_NO_AUTOTUNE) | (SLAR_OWN_STREAM if own_stream else 0)
+                 | (SLAR_DIRK_ONLY if dirk_only else 0))
     cfg.delta_floor = delta_floor
     cfg.aca_block = int(aca_block)
+    cfg.interp_order = int(interp_order)
     return cfg
 
 
