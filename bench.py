@@ -1,16 +1,17 @@
 """Benchmark: 2D-2V SLAR steps/s and sampled entries/s on the 2D-2V weak Landau workload
 (64 points per dimension, tree ((x1,x2),(v1,v2)), rank cap 32, eps 1e-5, dt 0.2), with the
-implicit LoMaC correction.  Headline: the FP64 path (FP64 entries, truncation, LoMaC and
-Newton) with the block-circulant preconditioner of the Newton-Krylov solve.  Beside it, on
-the same steps: the plain FP64 path (the paper's unpreconditioned JFNK), FP32 entries with
-the preconditioner, and FP32 entries with the learned JFNK warm start (network trained in the
-same run, untimed, on samples of seeded weak-Landau runs that the solver generates), each
-form's electric-energy history compared with an FP64 run truncated 100 times more tightly;
-the 1D-1V weak Landau workload in microseconds per step.  The line ends with a compact
-summary of the forms.
+implicit LoMaC correction.  Headline: the precision-split path (FP32 entry evaluation; FP64
+moments, truncation, LoMaC and Newton) with the block-circulant preconditioner of the
+Newton-Krylov solve and block cross approximation (two fibres per step).  Beside it, on the
+same steps: the plain FP64 path (the paper's unpreconditioned JFNK, one fibre per step), the
+preconditioned FP64 path, FP32 entries with one fibre per step and with the learned JFNK warm
+start (network trained in the same run, untimed, on samples of seeded weak-Landau runs that
+the solver generates), each form's electric-energy history compared with an FP64 run
+truncated 100 times more tightly; the 1D-1V weak Landau workload in microseconds per step.
+The line ends with a compact summary of the forms.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision fp64|fp32] [--solver precond|plain|learned] [--workload NAME]
+                    [--precision fp32|fp64] [--solver precond|plain|learned] [--workload NAME]
 
 One JSON line on rank 0.  Multi-GPU runs are independent replicas (the method has no
 data-parallel exchange): value = steps of all ranks / max-over-ranks time.
@@ -50,7 +51,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp32", "fp64", "bf16x3", "bf16x6"],
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3", "bf16x6"],
                    help="entry precision of the headline run (bf16x3: 2D2V workloads, "
                         "--profile-step only)")
     p.add_argument("--workload", default="landau_2d2v")
@@ -377,7 +378,8 @@ def run_ours(args, w):
     K = args.steps if args.fp64_steps is None else args.fp64_steps
     acc = None
     if K > 0:
-        wanted = [("fp64", "plain", 1), ("fp32", "precond", 1)] + ([("fp32", "learned", 1)] if net is not None else [])
+        wanted = [("fp64", "plain", 1), ("fp64", "precond", args.aca_block), ("fp32", "precond", 1)]
+        wanted += [("fp32", "learned", 1)] if net is not None else []
         wanted += [(args.precision, args.solver, int(b)) for b in args.block_forms.split(",") if b and int(b) > 1]
         if args.aca_block > 1:
             wanted.append((args.precision, args.solver, 1))

@@ -225,9 +225,13 @@ k_aca_row_pivot(const double* __restrict__ r, int M1, int M2, unsigned char* use
     return;
   }
   const double piv = r[j];
-  // one reciprocal instead of M2 FP64 divisions on this single CTA (a division costs about
-  // eight FP64-pipe instructions); v_k[j] = 1 exactly
-  const double inv = 1.0 / piv;
+  // one reciprocal for the CTA instead of M2 FP64 divisions (a division costs about eight
+  // FP64-pipe instructions, and every warp computing it serialises on the SM's few FP64
+  // units); v_k[j] = 1 exactly
+  __shared__ double inv_s;
+  if (threadIdx.x == 0) inv_s = 1.0 / piv;
+  __syncthreads();
+  const double inv = inv_s;
   for (int i = threadIdx.x; i < M2; i += PIV_THREADS) vout[i] = i == j ? 1.0 : r[i] * inv;
   if (threadIdx.x == 0) {
     pivJ[kk] = j;
@@ -255,12 +259,23 @@ __device__ void aca_finalize_body(const double* __restrict__ Ua, int M1, int kma
   const int replay = st->replay;
   const double eps = st->eps;
   __syncthreads();
-  if (tid <= kk) {
-    double a = 0.0, b = 0.0;
-    for (int blk = 0; blk < nbu; ++blk) a += __ldcg(part + (long long)blk * ldp + tid);
-    for (int blk = nbu; blk < nbu + nbv; ++blk) b += __ldcg(part + (long long)blk * ldp + tid);
-    du[tid] = a;
-    dv[tid] = b;
+  // the partials of dot l summed by one warp (lanes over blocks, shuffle tree): no thread
+  // walks a chain of dependent L2 loads
+  {
+    const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    for (int l = warp; l <= kk; l += nw) {
+      double a = 0.0, b = 0.0;
+      for (int blk = lane; blk < nbu; blk += 32) a += __ldcg(part + (long long)blk * ldp + l);
+      for (int blk = nbu + lane; blk < nbu + nbv; blk += 32) b += __ldcg(part + (long long)blk * ldp + l);
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+      }
+      if (lane == 0) {
+        du[l] = a;
+        dv[l] = b;
+      }
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -521,7 +536,10 @@ k_aca_block_pivot(double* __restrict__ rowbuf, int M1, int M2, unsigned char* us
     const double piv = r[j];
     const int a = nacc_s;
     double* vout = Va + (long long)(kk + a) * M2;
-    const double inv = 1.0 / piv;
+    __shared__ double inv_s;   // one FP64 division for the CTA
+    if (tid == 0) inv_s = 1.0 / piv;
+    __syncthreads();
+    const double inv = inv_s;
     for (int i = tid; i < M2; i += PIV_THREADS) vout[i] = i == j ? 1.0 : r[i] * inv;
     if (tid < nrows) coef_s[tid] = tid > t ? rowbuf[(long long)tid * M2 + j] : 0.0;
     __syncthreads();
@@ -666,12 +684,19 @@ k_aca_block_post(const double* __restrict__ Ua, int M1, const double* __restrict
   __shared__ int stop_s, redirect_s, kend_s, next_s[ACA_BMAX], nnext_s;
   const int tid = threadIdx.x;
   if (tid == 0) st->post_ctr = 0;
-  for (int w = tid; w < na * K; w += 256) {
+  // the partials of dot w summed by one warp (lanes over blocks, shuffle tree)
+  for (int w = warp; w < na * K; w += 8) {
     double a = 0.0, c = 0.0;
-    for (int q = 0; q < nbu; ++q) a += __ldcg(part + (long long)q * ldp + w);
-    for (int q = nbu; q < nbu + nbv; ++q) c += __ldcg(part + (long long)q * ldp + w);
-    du[w] = a;
-    dv[w] = c;
+    for (int q = lane; q < nbu; q += 32) a += __ldcg(part + (long long)q * ldp + w);
+    for (int q = nbu + lane; q < nbu + nbv; q += 32) c += __ldcg(part + (long long)q * ldp + w);
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+      du[w] = a;
+      dv[w] = c;
+    }
   }
   __syncthreads();
   if (tid == 0) {

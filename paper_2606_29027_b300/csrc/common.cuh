@@ -176,6 +176,15 @@ cudaError_t transpose(const double* A, int rows, int cols, double* B, cudaStream
 cudaError_t copy_cols(const double* A, int lda_rows, int rows, int cols, double* B, int ldb,
                       cudaStream_t s);
 cudaError_t to_float(const double* a, float* b, long long n, cudaStream_t s);
+// up to 8 FP64 -> FP32 conversions in one launch
+struct F32Batch {
+  const double* a[8];
+  float* b[8];
+  long long off[9] = {0};
+  int k = 0;
+  void add(const double* src, float* dst, long long n);
+};
+cudaError_t to_float_batch(const F32Batch& bt, cudaStream_t s);
 cudaError_t fill_identity(double* A, int n, int ld, cudaStream_t s);
 cudaError_t fill_zero(double* A, long long n, cudaStream_t s);
 

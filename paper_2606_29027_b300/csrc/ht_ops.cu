@@ -62,18 +62,20 @@ CorrView corr_view(const slar_ctx* c, bool with_corr) {
 slar_status refresh_f32_slot(slar_ctx* c, int slot) {
   if (c->f32_slot == slot) return SLAR_OK;
   const HTBuf& h = c->ht[slot];
-  for (int m = 0; m < c->d; ++m)
-    CK(to_float(h.U[m], c->U32[m], (long long)c->g.N[m] * h.r[m], c->s));
+  F32Batch bt;
+  for (int m = 0; m < c->d; ++m) bt.add(h.U[m], c->U32[m], (long long)c->g.N[m] * h.r[m]);
   if (c->d == 4) {
-    CK(to_float(h.B12, c->B12_32, (long long)h.r[4] * h.r[0] * h.r[1], c->s));
-    CK(to_float(h.B34, c->B34_32, (long long)h.r[5] * h.r[2] * h.r[3], c->s));
-    CK(to_float(h.Broot, c->Broot32, (long long)h.r[4] * h.r[5], c->s));
+    bt.add(h.B12, c->B12_32, (long long)h.r[4] * h.r[0] * h.r[1]);
+    bt.add(h.B34, c->B34_32, (long long)h.r[5] * h.r[2] * h.r[3]);
+    bt.add(h.Broot, c->Broot32, (long long)h.r[4] * h.r[5]);
+    CK(to_float_batch(bt, c->s));
     if (tc_pieces(c) > 0) {
       CK(split_transfer_bf16(c->B12_32, h.r[4], h.r[0], h.r[1], c->tc_b12, tc_pieces(c), c->s));
       CK(split_transfer_bf16(c->B34_32, h.r[5], h.r[2], h.r[3], c->tc_b34, tc_pieces(c), c->s));
     }
   } else {
-    CK(to_float(h.Broot, c->Broot32, (long long)h.r[0] * h.r[1], c->s));
+    bt.add(h.Broot, c->Broot32, (long long)h.r[0] * h.r[1]);
+    CK(to_float_batch(bt, c->s));
   }
   c->f32_slot = slot;
   return SLAR_OK;
@@ -81,11 +83,13 @@ slar_status refresh_f32_slot(slar_ctx* c, int slot) {
 
 slar_status refresh_f32_fields(slar_ctx* c, const double* E, bool with_corr) {
   if (c->cfg.precision == SLAR_FP64) return SLAR_OK;
-  if (E) CK(to_float(E, c->E32, (long long)c->dx * c->NX, c->s));
+  F32Batch bt;
+  if (E) bt.add(E, c->E32, (long long)c->dx * c->NX);
   if (with_corr && c->has_corr) {
-    CK(to_float(c->dC, c->dC32, (long long)(c->dv + 2) * c->NX, c->s));
-    CK(to_float(c->qv, c->qv32, (long long)3 * c->dv * c->g.N[c->dx], c->s));
+    bt.add(c->dC, c->dC32, (long long)(c->dv + 2) * c->NX);
+    bt.add(c->qv, c->qv32, (long long)3 * c->dv * c->g.N[c->dx]);
   }
+  CK(to_float_batch(bt, c->s));
   return SLAR_OK;
 }
 

@@ -116,7 +116,9 @@ k_dgemm_small(int tA, int tB, int M, int N, int K, double alpha, const double* _
 
 // ---------------------------------------------------------------------------------------
 // G = A^T A for a tall column-major A (m x n, n <= 64): each CTA reduces ROWS rows into a
-// partial n x n; a second kernel sums the partials in block order.
+// partial n x n; a second kernel sums the partials in block order.  (Summing them in the CTA
+// that finishes last instead puts n^2 chains of nblk dependent L2 loads on one SM, which costs
+// more on B300 than the second launch.)
 // ---------------------------------------------------------------------------------------
 constexpr int GR_ROWS = 64;
 
@@ -187,34 +189,40 @@ __global__ void k_chol_inv(const double* __restrict__ G, int n, double* __restri
                            double* __restrict__ Rinv, int* info) {
   // Column-equilibrated: factor D^{-1} G D^{-1} = Rt^T Rt with D = diag(sqrt(G_ii)), then
   // R = Rt D and R^{-1} = D^{-1} Rt^{-1}.  Equilibration makes the factorisation
-  // insensitive to the column scaling of the matrix whose Gram G is.
+  // insensitive to the column scaling of the matrix whose Gram G is.  B300 retires FP64 at a
+  // low rate with a long latency, so every division is taken once (reciprocals of the scale
+  // factors and of the pivots) and the chains use multiplications.
   extern __shared__ double chol_smem[];
   double (*a)[SLAR_MAX_RANK + 1] = reinterpret_cast<double (*)[SLAR_MAX_RANK + 1]>(chol_smem);
   double (*ri)[SLAR_MAX_RANK + 1] =
       reinterpret_cast<double (*)[SLAR_MAX_RANK + 1]>(chol_smem + SLAR_MAX_RANK * (SLAR_MAX_RANK + 1));
-  __shared__ double dsc[SLAR_MAX_RANK];
+  __shared__ double dsc[SLAR_MAX_RANK], dinv[SLAR_MAX_RANK], rinv[SLAR_MAX_RANK];
   __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
   for (int i = tid; i < n; i += blockDim.x) {
     const double gii = G[i * n + i];
     dsc[i] = gii > 0.0 ? sqrt(gii) : 1.0;
+    dinv[i] = 1.0 / dsc[i];
   }
   __syncthreads();
   for (int it = tid; it < n * n; it += blockDim.x) {
     const int i = it / n, j = it % n;
-    a[i][j] = G[it] / (dsc[i] * dsc[j]);
+    a[i][j] = G[it] * dinv[i] * dinv[j];
   }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     if (tid == 0) {
       const double dkk = a[k][k];
-      if (!(dkk > 0.0)) { bad = k + 1; a[k][k] = 1.0; }
-      else a[k][k] = sqrt(dkk);
+      double rkk;
+      if (!(dkk > 0.0)) { bad = k + 1; rkk = 1.0; }
+      else rkk = sqrt(dkk);
+      a[k][k] = rkk;
+      rinv[k] = 1.0 / rkk;
     }
     __syncthreads();
-    const double rkk = a[k][k];
-    for (int j = k + 1 + tid; j < n; j += blockDim.x) a[k][j] /= rkk;
+    const double rk = rinv[k];
+    for (int j = k + 1 + tid; j < n; j += blockDim.x) a[k][j] *= rk;
     __syncthreads();
     for (int it = tid; it < (n - k - 1) * (n - k - 1); it += blockDim.x) {
       const int i = k + 1 + it / (n - k - 1), j = k + 1 + it % (n - k - 1);
@@ -222,20 +230,21 @@ __global__ void k_chol_inv(const double* __restrict__ G, int n, double* __restri
     }
     __syncthreads();
   }
+  // R^{-1} column by column (back substitution, one column per thread)
   for (int j = tid; j < n; j += blockDim.x) {
     for (int i = 0; i < n; ++i) ri[i][j] = 0.0;
-    ri[j][j] = 1.0 / a[j][j];
+    ri[j][j] = rinv[j];
     for (int i = j - 1; i >= 0; --i) {
       double s = 0.0;
       for (int k2 = i + 1; k2 <= j; ++k2) s += a[i][k2] * ri[k2][j];
-      ri[i][j] = -s / a[i][i];
+      ri[i][j] = -s * rinv[i];
     }
   }
   __syncthreads();
   for (int it = tid; it < n * n; it += blockDim.x) {
     const int i = it / n, j = it % n;
     R[it] = (j >= i) ? a[i][j] * dsc[j] : 0.0;
-    Rinv[it] = ri[i][j] / dsc[i];
+    Rinv[it] = ri[i][j] * dinv[i];
   }
   if (tid == 0 && bad) info[0] = bad;
 }
@@ -329,6 +338,7 @@ constexpr int EIG_THREADS = 512;
 // Gram matrices of FP64 data (the rounding level), 1e-13 for those of FP32 entries and 1e-9
 // for BF16x3 entries, whose noise puts a cluster of eigenvalues near u^2 ||A|| (u the
 // entries' relative precision) that carries no information.
+template <int NT>
 __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, double* cc,
                               double* ss, int* rotated, double floor_rel) {
   const int tid = threadIdx.x;
@@ -336,24 +346,24 @@ __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, d
   const int m = ne - 1;
   const double tol = 1e-15;
   __shared__ unsigned short tri[(SLAR_MAX_N / 2) * (SLAR_MAX_N / 2 + 1) / 2];
-  __shared__ double fro_red[EIG_THREADS / 32];
+  __shared__ double fro_red[NT / 32];
   __shared__ double floor_s;
   // absolute floor: entries at the rounding (or data-noise) level of the matrix are not rotated
   {
     double f = 0.0;
-    for (int it = tid; it < ne * ne; it += EIG_THREADS) f += sA[it] * sA[it];
+    for (int it = tid; it < ne * ne; it += NT) f += sA[it] * sA[it];
     for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
     if ((tid & 31) == 0) fro_red[tid >> 5] = f;
     __syncthreads();
     if (tid == 0) {
       double t = 0.0;
-      for (int w = 0; w < EIG_THREADS / 32; ++w) t += fro_red[w];
+      for (int w = 0; w < NT / 32; ++w) t += fro_red[w];
       floor_s = floor_rel * sqrt(t);
     }
     __syncthreads();
   }
   const double afloor = floor_s;
-  for (int ia = tid; ia < half; ia += EIG_THREADS) {
+  for (int ia = tid; ia < half; ia += NT) {
     const int off = ia * half - ia * (ia - 1) / 2;
     for (int ib = ia; ib < half; ++ib) tri[off + ib - ia] = (unsigned short)((ia << 8) | ib);
   }
@@ -362,7 +372,7 @@ __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, d
     if (tid == 0) *rotated = 0;
     __syncthreads();
     for (int rnd = 0; rnd < m; ++rnd) {
-      for (int k = tid; k < half; k += EIG_THREADS) {
+      for (int k = tid; k < half; k += NT) {
         int p, q;
         if (k == 0) { p = rnd; q = ne - 1; }
         else { p = (rnd + k) % m; q = (rnd - k + m) % m; }
@@ -385,7 +395,7 @@ __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, d
       // upper-triangular block pairs (ia <= ib) from the precomputed table; the
       // transposed block is mirrored
       const int nblk = half * (half + 1) / 2;
-      for (int it = tid; it < nblk; it += EIG_THREADS) {
+      for (int it = tid; it < nblk; it += NT) {
         const int ia = tri[it] >> 8, ib = tri[it] & 0xff;
         const double sa = ss[ia], sb = ss[ib];
         if (sa == 0.0 && sb == 0.0) continue;
@@ -409,7 +419,7 @@ __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, d
           sA[qb * ne + qa] = z11;
         }
       }
-      for (int it = tid; it < ne * half; it += EIG_THREADS) {
+      for (int it = tid; it < ne * half; it += NT) {
         const int row = it / half, ib = it % half;
         const double sb = ss[ib];
         if (sb == 0.0) continue;
@@ -440,9 +450,10 @@ constexpr int TRI_FLAG = TRI_WORK - 1;                              // 1.0: job 
 constexpr int TRI_TRACE = TRI_WORK - 2;                             // trace of the matrix
 constexpr int EIG_SMEM_DOUBLES = SLAR_MAX_N * EIG_RTMAX + 2 * EIG_RTMAX * EIG_RTMAX + SLAR_MAX_N;
 
+template <int NT>
 __device__ void sort_write(const double* sA, int ne, int n, const double* V, int ldv, double* W,
                            double* Vout) {
-  for (int i = threadIdx.x; i < n; i += EIG_THREADS) {
+  for (int i = threadIdx.x; i < n; i += NT) {
     const double li = sA[i * ne + i];
     int pos = 0;
     for (int j = 0; j < n; ++j) {
@@ -454,14 +465,15 @@ __device__ void sort_write(const double* sA, int ne, int n, const double* V, int
   }
 }
 
-__global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long smem_doubles) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_jacobi(EigJob* jobs, long long smem_doubles) {
   extern __shared__ double smem[];
   __shared__ int pp[SLAR_MAX_N / 2], qq[SLAR_MAX_N / 2];
   __shared__ double cc[SLAR_MAX_N / 2], ss[SLAR_MAX_N / 2];
-  __shared__ double wred[EIG_THREADS / 32];
-  __shared__ int wred_i[EIG_THREADS / 32];
+  __shared__ double wred[NT / 32];
+  __shared__ int wred_i[NT / 32];
   __shared__ int piv_s, rotated, rt_s;
-  __shared__ double dpiv_s, trace_s;
+  __shared__ double dpiv_s, dinv_s, trace_s;
   const EigJob job = jobs[blockIdx.x];
   const int n = job.n;
   const int tid = threadIdx.x;
@@ -470,7 +482,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
     double* M = smem + SLAR_MAX_N * EIG_RTMAX;          // ne x ne
     double* Vs = M + EIG_RTMAX * EIG_RTMAX;             // ne x ne
     double* dg = Vs + EIG_RTMAX * EIG_RTMAX;            // n
-    for (int i = tid; i < n; i += EIG_THREADS) dg[i] = job.A[i * n + i];
+    for (int i = tid; i < n; i += NT) dg[i] = job.A[i * n + i];
     __syncthreads();
     if (tid == 0) {
       double t = 0.0;
@@ -487,7 +499,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
     for (int j = 0; j < rtmax; ++j) {
       double best = -1.0;
       int bi = -1;
-      for (int i = tid; i < n; i += EIG_THREADS)
+      for (int i = tid; i < n; i += NT)
         if (dg[i] > best) { best = dg[i]; bi = i; }
       for (int o = 16; o > 0; o >>= 1) {
         const double ob = __shfl_down_sync(0xffffffffu, best, o);
@@ -499,26 +511,30 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
       if (tid == 0) {
         double b = -1.0;
         int ib = -1;
-        for (int w = 0; w < EIG_THREADS / 32; ++w)
+        for (int w = 0; w < NT / 32; ++w)
           if (wred[w] > b || (wred[w] == b && wred_i[w] >= 0 && (ib < 0 || wred_i[w] < ib))) {
             b = wred[w]; ib = wred_i[w];
           }
         piv_s = ib;
         dpiv_s = b;
+        // one reciprocal square root for the CTA: on B300 an FP64 sqrt and division cost
+        // tens of FP64-pipe instructions, and every warp computing them serialises on the
+        // SM's few FP64 units
+        dinv_s = b > 0.0 ? 1.0 / sqrt(b) : 0.0;
       }
       __syncthreads();
       if (!(dpiv_s > 0.0) || piv_s < 0) break;
       const int p = piv_s;
-      const double inv = 1.0 / sqrt(dpiv_s);
+      const double inv = dinv_s;
       double* lj = L + j * n;
-      for (int i = tid; i < n; i += EIG_THREADS) {
+      for (int i = tid; i < n; i += NT) {
         double v = job.A[i * n + p];
         for (int t = 0; t < j; ++t) v -= L[t * n + i] * L[t * n + p];
         lj[i] = v * inv;
       }
       __syncthreads();
       double rem = 0.0;
-      for (int i = tid; i < n; i += EIG_THREADS) {
+      for (int i = tid; i < n; i += NT) {
         const double v = (i == p) ? -1.0 : dg[i] - lj[i] * lj[i];
         dg[i] = v;
         rem += fmax(v, 0.0);
@@ -529,7 +545,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
       if (tid == 0) {
         rt_s = j + 1;
         double t = 0.0;
-        for (int w = 0; w < EIG_THREADS / 32; ++w) t += wred[w];
+        for (int w = 0; w < NT / 32; ++w) t += wred[w];
         dpiv_s = t;   // trace left outside L L^T
       }
       __syncthreads();
@@ -550,11 +566,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
     if (!full) {
       if (rt == 0) {  // zero matrix: one zero eigenpair
         rt = 1;
-        for (int i = tid; i < n; i += EIG_THREADS) L[i] = 0.0;
+        for (int i = tid; i < n; i += NT) L[i] = 0.0;
       }
       const int ne = rt + (rt & 1);
       __syncthreads();
-      for (int it = tid; it < ne * ne; it += EIG_THREADS) {
+      for (int it = tid; it < ne * ne; it += NT) {
         const int a = it / ne, b = it % ne;
         double v = 0.0;
         if (a < rt && b < rt)
@@ -563,10 +579,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
         Vs[it] = (a == b) ? 1.0 : 0.0;
       }
       __syncthreads();
-      jacobi_sweeps(M, ne, Vs, pp, qq, cc, ss, &rotated, job.floor_rel);
-      // eigenvalue order of M (descending, ties by index)
+      jacobi_sweeps<NT>(M, ne, Vs, pp, qq, cc, ss, &rotated, job.floor_rel);
+      // eigenvalue order of M (descending, ties by index); 1/sqrt(lambda) once per eigenvalue
       __shared__ int order[EIG_RTMAX];
-      for (int i = tid; i < rt; i += EIG_THREADS) {
+      __shared__ double isq[EIG_RTMAX];
+      for (int i = tid; i < rt; i += NT) {
         const double li = M[i * ne + i];
         int pos = 0;
         for (int j = 0; j < rt; ++j) {
@@ -575,19 +592,20 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
         }
         order[pos] = i;
         job.W[pos] = li > 0.0 ? li : 0.0;
+        isq[pos] = li > 0.0 ? 1.0 / sqrt(li) : 0.0;
       }
-      for (int i = rt + tid; i < n; i += EIG_THREADS) job.W[i] = 0.0;
+      for (int i = rt + tid; i < n; i += NT) job.W[i] = 0.0;
       __syncthreads();
       // S[r][pos] = sum_a L[r][a] V[a][i] / sqrt(lambda_i)
-      for (int it = tid; it < n * n; it += EIG_THREADS) {
+      for (int it = tid; it < n * n; it += NT) {
         const int r = it / n, pos = it % n;
         double v = 0.0;
         if (pos < rt) {
           const int i = order[pos];
-          const double li = M[i * ne + i];
-          if (li > 0.0) {
+          const double is = isq[pos];
+          if (is > 0.0) {
             for (int a = 0; a < rt; ++a) v += L[a * n + r] * Vs[a * ne + i];
-            v /= sqrt(li);
+            v *= is;
           }
         }
         job.V[it] = v;
@@ -599,14 +617,14 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
     const int ne = n + (n & 1);
     double* sA = smem;
     double* V = job.work;
-    for (int it = tid; it < ne * ne; it += EIG_THREADS) {
+    for (int it = tid; it < ne * ne; it += NT) {
       const int i = it / ne, j = it % ne;
       sA[it] = (i < n && j < n) ? job.A[i * n + j] : 0.0;
       V[it] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
-    jacobi_sweeps(sA, ne, V, pp, qq, cc, ss, &rotated, job.floor_rel);
-    sort_write(sA, ne, n, V, ne, job.W, job.V);
+    jacobi_sweeps<NT>(sA, ne, V, pp, qq, cc, ss, &rotated, job.floor_rel);
+    sort_write<NT>(sA, ne, n, V, ne, job.W, job.V);
     return;
   }
   // the matrix in shared memory; its eigenvectors there too while both fit in the dynamic
@@ -614,14 +632,14 @@ __global__ void __launch_bounds__(EIG_THREADS) k_jacobi(EigJob* jobs, long long 
   const int ne = n + (n & 1);
   double* sA = smem;
   double* V = (2LL * ne * ne <= smem_doubles) ? smem + ne * ne : job.work;
-  for (int it = tid; it < ne * ne; it += EIG_THREADS) {
+  for (int it = tid; it < ne * ne; it += NT) {
     const int i = it / ne, j = it % ne;
     sA[it] = (i < n && j < n) ? job.A[i * n + j] : 0.0;
     V[it] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  jacobi_sweeps(sA, ne, V, pp, qq, cc, ss, &rotated, job.floor_rel);
-  sort_write(sA, ne, n, V, ne, job.W, job.V);
+  jacobi_sweeps<NT>(sA, ne, V, pp, qq, cc, ss, &rotated, job.floor_rel);
+  sort_write<NT>(sA, ne, n, V, ne, job.W, job.V);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1018,6 +1036,16 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
   if (i < n) b[i] = (float)a[i];
 }
 
+// several arrays in one launch: element i belongs to segment s with off[s] <= i < off[s + 1]
+__global__ void k_to_float_multi(F32Batch bt) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= bt.off[bt.k]) return;
+  int s = 0;
+  while (i >= bt.off[s + 1]) ++s;
+  const long long j = i - bt.off[s];
+  bt.b[s][j] = (float)bt.a[s][j];
+}
+
 __global__ void k_identity(double* A, int n, int ld) {
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= n * n) return;
@@ -1101,7 +1129,7 @@ cudaError_t linalg_init_attrs() {
   if (e != cudaSuccess) return e;
   size_t sm = sizeof(double) * EIG_SMEM_DOUBLES;
   if (sm < sizeof(double) * SLAR_MAX_N * SLAR_MAX_N) sm = sizeof(double) * SLAR_MAX_N * SLAR_MAX_N;
-  e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  e = cudaFuncSetAttribute(k_jacobi<EIG_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_tri_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * SLAR_MAX_N * SLAR_MAX_N));
@@ -1113,7 +1141,8 @@ cudaError_t linalg_init_attrs() {
 cudaError_t chol_inv(const double* G, int n, double* R, double* Rinv, int* info, cudaStream_t s) {
   if (n > SLAR_MAX_RANK) return cudaErrorInvalidValue;
   const int sm = (int)(sizeof(double) * 2 * SLAR_MAX_RANK * (SLAR_MAX_RANK + 1));
-  slar::count_launch(), k_chol_inv<<<1, 256, sm, s>>>(G, n, R, Rinv, info);
+  // one warp for orders up to 32: the factorisation is a chain of n block barriers
+  slar::count_launch(), k_chol_inv<<<1, n <= 32 ? 32 : 128, sm, s>>>(G, n, R, Rinv, info);
   return cudaGetLastError();
 }
 
@@ -1138,7 +1167,8 @@ cudaError_t eig_batched(const EigJob* jobs_host, int njobs, EigJob* jobs_dev, cu
   cudaError_t e = cudaMemcpyAsync(jobs_dev, jobs_host, sizeof(EigJob) * njobs,
                                   cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
-  slar::count_launch(), k_jacobi<<<njobs, EIG_THREADS, sm, s>>>(jobs_dev, (long long)(sm / sizeof(double)));
+  slar::count_launch(), k_jacobi<EIG_THREADS><<<njobs, EIG_THREADS, sm, s>>>(jobs_dev,
+                                                                           (long long)(sm / sizeof(double)));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // jobs that k_jacobi handed over (flag in their work array) go through the tridiagonal
@@ -1187,6 +1217,21 @@ cudaError_t copy_cols(const double* A, int lda, int rows, int cols, double* B, i
 cudaError_t to_float(const double* a, float* b, long long n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   slar::count_launch(), k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+void F32Batch::add(const double* src, float* dst, long long n) {
+  if (n <= 0) return;
+  a[k] = src;
+  b[k] = dst;
+  off[k + 1] = off[k] + n;
+  ++k;
+}
+
+cudaError_t to_float_batch(const F32Batch& bt, cudaStream_t s) {
+  if (bt.k == 0) return cudaSuccess;
+  const long long n = bt.off[bt.k];
+  slar::count_launch(), k_to_float_multi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(bt);
   return cudaGetLastError();
 }
 
