@@ -70,7 +70,11 @@ enum {
                               probed at the initial guess with one impulse per conserved
                               component, its (dv+2) x (dv+2) Fourier-mode blocks are inverted
                               and applied mode by mode (an addition to the paper, whose JFNK is
-                              unpreconditioned; the Newton stop test is unchanged) */
+                              unpreconditioned; the Newton stop test is unchanged).  The blocks
+                              are kept over BDF3 steps and probed again at the first BDF3 step,
+                              when dt changes, after 8 steps, after a failed solve, or when a
+                              solve needed more than 2 GMRES iterations beyond the solve that
+                              followed the last probe (stats.pc_built) */
     SLAR_LEARNED = 32,     /* warm start of the BDF3 solves from the network attached with
                               slar_attach_net: initial guess U* + s_D d(x) (kept only if its
                               residual is not larger than that of U(F*)) and a per-point block
@@ -139,6 +143,8 @@ typedef struct slar_stats {
     int eval_tile;          /* entries per CTA of the entry evaluator (autotuned: 16, 32, 64) */
     int rank_capped;        /* cross approximations and truncations of this step that stopped at
                                the rank cap with eps unmet (non-zero: sl_step returns SLAR_ERANK) */
+    int pc_built;           /* SLAR_PRECOND / SLAR_LEARNED: the block-circulant preconditioner was
+                               probed this step (else the previous one was reused) */
 } slar_stats;
 
 /* Host-side view of an HT state for import/export.  Layouts (row-major):
@@ -282,7 +288,10 @@ slar_status ht_import(slar_ctx* ctx, const slar_ht_view* view);
  * SLAR_EINVAL); the state is FP64 in every precision, so the run may resume in another entry
  * precision.  The network parameters are loaded only if a network of the same size is
  * attached.  A restored FP64 run continues bit for bit like the run that wrote the file
- * (same process: the autotuned evaluator tile is kept per process).  Both calls synchronise
+ * (same process: the autotuned evaluator tile is kept per process) with the paper's plain
+ * JFNK; with SLAR_PRECOND the block-circulant preconditioner is not saved and the next BDF3
+ * step probes it again, so the Newton iterates may differ from the straight run's (the
+ * converged U^{n+1} agree to the Newton tolerance).  Both calls synchronise
  * the context stream.  Errors: SLAR_EINVAL (no state, file cannot be opened / read /
  * written, wrong magic or version, mismatch), SLAR_ECUDA. */
 slar_status slar_checkpoint(slar_ctx* ctx, const char* path);

@@ -407,6 +407,7 @@ slar_status init_ht(slar_ctx* c, int n_terms, const double* factors) {
   c->has_corr = 0;
   c->step = 0;
   c->dt_hist[0] = c->dt_hist[1] = 0.0;
+  c->pc_age = -1;
   CKS(conserved_of_state(c, true));
   c->has_U = true;
   CK(cudaStreamSynchronize(c->s));
@@ -805,6 +806,7 @@ slar_status slar_restore(slar_ctx* c, const char* path) {
   c->dt_hist[0] = hd.dt_hist[0];
   c->dt_hist[1] = hd.dt_hist[1];
   for (int t = 0; t < 6; ++t) c->Sn[t] = hd.Sn[t];
+  c->pc_age = -1;   // the preconditioner is not saved: the next BDF3 step probes it again
   return SLAR_OK;
 }
 

@@ -201,6 +201,12 @@ struct slar_ctx {
   // SLAR calls and truncations that stopped at the rank cap with eps unmet (running count;
   // sl_step, slar_advect, ht_truncate and init_ht report SLAR_ERANK when it grows)
   long long rank_capped = 0;
+  // block-circulant preconditioner reuse: steps since the last probe (-1: none valid), the
+  // coefficient beta dt it was probed for, and the GMRES count of the solve right after it
+  int pc_age = -1;
+  double pc_coef = 0.0;
+  int pc_krylov_ref = 0;
+  bool pc_stale = false;
 
   char err[512] = {0};
 };
@@ -264,6 +270,8 @@ slar_status step_impl(slar_ctx* c, double dt, slar_stats* st);
 void bdf3_variable(const double h[3], double a[3], double* beta);
 // the largest ratio h_n / h_{n-1} admitted for variable-step BDF3
 constexpr double kBdf3RatioMax = 1.4877;
+// BDF3 steps a probed block-circulant preconditioner is kept at most
+constexpr int kPcMaxAge = 8;
 // adaptive step size: cfl / max_i(a_i / Delta_i), capped at dt_max and, after the start-up,
 // at kBdf3RatioMax times the previous step (field of the current state)
 slar_status cfl_dt(slar_ctx* c, double cfl, double dt_max, double* dt);

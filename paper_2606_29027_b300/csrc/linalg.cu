@@ -380,13 +380,32 @@ __device__ void jacobi_sweeps(double* sA, int ne, double* V, int* pp, int* qq, d
         const double apq = sA[p * ne + q];
         const double app = sA[p * ne + p], aqq = sA[q * ne + q];
         double c = 1.0, s = 0.0;
-        if (fabs(apq) > tol * sqrt(fabs(app * aqq)) && fabs(apq) > afloor) {
-          const double theta = (aqq - app) / (2.0 * apq);
-          const double t = fabs(theta) > 1e150
-                               ? 0.5 / theta
-                               : (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
-          s = t * c;
+        // On B300 a dependent FP64 division costs ~440 cycles and a square root ~680, so the
+        // test is squared and the angle is taken in FP32:
+        //   theta = d / e (d = a_qq - a_pp, e = 2 a_pq),
+        //   t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)) = sgn(d e) |e| / (|d| + sqrt(d^2 + e^2)),
+        //   c = 1 / sqrt(t^2 + 1), s = t c,
+        // from d and e scaled by the same power of two (exact); (c, s) is then made orthonormal
+        // to FP64 precision by two Newton steps for 1 / sqrt(c^2 + s^2) (FMAs only).  Any
+        // exactly orthogonal rotation keeps the spectrum; an angle good to 2^-24 leaves
+        // a'_pq ~ 1e-7 a_pq, which the sweeps clear like any other off-diagonal entry, and the
+        // stop test stays in FP64.
+        if (apq * apq > tol * tol * fabs(app * aqq) && fabs(apq) > afloor) {
+          const double d = aqq - app, e = 2.0 * apq;
+          int ex;
+          frexp(fmax(fabs(d), fabs(e)), &ex);
+          const float df = (float)ldexp(d, -ex), ef = (float)ldexp(e, -ex);
+          const float tf = (df * ef >= 0.f ? 1.f : -1.f) * fabsf(ef) / (fabsf(df) + sqrtf(df * df + ef * ef));
+          const float cf = rsqrtf(fmaf(tf, tf, 1.f));
+          c = (double)cf;
+          s = (double)(tf * cf);
+#pragma unroll
+          for (int it = 0; it < 2; ++it) {
+            const double r = fma(c, c, s * s);
+            const double kf = fma(-0.5, r, 1.5);
+            c *= kf;
+            s *= kf;
+          }
           *rotated = 1;
         }
         pp[k] = p; qq[k] = q; cc[k] = c; ss[k] = s;
@@ -496,22 +515,28 @@ __global__ void __launch_bounds__(NT) k_jacobi(EigJob* jobs, long long smem_doub
     const double stop = job.compress_rel * trace_s;
     const int rcap = job.tri ? TRI_RT + 1 : EIG_RTMAX;
     const int rtmax = n < rcap ? n : rcap;
+    // the reductions run on the warps that hold entries only: FP64 compares and adds of idle
+    // warps would queue on the SM's FP64 units like real work
+    const int nwa = (n + 31) / 32 < NT / 32 ? (n + 31) / 32 : NT / 32;
+    const bool act = (tid >> 5) < nwa;
     for (int j = 0; j < rtmax; ++j) {
       double best = -1.0;
       int bi = -1;
-      for (int i = tid; i < n; i += NT)
-        if (dg[i] > best) { best = dg[i]; bi = i; }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) { best = ob; bi = oi; }
+      if (act) {
+        for (int i = tid; i < n; i += NT)
+          if (dg[i] > best) { best = dg[i]; bi = i; }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) { best = ob; bi = oi; }
+        }
+        if ((tid & 31) == 0) { wred[tid >> 5] = best; wred_i[tid >> 5] = bi; }
       }
-      if ((tid & 31) == 0) { wred[tid >> 5] = best; wred_i[tid >> 5] = bi; }
       __syncthreads();
       if (tid == 0) {
         double b = -1.0;
         int ib = -1;
-        for (int w = 0; w < NT / 32; ++w)
+        for (int w = 0; w < nwa; ++w)
           if (wred[w] > b || (wred[w] == b && wred_i[w] >= 0 && (ib < 0 || wred_i[w] < ib))) {
             b = wred[w]; ib = wred_i[w];
           }
@@ -533,19 +558,21 @@ __global__ void __launch_bounds__(NT) k_jacobi(EigJob* jobs, long long smem_doub
         lj[i] = v * inv;
       }
       __syncthreads();
-      double rem = 0.0;
-      for (int i = tid; i < n; i += NT) {
-        const double v = (i == p) ? -1.0 : dg[i] - lj[i] * lj[i];
-        dg[i] = v;
-        rem += fmax(v, 0.0);
+      if (act) {
+        double rem = 0.0;
+        for (int i = tid; i < n; i += NT) {
+          const double v = (i == p) ? -1.0 : dg[i] - lj[i] * lj[i];
+          dg[i] = v;
+          rem += fmax(v, 0.0);
+        }
+        for (int o = 16; o > 0; o >>= 1) rem += __shfl_down_sync(0xffffffffu, rem, o);
+        if ((tid & 31) == 0) wred[tid >> 5] = rem;
       }
-      for (int o = 16; o > 0; o >>= 1) rem += __shfl_down_sync(0xffffffffu, rem, o);
-      if ((tid & 31) == 0) wred[tid >> 5] = rem;
       __syncthreads();
       if (tid == 0) {
         rt_s = j + 1;
         double t = 0.0;
-        for (int w = 0; w < NT / 32; ++w) t += wred[w];
+        for (int w = 0; w < nwa; ++w) t += wred[w];
         dpiv_s = t;   // trace left outside L L^T
       }
       __syncthreads();

@@ -825,9 +825,22 @@ slar_status solve_bdf(slar_ctx* c, double coef, double tol_abs, slar_stats* st) 
       CKS(eval_residual(c, w->U, w->rhs, w->G0, 1));
       st->g_evals += 1;
     }
-    CKS(pc_probe(c, w->U));
-    st->g_evals += c->dv + 2;
+    // the blocks of the previous BDF3 step are reused unless they are missing, were probed for
+    // another beta dt, are 8 steps old, or the last solve with them needed more than 2 GMRES
+    // iterations beyond the solve right after their probe (or failed)
+    const bool probe = c->pc_age < 0 || c->pc_stale || c->pc_age >= kPcMaxAge || coef != c->pc_coef;
+    if (probe) {
+      CKS(pc_probe(c, w->U));
+      st->g_evals += c->dv + 2;
+      c->pc_age = 0;
+      c->pc_coef = coef;
+      st->pc_built = 1;
+    } else {
+      c->pc_age += 1;
+    }
     CKS(jfnk(c, coef, tol_abs, &ss, true));
+    if (probe) c->pc_krylov_ref = ss.krylov;
+    c->pc_stale = !ss.converged || ss.krylov > c->pc_krylov_ref + 2;
     if (!ss.converged) {
       st->fallback = 1;
       st->newton += ss.newton;

@@ -51,7 +51,8 @@ class Stats(C.Structure):
                 ("totals", C.c_double * 4), ("eval_ms", C.c_double), ("eval_flop", C.c_double),
                 ("launches", C.c_longlong), ("phase_ms", C.c_double * 6),
                 ("guess_used", C.c_int), ("fallback", C.c_int), ("recorded", C.c_int),
-                ("g_evals", C.c_int), ("eval_tile", C.c_int), ("rank_capped", C.c_int)]
+                ("g_evals", C.c_int), ("eval_tile", C.c_int), ("rank_capped", C.c_int),
+                ("pc_built", C.c_int)]
 
     def to_dict(self):
         return dict(entries=self.entries, ranks=list(self.ranks), aca_rank=list(self.aca_rank[: self.n_slar]),
