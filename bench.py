@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--train-iters", type=int, default=1500)
     p.add_argument("--large-steps", type=int, default=3,
                    help="timed steps of the 128^4 configurations (0 skips them)")
+    p.add_argument("--c5-steps", type=int, default=8,
+                   help="BDF3 steps of the 128^4 strong-Landau learned / precond / plain comparison (0: skip)")
     p.add_argument("--ensemble-runs", type=int, default=64)
     p.add_argument("--ensemble-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -459,6 +461,48 @@ def run_ours(args, w):
                                f"after the DIRK3 start-up")
             large[wname] = res
 
+    # ---- the 2D-2V strong Landau configuration with the learned warm start: the network
+    # trained (untimed, offline) on solver-generated samples of seeded strong-Landau runs at
+    # 128^4 (alpha ~ U[0.3, 0.6], k ~ U[0.4, 0.6], seed 7; weights shipped with the package),
+    # on the held-out run alpha 0.5, k 0.5; learned vs preconditioner alone vs the paper's
+    # plain JFNK, FP32 entries, the same Newton tolerance ----
+    c5 = None
+    if args.c5_steps > 0:
+        from paper_2606_29027_b300 import warmstart
+        wpath = os.path.join(ROOT, "paper_2606_29027_b300", "weights", "warmstart_strong_landau_128.npy")
+        held = inputs.landau_2d2v(n=128, alpha=0.5, k=0.5, cap=64, dt=0.2)
+        c5 = {"workload": "2D2V strong Landau alpha 0.5, k 0.5, 128^4, v in [-6,6]^2, rank cap 64, eps 1e-5, "
+                          f"dt 0.2; {args.c5_steps} BDF3 steps after the DIRK3 start-up; FP32 entries",
+              "network": json.load(open(wpath.replace(".npy", ".json"))) if os.path.exists(wpath) else None}
+        for solver in ("learned", "precond", "plain"):
+            if solver == "learned" and not os.path.exists(wpath):
+                continue
+            cc = slar.Context(slar.make_config(held, precision="fp32", solver=solver, profile=True), stream=stream)
+            net5 = None
+            if solver == "learned":
+                net5 = slar.Net(4, 128, 128, max_batch=1, stream=stream)
+                net5.set_params(warmstart.load_params(wpath))
+                cc.attach_net(net5)
+            with torch.cuda.stream(stream):
+                cc.init_ht(inputs.initial_factors(held))
+                for _ in range(2):
+                    cc.step(held.dt)
+            barrier()
+            ms5, st5 = time_steps(cc, held, args.c5_steps, flush, stream)
+            t5 = float(sum(ms5))
+            c5[solver] = {"value": args.c5_steps / (t5 / 1000.0), "unit": UNIT, "ms_per_step": t5 / args.c5_steps,
+                          "newton_per_step": float(np.mean([x.newton for x in st5])),
+                          "krylov_per_step": float(np.mean([x.krylov for x in st5])),
+                          "g_evals_per_step": float(np.mean([x.g_evals for x in st5])),
+                          "jfnk_ms_per_step": float(np.mean([x.phase_ms[4] for x in st5])),
+                          "guess_used_steps": int(sum(x.guess_used for x in st5)),
+                          "fallback_steps": int(sum(x.fallback for x in st5)),
+                          "rank_capped_steps": int(sum(1 for x in st5 if x.rank_capped)),
+                          "W_last": st5[-1].field_energy}
+            del cc
+            if net5 is not None:
+                net5.close()
+
     # ---- ensemble of uneven runs (1D1V/2D2V Landau/two-stream, 32-128 points per
     # dimension, rank caps 8-48), concurrent on private streams vs one after another ----
     ensemble = None
@@ -550,6 +594,7 @@ def run_ours(args, w):
             "warm_start_training": train_info,
             "ensemble": ensemble,
             "large_128": large,
+            "c5_strong_landau_learned": c5,
             "newton_per_step": float(np.mean([s.newton for s in stats])),
             "krylov_per_step": float(np.mean([s.krylov for s in stats])),
             "roofline": {"kernel": f"k_sl_eval_dev<{'double' if args.precision == 'fp64' else 'float'}> "
@@ -587,6 +632,8 @@ def run_ours(args, w):
         "forms_launches_per_step": {k: round(v["launches_per_step"], 1) for k, v in forms.items()},
         "learned_guess_used_steps": forms.get("fp32_learned", {}).get("guess_used_steps"),
         "c1_us_per_step": c1["us_per_step"] if c1 else None,
+        "c5_g_evals_per_step": ({k: round(v["g_evals_per_step"], 1) for k, v in c5.items()
+                                 if isinstance(v, dict) and "g_evals_per_step" in v} if c5 else None),
         "cpu_single_thread_steps_per_s": line.get("cpu_baseline", {}).get("single_thread"),
         "roofline_frac": achieved / peak}
     print(json.dumps(line), flush=True)

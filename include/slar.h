@@ -74,7 +74,9 @@ enum {
                               are kept over BDF3 steps and probed again at the first BDF3 step,
                               when dt changes, after 8 steps, after a failed solve, or when a
                               solve needed more than 2 GMRES iterations beyond the solve that
-                              followed the last probe (stats.pc_built) */
+                              followed the last probe (stats.pc_built).  After a preconditioned
+                              solve that did not converge (stats.fallback) the next 8 BDF3 steps
+                              are solved by plain JFNK. */
     SLAR_LEARNED = 32,     /* warm start of the BDF3 solves from the network attached with
                               slar_attach_net: initial guess U* + s_D d(x) (kept only if its
                               residual is not larger than that of U(F*)) and a per-point block

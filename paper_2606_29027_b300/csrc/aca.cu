@@ -987,8 +987,13 @@ slar_status eval_check_rows(slar_ctx* c, int in, bool with_corr, double tau, con
   }
   const int cand[3] = {16, 32, 64};
   float best_ms = 1e30f;
-  int best = 32;
+  int best = 16;
+  const bool f32 = c->cfg.precision != SLAR_FP64;
   for (int q = 0; q < 3; ++q) {
+    // a tile whose shared memory does not fit at these ranks is not a candidate
+    const int fit = f32 ? sl_eval_fit_tile<float>(c->g, c->ht[in].r, cand[q])
+                        : sl_eval_fit_tile<double>(c->g, c->ht[in].r, cand[q]);
+    if (fit != cand[q]) continue;
     c->eval_tile = cand[q];
     CKS(eval_entries(c, in, with_corr, a, 0));   // warm-up (and the values, if last)
     CK(cudaEventRecord(c->tune_ev[0], c->s));
@@ -1070,6 +1075,9 @@ slar_status slar_call(slar_ctx* c, int in, bool with_corr, double tau, const dou
     CKS(eval_check_rows(c, in, with_corr, tau, E));
     chk_entries = (long long)c->n_chk * M2;
   }
+  if (!tc)
+    c->eval_tile = f32 ? sl_eval_fit_tile<float>(c->g, hin.r, c->eval_tile)
+                       : sl_eval_fit_tile<double>(c->g, hin.r, c->eval_tile);
   const size_t need = tc ? sl_eval_tc_smem(hin.r, tc)
                          : f32 ? sl_eval_smem<float>(c->g, hin.r, c->eval_tile)
                                : sl_eval_smem<double>(c->g, hin.r, c->eval_tile);

@@ -165,6 +165,9 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
     g.h[m] = m < c->d ? (cfg->hi[m] - cfg->lo[m]) / cfg->N[m] : 1.0;
     g.lof[m] = (float)g.lo[m];
     g.hf[m] = (float)g.h[m];
+    // 16 FP32 ulps (2^-23 relative) of the largest cell coordinate a foot can take
+    const double tmax = g.N[m] + std::max(std::fabs(g.lo[m]), std::fabs(m < c->d ? cfg->hi[m] : 1.0)) / g.h[m];
+    g.guard[m] = (float)(16.0 * std::ldexp(1.0, -23) * tmax);
   }
   for (int m = 0; m < c->dx; ++m) g.NX *= g.N[m];
   for (int m = 0; m < c->dv; ++m) g.NV *= g.N[c->dx + m];
@@ -408,6 +411,7 @@ slar_status init_ht(slar_ctx* c, int n_terms, const double* factors) {
   c->step = 0;
   c->dt_hist[0] = c->dt_hist[1] = 0.0;
   c->pc_age = -1;
+  c->pc_off = 0;
   CKS(conserved_of_state(c, true));
   c->has_U = true;
   CK(cudaStreamSynchronize(c->s));
@@ -807,6 +811,7 @@ slar_status slar_restore(slar_ctx* c, const char* path) {
   c->dt_hist[1] = hd.dt_hist[1];
   for (int t = 0; t < 6; ++t) c->Sn[t] = hd.Sn[t];
   c->pc_age = -1;   // the preconditioner is not saved: the next BDF3 step probes it again
+  c->pc_off = 0;
   return SLAR_OK;
 }
 

@@ -32,6 +32,7 @@ struct GridDesc {
   int NX;  // prod of spatial N
   int NV;  // prod of velocity N
   int S;   // interpolation stencil points per dimension: 3 (quadratic) or 5 (quartic, FP64)
+  float guard[4];   // FP32 paths: cells from a face below which a foot is traced again in FP64
 };
 
 template <typename T>
@@ -105,6 +106,9 @@ cudaError_t launch_sl_eval_dev(const GridDesc& g, const EvalParams<T>* P, const 
                                size_t smem_bytes, cudaStream_t s, int tile = 32);
 template <typename T>
 size_t sl_eval_smem(const GridDesc& g, const int* ranks6, int tile = 32);
+// the largest evaluator tile <= tile whose shared memory fits the opt-in limit at these ranks
+template <typename T>
+int sl_eval_fit_tile(const GridDesc& g, const int* ranks6, int tile);
 // opt the evaluator kernels into large dynamic shared memory (call before any capture)
 cudaError_t sl_eval_init_attrs();
 cudaError_t linalg_init_attrs();

@@ -207,6 +207,7 @@ struct slar_ctx {
   double pc_coef = 0.0;
   int pc_krylov_ref = 0;
   bool pc_stale = false;
+  int pc_off = 0;   // BDF3 steps left before the preconditioned solve is tried again
 
   char err[512] = {0};
 };
@@ -272,6 +273,8 @@ void bdf3_variable(const double h[3], double a[3], double* beta);
 constexpr double kBdf3RatioMax = 1.4877;
 // BDF3 steps a probed block-circulant preconditioner is kept at most
 constexpr int kPcMaxAge = 8;
+// BDF3 steps solved by plain JFNK after a preconditioned solve fell back to it
+constexpr int kPcOffSteps = 8;
 // adaptive step size: cfl / max_i(a_i / Delta_i), capped at dt_max and, after the start-up,
 // at kBdf3RatioMax times the previous step (field of the current state)
 slar_status cfl_dt(slar_ctx* c, double cfl, double dt_max, double* dt);

@@ -235,7 +235,7 @@ __device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& 
 
 // ---- FP32 variants (FP32 / BF16x3 entry paths): the same formulas in single precision.
 // Their feet can differ from the FP64 ones by ~1e-7 relative.  Where that could move an
-// entry to the neighbouring stencil -- its FP32 foot lies within kFaceGuard cells of a cell
+// entry to the neighbouring stencil -- its FP32 foot lies within g.guard cells of a cell
 // face, and the two quadratic stencils there differ by Delta^3 f''' / 8 -- the foot is traced
 // again in FP64 (foot_cells_ft), so both paths interpolate from the same cells.
 
@@ -334,14 +334,13 @@ __device__ __forceinline__ void trace_foot_f(const GridDesc& g, const float* E, 
   else trace_foot_ft<1>(g, E, tau_d, euler, idx, foot);
 }
 
-// Distance (in cells) from a cell face below which an FP32 foot is traced again in FP64.
-// The FP32 foot's error is a few ulps of its cell coordinate t = (y - lo) / Delta (|t| of a
-// few hundred at most), i.e. below 1e-4 cells; 1/2048 leaves a factor of four.
-constexpr float kFaceGuard = 1.0f / 2048.0f;
-
 // Foot, cells and weights of one entry in the FP32 paths (2 DX dimensions): the FP32 foot,
-// unless it lies within kFaceGuard of a cell face in some dimension, in which case the entry
-// takes the FP64 foot (E64 given) with the FP64 path's cells and weights (rounded to FP32).
+// unless it lies within g.guard[m] cells of a cell face in some dimension m, in which case the
+// entry takes the FP64 foot (E64 given) with the FP64 path's cells and weights (rounded to
+// FP32).  The guard is 16 FP32 ulps of the largest cell coordinate |t| = |y - lo| / Delta the
+// foot can take (N plus the box offset in cells): the FP32 RK3 foot carries a few ulps of y
+// and of t, so 16 leaves a margin of about four, and fewer feet pay for the FP64 trace (a
+// dependent FP64 division costs ~440 cycles on B300, and a warp waits for its slowest lane).
 // rows / w: [2 DX][3].
 template <int DX>
 __device__ __forceinline__ void foot_cells_ft(const GridDesc& g, const float* E32, const double* E64, double tau,
@@ -353,7 +352,7 @@ __device__ __forceinline__ void foot_cells_ft(const GridDesc& g, const float* E3
   for (int m = 0; m < D; ++m) {
     const float t = (foot[m] - g.lof[m]) / g.hf[m];
     const float fr = t - floorf(t);
-    near |= !(fr >= kFaceGuard && fr <= 1.f - kFaceGuard);   // also catches a non-finite t
+    near |= !(fr >= g.guard[m] && fr <= 1.f - g.guard[m]);   // also catches a non-finite t
   }
   if (near && E64) {
     double fd[4];

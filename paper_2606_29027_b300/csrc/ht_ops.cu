@@ -130,8 +130,10 @@ slar_status eval_entries(slar_ctx* c, int slot, bool with_corr, const EvalArgs& 
                           &c->ast->tc_err, tc_pieces(c), c->s);
   } else if (c->cfg.precision != SLAR_FP64) {
     CKS(refresh_f32_slot(c, slot));
+    c->eval_tile = sl_eval_fit_tile<float>(c->g, c->ht[slot].r, c->eval_tile);
     e = launch_sl_eval<float>(c->g, view32_slot(c, slot), corr_view(c, with_corr), b, at_grid, c->s, c->eval_tile);
   } else {
+    c->eval_tile = sl_eval_fit_tile<double>(c->g, c->ht[slot].r, c->eval_tile);
     e = launch_sl_eval<double>(c->g, view64(c, slot), corr_view(c, with_corr), a, at_grid, c->s, c->eval_tile);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "sl_eval kernel");

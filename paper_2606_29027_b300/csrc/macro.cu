@@ -794,8 +794,14 @@ slar_status solve_bdf(slar_ctx* c, double coef, double tol_abs, slar_stats* st) 
   cudaStream_t s = c->s;
   const int n = w->nvec;
   double* misc = w->sc + SC_MISC;
-  const bool learned = (c->cfg.flags & SLAR_LEARNED) && c->net;
-  const bool pc = learned || (c->cfg.flags & (SLAR_PRECOND | SLAR_LEARNED));
+  // the preconditioned (and learned) solve is switched off for kPcOffSteps BDF3 steps after
+  // one that did not converge and fell back to plain JFNK: where the block-circulant model of
+  // the Jacobian does not hold (strongly non-uniform states at large CFL numbers) each step
+  // would otherwise pay for a failed solve and the plain one
+  const bool pc_on = c->pc_off == 0;
+  if (c->pc_off > 0) c->pc_off -= 1;
+  const bool learned = (c->cfg.flags & SLAR_LEARNED) && c->net && pc_on;
+  const bool pc = pc_on && (learned || (c->cfg.flags & (SLAR_PRECOND | SLAR_LEARNED)));
   CK(cudaMemcpyAsync(w->U, w->Ufs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   SolveStats ss;
   if (!pc) {
@@ -843,6 +849,7 @@ slar_status solve_bdf(slar_ctx* c, double coef, double tol_abs, slar_stats* st) 
     c->pc_stale = !ss.converged || ss.krylov > c->pc_krylov_ref + 2;
     if (!ss.converged) {
       st->fallback = 1;
+      c->pc_off = kPcOffSteps;
       st->newton += ss.newton;
       st->krylov += ss.krylov;
       st->g_evals += ss.g_evals;

@@ -574,9 +574,11 @@ cudaError_t launch_tile_dev(const GridDesc& g, const EvalParams<T>* P, const Eva
   return cudaGetLastError();
 }
 
+constexpr int kEvalSmemMax = 200 * 1024;   // opt-in dynamic shared memory of the evaluators
+
 template <typename T, int TILE>
 cudaError_t set_attrs_tile() {
-  const int mx = 200 * 1024;
+  const int mx = kEvalSmemMax;
   cudaError_t e = cudaFuncSetAttribute(k_sl_eval<T, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_dev<T, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   return e;
@@ -585,6 +587,19 @@ cudaError_t set_attrs_tile() {
 }  // namespace
 
 bool eval_tile_ok(int tile) { return tile == 16 || tile == 32 || tile == 64; }
+
+template <typename T>
+size_t sl_eval_smem(const GridDesc& g, const int* r6, int tile);
+
+// the largest tile <= `tile` (16, 32, 64) whose shared memory fits the evaluator's opt-in
+// limit at these ranks (FP64 at rank 64 with tile 64 does not)
+template <typename T>
+int sl_eval_fit_tile(const GridDesc& g, const int* r6, int tile) {
+  while (tile > 16 && sl_eval_smem<T>(g, r6, tile) > (size_t)kEvalSmemMax) tile /= 2;
+  return tile;
+}
+template int sl_eval_fit_tile<double>(const GridDesc&, const int*, int);
+template int sl_eval_fit_tile<float>(const GridDesc&, const int*, int);
 
 template <typename T>
 cudaError_t launch_sl_eval(const GridDesc& g, const HTView<T>& ht, const CorrView& corr,

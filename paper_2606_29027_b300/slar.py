@@ -62,7 +62,7 @@ class Stats(C.Structure):
                     launches=self.launches, phase_ms=list(self.phase_ms),
                     guess_used=bool(self.guess_used), fallback=bool(self.fallback),
                     recorded=bool(self.recorded), g_evals=self.g_evals, eval_tile=self.eval_tile,
-                    rank_capped=self.rank_capped)
+                    rank_capped=self.rank_capped, pc_built=bool(self.pc_built))
 
 
 class HTView(C.Structure):
