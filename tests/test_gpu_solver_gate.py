@@ -1,0 +1,68 @@
+"""GPU tests of the Newton-Krylov solver policy and of the evaluator's launch shape at large
+ranks.
+
+* The block-circulant preconditioner (an addition to the paper's plain JFNK) is probed at the
+  first BDF3 step and kept while it works: the converged U^{n+1} equals the plain JFNK one to
+  the Newton tolerance, with fewer probes than BDF3 steps.
+* After a preconditioned solve falls back to plain JFNK, the next 8 BDF3 steps are solved by
+  plain JFNK alone (no probe, no fallback), then the preconditioner is tried again.  The
+  failure is made on the host side: newton_max = 1 stops every solve short of the tolerance.
+* FP64 entries at rank 64 (2D-2V strong Landau 64^4, rank cap 64): the evaluator's tile is
+  clamped to the shared memory that fits, so the steps run (64 entries per CTA would need more
+  than the evaluator's 200 KB).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_29027_b300 import inputs, slar
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(w, steps, **kw):
+    ctx = slar.Context(slar.make_config(w, **kw))
+    ctx.init_ht(inputs.initial_factors(w))
+    st = [ctx.step(w.dt) for _ in range(steps)]
+    U = torch.zeros((w.dv + 2, ctx.NX), dtype=torch.float64, device="cuda")
+    ctx.get_conserved(U)
+    ctx.close()
+    return st, U.cpu().numpy()
+
+
+def test_preconditioner_kept_between_probes():
+    w = inputs.landau_2d2v(n=16, alpha=0.2, eps=1e-6, cap=16)
+    sp, Up = _run(w, 12, solver="plain")
+    sc, Uc = _run(w, 12, solver="precond")
+    bdf = sc[2:]
+    assert all(s.converged for s in sc)
+    assert bdf[0].pc_built == 1
+    assert 1 <= sum(s.pc_built for s in bdf) < len(bdf)
+    assert np.max(np.abs(Uc - Up)) <= 1e-9 * np.max(np.abs(Up))
+    assert sum(s.g_evals for s in bdf) < sum(s.g_evals for s in sp[2:])
+
+
+def test_preconditioner_off_after_fallback():
+    w = inputs.landau_2d2v(n=16, alpha=0.2, eps=1e-6, cap=16)
+    st, _ = _run(w, 13, solver="precond", newton_max=1)
+    bdf = st[2:]
+    assert all(s.status == slar.SLAR_ENOCONV for s in st)
+    assert bdf[0].pc_built == 1 and bdf[0].fallback == 1
+    for s in bdf[1:9]:
+        assert s.pc_built == 0 and s.fallback == 0
+    assert bdf[9].pc_built == 1 and bdf[9].fallback == 1
+
+
+def test_fp64_rank64_evaluator_fits():
+    w = inputs.landau_2d2v(n=64, alpha=0.5, k=0.5, cap=64, dt=0.2)
+    ctx = slar.Context(slar.make_config(w, precision="fp64", solver="precond"))
+    ctx.init_ht(inputs.initial_factors(w))
+    prev = 0
+    for _ in range(3):
+        s = ctx.step(w.dt)
+        assert s.converged and s.status in (slar.SLAR_OK, slar.SLAR_ERANK)
+        if prev == 64:   # the step evaluated a state of rank 64
+            assert s.eval_tile in (16, 32)
+        prev = max(s.ranks)
+    ctx.close()
+    assert prev == 64
