@@ -166,20 +166,23 @@ def test_nan_in_conserved_variables_gives_enan():
 def test_newton_cap_gives_enoconv_and_fallback(solver):
     """newton_max = 1 cannot reach the 1e-12 Newton tolerance: the step returns
     SLAR_ENOCONV; the preconditioned and learned solves report that they fell back to
-    plain JFNK from U(F*)."""
+    plain JFNK from U(F*) at the first BDF3 step, and the next BDF3 step is solved by plain
+    JFNK alone (the preconditioned solve is switched off after a fallback)."""
     w = inputs.landau_1d1v(N=(32, 64), alpha=0.3)
     ctx = _ctx(w, solver=solver, newton_max=1)
     if solver == "learned":
         net = slar.Net(w.dv + 2, w.N[0], 1, hidden=8, max_batch=2)
         ctx.attach_net(net)
-    statuses, fallbacks = [], []
+    statuses, fallbacks, built = [], [], []
     for _ in range(4):
         s = ctx.step(w.dt)
         statuses.append(s.status)
         fallbacks.append(s.fallback)
+        built.append(s.pc_built)
     assert statuses[-1] == slar.SLAR_ENOCONV
     if solver != "plain":
-        assert fallbacks[-1]          # BDF3 step (index 3): preconditioned solve, then plain JFNK
+        assert fallbacks[2] and built[2]   # first BDF3 step: preconditioned solve, then plain JFNK
+        assert not fallbacks[3] and not built[3]   # next BDF3 step: plain JFNK only
 
 
 def test_replayed_pivots_outside_the_matricisation_are_rejected():
