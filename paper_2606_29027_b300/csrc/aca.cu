@@ -795,7 +795,7 @@ slar_status aca_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle h, int
     if (ev) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], s));
     cudaError_t e =
         tc ? launch_sl_eval_tc_dev(c->g, static_cast<const EvalParams<float>*>(c->evp), a, c->tc_b12, c->tc_b34,
-                                   &c->ast->tc_err, tc, smem, s)
+                                   c->tc_broot, &c->ast->tc_err, tc, smem, c->tc_sc, s)
         : f32 ? launch_sl_eval_dev<float>(c->g, static_cast<const EvalParams<float>*>(c->evp), a, smem, s,
                                           c->eval_tile)
               : launch_sl_eval_dev<double>(c->g, static_cast<const EvalParams<double>*>(c->evp), a, smem, s,
@@ -862,7 +862,7 @@ slar_status aca_block_step(slar_ctx* c, size_t smem, cudaGraphConditionalHandle 
     if (ev) CK(cudaEventRecord(c->prof_ev[2 * c->prof_n], s));
     cudaError_t e =
         tc ? launch_sl_eval_tc_dev(c->g, static_cast<const EvalParams<float>*>(c->evp), a, c->tc_b12, c->tc_b34,
-                                   &c->ast->tc_err, tc, smem, s)
+                                   c->tc_broot, &c->ast->tc_err, tc, smem, c->tc_sc, s)
         : f32 ? launch_sl_eval_dev<float>(c->g, static_cast<const EvalParams<float>*>(c->evp), a, smem, s,
                                           c->eval_tile)
               : launch_sl_eval_dev<double>(c->g, static_cast<const EvalParams<double>*>(c->evp), a, smem, s,

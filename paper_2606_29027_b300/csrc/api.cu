@@ -96,7 +96,7 @@ void free_ctx(slar_ctx* c) {
     F(c->ht[sl].B12); F(c->ht[sl].B34); F(c->ht[sl].Broot);
   }
   for (int m = 0; m < 4; ++m) { F(c->U32[m]); F(c->Qleaf[m]); F(c->Rleaf[m]); }
-  F(c->B12_32); F(c->B34_32); F(c->Broot32); F(c->tc_b12); F(c->tc_b34); F(c->Ik); F(c->Lt[0]); F(c->Lt[1]);
+  F(c->B12_32); F(c->B34_32); F(c->Broot32); F(c->tc_b12); F(c->tc_b34); F(c->tc_scratch); F(c->tc_broot); F(c->Ik); F(c->Lt[0]); F(c->Lt[1]);
   F(c->dC); F(c->qv); F(c->dC32); F(c->qv32); F(c->E32); F(c->Uc); F(c->Uh1); F(c->Uh2);
   F(c->Ua); F(c->Va); F(c->rowbuf); F(c->usedr); F(c->usedc); F(c->pivI); F(c->pivJ);
   F(c->ast); F(c->aca_part); F(c->aca_dots);
@@ -202,11 +202,17 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   if (d == 4) { A(c->B12_32, (size_t)R * R * R); A(c->B34_32, (size_t)R * R * R); }
   A(c->Broot32, (size_t)R * R);
   if (tc_pieces(c) > 0) {
+    // prologue scratch for the largest launch: a block of ACA_BMAX fibres (or the check
+    // rows) of the longer matricisation side, whole 128-entry tiles
+    const long long cap = ((long long)ACA_BMAX * std::max(c->M1, c->M2) + 127) / 128 * 128;
     if (cudaMalloc(&c->tc_b12, (size_t)tc_split_bytes(tc_pieces(c))) != cudaSuccess ||
-        cudaMalloc(&c->tc_b34, (size_t)tc_split_bytes(tc_pieces(c))) != cudaSuccess) {
+        cudaMalloc(&c->tc_b34, (size_t)tc_split_bytes(tc_pieces(c))) != cudaSuccess ||
+        cudaMalloc(&c->tc_scratch, (size_t)tc_scratch_bytes(cap)) != cudaSuccess ||
+        cudaMalloc(&c->tc_broot, (size_t)64 * 64 * 2 * 3) != cudaSuccess) {
       free_ctx(c);
       return SLAR_ENOMEM;
     }
+    c->tc_sc = tc_scratch_view(c->tc_scratch, cap);
   }
   A(c->Ik, (size_t)R * R);
   if (d == 2) { A(c->Lt[0], (size_t)c->M1 * c->kmax); A(c->Lt[1], (size_t)c->M2 * c->kmax); }

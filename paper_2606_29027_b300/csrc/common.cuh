@@ -112,18 +112,33 @@ int sl_eval_fit_tile(const GridDesc& g, const int* ranks6, int tile);
 // opt the evaluator kernels into large dynamic shared memory (call before any capture)
 cudaError_t sl_eval_init_attrs();
 cudaError_t linalg_init_attrs();
-// tensor-core (tcgen05) evaluator for d = 4 trees (sl_eval_tc.cu): 128 entries per CTA;
-// pieces = 2 (BF16x3) or 3 (BF16x6); b12 / b34 are the transfer tensors pre-split by
-// split_transfer_bf16 with the same piece count (tc_split_bytes(pieces) each); err (device
-// int) is set if an MMA completion wait runs out
+// tensor-core (tcgen05) evaluator for d = 4 trees (sl_eval_tc.cu): a prologue kernel (feet,
+// leaf gathers, operand split; several CTAs per SM) writes per-entry scratch that the
+// tensor-core kernel (128 entries per CTA, one CTA per SM) reads; pieces = 2 (BF16x3) or 3
+// (BF16x6); b12 / b34 are the transfer tensors pre-split by split_transfer_bf16 with the same
+// piece count (tc_split_bytes(pieces) each); err (device int) is set if an MMA completion
+// wait runs out.  Scratch: tc_scratch_bytes(cap) bytes for cap entries (a multiple of 128).
+struct TcScratch {
+  unsigned char* a;   // A tiles per 128-entry tile
+  float* c1;          // [cap][2][64]
+  int* rows;          // [cap][12]
+  float* w;           // [cap][12]
+  long long cap;
+};
+long long tc_scratch_bytes(long long cap);
+TcScratch tc_scratch_view(void* base, long long cap);
 size_t sl_eval_tc_smem(const int* ranks6, int pieces);
 long long tc_split_bytes(int pieces);
 cudaError_t sl_eval_tc_init_attrs();
 cudaError_t split_transfer_bf16(const float* B, int rp, int ra, int rb, void* out, int pieces, cudaStream_t s);
+// Broot [r12][r34] pre-split for the root contraction on the tensor cores (<= 24 KiB)
+cudaError_t split_root_bf16(const float* Broot, int r12, int r34, void* out, int pieces, cudaStream_t s);
 cudaError_t launch_sl_eval_tc(const GridDesc& g, const HTView<float>& ht, const CorrView& corr, const EvalArgs& a,
-                              const void* b12, const void* b34, int* err, int pieces, cudaStream_t s);
+                              const void* b12, const void* b34, const void* broot, int* err, int pieces,
+                              const TcScratch& sc, cudaStream_t s);
 cudaError_t launch_sl_eval_tc_dev(const GridDesc& g, const EvalParams<float>* P, const EvalArgs& a, const void* b12,
-                                  const void* b34, int* err, int pieces, size_t smem_bytes, cudaStream_t s);
+                                  const void* b34, const void* broot, int* err, int pieces, size_t smem_bytes,
+                                  const TcScratch& sc, cudaStream_t s);
 
 // dense FP64 linear algebra (linalg.cu)
 // C[b] = alpha op(A[b]) op(B[b]) + beta C[b]; row-major; op(A) is M x K.

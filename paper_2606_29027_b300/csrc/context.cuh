@@ -76,6 +76,9 @@ struct slar_ctx {
   float* B12_32 = nullptr;
   float* B34_32 = nullptr;
   float* Broot32 = nullptr;
+  void* tc_scratch = nullptr;   // the tensor-core evaluator's prologue scratch (tc_sc views it)
+  slar::TcScratch tc_sc{};
+  void* tc_broot = nullptr;  // the FP32 shadow's root matrix pre-split for the tensor cores
   void* tc_b12 = nullptr;   // BF16x3 pre-split transfer tensors of the FP32 shadow
   void* tc_b34 = nullptr;
   double* Ik = nullptr;     // identity (kmax x kmax)

@@ -72,6 +72,7 @@ slar_status refresh_f32_slot(slar_ctx* c, int slot) {
     if (tc_pieces(c) > 0) {
       CK(split_transfer_bf16(c->B12_32, h.r[4], h.r[0], h.r[1], c->tc_b12, tc_pieces(c), c->s));
       CK(split_transfer_bf16(c->B34_32, h.r[5], h.r[2], h.r[3], c->tc_b34, tc_pieces(c), c->s));
+      CK(split_root_bf16(c->Broot32, h.r[4], h.r[5], c->tc_broot, tc_pieces(c), c->s));
     }
   } else {
     bt.add(h.Broot, c->Broot32, (long long)h.r[0] * h.r[1]);
@@ -127,7 +128,7 @@ slar_status eval_entries(slar_ctx* c, int slot, bool with_corr, const EvalArgs& 
   if (tc_pieces(c) > 0 && !at_grid) {
     CKS(refresh_f32_slot(c, slot));
     e = launch_sl_eval_tc(c->g, view32_slot(c, slot), corr_view(c, with_corr), b, c->tc_b12, c->tc_b34,
-                          &c->ast->tc_err, tc_pieces(c), c->s);
+                          c->tc_broot, &c->ast->tc_err, tc_pieces(c), c->tc_sc, c->s);
   } else if (c->cfg.precision != SLAR_FP64) {
     CKS(refresh_f32_slot(c, slot));
     c->eval_tile = sl_eval_fit_tile<float>(c->g, c->ht[slot].r, c->eval_tile);

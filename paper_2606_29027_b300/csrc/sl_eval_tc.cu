@@ -69,7 +69,8 @@ template <int PC> __host__ __device__ constexpr int tc_out34() { return 3 * tc_w
 template <int PC> __host__ __device__ constexpr int tc_out12b() { return 3 * tc_w<PC>() + 128; }
 template <int PC> __host__ __device__ constexpr int tc_out34b() { return 3 * tc_w<PC>() + 192; }
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;
-constexpr int TC_HEAD_BYTES = 16384;     // feet, weights, rows, values, partial sums
+constexpr int TC_HEAD_BYTES = 2048;      // values and partial sums of the root
+constexpr int PRO_HEAD_BYTES = 16384;    // prologue: feet, weights, rows
 constexpr int TC_MIN_SMEM = 120 * 1024;  // one CTA per SM: the 512-column allocation never waits
 
 __host__ __device__ __forceinline__ int r16(int r) { return ((r + 15) / 16) * 16; }
@@ -79,24 +80,25 @@ __host__ __device__ __forceinline__ int al128(int x) { return (x + 127) & ~127; 
 __host__ __device__ __forceinline__ int stage_ld(int r) { return r | 1; }   // odd row stride
 
 struct TcLayout {
-  int stage, A0, A1, B, slot, total;
+  int A0, A1, B, slot, rootB, total;
 };
 
 template <int PC>
 __host__ __device__ __forceinline__ TcLayout tc_layout(int r0, int r1, int r2, int r3, int r12, int r34) {
   TcLayout L;
-  (void)r34;
-  const int ra = r0 > r2 ? r0 : r2, rb = r1 > r3 ? r1 : r3;
-  const int rmax = ra > rb ? ra : rb;
-  int st = TC_TILE * stage_ld(rmax);
-  if (r12 * 64 > st) st = r12 * 64;   // Broot staged with row stride 64
+  (void)r0;
+  (void)r2;
   int o = TC_HEAD_BYTES;
-  L.stage = o; o = al128(o + 4 * st);
   L.A0 = o; o += TC_TILE * r16(r1) * 2 * PC;
   L.A1 = o; o += TC_TILE * r16(r3) * 2 * PC;
   const int s0 = tc_width<PC>(r16(r0)) * r16(r1) * 2 * PC, s1 = tc_width<PC>(r16(r2)) * r16(r3) * 2 * PC;
   L.slot = s0 > s1 ? s0 : s1;
   L.B = o; o += TC_STAGES * L.slot;
+  // the root contraction reuses the A and B regions once the chunk stream is over: its A
+  // operand (c34, 128 x r34) at A0, the pre-split Broot after it
+  L.rootB = al128(L.A0 + TC_TILE * r16(r34) * 2 * PC);
+  const int root_end = L.rootB + r16(r12) * r16(r34) * 2 * PC;
+  if (root_end > o) o = root_end;
   L.total = o > TC_MIN_SMEM ? o : TC_MIN_SMEM;
   return L;
 }
@@ -310,11 +312,33 @@ __device__ __forceinline__ void gather_leaf(float* stage, const float* __restric
   }
 }
 
-// stage (128 x r) -> A operand tiles (PC pieces), K padded to r16 with zeros
+// Pre-split Broot [r12][r34] (FP32) into the B operand of the root contraction: rows n = p
+// (N = r12 padded to 16), K = q (r34 padded to 16), one tile in the layout of a chunk with
+// wc = N, PC pieces.
 template <int PC>
+__global__ void k_split_root(const float* __restrict__ B, int r12, int r34, unsigned char* __restrict__ out) {
+  const int n16 = r16(r12), kr16 = r16(r34), ks = kr16 / 16, ng = kr16 / 8;
+  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= n16 * ng) return;
+  const int n = it / ng, kg = it % ng;
+  float x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int b = kg * 8 + j;
+    x[j] = (n < r12 && b < r34) ? B[(long long)n * r34 + b] : 0.f;
+  }
+  uint4 pc[PC];
+  split8<PC>(x, pc);
+  const int off = (kg >> 1) * n16 * 32 + (n >> 3) * 256 + (kg & 1) * 128 + (n & 7) * 16;
+#pragma unroll
+  for (int q = 0; q < PC; ++q) *reinterpret_cast<uint4*>(out + q * ks * n16 * 32 + off) = pc[q];
+}
+
+// stage (128 x r) -> A operand tiles (PC pieces), K padded to r16 with zeros
+template <int PC, int NT = TC_THREADS>
 __device__ __forceinline__ void stage_to_operand(const float* stage, int r, unsigned char* A) {
   const int ld = stage_ld(r), rb16 = r16(r), ks = rb16 / 16, ng = rb16 / 8;
-  for (int it = threadIdx.x; it < TC_TILE * ng; it += TC_THREADS) {
+  for (int it = threadIdx.x; it < TC_TILE * ng; it += NT) {
     const int e = it & (TC_TILE - 1), kg = it >> 7;
     float x[8];
 #pragma unroll
@@ -397,12 +421,132 @@ __device__ __forceinline__ void drain_chunk3(const float* creg, uint32_t trow, u
   }
 }
 
+// Scratch of the prologue, per entry e of a launch (capacity a multiple of TC_TILE):
+//   A tiles  tile t = e / 128 at a + t * tc_abytes: the split c2 of node 0 (leaf 1) and of
+//            node 1 (leaf 3) in the shared-memory operand layout, copied in one bulk copy;
+//   c1       c1[e][node][64] FP32 (leaf 0, leaf 2; zero beyond the rank);
+//   rows, w  the entry's stencil rows and weights [4][3] (for the correction epilogue).
+template <int PC>
+__host__ __device__ __forceinline__ long long tc_abytes(int r1, int r3) {
+  return (long long)TC_TILE * (r16(r1) + r16(r3)) * 2 * PC;
+}
+
+// Leaf gather of the prologue, a warp per entry row (lanes over the leaf's columns, no
+// integer division per item), four rows in flight per warp: row e of c = sum_s w[e][m][s]
+// U_m[row_s][:], zero for e >= nT.  Into the stage (row stride stage_ld(r)) for the A
+// operands, or into c1[e][node][0..63] (zero beyond r) in global scratch.
+constexpr int PRO_THREADS = 256;
+template <bool TO_C1>
+__device__ __forceinline__ void gather_rows(float* dst, const float* __restrict__ U, int r, int m, int nT,
+                                            const int* srow, const float* sw, int node) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ld = stage_ld(r);
+  for (int e0 = 4 * warp; e0 < TC_TILE; e0 += 4 * (PRO_THREADS / 32)) {
+    const float* u[4][3];
+    float w[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = e0 + k;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        u[k][q] = U + (long long)(e < nT ? srow[(e * 4 + m) * 3 + q] : 0) * r;
+        w[k][q] = e < nT ? sw[(e * 4 + m) * 3 + q] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      const int col = c0 + lane;
+      float v[4][3];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[k][q] = col < r ? __ldg(u[k][q] + col) : 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float x = w[k][0] * v[k][0] + w[k][1] * v[k][1] + w[k][2] * v[k][2];
+        if (TO_C1) dst[(long long)(e0 + k) * 128 + node * 64 + col] = x;   // zero beyond r (v = 0)
+        else if (col < r) dst[(e0 + k) * ld + col] = x;
+      }
+    }
+  }
+}
+
+// Prologue of the tensor-core evaluator, one CTA per 128-entry tile: the feet, cells and
+// weights, the four leaf gathers, the BF16 split of c2 of both nodes into the A tiles of
+// the tile and c1 of both nodes, all into global scratch.  A separate kernel so that these
+// latency-bound steps run at several CTAs per SM and overlap one another, while the
+// tensor-core kernel (one CTA per SM) starts its MMAs as soon as one bulk copy of the A
+// tiles has landed.
+template <bool DEV, int PC>
+__global__ void __launch_bounds__(PRO_THREADS)
+k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restrict__ P, EvalArgs a,
+              TcScratch sc) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  HTView<float> ht;
+  if (DEV) {
+    const EvalParams<float> q = *P;
+    ht = q.ht;
+    a.tau = q.tau;
+    a.E = q.E;
+    a.E32 = q.E32;
+    a.foot_euler = q.foot_euler;
+  } else {
+    ht = ht_arg;
+  }
+  if ((a.done && *a.done) || (a.skip && *a.skip)) return;
+  if (a.kidx) a.pivot += *a.kidx;
+  const long long e0 = (long long)blockIdx.x * TC_TILE;
+  const long long n_act = a.nact ? min(a.n, (long long)(*a.nact) * a.nper) : a.n;
+  if (e0 >= n_act) return;
+  const int nT = (int)min((long long)TC_TILE, n_act - e0);
+  const int tid = threadIdx.x;
+  float* sw = reinterpret_cast<float*>(smem_raw);                     // 128 x 12
+  int* srow = reinterpret_cast<int*>(sw + TC_TILE * 12);              // 128 x 12
+  float* stage = reinterpret_cast<float*>(smem_raw + PRO_HEAD_BYTES);
+  if (tid < nT) {
+    int idx[4];
+    decode_tuple(g, a, e0 + tid, idx);
+    float foot[4];
+    int r[12];
+    float w[12];
+    foot_cells_ft<2>(g, a.E32, a.E, a.tau, a.foot_euler, idx, foot, r, w);   // d = 4: two spatial dimensions
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      srow[tid * 12 + k] = r[k];
+      sw[tid * 12 + k] = w[k];
+      sc.rows[(e0 + tid) * 12 + k] = r[k];
+      sc.w[(e0 + tid) * 12 + k] = w[k];
+    }
+  }
+  __syncthreads();
+  unsigned char* At = sc.a + (long long)blockIdx.x * tc_abytes<PC>(ht.r[1], ht.r[3]);
+  float* c1 = sc.c1 + e0 * 128;
+  // c1 of both nodes straight to the scratch, then c2 of each node through the stage
+  gather_rows<true>(c1, ht.U[0], ht.r[0], 0, nT, srow, sw, 0);
+  gather_rows<true>(c1, ht.U[2], ht.r[2], 2, nT, srow, sw, 1);
+  gather_rows<false>(stage, ht.U[1], ht.r[1], 1, nT, srow, sw, 0);
+  __syncthreads();
+  stage_to_operand<PC, PRO_THREADS>(stage, ht.r[1], At);
+  __syncthreads();
+  gather_rows<false>(stage, ht.U[3], ht.r[3], 3, nT, srow, sw, 0);
+  __syncthreads();
+  stage_to_operand<PC, PRO_THREADS>(stage, ht.r[3], At + (long long)TC_TILE * r16(ht.r[1]) * 2 * PC);
+}
+
+size_t tc_prologue_smem(const int* r6) {
+  int rmax = 1;
+  for (int m = 0; m < 4; ++m) rmax = r6[m] > rmax ? r6[m] : rmax;
+  return (size_t)PRO_HEAD_BYTES + (size_t)4 * TC_TILE * stage_ld(rmax);
+}
+
 template <bool DEV, int PC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalParams<float>* __restrict__ P,
-             EvalArgs a, const unsigned char* __restrict__ b12, const unsigned char* __restrict__ b34, int* err) {
+             EvalArgs a, const unsigned char* __restrict__ b12, const unsigned char* __restrict__ b34, int* err,
+             TcScratch sc, const unsigned char* __restrict__ broot) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long s_bar[3 * TC_STAGES];   // full, mma_done, drained
+  // full, mma_done, drained (per stage); A tiles; root B; root MMAs
+  __shared__ __align__(8) unsigned long long s_bar[3 * TC_STAGES + 3];
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   HTView<float> ht;
@@ -433,17 +577,15 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   const int nT = (int)min((long long)TC_TILE, n_act - e0);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TcLayout L = tc_layout<PC>(ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34);
-  float* sfoot = reinterpret_cast<float*>(smem_raw);                 // 128 x 4
-  float* sw = sfoot + TC_TILE * 4;                                    // 128 x 12
-  int* srow = reinterpret_cast<int*>(sw + TC_TILE * 12);              // 128 x 12
-  double* sval = reinterpret_cast<double*>(srow + TC_TILE * 12);      // 128
+  double* sval = reinterpret_cast<double*>(smem_raw);                // 128
   float* spart = reinterpret_cast<float*>(sval + TC_TILE);            // 128
-  float* stage = reinterpret_cast<float*>(smem_raw + L.stage);
   unsigned char* A0 = smem_raw + L.A0;
   unsigned char* A1 = smem_raw + L.A1;
   const uint32_t bslot = smem_u32(smem_raw + L.B);
   const uint32_t full = smem_u32(&s_bar[0]), mdone = smem_u32(&s_bar[TC_STAGES]),
-                 drained = smem_u32(&s_bar[2 * TC_STAGES]);
+                 drained = smem_u32(&s_bar[2 * TC_STAGES]), abar = smem_u32(&s_bar[3 * TC_STAGES]),
+                 rbar = smem_u32(&s_bar[3 * TC_STAGES + 1]), rdone = smem_u32(&s_bar[3 * TC_STAGES + 2]);
+  const long long abytes = tc_abytes<PC>(ht.r[1], ht.r[3]);
 
   const TcNode N0 = tc_node<PC>(ht.r[0], ht.r[1], ht.r12, smem_u32(A0), b12, tc_out12<PC>());
   const TcNode N1 = tc_node<PC>(ht.r[2], ht.r[3], ht.r34, smem_u32(A1), b34, tc_out34<PC>());
@@ -461,6 +603,9 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
       mbar_init(mdone + 8 * i, 1);
       mbar_init(drained + 8 * i, TC_CONSUMERS / 32);
     }
+    mbar_init(abar, 1);
+    mbar_init(rbar, 1);
+    mbar_init(rdone, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
@@ -488,54 +633,38 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   };
   const bool copier = tid == TC_COPY_WARP * 32, issuer = tid == TC_MMA_WARP * 32;
   int n_copy = 0;
-  if (copier)
+  if (copier) {
+    // the tile's A operands (both nodes, written by the prologue) in one bulk copy
+    mbar_expect_tx(abar, (uint32_t)abytes);
+    bulk_g2s(smem_u32(A0), sc.a + (long long)blockIdx.x * abytes, (uint32_t)abytes, abar);
     for (; n_copy < TC_STAGES && n_copy < nchunk; ++n_copy) issue_copy(n_copy);
-
-  // 1. feet and weights
-  if (tid < nT) {
-    int idx[4];
-    decode_tuple(g, a, e0 + tid, idx);
-    float foot[4];
-    int r[12];
-    float w[12];
-    foot_cells_ft<2>(g, a.E32, a.E, a.tau, a.foot_euler, idx, foot, r, w);   // d = 4: two spatial dimensions
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-#pragma unroll
-      for (int s = 0; s < 3; ++s) {
-        srow[(tid * 4 + m) * 3 + s] = r[3 * m + s];
-        sw[(tid * 4 + m) * 3 + s] = w[3 * m + s];
-      }
-      sfoot[tid * 4 + m] = foot[m];
-    }
   }
-  __syncthreads();
 
-  // 2. operands: c2 of both nodes split into the A tiles, c1 of node 0 into registers,
-  //    c1 of node 1 left in the stage for the node switch
+  // 2. c1 of node 0 into registers (from the prologue's scratch; zero beyond the rank)
   const int e_own = 32 * (warp & 3) + lane;   // the tensor-memory lane this warp may access
   const int half = (warp >> 2) & 1;           // the two warps of a lane quadrant split the p's
   const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
   float creg[64];
-  gather_leaf(stage, ht.U[1], ht.r[1], 1, nT, srow, sw);
-  __syncthreads();
-  stage_to_operand<PC>(stage, ht.r[1], A0);
-  __syncthreads();
-  gather_leaf(stage, ht.U[3], ht.r[3], 3, nT, srow, sw);
-  __syncthreads();
-  stage_to_operand<PC>(stage, ht.r[3], A1);
-  __syncthreads();
-  gather_leaf(stage, ht.U[0], ht.r[0], 0, nT, srow, sw);
-  __syncthreads();
-  if (warp < 8) stage_to_regs(stage, ht.r[0], e_own, creg);
-  __syncthreads();
-  gather_leaf(stage, ht.U[2], ht.r[2], 2, nT, srow, sw);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A tiles -> tensor cores
-  __syncthreads();
+  auto load_c1 = [&](int node) {
+    const float4* src = reinterpret_cast<const float4*>(sc.c1 + (e0 + e_own) * 128 + node * 64);
+#pragma unroll
+    for (int q4 = 0; q4 < 16; ++q4) {
+      const float4 v = src[q4];
+      creg[4 * q4] = v.x;
+      creg[4 * q4 + 1] = v.y;
+      creg[4 * q4 + 2] = v.z;
+      creg[4 * q4 + 3] = v.w;
+    }
+  };
+  if (warp < 8) load_c1(0);
 
   // 3. the chunk stream
   int n_mma = 0;
   if (issuer) {
+    if (!wait_one(abar, 0)) {
+      *(volatile int*)&s_abort = 1;
+      atomicExch(err, 1);
+    }
     for (int j = 0; j < nchunk; ++j) {
       if (*(volatile int*)&s_abort) break;
       const int s = j % TC_STAGES;
@@ -584,11 +713,7 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     }
   } else if (warp < 8) {
     for (int c = 0; c < nchunk; ++c) {
-      if (c == N0.nch) {
-        // node switch: c1 of node 1 (left in the stage) into registers
-        consumer_sync();
-        stage_to_regs(stage, ht.r[2], e_own, creg);
-      }
+      if (c == N0.nch) load_c1(1);   // node switch: c1 of node 1
       const int s = c % TC_STAGES;
       if (!__any_sync(0xffffffffu, *(volatile int*)&s_abort != 0)) {
         if (!wait_warp(mdone + 8 * s, (c / TC_STAGES) & 1)) {
@@ -628,6 +753,7 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   }
 
   // copies and MMAs still in flight (only after an abort) end before the CTA does
+  if (copier) wait_one(abar, 0);
   if (copier)
     for (int k = n_copy - TC_STAGES < 0 ? 0 : n_copy - TC_STAGES; k < n_copy; ++k)
       wait_one(full + 8 * (k % TC_STAGES), (k / TC_STAGES) & 1);
@@ -640,80 +766,122 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   const bool ok = *(volatile int*)&s_abort == 0;
 
   if (ok) {
-    // 4. root: sum_p c12[e][p] sum_q Broot[p][q] c34[e][q]; the two warps of a lane
-    //    quadrant take p < 32 and p >= 32
+    // 4. root on the tensor cores: T[e][p] = sum_q c34[e][q] Broot[p][q], a [128 x r34] x
+    //    [r34 x r12] GEMM (c34 split into PC BF16 pieces as the A operand over the freed A
+    //    region, the pre-split Broot bulk-copied after it), then sum_p c12[e][p] T[e][p] per
+    //    entry; the two warps of a lane quadrant take p < 32 and p >= 32
     const int rl = ht.r12, rr = ht.r34;
-    {
-      const int n = rl * 64;
-      for (int base = tid; base < n; base += 4 * TC_THREADS) {
-        float x[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int it = base + k * TC_THREADS, p = it >> 6, q = it & 63;
-          x[k] = (it < n && q < rr) ? __ldg(ht.Broot + (long long)p * rr + q) : 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (base + k * TC_THREADS < n) stage[base + k * TC_THREADS] = x[k];
-      }
+    const int n16 = r16(rl), kr16 = r16(rr), ksr = kr16 / 16;
+    unsigned char* RA = smem_raw + L.A0;
+    const uint32_t rb_addr = smem_u32(smem_raw + L.rootB);
+    const uint32_t rbytes = (uint32_t)(n16 * kr16 * 2 * PC);
+    bool root_mma = false;
+    if (copier) {
+      mbar_expect_tx(rbar, rbytes);
+      bulk_g2s(rb_addr, broot, rbytes, rbar);
     }
-    __syncthreads();
+    float c12h[32];
     if (warp < 8) {
-      float c34[64], c12[64];
+      float c34[64];
       tmem_ld64(trow + tc_out34<PC>(), c34);
-      tmem_ld64(trow + tc_out12<PC>(), c12);
+      tmem_ld32(trow + tc_out12<PC>() + half * 32, c12h);
       tmem_wait_ld();
       if constexpr (PC == 3) {
         // the second partial sums of nodes whose a-range spans both halves of a chunk, 16
         // columns at a time
+        float cb[16];
+        if (N1.ra16 > 32) {
 #pragma unroll
-        for (int q0 = 0; q0 < 64; q0 += 16) {
-          float cb[16];
-          if (N1.ra16 > 32) {
+          for (int q0 = 0; q0 < 64; q0 += 16) {
             tmem_ld16(trow + tc_out34b<PC>() + q0, cb);
             tmem_wait_ld();
 #pragma unroll
             for (int q = 0; q < 16; ++q) c34[q0 + q] += cb[q];
           }
-          if (N0.ra16 > 32) {
-            tmem_ld16(trow + tc_out12b<PC>() + q0, cb);
+        }
+        if (N0.ra16 > 32) {
+#pragma unroll
+          for (int q0 = 0; q0 < 32; q0 += 16) {
+            tmem_ld16(trow + tc_out12b<PC>() + half * 32 + q0, cb);
             tmem_wait_ld();
 #pragma unroll
-            for (int q = 0; q < 16; ++q) c12[q0 + q] += cb[q];
+            for (int q = 0; q < 16; ++q) c12h[q0 + q] += cb[q];
           }
         }
       }
 #pragma unroll
-      for (int q = 0; q < 64; ++q) {
+      for (int q = 0; q < 64; ++q)
         if (q >= rr) c34[q] = 0.f;
-        if (q >= rl) c12[q] = 0.f;
-      }
-      float acc = 0.f;
+      // row e_own of the A operand: this warp's half of the 8-column K groups
 #pragma unroll
-      for (int p = 0; p < 64; ++p) {
-        if ((p >> 5) == half && p < rl) {
-          const float4* Bp = reinterpret_cast<const float4*>(stage + p * 64);
-          float s4[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int g4 = 0; g4 < 4; ++g4) {
+        const int kg = half * 4 + g4;
+        if (kg * 8 < kr16) {
+          float x[8];
 #pragma unroll
-          for (int q4 = 0; q4 < 16; ++q4) {
-            const float4 bq = Bp[q4];
-            s4[0] = fmaf(bq.x, c34[4 * q4], s4[0]);
-            s4[1] = fmaf(bq.y, c34[4 * q4 + 1], s4[1]);
-            s4[2] = fmaf(bq.z, c34[4 * q4 + 2], s4[2]);
-            s4[3] = fmaf(bq.w, c34[4 * q4 + 3], s4[3]);
-          }
-          acc = fmaf(c12[p], (s4[0] + s4[1]) + (s4[2] + s4[3]), acc);
+          for (int j = 0; j < 8; ++j) x[j] = c34[kg * 8 + j];
+          uint4 pcs[PC];
+          split8<PC>(x, pcs);
+          const int off = (kg >> 1) * 4096 + (e_own >> 3) * 256 + (kg & 1) * 128 + (e_own & 7) * 16;
+#pragma unroll
+          for (int q = 0; q < PC; ++q) *reinterpret_cast<uint4*>(RA + q * ksr * 4096 + off) = pcs[q];
         }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A operand -> tensor cores
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (issuer) {
+      if (wait_one(rbar, 0)) {
+        root_mma = true;
+        fence_after();
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n16 >> 3) << 17) |
+                               ((uint32_t)(TC_TILE >> 4) << 24);
+        for (int k = 0; k < ksr; ++k) {
+          auto ad = [&](int q) { return tc_desc(smem_u32(RA) + (q * ksr + k) * 4096); };
+          auto bd = [&](int q) { return tc_desc(rb_addr + (q * ksr + k) * n16 * 32); };
+          mma_bf16(tmem, ad(0), bd(0), idesc, k > 0 ? 1u : 0u);
+          mma_bf16(tmem, ad(0), bd(1), idesc, 1u);
+          mma_bf16(tmem, ad(1), bd(0), idesc, 1u);
+          if constexpr (PC == 3) {
+            mma_bf16(tmem, ad(0), bd(2), idesc, 1u);
+            mma_bf16(tmem, ad(2), bd(0), idesc, 1u);
+            mma_bf16(tmem, ad(1), bd(1), idesc, 1u);
+          }
+        }
+        mma_commit(rdone);
+      } else {
+        *(volatile int*)&s_abort = 1;
+        atomicExch(err, 1);
+      }
+    }
+    if (warp < 8) {
+      float acc = 0.f;
+      if (wait_warp(rdone, 0)) {
+        fence_after();
+        float t[32];
+        tmem_ld32(trow + (uint32_t)(half * 32), t);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (half * 32 + i < rl) acc = fmaf(c12h[i], t[i], acc);
+      } else if (lane == 0) {
+        *(volatile int*)&s_abort = 1;
+        atomicExch(err, 1);
       }
       if (half == 1) spart[e_own] = acc;
       consumer_sync();
       if (half == 0) sval[e_own] = (double)(acc + spart[e_own]);
     }
+    // the root's copy and MMAs have completed before the CTA leaves (waits bounded)
+    if (copier) wait_one(rbar, 0);
+    if (issuer && root_mma) wait_one(rdone, 0);
     __syncthreads();
     // 5. correction and residual epilogue
     if (tid < nT) {
       double val = sval[tid];
-      if (corr.has) val += (double)correction_rw_ft<2>(g, corr, srow + tid * 12, sw + tid * 12);
+      if (corr.has) val += (double)correction_rw_ft<2>(g, corr, sc.rows + (e0 + tid) * 12, sc.w + (e0 + tid) * 12);
       const long long e = e0 + tid;
       if (a.X) {
         const long long fib = a.nper ? e / a.nper : 0;
@@ -755,13 +923,50 @@ size_t sl_eval_tc_smem(const int* r6, int pieces) {
 
 long long tc_split_bytes(int pieces) { return 64LL * 64 * 64 * 2 * pieces; }
 
+long long tc_scratch_bytes(long long cap) {
+  // A tiles (at most 128 + 128 padded columns x 3 BF16 pieces per entry), c1 (2 x 64 FP32),
+  // rows and weights (12 + 12)
+  return cap * ((128 + 128) * 2 * 3 + 128 * 4 + 24 * 4);
+}
+
+TcScratch tc_scratch_view(void* base, long long cap) {
+  TcScratch sc;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  sc.a = p;
+  p += cap * (128 + 128) * 2 * 3;
+  sc.c1 = reinterpret_cast<float*>(p);
+  p += cap * 128 * 4;
+  sc.rows = reinterpret_cast<int*>(p);
+  p += cap * 12 * 4;
+  sc.w = reinterpret_cast<float*>(p);
+  sc.cap = cap;
+  return sc;
+}
+
 cudaError_t sl_eval_tc_init_attrs() {
   const int mx = 220 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_sl_eval_tc<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  const int mp = (int)(PRO_HEAD_BYTES + 4 * TC_TILE * stage_ld(64));
+  cudaError_t e = cudaFuncSetAttribute(k_tc_prologue<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mp);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_prologue<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mp);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_prologue<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mp);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_prologue<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mp);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_tc<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_tc<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_tc<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sl_eval_tc<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   return e;
+}
+
+cudaError_t split_root_bf16(const float* Broot, int r12, int r34, void* out, int pieces, cudaStream_t s) {
+  if (r12 < 1 || r34 < 1 || r12 > 64 || r34 > 64 || (pieces != 2 && pieces != 3)) return cudaErrorInvalidValue;
+  const int n = r16(r12) * (r16(r34) / 8);
+  if (pieces == 3)
+    slar::count_launch(), k_split_root<3><<<(n + 255) / 256, 256, 0, s>>>(Broot, r12, r34,
+                                                                         static_cast<unsigned char*>(out));
+  else
+    slar::count_launch(), k_split_root<2><<<(n + 255) / 256, 256, 0, s>>>(Broot, r12, r34,
+                                                                         static_cast<unsigned char*>(out));
+  return cudaGetLastError();
 }
 
 cudaError_t split_transfer_bf16(const float* B, int rp, int ra, int rb, void* out, int pieces, cudaStream_t s) {
@@ -777,36 +982,63 @@ cudaError_t split_transfer_bf16(const float* B, int rp, int ra, int rb, void* ou
   return cudaGetLastError();
 }
 
-cudaError_t launch_sl_eval_tc(const GridDesc& g, const HTView<float>& ht, const CorrView& corr, const EvalArgs& a,
-                              const void* b12, const void* b34, int* err, int pieces, cudaStream_t s) {
-  if (a.n <= 0) return cudaSuccess;
-  if (g.d != 4) return cudaErrorInvalidValue;
+cudaError_t launch_sl_eval_tc(const GridDesc& g, const HTView<float>& ht, const CorrView& corr, const EvalArgs& a0,
+                              const void* b12, const void* b34, const void* broot_, int* err, int pieces,
+                              const TcScratch& sc, cudaStream_t s) {
+  const unsigned char* broot = static_cast<const unsigned char*>(broot_);
+  if (a0.n <= 0) return cudaSuccess;
+  if (g.d != 4 || sc.cap < TC_TILE) return cudaErrorInvalidValue;
+  // entries beyond the scratch capacity: index tuples are evaluated in chunks of it
+  if (a0.n > sc.cap && (a0.mode != EVAL_TUPLES || a0.X)) return cudaErrorInvalidValue;
   const int r6[6] = {ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34};
   const size_t sm = sl_eval_tc_smem(r6, pieces);
-  const long long blocks = (a.n + TC_TILE - 1) / TC_TILE;
+  const size_t smp = tc_prologue_smem(r6);
   const unsigned char* p12 = static_cast<const unsigned char*>(b12);
   const unsigned char* p34 = static_cast<const unsigned char*>(b34);
-  if (pieces == 3)
-    slar::count_launch(), k_sl_eval_tc<false, 3><<<(unsigned)blocks, TC_THREADS, sm, s>>>(g, ht, corr, nullptr, a, p12,
-                                                                                         p34, err);
-  else
-    slar::count_launch(), k_sl_eval_tc<false, 2><<<(unsigned)blocks, TC_THREADS, sm, s>>>(g, ht, corr, nullptr, a, p12,
-                                                                                         p34, err);
-  return cudaGetLastError();
+  for (long long off = 0; off < a0.n; off += sc.cap) {
+    EvalArgs a = a0;
+    if (a0.n > sc.cap) {
+      a.n = a0.n - off < sc.cap ? a0.n - off : sc.cap;
+      a.idx = a0.idx + off * g.d;
+      a.out = a0.out + off;
+    }
+    const long long blocks = (a.n + TC_TILE - 1) / TC_TILE;
+    if (pieces == 3) {
+      slar::count_launch(), k_tc_prologue<false, 3><<<(unsigned)blocks, PRO_THREADS, smp, s>>>(g, ht, nullptr, a, sc);
+      slar::count_launch(), k_sl_eval_tc<false, 3><<<(unsigned)blocks, TC_THREADS, sm, s>>>(g, ht, corr, nullptr, a,
+                                                                                           p12, p34, err, sc, broot);
+    } else {
+      slar::count_launch(), k_tc_prologue<false, 2><<<(unsigned)blocks, PRO_THREADS, smp, s>>>(g, ht, nullptr, a, sc);
+      slar::count_launch(), k_sl_eval_tc<false, 2><<<(unsigned)blocks, TC_THREADS, sm, s>>>(g, ht, corr, nullptr, a,
+                                                                                           p12, p34, err, sc, broot);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_sl_eval_tc_dev(const GridDesc& g, const EvalParams<float>* P, const EvalArgs& a, const void* b12,
-                                  const void* b34, int* err, int pieces, size_t sm, cudaStream_t s) {
-  if (g.d != 4) return cudaErrorInvalidValue;
+                                  const void* b34, const void* broot_, int* err, int pieces, size_t sm,
+                                  const TcScratch& sc, cudaStream_t s) {
+  const unsigned char* broot = static_cast<const unsigned char*>(broot_);
+  if (g.d != 4 || a.n > sc.cap) return cudaErrorInvalidValue;
   const long long blocks = (a.n + TC_TILE - 1) / TC_TILE;
   const unsigned char* p12 = static_cast<const unsigned char*>(b12);
   const unsigned char* p34 = static_cast<const unsigned char*>(b34);
-  if (pieces == 3)
+  // the prologue's shared memory for the largest ranks (the ranks are read on the device)
+  const size_t smp = (size_t)PRO_HEAD_BYTES + (size_t)4 * TC_TILE * stage_ld(64);
+  if (pieces == 3) {
+    slar::count_launch(), k_tc_prologue<true, 3><<<(unsigned)blocks, PRO_THREADS, smp, s>>>(g, HTView<float>{}, P, a,
+                                                                                         sc);
     slar::count_launch(), k_sl_eval_tc<true, 3><<<(unsigned)blocks, TC_THREADS, sm, s>>>(
-        g, HTView<float>{}, CorrView{}, P, a, p12, p34, err);
-  else
+        g, HTView<float>{}, CorrView{}, P, a, p12, p34, err, sc, broot);
+  } else {
+    slar::count_launch(), k_tc_prologue<true, 2><<<(unsigned)blocks, PRO_THREADS, smp, s>>>(g, HTView<float>{}, P, a,
+                                                                                         sc);
     slar::count_launch(), k_sl_eval_tc<true, 2><<<(unsigned)blocks, TC_THREADS, sm, s>>>(
-        g, HTView<float>{}, CorrView{}, P, a, p12, p34, err);
+        g, HTView<float>{}, CorrView{}, P, a, p12, p34, err, sc, broot);
+  }
   return cudaGetLastError();
 }
 

@@ -13,10 +13,10 @@ the calls of a run.
 
 Bars: FP64 GPU vs the oracle 1e-9 (relative L2 on f); FP32 entries vs the FP64 GPU step 1e-5;
 BF16x6 entries (six BF16 products, ~2^-24 relative per product, but summed over K terms of
-mixed sign: their entry error against the oracle is 1.5x the FP32 evaluator's, 1.15e-6 against
-7.3e-7 at rank 64) 2e-5, twice the FP32 bar; BF16x3 entries (three BF16 products, ~2^-16
-relative per product) vs FP64 three times the oracle's own step response to 2^-16 relative
-noise on its entries."""
+mixed sign, and the root contraction on the tensor cores too: their entry error against the
+oracle is up to 2.1x the FP32 evaluator's, 1.56e-6 against 7.35e-7 at rank 64) 3e-5, three
+times the FP32 bar; BF16x3 entries (three BF16 products, ~2^-16 relative per product) vs FP64
+three times the oracle's own step response to 2^-16 relative noise on its entries."""
 import numpy as np
 import pytest
 
@@ -104,7 +104,7 @@ def test_reduced_precision_f_matches_fp64_step(oracle_step, prec):
     f64 = _gpu_f(w, "fp64", path, pivots)
     fr = _gpu_f(w, prec, path, pivots)
     err = relerr(fr, f64)
-    bar = {"fp32": 1e-5, "bf16x6": 2e-5, "bf16x3": 3.0 * sens}[prec]
+    bar = {"fp32": 1e-5, "bf16x6": 3e-5, "bf16x3": 3.0 * sens}[prec]
     print(f"{w.name} {prec}: |f - f_fp64| / |f_fp64| = {err:.2e} (bar {bar:.2e}; oracle response to "
           f"2^-16 entry noise {sens:.2e})")
     assert err < bar
