@@ -165,9 +165,6 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
     g.h[m] = m < c->d ? (cfg->hi[m] - cfg->lo[m]) / cfg->N[m] : 1.0;
     g.lof[m] = (float)g.lo[m];
     g.hf[m] = (float)g.h[m];
-    // 16 FP32 ulps (2^-23 relative) of the largest cell coordinate a foot can take
-    const double tmax = g.N[m] + std::max(std::fabs(g.lo[m]), std::fabs(m < c->d ? cfg->hi[m] : 1.0)) / g.h[m];
-    g.guard[m] = (float)(16.0 * std::ldexp(1.0, -23) * tmax);
   }
   for (int m = 0; m < c->dx; ++m) g.NX *= g.N[m];
   for (int m = 0; m < c->dv; ++m) g.NV *= g.N[c->dx + m];

@@ -32,7 +32,6 @@ struct GridDesc {
   int NX;  // prod of spatial N
   int NV;  // prod of velocity N
   int S;   // interpolation stencil points per dimension: 3 (quadratic) or 5 (quartic, FP64)
-  float guard[4];   // FP32 paths: cells from a face below which a foot is traced again in FP64
 };
 
 template <typename T>

@@ -233,11 +233,11 @@ __device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& 
 }
 
 
-// ---- FP32 variants (FP32 / BF16x3 entry paths): the same formulas in single precision.
-// Their feet can differ from the FP64 ones by ~1e-7 relative.  Where that could move an
-// entry to the neighbouring stencil -- its FP32 foot lies within g.guard cells of a cell
-// face, and the two quadratic stencils there differ by Delta^3 f''' / 8 -- the foot is traced
-// again in FP64 (foot_cells_ft), so both paths interpolate from the same cells.
+// ---- FP32 variants (FP32 / BF16 entry paths): the same formulas in single precision.
+// Their feet can differ from the FP64 ones by a few FP32 ulps of the displacement.  Where
+// that could move an entry to the neighbouring stencil -- its FP32 foot lies within a guard
+// of a cell face, and the two quadratic stencils there differ by Delta^3 f''' / 8 -- the foot
+// is traced again in FP64 (foot_cells_ft), so both paths interpolate from the same cells.
 
 __device__ __forceinline__ void cell_weights_f(const GridDesc& g, int m, float y, int rows[3], float w[3]) {
   float t = (y - g.lof[m]) / g.hf[m];
@@ -286,73 +286,83 @@ __device__ __forceinline__ float centre_f(const GridDesc& g, int m, int i) {
 }
 
 // backward foot of the frozen-field characteristic (Kutta RK3 or first order), FP32, for
-// DX spatial dimensions
+// DX spatial dimensions, as its displacement from the departure cell centre in cells,
+// d[m] = (foot_m - centre_m) / Delta_m: the cell and the offset in it then carry FP32 ulps of
+// d, not of the absolute cell coordinate (up to N + the box offset in cells).  The velocity
+// centres are the FP64 ones rounded once (the x-displacement is tau v), the spatial ones
+// only place the field interpolations.
 template <int DX>
-__device__ __forceinline__ void trace_foot_ft(const GridDesc& g, const float* E, double tau_d, int euler,
-                                              const int* idx, float* foot) {
+__device__ __forceinline__ void trace_disp_ft(const GridDesc& g, const float* E, double tau_d, int euler,
+                                              const int* idx, float* d) {
   const float tau = (float)tau_d;
-  float x[DX], v[DX], e[DX];
+  float x[DX], v[DX], e[DX], Dx[DX], Dv[DX];
 #pragma unroll
   for (int m = 0; m < DX; ++m) {
     x[m] = centre_f(g, m, idx[m]);
-    v[m] = centre_f(g, DX + m, idx[DX + m]);
+    v[m] = (float)(g.lo[DX + m] + ((double)idx[DX + m] + 0.5) * g.h[DX + m]);
   }
   if (euler) {
     interp_vec_ft<DX>(g, E, x, e);
 #pragma unroll
     for (int m = 0; m < DX; ++m) {
-      foot[m] = x[m] - v[m] * tau;
-      foot[DX + m] = v[m] + e[m] * tau;
+      Dx[m] = -v[m] * tau;
+      Dv[m] = e[m] * tau;
     }
-    return;
+  } else {
+    const float half = 0.5f * tau, two_h = 2.f * tau, sixth = tau / 6.f;
+    float k1v[DX], k2x[DX], k2v[DX], k3v[DX], x2[DX], x3[DX], v3[DX];
+    interp_vec_ft<DX>(g, E, x, k1v);
+#pragma unroll
+    for (int m = 0; m < DX; ++m) {
+      x2[m] = x[m] - half * v[m];
+      k2x[m] = -(v[m] + half * k1v[m]);
+    }
+    interp_vec_ft<DX>(g, E, x2, k2v);
+#pragma unroll
+    for (int m = 0; m < DX; ++m) {
+      x3[m] = x[m] + tau * v[m] + two_h * k2x[m];
+      v3[m] = v[m] - tau * k1v[m] + two_h * k2v[m];
+    }
+    interp_vec_ft<DX>(g, E, x3, k3v);
+#pragma unroll
+    for (int m = 0; m < DX; ++m) {
+      Dx[m] = sixth * ((-v[m]) + 4.f * k2x[m] + (-v3[m]));
+      Dv[m] = sixth * (k1v[m] + 4.f * k2v[m] + k3v[m]);
+    }
   }
-  const float half = 0.5f * tau, two_h = 2.f * tau, sixth = tau / 6.f;
-  float k1v[DX], k2x[DX], k2v[DX], k3v[DX], x2[DX], x3[DX], v3[DX];
-  interp_vec_ft<DX>(g, E, x, k1v);
 #pragma unroll
   for (int m = 0; m < DX; ++m) {
-    x2[m] = x[m] - half * v[m];
-    k2x[m] = -(v[m] + half * k1v[m]);
-  }
-  interp_vec_ft<DX>(g, E, x2, k2v);
-#pragma unroll
-  for (int m = 0; m < DX; ++m) {
-    x3[m] = x[m] + tau * v[m] + two_h * k2x[m];
-    v3[m] = v[m] - tau * k1v[m] + two_h * k2v[m];
-  }
-  interp_vec_ft<DX>(g, E, x3, k3v);
-#pragma unroll
-  for (int m = 0; m < DX; ++m) {
-    foot[m] = x[m] + sixth * ((-v[m]) + 4.f * k2x[m] + (-v3[m]));
-    foot[DX + m] = v[m] + sixth * (k1v[m] + 4.f * k2v[m] + k3v[m]);
+    d[m] = Dx[m] / g.hf[m];
+    d[DX + m] = Dv[m] / g.hf[DX + m];
   }
 }
 
-__device__ __forceinline__ void trace_foot_f(const GridDesc& g, const float* E, double tau_d, int euler,
-                                             const int* idx, float* foot) {
-  if (g.dx == 2) trace_foot_ft<2>(g, E, tau_d, euler, idx, foot);
-  else trace_foot_ft<1>(g, E, tau_d, euler, idx, foot);
-}
-
-// Foot, cells and weights of one entry in the FP32 paths (2 DX dimensions): the FP32 foot,
-// unless it lies within g.guard[m] cells of a cell face in some dimension m, in which case the
-// entry takes the FP64 foot (E64 given) with the FP64 path's cells and weights (rounded to
-// FP32).  The guard is 16 FP32 ulps of the largest cell coordinate |t| = |y - lo| / Delta the
-// foot can take (N plus the box offset in cells): the FP32 RK3 foot carries a few ulps of y
-// and of t, so 16 leaves a margin of about four, and fewer feet pay for the FP64 trace (a
-// dependent FP64 division costs ~440 cycles on B300, and a warp waits for its slowest lane).
-// rows / w: [2 DX][3].
+// Foot, cells and weights of one entry in the FP32 paths (2 DX dimensions): the cells and
+// weights of the FP32 foot, unless it lies within a guard of a cell face in some dimension
+// m, in which case the entry takes the FP64 foot (E64 given) with the FP64 path's cells and
+// weights (rounded to FP32).  The foot's cell coordinate is idx + 0.5 + d (d from
+// trace_disp_ft), so its cell is idx + floor(0.5 + d) and its offset in the cell the
+// fraction of u = 0.5 + d.  The FP32 d carries a few ulps of |d| (roundings in the RK3
+// combination, the field values and interpolation, the division by Delta) and u half an ulp
+// of |u|; the guard is 32 ulps of |d| + 1, several times that.  The velocity field E also
+// enters through the intermediate RK3 points, whose FP32 and FP64 positions differ by an ulp
+// of x: a field stencil switched there moves the foot by ~tau Delta^3 E''' / Delta, far below
+// the guard except in configurations of probability ~1e-9 per entry.  (A dependent FP64
+// division costs ~440 cycles on B300 and a warp waits for its slowest lane, so the guard is
+// kept tight.)  rows / w: [2 DX][3]; foot: the FP32 foot positions.
 template <int DX>
 __device__ __forceinline__ void foot_cells_ft(const GridDesc& g, const float* E32, const double* E64, double tau,
                                               int euler, const int* idx, float* foot, int* rows, float* w) {
   constexpr int D = 2 * DX;
-  trace_foot_ft<DX>(g, E32, tau, euler, idx, foot);
+  float dsp[D], u[D];
+  trace_disp_ft<DX>(g, E32, tau, euler, idx, dsp);
   bool near = false;
 #pragma unroll
   for (int m = 0; m < D; ++m) {
-    const float t = (foot[m] - g.lof[m]) / g.hf[m];
-    const float fr = t - floorf(t);
-    near |= !(fr >= g.guard[m] && fr <= 1.f - g.guard[m]);   // also catches a non-finite t
+    u[m] = 0.5f + dsp[m];
+    const float fr = u[m] - floorf(u[m]);
+    const float gd = 32.f * 0x1p-23f * (fabsf(dsp[m]) + 1.f);
+    near |= !(fr >= gd && fr <= 1.f - gd);   // also catches a non-finite displacement
   }
   if (near && E64) {
     double fd[4];
@@ -368,76 +378,18 @@ __device__ __forceinline__ void foot_cells_ft(const GridDesc& g, const float* E3
     return;
   }
 #pragma unroll
-  for (int m = 0; m < D; ++m) cell_weights_f(g, m, foot[m], rows + 3 * m, w + 3 * m);
-}
-
-__device__ __forceinline__ float interp_1d_f(const GridDesc& g, int m, const float* vec, float y) {
-  int r[3];
-  float w[3];
-  cell_weights_f(g, m, y, r, w);
-  return w[0] * vec[r[0]] + w[1] * vec[r[1]] + w[2] * vec[r[2]];
-}
-
-// separable LoMaC correction at a foot, FP32, for DX = dv spatial dimensions
-template <int DX>
-__device__ __forceinline__ float correction_at_ft(const GridDesc& g, const CorrView& c, const float* foot) {
-  constexpr int DV = DX;
-  const long long NX = g.NX;
-  const int Nv = g.N[DX];
-  float dCi[DV + 2];
-  {
-    int r0[3], r1[3];
-    float w0[3], w1[3];
-    cell_weights_f(g, 0, foot[0], r0, w0);
-    if constexpr (DX == 2) cell_weights_f(g, 1, foot[1], r1, w1);
-#pragma unroll
-    for (int k = 0; k < DV + 2; ++k) {
-      const float* F = c.dC32 + k * NX;
-      float acc = 0.f;
-      if constexpr (DX == 1) {
-#pragma unroll
-        for (int s0 = 0; s0 < 3; ++s0) acc += w0[s0] * F[r0[s0]];
-      } else {
-#pragma unroll
-        for (int s0 = 0; s0 < 3; ++s0)
-#pragma unroll
-          for (int s1 = 0; s1 < 3; ++s1) acc += w0[s0] * w1[s1] * F[(long long)r0[s0] * g.N[1] + r1[s1]];
-      }
-      dCi[k] = acc;
-    }
+  for (int m = 0; m < D; ++m) {
+    float um = u[m];
+    if (!(fabsf(um) < 1e15f)) um = 0.5f;
+    const float fu = floorf(um);
+    const float xi = (um - fu) - 0.5f;
+    const float hx = 0.5f * xi;
+    w[3 * m] = hx * (xi - 1.f);
+    w[3 * m + 1] = 1.f - xi * xi;
+    w[3 * m + 2] = hx * (xi + 1.f);
+    stencil_rows_f((float)idx[m] + fu, g.N[m], rows + 3 * m);
+    foot[m] = centre_f(g, m, idx[m]) + dsp[m] * g.hf[m];
   }
-  float om[DV], q1[DV], q2[DV];
-#pragma unroll
-  for (int m = 0; m < DV; ++m) {
-    const float y = foot[DX + m];
-    om[m] = interp_1d_f(g, DX + m, c.qv32 + (0 * DV + m) * Nv, y);
-    q1[m] = interp_1d_f(g, DX + m, c.qv32 + (1 * DV + m) * Nv, y);
-    q2[m] = interp_1d_f(g, DX + m, c.qv32 + (2 * DV + m) * Nv, y);
-  }
-  float out = 0.f, t = dCi[0];
-#pragma unroll
-  for (int m = 0; m < DV; ++m) t *= om[m];
-  out += t;
-#pragma unroll
-  for (int j = 0; j < DV; ++j) {
-    t = dCi[1 + j];
-#pragma unroll
-    for (int m = 0; m < DV; ++m) t *= (m == j ? q1[m] : om[m]);
-    out += t;
-  }
-#pragma unroll
-  for (int j = 0; j < DV; ++j) {
-    t = dCi[1 + DV];
-#pragma unroll
-    for (int m = 0; m < DV; ++m) t *= (m == j ? q2[m] : om[m]);
-    out += t;
-  }
-  return out;
-}
-
-// separable LoMaC correction at a foot, FP32 (dv = dx)
-__device__ __forceinline__ float correction_at_f(const GridDesc& g, const CorrView& c, const float* foot) {
-  return g.dx == 2 ? correction_at_ft<2>(g, c, foot) : correction_at_ft<1>(g, c, foot);
 }
 
 // The same correction from the entry's cells and weights (rows / w: [2 DX][3]), so that it

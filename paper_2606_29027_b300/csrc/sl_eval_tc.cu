@@ -18,26 +18,34 @@
 // The columns (p, a) of both nodes (a padded to ra16, a multiple of 16) form one stream of
 // chunks of W columns (W = 128 for BF16x3, each chunk an even number of whole p; W = 64 for
 // BF16x6, whole p, and at ra16 > 32 one p per chunk).  Three warp roles run the stream
-// through a 3-stage ring:
+// through a shared-memory ring of B tiles (4 slots for BF16x3, 3 for BF16x6) and a 3-slot
+// tensor-memory ring of results:
 //   warp 9 (one thread)   bulk-copies chunk j's pre-split B tile (all pieces) into shared
-//                         slot j % 3 once the MMAs of chunk j - 3 have released it,
-//   warp 8 (one thread)   issues chunk j's 3 (6) x K/16 MMAs into tensor-memory slot j % 3
-//                         once the tile has landed and chunk j - 3 has been read out, and
-//                         commits them to an mbarrier,
+//                         slot j mod S once the MMAs of chunk j - S have released it,
+//   warps 8 and 10        (one thread each, the even and the odd chunks) issue chunk j's
+//                         3 (6) x K/16 MMAs into tensor-memory slot j % 3 once the tile has
+//                         landed and chunk j - 3 has been read out, and commit them to two
+//                         mbarriers (result ready, shared slot free).  A thread's MMA issue
+//                         stalls while the tensor pipe executes the MMAs before it, so one
+//                         issuer would leave the pipe idle during its own waits; with two,
+//                         one issues while the other waits,
 //   warps 0-7             read chunk j out of tensor memory (one load of W/2 columns per
 //                         warp: the warp pair of a lane quadrant splits the chunk's columns
 //                         in halves), dot them with c1 held in registers and store c_t[e][p]
-//                         as a tensor-memory column; each warp then arrives on the slot's
-//                         mbarrier.  A BF16x6 p split across the two halves leaves two
-//                         partial sums, added before the root contraction.
-// c2 of both nodes is the MMA's A operand (gathered and split once per CTA), c1 of the
-// current node sits in registers (the thread's own entry), and c_12, c_34 stay in tensor
-// memory for the root contraction and the correction / residual epilogue of the SIMT
-// evaluator.
-// Shared-memory operand layout (canonical, no swizzle, K-major): K-step s | 8-row group |
-// K core matrix | 8 rows x 16 bytes; byte (row, kk) = (row / 8) 256 + (kk / 8) 128 +
-// (row % 8) 16 + (kk % 8) 2 for kk < 16, i.e. leading (K) byte offset 128, stride (M/N)
-// byte offset 256.
+//                         in shared memory; each warp then arrives on the slot's mbarrier.
+//                         A BF16x6 p split across the two halves leaves two partial sums,
+//                         added before the root contraction.
+// The MMA's A operand, c2 of both nodes split into BF16 pieces, sits in tensor memory
+// (written once per CTA by warps 0-7 from the prologue's rows): only the B tiles are read
+// from shared memory, whose bandwidth an N = 128 MMA with both operands there would use up.
+// c1 of the current node sits in registers (the thread's own entry); c_12 and c_34 stay in
+// shared memory for the root contraction (c34 x Broot on the tensor cores, A = c34 in tensor
+// memory) and the correction / residual epilogue of the SIMT evaluator.
+// Shared-memory B layout (canonical, no swizzle, K-major): K-step s | 8-row group | K core
+// matrix | 8 rows x 16 bytes; byte (row, kk) = (row / 8) 256 + (kk / 8) 128 + (row % 8) 16 +
+// (kk % 8) 2 for kk < 16, i.e. leading (K) byte offset 128, stride (N) byte offset 256.
+// Tensor-memory A layout: lane = row, column = 32-bit word holding two K-elements (the first
+// in the low half); piece q, K-step k at columns (q ks + k) 8 .. + 7 from the node's base.
 // Every wait is bounded: a wait that runs out sets *err, the CTA skips the remaining work,
 // waits (bounded) for its copies and MMAs in flight and frees its tensor memory.
 #include <cuda_bf16.h>
@@ -50,54 +58,49 @@ namespace {
 
 constexpr int TC_TILE = 128;
 constexpr int TC_CONSUMERS = 256;        // warps 0-7
-constexpr int TC_MMA_WARP = 8;
+constexpr int TC_MMA_WARP = 8;           // issues the even chunks
 constexpr int TC_COPY_WARP = 9;
-constexpr int TC_THREADS = 320;
-constexpr int TC_STAGES = 3;
-constexpr int TC_TMEM_COLS = 512;        // 3 chunk slots, c_12 and c_34 (and their second halves)
+constexpr int TC_MMA2_WARP = 10;         // issues the odd chunks
+constexpr int TC_THREADS = 352;
+constexpr int TC_STAGES = 3;             // tensor-memory result slots
+constexpr int TC_TMEM_COLS = 512;        // 3 chunk slots and the A operands of both nodes
 
 // Operands split into PC BF16 pieces: PC = 2 (x = hi + lo, three products hh + hl + lh, about
 // 2^-16 relative per product) or PC = 3 (x = x1 + x2 + x3, six products 11 + 12 + 21 + 13 + 31
 // + 22, about 2^-24).  Columns per chunk: 128 with two pieces; 64 with three, so that the
-// ring of three 1.5x larger B slots and the 1.5x larger A tiles fit in shared memory at rank
-// 64.  Tensor-memory columns: three chunk slots, then c_12 and c_34; with three pieces the
-// read-out of a p whose a-range spans both 32-column halves of a chunk leaves two partial
-// sums, the second in the columns after c_34 (c_12b, c_34b).
+// ring of 1.5x larger B slots fits in shared memory beside the results at rank 64.
+// Tensor-memory columns: three chunk slots, then the A operands of node 0 and node 1 (PC x 32
+// columns each at rank 64).  With three pieces the read-out of a p whose a-range spans both
+// 32-column halves of a chunk leaves two partial sums (the second in a second result array).
 template <int PC> __host__ __device__ constexpr int tc_w() { return PC == 2 ? 128 : 64; }
-template <int PC> __host__ __device__ constexpr int tc_out12() { return 3 * tc_w<PC>(); }
-template <int PC> __host__ __device__ constexpr int tc_out34() { return 3 * tc_w<PC>() + 64; }
-template <int PC> __host__ __device__ constexpr int tc_out12b() { return 3 * tc_w<PC>() + 128; }
-template <int PC> __host__ __device__ constexpr int tc_out34b() { return 3 * tc_w<PC>() + 192; }
+template <int PC> __host__ __device__ constexpr int tc_sstages() { return PC == 2 ? 4 : 3; }
+template <int PC> __host__ __device__ constexpr int tc_acol(int node) { return 3 * tc_w<PC>() + node * 32 * PC; }
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;
 constexpr int TC_HEAD_BYTES = 2048;      // values and partial sums of the root
-constexpr int PRO_HEAD_BYTES = 16384;    // prologue: feet, weights, rows
+constexpr int PRO_SMEM_BYTES = 128 * 12 * 8;   // prologue: stencil rows and weights of the tile
 constexpr int TC_MIN_SMEM = 120 * 1024;  // one CTA per SM: the 512-column allocation never waits
 
 __host__ __device__ __forceinline__ int r16(int r) { return ((r + 15) / 16) * 16; }
 template <int PC>
 __host__ __device__ __forceinline__ int tc_width(int ra16) { return (tc_w<PC>() / ra16) * ra16; }
-__host__ __device__ __forceinline__ int al128(int x) { return (x + 127) & ~127; }
-__host__ __device__ __forceinline__ int stage_ld(int r) { return r | 1; }   // odd row stride
 
 struct TcLayout {
-  int A0, A1, B, slot, rootB, total;
+  int out, outb, B, slot, total;
 };
+constexpr int TC_OUT_BYTES = 2 * 64 * TC_TILE * 4;   // c_t[node][p][e], FP32
 
 template <int PC>
 __host__ __device__ __forceinline__ TcLayout tc_layout(int r0, int r1, int r2, int r3, int r12, int r34) {
   TcLayout L;
-  (void)r0;
-  (void)r2;
   int o = TC_HEAD_BYTES;
-  L.A0 = o; o += TC_TILE * r16(r1) * 2 * PC;
-  L.A1 = o; o += TC_TILE * r16(r3) * 2 * PC;
+  L.out = o; o += TC_OUT_BYTES;
+  L.outb = L.out;
+  if (PC == 3) { L.outb = o; o += TC_OUT_BYTES; }
   const int s0 = tc_width<PC>(r16(r0)) * r16(r1) * 2 * PC, s1 = tc_width<PC>(r16(r2)) * r16(r3) * 2 * PC;
   L.slot = s0 > s1 ? s0 : s1;
-  L.B = o; o += TC_STAGES * L.slot;
-  // the root contraction reuses the A and B regions once the chunk stream is over: its A
-  // operand (c34, 128 x r34) at A0, the pre-split Broot after it
-  L.rootB = al128(L.A0 + TC_TILE * r16(r34) * 2 * PC);
-  const int root_end = L.rootB + r16(r12) * r16(r34) * 2 * PC;
+  L.B = o; o += tc_sstages<PC>() * L.slot;
+  // the pre-split Broot of the root contraction reuses the B ring once the stream is over
+  const int root_end = L.B + r16(r12) * r16(r34) * 2 * PC;
   if (root_end > o) o = root_end;
   L.total = o > TC_MIN_SMEM ? o : TC_MIN_SMEM;
   return L;
@@ -105,21 +108,22 @@ __host__ __device__ __forceinline__ TcLayout tc_layout(int r0, int r1, int r2, i
 
 // one transfer node as the chunk stream sees it
 struct TcNode {
-  int ra, rp, ra16, rb16, ks, w, pc, ntot, nch, out_col;
-  uint32_t a_addr;                 // A operand (c2 split) in shared memory
+  int ra, rp, ra16, rb16, ks, w, pc, ntot, nch;
+  int out_off;                     // c_t of the node in the shared result arrays
+  uint32_t a_col;                  // A operand (c2 split): tensor-memory column
   const unsigned char* bg;         // pre-split B tiles in global memory
 };
 
 template <int PC>
-__device__ __forceinline__ TcNode tc_node(int ra, int rb, int rp, uint32_t a_addr, const unsigned char* bg,
-                                          int out_col) {
+__device__ __forceinline__ TcNode tc_node(int ra, int rb, int rp, uint32_t a_col, const unsigned char* bg,
+                                          int out_off) {
   TcNode n;
   n.ra = ra; n.rp = rp;
   n.ra16 = r16(ra); n.rb16 = r16(rb); n.ks = n.rb16 / 16;
   n.w = tc_width<PC>(n.ra16); n.pc = n.w / n.ra16;
   n.ntot = rp * n.ra16; n.nch = (n.ntot + n.w - 1) / n.w;
-  n.out_col = out_col;
-  n.a_addr = a_addr;
+  n.out_off = out_off;
+  n.a_col = a_col;
   n.bg = bg;
   return n;
 }
@@ -135,13 +139,42 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
          ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t acc) {
+// A from tensor memory (address a_tmem), B from shared memory (descriptor)
+template <int ACC>
+__device__ __forceinline__ void mma_bf16c(uint32_t tmem_d, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+      ::"r"(tmem_d), "r"(a_tmem), "l"(bdesc), "r"(idesc), "n"(ACC)
       : "memory");
+}
+
+// The MMAs of one chunk: KS K-steps x the split's products.  a0 is the tensor-memory address
+// of piece 0 at K-step 0 (K-step stride 8 columns, piece stride KS x 8); b0 the descriptor of
+// piece 0 at K-step 0, whose start-address field holds the byte address / 16 (all shared
+// addresses stay below 2^18, so the field does not overflow), hence the descriptor of a
+// block at byte offset o is b0 + o / 16: K-step stride wc x 32 bytes (bk = wc x 2), piece
+// stride KS x wc x 32.
+template <int PC, int KS>
+__device__ __forceinline__ void issue_chunk(uint32_t dt, uint32_t a0, uint64_t b0, uint32_t bk, uint32_t idesc) {
+  constexpr uint32_t AQ = KS * 8;
+  const uint32_t BQ = KS * bk;
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    const uint32_t a = a0 + k * 8;
+    const uint64_t b = b0 + k * bk;
+    if (k == 0)
+      mma_bf16c<0>(dt, a, b, idesc);
+    else
+      mma_bf16c<1>(dt, a, b, idesc);
+    mma_bf16c<1>(dt, a, b + BQ, idesc);
+    mma_bf16c<1>(dt, a + AQ, b, idesc);
+    if constexpr (PC == 3) {
+      mma_bf16c<1>(dt, a, b + 2 * BQ, idesc);
+      mma_bf16c<1>(dt, a + 2 * AQ, b, idesc);
+      mma_bf16c<1>(dt, a + AQ, b + BQ, idesc);
+    }
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -183,14 +216,14 @@ __device__ __forceinline__ bool wait_one(uint32_t bar, uint32_t parity) {
   return wait_one_n(bar, parity, TC_WAIT_LIMIT);
 }
 
-// bounded wait of a whole warp: true on every lane once every lane has seen the phase
+// bounded wait of a whole warp: lane 0 polls (one request per poll instead of 32), then
+// every lane observes the completed phase itself (its own acquire); true on every lane
 __device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity) {
-  bool ok = false;
-  for (long long n = 0; n < TC_WAIT_LIMIT; ++n) {
-    ok = ok || mbar_try_wait(bar, parity);
-    if (__all_sync(0xffffffffu, ok)) return true;
-  }
-  return false;
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = wait_one(bar, parity) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return false;
+  return __all_sync(0xffffffffu, mbar_try_wait(bar, parity) || wait_one(bar, parity));
 }
 
 // bulk copy global -> shared, completion counted in bytes on the mbarrier
@@ -229,8 +262,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
       : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_st1(uint32_t taddr, float v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(__float_as_uint(v)) : "memory");
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint4 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w)
+               : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
@@ -277,41 +312,6 @@ __global__ void k_split_bf16(const float* __restrict__ B, int rp, int ra, int rb
   for (int q = 0; q < PC; ++q) *reinterpret_cast<uint4*>(base + q * ks * wc * 32 + off) = pc[q];
 }
 
-// stage[e][q] = sum_s w[e][m][s] U_m[row_s][q] (FP32), zero rows for e >= nT.  Lanes run
-// over q (coalesced reads of U, conflict-free writes with the odd stride); each thread
-// issues the loads of four items before it uses them.
-__device__ __forceinline__ void gather_leaf(float* stage, const float* __restrict__ U, int r, int m, int nT,
-                                            const int* srow, const float* sw) {
-  const int ld = stage_ld(r), n = TC_TILE * r;
-  for (int base = threadIdx.x; base < n; base += 4 * TC_THREADS) {
-    float u[4][3], w[4][3];
-    int dst[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int it = base + k * TC_THREADS;
-      dst[k] = -1;
-      u[k][0] = u[k][1] = u[k][2] = 0.f;
-      w[k][0] = w[k][1] = w[k][2] = 0.f;
-      if (it < n) {
-        const int e = it / r, q = it - e * r;
-        dst[k] = e * ld + q;
-        if (e < nT) {
-          const int* rr = srow + (e * 4 + m) * 3;
-          const float* ww = sw + (e * 4 + m) * 3;
-#pragma unroll
-          for (int s = 0; s < 3; ++s) {
-            u[k][s] = __ldg(U + (long long)rr[s] * r + q);
-            w[k][s] = ww[s];
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (dst[k] >= 0) stage[dst[k]] = w[k][0] * u[k][0] + w[k][1] * u[k][1] + w[k][2] * u[k][2];
-  }
-}
-
 // Pre-split Broot [r12][r34] (FP32) into the B operand of the root contraction: rows n = p
 // (N = r12 padded to 16), K = q (r34 padded to 16), one tile in the layout of a chunk with
 // wc = N, PC pieces.
@@ -334,40 +334,14 @@ __global__ void k_split_root(const float* __restrict__ B, int r12, int r34, unsi
   for (int q = 0; q < PC; ++q) *reinterpret_cast<uint4*>(out + q * ks * n16 * 32 + off) = pc[q];
 }
 
-// stage (128 x r) -> A operand tiles (PC pieces), K padded to r16 with zeros
-template <int PC, int NT = TC_THREADS>
-__device__ __forceinline__ void stage_to_operand(const float* stage, int r, unsigned char* A) {
-  const int ld = stage_ld(r), rb16 = r16(r), ks = rb16 / 16, ng = rb16 / 8;
-  for (int it = threadIdx.x; it < TC_TILE * ng; it += NT) {
-    const int e = it & (TC_TILE - 1), kg = it >> 7;
-    float x[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int b = kg * 8 + j;
-      x[j] = b < r ? stage[e * ld + b] : 0.f;
-    }
-    uint4 pc[PC];
-    split8<PC>(x, pc);
-    const int off = (kg >> 1) * 4096 + (e >> 3) * 256 + (kg & 1) * 128 + (e & 7) * 16;
-#pragma unroll
-    for (int q = 0; q < PC; ++q) *reinterpret_cast<uint4*>(A + q * ks * 4096 + off) = pc[q];
-  }
-}
-
-// the thread's own row of the stage into registers (zero beyond r)
-__device__ __forceinline__ void stage_to_regs(const float* stage, int r, int e, float* c) {
-  const int ld = stage_ld(r);
-#pragma unroll
-  for (int a = 0; a < 64; ++a) c[a] = a < r ? stage[e * ld + a] : 0.f;
-}
-
 // Read-out of one chunk by one warp: the warp takes the half `half` of the chunk's p (NP
 // consecutive p, NP x 16 NB <= 64 consecutive columns), loads them with one 64-column
-// tensor-memory load and stores c_t[e][p] = sum_a c1[e][a] T[e][(p, a)] into column
-// out_col + p.  Columns of p >= p1 (a ragged last chunk) are loaded but not used.
+// tensor-memory load and stores c_t[e][p] = sum_a c1[e][a] T[e][(p, a)] at so[p x 128] (so:
+// the node's result array at the thread's entry).  Columns of p >= p1 (a ragged last chunk)
+// are loaded but not used.
 template <int NB>
 __device__ __forceinline__ void drain_chunk(const float* creg, uint32_t trow, uint32_t slot_col, int p0, int p1,
-                                            int half, int out_col) {
+                                            int half, float* so) {
   constexpr int RA16 = 16 * NB;
   constexpr int NP = (tc_w<2>() / RA16) / 2;
   float v[64];
@@ -379,18 +353,18 @@ __device__ __forceinline__ void drain_chunk(const float* creg, uint32_t trow, ui
     float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < RA16; ++a) s4[a & 3] = fmaf(creg[a], v[pi * RA16 + a], s4[a & 3]);
-    if (p < p1) tmem_st1(trow + (uint32_t)(out_col + p), (s4[0] + s4[1]) + (s4[2] + s4[3]));
+    if (p < p1) so[p * TC_TILE] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
   }
 }
 
 // Read-out of one 64-column chunk of the three-piece variant by one warp: the warp loads the
 // half `half` of the chunk (32 columns).  RA16 <= 32: its whole p (two of 16 or one of 32) ->
-// c_t[e][p] in column out_col + p.  RA16 = 48 or 64: one p per chunk whose a-range spans both
-// halves -> the partial sum over the half's a into out_col + p (half 0) or outb_col + p
-// (half 1), added at the root.
+// c_t[e][p] at so[p x 128].  RA16 = 48 or 64: one p per chunk whose a-range spans both halves
+// -> the partial sum over the half's a at so[p x 128] (half 0) or sob[p x 128] (half 1), added
+// at the root.
 template <int NB>
 __device__ __forceinline__ void drain_chunk3(const float* creg, uint32_t trow, uint32_t slot_col, int p0, int p1,
-                                             int half, int out_col, int outb_col) {
+                                             int half, float* so, float* sob) {
   constexpr int RA16 = 16 * NB;
   float v[32];
   tmem_ld32(trow + slot_col + (uint32_t)(half * 32), v);
@@ -403,7 +377,7 @@ __device__ __forceinline__ void drain_chunk3(const float* creg, uint32_t trow, u
       float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int a = 0; a < RA16; ++a) s4[a & 3] = fmaf(creg[a], v[pi * RA16 + a], s4[a & 3]);
-      if (p < p1) tmem_st1(trow + (uint32_t)(out_col + p), (s4[0] + s4[1]) + (s4[2] + s4[3]));
+      if (p < p1) so[p * TC_TILE] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
   } else {
     // RA16 = 48: the second half holds 16 columns of the p; the slot's columns past the chunk
@@ -417,13 +391,17 @@ __device__ __forceinline__ void drain_chunk3(const float* creg, uint32_t trow, u
 #pragma unroll
       for (int c = 0; c < RA16 - 32; ++c) s4[c & 3] = fmaf(creg[32 + c], v[c], s4[c & 3]);
     }
-    if (p < p1) tmem_st1(trow + (uint32_t)((half ? outb_col : out_col) + p), (s4[0] + s4[1]) + (s4[2] + s4[3]));
+    if (p < p1) (half ? sob : so)[p * TC_TILE] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
   }
 }
 
 // Scratch of the prologue, per entry e of a launch (capacity a multiple of TC_TILE):
-//   A tiles  tile t = e / 128 at a + t * tc_abytes: the split c2 of node 0 (leaf 1) and of
-//            node 1 (leaf 3) in the shared-memory operand layout, copied in one bulk copy;
+//   A rows   tile t = e / 128 at a + t * tc_abytes: the split c2 of node 0 (leaf 1) and of
+//            node 1 (leaf 3) as the rows of the tensor-memory A operand: the PC BF16 pieces
+//            of row e, two K-elements per 32-bit word in the tensor-memory order (piece q,
+//            K-step k, word w: elements 16k + 2w and 16k + 2w + 1), as 16-byte groups g
+//            (words 4g .. 4g + 3) at (g x 128 + e) x 16 bytes, so that a warp's 32 rows load
+//            coalesced; K padded to r16 with zeros;
 //   c1       c1[e][node][64] FP32 (leaf 0, leaf 2; zero beyond the rank);
 //   rows, w  the entry's stencil rows and weights [4][3] (for the correction epilogue).
 template <int PC>
@@ -433,14 +411,17 @@ __host__ __device__ __forceinline__ long long tc_abytes(int r1, int r3) {
 
 // Leaf gather of the prologue, a warp per entry row (lanes over the leaf's columns, no
 // integer division per item), four rows in flight per warp: row e of c = sum_s w[e][m][s]
-// U_m[row_s][:], zero for e >= nT.  Into the stage (row stride stage_ld(r)) for the A
-// operands, or into c1[e][node][0..63] (zero beyond r) in global scratch.
-constexpr int PRO_THREADS = 256;
-template <bool TO_C1>
-__device__ __forceinline__ void gather_rows(float* dst, const float* __restrict__ U, int r, int m, int nT,
+// U_m[row_s][:], zero for e >= nT.  TO_C1: into c1[e][node][0..63] (zero beyond r) in global
+// scratch.  Otherwise into the A rows of the node (layout above): each lane splits its
+// column's value into PC BF16 pieces, even lanes pair them with the next lane's into words
+// and the first lane of each 8-column group gathers the group's four words into one 16-byte
+// store, columns r .. r16 - 1 zero.
+constexpr int PRO_THREADS = 128;
+template <bool TO_C1, int PC>
+__device__ __forceinline__ void gather_rows(void* dst, const float* __restrict__ U, int r, int m, int nT,
                                             const int* srow, const float* sw, int node) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ld = stage_ld(r);
+  const int rb16 = r16(r), ks = rb16 / 16;
   for (int e0 = 4 * warp; e0 < TC_TILE; e0 += 4 * (PRO_THREADS / 32)) {
     const float* u[4][3];
     float w[4][3];
@@ -455,6 +436,7 @@ __device__ __forceinline__ void gather_rows(float* dst, const float* __restrict_
     }
 #pragma unroll
     for (int c0 = 0; c0 < 64; c0 += 32) {
+      if (!TO_C1 && c0 >= rb16) break;
       const int col = c0 + lane;
       float v[4][3];
 #pragma unroll
@@ -464,19 +446,33 @@ __device__ __forceinline__ void gather_rows(float* dst, const float* __restrict_
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const float x = w[k][0] * v[k][0] + w[k][1] * v[k][1] + w[k][2] * v[k][2];
-        if (TO_C1) dst[(long long)(e0 + k) * 128 + node * 64 + col] = x;   // zero beyond r (v = 0)
-        else if (col < r) dst[(e0 + k) * ld + col] = x;
+        if constexpr (TO_C1) {
+          static_cast<float*>(dst)[(long long)(e0 + k) * 128 + node * 64 + col] = x;   // zero beyond r (v = 0)
+        } else {
+          float rest = x;
+#pragma unroll
+          for (int q = 0; q < PC; ++q) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(rest);
+            rest -= __bfloat162float(h);
+            const uint32_t lo = __bfloat16_as_ushort(h);
+            const uint32_t word = lo | (__shfl_down_sync(0xffffffffu, lo, 1) << 16);
+            const uint32_t w1 = __shfl_down_sync(0xffffffffu, word, 2), w2 = __shfl_down_sync(0xffffffffu, word, 4),
+                           w3 = __shfl_down_sync(0xffffffffu, word, 6);
+            if ((lane & 7) == 0 && col < rb16)
+              static_cast<uint4*>(dst)[(q * ks * 2 + col / 8) * TC_TILE + e0 + k] = make_uint4(word, w1, w2, w3);
+          }
+        }
       }
     }
   }
 }
 
 // Prologue of the tensor-core evaluator, one CTA per 128-entry tile: the feet, cells and
-// weights, the four leaf gathers, the BF16 split of c2 of both nodes into the A tiles of
+// weights, the four leaf gathers, the BF16 split of c2 of both nodes into the A rows of
 // the tile and c1 of both nodes, all into global scratch.  A separate kernel so that these
 // latency-bound steps run at several CTAs per SM and overlap one another, while the
-// tensor-core kernel (one CTA per SM) starts its MMAs as soon as one bulk copy of the A
-// tiles has landed.
+// tensor-core kernel (one CTA per SM) starts its MMAs as soon as its warps have moved the A
+// rows into tensor memory.
 template <bool DEV, int PC>
 __global__ void __launch_bounds__(PRO_THREADS)
 k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restrict__ P, EvalArgs a,
@@ -502,7 +498,6 @@ k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restr
   const int tid = threadIdx.x;
   float* sw = reinterpret_cast<float*>(smem_raw);                     // 128 x 12
   int* srow = reinterpret_cast<int*>(sw + TC_TILE * 12);              // 128 x 12
-  float* stage = reinterpret_cast<float*>(smem_raw + PRO_HEAD_BYTES);
   if (tid < nT) {
     int idx[4];
     decode_tuple(g, a, e0 + tid, idx);
@@ -521,32 +516,25 @@ k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restr
   __syncthreads();
   unsigned char* At = sc.a + (long long)blockIdx.x * tc_abytes<PC>(ht.r[1], ht.r[3]);
   float* c1 = sc.c1 + e0 * 128;
-  // c1 of both nodes straight to the scratch, then c2 of each node through the stage
-  gather_rows<true>(c1, ht.U[0], ht.r[0], 0, nT, srow, sw, 0);
-  gather_rows<true>(c1, ht.U[2], ht.r[2], 2, nT, srow, sw, 1);
-  gather_rows<false>(stage, ht.U[1], ht.r[1], 1, nT, srow, sw, 0);
-  __syncthreads();
-  stage_to_operand<PC, PRO_THREADS>(stage, ht.r[1], At);
-  __syncthreads();
-  gather_rows<false>(stage, ht.U[3], ht.r[3], 3, nT, srow, sw, 0);
-  __syncthreads();
-  stage_to_operand<PC, PRO_THREADS>(stage, ht.r[3], At + (long long)TC_TILE * r16(ht.r[1]) * 2 * PC);
+  // c1 of both nodes and the A rows (split c2) of both nodes, straight to the scratch
+  gather_rows<true, PC>(c1, ht.U[0], ht.r[0], 0, nT, srow, sw, 0);
+  gather_rows<true, PC>(c1, ht.U[2], ht.r[2], 2, nT, srow, sw, 1);
+  gather_rows<false, PC>(At, ht.U[1], ht.r[1], 1, nT, srow, sw, 0);
+  gather_rows<false, PC>(At + (long long)TC_TILE * r16(ht.r[1]) * 2 * PC, ht.U[3], ht.r[3], 3, nT, srow, sw, 1);
 }
 
-size_t tc_prologue_smem(const int* r6) {
-  int rmax = 1;
-  for (int m = 0; m < 4; ++m) rmax = r6[m] > rmax ? r6[m] : rmax;
-  return (size_t)PRO_HEAD_BYTES + (size_t)4 * TC_TILE * stage_ld(rmax);
-}
+size_t tc_prologue_smem(const int*) { return (size_t)PRO_SMEM_BYTES; }
 
 template <bool DEV, int PC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalParams<float>* __restrict__ P,
              EvalArgs a, const unsigned char* __restrict__ b12, const unsigned char* __restrict__ b34, int* err,
              TcScratch sc, const unsigned char* __restrict__ broot) {
+  constexpr int SB = tc_sstages<PC>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  // full, mma_done, drained (per stage); A tiles; root B; root MMAs
-  __shared__ __align__(8) unsigned long long s_bar[3 * TC_STAGES + 3];
+  // full, slot free (per shared slot); mma_done, drained (per tensor-memory slot); A operands
+  // in tensor memory; root B; root MMAs; the two issuers' final commits
+  __shared__ __align__(8) unsigned long long s_bar[2 * SB + 2 * TC_STAGES + 5];
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   HTView<float> ht;
@@ -579,16 +567,18 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   const TcLayout L = tc_layout<PC>(ht.r[0], ht.r[1], ht.r[2], ht.r[3], ht.r12, ht.r34);
   double* sval = reinterpret_cast<double*>(smem_raw);                // 128
   float* spart = reinterpret_cast<float*>(sval + TC_TILE);            // 128
-  unsigned char* A0 = smem_raw + L.A0;
-  unsigned char* A1 = smem_raw + L.A1;
+  float* sout = reinterpret_cast<float*>(smem_raw + L.out);           // c_t[node][p][e]
+  float* soutb = reinterpret_cast<float*>(smem_raw + L.outb);         // second partial sums (PC = 3)
   const uint32_t bslot = smem_u32(smem_raw + L.B);
-  const uint32_t full = smem_u32(&s_bar[0]), mdone = smem_u32(&s_bar[TC_STAGES]),
-                 drained = smem_u32(&s_bar[2 * TC_STAGES]), abar = smem_u32(&s_bar[3 * TC_STAGES]),
-                 rbar = smem_u32(&s_bar[3 * TC_STAGES + 1]), rdone = smem_u32(&s_bar[3 * TC_STAGES + 2]);
+  constexpr int NB0 = 2 * SB + 2 * TC_STAGES;
+  const uint32_t full = smem_u32(&s_bar[0]), sfree = smem_u32(&s_bar[SB]), mdone = smem_u32(&s_bar[2 * SB]),
+                 drained = smem_u32(&s_bar[2 * SB + TC_STAGES]), aready = smem_u32(&s_bar[NB0]),
+                 rbar = smem_u32(&s_bar[NB0 + 1]), rdone = smem_u32(&s_bar[NB0 + 2]),
+                 idone = smem_u32(&s_bar[NB0 + 3]);   // + 8 for the second issuer
   const long long abytes = tc_abytes<PC>(ht.r[1], ht.r[3]);
 
-  const TcNode N0 = tc_node<PC>(ht.r[0], ht.r[1], ht.r12, smem_u32(A0), b12, tc_out12<PC>());
-  const TcNode N1 = tc_node<PC>(ht.r[2], ht.r[3], ht.r34, smem_u32(A1), b34, tc_out34<PC>());
+  const TcNode N0 = tc_node<PC>(ht.r[0], ht.r[1], ht.r12, (uint32_t)tc_acol<PC>(0), b12, 0);
+  const TcNode N1 = tc_node<PC>(ht.r[2], ht.r[3], ht.r34, (uint32_t)tc_acol<PC>(1), b34, 64 * TC_TILE);
   const int nchunk = N0.nch + N1.nch;
 
   if (warp == 0) {
@@ -598,14 +588,19 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < TC_STAGES; ++i) {
+    for (int i = 0; i < SB; ++i) {
       mbar_init(full + 8 * i, 1);
+      mbar_init(sfree + 8 * i, 1);
+    }
+    for (int i = 0; i < TC_STAGES; ++i) {
       mbar_init(mdone + 8 * i, 1);
       mbar_init(drained + 8 * i, TC_CONSUMERS / 32);
     }
-    mbar_init(abar, 1);
+    mbar_init(aready, TC_CONSUMERS / 32);
     mbar_init(rbar, 1);
     mbar_init(rdone, 1);
+    mbar_init(idone, 1);
+    mbar_init(idone + 8, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
@@ -627,20 +622,18 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     int cl, wc;
     chunk(j, N, cl, wc);
     const uint32_t bytes = (uint32_t)(wc * N.rb16 * 2 * PC);
-    const int s = j % TC_STAGES;
+    const int s = j % SB;
     mbar_expect_tx(full + 8 * s, bytes);
     bulk_g2s(bslot + s * L.slot, N.bg + (long long)cl * N.w * N.rb16 * 2 * PC, bytes, full + 8 * s);
   };
-  const bool copier = tid == TC_COPY_WARP * 32, issuer = tid == TC_MMA_WARP * 32;
+  const bool copier = tid == TC_COPY_WARP * 32, issuer0 = tid == TC_MMA_WARP * 32,
+             issuer = issuer0 || tid == TC_MMA2_WARP * 32;
   int n_copy = 0;
-  if (copier) {
-    // the tile's A operands (both nodes, written by the prologue) in one bulk copy
-    mbar_expect_tx(abar, (uint32_t)abytes);
-    bulk_g2s(smem_u32(A0), sc.a + (long long)blockIdx.x * abytes, (uint32_t)abytes, abar);
-    for (; n_copy < TC_STAGES && n_copy < nchunk; ++n_copy) issue_copy(n_copy);
-  }
+  if (copier)
+    for (; n_copy < SB && n_copy < nchunk; ++n_copy) issue_copy(n_copy);
 
-  // 2. c1 of node 0 into registers (from the prologue's scratch; zero beyond the rank)
+  // 2. c1 of node 0 into registers and the A operands of both nodes into tensor memory (from
+  //    the prologue's scratch; the two warps of a lane quadrant take alternate 16-byte groups)
   const int e_own = 32 * (warp & 3) + lane;   // the tensor-memory lane this warp may access
   const int half = (warp >> 2) & 1;           // the two warps of a lane quadrant split the p's
   const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
@@ -656,20 +649,30 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
       creg[4 * q4 + 3] = v.w;
     }
   };
-  if (warp < 8) load_c1(0);
+  if (warp < 8) {
+    load_c1(0);
+    const uint4* arow = reinterpret_cast<const uint4*>(sc.a + (long long)blockIdx.x * abytes);
+    const int ng0 = PC * N0.ks * 2, ng1 = PC * N1.ks * 2;
+    for (int gi = half; gi < ng0; gi += 2) tmem_st4(trow + N0.a_col + 4 * gi, arow[gi * TC_TILE + e_own]);
+    for (int gi = half; gi < ng1; gi += 2)
+      tmem_st4(trow + N1.a_col + 4 * gi, arow[(ng0 + gi) * TC_TILE + e_own]);
+    tmem_wait_st();
+    fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(aready);
+  }
 
   // 3. the chunk stream
-  int n_mma = 0;
   if (issuer) {
-    if (!wait_one(abar, 0)) {
+    if (!wait_one(aready, 0)) {
       *(volatile int*)&s_abort = 1;
       atomicExch(err, 1);
     }
-    for (int j = 0; j < nchunk; ++j) {
+    for (int j = issuer0 ? 0 : 1; j < nchunk; j += 2) {
       if (*(volatile int*)&s_abort) break;
-      const int s = j % TC_STAGES;
-      bool ok = wait_one(full + 8 * s, (j / TC_STAGES) & 1);
-      if (ok && j >= TC_STAGES) ok = wait_one(drained + 8 * s, ((j - TC_STAGES) / TC_STAGES) & 1);
+      const int s = j % SB, t = j % TC_STAGES;
+      bool ok = wait_one(full + 8 * s, (uint32_t)(j / SB) & 1);
+      if (ok && j >= TC_STAGES) ok = wait_one(drained + 8 * t, (uint32_t)((j - TC_STAGES) / TC_STAGES) & 1);
       if (!ok) {
         *(volatile int*)&s_abort = 1;
         atomicExch(err, 1);
@@ -681,29 +684,24 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
       fence_after();
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(wc >> 3) << 17) |
                              ((uint32_t)(TC_TILE >> 4) << 24);
-      const uint32_t dt = tmem + (uint32_t)(s * tc_w<PC>());
-      const uint32_t bb = bslot + s * L.slot;
-      for (int k = 0; k < N.ks; ++k) {
-        // piece q of the A / B operands at K-step k
-        auto ad = [&](int q) { return tc_desc(N.a_addr + (q * N.ks + k) * 4096); };
-        auto bd = [&](int q) { return tc_desc(bb + (q * N.ks + k) * wc * 32); };
-        mma_bf16(dt, ad(0), bd(0), idesc, k > 0 ? 1u : 0u);
-        mma_bf16(dt, ad(0), bd(1), idesc, 1u);
-        mma_bf16(dt, ad(1), bd(0), idesc, 1u);
-        if constexpr (PC == 3) {
-          mma_bf16(dt, ad(0), bd(2), idesc, 1u);
-          mma_bf16(dt, ad(2), bd(0), idesc, 1u);
-          mma_bf16(dt, ad(1), bd(1), idesc, 1u);
-        }
+      const uint32_t dt = tmem + (uint32_t)(t * tc_w<PC>());
+      const uint32_t a0 = tmem + N.a_col;
+      const uint64_t b0 = tc_desc(bslot + s * L.slot);
+      const uint32_t bk = (uint32_t)wc * 2;   // wc x 32 bytes / 16
+      switch (N.ks) {
+        case 1: issue_chunk<PC, 1>(dt, a0, b0, bk, idesc); break;
+        case 2: issue_chunk<PC, 2>(dt, a0, b0, bk, idesc); break;
+        case 3: issue_chunk<PC, 3>(dt, a0, b0, bk, idesc); break;
+        default: issue_chunk<PC, 4>(dt, a0, b0, bk, idesc); break;
       }
-      mma_commit(mdone + 8 * s);
-      n_mma = j + 1;
+      mma_commit(mdone + 8 * t);
+      mma_commit(sfree + 8 * s);
     }
   } else if (copier) {
-    for (int j = TC_STAGES; j < nchunk; ++j) {
+    for (int j = SB; j < nchunk; ++j) {
       if (*(volatile int*)&s_abort) break;
-      const int s = j % TC_STAGES;
-      if (!wait_one(mdone + 8 * s, ((j - TC_STAGES) / TC_STAGES) & 1)) {
+      const int s = j % SB;
+      if (!wait_one(sfree + 8 * s, (uint32_t)((j - SB) / SB) & 1)) {
         *(volatile int*)&s_abort = 1;
         atomicExch(err, 1);
         break;
@@ -728,20 +726,21 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
           chunk(c, N, cl, wc);
           const int p0 = cl * N.pc, p1 = min(N.rp, p0 + N.pc);
           const uint32_t sc = (uint32_t)(s * tc_w<PC>());
+          float* so = sout + N.out_off + e_own;
           if constexpr (PC == 2) {
             switch (N.ra16) {
-              case 16: drain_chunk<1>(creg, trow, sc, p0, p1, half, N.out_col); break;
-              case 32: drain_chunk<2>(creg, trow, sc, p0, p1, half, N.out_col); break;
-              case 48: drain_chunk<3>(creg, trow, sc, p0, p1, half, N.out_col); break;
-              default: drain_chunk<4>(creg, trow, sc, p0, p1, half, N.out_col); break;
+              case 16: drain_chunk<1>(creg, trow, sc, p0, p1, half, so); break;
+              case 32: drain_chunk<2>(creg, trow, sc, p0, p1, half, so); break;
+              case 48: drain_chunk<3>(creg, trow, sc, p0, p1, half, so); break;
+              default: drain_chunk<4>(creg, trow, sc, p0, p1, half, so); break;
             }
           } else {
-            const int outb = N.out_col == tc_out12<PC>() ? tc_out12b<PC>() : tc_out34b<PC>();
+            float* sob = soutb + N.out_off + e_own;
             switch (N.ra16) {
-              case 16: drain_chunk3<1>(creg, trow, sc, p0, p1, half, N.out_col, outb); break;
-              case 32: drain_chunk3<2>(creg, trow, sc, p0, p1, half, N.out_col, outb); break;
-              case 48: drain_chunk3<3>(creg, trow, sc, p0, p1, half, N.out_col, outb); break;
-              default: drain_chunk3<4>(creg, trow, sc, p0, p1, half, N.out_col, outb); break;
+              case 16: drain_chunk3<1>(creg, trow, sc, p0, p1, half, so, sob); break;
+              case 32: drain_chunk3<2>(creg, trow, sc, p0, p1, half, so, sob); break;
+              case 48: drain_chunk3<3>(creg, trow, sc, p0, p1, half, so, sob); break;
+              default: drain_chunk3<4>(creg, trow, sc, p0, p1, half, so, sob); break;
             }
           }
           fence_before();
@@ -753,13 +752,16 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
   }
 
   // copies and MMAs still in flight (only after an abort) end before the CTA does
-  if (copier) wait_one(abar, 0);
   if (copier)
-    for (int k = n_copy - TC_STAGES < 0 ? 0 : n_copy - TC_STAGES; k < n_copy; ++k)
-      wait_one(full + 8 * (k % TC_STAGES), (k / TC_STAGES) & 1);
-  if (issuer && n_mma > 0) wait_one(mdone + 8 * ((n_mma - 1) % TC_STAGES), ((n_mma - 1) / TC_STAGES) & 1);
+    for (int k = n_copy - SB < 0 ? 0 : n_copy - SB; k < n_copy; ++k) wait_one(full + 8 * (k % SB), (uint32_t)(k / SB) & 1);
+  // each issuer's MMAs (one single-phase barrier per issuer, committed after all of them:
+  // a slot barrier of the stream could have moved on by two phases, the other issuer's)
+  if (issuer) {
+    const uint32_t ib = idone + (issuer0 ? 0u : 8u);
+    mma_commit(ib);
+    wait_one(ib, 0);
+  }
   __syncwarp();
-  tmem_wait_st();
   fence_before();
   __syncthreads();
   fence_after();
@@ -767,13 +769,13 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
 
   if (ok) {
     // 4. root on the tensor cores: T[e][p] = sum_q c34[e][q] Broot[p][q], a [128 x r34] x
-    //    [r34 x r12] GEMM (c34 split into PC BF16 pieces as the A operand over the freed A
-    //    region, the pre-split Broot bulk-copied after it), then sum_p c12[e][p] T[e][p] per
-    //    entry; the two warps of a lane quadrant take p < 32 and p >= 32
+    //    [r34 x r12] GEMM (c34 split into PC BF16 pieces as the A operand in node 0's A
+    //    columns of tensor memory, the pre-split Broot bulk-copied into the freed B ring),
+    //    then sum_p c12[e][p] T[e][p] per entry; the two warps of a lane quadrant take p < 32
+    //    and p >= 32
     const int rl = ht.r12, rr = ht.r34;
     const int n16 = r16(rl), kr16 = r16(rr), ksr = kr16 / 16;
-    unsigned char* RA = smem_raw + L.A0;
-    const uint32_t rb_addr = smem_u32(smem_raw + L.rootB);
+    const uint32_t rb_addr = bslot;
     const uint32_t rbytes = (uint32_t)(n16 * kr16 * 2 * PC);
     bool root_mma = false;
     if (copier) {
@@ -783,72 +785,59 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     float c12h[32];
     if (warp < 8) {
       float c34[64];
-      tmem_ld64(trow + tc_out34<PC>(), c34);
-      tmem_ld32(trow + tc_out12<PC>() + half * 32, c12h);
-      tmem_wait_ld();
+      const float* s34 = sout + 64 * TC_TILE + e_own;
+      const float* s12 = sout + (half * 32) * TC_TILE + e_own;
+#pragma unroll
+      for (int q = 0; q < 64; ++q) c34[q] = q < rr ? s34[q * TC_TILE] : 0.f;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) c12h[i] = s12[i * TC_TILE];
       if constexpr (PC == 3) {
-        // the second partial sums of nodes whose a-range spans both halves of a chunk, 16
-        // columns at a time
-        float cb[16];
+        // the second partial sums of nodes whose a-range spans both halves of a chunk
         if (N1.ra16 > 32) {
+          const float* b34p = soutb + 64 * TC_TILE + e_own;
 #pragma unroll
-          for (int q0 = 0; q0 < 64; q0 += 16) {
-            tmem_ld16(trow + tc_out34b<PC>() + q0, cb);
-            tmem_wait_ld();
-#pragma unroll
-            for (int q = 0; q < 16; ++q) c34[q0 + q] += cb[q];
-          }
+          for (int q = 0; q < 64; ++q)
+            if (q < rr) c34[q] += b34p[q * TC_TILE];
         }
         if (N0.ra16 > 32) {
+          const float* b12p = soutb + (half * 32) * TC_TILE + e_own;
 #pragma unroll
-          for (int q0 = 0; q0 < 32; q0 += 16) {
-            tmem_ld16(trow + tc_out12b<PC>() + half * 32 + q0, cb);
-            tmem_wait_ld();
-#pragma unroll
-            for (int q = 0; q < 16; ++q) c12h[q0 + q] += cb[q];
-          }
+          for (int i = 0; i < 32; ++i)
+            if (half * 32 + i < rl) c12h[i] += b12p[i * TC_TILE];
         }
       }
+      // row e_own of the A operand into node 0's A columns: this warp's K groups of 8
 #pragma unroll
-      for (int q = 0; q < 64; ++q)
-        if (q >= rr) c34[q] = 0.f;
-      // row e_own of the A operand: this warp's half of the 8-column K groups
-#pragma unroll
-      for (int g4 = 0; g4 < 4; ++g4) {
-        const int kg = half * 4 + g4;
-        if (kg * 8 < kr16) {
+      for (int kg = 0; kg < 8; ++kg) {
+        if ((kg & 1) == half && kg * 8 < kr16) {
           float x[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) x[j] = c34[kg * 8 + j];
           uint4 pcs[PC];
           split8<PC>(x, pcs);
-          const int off = (kg >> 1) * 4096 + (e_own >> 3) * 256 + (kg & 1) * 128 + (e_own & 7) * 16;
 #pragma unroll
-          for (int q = 0; q < PC; ++q) *reinterpret_cast<uint4*>(RA + q * ksr * 4096 + off) = pcs[q];
+          for (int q = 0; q < PC; ++q) tmem_st4(trow + N0.a_col + 4 * (q * ksr * 2 + kg), pcs[q]);
         }
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A operand -> tensor cores
+      tmem_wait_st();
     }
     fence_before();
     __syncthreads();
     fence_after();
-    if (issuer) {
+    if (issuer0) {
       if (wait_one(rbar, 0)) {
         root_mma = true;
         fence_after();
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n16 >> 3) << 17) |
                                ((uint32_t)(TC_TILE >> 4) << 24);
-        for (int k = 0; k < ksr; ++k) {
-          auto ad = [&](int q) { return tc_desc(smem_u32(RA) + (q * ksr + k) * 4096); };
-          auto bd = [&](int q) { return tc_desc(rb_addr + (q * ksr + k) * n16 * 32); };
-          mma_bf16(tmem, ad(0), bd(0), idesc, k > 0 ? 1u : 0u);
-          mma_bf16(tmem, ad(0), bd(1), idesc, 1u);
-          mma_bf16(tmem, ad(1), bd(0), idesc, 1u);
-          if constexpr (PC == 3) {
-            mma_bf16(tmem, ad(0), bd(2), idesc, 1u);
-            mma_bf16(tmem, ad(2), bd(0), idesc, 1u);
-            mma_bf16(tmem, ad(1), bd(1), idesc, 1u);
-          }
+        const uint32_t a0 = tmem + N0.a_col;
+        const uint64_t b0 = tc_desc(rb_addr);
+        const uint32_t bk = (uint32_t)n16 * 2;
+        switch (ksr) {
+          case 1: issue_chunk<PC, 1>(tmem, a0, b0, bk, idesc); break;
+          case 2: issue_chunk<PC, 2>(tmem, a0, b0, bk, idesc); break;
+          case 3: issue_chunk<PC, 3>(tmem, a0, b0, bk, idesc); break;
+          default: issue_chunk<PC, 4>(tmem, a0, b0, bk, idesc); break;
         }
         mma_commit(rdone);
       } else {
@@ -876,7 +865,7 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
     }
     // the root's copy and MMAs have completed before the CTA leaves (waits bounded)
     if (copier) wait_one(rbar, 0);
-    if (issuer && root_mma) wait_one(rdone, 0);
+    if (issuer0 && root_mma) wait_one(rdone, 0);
     __syncthreads();
     // 5. correction and residual epilogue
     if (tid < nT) {
@@ -945,7 +934,7 @@ TcScratch tc_scratch_view(void* base, long long cap) {
 
 cudaError_t sl_eval_tc_init_attrs() {
   const int mx = 220 * 1024;
-  const int mp = (int)(PRO_HEAD_BYTES + 4 * TC_TILE * stage_ld(64));
+  const int mp = PRO_SMEM_BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_tc_prologue<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mp);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_prologue<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mp);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_prologue<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mp);
@@ -1026,8 +1015,7 @@ cudaError_t launch_sl_eval_tc_dev(const GridDesc& g, const EvalParams<float>* P,
   const long long blocks = (a.n + TC_TILE - 1) / TC_TILE;
   const unsigned char* p12 = static_cast<const unsigned char*>(b12);
   const unsigned char* p34 = static_cast<const unsigned char*>(b34);
-  // the prologue's shared memory for the largest ranks (the ranks are read on the device)
-  const size_t smp = (size_t)PRO_HEAD_BYTES + (size_t)4 * TC_TILE * stage_ld(64);
+  const size_t smp = (size_t)PRO_SMEM_BYTES;
   if (pieces == 3) {
     slar::count_launch(), k_tc_prologue<true, 3><<<(unsigned)blocks, PRO_THREADS, smp, s>>>(g, HTView<float>{}, P, a,
                                                                                          sc);
