@@ -28,7 +28,8 @@ struct GridDesc {
   int d, dx, dv;
   int N[4];
   double lo[4], h[4];
-  float lof[4], hf[4];   // the same in FP32 (the FP32 / BF16x3 paths do no FP64 arithmetic)
+  float lof[4], hf[4];   // the same in FP32 (the FP32 / BF16 paths' arithmetic)
+  float ihf[4];          // 1 / h rounded to FP32
   int NX;  // prod of spatial N
   int NV;  // prod of velocity N
   int S;   // interpolation stencil points per dimension: 3 (quadratic) or 5 (quartic, FP64)

@@ -215,20 +215,25 @@ __device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& 
       if (m < g.d) idx[m] = a.idx[e * g.d + m];
     return;
   }
-  // one fibre at *pivot, or fibre e / nper of a block at pivot[e / nper]
-  const long long fib = a.nper ? e / a.nper : 0;
-  const long long within = a.nper ? e - fib * a.nper : e;
-  const long long piv = (long long)a.pivot[fib];
-  const long long left = (a.mode == EVAL_ROW) ? piv : within;
-  const long long right = (a.mode == EVAL_ROW) ? within : piv;
+  // one fibre at *pivot, or fibre e / nper of a block at pivot[e / nper]; every index here
+  // is below 2^31 (a launch's entries, a fibre's length, a matricisation's row count), so
+  // 32-bit divisions (a 64-bit one is a long software sequence)
+  const unsigned eu = (unsigned)e, nper = (unsigned)a.nper;
+  const unsigned fib = nper ? eu / nper : 0u;
+  const unsigned within = nper ? eu - fib * nper : eu;
+  const unsigned piv = (unsigned)a.pivot[fib];
+  const unsigned left = (a.mode == EVAL_ROW) ? piv : within;
+  const unsigned right = (a.mode == EVAL_ROW) ? within : piv;
   if (g.d == 2) {
     idx[0] = (int)left;
     idx[1] = (int)right;
   } else {
-    idx[0] = (int)(left / g.N[1]);
-    idx[1] = (int)(left % g.N[1]);
-    idx[2] = (int)(right / g.N[3]);
-    idx[3] = (int)(right % g.N[3]);
+    const unsigned n1 = (unsigned)g.N[1], n3 = (unsigned)g.N[3];
+    const unsigned l1 = left / n1, r1 = right / n3;
+    idx[0] = (int)l1;
+    idx[1] = (int)(left - l1 * n1);
+    idx[2] = (int)r1;
+    idx[3] = (int)(right - r1 * n3);
   }
 }
 
@@ -240,7 +245,7 @@ __device__ __forceinline__ void decode_tuple(const GridDesc& g, const EvalArgs& 
 // is traced again in FP64 (foot_cells_ft), so both paths interpolate from the same cells.
 
 __device__ __forceinline__ void cell_weights_f(const GridDesc& g, int m, float y, int rows[3], float w[3]) {
-  float t = (y - g.lof[m]) / g.hf[m];
+  float t = (y - g.lof[m]) * g.ihf[m];
   if (!(fabsf(t) < 1e15f)) t = 0.f;
   const float jf = floorf(t);
   const float xi = t - jf - 0.5f;
@@ -332,8 +337,8 @@ __device__ __forceinline__ void trace_disp_ft(const GridDesc& g, const float* E,
   }
 #pragma unroll
   for (int m = 0; m < DX; ++m) {
-    d[m] = Dx[m] / g.hf[m];
-    d[DX + m] = Dv[m] / g.hf[DX + m];
+    d[m] = Dx[m] * g.ihf[m];
+    d[DX + m] = Dv[m] * g.ihf[DX + m];
   }
 }
 

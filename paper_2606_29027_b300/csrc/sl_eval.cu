@@ -367,9 +367,10 @@ __device__ __forceinline__ void sl_eval_body(const GridDesc& g, const HTView<T>&
       if (t < nT) {
         // residual of fibre element `e` against the k previous terms: X at the fibre's pivot,
         // Y at the element's position along the fibre
-        const long long fib = a.nper ? (e0 + t) / a.nper : 0;
+        const unsigned et = (unsigned)(e0 + t), nper = (unsigned)a.nper;   // below 2^31: 32-bit division
+        const unsigned fib = nper ? et / nper : 0u;
         const long long piv = (long long)a.pivot[fib];
-        const long long e = a.nper ? (e0 + t) - fib * a.nper : e0 + t;
+        const long long e = (long long)(nper ? et - fib * nper : et);
         const int k = a.kterms;
         int l = 0;
         for (; l + 4 <= k; l += 4) {

@@ -410,7 +410,9 @@ __host__ __device__ __forceinline__ long long tc_abytes(int r1, int r3) {
 }
 
 // Leaf gather of the prologue, a warp per entry row (lanes over the leaf's columns, no
-// integer division per item), four rows in flight per warp: row e of c = sum_s w[e][m][s]
+// integer division per item), eight rows (24 loads) in flight per warp: the prologue's grid
+// fits the GPU in one wave, so its time is one warp's chain of dependent loads, and more
+// loads in flight shorten it.  Row e of c = sum_s w[e][m][s]
 // U_m[row_s][:], zero for e >= nT.  TO_C1: into c1[e][node][0..63] (zero beyond r) in global
 // scratch.  Otherwise into the A rows of the node (layout above): each lane splits its
 // column's value into PC BF16 pieces, even lanes pair them with the next lane's into words
@@ -422,15 +424,16 @@ __device__ __forceinline__ void gather_rows(void* dst, const float* __restrict__
                                             const int* srow, const float* sw, int node) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rb16 = r16(r), ks = rb16 / 16;
-  for (int e0 = 4 * warp; e0 < TC_TILE; e0 += 4 * (PRO_THREADS / 32)) {
-    const float* u[4][3];
-    float w[4][3];
+  constexpr int RPI = 8;
+  for (int e0 = RPI * warp; e0 < TC_TILE; e0 += RPI * (PRO_THREADS / 32)) {
+    int u[RPI][3];   // row offsets into U (a leaf has at most 128 rows of r <= 64 columns)
+    float w[RPI][3];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < RPI; ++k) {
       const int e = e0 + k;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        u[k][q] = U + (long long)(e < nT ? srow[(e * 4 + m) * 3 + q] : 0) * r;
+        u[k][q] = (e < nT ? srow[(e * 4 + m) * 3 + q] : 0) * r;
         w[k][q] = e < nT ? sw[(e * 4 + m) * 3 + q] : 0.f;
       }
     }
@@ -438,13 +441,13 @@ __device__ __forceinline__ void gather_rows(void* dst, const float* __restrict__
     for (int c0 = 0; c0 < 64; c0 += 32) {
       if (!TO_C1 && c0 >= rb16) break;
       const int col = c0 + lane;
-      float v[4][3];
+      float v[RPI][3];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < RPI; ++k)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) v[k][q] = col < r ? __ldg(u[k][q] + col) : 0.f;
+        for (int q = 0; q < 3; ++q) v[k][q] = col < r ? __ldg(U + u[k][q] + col) : 0.f;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < RPI; ++k) {
         const float x = w[k][0] * v[k][0] + w[k][1] * v[k][1] + w[k][2] * v[k][2];
         if constexpr (TO_C1) {
           static_cast<float*>(dst)[(long long)(e0 + k) * 128 + node * 64 + col] = x;   // zero beyond r (v = 0)
@@ -474,7 +477,7 @@ __device__ __forceinline__ void gather_rows(void* dst, const float* __restrict__
 // tensor-core kernel (one CTA per SM) starts its MMAs as soon as its warps have moved the A
 // rows into tensor memory.
 template <bool DEV, int PC>
-__global__ void __launch_bounds__(PRO_THREADS)
+__global__ void __launch_bounds__(PRO_THREADS, 4)   // 4 CTAs per SM: 592 >= the 512 tiles of 65536 entries
 k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restrict__ P, EvalArgs a,
               TcScratch sc) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -509,11 +512,14 @@ k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restr
     for (int k = 0; k < 12; ++k) {
       srow[tid * 12 + k] = r[k];
       sw[tid * 12 + k] = w[k];
-      sc.rows[(e0 + tid) * 12 + k] = r[k];
-      sc.w[(e0 + tid) * 12 + k] = w[k];
     }
   }
   __syncthreads();
+  // the tile's rows and weights to the scratch (for the correction epilogue), coalesced
+  for (int i = tid; i < nT * 12; i += PRO_THREADS) {
+    sc.rows[e0 * 12 + i] = srow[i];
+    sc.w[e0 * 12 + i] = sw[i];
+  }
   unsigned char* At = sc.a + (long long)blockIdx.x * tc_abytes<PC>(ht.r[1], ht.r[3]);
   float* c1 = sc.c1 + e0 * 128;
   // c1 of both nodes and the A rows (split c2) of both nodes, straight to the scratch
@@ -873,9 +879,10 @@ k_sl_eval_tc(GridDesc g, HTView<float> ht_arg, CorrView corr_arg, const EvalPara
       if (corr.has) val += (double)correction_rw_ft<2>(g, corr, sc.rows + (e0 + tid) * 12, sc.w + (e0 + tid) * 12);
       const long long e = e0 + tid;
       if (a.X) {
-        const long long fib = a.nper ? e / a.nper : 0;
+        const unsigned eu = (unsigned)e, nper = (unsigned)a.nper;   // below 2^31: 32-bit division
+        const unsigned fib = nper ? eu / nper : 0u;
         const long long piv = (long long)a.pivot[fib];
-        const long long ey = a.nper ? e - fib * a.nper : e;
+        const long long ey = (long long)(nper ? eu - fib * nper : eu);
         for (int l = 0; l < a.kterms; ++l) val -= a.X[piv + l * a.ldX] * a.Y[ey + l * a.ldY];
       }
       a.out[e] = val;

@@ -88,7 +88,10 @@ def test_tc_ragged_tail_and_single_entry(prec):
 @pytest.mark.parametrize("replay", [True, False])
 def test_tc_slar_call_close_to_oracle(replay, prec):
     """Cross approximation with the tensor-core evaluator (graph path, parameters read from
-    device memory): with the oracle's pivots the result differs by the BF16x3 rounding."""
+    device memory): with the oracle's pivots the result differs by the BF16x3 rounding.
+    Free-running, both approximations stop at eps on their own pivots, so they differ by up
+    to a few eps, plus (BF16x3) the entries' own ~1e-5 relative rounding, which is the size of
+    eps here and which the cross approximation sees as part of the tensor."""
     from oracle import cross
     from oracle import ht as htmod
     import convert
@@ -105,7 +108,7 @@ def test_tc_slar_call_close_to_oracle(replay, prec):
     got = htmod.densify(convert.from_lib(ctx.export()))
     err = P.relerr(got, htmod.densify(want))
     print(f"slar call {prec} vs oracle", err)
-    assert err < (TOL[prec] if replay else 3 * eps)
+    assert err < (TOL[prec] if replay else 3 * eps + (1e-5 if prec == "bf16x3" else 0.0))
     ctx.close()
 
 
