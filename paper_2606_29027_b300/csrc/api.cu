@@ -165,7 +165,8 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
     g.h[m] = m < c->d ? (cfg->hi[m] - cfg->lo[m]) / cfg->N[m] : 1.0;
     g.lof[m] = (float)g.lo[m];
     g.hf[m] = (float)g.h[m];
-    g.ihf[m] = (float)(1.0 / g.h[m]);
+    g.ih[m] = 1.0 / g.h[m];
+    g.ihf[m] = (float)g.ih[m];
   }
   for (int m = 0; m < c->dx; ++m) g.NX *= g.N[m];
   for (int m = 0; m < c->dv; ++m) g.NV *= g.N[c->dx + m];

@@ -28,6 +28,7 @@ struct GridDesc {
   int d, dx, dv;
   int N[4];
   double lo[4], h[4];
+  double ih[4];          // 1 / h (FP64)
   float lof[4], hf[4];   // the same in FP32 (the FP32 / BF16 paths' arithmetic)
   float ihf[4];          // 1 / h rounded to FP32
   int NX;  // prod of spatial N

@@ -60,11 +60,13 @@ __device__ __forceinline__ void stencil_rows_f(float jf, int n, int rows[3]) {
 
 // cell and weights of coordinate y in dimension m (oracle: grid.locate and
 // grid.stencil_weights): the quadratic weights for S = 3; for S = 5 the quartic Lagrange
-// weights L_k(xi) = prod_{m != k} (xi - m) / (k - m), k = -2..2
-template <int S = 3>
+// weights L_k(xi) = prod_{m != k} (xi - m) / (k - m), k = -2..2.  RCP: the cell coordinate
+// as (y - a) times the FP64 reciprocal of Delta instead of the IEEE quotient (within an ulp
+// of it; for the FP32 paths' re-trace, where a dependent FP64 division costs ~440 cycles)
+template <int S = 3, bool RCP = false>
 __device__ __forceinline__ void cell_weights(const GridDesc& g, int m, double y, int rows[S], double w[S]) {
   static_assert(S == 3 || S == 5, "quadratic or quartic stencils");
-  double t = __ddiv_rn(dsub(y, g.lo[m]), g.h[m]);
+  double t = RCP ? dmul(dsub(y, g.lo[m]), g.ih[m]) : __ddiv_rn(dsub(y, g.lo[m]), g.h[m]);
   if (!(fabs(t) < 1e15)) t = 0.0;  // non-finite or absurd feet still index inside the grid
   double jf = floor(t);
   double xi = dsub(dsub(t, jf), 0.5);
@@ -87,17 +89,17 @@ __device__ __forceinline__ void cell_weights(const GridDesc& g, int m, double y,
 
 // tensor-product interpolation of a spatial field at point p (dx dims), lexicographic
 // stencil order, acc = acc + (w1 w2) v  (oracle: sl.interp_spatial)
-template <int S = 3>
+template <int S = 3, bool RCP = false>
 __device__ double interp_spatial(const GridDesc& g, const double* F, const double* p) {
   int r0[S], r1[S];
   double w0[S], w1[S];
-  cell_weights<S>(g, 0, p[0], r0, w0);
+  cell_weights<S, RCP>(g, 0, p[0], r0, w0);
   double acc = 0.0;
   if (g.dx == 1) {
     for (int s = 0; s < S; ++s) acc = dadd(acc, dmul(w0[s], F[r0[s]]));
     return acc;
   }
-  cell_weights<S>(g, 1, p[1], r1, w1);
+  cell_weights<S, RCP>(g, 1, p[1], r1, w1);
   const int N1 = g.N[1];
   for (int s0 = 0; s0 < S; ++s0)
     for (int s1 = 0; s1 < S; ++s1)
@@ -110,8 +112,9 @@ __device__ __forceinline__ double centre(const GridDesc& g, int m, int i) {
 }
 
 // backward foot of the frozen-field characteristic (oracle: sl.trace_feet); the field is
-// interpolated with the S-point stencil
-template <int S = 3>
+// interpolated with the S-point stencil (RCP: cell coordinates by reciprocals, see
+// cell_weights)
+template <int S = 3, bool RCP = false>
 __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int euler,
                            const int* idx, double* foot) {
   const int dx = g.dx;
@@ -123,7 +126,7 @@ __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int e
   const long long NX = g.NX;
   if (euler) {
     for (int m = 0; m < dx; ++m) {
-      double e = interp_spatial<S>(g, E + m * NX, x);
+      double e = interp_spatial<S, RCP>(g, E + m * NX, x);
       foot[m] = dsub(x[m], dmul(v[m], tau));
       foot[dx + m] = dadd(v[m], dmul(e, tau));
     }
@@ -134,7 +137,7 @@ __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int e
   double k1x[2], k1v[2], x2[2], v2[2], k2x[2], k2v[2], x3[2], v3[2], k3x[2], k3v[2];
   for (int m = 0; m < dx; ++m) {
     k1x[m] = -v[m];
-    k1v[m] = interp_spatial<S>(g, E + m * NX, x);
+    k1v[m] = interp_spatial<S, RCP>(g, E + m * NX, x);
   }
   for (int m = 0; m < dx; ++m) {
     x2[m] = dadd(x[m], dmul(half, k1x[m]));
@@ -142,7 +145,7 @@ __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int e
   }
   for (int m = 0; m < dx; ++m) {
     k2x[m] = -v2[m];
-    k2v[m] = interp_spatial<S>(g, E + m * NX, x2);
+    k2v[m] = interp_spatial<S, RCP>(g, E + m * NX, x2);
   }
   for (int m = 0; m < dx; ++m) {
     x3[m] = dadd(dsub(x[m], dmul(h, k1x[m])), dmul(two_h, k2x[m]));
@@ -150,7 +153,7 @@ __device__ void trace_foot(const GridDesc& g, const double* E, double tau, int e
   }
   for (int m = 0; m < dx; ++m) {
     k3x[m] = -v3[m];
-    k3v[m] = interp_spatial<S>(g, E + m * NX, x3);
+    k3v[m] = interp_spatial<S, RCP>(g, E + m * NX, x3);
   }
   for (int m = 0; m < dx; ++m) {
     foot[m] = dadd(x[m], dmul(sixth, dadd(dadd(k1x[m], dmul(4.0, k2x[m])), k3x[m])));
@@ -344,8 +347,9 @@ __device__ __forceinline__ void trace_disp_ft(const GridDesc& g, const float* E,
 
 // Foot, cells and weights of one entry in the FP32 paths (2 DX dimensions): the cells and
 // weights of the FP32 foot, unless it lies within a guard of a cell face in some dimension
-// m, in which case the entry takes the FP64 foot (E64 given) with the FP64 path's cells and
-// weights (rounded to FP32).  The foot's cell coordinate is idx + 0.5 + d (d from
+// m, in which case the entry takes the FP64 foot (E64 given) and its cells and weights
+// (rounded to FP32), with the cell coordinates by FP64 reciprocals: within an ulp of the
+// FP64 path's quotients, so the same cells except for feet within ~1e-14 cells of a face.  The foot's cell coordinate is idx + 0.5 + d (d from
 // trace_disp_ft), so its cell is idx + floor(0.5 + d) and its offset in the cell the
 // fraction of u = 0.5 + d.  The FP32 d carries a few ulps of |d| (roundings in the RK3
 // combination, the field values and interpolation, the division by Delta) and u half an ulp
@@ -371,11 +375,11 @@ __device__ __forceinline__ void foot_cells_ft(const GridDesc& g, const float* E3
   }
   if (near && E64) {
     double fd[4];
-    trace_foot(g, E64, tau, euler, idx, fd);
+    trace_foot<3, true>(g, E64, tau, euler, idx, fd);
 #pragma unroll
     for (int m = 0; m < D; ++m) {
       double wd[3];
-      cell_weights(g, m, fd[m], rows + 3 * m, wd);
+      cell_weights<3, true>(g, m, fd[m], rows + 3 * m, wd);
 #pragma unroll
       for (int s = 0; s < 3; ++s) w[3 * m + s] = (float)wd[s];
       foot[m] = (float)fd[m];

@@ -77,7 +77,7 @@ template <int PC> __host__ __device__ constexpr int tc_sstages() { return PC == 
 template <int PC> __host__ __device__ constexpr int tc_acol(int node) { return 3 * tc_w<PC>() + node * 32 * PC; }
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;
 constexpr int TC_HEAD_BYTES = 2048;      // values and partial sums of the root
-constexpr int PRO_SMEM_BYTES = 128 * 12 * 8;   // prologue: stencil rows and weights of the tile
+constexpr int PRO_SMEM_BYTES = 32 * 12 * 8;    // prologue: stencil rows and weights of its 32 entries
 constexpr int TC_MIN_SMEM = 120 * 1024;  // one CTA per SM: the 512-column allocation never waits
 
 __host__ __device__ __forceinline__ int r16(int r) { return ((r + 15) / 16) * 16; }
@@ -417,15 +417,19 @@ __host__ __device__ __forceinline__ long long tc_abytes(int r1, int r3) {
 // scratch.  Otherwise into the A rows of the node (layout above): each lane splits its
 // column's value into PC BF16 pieces, even lanes pair them with the next lane's into words
 // and the first lane of each 8-column group gathers the group's four words into one 16-byte
-// store, columns r .. r16 - 1 zero.
+// store, columns r .. r16 - 1 zero.  A prologue CTA holds PRO_TILE entries, a quarter of a
+// tensor-core tile (a_off: its first row in the tile's A rows); its four warps take eight
+// rows each.
 constexpr int PRO_THREADS = 128;
+constexpr int PRO_TILE = 32;
 template <bool TO_C1, int PC>
 __device__ __forceinline__ void gather_rows(void* dst, const float* __restrict__ U, int r, int m, int nT,
-                                            const int* srow, const float* sw, int node) {
+                                            const int* srow, const float* sw, int node, int a_off) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rb16 = r16(r), ks = rb16 / 16;
   constexpr int RPI = 8;
-  for (int e0 = RPI * warp; e0 < TC_TILE; e0 += RPI * (PRO_THREADS / 32)) {
+  static_assert(RPI * (PRO_THREADS / 32) == PRO_TILE, "one pass of the warps covers the tile");
+  for (int e0 = RPI * warp; e0 < PRO_TILE; e0 += RPI * (PRO_THREADS / 32)) {
     int u[RPI][3];   // row offsets into U (a leaf has at most 128 rows of r <= 64 columns)
     float w[RPI][3];
 #pragma unroll
@@ -462,7 +466,7 @@ __device__ __forceinline__ void gather_rows(void* dst, const float* __restrict__
             const uint32_t w1 = __shfl_down_sync(0xffffffffu, word, 2), w2 = __shfl_down_sync(0xffffffffu, word, 4),
                            w3 = __shfl_down_sync(0xffffffffu, word, 6);
             if ((lane & 7) == 0 && col < rb16)
-              static_cast<uint4*>(dst)[(q * ks * 2 + col / 8) * TC_TILE + e0 + k] = make_uint4(word, w1, w2, w3);
+              static_cast<uint4*>(dst)[(q * ks * 2 + col / 8) * TC_TILE + a_off + e0 + k] = make_uint4(word, w1, w2, w3);
           }
         }
       }
@@ -470,14 +474,15 @@ __device__ __forceinline__ void gather_rows(void* dst, const float* __restrict__
   }
 }
 
-// Prologue of the tensor-core evaluator, one CTA per 128-entry tile: the feet, cells and
+// Prologue of the tensor-core evaluator, one CTA per 32 entries (a quarter of a tensor-core
+// tile, so that a one-fibre launch of 16384 entries spreads over 512 CTAs): the feet, cells and
 // weights, the four leaf gathers, the BF16 split of c2 of both nodes into the A rows of
 // the tile and c1 of both nodes, all into global scratch.  A separate kernel so that these
 // latency-bound steps run at several CTAs per SM and overlap one another, while the
 // tensor-core kernel (one CTA per SM) starts its MMAs as soon as its warps have moved the A
 // rows into tensor memory.
 template <bool DEV, int PC>
-__global__ void __launch_bounds__(PRO_THREADS, 4)   // 4 CTAs per SM: 592 >= the 512 tiles of 65536 entries
+__global__ void __launch_bounds__(PRO_THREADS, 4)   // 4 CTAs per SM: 592 >= the 512 CTAs of a 16384-entry fibre
 k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restrict__ P, EvalArgs a,
               TcScratch sc) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -494,13 +499,16 @@ k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restr
   }
   if ((a.done && *a.done) || (a.skip && *a.skip)) return;
   if (a.kidx) a.pivot += *a.kidx;
-  const long long e0 = (long long)blockIdx.x * TC_TILE;
+  // PRO_TILE entries from e0: rows a_off .. a_off + PRO_TILE - 1 of tensor-core tile `tile`
+  const long long e0 = (long long)blockIdx.x * PRO_TILE;
+  const long long tile = blockIdx.x / (TC_TILE / PRO_TILE);
+  const int a_off = (int)(e0 - tile * TC_TILE);
   const long long n_act = a.nact ? min(a.n, (long long)(*a.nact) * a.nper) : a.n;
   if (e0 >= n_act) return;
-  const int nT = (int)min((long long)TC_TILE, n_act - e0);
+  const int nT = (int)min((long long)PRO_TILE, n_act - e0);
   const int tid = threadIdx.x;
-  float* sw = reinterpret_cast<float*>(smem_raw);                     // 128 x 12
-  int* srow = reinterpret_cast<int*>(sw + TC_TILE * 12);              // 128 x 12
+  float* sw = reinterpret_cast<float*>(smem_raw);                     // PRO_TILE x 12
+  int* srow = reinterpret_cast<int*>(sw + PRO_TILE * 12);             // PRO_TILE x 12
   if (tid < nT) {
     int idx[4];
     decode_tuple(g, a, e0 + tid, idx);
@@ -520,13 +528,14 @@ k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restr
     sc.rows[e0 * 12 + i] = srow[i];
     sc.w[e0 * 12 + i] = sw[i];
   }
-  unsigned char* At = sc.a + (long long)blockIdx.x * tc_abytes<PC>(ht.r[1], ht.r[3]);
+  unsigned char* At = sc.a + tile * tc_abytes<PC>(ht.r[1], ht.r[3]);
   float* c1 = sc.c1 + e0 * 128;
   // c1 of both nodes and the A rows (split c2) of both nodes, straight to the scratch
-  gather_rows<true, PC>(c1, ht.U[0], ht.r[0], 0, nT, srow, sw, 0);
-  gather_rows<true, PC>(c1, ht.U[2], ht.r[2], 2, nT, srow, sw, 1);
-  gather_rows<false, PC>(At, ht.U[1], ht.r[1], 1, nT, srow, sw, 0);
-  gather_rows<false, PC>(At + (long long)TC_TILE * r16(ht.r[1]) * 2 * PC, ht.U[3], ht.r[3], 3, nT, srow, sw, 1);
+  gather_rows<true, PC>(c1, ht.U[0], ht.r[0], 0, nT, srow, sw, 0, 0);
+  gather_rows<true, PC>(c1, ht.U[2], ht.r[2], 2, nT, srow, sw, 1, 0);
+  gather_rows<false, PC>(At, ht.U[1], ht.r[1], 1, nT, srow, sw, 0, a_off);
+  gather_rows<false, PC>(At + (long long)TC_TILE * r16(ht.r[1]) * 2 * PC, ht.U[3], ht.r[3], 3, nT, srow, sw, 1,
+                         a_off);
 }
 
 size_t tc_prologue_smem(const int*) { return (size_t)PRO_SMEM_BYTES; }
@@ -998,13 +1007,13 @@ cudaError_t launch_sl_eval_tc(const GridDesc& g, const HTView<float>& ht, const 
       a.idx = a0.idx + off * g.d;
       a.out = a0.out + off;
     }
-    const long long blocks = (a.n + TC_TILE - 1) / TC_TILE;
+    const long long blocks = (a.n + TC_TILE - 1) / TC_TILE, pblocks = (a.n + PRO_TILE - 1) / PRO_TILE;
     if (pieces == 3) {
-      slar::count_launch(), k_tc_prologue<false, 3><<<(unsigned)blocks, PRO_THREADS, smp, s>>>(g, ht, nullptr, a, sc);
+      slar::count_launch(), k_tc_prologue<false, 3><<<(unsigned)pblocks, PRO_THREADS, smp, s>>>(g, ht, nullptr, a, sc);
       slar::count_launch(), k_sl_eval_tc<false, 3><<<(unsigned)blocks, TC_THREADS, sm, s>>>(g, ht, corr, nullptr, a,
                                                                                            p12, p34, err, sc, broot);
     } else {
-      slar::count_launch(), k_tc_prologue<false, 2><<<(unsigned)blocks, PRO_THREADS, smp, s>>>(g, ht, nullptr, a, sc);
+      slar::count_launch(), k_tc_prologue<false, 2><<<(unsigned)pblocks, PRO_THREADS, smp, s>>>(g, ht, nullptr, a, sc);
       slar::count_launch(), k_sl_eval_tc<false, 2><<<(unsigned)blocks, TC_THREADS, sm, s>>>(g, ht, corr, nullptr, a,
                                                                                            p12, p34, err, sc, broot);
     }
@@ -1019,17 +1028,17 @@ cudaError_t launch_sl_eval_tc_dev(const GridDesc& g, const EvalParams<float>* P,
                                   const TcScratch& sc, cudaStream_t s) {
   const unsigned char* broot = static_cast<const unsigned char*>(broot_);
   if (g.d != 4 || a.n > sc.cap) return cudaErrorInvalidValue;
-  const long long blocks = (a.n + TC_TILE - 1) / TC_TILE;
+  const long long blocks = (a.n + TC_TILE - 1) / TC_TILE, pblocks = (a.n + PRO_TILE - 1) / PRO_TILE;
   const unsigned char* p12 = static_cast<const unsigned char*>(b12);
   const unsigned char* p34 = static_cast<const unsigned char*>(b34);
   const size_t smp = (size_t)PRO_SMEM_BYTES;
   if (pieces == 3) {
-    slar::count_launch(), k_tc_prologue<true, 3><<<(unsigned)blocks, PRO_THREADS, smp, s>>>(g, HTView<float>{}, P, a,
+    slar::count_launch(), k_tc_prologue<true, 3><<<(unsigned)pblocks, PRO_THREADS, smp, s>>>(g, HTView<float>{}, P, a,
                                                                                          sc);
     slar::count_launch(), k_sl_eval_tc<true, 3><<<(unsigned)blocks, TC_THREADS, sm, s>>>(
         g, HTView<float>{}, CorrView{}, P, a, p12, p34, err, sc, broot);
   } else {
-    slar::count_launch(), k_tc_prologue<true, 2><<<(unsigned)blocks, PRO_THREADS, smp, s>>>(g, HTView<float>{}, P, a,
+    slar::count_launch(), k_tc_prologue<true, 2><<<(unsigned)pblocks, PRO_THREADS, smp, s>>>(g, HTView<float>{}, P, a,
                                                                                          sc);
     slar::count_launch(), k_sl_eval_tc<true, 2><<<(unsigned)blocks, TC_THREADS, sm, s>>>(
         g, HTView<float>{}, CorrView{}, P, a, p12, p34, err, sc, broot);
