@@ -379,12 +379,34 @@ k_aca_post(const double* __restrict__ Ua, int M1, const double* __restrict__ Va,
     const int M = isu ? M1 : M2;
     const int s0 = (isu ? blk : blk - nbu) * DOT_SEG;
     const double* xk = X + (long long)kk * M;
-    for (int l = warp; l <= kk; l += 8) {
-      const double* xl = X + (long long)l * M;
-      double acc = 0.0;
-      for (int i = s0 + lane; i < s0 + DOT_SEG && i < M; i += 32) acc += xl[i] * xk[i];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if (lane == 0) part[(long long)blk * ldp + l] = acc;
+    // the new factor's segment in registers; each warp takes two columns l per pass (16 loads
+    // in flight per lane)
+    constexpr int J = DOT_SEG / 32;
+    double xr[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int i = s0 + lane + 32 * j;
+      xr[j] = i < M ? xk[i] : 0.0;
+    }
+    for (int l = warp; l <= kk; l += 16) {   // columns l and l + 8
+      const int l2 = l + 8;
+      const bool has2 = l2 <= kk;
+      double a = 0.0, b = 0.0;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int i = s0 + lane + 32 * j;
+        a += (i < M ? X[(long long)l * M + i] : 0.0) * xr[j];
+        b += ((has2 && i < M) ? X[(long long)l2 * M + i] : 0.0) * xr[j];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+      }
+      if (lane == 0) {
+        part[(long long)blk * ldp + l] = a;
+        if (has2) part[(long long)blk * ldp + l2] = b;
+      }
     }
     if (isu) {
       // maximum of |u_k| over the unused rows of this segment, for the next row pivot
@@ -617,7 +639,10 @@ __global__ void k_aca_block_fsub(double* __restrict__ Ua, int M1, const double* 
 // of U (t < nact, l < k + nact), blocks [nbu, nbu + nbv) those of the new v_t with V, blocks
 // [nbu + nbv, + n_chk) apply the new terms to the check rows and keep their norms after each
 // term; the last block accepts the terms in order (norm estimate, rank-1 test, check rows),
-// and picks the next block's rows.
+// and picks the next block's rows.  A dot block keeps two new factors' segment in registers
+// and each warp takes two columns l per pass (32 loads in flight per lane); the last block
+// sums each dot's partials in one thread with four accumulators (fixed order) -- the dots
+// are chains of L2 loads, and these are the loads that can be in flight at once.
 __global__ void __launch_bounds__(256)
 k_aca_block_post(const double* __restrict__ Ua, int M1, const double* __restrict__ Va, int M2, int kmax, int nbu,
                  int nbv, double* __restrict__ part, int ldp, AcaState* st, int* pivI, unsigned char* usedr, int n_chk,
@@ -641,14 +666,47 @@ k_aca_block_post(const double* __restrict__ Ua, int M1, const double* __restrict
     const double* X = isu ? Ua : Va;
     const int M = isu ? M1 : M2;
     const int s0 = (isu ? blk : blk - nbu) * DOT_SEG;
-    for (int w = warp; w < na * K; w += 8) {
-      const int t = w / K, l = w - t * K;
-      const double* xt = X + (long long)(kk + t) * M;
-      const double* xl = X + (long long)l * M;
-      double acc = 0.0;
-      for (int i = s0 + lane; i < s0 + DOT_SEG && i < M; i += 32) acc += xl[i] * xt[i];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if (lane == 0) part[(long long)blk * ldp + w] = acc;
+    constexpr int J = DOT_SEG / 32;
+    double* pb = part + (long long)blk * ldp;
+    for (int t0 = 0; t0 < na; t0 += 2) {
+      const bool two = t0 + 1 < na;
+      double x0[J], x1[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int i = s0 + lane + 32 * j;
+        x0[j] = i < M ? X[(long long)(kk + t0) * M + i] : 0.0;
+        x1[j] = (two && i < M) ? X[(long long)(kk + t0 + 1) * M + i] : 0.0;
+      }
+      for (int l = warp; l < K; l += 16) {   // columns l and l + 8
+        const int l2 = l + 8;
+        const bool has2 = l2 < K;
+        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int i = s0 + lane + 32 * j;
+          const double y = i < M ? X[(long long)l * M + i] : 0.0;
+          const double y2 = (has2 && i < M) ? X[(long long)l2 * M + i] : 0.0;
+          a0 += y * x0[j];
+          a1 += y * x1[j];
+          b0 += y2 * x0[j];
+          b1 += y2 * x1[j];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a0 += __shfl_down_sync(0xffffffffu, a0, o);
+          a1 += __shfl_down_sync(0xffffffffu, a1, o);
+          b0 += __shfl_down_sync(0xffffffffu, b0, o);
+          b1 += __shfl_down_sync(0xffffffffu, b1, o);
+        }
+        if (lane == 0) {
+          pb[t0 * K + l] = a0;
+          if (two) pb[(t0 + 1) * K + l] = a1;
+          if (has2) {
+            pb[t0 * K + l2] = b0;
+            if (two) pb[(t0 + 1) * K + l2] = b1;
+          }
+        }
+      }
     }
   } else {
     const int q = blk - nbu - nbv;
@@ -684,19 +742,13 @@ k_aca_block_post(const double* __restrict__ Ua, int M1, const double* __restrict
   __shared__ int stop_s, redirect_s, kend_s, next_s[ACA_BMAX], nnext_s;
   const int tid = threadIdx.x;
   if (tid == 0) st->post_ctr = 0;
-  // the partials of dot w summed by one warp (lanes over blocks, shuffle tree)
-  for (int w = warp; w < na * K; w += 8) {
-    double a = 0.0, c = 0.0;
-    for (int q = lane; q < nbu; q += 32) a += __ldcg(part + (long long)q * ldp + w);
-    for (int q = nbu + lane; q < nbu + nbv; q += 32) c += __ldcg(part + (long long)q * ldp + w);
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      c += __shfl_down_sync(0xffffffffu, c, o);
-    }
-    if (lane == 0) {
-      du[w] = a;
-      dv[w] = c;
-    }
+  // the partials of dot w summed by one thread (four accumulators, fixed order)
+  for (int w = tid; w < na * K; w += 256) {
+    double a[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < nbu; ++q) a[q & 3] += __ldcg(part + (long long)q * ldp + w);
+    for (int q = 0; q < nbv; ++q) c[q & 3] += __ldcg(part + (long long)(nbu + q) * ldp + w);
+    du[w] = (a[0] + a[1]) + (a[2] + a[3]);
+    dv[w] = (c[0] + c[1]) + (c[2] + c[3]);
   }
   __syncthreads();
   if (tid == 0) {
