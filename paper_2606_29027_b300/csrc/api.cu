@@ -276,7 +276,7 @@ slar_status slar_create(const slar_config* cfg, void* stream, slar_ctx** out) {
   A(c->E, (size_t)c->dx * c->NX); A(c->E1, (size_t)c->dx * c->NX);
   A(c->E2, (size_t)c->dx * c->NX); A(c->E3, (size_t)c->dx * c->NX);
   A(c->mom, (size_t)c->n_mom * c->NX);
-  A(c->lvec, (size_t)2 * 4 * 64 + 9 * 64 + 9 * 64 * 64);
+  A(c->lvec, (size_t)2 * 4 * 64 + 9 * 64 + 9 * 64 * 64 + 9 * 64);
   c->spec_len = (long long)2 * 24 * c->NX;
   A(c->spec, (size_t)c->spec_len);
   A(c->rho, (size_t)c->NX);

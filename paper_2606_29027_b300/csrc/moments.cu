@@ -63,45 +63,52 @@ __global__ void k_leaf_moments(GridDesc g, const double* U0, int r0, const doubl
   lv[((long long)m * 4 + p) * ldr + a] = s * g.h[mu];
 }
 
-// d = 4: m34[mom][q] = sum_mon sum_{c,e} B34[q][c][e] lv0[p1][c] lv1[p2][e];
-//        t12[mom][p] = sum_q Broot[p][q] m34[mom][q]
-// d = 2: t12[mom][a] = sum_b Broot[a][b] lv0[p1][b]
-__global__ void k_mom_root(int d, MomentTable tab, const double* B34, int r2, int r3, int r34,
-                           const double* Broot, int rl, const double* lv, int ldr, double* t12) {
-  __shared__ double m34[64];
+// d = 4, first stage: m34[mom][q] = sum_mon sum_{c,e} B34[q][c][e] lv0[p1][c] lv1[p2][e], one
+// CTA per (q, mom), a thread per c (the e-sum in four accumulators), the c-sum by shuffles:
+// B300 retires about two FP64 FMAs per clock per SM, so the r34 r2 r3 FMAs of a moment are
+// spread over r34 SMs and their dependent chains cut fourfold
+__global__ void k_mom_m34(MomentTable tab, const double* B34, int r2, int r3, const double* lv, int ldr,
+                          double* m34) {
+  __shared__ double red[2];
+  const int q = blockIdx.x, mom = blockIdx.y, c = threadIdx.x;   // 64 threads >= r2
+  double s = 0.0;
+  if (c < r2) {
+    const double* B = B34 + ((long long)q * r2 + c) * r3;
+    for (int mo = 0; mo < tab.nmon[mom]; ++mo) {
+      const double* l0 = lv + (0 * 4 + tab.e[mom][mo][0]) * ldr;
+      const double* l1 = lv + (1 * 4 + tab.e[mom][mo][1]) * ldr;
+      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int e = 0; e < r3; ++e) t[e & 3] += B[e] * l1[e];
+      s += l0[c] * ((t[0] + t[1]) + (t[2] + t[3]));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) m34[mom * 64 + q] = red[0] + red[1];
+}
+
+// d = 4, second stage: t12[mom][p] = sum_q Broot[p][q] m34[mom][q]
+__global__ void k_mom_t12(const double* Broot, int rl, int r34, const double* m34, double* t12) {
+  const int mom = blockIdx.x, p = threadIdx.x;
+  if (p >= rl) return;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = 0; q < r34; ++q) a[q & 3] += Broot[p * r34 + q] * m34[mom * 64 + q];
+  t12[mom * 64 + p] = (a[0] + a[1]) + (a[2] + a[3]);
+}
+
+// d = 2: t12[mom][a] = sum_b Broot[a][b] lv0[p1][b] (Broot is r0 x r1, the velocity leaf has
+// rank r1)
+__global__ void k_mom_root_1d(MomentTable tab, int r1, const double* Broot, int r0, const double* lv, int ldr,
+                              double* t12) {
   const int mom = blockIdx.x;
-  const int tid = threadIdx.x;
-  if (d == 4) {
-    for (int q = tid; q < r34; q += blockDim.x) {
-      double s = 0.0;
-      for (int mo = 0; mo < tab.nmon[mom]; ++mo) {
-        const double* l0 = lv + (0 * 4 + tab.e[mom][mo][0]) * ldr;
-        const double* l1 = lv + (1 * 4 + tab.e[mom][mo][1]) * ldr;
-        const double* B = B34 + (long long)q * r2 * r3;
-        for (int cc = 0; cc < r2; ++cc) {
-          double t = 0.0;
-          for (int e = 0; e < r3; ++e) t += B[cc * r3 + e] * l1[e];
-          s += l0[cc] * t;
-        }
-      }
-      m34[q] = s;
+  for (int a = threadIdx.x; a < r0; a += blockDim.x) {
+    double s = 0.0;
+    for (int mo = 0; mo < tab.nmon[mom]; ++mo) {
+      const double* l0 = lv + (0 * 4 + tab.e[mom][mo][0]) * ldr;
+      for (int b = 0; b < r1; ++b) s += Broot[a * r1 + b] * l0[b];
     }
-    __syncthreads();
-    for (int p = tid; p < rl; p += blockDim.x) {
-      double s = 0.0;
-      for (int q = 0; q < r34; ++q) s += Broot[p * r34 + q] * m34[q];
-      t12[mom * 64 + p] = s;
-    }
-  } else {
-    // rl = r0, Broot is r0 x r1 and the velocity leaf has rank r3 (passed as r34)
-    for (int a = tid; a < rl; a += blockDim.x) {
-      double s = 0.0;
-      for (int mo = 0; mo < tab.nmon[mom]; ++mo) {
-        const double* l0 = lv + (0 * 4 + tab.e[mom][mo][0]) * ldr;
-        for (int b = 0; b < r34; ++b) s += Broot[a * r34 + b] * l0[b];
-      }
-      t12[mom * 64 + a] = s;
-    }
+    t12[mom * 64 + a] = s;
   }
 }
 
@@ -181,6 +188,7 @@ slar_status compute_moments(slar_ctx* c, int slot, bool with_corr, double* out, 
   double* lv = c->lvec;              // [2][4][64]
   double* t12 = lv + 2 * 4 * 64;     // [9][64]
   double* Bt = t12 + MAXMOM * 64;    // [9][64*64]
+  double* m34 = Bt + MAXMOM * 64 * 64;   // [9][64]
   const int dx = c->dx;
   const int vl0 = dx, vl1 = dx + 1;
   dim3 g1((64 + 63) / 64, c->dv, 4);
@@ -188,7 +196,9 @@ slar_status compute_moments(slar_ctx* c, int slot, bool with_corr, double* out, 
                                   c->dv == 2 ? h.r[vl1] : 0, lv, ldr);
   CK(cudaGetLastError());
   if (c->d == 4) {
-    slar::count_launch(), k_mom_root<<<nmom, 64, 0, s>>>(4, tab, h.B34, h.r[2], h.r[3], h.r[5], h.Broot, h.r[4], lv, ldr, t12);
+    slar::count_launch(), k_mom_m34<<<dim3(h.r[5], nmom), 64, 0, s>>>(tab, h.B34, h.r[2], h.r[3], lv, ldr, m34);
+    CK(cudaGetLastError());
+    slar::count_launch(), k_mom_t12<<<nmom, 64, 0, s>>>(h.Broot, h.r[4], h.r[5], m34, t12);
     CK(cudaGetLastError());
     dim3 g2((h.r[0] * h.r[1] + 127) / 128, nmom);
     slar::count_launch(), k_mom_bt<<<g2, 128, 0, s>>>(h.B12, h.r[0], h.r[1], h.r[4], t12, Bt);
@@ -200,7 +210,7 @@ slar_status compute_moments(slar_ctx* c, int slot, bool with_corr, double* out, 
     CK(dgemm(0, 1, N0, N1, r1, 1.0, c->T1, r1, (long long)N0 * r1, h.U[1], r1, 0, 0.0, out, N1,
              (long long)c->NX, nmom, s));
   } else {
-    slar::count_launch(), k_mom_root<<<nmom, 64, 0, s>>>(2, tab, nullptr, 0, 0, h.r[1], h.Broot, h.r[0], lv, ldr, t12);
+    slar::count_launch(), k_mom_root_1d<<<nmom, 64, 0, s>>>(tab, h.r[1], h.Broot, h.r[0], lv, ldr, t12);
     CK(cudaGetLastError());
     dim3 g2((g.N[0] + 127) / 128, nmom);
     slar::count_launch(), k_mom_field_1d<<<g2, 128, 0, s>>>(h.U[0], g.N[0], h.r[0], t12, out, c->NX);
