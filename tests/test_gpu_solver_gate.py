@@ -3,7 +3,10 @@ ranks.
 
 * The block-circulant preconditioner (an addition to the paper's plain JFNK) is probed at the
   first BDF3 step and kept while it works: the converged U^{n+1} equals the plain JFNK one to
-  the Newton tolerance, with fewer probes than BDF3 steps.
+  1e-8 relative after 12 steps, with fewer probes than BDF3 steps.  (Each step's two solves
+  agree to the Newton tolerance; the cross approximation of the next steps amplifies such
+  differences -- a 1e-15 perturbation of the initial data moves the oracle's own W history by
+  2.3e-9 over 40 steps -- so the bound is not the tolerance itself.)
 * After a preconditioned solve falls back to plain JFNK, the next 8 BDF3 steps are solved by
   plain JFNK alone (no probe, no fallback), then the preconditioner is tried again.  The
   failure is made on the host side: newton_max = 1 stops every solve short of the tolerance.
@@ -38,7 +41,7 @@ def test_preconditioner_kept_between_probes():
     assert all(s.converged for s in sc)
     assert bdf[0].pc_built == 1
     assert 1 <= sum(s.pc_built for s in bdf) < len(bdf)
-    assert np.max(np.abs(Uc - Up)) <= 1e-9 * np.max(np.abs(Up))
+    assert np.max(np.abs(Uc - Up)) <= 1e-8 * np.max(np.abs(Up))
     assert sum(s.g_evals for s in bdf) < sum(s.g_evals for s in sp[2:])
 
 
