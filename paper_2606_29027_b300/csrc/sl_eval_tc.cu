@@ -77,7 +77,7 @@ template <int PC> __host__ __device__ constexpr int tc_sstages() { return PC == 
 template <int PC> __host__ __device__ constexpr int tc_acol(int node) { return 3 * tc_w<PC>() + node * 32 * PC; }
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;
 constexpr int TC_HEAD_BYTES = 2048;      // values and partial sums of the root
-constexpr int PRO_SMEM_BYTES = 32 * 12 * 8;    // prologue: stencil rows and weights of its 32 entries
+constexpr int PRO_SMEM_BYTES = 128 * 12 * 8;   // prologue: stencil rows and weights of up to 128 entries
 constexpr int TC_MIN_SMEM = 120 * 1024;  // one CTA per SM: the 512-column allocation never waits
 
 __host__ __device__ __forceinline__ int r16(int r) { return ((r + 15) / 16) * 16; }
@@ -417,19 +417,17 @@ __host__ __device__ __forceinline__ long long tc_abytes(int r1, int r3) {
 // scratch.  Otherwise into the A rows of the node (layout above): each lane splits its
 // column's value into PC BF16 pieces, even lanes pair them with the next lane's into words
 // and the first lane of each 8-column group gathers the group's four words into one 16-byte
-// store, columns r .. r16 - 1 zero.  A prologue CTA holds PRO_TILE entries, a quarter of a
-// tensor-core tile (a_off: its first row in the tile's A rows); its four warps take eight
-// rows each.
+// store, columns r .. r16 - 1 zero.  A prologue CTA holds ptile entries (32 or 128: a
+// quarter of a tensor-core tile or a whole one; a_off: its first row in the tile's A rows);
+// its four warps take eight rows per pass.
 constexpr int PRO_THREADS = 128;
-constexpr int PRO_TILE = 32;
 template <bool TO_C1, int PC>
 __device__ __forceinline__ void gather_rows(void* dst, const float* __restrict__ U, int r, int m, int nT,
-                                            const int* srow, const float* sw, int node, int a_off) {
+                                            const int* srow, const float* sw, int node, int a_off, int ptile) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rb16 = r16(r), ks = rb16 / 16;
   constexpr int RPI = 8;
-  static_assert(RPI * (PRO_THREADS / 32) == PRO_TILE, "one pass of the warps covers the tile");
-  for (int e0 = RPI * warp; e0 < PRO_TILE; e0 += RPI * (PRO_THREADS / 32)) {
+  for (int e0 = RPI * warp; e0 < ptile; e0 += RPI * (PRO_THREADS / 32)) {
     int u[RPI][3];   // row offsets into U (a leaf has at most 128 rows of r <= 64 columns)
     float w[RPI][3];
 #pragma unroll
@@ -474,8 +472,9 @@ __device__ __forceinline__ void gather_rows(void* dst, const float* __restrict__
   }
 }
 
-// Prologue of the tensor-core evaluator, one CTA per 32 entries (a quarter of a tensor-core
-// tile, so that a one-fibre launch of 16384 entries spreads over 512 CTAs): the feet, cells and
+// Prologue of the tensor-core evaluator, one CTA per ptile entries: 32 (a quarter of a
+// tensor-core tile, so that a one-fibre launch of 16384 entries spreads over 512 CTAs) while
+// the grid stays within two waves of four CTAs per SM, else 128: the feet, cells and
 // weights, the four leaf gathers, the BF16 split of c2 of both nodes into the A rows of
 // the tile and c1 of both nodes, all into global scratch.  A separate kernel so that these
 // latency-bound steps run at several CTAs per SM and overlap one another, while the
@@ -484,7 +483,7 @@ __device__ __forceinline__ void gather_rows(void* dst, const float* __restrict__
 template <bool DEV, int PC>
 __global__ void __launch_bounds__(PRO_THREADS, 4)   // 4 CTAs per SM: 592 >= the 512 CTAs of a 16384-entry fibre
 k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restrict__ P, EvalArgs a,
-              TcScratch sc) {
+              TcScratch sc, int ptile) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   HTView<float> ht;
   if (DEV) {
@@ -499,16 +498,16 @@ k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restr
   }
   if ((a.done && *a.done) || (a.skip && *a.skip)) return;
   if (a.kidx) a.pivot += *a.kidx;
-  // PRO_TILE entries from e0: rows a_off .. a_off + PRO_TILE - 1 of tensor-core tile `tile`
-  const long long e0 = (long long)blockIdx.x * PRO_TILE;
-  const long long tile = blockIdx.x / (TC_TILE / PRO_TILE);
+  // ptile entries from e0: rows a_off .. a_off + ptile - 1 of tensor-core tile `tile`
+  const long long e0 = (long long)blockIdx.x * ptile;
+  const long long tile = e0 / TC_TILE;
   const int a_off = (int)(e0 - tile * TC_TILE);
   const long long n_act = a.nact ? min(a.n, (long long)(*a.nact) * a.nper) : a.n;
   if (e0 >= n_act) return;
-  const int nT = (int)min((long long)PRO_TILE, n_act - e0);
+  const int nT = (int)min((long long)ptile, n_act - e0);
   const int tid = threadIdx.x;
-  float* sw = reinterpret_cast<float*>(smem_raw);                     // PRO_TILE x 12
-  int* srow = reinterpret_cast<int*>(sw + PRO_TILE * 12);             // PRO_TILE x 12
+  float* sw = reinterpret_cast<float*>(smem_raw);                     // ptile x 12
+  int* srow = reinterpret_cast<int*>(sw + TC_TILE * 12);              // ptile x 12
   if (tid < nT) {
     int idx[4];
     decode_tuple(g, a, e0 + tid, idx);
@@ -531,14 +530,18 @@ k_tc_prologue(GridDesc g, HTView<float> ht_arg, const EvalParams<float>* __restr
   unsigned char* At = sc.a + tile * tc_abytes<PC>(ht.r[1], ht.r[3]);
   float* c1 = sc.c1 + e0 * 128;
   // c1 of both nodes and the A rows (split c2) of both nodes, straight to the scratch
-  gather_rows<true, PC>(c1, ht.U[0], ht.r[0], 0, nT, srow, sw, 0, 0);
-  gather_rows<true, PC>(c1, ht.U[2], ht.r[2], 2, nT, srow, sw, 1, 0);
-  gather_rows<false, PC>(At, ht.U[1], ht.r[1], 1, nT, srow, sw, 0, a_off);
+  gather_rows<true, PC>(c1, ht.U[0], ht.r[0], 0, nT, srow, sw, 0, 0, ptile);
+  gather_rows<true, PC>(c1, ht.U[2], ht.r[2], 2, nT, srow, sw, 1, 0, ptile);
+  gather_rows<false, PC>(At, ht.U[1], ht.r[1], 1, nT, srow, sw, 0, a_off, ptile);
   gather_rows<false, PC>(At + (long long)TC_TILE * r16(ht.r[1]) * 2 * PC, ht.U[3], ht.r[3], 3, nT, srow, sw, 1,
-                         a_off);
+                         a_off, ptile);
 }
 
 size_t tc_prologue_smem(const int*) { return (size_t)PRO_SMEM_BYTES; }
+
+// entries per prologue CTA: 32 while the grid stays within two waves of four such CTAs per SM
+// on 148 SMs, else 128
+int tc_prologue_tile(long long n) { return (n + 31) / 32 <= 2 * 4 * 148 ? 32 : 128; }
 
 template <bool DEV, int PC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -1007,13 +1010,16 @@ cudaError_t launch_sl_eval_tc(const GridDesc& g, const HTView<float>& ht, const 
       a.idx = a0.idx + off * g.d;
       a.out = a0.out + off;
     }
-    const long long blocks = (a.n + TC_TILE - 1) / TC_TILE, pblocks = (a.n + PRO_TILE - 1) / PRO_TILE;
+    const int pt = tc_prologue_tile(a.n);
+    const long long blocks = (a.n + TC_TILE - 1) / TC_TILE, pblocks = (a.n + pt - 1) / pt;
     if (pieces == 3) {
-      slar::count_launch(), k_tc_prologue<false, 3><<<(unsigned)pblocks, PRO_THREADS, smp, s>>>(g, ht, nullptr, a, sc);
+      slar::count_launch(), k_tc_prologue<false, 3><<<(unsigned)pblocks, PRO_THREADS, smp, s>>>(g, ht, nullptr, a, sc,
+                                                                                             pt);
       slar::count_launch(), k_sl_eval_tc<false, 3><<<(unsigned)blocks, TC_THREADS, sm, s>>>(g, ht, corr, nullptr, a,
                                                                                            p12, p34, err, sc, broot);
     } else {
-      slar::count_launch(), k_tc_prologue<false, 2><<<(unsigned)pblocks, PRO_THREADS, smp, s>>>(g, ht, nullptr, a, sc);
+      slar::count_launch(), k_tc_prologue<false, 2><<<(unsigned)pblocks, PRO_THREADS, smp, s>>>(g, ht, nullptr, a, sc,
+                                                                                             pt);
       slar::count_launch(), k_sl_eval_tc<false, 2><<<(unsigned)blocks, TC_THREADS, sm, s>>>(g, ht, corr, nullptr, a,
                                                                                            p12, p34, err, sc, broot);
     }
@@ -1028,18 +1034,19 @@ cudaError_t launch_sl_eval_tc_dev(const GridDesc& g, const EvalParams<float>* P,
                                   const TcScratch& sc, cudaStream_t s) {
   const unsigned char* broot = static_cast<const unsigned char*>(broot_);
   if (g.d != 4 || a.n > sc.cap) return cudaErrorInvalidValue;
-  const long long blocks = (a.n + TC_TILE - 1) / TC_TILE, pblocks = (a.n + PRO_TILE - 1) / PRO_TILE;
+  const int pt = tc_prologue_tile(a.n);
+  const long long blocks = (a.n + TC_TILE - 1) / TC_TILE, pblocks = (a.n + pt - 1) / pt;
   const unsigned char* p12 = static_cast<const unsigned char*>(b12);
   const unsigned char* p34 = static_cast<const unsigned char*>(b34);
   const size_t smp = (size_t)PRO_SMEM_BYTES;
   if (pieces == 3) {
     slar::count_launch(), k_tc_prologue<true, 3><<<(unsigned)pblocks, PRO_THREADS, smp, s>>>(g, HTView<float>{}, P, a,
-                                                                                         sc);
+                                                                                         sc, pt);
     slar::count_launch(), k_sl_eval_tc<true, 3><<<(unsigned)blocks, TC_THREADS, sm, s>>>(
         g, HTView<float>{}, CorrView{}, P, a, p12, p34, err, sc, broot);
   } else {
     slar::count_launch(), k_tc_prologue<true, 2><<<(unsigned)pblocks, PRO_THREADS, smp, s>>>(g, HTView<float>{}, P, a,
-                                                                                         sc);
+                                                                                         sc, pt);
     slar::count_launch(), k_sl_eval_tc<true, 2><<<(unsigned)blocks, TC_THREADS, sm, s>>>(
         g, HTView<float>{}, CorrView{}, P, a, p12, p34, err, sc, broot);
   }
