@@ -743,12 +743,21 @@ k_aca_block_post(const double* __restrict__ Ua, int M1, const double* __restrict
   const int tid = threadIdx.x;
   if (tid == 0) st->post_ctr = 0;
   // the partials of dot w summed by one thread (four accumulators, fixed order)
+  auto sum4 = [&](const double* p0, int nb, int w) {   // partials nb apart by ldp, four chains
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int q = 0;
+    for (; q + 4 <= nb; q += 4) {
+      a0 += __ldcg(p0 + (long long)q * ldp + w);
+      a1 += __ldcg(p0 + (long long)(q + 1) * ldp + w);
+      a2 += __ldcg(p0 + (long long)(q + 2) * ldp + w);
+      a3 += __ldcg(p0 + (long long)(q + 3) * ldp + w);
+    }
+    for (; q < nb; ++q) a0 += __ldcg(p0 + (long long)q * ldp + w);
+    return (a0 + a1) + (a2 + a3);
+  };
   for (int w = tid; w < na * K; w += 256) {
-    double a[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int q = 0; q < nbu; ++q) a[q & 3] += __ldcg(part + (long long)q * ldp + w);
-    for (int q = 0; q < nbv; ++q) c[q & 3] += __ldcg(part + (long long)(nbu + q) * ldp + w);
-    du[w] = (a[0] + a[1]) + (a[2] + a[3]);
-    dv[w] = (c[0] + c[1]) + (c[2] + c[3]);
+    du[w] = sum4(part, nbu, w);
+    dv[w] = sum4(part + (long long)nbu * ldp, nbv, w);
   }
   __syncthreads();
   if (tid == 0) {

@@ -77,9 +77,16 @@ __global__ void k_mom_m34(MomentTable tab, const double* B34, int r2, int r3, co
     for (int mo = 0; mo < tab.nmon[mom]; ++mo) {
       const double* l0 = lv + (0 * 4 + tab.e[mom][mo][0]) * ldr;
       const double* l1 = lv + (1 * 4 + tab.e[mom][mo][1]) * ldr;
-      double t[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int e = 0; e < r3; ++e) t[e & 3] += B[e] * l1[e];
-      s += l0[c] * ((t[0] + t[1]) + (t[2] + t[3]));
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+      int e = 0;
+      for (; e + 4 <= r3; e += 4) {
+        t0 += B[e] * l1[e];
+        t1 += B[e + 1] * l1[e + 1];
+        t2 += B[e + 2] * l1[e + 2];
+        t3 += B[e + 3] * l1[e + 3];
+      }
+      for (; e < r3; ++e) t0 += B[e] * l1[e];
+      s += l0[c] * ((t0 + t1) + (t2 + t3));
     }
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -92,9 +99,18 @@ __global__ void k_mom_m34(MomentTable tab, const double* B34, int r2, int r3, co
 __global__ void k_mom_t12(const double* Broot, int rl, int r34, const double* m34, double* t12) {
   const int mom = blockIdx.x, p = threadIdx.x;
   if (p >= rl) return;
-  double a[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int q = 0; q < r34; ++q) a[q & 3] += Broot[p * r34 + q] * m34[mom * 64 + q];
-  t12[mom * 64 + p] = (a[0] + a[1]) + (a[2] + a[3]);
+  const double* b = Broot + p * r34;
+  const double* m = m34 + mom * 64;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int q = 0;
+  for (; q + 4 <= r34; q += 4) {
+    a0 += b[q] * m[q];
+    a1 += b[q + 1] * m[q + 1];
+    a2 += b[q + 2] * m[q + 2];
+    a3 += b[q + 3] * m[q + 3];
+  }
+  for (; q < r34; ++q) a0 += b[q] * m[q];
+  t12[mom * 64 + p] = (a0 + a1) + (a2 + a3);
 }
 
 // d = 2: t12[mom][a] = sum_b Broot[a][b] lv0[p1][b] (Broot is r0 x r1, the velocity leaf has
