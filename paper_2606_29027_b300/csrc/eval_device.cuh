@@ -345,6 +345,89 @@ __device__ __forceinline__ void trace_disp_ft(const GridDesc& g, const float* E,
   }
 }
 
+// Both (DX) components of a spatial field at p for the FP32 paths' FP64 re-trace: the same
+// IEEE operation sequence per component as interp_spatial<3, true> (so bit-identical
+// values), with the cells and weights computed once and the two components' chains side by
+// side -- the re-trace's dependent FP64 latency is what a prologue warp waits for.
+template <int DX>
+__device__ __forceinline__ void interp_vec_rt(const GridDesc& g, const double* E, const double* p, double* out) {
+  const long long NX = g.NX;
+  int r0[3], r1[3];
+  double w0[3], w1[3];
+  cell_weights<3, true>(g, 0, p[0], r0, w0);
+  if constexpr (DX == 1) {
+    double acc = 0.0;
+#pragma unroll
+    for (int s0 = 0; s0 < 3; ++s0) acc = dadd(acc, dmul(w0[s0], E[r0[s0]]));
+    out[0] = acc;
+  } else {
+    cell_weights<3, true>(g, 1, p[1], r1, w1);
+    const int N1 = g.N[1];
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int s0 = 0; s0 < 3; ++s0)
+#pragma unroll
+      for (int s1 = 0; s1 < 3; ++s1) {
+        const double ww = dmul(w0[s0], w1[s1]);
+        const long long o = (long long)r0[s0] * N1 + r1[s1];
+        a0 = dadd(a0, dmul(ww, E[o]));
+        a1 = dadd(a1, dmul(ww, E[NX + o]));
+      }
+    out[0] = a0;
+    out[1] = a1;
+  }
+}
+
+// trace_foot<3, true> (the same operations, hence the same foot) with the field
+// interpolated by interp_vec_rt
+template <int DX>
+__device__ __forceinline__ void trace_foot_rt(const GridDesc& g, const double* E, double tau, int euler,
+                                              const int* idx, double* foot) {
+  double x[DX], v[DX];
+#pragma unroll
+  for (int m = 0; m < DX; ++m) {
+    x[m] = centre(g, m, idx[m]);
+    v[m] = centre(g, DX + m, idx[DX + m]);
+  }
+  if (euler) {
+    double e[DX];
+    interp_vec_rt<DX>(g, E, x, e);
+#pragma unroll
+    for (int m = 0; m < DX; ++m) {
+      foot[m] = dsub(x[m], dmul(v[m], tau));
+      foot[DX + m] = dadd(v[m], dmul(e[m], tau));
+    }
+    return;
+  }
+  const double h = tau;
+  const double half = h / 2.0, two_h = 2.0 * h, sixth = __ddiv_rn(h, 6.0);
+  double k1x[DX], k1v[DX], x2[DX], v2[DX], k2x[DX], k2v[DX], x3[DX], v3[DX], k3x[DX], k3v[DX];
+#pragma unroll
+  for (int m = 0; m < DX; ++m) k1x[m] = -v[m];
+  interp_vec_rt<DX>(g, E, x, k1v);
+#pragma unroll
+  for (int m = 0; m < DX; ++m) {
+    x2[m] = dadd(x[m], dmul(half, k1x[m]));
+    v2[m] = dadd(v[m], dmul(half, k1v[m]));
+  }
+#pragma unroll
+  for (int m = 0; m < DX; ++m) k2x[m] = -v2[m];
+  interp_vec_rt<DX>(g, E, x2, k2v);
+#pragma unroll
+  for (int m = 0; m < DX; ++m) {
+    x3[m] = dadd(dsub(x[m], dmul(h, k1x[m])), dmul(two_h, k2x[m]));
+    v3[m] = dadd(dsub(v[m], dmul(h, k1v[m])), dmul(two_h, k2v[m]));
+  }
+#pragma unroll
+  for (int m = 0; m < DX; ++m) k3x[m] = -v3[m];
+  interp_vec_rt<DX>(g, E, x3, k3v);
+#pragma unroll
+  for (int m = 0; m < DX; ++m) {
+    foot[m] = dadd(x[m], dmul(sixth, dadd(dadd(k1x[m], dmul(4.0, k2x[m])), k3x[m])));
+    foot[DX + m] = dadd(v[m], dmul(sixth, dadd(dadd(k1v[m], dmul(4.0, k2v[m])), k3v[m])));
+  }
+}
+
 // Foot, cells and weights of one entry in the FP32 paths (2 DX dimensions): the cells and
 // weights of the FP32 foot, unless it lies within a guard of a cell face in some dimension
 // m, in which case the entry takes the FP64 foot (E64 given) and its cells and weights
@@ -375,7 +458,7 @@ __device__ __forceinline__ void foot_cells_ft(const GridDesc& g, const float* E3
   }
   if (near && E64) {
     double fd[4];
-    trace_foot<3, true>(g, E64, tau, euler, idx, fd);
+    trace_foot_rt<DX>(g, E64, tau, euler, idx, fd);
 #pragma unroll
     for (int m = 0; m < D; ++m) {
       double wd[3];
