@@ -41,8 +41,8 @@ FP64_PEAK_TFLOPS = 1.25                              # nominal B300 FP64 (recipe
 # DRAM bytes (read + write) per launch of the entry evaluator on this workload, by entry
 # precision, from an ncu capture (cold cache); None where no capture of the current kernel
 # exists
-EVAL_TRAFFIC_BYTES = {"fp32": 270888.0, "fp64": None}
-EVAL_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over 32 launches of "
+EVAL_TRAFFIC_BYTES = {"fp32": 295542.0, "fp64": None}
+EVAL_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over 26 launches of "
                        "k_sl_eval_dev<float> in the warm-up steps of this workload (block cross "
                        "approximation b = 2; cold cache under ncu)")
 
