@@ -35,6 +35,11 @@ HSVD truncation of Supp. B.1.  The reading implemented here (deterministic):
    row of largest residual.
 2. The factors A ~ U V^T are embedded exactly as an HT: d = 2: leaves U, V and root I;
    d = 4: identity leaves, B12[a,b,p] = U[(a,b),p], B34[c,e,q] = V[(c,e),q], root I.
+2'. (Option, d = 4.)  Leaf bases of rank r_mu <= N_mu instead of the identity: each leaf
+   unfolding of the cross factors -- one side weighted by the other side's triangular QR
+   factor, so that its norm is ||A||_F -- is compressed by greedy column-pivoted QR to a
+   residual of eps / (2 sqrt(2d - 3)) of ||A||_F (``compress_leaves``); the truncation then
+   eigen-solves leaf Gram matrices of order r_mu instead of N_mu.
 3. HSVD truncation (``ht.truncate``) with eps and the rank cap gives the new HT, whose
    leaf columns 0 are the leading mode singular vectors needed by the LoMaC weight.
 
@@ -324,12 +329,83 @@ def embed(U: np.ndarray, V: np.ndarray, N) -> htmod.HT:
                     Broot=np.eye(k), B12=B12.copy(), B34=B34.copy())
 
 
+def qrcp_basis(M: np.ndarray, tol: float):
+    """Orthonormal basis of columns of M (n x m, in memory) chosen greedily by column
+    pivoting (Businger-Golub): each step takes the column of largest residual norm (ties as
+    in the cross approximation: within a relative 1e-10 of the maximum, the lowest index),
+    normalises its residual against the basis so far (two Gram-Schmidt passes), and stops
+    once the residual Frobenius norm ||M - Q Q^T M||_F is at most tol or the basis has
+    min(n, m) columns.  Returns (Q (n x r), chosen column indices)."""
+    n, m = M.shape
+    Rm = np.array(M, dtype=np.float64, copy=True)
+    Q = np.zeros((n, 0))
+    cols = []
+    used = np.zeros(m, dtype=bool)
+    while Q.shape[1] < min(n, m):
+        norms2 = np.einsum("ij,ij->j", Rm, Rm)
+        if math.sqrt(float(norms2.sum())) <= tol:
+            break
+        j = argmax_tie(np.sqrt(norms2), used)
+        q = Rm[:, j].copy()
+        for _ in range(2):
+            q = q - Q @ (Q.T @ q)
+        nq = float(np.linalg.norm(q))
+        if nq == 0.0:
+            break
+        q = q / nq
+        Q = np.concatenate([Q, q[:, None]], axis=1)
+        used[j] = True
+        cols.append(int(j))
+        Rm = Rm - np.outer(q, q @ Rm)
+    return Q, cols
+
+
+def compress_leaves(U: np.ndarray, V: np.ndarray, N, eps: float) -> htmod.HT:
+    """HT with orthonormal leaf bases of rank r_mu <= N_mu for A = U V^T on the d = 4 root
+    split (step 2' of the module docstring): the identity leaves of ``embed`` replaced by
+    bases of the leaf unfoldings of the cross factors, chosen by ``qrcp_basis``.
+
+    With V = Q_V R_V, W = U R_V^T (so A = W Q_V^T and ||W||_F = ||A||_F): the mode-x1 and
+    mode-x2 unfoldings of W (as N0 x N1 x K) give Q0, Q1 at tolerance eps_l ||A||_F each, and
+    C12 = W x_0 Q0^T x_1 Q1^T.  With C12 (as r0 r1 x K) = Q_C R_C and Z = Q_V R_C^T (so the
+    compressed A' = (Q0 (x) Q1) Q_C Z^T and ||Z||_F = ||A'||_F): the mode-v1 and mode-v2
+    unfoldings of Z give Q2, Q3, and C34 = Z x_0 Q2^T x_1 Q3^T.  The HT: leaves Q0..Q3,
+    B12 = Q_C (r0, r1, K), B34 = C34 (r2, r3, K), root I_K.  Each projection removes at most
+    eps_l of the norm it acts on, so ||A - HT|| <= ~4 eps_l ||A||_F; eps_l =
+    eps / (2 sqrt(2d - 3)) keeps that below the eps of the truncation that follows."""
+    if len(N) != 4:
+        raise ValueError("leaf compression is for d = 4 (d = 2 leaves are the factors)")
+    K = U.shape[1]
+    n0, n1, n2, n3 = (int(x) for x in N)
+    eps_l = eps / (2.0 * math.sqrt(5.0))
+    if K == 0:
+        return htmod.HT(U=[np.zeros((n, 0)) for n in (n0, n1, n2, n3)], Broot=np.zeros((0, 0)),
+                        B12=np.zeros((0, 0, 0)), B34=np.zeros((0, 0, 0)))
+    QV, RV = np.linalg.qr(V)
+    W = (U @ RV.T).reshape(n0, n1, K)
+    tol = eps_l * float(np.linalg.norm(W))
+    Q0, _ = qrcp_basis(W.reshape(n0, n1 * K), tol)
+    Q1, _ = qrcp_basis(np.transpose(W, (1, 0, 2)).reshape(n1, n0 * K), tol)
+    C12 = np.einsum("abk,ax,by->xyk", W, Q0, Q1)
+    r0, r1 = Q0.shape[1], Q1.shape[1]
+    QC, RC = np.linalg.qr(C12.reshape(r0 * r1, K))
+    kk = QC.shape[1]
+    Z = (QV @ RC.T).reshape(n2, n3, kk)
+    tol2 = eps_l * float(np.linalg.norm(Z))
+    Q2, _ = qrcp_basis(Z.reshape(n2, n3 * kk), tol2)
+    Q3, _ = qrcp_basis(np.transpose(Z, (1, 0, 2)).reshape(n3, n2 * kk), tol2)
+    C34 = np.einsum("cek,cx,ey->xyk", Z, Q2, Q3)
+    return htmod.HT(U=[Q0, Q1, Q2, Q3], Broot=np.eye(kk), B12=QC.reshape(r0, r1, kk), B34=C34)
+
+
 def htaca(entry_fn: Callable[[np.ndarray], np.ndarray], N, eps: float, cap: int,
-          pivots=None, return_info: bool = False, block: int = 1):
+          pivots=None, return_info: bool = False, block: int = 1, leaf_compress: bool = False):
     """Build the HT of the tensor whose entries are entry_fn(idx (S, d)) from sampled row
     and column fibres of the root-split matricisation, then truncate (module docstring).
     block > 1: the block cross approximation (``aca_block``) with that many fibres per step;
-    replayed pivots give the same cross approximation whatever the blocking."""
+    replayed pivots give the same cross approximation whatever the blocking.  leaf_compress
+    (d = 4): orthonormal leaf bases of rank r_mu from the cross factors (``compress_leaves``)
+    instead of identity leaves of order N_mu before the truncation."""
     d = len(N)
     half = d // 2
     Nl, Nr = N[:half], N[half:]
@@ -355,7 +431,10 @@ def htaca(entry_fn: Callable[[np.ndarray], np.ndarray], N, eps: float, cap: int,
         res = aca_block(rows_fn, cols_fn, M1, M2, eps, cap, block)
     else:
         res = aca(row_fn, col_fn, M1, M2, eps, cap, pivots)
-    full = embed(res["U"], res["V"], N)
+    if leaf_compress and d == 4:
+        full = compress_leaves(res["U"], res["V"], N, eps)
+    else:
+        full = embed(res["U"], res["V"], N)
     out, tinfo = htmod.truncate(full, eps, cap, return_info=True)
     if return_info:
         info = dict(aca_rank=res["U"].shape[1], pivots=list(zip(res["I"], res["J"])),
